@@ -1,0 +1,181 @@
+/*
+ * PointEMRay CPU oracle (TEST INFRASTRUCTURE ONLY -- only tests/, the smoke
+ * check and the benchmark's CPU-baseline leg load this library).
+ *
+ * A plain, slow, brute-force statement of the SBR-on-points method of
+ * PointEMRay (arXiv 2408.15583), written from the paper:
+ *   - geometry (GFB, fusion, bounce tracing) in oracle_core.h, compiled twice:
+ *     or_*_f32 (FP32 geometry, the bit-exact target of the GPU path) and
+ *     or_*_f64 (FP64 physics reference);
+ *   - the physical-optics field sum of Eq. 5-14 here, always in FP64 with
+ *     Neumaier-compensated sums over rays.
+ * Shares no code with the CUDA path.  Build: gcc -O2 -ffp-contract=off
+ * (no fast-math) -fopenmp -shared -fPIC.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+  double o[3], u[3], v[3], d[3];
+  double pitch;
+  int32_t W, H;
+} or_view;
+
+#define R float
+#define SFX(x) x##_f32
+#define SQRT sqrtf
+#define FLOOR floorf
+#include "oracle_core.h"
+#undef R
+#undef SFX
+#undef SQRT
+#undef FLOOR
+
+#define R double
+#define SFX(x) x##_f64
+#define SQRT sqrt
+#define FLOOR floor
+#include "oracle_core.h"
+#undef R
+#undef SFX
+#undef SQRT
+#undef FLOOR
+
+int or_abi_version(void) { return 1; }
+
+void or_gfb(int fp64, const or_view *v, const float *pos, const float *nrm,
+            const float *rad, int64_t n, int mode, double delta,
+            const int64_t *pix, int64_t npix, double *depth, int64_t *idx,
+            double *nrm_out) {
+  if (fp64)
+    gfb_f64(v, pos, nrm, rad, n, mode, delta, pix, npix, depth, idx, nrm_out);
+  else
+    gfb_f32(v, pos, nrm, rad, n, mode, delta, pix, npix, depth, idx, nrm_out);
+}
+
+int64_t or_aggregate(int fp64, int nv, const or_view *views, const double *depth,
+                     const double *nrm, const uint8_t *mask, double tau,
+                     const double *bmin, double inv_vox, int G, int64_t *out_id,
+                     double *out_c, double *out_n, double *out_r,
+                     int32_t *out_count, uint8_t *keep) {
+  if (fp64)
+    return aggregate_f64(nv, views, depth, nrm, mask, tau, bmin, inv_vox, G,
+                         out_id, out_c, out_n, out_r, out_count, keep);
+  return aggregate_f32(nv, views, depth, nrm, mask, tau, bmin, inv_vox, G, out_id,
+                       out_c, out_n, out_r, out_count, keep);
+}
+
+void or_trace(int fp64, const or_view *v, const int64_t *pix, int64_t nr,
+              const double *first_t, const int64_t *first_idx,
+              const double *first_n, const double *sc, const double *sn,
+              const double *sr, const int64_t *sid, int64_t ns, int mb, double eps,
+              double r_ov, int do_shadow, int32_t *M, int64_t *ids, double *p,
+              double *n, double *k, double *u, double *vv, double *path,
+              uint8_t *psi) {
+  if (fp64)
+    trace_f64(v, pix, nr, first_t, first_idx, first_n, sc, sn, sr, sid, ns, mb,
+              eps, r_ov, do_shadow, M, ids, p, n, k, u, vv, path, psi);
+  else
+    trace_f32(v, pix, nr, first_t, first_idx, first_n, sc, sn, sr, sid, ns, mb,
+              eps, r_ov, do_shadow, M, ids, p, n, k, u, vv, path, psi);
+}
+
+/* ---------------------------------------------------------------------------
+ * Physical optics (Sec. II-B, II-C).
+ * ------------------------------------------------------------------------- */
+
+static const double OR_C0 = 299792458.0;
+static const double OR_PI = 3.14159265358979323846;
+
+static void cross3(const double *a, const double *b, double *c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double *a, const double *b) {
+  return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+/* sinc(x) = sin(x)/x, sinc(0) = 1: the unnormalised sinc that results from
+ * integrating exp(-j q u) over an interval of length U (Eq. 10-11). */
+static double sinc(double x) { return x == 0.0 ? 1.0 : sin(x) / x; }
+
+/* Neumaier-compensated accumulator. */
+typedef struct {
+  double s, c;
+} or_acc;
+static void acc_add(or_acc *a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x))
+    a->c += (a->s - t) + x;
+  else
+    a->c += (x - t) + a->s;
+  a->s = t;
+}
+
+/* Eq. 14 without the common factor -j eta0 k0 / (2 pi):
+ *   Sigma(f, pol) = sum_l Phi_l Psi_l |u' x v'| sinc(q.u'/2) sinc(q.v'/2)
+ *                   [(n x h) x ks] x ks exp(-j k (d - ks . p))
+ * with q = k (k_in - ks) and u', v' from Eq. 12-13 (k_in is the ray's
+ * direction of travel into its last hit).  Two transmit polarisations: for a
+ * screen frame (u_hat, v_hat, w_hat) with propagation -w_hat, the electric
+ * field along theta_hat = u_hat (V) has magnetic polarisation -v_hat and the
+ * one along phi_hat = v_hat (H) has +u_hat; both are carried by the
+ * propagated tube vectors, so h_V = -v/|v| and h_H = u/|u|.
+ * Output E[obs][f][pol(V,H)][xyz][re,im]. */
+void or_po_field(int64_t nr, const double *p, const double *n, const double *k,
+                 const double *u, const double *v, const double *path,
+                 const uint8_t *use, int nf, const double *freqs, int nobs,
+                 const double *ks_dirs, double *E) {
+  for (int o = 0; o < nobs; ++o) {
+    const double *ks = ks_dirs + 3 * o;
+    for (int f = 0; f < nf; ++f) {
+      double kw = 2.0 * OR_PI * freqs[f] / OR_C0;
+      or_acc acc[2][3][2];
+      memset(acc, 0, sizeof(acc));
+      for (int64_t l = 0; l < nr; ++l) {
+        if (!use[l]) continue;
+        const double *pl = p + 3 * l, *nl = n + 3 * l, *kl = k + 3 * l;
+        const double *ul = u + 3 * l, *vl = v + 3 * l;
+        double nk = dot3(nl, kl);
+        if (nk == 0.0) continue;
+        double up[3], vp[3], nu = dot3(nl, ul) / nk, nv = dot3(nl, vl) / nk;
+        for (int c = 0; c < 3; ++c) {
+          up[c] = ul[c] - kl[c] * nu;
+          vp[c] = vl[c] - kl[c] * nv;
+        }
+        double cr[3];
+        cross3(up, vp, cr);
+        double area = sqrt(dot3(cr, cr));
+        double q[3];
+        for (int c = 0; c < 3; ++c) q[c] = kw * (kl[c] - ks[c]);
+        double amp = area * sinc(0.5 * dot3(q, up)) * sinc(0.5 * dot3(q, vp));
+        double ph = kw * (path[l] - dot3(ks, pl));
+        double cre = cos(ph), cim = -sin(ph);
+        double lu = sqrt(dot3(ul, ul)), lv = sqrt(dot3(vl, vl));
+        double h[2][3];
+        for (int c = 0; c < 3; ++c) {
+          h[0][c] = -vl[c] / lv; /* V: E along theta_hat */
+          h[1][c] = ul[c] / lu;  /* H: E along phi_hat   */
+        }
+        for (int pol = 0; pol < 2; ++pol) {
+          double a[3], b[3], vec[3];
+          cross3(nl, h[pol], a);
+          cross3(a, ks, b);
+          cross3(b, ks, vec);
+          for (int c = 0; c < 3; ++c) {
+            acc_add(&acc[pol][c][0], amp * vec[c] * cre);
+            acc_add(&acc[pol][c][1], amp * vec[c] * cim);
+          }
+        }
+      }
+      for (int pol = 0; pol < 2; ++pol)
+        for (int c = 0; c < 3; ++c)
+          for (int ri = 0; ri < 2; ++ri)
+            E[((((int64_t)o * nf + f) * 2 + pol) * 3 + c) * 2 + ri] =
+                acc[pol][c][ri].s + acc[pol][c][ri].c;
+    }
+  }
+}

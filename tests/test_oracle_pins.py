@@ -1,0 +1,518 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics
+fix, never against the oracle's own formulas retyped.
+
+Pins used: hand-worked intersection cases (counts and depths read off the
+geometry), Eq. 22 values at chosen angles, the edge rule on a hand-drawn mask,
+the Eq. 23 selection/blend on a two-splat case worked by hand, the epsilon
+rule, the mirror paths of a dihedral and a trihedral, the textbook PO
+plate pattern (4 pi A^2/lambda^2) cos^2(theta) sinc^2(k a sin(theta)), the
+parallelogram PO integral, the exact PO backscatter of a sphere, the phase
+convention under translation, f^2 scaling, and the realised-aperture forms of
+the dihedral and trihedral RCS.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+C0 = scenes.C0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def down_view(W, H, pitch, z=5.0):
+    """Screen at height z looking down -z; u = x, v = y."""
+    return oracle.View(o=np.array([0.0, 0.0, z]), u=np.array([1.0, 0.0, 0.0]),
+                       v=np.array([0.0, 1.0, 0.0]), d=np.array([0.0, 0.0, -1.0]),
+                       pitch=pitch, W=W, H=H)
+
+
+def mk_scene(pos, nrm, rad):
+    return scenes.Scene(pos=np.asarray(pos, np.float32), nrm=np.asarray(nrm, np.float32),
+                        rad=np.asarray(rad, np.float32))
+
+
+# ----------------------------------------------------------------------------
+# a2/a3: GFB (Alg. 1)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_gfb_single_disk_handmade(mode):
+    # unit disk at the origin; 8x8 pixels of pitch 0.5 => centres at
+    # +-0.25, +-0.75, ...; exactly 12 centres lie within radius 1.
+    sc = mk_scene([[0, 0, 0]], [[0, 0, -1]], [1.0])
+    g = oracle.gfb(sc, down_view(8, 8, 0.5), mode)
+    hit = g.idx >= 0
+    assert hit.sum() == 12
+    assert np.all(g.depth[hit] == 5.0)
+    assert np.all(np.isinf(g.depth[~hit]))
+    # the stored normal is turned to face the view (n . d < 0)
+    assert np.all(g.nrm[hit] == np.array([0.0, 0.0, 1.0]))
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_gfb_nearest_and_tie_break(mode):
+    # A at z=0 (idx 0), B and its duplicate C at z=1 (idx 1, 2): B wins
+    # (nearest; equal depth -> smaller index), depth 4.
+    sc = mk_scene([[0, 0, 0], [0, 0, 1], [0, 0, 1]], [[0, 0, 1]] * 3, [10.0] * 3)
+    g = oracle.gfb(sc, down_view(4, 4, 0.5), mode)
+    assert np.all(g.idx == 1)
+    assert np.all(g.depth == 4.0)
+    k = g.keys()
+    assert np.all(k == ((np.uint64(np.float32(4.0).view(np.uint32)) << np.uint64(32)) | np.uint64(1)))
+
+
+@pytest.mark.parametrize("mode,tol", [("fp32", 3e-6), ("fp64", 2e-7)])
+def test_gfb_tilted_plate_depth_is_ray_plane(mode, tol):
+    # every surfel lies in the plane z = 0.3 x + 0.1 y with the plane's
+    # normal, so any hit's depth is the ray-plane distance (up to the FP32
+    # rounding of the stored positions).
+    rng = np.random.default_rng(5)
+    xy = rng.uniform(-0.5, 0.5, size=(3000, 2))
+    z = 0.3 * xy[:, 0] + 0.1 * xy[:, 1]
+    n = np.array([-0.3, -0.1, 1.0]) / math.sqrt(1.1)
+    sc = mk_scene(np.c_[xy, z], np.tile(n, (3000, 1)), np.full(3000, 0.03))
+    v = oracle.view_from_angles(30.0, 20.0, [0, 0, 0], 0.8, 40, 40, mode)
+    g = oracle.gfb(sc, v, mode)
+    hit = g.idx >= 0
+    assert hit.sum() > 300
+    j, i = np.divmod(np.arange(40 * 40), 40)
+    a = ((i + 0.5) - 20) * v.pitch
+    b = ((j + 0.5) - 20) * v.pitch
+    o = v.o[None] + a[:, None] * v.u[None] + b[:, None] * v.v[None]
+    # ray-plane: n.(o + t d) = 0
+    t = -(o @ n) / (v.d @ n)
+    assert np.max(np.abs(g.depth[hit] - t[hit]) / t[hit]) < tol
+
+
+def test_gfb_sphere_normals_are_radial():
+    sc = scenes.sphere(5000, 1.0)
+    v = oracle.view_from_angles(70.0, 10.0, [0, 0, 0], 1.05, 48, 48, "fp64")
+    g = oracle.gfb(sc, v, "fp64")
+    hit = g.idx >= 0
+    j, i = np.divmod(np.arange(48 * 48), 48)
+    a = ((i + 0.5) - 24) * v.pitch
+    b = ((j + 0.5) - 24) * v.pitch
+    o = v.o[None] + a[:, None] * v.u[None] + b[:, None] * v.v[None]
+    x = o[hit] + g.depth[hit][:, None] * v.d[None]
+    radial = x / np.linalg.norm(x, axis=1, keepdims=True)
+    ang = np.arccos(np.clip((radial * g.nrm[hit]).sum(1), -1, 1))
+    # the hit lies on a tangent disk within R of its centre: angle <~ R/a
+    assert np.max(ang) < 1.2 * float(sc.rad.max())
+    # and the normal faces the view
+    assert np.all(g.nrm[hit] @ v.d < 0)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_gfb_tube_mode_handmade(mode):
+    # 4x4 pixels, pitch 0.5; P0 on the axis of pixel (0.25, 0.25) at depth 5,
+    # P1 0.05 off that axis but 1 m closer: both inside delta = 0.1, P1 is
+    # nearer the tube origin => depth = |P1 - o| = sqrt(0.05^2 + 4^2).
+    sc = mk_scene([[0.25, 0.25, 0.0], [0.25, 0.30, 1.0]], [[0, 0, 1]] * 2, [0.0, 0.0])
+    g = oracle.gfb(sc, down_view(4, 4, 0.5), mode, tube=True, delta=0.1)
+    hit = np.flatnonzero(g.idx >= 0)
+    assert list(hit) == [2 * 4 + 2]
+    assert g.idx[hit[0]] == 1
+    assert abs(g.depth[hit[0]] - math.sqrt(0.05 ** 2 + 16.0)) < 1e-6
+
+
+def test_gfb_fp32_and_fp64_agree():
+    sc = scenes.sphere(4000, 1.0)
+    v32 = oracle.view_from_angles(50.0, 30.0, [0, 0, 0], 1.05, 64, 64, "fp32")
+    g32 = oracle.gfb(sc, v32, "fp32")
+    g64 = oracle.gfb(sc, v32, "fp64")
+    same = g32.idx == g64.idx
+    assert same.mean() > 0.995
+    both = same & (g32.idx >= 0)
+    # FP32 cancellation in (c - o) . n / (d . n) grows as d . n -> 0
+    assert np.max(np.abs(g32.depth[both] - g64.depth[both]) / g64.depth[both]) < 2e-5
+
+
+# ----------------------------------------------------------------------------
+# a4: edge filter, fusion, Eq. 22
+# ----------------------------------------------------------------------------
+
+def _handmade_gfb(view, depth, nrm, mask):
+    W, H = view.W, view.H
+    return oracle.Gfb(depth=np.asarray(depth, np.float64).ravel(),
+                      idx=np.where(np.asarray(mask).ravel() > 0, 0, -1).astype(np.int64),
+                      nrm=np.asarray(nrm, np.float64).reshape(W * H, 3), view=view, pix=None)
+
+
+def _exact_fuse(bmin_z=-0.0625):
+    # voxel = 0.125 m, grid origin at -0.3125 so pixel centres (multiples of
+    # 0.125) fall in the middle of distinct voxels.
+    return oracle.FuseParams(tau=3.0, bmin=np.array([-0.3125, -0.3125, bmin_z]),
+                             inv_vox=8.0, G=256)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_eq22_radius_values(mode):
+    L = 0.125
+    v = down_view(5, 5, L)
+    cases = {0.0: math.sqrt(2) * L,                      # s = 1
+             60.0: 2.0 * L,                              # s = sqrt(2)
+             85.0: 3.535 * L,                            # s = 3.39 >= 2.5
+             math.degrees(math.acos(0.165)): math.sqrt(2) * L * math.sqrt(1 / 0.165)}
+    for alpha, R_expect in cases.items():
+        n = np.array([math.sin(math.radians(alpha)), 0.0, math.cos(math.radians(alpha))])
+        n = n.astype(np.float32).astype(np.float64)
+        g = _handmade_gfb(v, np.full(25, 5.0), np.tile(n, (25, 1)), np.ones(25))
+        s = oracle.aggregate([g], _exact_fuse(), mode)
+        # only the 3x3 interior survives the edge rule; one splat per pixel
+        assert list(s.id) == [6, 7, 8, 11, 12, 13, 16, 17, 18]
+        assert np.all(s.count == 1)
+        assert np.allclose(s.r, R_expect, rtol=2e-7), (alpha, s.r[0], R_expect)
+        # centres are the pixels' surface points (z = 0)
+        assert np.all(s.c[:, 2] == 0.0)
+        assert np.allclose(s.c[:, 0], np.tile([-0.125, 0.0, 0.125], 3))
+
+
+def test_eq22_continuity_at_2_5():
+    # sqrt(2) * 2.5 = 3.5355...; the paper caps with 3.535 L (Eq. 22)
+    L = 0.125
+    v = down_view(5, 5, L)
+    for cosv, R_expect in ((1 / 2.5 ** 2 * 1.0001, math.sqrt(2) * L * math.sqrt(1 / (1 / 2.5 ** 2 * 1.0001))),
+                           (1 / 2.5 ** 2 * 0.9999, 3.535 * L)):
+        n = np.array([math.sqrt(1 - cosv ** 2), 0.0, cosv]).astype(np.float32).astype(np.float64)
+        g = _handmade_gfb(v, np.full(25, 5.0), np.tile(n, (25, 1)), np.ones(25))
+        s = oracle.aggregate([g], _exact_fuse(), "fp64")
+        assert abs(s.r[0] - R_expect) < 2e-4 * L
+
+
+def test_edge_filter_handmade():
+    # 6x6, a hole at (i=2, j=2), depth 5 for i<=3 and 6 for i>=4
+    # (jump 1 > 3 L = 0.375).  Border pixels, the hole's 4-neighbours and both
+    # sides of the jump are edges; the survivors were worked out by hand.
+    L = 0.125
+    v = down_view(6, 6, L)
+    mask = np.ones((6, 6))
+    mask[2, 2] = 0
+    depth = np.where(np.arange(6)[None, :] >= 4, 6.0, 5.0) * np.ones((6, 1))
+    g = _handmade_gfb(v, depth, np.tile([0, 0, 1.0], (36, 1)), mask)
+    s = oracle.aggregate([g], _exact_fuse(-2.0), "fp64")
+    assert sorted(np.flatnonzero(s.keep)) == [7, 19, 25, 26]
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_fusion_average_over_views(mode):
+    # two views with the same frame; view 1 sees the surface 1/32 m lower and
+    # with flipped normals.  Every voxel gets one contributor per view: count 2,
+    # centre z = the mean (-1/64), normal = the owner's (flips undone), owner =
+    # the view-0 pixel.
+    L = 0.125
+    v0 = down_view(5, 5, L)
+    v1 = down_view(5, 5, L)
+    n = np.array([0.0, 0.6, 0.8])
+    g0 = _handmade_gfb(v0, np.full(25, 5.0), np.tile(n, (25, 1)), np.ones(25))
+    g1 = _handmade_gfb(v1, np.full(25, 5.03125), np.tile(-n, (25, 1)), np.ones(25))
+    s = oracle.aggregate([g0, g1], _exact_fuse(), mode)
+    assert list(s.id) == [6, 7, 8, 11, 12, 13, 16, 17, 18]
+    assert np.all(s.count == 2)
+    assert np.all(s.c[:, 2] == -0.015625)
+    assert np.allclose(s.n, n[None], atol=1e-7)
+
+
+# ----------------------------------------------------------------------------
+# a5: Eq. 23 overlap selection / blend, epsilon, mirror paths
+# ----------------------------------------------------------------------------
+
+def _splats(rows):
+    ids, c, n, r = zip(*rows)
+    order = np.argsort(ids)
+    a = lambda x: np.asarray(x, np.float64)[order]
+    return oracle.Splats(id=np.asarray(ids, np.int64)[order], c=a(c), n=a(n), r=a(r),
+                         count=np.ones(len(ids), np.int32), keep=np.zeros(0, np.uint8))
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_eq23_overlap_select_and_blend(mode):
+    # Ray straight down the z axis.  Splat A (id 10): centre (0.5,0,0), normal
+    # +z, R 1 -> hit at z=0 (t=5), rho = 0.5.  Splat B (id 20): normal
+    # (0.6,0,0.8), centre (0.9,0,-0.625), R 1.5 -> its plane meets the axis at
+    # z=0.05 (t=4.95), |e| = 1.125, rho = 0.75.  Splat C (id 30) far below.
+    rows = [(20, [0.9, 0, -0.625], [0.6, 0, 0.8], 1.5),
+            (10, [0.5, 0, 0], [0, 0, 1], 1.0),
+            (30, [0, 0, -3.0], [0, 0, 1], 1.0)]
+    S = _splats(rows)
+    v = down_view(1, 1, 1.0)
+    # r = 0.1: A is within r of the nearest hit (B) and is closer to its centre
+    tr = oracle.trace(v, S, 1, 1e-3, 0.1, mode=mode)
+    assert tr.M[0] == 1 and tr.ids[0, 0] == 10
+    assert np.allclose(tr.p[0], [0, 0, 0], atol=1e-6)
+    m = 0.5 * np.array([0, 0, 1.0]) + 0.25 * np.array([0.6, 0, 0.8])
+    assert np.allclose(tr.n[0], m / np.linalg.norm(m), atol=2e-7)
+    # r = 0.01: only the nearest (B) is a candidate
+    tr = oracle.trace(v, S, 1, 1e-3, 0.01, mode=mode)
+    assert tr.ids[0, 0] == 20
+    assert np.allclose(tr.p[0], [0, 0, 0.05], atol=1e-6)
+    assert np.allclose(tr.n[0], [0.6, 0, 0.8], atol=2e-7)
+
+
+def test_eq23_tie_break_smaller_id():
+    rows = [(7, [0.2, 0, 0], [0, 0, 1], 1.0), (5, [0.2, 0, 0], [0, 0, 1], 1.0)]
+    tr = oracle.trace(down_view(1, 1, 1.0), _splats(rows), 1, 1e-3, 0.1)
+    assert tr.ids[0, 0] == 5
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_epsilon_minimum_travel(mode):
+    # Bounce 1 from a GFB on the plane z=0; the reflected ray goes straight up.
+    # A splat at z=0 (the surface itself) is never re-hit; a splat at height h
+    # is hit iff h > eps (Fig. 4b).
+    v = down_view(1, 1, 1.0)
+    first = oracle.Gfb(depth=np.array([5.0]), idx=np.array([0]), nrm=np.array([[0, 0, 1.0]]),
+                       view=v, pix=None)
+    eps = 0.01
+    for h, M_expect in ((2 * eps, 2), (0.5 * eps, 1)):
+        S = _splats([(1, [0, 0, 0], [0, 0, 1], 1.0), (2, [0, 0, h], [0, 0, 1], 1.0)])
+        tr = oracle.trace(v, S, 2, eps, 1e-4, first=first, mode=mode)
+        assert tr.M[0] == M_expect
+        if M_expect == 2:
+            assert tr.ids[0, 1] == 2
+            assert abs(tr.path[0] - (-0.0 + h)) < 1e-7
+
+
+@pytest.fixture(scope="module")
+def dihedral_geom():
+    sc = scenes.dihedral(6000, seed=21)
+    vd = scenes.aggregation_views(sc, 128, 128)
+    S, gv, gf, fp = oracle.build_geometry(sc, vd, "fp32")
+    return sc, S, gv
+
+
+def test_dihedral_interior_rays_bounce_twice(dihedral_geom):
+    # At phi = 45 deg broadside, a ray hitting plate y=0 at (x1, 0, z) is
+    # mirrored to (0, x1, z) on plate x=0 and leaves: exactly 2 bounces.
+    sc, S, gv = dihedral_geom
+    eps = oracle.default_eps(gv)
+    sw = scenes._sweep_over(sc, [90.0], [45.0], 64, [3e9], 3)
+    v = oracle.sweep_views(sw)[0]
+    first = oracle.gfb(sc, v)
+    tr = oracle.trace(v, S, 3, eps, eps, first=first)
+    hit = first.idx >= 0
+    j, i = np.divmod(np.arange(64 * 64), 64)
+    o = v.o[None] + (((i + 0.5) - 32) * v.pitch)[:, None] * v.u[None] + \
+        (((j + 0.5) - 32) * v.pitch)[:, None] * v.v[None]
+    p1 = o + np.where(hit, first.depth, 0)[:, None] * v.d[None]
+    m = 4 * float(S.r.max())
+    inner = hit & (np.abs(p1[:, 2]) < 0.25 - m) & (np.abs(p1[:, 0] - p1[:, 1]) > m) & \
+        (np.maximum(p1[:, 0], p1[:, 1]) < 0.5 - m)
+    assert inner.sum() > 500
+    assert np.all(tr.M[inner] == 2)
+    assert np.all(tr.psi[inner] == 1)
+    mirror = np.stack([p1[:, 1], p1[:, 0], p1[:, 2]], 1)
+    assert np.max(np.abs(tr.p[inner] - mirror[inner])) < 1e-5
+
+
+def test_trihedral_axis_triple_bounce_aperture():
+    # Along the trihedral's symmetry axis every ray in the triple-bounce
+    # aperture (area sqrt(3) a^2) returns after exactly 3 reflections, and
+    # sigma = 4 pi A_eff^2 / lambda^2 with A_eff the realised aperture
+    # (12 pi a^4 / lambda^2 for the ideal corner).
+    a = 0.3
+    sc = scenes.trihedral(9000, a=a, seed=8)
+    vd = scenes.aggregation_views(sc, 128, 128)
+    S, gv, gf, fp = oracle.build_geometry(sc, vd, "fp32")
+    eps = oracle.default_eps(gv)
+    th = math.degrees(math.acos(1 / math.sqrt(3)))
+    sw = scenes._sweep_over(sc, [th], [45.0], 96, [10e9], 3)
+    res = oracle.rcs_sweep(sc, sw, S, eps, eps)
+    tr, v = res.traces[0], res.views[0]
+    n3 = int(((tr.M == 3) & (tr.psi == 1)).sum())
+    a_eff = n3 * v.pitch ** 2
+    assert abs(a_eff / (math.sqrt(3) * a * a) - 1) < 0.12
+    lam = C0 / 10e9
+    sig = res.sigma[0, 0, 0, 0]
+    assert abs(oracle.db(sig) - oracle.db(4 * math.pi * a_eff ** 2 / lam ** 2)) < 0.5
+    assert abs(oracle.db(sig) - oracle.db(12 * math.pi * a ** 4 / lam ** 2)) < 1.5
+
+
+# ----------------------------------------------------------------------------
+# a6/a7: PO field (Eq. 5-14)
+# ----------------------------------------------------------------------------
+
+def _plate_cells(theta_deg, a, b, nu, nv, shift=(0.0, 0.0, 0.0), skew=0.0):
+    """Synthetic last-hit records of an a x b plate in the plane z=0 tiled by
+    the projections of nu x nv screen cells (incidence in the xz-plane)."""
+    th = math.radians(theta_deg)
+    w = np.array([math.sin(th), 0, math.cos(th)])
+    u = np.array([math.cos(th), 0, -math.sin(th)])
+    v = np.array([0, 1.0, 0])
+    d = -w
+    Lu = a / nu * math.cos(th)
+    us = Lu * u
+    vs = (b / nv) * v + skew * us      # a skewed cell (non-orthogonal u', v')
+    # projected cell vectors on the plate (Eq. 12-13 with n = z)
+    up = us - d * (us[2] / d[2])
+    vp = vs - d * (vs[2] / d[2])
+    ii, jj = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    ps = (ii.ravel()[:, None] - (nu - 1) / 2) * up[None] + (jj.ravel()[:, None] - (nv - 1) / 2) * vp[None]
+    ps = ps + np.asarray(shift)[None]
+    nr = ps.shape[0]
+    tr = oracle.Trace(M=np.ones(nr, np.int32), ids=np.zeros((nr, 1), np.int64), p=ps,
+                      n=np.tile([0, 0, 1.0], (nr, 1)), k=np.tile(d, (nr, 1)),
+                      u=np.tile(us, (nr, 1)), v=np.tile(vs, (nr, 1)), path=ps @ d,
+                      psi=np.ones(nr, np.uint8))
+    return tr, w, u, v, up * nu, vp * nv
+
+
+@pytest.mark.parametrize("theta", [0.0, 10.0, 25.0, 40.0, 60.0])
+def test_po_plate_pattern_textbook(theta):
+    f = 3e9
+    lam = C0 / f
+    k = 2 * math.pi / lam
+    a, b = 0.5, 0.3
+    tr, w, u, v, _, _ = _plate_cells(theta, a, b, 40, 30)
+    E = oracle.po_field(tr, [f], w)[0]
+    s = oracle.sigma_from_field(E, [f], u, v)[0]
+    x = k * a * math.sin(math.radians(theta))
+    ref = 4 * math.pi * (a * b) ** 2 / lam ** 2 * math.cos(math.radians(theta)) ** 2 * \
+        (math.sin(x) / x if x else 1.0) ** 2
+    assert abs(s[0, 0] / ref - 1) < 1e-9
+    assert abs(s[1, 1] / ref - 1) < 1e-9
+    # single-bounce PO has no cross-polarised backscatter
+    assert s[0, 1] < 1e-20 * ref and s[1, 0] < 1e-20 * ref
+
+
+def test_po_parallelogram_cells_use_cross_product_area():
+    # With skewed (non-orthogonal) cells the exact integral over the tiled
+    # parallelogram is |U x V| sinc(q.U/2) sinc(q.V/2); the sum of per-cell
+    # Eq. 11 terms equals it only with the area |u' x v'|.
+    f = 5e9
+    lam = C0 / f
+    k = 2 * math.pi / lam
+    tr, w, u, v, U, V = _plate_cells(35.0, 0.4, 0.25, 32, 20, skew=0.7)
+    E = oracle.po_field(tr, [f], w)[0]
+    q = k * (-w - w)
+    sinc = lambda x: math.sin(x) / x if x else 1.0
+    I = np.linalg.norm(np.cross(U, V)) * sinc(q @ U / 2) * sinc(q @ V / 2)
+    # vector factor for pol H (h = u_hat) with n = z
+    n = np.array([0, 0, 1.0])
+    vec = np.cross(np.cross(np.cross(n, u), w), w)
+    assert np.allclose(E[0, 1].real, I * vec, rtol=1e-9, atol=1e-12 * abs(I))
+    assert np.allclose(E[0, 1].imag, 0.0, atol=1e-9 * abs(I))
+
+
+def test_po_translation_phase_convention():
+    # exp(+j w t) convention with exp(-j k.r) propagation: moving the target by
+    # t multiplies the field by exp(-j q.t), q = k (k_in - k_s).
+    f = 3e9
+    k = 2 * math.pi * f / C0
+    t = np.array([0.013, -0.02, 0.031])
+    tr0, w, u, v, _, _ = _plate_cells(20.0, 0.3, 0.3, 16, 16)
+    tr1, *_ = _plate_cells(20.0, 0.3, 0.3, 16, 16, shift=t)
+    E0 = oracle.po_field(tr0, [f], w)[0]
+    E1 = oracle.po_field(tr1, [f], w)[0]
+    q = k * (-w - w)
+    assert np.allclose(E1, E0 * np.exp(-1j * (q @ t)), rtol=1e-9, atol=1e-12)
+
+
+def test_po_broadside_f_squared():
+    tr, w, u, v, _, _ = _plate_cells(0.0, 0.4, 0.4, 20, 20)
+    fs = [2e9, 4e9]
+    E = oracle.po_field(tr, fs, w)[0]
+    s = oracle.sigma_from_field(E, fs, u, v)
+    assert abs(s[1, 0, 0] / s[0, 0, 0] - 4.0) < 1e-12
+
+
+def test_po_sphere_exact_backscatter():
+    # exact PO backscatter of a sphere: sigma = 4 pi k^2 a^4 |e^{jb}/(jb) +
+    # (e^{jb} - 1)/b^2|^2 with b = 2ka (-> pi a^2).  Synthetic hits on the exact
+    # sphere; the discrete cell sum misses part of the shadow-boundary term,
+    # which is O(1/b) of the field.
+    f = 3e9
+    k = 2 * math.pi * f / C0
+    a, W = 1.0, 300
+    ext = a * 1.02
+    L = 2 * ext / W
+    c = (np.arange(W) + 0.5 - W / 2) * L
+    X, Y = np.meshgrid(c, c)
+    X, Y = X.ravel(), Y.ravel()
+    hit = X * X + Y * Y < a * a
+    Z = np.sqrt(np.maximum(a * a - X * X - Y * Y, 0))
+    p = np.stack([X, Y, Z], 1)[hit]
+    nr = p.shape[0]
+    d = np.array([0, 0, -1.0])
+    tr = oracle.Trace(M=np.ones(nr, np.int32), ids=np.zeros((nr, 1), np.int64), p=p, n=p / a,
+                      k=np.tile(d, (nr, 1)), u=np.tile([L, 0, 0], (nr, 1)),
+                      v=np.tile([0, L, 0], (nr, 1)), path=p @ d, psi=np.ones(nr, np.uint8))
+    E = oracle.po_field(tr, [f], [0, 0, 1.0])[0]
+    s = oracle.sigma_from_field(E, [f], [1, 0, 0], [0, 1, 0])[0]
+    b = 2 * k * a
+    ref = 4 * math.pi * k ** 2 * a ** 4 * abs(np.exp(1j * b) / (1j * b) + (np.exp(1j * b) - 1) / b ** 2) ** 2
+    bound_db = 20 * math.log10(1 + 2.0 / b)
+    for pol in (0, 1):
+        assert abs(oracle.db(s[pol, pol]) - oracle.db(ref)) < bound_db
+
+
+# ----------------------------------------------------------------------------
+# a7: end-to-end RCS through the oracle
+# ----------------------------------------------------------------------------
+
+def test_rcs_dihedral_realised_aperture(dihedral_geom):
+    # broadside to one face (phi = 0): single bounce, sigma = 4 pi (N L^2)^2 /
+    # lambda^2; at phi = 45: every hit is a double bounce, same form with the
+    # double-bounce aperture, which tends to sqrt(2) a b (8 pi a^2 b^2/lambda^2).
+    sc, S, gv = dihedral_geom
+    eps = oracle.default_eps(gv)
+    f = 3e9
+    lam = C0 / f
+    sw = scenes._sweep_over(sc, [90.0, 90.0], [0.0, 45.0], 96, [f], 2)
+    res = oracle.rcs_sweep(sc, sw, S, eps, eps)
+    L = res.views[0].pitch
+    n1 = int((res.traces[0].M == 1).sum())
+    assert res.traces[0].M.max() == 1
+    s0 = res.sigma[0, 0]
+    assert abs(oracle.db(s0[0, 0]) - oracle.db(4 * math.pi * (n1 * L * L) ** 2 / lam ** 2)) < 1e-3
+    assert abs(oracle.db(s0[1, 1]) - oracle.db(4 * math.pi * (n1 * L * L) ** 2 / lam ** 2)) < 1e-3
+    tr = res.traces[1]
+    n2 = int(((tr.M == 2) & (tr.psi == 1)).sum())
+    s45 = res.sigma[1, 0]
+    ap = n2 * L * L
+    assert abs(oracle.db(s45[0, 0]) - oracle.db(4 * math.pi * ap ** 2 / lam ** 2)) < 0.05
+    assert abs(oracle.db(s45[1, 1]) - oracle.db(4 * math.pi * ap ** 2 / lam ** 2)) < 0.05
+    assert abs(ap / (math.sqrt(2) * 0.25) - 1) < 0.15
+
+
+def test_rcs_dihedral_mirror_symmetry():
+    # the regular-grid dihedral is symmetric about x = y, so
+    # sigma(phi) = sigma(90 deg - phi)
+    sc = scenes.dihedral(4000, seed=3, jitter=False)
+    vd = scenes.aggregation_views(sc, 96, 96)
+    S, gv, gf, fp = oracle.build_geometry(sc, vd, "fp64")
+    eps = oracle.default_eps(gv)
+    sw = scenes._sweep_over(sc, [90.0] * 4, [12.0, 78.0, 30.0, 60.0], 64, [3e9], 2)
+    res = oracle.rcs_sweep(sc, sw, S, eps, eps, mode="fp64")
+    sd = oracle.db(res.sigma[:, 0, 0, 0])
+    assert abs(sd[0] - sd[1]) < 0.05
+    assert abs(sd[2] - sd[3]) < 0.05
+
+
+def test_rcs_sphere_surfels_vs_exact_po():
+    sc = scenes.sphere(20000, 1.0)
+    f = 3e9
+    k = 2 * math.pi * f / C0
+    sw = scenes._sweep_over(sc, [90.0, 30.0], [0.0, 200.0], 128, [f], 1)
+    res = oracle.rcs_sweep(sc, sw, None, 0.01, 0.01)
+    b = 2 * k
+    ref = 4 * math.pi * k ** 2 * abs(np.exp(1j * b) / (1j * b) + (np.exp(1j * b) - 1) / b ** 2) ** 2
+    assert np.max(np.abs(oracle.db(res.sigma[:, 0, 0, 0]) - oracle.db(ref))) < 0.15
+    assert np.max(np.abs(oracle.db(res.sigma[:, 0, 1, 1]) - oracle.db(ref))) < 0.15
+
+
+def test_golden_closed_forms():
+    """The textbook values of the standard workloads' targets (stored with
+    their sources) agree with the formulas the pins above rely on."""
+    g = json.load(open(os.path.join(GOLDEN, "closed_forms.json")))
+    for row in g["rows"]:
+        lam = C0 / row["freq_hz"]
+        val = {"plate": lambda r: 4 * math.pi * (r["a"] * r["b"]) ** 2 / lam ** 2,
+               "dihedral": lambda r: 8 * math.pi * (r["a"] * r["b"]) ** 2 / lam ** 2,
+               "sphere": lambda r: math.pi * r["a"] ** 2,
+               "trihedral": lambda r: 12 * math.pi * r["a"] ** 4 / lam ** 2}[row["kind"]](row)
+        assert abs(10 * math.log10(val) - row["dbsm"]) < 0.01, row
