@@ -412,12 +412,20 @@ def test_po_translation_phase_convention():
     assert np.allclose(E1, E0 * np.exp(-1j * (q @ t)), rtol=1e-9, atol=1e-12)
 
 
-def test_po_broadside_f_squared():
+def test_po_broadside_f_squared_and_polarisation_free():
     tr, w, u, v, _, _ = _plate_cells(0.0, 0.4, 0.4, 20, 20)
     fs = [2e9, 4e9]
     E = oracle.po_field(tr, fs, w)[0]
     s = oracle.sigma_from_field(E, fs, u, v)
     assert abs(s[1, 0, 0] / s[0, 0, 0] - 4.0) < 1e-12
+    # a flat plate at normal incidence has no preferred polarisation: the
+    # backscattered field is the same multiple c of the incident e for e = V
+    # (theta_hat = u) and e = H (phi_hat = v).
+    cV = E[0, 0] @ u
+    cH = E[0, 1] @ v
+    assert abs(cV - cH) < 1e-12 * abs(cV)
+    assert np.allclose(E[0, 0], cV * u, atol=1e-12 * abs(cV))
+    assert np.allclose(E[0, 1], cH * v, atol=1e-12 * abs(cH))
 
 
 def test_po_sphere_exact_backscatter():
