@@ -1,0 +1,412 @@
+#!/usr/bin/env python3
+"""Benchmark of the SBR-on-points hot path on GB300.
+
+One step = the whole path for one synthetic target: splat the points into
+the 8 aggregation views (GFBs), fuse them into splats, then the full
+monostatic sweep (per angle: incidence screen, splat for bounce 1, bounces
+2..mb through the splats, visibility, PO field over all frequencies, sigma).
+
+Printed (rank 0): one JSON line with ray-bounces/s (executed intersection
+queries, shadow rays included) as `value`, RCS samples/s beside it, the
+end-to-end figure through the C ABI with host buffers, the roofline of the
+dominant kernel, the CPU oracle's rate on a bounded sample, clocks and the
+number of kernels launched.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload sphere|dihedral|composite]
+  python bench.py --impl reference ...   (the CPU oracle, timed on the host)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+
+def make_workload(name):
+    if name == "sphere":
+        wl = scenes.workload_sphere()
+        desc = dict(workload="PEC sphere a=1 m, 200k Fibonacci points, 1024^2 rays, 64 freqs "
+                             "8-12 GHz, 360 azimuths, mb=2, 8 GFB views 512^2",
+                    points=200_000, rays=1024 * 1024, freqs=64, angles=360, max_bounces=2)
+    elif name == "dihedral":
+        wl = scenes.workload_dihedral()
+        desc = dict(workload="PEC dihedral 0.5 m, 10k points, 128^2 rays, 3 GHz, 91 azimuths, "
+                             "mb=2, 8 GFB views 512^2",
+                    points=10_000, rays=128 * 128, freqs=1, angles=91, max_bounces=2)
+    elif name == "composite":
+        wl = scenes.workload_composite()
+        desc = dict(workload="composite trihedral+plate+cylinder, 1M points (noise lambda/50, "
+                             "PCA normals), 2048^2 rays, 10 GHz, 72 azimuths, mb=5, "
+                             "8 GFB views 512^2",
+                    points=1_000_000, rays=2048 * 2048, freqs=1, angles=72, max_bounces=5)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return wl, desc
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pe_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2408_15583_gb300 import _lib, api, pipeline
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    lib = _lib.load()
+    wl, desc = make_workload(args.workload)
+    sc, sw, vd = wl.scene, wl.sweep, wl.views
+    stream = torch.cuda.current_stream()
+
+    pos, nrm, rad = pipeline.scene_to_device(sc, dev)
+    gv = pipeline.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, vd.W, vd.H)
+    prm = pipeline.default_params(sc.pos, gv)
+    sargs = api.SweepArgs.from_sweep(sw)
+    ws = api.workspace(sargs.workspace_bytes(), dev)
+    geom = api.alloc_geom(gv, dev)
+    A, F = sw.n_angles, sw.n_freq
+    E = torch.empty((A, F, 2, 3, 2), dtype=torch.float64, device=dev)
+    sig = torch.empty((A, F, 2, 2), dtype=torch.float64, device=dev)
+    stats = torch.zeros(8, dtype=torch.int64, device=dev)
+    gfb_ws = None
+
+    def step(p, n, r, st=None):
+        g = api.build_gfb(gv, p, n, r, 0, 0.0, outputs=("nd", "mask"))
+        api.aggregate_views(gv, g["nd"], g["mask"], prm, geom=geom)
+        api.rcs_sweep(sargs, p, n, r, geom, prm, ws=ws, E=E, sigma=sig, stats=st)
+
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    # warm-up
+    for _ in range(args.warmup):
+        step(pos, nrm, rad)
+    api.stream_check()
+
+    # one counted step for the ray-bounce count (device counters)
+    stats.zero_()
+    step(pos, nrm, rad, stats)
+    api.stream_check()
+    st = stats.cpu().numpy()
+    bounces_per_step = int(st[0] + st[1])
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed between steps (outside the events)
+    clk = ClockSampler(local_rank)
+    clk.start()
+    l0 = lib.pe_kernel_launches()
+    barrier()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(pos, nrm, rad, stats)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    barrier()
+    launches = lib.pe_kernel_launches() - l0
+    clocks = clk.stop()
+    api.stream_check()
+
+    # end to end through the C ABI with host buffers: pinned H2D of the
+    # points each step, D2H of the field and sigma
+    hp = torch.from_numpy(np.ascontiguousarray(sc.pos)).pin_memory()
+    hn = torch.from_numpy(np.ascontiguousarray(sc.nrm)).pin_memory()
+    hr = torch.from_numpy(np.ascontiguousarray(sc.rad)).pin_memory()
+    hE = torch.empty(E.shape, dtype=E.dtype).pin_memory()
+    hS = torch.empty(sig.shape, dtype=sig.dtype).pin_memory()
+    dp, dn, dr = torch.empty_like(pos), torch.empty_like(nrm), torch.empty_like(rad)
+    barrier()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dp.copy_(hp, non_blocking=True)
+        dn.copy_(hn, non_blocking=True)
+        dr.copy_(hr, non_blocking=True)
+        step(dp, dn, dr)
+        hE.copy_(E, non_blocking=True)
+        hS.copy_(sig, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    barrier()
+    h2d = int(hp.numel() * 4 + hn.numel() * 4 + hr.numel() * 4)
+    d2h = int(hE.numel() * 8 + hS.numel() * 8)
+
+    # roofline of the dominant kernel, timed alone on the launching stream
+    roof = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream)
+
+    t_ms = total_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms, e2e_ms = float(t[0]), float(t[1])
+    per_gpu_units = bounces_per_step * args.steps
+    value = per_gpu_units * world / (t_ms / 1e3)
+    samples = A * F * 2 * args.steps * world
+    out = {
+        "metric": "ray-bounces/s",
+        "value": value,
+        "unit": "ray-bounces/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": dict(desc, l2="flushed between steps (512 MB write outside the timed events)",
+                       ray_bounces_per_step=bounces_per_step,
+                       shadow_queries_per_step=int(st[1]), parallelism=f"replicas{world}"),
+        "rcs_samples_per_s": samples / (t_ms / 1e3),
+        "e2e": {"value": per_gpu_units * world / (e2e_ms / 1e3), "unit": "ray-bounces/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "rcs_samples_per_s": samples / (e2e_ms / 1e3)},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    return out
+
+
+def roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream):
+    """Time pe_po_field alone (same kernel and launch shape as inside the
+    sweep) on one batch of traced angles; ALU roofline."""
+    import torch
+    nb = min(sw.n_angles, 16)
+    views = [api.view_from_angles(sw.theta_deg[a], sw.phi_deg[a], sw.centre, sw.extent, sw.W, sw.H)
+             for a in range(nb)]
+    keys = api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, nrm, geom, sw.max_bounces, prm, ids=False)
+    ks = np.array([[-x for x in v.d] for v in views], np.float32)
+    valid = int(((h.M >= 1) & (h.psi > 0)).sum())
+    terms = valid * sw.n_freq
+    E = api.po_field(h, nb, sw.W * sw.H, ks, sw.freqs_hz)
+    torch.cuda.synchronize()
+    reps = 5
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        api.po_field(h, nb, sw.W * sw.H, ks, sw.freqs_hz, out=E)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops_per_term = PO_FLOPS_PER_TERM
+    achieved = terms * flops_per_term / (ms / 1e3) / 1e12
+    peak, src = alu_peak()
+    return {"kernel": "po_kernel (+po_reduce_kernel)", "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": src, "flops_per_term": flops_per_term, "terms_per_launch": terms,
+            "ms_per_launch": ms}
+
+
+# Algorithmic FP32 work of one (ray, frequency) term of Eq. 14 as the kernel
+# evaluates it (FMA = 2): two sinc arguments (2), two sinc evaluations
+# (Taylor, 5 FMA each: 20), their product and the amplitude split (3),
+# double-float phase k*delta and its reduction mod 2 pi (2 mul + 5 FMA + 1
+# add: 13), e^{-j phi} (2 special-function ops, counted 1 each: 2), and 12
+# complex-vector multiply-adds (24).
+PO_FLOPS_PER_TERM = 64
+
+
+def alu_peak():
+    """FP32 peak = 152 SMs x 128 FP32 lanes x 2 (FMA) x SM clock.  With the
+    measured median SM clock under load when MEASURED_PEAKS.json has it."""
+    mhz = 2070.0
+    src = "152 SM x 128 FP32 lanes x 2 x 2070 MHz (max clock)"
+    try:
+        m = json.load(open(MEASURED))
+        c = m.get("clocks_under_load", {}).get("sm_mhz_median")
+        if c:
+            mhz = float(c)
+            src = f"152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz (measured median SM clock under load)"
+    except (OSError, ValueError):
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, src
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle arm (cpu_baseline leg and --impl reference)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(wl, n_pix=1024, view_px=64, seed=0):
+    """The oracle on a bounded sample of the workload: one incidence angle,
+    n_pix random rays of its screen, splats from the 8 aggregation views at
+    view_px^2 (oracle-built inside the sample), all frequencies.  Returns
+    (ray-bounces executed, seconds)."""
+    import oracle
+    sc, sw, vd = wl.scene, wl.sweep, wl.views
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    vd_s = scenes.GfbViews(vd.theta_deg, vd.phi_deg, view_px, view_px, vd.centre, vd.extent)
+    S, gv, _, _ = oracle.build_geometry(sc, vd_s, "fp64")
+    eps = oracle.default_eps(gv)
+    v = oracle.view_from_angles(sw.theta_deg[0], sw.phi_deg[0], sw.centre, sw.extent, sw.W, sw.H,
+                                "fp64")
+    pix = np.sort(rng.choice(sw.W * sw.H, size=min(n_pix, sw.W * sw.H), replace=False))
+    first = oracle.gfb(sc, v, "fp64", pix=pix)
+    tr = oracle.trace(v, S, sw.max_bounces, eps, eps, first=first, pix=pix, mode="fp64")
+    oracle.po_field(tr, sw.freqs_hz, -v.d)
+    dt = time.perf_counter() - t0
+    queries = len(pix) + int(np.maximum(tr.M - 1, 0).sum()) + int(((tr.M >= 1) &
+                                                                  (tr.M < sw.max_bounces)).sum())
+    queries += int((tr.M >= 2).sum())   # shadow rays
+    return queries, dt, len(pix), view_px
+
+
+def cpu_baseline(wl):
+    q, dt, npix, vpx = oracle_sample(wl)
+    return {"value": q / dt, "unit": "ray-bounces/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle, one incidence angle, {npix} random rays of the "
+                      f"{wl.sweep.W}x{wl.sweep.H} screen, splats fused from the 8 views at "
+                      f"{vpx}^2 (built inside the sample), {wl.sweep.n_freq} frequencies; "
+                      f"{q} ray-bounces in {dt:.1f} s (all cores via OpenMP)"}
+
+
+def run_reference(args):
+    wl, desc = make_workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(wl, n_pix=64, view_px=32)
+    tot_q, tot_t = 0, 0.0
+    for k in range(args.steps):
+        q, dt, npix, vpx = oracle_sample(wl, n_pix=256, view_px=48, seed=k)
+        tot_q += q
+        tot_t += dt
+    v = tot_q / tot_t
+    return {
+        "impl": "reference", "metric": "ray-bounces/s", "value": v, "unit": "ray-bounces/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+        "cpu_baseline": {"value": v, "unit": "ray-bounces/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"each step: FP64 oracle, one angle, {npix} random rays, "
+                                   f"splats from 8 views at {vpx}^2 built inside the step"},
+        "e2e": {"value": v, "unit": "ray-bounces/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "dihedral", "composite"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and not args.no_cpu_baseline:
+        wl, _ = make_workload(args.workload)
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,320 @@
+/*
+ * pointemray.h -- C ABI of the GB300 (sm_103a) SBR-on-points library.
+ *
+ * The library implements the data-parallel path of PointEMRay (Yang, Liu, Yu,
+ * Cui, arXiv 2408.15583): screen-based point-ray intersection that splats
+ * oriented points into geometric frame buffers (GFBs), GFB-assisted multiple
+ * bounce computation, and the physical-optics (PO) field sum that gives the
+ * radar cross section (RCS) of a PEC target under plane-wave excitation.
+ *
+ * Conventions (every entry point):
+ *   - Pointers named *_dev are DEVICE pointers owned by the caller; pointers
+ *     without the suffix are HOST pointers read during the call only.  The
+ *     library never allocates or frees caller-visible memory; scratch memory
+ *     is the caller's `ws` buffer of at least the size the matching
+ *     *_workspace() query returns (256-byte aligned).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Every call is asynchronous on `stream`.  Argument errors are
+ *     returned synchronously; device-side conditions (queue or candidate-list
+ *     overflow, bounded waits that timed out) are reported by
+ *     pe_stream_check().  No C++ exception crosses the ABI.
+ *   - Arrays are row-major.  Points are float32 [N][3] (x,y,z).  A view's
+ *     pixel (i, j) (column i along u, row j along v) has linear index
+ *     j * W + i.  Several views are stored back to back in view order.
+ *   - Float arithmetic that decides a hit (ray/disk tests, depth keys,
+ *     reflections, Eq. 23) follows one fixed IEEE-754 binary32 operation order
+ *     without contraction, so hit indices and bounce counts are reproducible
+ *     bit for bit and independent of launch configuration.
+ *   - Calls on different streams may run concurrently; they share the
+ *     device-side error word read by pe_stream_check().
+ */
+#ifndef POINTEMRAY_H
+#define POINTEMRAY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PE_ABI_VERSION 1
+#define PE_MAX_VIEWS 16       /* views per aggregated geometry            */
+#define PE_MAX_BATCH 64       /* views (angles) per pe_build_gfb call      */
+#define PE_MAX_CAND 32        /* Eq. 23 overlap candidates kept per query  */
+
+typedef enum {
+  PE_OK = 0,
+  PE_EINVAL = 1,        /* bad argument (null pointer, size, alignment)    */
+  PE_ENOMEM = 2,        /* workspace smaller than the query returned        */
+  PE_ECUDA = 3,         /* a CUDA runtime call failed (see pe_last_error)   */
+  PE_ETIMEOUT = 4,      /* a bounded device wait gave up                    */
+  PE_EOVERFLOW = 5,     /* a fixed-capacity device list overflowed          */
+  PE_EUNSUPPORTED = 6   /* valid request outside what this build supports   */
+} pe_status;
+
+/* An orthographic ray screen (the paper's uvwo frame, Sec. III-A around
+ * Eq. 15-16): u, v, w orthonormal with u x v = w, w pointing from the target
+ * toward the transmitter.  `o` is the screen centre, placed outside the
+ * target; rays leave pixel centres o + a u + b v along d = -w, where
+ * a = ((i + 0.5) - W/2) * pitch and b = ((j + 0.5) - H/2) * pitch.
+ * All values are float32 (hosts compute them in FP64 and round once). */
+typedef struct {
+  float o[3], u[3], v[3], d[3];
+  float pitch;
+  int32_t W, H;
+} pe_view;
+
+/* Method parameters (values the paper leaves open are chosen by the caller).
+ *   delta      ray-tube radius of Alg. 1 (tube mode), metres;
+ *   eps        minimum travel distance of reflected rays (Sec. III-B, Fig. 4b);
+ *   overlap_r  radius r of the Eq. 23 overlap sphere, metres;
+ *   edge_tau   edge rule: a GFB pixel is an edge if a 4-neighbour is outside
+ *              the image or empty, or differs in depth by more than
+ *              edge_tau * pitch (stands in for the paper's Canny filter);
+ *   fuse_grid  voxel grid size G of the fusion step (Sec. III-B: 256);
+ *   bbox_min   voxel grid origin (float32), inv_voxel = G / (longest bbox edge)
+ *              as float32;
+ *   first_bounce_from_geom  0: bounce 1 from the incidence view's GFB
+ *              (PO path of Sec. III-A); 1: bounce 1 traced against the
+ *              aggregated splats as in Alg. 3. */
+typedef struct {
+  float delta;
+  float eps;
+  float overlap_r;
+  float edge_tau;
+  int32_t fuse_grid;
+  float bbox_min[3];
+  float inv_voxel;
+  int32_t first_bounce_from_geom;
+} pe_params;
+
+/* Aggregated splat geometry (Alg. 3 lines 1-3).  One caller-allocated device
+ * blob holds, for each view v (pixel offset off_v = sum of earlier W*H):
+ *   splat_cr[off_v + p] = {cx, cy, cz, R}   (R = 0: no splat owned here)
+ *   splat_nf[off_v + p] = {nx, ny, nz, count}
+ * and a conservative bounding-box pyramid per view (leaf tiles of 8x8 pixels,
+ * each level 4x4 tiles of the one below) in that view's (u, v, d) frame.
+ * A splat's id is its owner pixel's global index off_v + p.
+ * Layout is fully determined by the views; use pe_geom_bytes() to size it. */
+typedef struct {
+  int32_t n_views;
+  pe_view views[PE_MAX_VIEWS];
+  void *blob_dev;          /* caller-owned, pe_geom_bytes() bytes, 256-aligned */
+  size_t blob_bytes;
+} pe_geom;
+
+/* Per-ray last-hit records (Alg. 3 hitRecord; Eq. 14 inputs), indexed by ray
+ * slot = view * W * H + pixel.  All device pointers, caller-owned.
+ *   p, n, k, u, v : float32 [n][3]  last hit point, normal (turned against the
+ *                   incoming ray), incoming direction k^(M-1), incoming tube
+ *                   vectors u^(M-1), v^(M-1) (screen cell vectors pitch*u,
+ *                   pitch*v reflected at every bounce);
+ *   path          : float64 [n]     image-method path length d^(M)
+ *                   (k^(0) . p^(1) + sum |p^(m) - p^(m-1)|);
+ *   M             : int32 [n]       bounces (0 = the ray missed: Phi = 0);
+ *   psi           : uint8 [n]       visibility of the receiver (Psi);
+ *   ids           : uint32 [mb][n]  hit id per bounce (point index for a
+ *                   GFB bounce, splat id for a splat bounce, 0xFFFFFFFF after
+ *                   the last); may be NULL. */
+typedef struct {
+  float *p, *n, *k, *u, *v;
+  double *path;
+  int32_t *M;
+  uint8_t *psi;
+  uint32_t *ids;
+  int64_t n_rays;
+  int32_t max_bounces;
+} pe_hits;
+
+/* Device counters of a trace (int64): [0] executed intersection queries
+ * (primary GFB lookups + march queries, misses included), [1] shadow queries,
+ * [2] splat tests, [3] pyramid node tests. */
+#define PE_STATS_WORDS 8
+
+/* Library version of this header's ABI. */
+int pe_abi_version(void);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all threads, all devices) -- a diagnostic counter with no counterpart in
+ * the paper. */
+int64_t pe_kernel_launches(void);
+
+/* Human-readable text of the last error on the calling host thread. */
+const char *pe_last_error(void);
+
+/* Synchronise `stream` and return the first device-side condition raised by
+ * kernels since the last check (PE_EOVERFLOW, PE_ETIMEOUT), or PE_ECUDA if
+ * the stream reports an error; clears the device error word. */
+pe_status pe_stream_check(void *stream);
+
+/* ---------------------------------------------------------------------------
+ * a2/a3  Screen-based point-ray intersection (Alg. 1) -> GFBs.
+ * ------------------------------------------------------------------------- */
+
+/* Workspace bytes for pe_build_gfb over these views: one uint64 depth key per
+ * pixel plus 256 bytes. */
+size_t pe_build_gfb_workspace(int32_t n_views, const pe_view *views);
+
+/* Splat every point into every view (Alg. 1 with every candidate kept, i.e.
+ * K unbounded: the nearest candidate per pixel is a min over a packed 64-bit
+ * key (float bits of depth) << 32 | point index, so ties go to the smaller
+ * index and the result is deterministic).
+ *   mode 0 (surfel): point i is a two-sided disk of radius rad_dev[i] with
+ *     normal nrm_dev[i]; depth = ray parameter t of the hit (t > 0);
+ *   mode 1 (tube, Alg. 1): a point is a candidate when its distance to the
+ *     pixel's central ray is < delta and it lies in front; depth =
+ *     |point - ray origin| (Alg. 1's Length(p - o)); nrm/rad may be NULL.
+ * Outputs (device, per view back to back, any may be NULL):
+ *   gfb_nd_dev  float32 [pix][4] = (nx, ny, nz, depth): the hit point's
+ *               normal turned to face the view (n . d < 0); (0,0,0,+inf) on a
+ *               miss; tube mode stores a zero normal;
+ *   gfb_hit_dev uint32 [pix] point index or 0xFFFFFFFF;
+ *   gfb_mask_dev uint8 [pix] 1 on a hit;
+ *   keys_dev    uint64 [pix] the raw keys (UINT64_MAX on a miss).
+ * Requires 1 <= n_views <= PE_MAX_BATCH, n_points < 2^32 - 1. */
+pe_status pe_build_gfb(const pe_view *views, int32_t n_views,
+                       const float *pos_dev, const float *nrm_dev,
+                       const float *rad_dev, int64_t n_points, int32_t mode,
+                       float delta, void *ws, size_t ws_bytes,
+                       float *gfb_nd_dev, uint32_t *gfb_hit_dev,
+                       uint8_t *gfb_mask_dev, uint64_t *keys_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * a4  GFB aggregation: edge filter, voxel fusion, splats (Alg. 3 lines 1-3,
+ *     Eq. 22).
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of the pe_geom blob for these views. */
+size_t pe_geom_bytes(int32_t n_views, const pe_view *views);
+
+/* Workspace bytes for pe_aggregate_views (dense G^3 voxel counters + one
+ * entry per GFB pixel + scan scratch). */
+size_t pe_aggregate_workspace(int32_t n_views, const pe_view *views,
+                              int32_t fuse_grid);
+
+/* Fuse the GFBs of n_views views (as written by pe_build_gfb: gfb_nd_dev and
+ * gfb_mask_dev, views back to back) into splats.  Edge pixels are dropped;
+ * every remaining pixel's surface point o + depth * d falls in a voxel of the
+ * fuse_grid^3 grid; each non-empty voxel becomes one splat whose centre is
+ * the mean of its points and whose normal is the normalised mean of their
+ * normals (each first turned into the hemisphere of the voxel's first
+ * contributor), both summed in FP64 in (view, pixel) order, and whose radius
+ * is the largest Eq. 22 value over its contributors (L = the contributor's
+ * view pitch, p = its view direction).  The splat is stored at its owner
+ * pixel: the first contributor in (view, pixel) order.  Then the bounding
+ * pyramids are built.  out->views/n_views/blob_dev must be set by the caller
+ * (views identical to `views`).  Requires n_views <= PE_MAX_VIEWS,
+ * fuse_grid <= 256. */
+pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
+                             const float *gfb_nd_dev, const uint8_t *gfb_mask_dev,
+                             const pe_params *params, void *ws, size_t ws_bytes,
+                             pe_geom *out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * a5  GFB-assisted multiple-bounce computation (Alg. 3 lines 4-9, Eq. 2-4,
+ *     Eq. 23) and the visibility test Psi (Eq. 14).
+ * ------------------------------------------------------------------------- */
+
+/* Workspace bytes for pe_trace_bounces over n_views ray screens of this size
+ * (two ray queues of uint32 slots + counters). */
+size_t pe_trace_workspace(int32_t n_views, const pe_view *views);
+
+/* Trace every pixel ray of n_views ray screens (e.g. one per monostatic
+ * angle).  Bounce 1: from the screen's own GFB keys (keys_dev as written by
+ * pe_build_gfb for these views, surfel mode) with the point's normal nrm_dev
+ * turned to face the view, or -- when params->first_bounce_from_geom -- by
+ * marching the splats from the screen (tmin 0; keys/nrm may be NULL).
+ * Bounces 2..max_bounces: reflect the direction, the tube vectors and the
+ * polarisation at the current normal (Eq. 2-4: a - 2 (a . n) n), march the
+ * splats from the hit point (t > eps), take the nearest hit t* and, among the
+ * hits with t <= t* + overlap_r, the one whose hit point is closest to its
+ * splat's centre relative to its radius (ties: smaller t, then smaller id);
+ * the normal is the Eq. 23 blend of the candidates' normals (each turned
+ * against the ray, weights 1 - |p_i - c_i| / R_i, summed in splat-id order,
+ * normalised, turned against the ray).  A miss ends the ray.
+ * Psi: for rays with M >= 2 a shadow ray from the last hit toward the
+ * receiver (monostatic: along w, t > eps) is tested against the splats;
+ * Psi = 1 for M = 1 (the incident ray itself reached that point).
+ * Outputs go to `hits` (n_rays = n_views * W * H; all views same W, H).
+ * stats_dev: int64 [PE_STATS_WORDS] counters, accumulated (caller zeroes), or
+ * NULL.  geom may be NULL when max_bounces == 1 and bounce 1 comes from the
+ * GFB. */
+pe_status pe_trace_bounces(const pe_view *views, int32_t n_views,
+                           const uint64_t *keys_dev, const float *nrm_dev,
+                           const pe_geom *geom, int32_t max_bounces,
+                           const pe_params *params, void *ws, size_t ws_bytes,
+                           const pe_hits *hits, int64_t *stats_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * a6  Physical-optics field sum (Eq. 5-14).
+ * ------------------------------------------------------------------------- */
+
+/* Workspace bytes for pe_po_field. */
+size_t pe_po_workspace(int32_t n_groups, int64_t rays_per_group, int32_t n_freq);
+
+/* For each group g of rays_per_group consecutive ray slots (e.g. one
+ * monostatic angle) with observation direction ks[g] (unit, host float32
+ * [n_groups][3], toward the receiver) and each frequency f (host float64
+ * [n_freq], Hz), the Eq. 14 sum without its factor -j eta0 k0 / (2 pi):
+ *   Sigma = sum_l Phi_l Psi_l |u' x v'| sinc(q.u'/2) sinc(q.v'/2)
+ *           [(n x h) x ks] x ks exp(-j k (d_l - ks . p_l)),
+ * q = k (k_in - ks), u', v' from Eq. 12-13 with k_in, sinc(x) = sin(x)/x,
+ * for the two transmit polarisations V (E along theta_hat = screen u; magnetic
+ * polarisation -v/|v|) and H (E along phi_hat = screen v; h = u/|u|), with u,
+ * v the propagated tube vectors.  E_dev: float64 [n_groups][n_freq][2][3][2]
+ * (pol, xyz, re/im), device.  Per-term arithmetic is float32 with the phase
+ * argument in double-float and reduced modulo 2 pi; sums are compensated in
+ * float32 per thread and reduced in float64 in a fixed order (deterministic).
+ * RCS: sigma = k^2/pi |e_rx . Sigma|^2. */
+pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t rays_per_group,
+                      const float *ks, const double *freqs_hz, int32_t n_freq,
+                      void *ws, size_t ws_bytes, double *E_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * a1/a7  Monostatic RCS sweep (whole path: a1-a6 per batch of angles).
+ * ------------------------------------------------------------------------- */
+
+/* A monostatic sweep: incidence (theta_deg[a], phi_deg[a]); ray screen
+ * W x H centred at `centre`, half-width `extent` (>= the target's bounding
+ * radius), pitch = 2 extent / W; frequencies; bounces. */
+typedef struct {
+  int32_t n_angles;
+  const double *theta_deg;   /* host [n_angles] */
+  const double *phi_deg;     /* host [n_angles] */
+  int32_t W, H;
+  double centre[3];
+  double extent;
+  int32_t n_freq;
+  const double *freqs_hz;    /* host [n_freq] */
+  int32_t max_bounces;
+  int32_t angle_batch;       /* angles per batch (1..PE_MAX_BATCH), 0 = auto */
+} pe_sweep;
+
+/* The view of a monostatic incidence (a1): w = (sin t cos p, sin t sin p,
+ * cos t), u = theta_hat, v = phi_hat, pitch = 2 extent / W, screen centre
+ * centre + (extent + pitch) w, d = -w; computed in FP64, rounded to float32. */
+pe_status pe_view_from_angles(double theta_deg, double phi_deg, const double centre[3],
+                              double extent, int32_t W, int32_t H, pe_view *out);
+
+/* Workspace bytes for pe_rcs_sweep. */
+size_t pe_rcs_sweep_workspace(const pe_sweep *sweep);
+
+/* Run the sweep on the scene (points, surfel normals, radii: device) and the
+ * aggregated geometry `geom` (NULL allowed when max_bounces == 1):
+ * per batch of angles, splat the points into the incidence screens
+ * (bounce 1), trace bounces 2..mb, test Psi, and sum the PO field.
+ * E_dev: float64 [n_angles][n_freq][2][3][2] (device, required);
+ * sigma_dev: float64 [n_angles][n_freq][2 tx][2 rx] m^2 (device, nullable),
+ * tx/rx in (V, H); stats_dev as in pe_trace_bounces (nullable). */
+pe_status pe_rcs_sweep(const pe_sweep *sweep, const float *pos_dev,
+                       const float *nrm_dev, const float *rad_dev, int64_t n_points,
+                       const pe_geom *geom, const pe_params *params, void *ws,
+                       size_t ws_bytes, double *E_dev, double *sigma_dev,
+                       int64_t *stats_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POINTEMRAY_H */

@@ -1,0 +1,105 @@
+"""ctypes declarations of the C ABI in ``include/pointemray.h``.
+
+Loading fails loudly when the compiled library is missing: there is no CPU
+fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpointemray.so")
+
+PE_MAX_VIEWS = 16
+PE_MAX_BATCH = 64
+PE_STATS_WORDS = 8
+
+STATUS = {0: "PE_OK", 1: "PE_EINVAL", 2: "PE_ENOMEM", 3: "PE_ECUDA", 4: "PE_ETIMEOUT",
+          5: "PE_EOVERFLOW", 6: "PE_EUNSUPPORTED"}
+
+
+class PeView(C.Structure):
+    _fields_ = [("o", C.c_float * 3), ("u", C.c_float * 3), ("v", C.c_float * 3),
+                ("d", C.c_float * 3), ("pitch", C.c_float), ("W", C.c_int32), ("H", C.c_int32)]
+
+
+class PeParams(C.Structure):
+    _fields_ = [("delta", C.c_float), ("eps", C.c_float), ("overlap_r", C.c_float),
+                ("edge_tau", C.c_float), ("fuse_grid", C.c_int32), ("bbox_min", C.c_float * 3),
+                ("inv_voxel", C.c_float), ("first_bounce_from_geom", C.c_int32)]
+
+
+class PeGeom(C.Structure):
+    _fields_ = [("n_views", C.c_int32), ("views", PeView * PE_MAX_VIEWS),
+                ("blob_dev", C.c_void_p), ("blob_bytes", C.c_size_t)]
+
+
+class PeHits(C.Structure):
+    _fields_ = [("p", C.c_void_p), ("n", C.c_void_p), ("k", C.c_void_p), ("u", C.c_void_p),
+                ("v", C.c_void_p), ("path", C.c_void_p), ("M", C.c_void_p), ("psi", C.c_void_p),
+                ("ids", C.c_void_p), ("n_rays", C.c_int64), ("max_bounces", C.c_int32)]
+
+
+class PeSweep(C.Structure):
+    _fields_ = [("n_angles", C.c_int32), ("theta_deg", C.c_void_p), ("phi_deg", C.c_void_p),
+                ("W", C.c_int32), ("H", C.c_int32), ("centre", C.c_double * 3),
+                ("extent", C.c_double), ("n_freq", C.c_int32), ("freqs_hz", C.c_void_p),
+                ("max_bounces", C.c_int32), ("angle_batch", C.c_int32)]
+
+
+# name -> (restype, argtypes)
+P = C.c_void_p
+SIGNATURES = {
+    "pe_abi_version": (C.c_int, []),
+    "pe_kernel_launches": (C.c_int64, []),
+    "pe_last_error": (C.c_char_p, []),
+    "pe_stream_check": (C.c_int, [P]),
+    "pe_view_from_angles": (C.c_int, [C.c_double, C.c_double, P, C.c_double, C.c_int32,
+                                      C.c_int32, P]),
+    "pe_build_gfb_workspace": (C.c_size_t, [C.c_int32, P]),
+    "pe_build_gfb": (C.c_int, [P, C.c_int32, P, P, P, C.c_int64, C.c_int32, C.c_float, P,
+                               C.c_size_t, P, P, P, P, P]),
+    "pe_geom_bytes": (C.c_size_t, [C.c_int32, P]),
+    "pe_aggregate_workspace": (C.c_size_t, [C.c_int32, P, C.c_int32]),
+    "pe_aggregate_views": (C.c_int, [P, C.c_int32, P, P, P, P, C.c_size_t, P, P]),
+    "pe_trace_workspace": (C.c_size_t, [C.c_int32, P]),
+    "pe_trace_bounces": (C.c_int, [P, C.c_int32, P, P, P, C.c_int32, P, P, C.c_size_t, P, P,
+                                   P]),
+    "pe_po_workspace": (C.c_size_t, [C.c_int32, C.c_int64, C.c_int32]),
+    "pe_po_field": (C.c_int, [P, C.c_int32, C.c_int64, P, P, C.c_int32, P, C.c_size_t, P, P]),
+    "pe_rcs_sweep_workspace": (C.c_size_t, [P]),
+    "pe_rcs_sweep": (C.c_int, [P, P, P, P, C.c_int64, P, P, P, C.c_size_t, P, P, P, P]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libpointemray.so (build it first with ``paper_2408_15583_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"libpointemray.so is not built ({LIB_PATH}); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` -- there is no CPU fallback")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PeError(RuntimeError):
+    def __init__(self, status, where):
+        msg = load().pe_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, where):
+    if status != 0:
+        raise PeError(status, where)

@@ -1,0 +1,469 @@
+// a4: GFB aggregation (Alg. 3 lines 1-3): edge filter, voxel fusion, Eq. 22
+// splat radius, owner-pixel placement, and the bounding pyramids the march
+// uses in place of the paper's splat acceleration structure.
+//
+// Fusion is a counting sort on a dense G^3 voxel grid (G <= 256): count
+// contributors per voxel, exclusive scan, scatter pixel keys into voxel
+// segments, then one thread per segment orders its keys by (view, pixel) and
+// sums in FP64 in that order -- the same order as a sort by
+// (voxel, view, pixel), so the result is bit-identical whatever the atomic
+// order of the scatter.
+#include <cstring>
+
+#include "pe_internal.cuh"
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanThreads * kScanPer;
+constexpr int kSegLocal = 64;
+
+__device__ __forceinline__ int view_of(const pe_geom_layout &L, int64_t g) {
+  int v = 0;
+  while (v + 1 < L.nv && g >= L.pix_off[v + 1]) ++v;
+  return v;
+}
+
+// Edge rule + voxel of the pixel's surface point; counts contributors.
+__global__ void fuse_classify_kernel(const __grid_constant__ pe_geom_layout L,
+                                     const float4 *__restrict__ nd,
+                                     const uint8_t *__restrict__ mask, float tau,
+                                     float bx, float by, float bz, float inv_vox, int G,
+                                     uint32_t *__restrict__ vox_of, uint32_t *__restrict__ count) {
+  int64_t total = L.pix_off[L.nv];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t vox = PE_NONE;
+    if (mask[g]) {
+      int v = view_of(L, g);
+      const pe_view &V = L.view[v];
+      int64_t off = L.pix_off[v], p = g - off;
+      int i = (int)(p % V.W), j = (int)(p / V.W);
+      float t = nd[g].w;
+      float tauL = pe_mul(tau, V.pitch);
+      bool edge = false;
+      const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        int ii = i + di[k], jj = j + dj[k];
+        if (ii < 0 || jj < 0 || ii >= V.W || jj >= V.H) {
+          edge = true;
+          continue;
+        }
+        int64_t q = off + (int64_t)jj * V.W + ii;
+        if (!mask[q]) {
+          edge = true;
+          continue;
+        }
+        float dt = fabsf(pe_sub(nd[q].w, t));
+        if (dt > tauL) edge = true;
+      }
+      if (!edge) {
+        pe_f3 o = pe_pixel_origin(V, i, j);
+        pe_f3 x = pe_ray_at(o, t, pe_v3(V.d));
+        float f[3] = {pe_mul(pe_sub(x.x, bx), inv_vox), pe_mul(pe_sub(x.y, by), inv_vox),
+                      pe_mul(pe_sub(x.z, bz), inv_vox)};
+        int ix[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          float c = floorf(fminf(fmaxf(f[k], -1.0f), (float)G));
+          int ci = (int)c;
+          ix[k] = ci < 0 ? 0 : (ci > G - 1 ? G - 1 : ci);
+        }
+        vox = (uint32_t)((ix[0] * G + ix[1]) * G + ix[2]);
+        atomicAdd(count + vox, 1u);
+      }
+    }
+    vox_of[g] = vox;
+  }
+}
+
+// ---- exclusive scan over n uint32 (n up to 2^24 + 1) ------------------------
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *total) {
+  __shared__ uint32_t warp_sums[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t v = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) warp_sums[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    uint32_t w = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) warp_sums[lane] = w;
+  }
+  __syncthreads();
+  uint32_t before = (wid > 0 ? warp_sums[wid - 1] : 0) + v - x;
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    scan_tile_sums(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ sums) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k)
+    if (base + k < n) s += in[base + k];
+  uint32_t tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the tile sums in one block (n_tiles <= kScanTile).
+__global__ void __launch_bounds__(kScanThreads)
+    scan_tile_offsets(uint32_t *__restrict__ sums, int64_t n_tiles) {
+  int64_t base = (int64_t)threadIdx.x * kScanPer;
+  uint32_t loc[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    loc[k] = base + k < n_tiles ? sums[base + k] : 0;
+    s += loc[k];
+  }
+  uint32_t run = block_exclusive_scan(s, nullptr);
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < n_tiles) sums[base + k] = run;
+    run += loc[k];
+  }
+}
+
+// out[i] = sum of in[0..i) for i in [0, n]; out has n + 1 entries.
+__global__ void __launch_bounds__(kScanThreads)
+    scan_apply(const uint32_t *__restrict__ in, int64_t n, const uint32_t *__restrict__ tile_off,
+               uint32_t *__restrict__ out) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  uint32_t loc[kScanPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    loc[k] = base + k < n ? in[base + k] : 0;
+    s += loc[k];
+  }
+  uint32_t run = block_exclusive_scan(s, nullptr) + tile_off[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < n) out[base + k] = run;
+    if (base + k == n - 1) out[n] = run + loc[k];
+    run += loc[k];
+  }
+}
+
+// Scatter each kept pixel's key (voxel << 40 | view << 32 | pixel) into its
+// voxel's segment (order inside a segment is arbitrary here).
+__global__ void fuse_scatter_kernel(const __grid_constant__ pe_geom_layout L,
+                                    const uint32_t *__restrict__ vox_of,
+                                    const uint32_t *__restrict__ offs, uint32_t *__restrict__ count,
+                                    unsigned long long *__restrict__ entries) {
+  int64_t total = L.pix_off[L.nv];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t vox = vox_of[g];
+    if (vox == PE_NONE) continue;
+    int v = view_of(L, g);
+    uint32_t slot = offs[vox] + atomicSub(count + vox, 1u) - 1u;
+    entries[slot] = ((unsigned long long)vox << 40) | ((unsigned long long)v << 32) |
+                    (unsigned long long)(g - L.pix_off[v]);
+  }
+}
+
+// Eq. 22 for one contributor in FP64: s = sqrt(|n| |p| / |n . p|),
+// R = sqrt(2) L s if s < 2.5 else 3.535 L.
+__device__ __forceinline__ double eq22(pe_f3 n, pe_f3 p, double L) {
+  double nx = n.x, ny = n.y, nz = n.z, px = p.x, py = p.y, pz = p.z;
+  double nn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), __dmul_rn(nz, nz)));
+  double pp = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz)));
+  double np = __dadd_rn(__dadd_rn(__dmul_rn(nx, px), __dmul_rn(ny, py)), __dmul_rn(nz, pz));
+  if (np < 0) np = -np;
+  double s = np > 0 ? __dsqrt_rn(__ddiv_rn(__dmul_rn(nn, pp), np)) : __longlong_as_double(0x7ff0000000000000ll);
+  if (s < 2.5) return __dmul_rn(__dmul_rn(1.4142135623730951, L), s);
+  return __dmul_rn(3.535, L);
+}
+
+struct seg_acc {
+  double sp[3], sn[3], rmax;
+  pe_f3 n0;
+  bool first;
+};
+
+__device__ __forceinline__ void seg_add(seg_acc &a, const pe_geom_layout &L,
+                                        const float4 *__restrict__ nd, unsigned long long key) {
+  int v = (int)((key >> 32) & 0xff);
+  int64_t p = (int64_t)(key & 0xffffffffull);
+  const pe_view &V = L.view[v];
+  float4 q = nd[L.pix_off[v] + p];
+  int i = (int)(p % V.W), j = (int)(p / V.W);
+  pe_f3 x = pe_ray_at(pe_pixel_origin(V, i, j), q.w, pe_v3(V.d));
+  pe_f3 n = {q.x, q.y, q.z};
+  if (a.first) {
+    a.n0 = n;
+    a.first = false;
+  }
+  if (pe_dot(n, a.n0) < 0.0f) n = pe_neg3(n);
+  a.sp[0] = __dadd_rn(a.sp[0], (double)x.x);
+  a.sp[1] = __dadd_rn(a.sp[1], (double)x.y);
+  a.sp[2] = __dadd_rn(a.sp[2], (double)x.z);
+  a.sn[0] = __dadd_rn(a.sn[0], (double)n.x);
+  a.sn[1] = __dadd_rn(a.sn[1], (double)n.y);
+  a.sn[2] = __dadd_rn(a.sn[2], (double)n.z);
+  double r = eq22(n, pe_v3(V.d), (double)V.pitch);
+  if (r > a.rmax) a.rmax = r;
+}
+
+// One thread per voxel segment: order the keys, FP64 sums in that order,
+// Eq. 22 maximum, write the splat at the owner pixel.
+__global__ void fuse_segment_kernel(const __grid_constant__ pe_geom_layout L,
+                                    const float4 *__restrict__ nd,
+                                    const unsigned long long *__restrict__ entries,
+                                    const uint32_t *__restrict__ offs, int64_t nvox,
+                                    float4 *__restrict__ cr, float4 *__restrict__ nf) {
+  const int64_t n_entries = offs[nvox];  // kept pixels, written by scan_apply
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_entries;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long k0 = entries[s];
+    uint32_t vox = (uint32_t)(k0 >> 40);
+    if (offs[vox] != (uint32_t)s) continue;
+    int64_t len = (int64_t)offs[vox + 1] - s;
+    seg_acc a;
+    a.sp[0] = a.sp[1] = a.sp[2] = a.sn[0] = a.sn[1] = a.sn[2] = 0.0;
+    a.rmax = 0.0;
+    a.first = true;
+    unsigned long long owner;
+    if (len <= kSegLocal) {
+      unsigned long long buf[kSegLocal];
+      for (int64_t e = 0; e < len; ++e) {
+        unsigned long long k = entries[s + e];
+        int64_t m = e;
+        while (m > 0 && buf[m - 1] > k) {
+          buf[m] = buf[m - 1];
+          --m;
+        }
+        buf[m] = k;
+      }
+      owner = buf[0];
+      for (int64_t e = 0; e < len; ++e) seg_add(a, L, nd, buf[e]);
+    } else {
+      // long segment: visit keys in increasing order by repeated minimum
+      unsigned long long last = 0;
+      bool have = false;
+      owner = ~0ull;
+      for (int64_t e = 0; e < len; ++e) {
+        unsigned long long best = ~0ull;
+        for (int64_t f = 0; f < len; ++f) {
+          unsigned long long k = entries[s + f];
+          if ((!have || k > last) && k < best) best = k;
+        }
+        if (!have) owner = best;
+        seg_add(a, L, nd, best);
+        last = best;
+        have = true;
+      }
+    }
+    double cnt = (double)len;
+    double m = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a.sn[0], a.sn[0]), __dmul_rn(a.sn[1], a.sn[1])),
+                                    __dmul_rn(a.sn[2], a.sn[2])));
+    int v0 = (int)((owner >> 32) & 0xff);
+    int64_t id = L.pix_off[v0] + (int64_t)(owner & 0xffffffffull);
+    cr[id] = make_float4(__double2float_rn(__ddiv_rn(a.sp[0], cnt)),
+                         __double2float_rn(__ddiv_rn(a.sp[1], cnt)),
+                         __double2float_rn(__ddiv_rn(a.sp[2], cnt)), __double2float_rn(a.rmax));
+    nf[id] = make_float4(__double2float_rn(__ddiv_rn(a.sn[0], m)),
+                         __double2float_rn(__ddiv_rn(a.sn[1], m)),
+                         __double2float_rn(__ddiv_rn(a.sn[2], m)), (float)len);
+  }
+}
+
+// Leaf boxes: bounds of the owned splats' spheres in the view's (u, v, d)
+// frame, padded for rounding.  Empty tiles get lo = +inf, hi = -inf.
+__global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, int v,
+                                    float4 *__restrict__ nodes) {
+  const pe_view &V = L.view[v];
+  int tw = L.tw[v][0], th = L.th[v][0];
+  const float4 *cr = L.cr + L.pix_off[v];
+  float pad = L.pad[v];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tw * th; t += gridDim.x * blockDim.x) {
+    int tx = t % tw, ty = t / tw;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int jj = 0; jj < PE_LEAF; ++jj) {
+      int j = ty * PE_LEAF + jj;
+      if (j >= V.H) break;
+      for (int ii = 0; ii < PE_LEAF; ++ii) {
+        int i = tx * PE_LEAF + ii;
+        if (i >= V.W) break;
+        float4 c = cr[(int64_t)j * V.W + i];
+        if (!(c.w > 0.0f)) continue;
+        float qx = c.x - V.o[0], qy = c.y - V.o[1], qz = c.z - V.o[2];
+        float a[3] = {qx * V.u[0] + qy * V.u[1] + qz * V.u[2],
+                      qx * V.v[0] + qy * V.v[1] + qz * V.v[2],
+                      qx * V.d[0] + qy * V.d[1] + qz * V.d[2]};
+        float r = c.w * 1.000001f + pad;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = fminf(lo[k], a[k] - r);
+          hi[k] = fmaxf(hi[k], a[k] + r);
+        }
+      }
+    }
+    int64_t nid = L.node_off[v][0] + t;
+    nodes[2 * nid] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    nodes[2 * nid + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+  }
+}
+
+__global__ void pyramid_up_kernel(const __grid_constant__ pe_geom_layout L, int v, int l,
+                                  float4 *__restrict__ nodes) {
+  int tw = L.tw[v][l], th = L.th[v][l];
+  int cw = L.tw[v][l - 1], ch = L.th[v][l - 1];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tw * th; t += gridDim.x * blockDim.x) {
+    int tx = t % tw, ty = t / tw;
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+    float4 hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+    for (int j = 0; j < PE_FAN; ++j)
+      for (int i = 0; i < PE_FAN; ++i) {
+        int cx = tx * PE_FAN + i, cy = ty * PE_FAN + j;
+        if (cx >= cw || cy >= ch) continue;
+        int64_t c = L.node_off[v][l - 1] + (int64_t)cy * cw + cx;
+        float4 a = nodes[2 * c], b = nodes[2 * c + 1];
+        lo.x = fminf(lo.x, a.x);
+        lo.y = fminf(lo.y, a.y);
+        lo.z = fminf(lo.z, a.z);
+        hi.x = fmaxf(hi.x, b.x);
+        hi.y = fmaxf(hi.y, b.y);
+        hi.z = fmaxf(hi.z, b.z);
+      }
+    int64_t nid = L.node_off[v][l] + t;
+    nodes[2 * nid] = lo;
+    nodes[2 * nid + 1] = hi;
+  }
+}
+
+int grid_for(int64_t n, int threads, int cap) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+int sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+struct agg_ws {
+  uint32_t *count, *offs, *tile, *vox_of;
+  unsigned long long *entries;
+};
+
+agg_ws carve_agg(pe_carve &c, int64_t total_pix, int G) {
+  agg_ws w;
+  int64_t nv = (int64_t)G * G * G;
+  w.count = c.take<uint32_t>((size_t)nv);
+  w.offs = c.take<uint32_t>((size_t)nv + 1);
+  w.tile = c.take<uint32_t>((size_t)((nv + kScanTile - 1) / kScanTile));
+  w.vox_of = c.take<uint32_t>((size_t)total_pix);
+  w.entries = c.take<unsigned long long>((size_t)total_pix);
+  return w;
+}
+
+}  // namespace
+
+extern "C" size_t pe_aggregate_workspace(int32_t n_views, const pe_view *views,
+                                         int32_t fuse_grid) {
+  pe_geom_layout L;
+  if (!pe_make_layout(n_views, views, &L) || fuse_grid < 1 || fuse_grid > 256) return 0;
+  pe_carve c{nullptr, 0};
+  carve_agg(c, L.pix_off[L.nv], fuse_grid);
+  return c.bytes() + 256;
+}
+
+extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
+                                        const float *gfb_nd, const uint8_t *gfb_mask,
+                                        const pe_params *prm, void *ws, size_t ws_bytes,
+                                        pe_geom *out, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!views || !gfb_nd || !gfb_mask || !prm || !out)
+    return pe_fail(PE_EINVAL, "pe_aggregate_views: null argument");
+  pe_geom_layout L;
+  if (!pe_make_layout(n_views, views, &L))
+    return pe_fail(PE_EINVAL, "pe_aggregate_views: 1 <= n_views <= %d with valid views",
+                   PE_MAX_VIEWS);
+  int G = prm->fuse_grid;
+  if (G < 1 || G > 256) return pe_fail(PE_EINVAL, "pe_aggregate_views: fuse_grid in [1, 256]");
+  if (!pe_aligned(gfb_nd, 16)) return pe_fail(PE_EINVAL, "pe_aggregate_views: gfb_nd alignment");
+  if (out->n_views != n_views || !out->blob_dev)
+    return pe_fail(PE_EINVAL, "pe_aggregate_views: out must name the same views and a blob");
+  for (int v = 0; v < n_views; ++v)
+    if (memcmp(&out->views[v], &views[v], sizeof(pe_view)) != 0)
+      return pe_fail(PE_EINVAL, "pe_aggregate_views: out->views differ from views");
+  size_t o_cr, o_nf, o_nodes, tot;
+  pe_layout_offsets(L, &o_cr, &o_nf, &o_nodes, &tot);
+  if (out->blob_bytes < tot || !pe_aligned(out->blob_dev, 256))
+    return pe_fail(PE_ENOMEM, "pe_aggregate_views: geometry blob needs %zu bytes", tot);
+  size_t need = pe_aggregate_workspace(n_views, views, G);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_aggregate_views: workspace needs %zu bytes", need);
+
+  char *blob = static_cast<char *>(out->blob_dev);
+  float4 *cr = reinterpret_cast<float4 *>(blob + o_cr);
+  float4 *nf = reinterpret_cast<float4 *>(blob + o_nf);
+  float4 *nodes = reinterpret_cast<float4 *>(blob + o_nodes);
+  L.cr = cr;
+  L.nf = nf;
+  L.nodes = nodes;
+
+  int64_t total_pix = L.pix_off[n_views];
+  int64_t nvox = (int64_t)G * G * G;
+  pe_carve c{static_cast<char *>(ws), 0};
+  agg_ws w = carve_agg(c, total_pix, G);
+  const float4 *nd = reinterpret_cast<const float4 *>(gfb_nd);
+  int cap = sms() * 16;
+
+  PE_TRY_CUDA(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * nvox, s));
+  PE_TRY_CUDA(cudaMemsetAsync(cr, 0, sizeof(float4) * total_pix, s));
+  PE_TRY_CUDA(cudaMemsetAsync(nf, 0, sizeof(float4) * total_pix, s));
+  fuse_classify_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(
+      L, nd, gfb_mask, prm->edge_tau, prm->bbox_min[0], prm->bbox_min[1], prm->bbox_min[2],
+      prm->inv_voxel, G, w.vox_of, w.count);
+  PE_TRY_LAUNCH("fuse_classify_kernel");
+  int64_t n_tiles = (nvox + kScanTile - 1) / kScanTile;
+  if (n_tiles > kScanTile) return pe_fail(PE_EUNSUPPORTED, "voxel grid too large for the scan");
+  scan_tile_sums<<<(int)n_tiles, kScanThreads, 0, s>>>(w.count, nvox, w.tile);
+  PE_TRY_LAUNCH("scan_tile_sums");
+  scan_tile_offsets<<<1, kScanThreads, 0, s>>>(w.tile, n_tiles);
+  PE_TRY_LAUNCH("scan_tile_offsets");
+  scan_apply<<<(int)n_tiles, kScanThreads, 0, s>>>(w.count, nvox, w.tile, w.offs);
+  PE_TRY_LAUNCH("scan_apply");
+  fuse_scatter_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, w.vox_of, w.offs,
+                                                                     w.count, w.entries);
+  PE_TRY_LAUNCH("fuse_scatter_kernel");
+  // segment heads are found by slot; the kernel reads the entry count
+  // offs[nvox] on the device (at most total_pix)
+  fuse_segment_kernel<<<grid_for(total_pix, 128, cap), 128, 0, s>>>(L, nd, w.entries, w.offs,
+                                                                     nvox, cr, nf);
+  PE_TRY_LAUNCH("fuse_segment_kernel");
+  for (int v = 0; v < n_views; ++v) {
+    pyramid_leaf_kernel<<<grid_for((int64_t)L.tw[v][0] * L.th[v][0], 128, cap), 128, 0, s>>>(
+        L, v, nodes);
+    PE_TRY_LAUNCH("pyramid_leaf_kernel");
+    for (int l = 1; l < L.nlev[v]; ++l) {
+      pyramid_up_kernel<<<grid_for((int64_t)L.tw[v][l] * L.th[v][l], 128, cap), 128, 0, s>>>(
+          L, v, l, nodes);
+      PE_TRY_LAUNCH("pyramid_up_kernel");
+    }
+  }
+  return PE_OK;
+}

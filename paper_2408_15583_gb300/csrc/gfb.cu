@@ -1,0 +1,203 @@
+// a2/a3: screen-based point-ray intersection (Alg. 1) as a scatter splat.
+//
+// Alg. 1 gathers, per ray tube, the points within the tube and keeps the one
+// nearest the tube's origin.  With every candidate kept (K unbounded) that is
+// a minimum over (point, pixel) pairs, so it can be computed by scattering:
+// each point visits the pixels its footprint covers, tests the exact ray,
+// and lowers the pixel's 64-bit key (float bits of depth << 32 | index) with
+// atomicMin.  Depths are positive, so the key order is the depth order and
+// ties go to the smaller index: the result does not depend on thread order.
+#include "pe_internal.cuh"
+
+namespace {
+
+constexpr int kSplatThreads = 256;
+
+// Surfel (mode 0) or tube (mode 1) test of point c against pixel (i, j).
+__device__ __forceinline__ bool splat_test(const pe_view &V, int i, int j, pe_f3 c, pe_f3 n,
+                                           float R, int mode, float &depth) {
+  pe_f3 o = pe_pixel_origin(V, i, j);
+  pe_f3 d = pe_v3(V.d);
+  if (mode == 0) {
+    pe_f3 x, e;
+    return pe_hit_disk(o, d, c, n, R, 0.0f, depth, x, e);
+  }
+  // tube: distance of c to the central ray below delta, in front, score |c - o|
+  pe_f3 q = pe_sub3(c, o);
+  float t = pe_dot(q, d);
+  pe_f3 x = pe_ray_at(o, t, d);
+  pe_f3 e = pe_sub3(x, c);
+  if (!(pe_dot(e, e) < pe_mul(R, R))) return false;
+  if (!(t > 0.0f)) return false;
+  depth = pe_sqrt(pe_dot(q, q));
+  return true;
+}
+
+__global__ void __launch_bounds__(kSplatThreads)
+    splat_kernel(const __grid_constant__ pe_view_batch vb, const float *__restrict__ pos,
+                 const float *__restrict__ nrm, const float *__restrict__ rad, int64_t n,
+                 int mode, float delta, unsigned long long *__restrict__ keys) {
+  const int vi = blockIdx.y;
+  const pe_view &V = vb.v[vi];
+  const int W = V.W, H = V.H;
+  unsigned long long *kv = keys + (int64_t)vi * W * H;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    pe_f3 c = {__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2)};
+    pe_f3 nn = {0.f, 0.f, 0.f};
+    float R;
+    if (mode == 0) {
+      nn = {__ldg(nrm + 3 * p), __ldg(nrm + 3 * p + 1), __ldg(nrm + 3 * p + 2)};
+      R = __ldg(rad + p);
+    } else {
+      R = delta;
+    }
+    if (!(R >= 0.0f)) continue;
+    // Footprint: an orthographic projection does not enlarge a disk, so every
+    // pixel whose ray can hit it lies within R of c's projection; one extra
+    // pixel of margin covers rounding.  (Not part of the exact test.)
+    float qx = c.x - V.o[0], qy = c.y - V.o[1], qz = c.z - V.o[2];
+    float inv = 1.0f / V.pitch;
+    float ci = (qx * V.u[0] + qy * V.u[1] + qz * V.u[2]) * inv + 0.5f * W - 0.5f;
+    float cj = (qx * V.v[0] + qy * V.v[1] + qz * V.v[2]) * inv + 0.5f * H - 0.5f;
+    if (!(fabsf(ci) < 1e30f) || !(fabsf(cj) < 1e30f)) continue;  // NaN / inf
+    float rp = R * inv + 1.0f;
+    float fi0 = fmaxf(floorf(ci - rp), 0.0f), fi1 = fminf(ceilf(ci + rp), (float)(W - 1));
+    float fj0 = fmaxf(floorf(cj - rp), 0.0f), fj1 = fminf(ceilf(cj + rp), (float)(H - 1));
+    if (!(fi0 <= fi1) || !(fj0 <= fj1)) continue;
+    int i0 = (int)fi0, i1 = (int)fi1, j0 = (int)fj0, j1 = (int)fj1;
+    for (int j = j0; j <= j1; ++j)
+      for (int i = i0; i <= i1; ++i) {
+        float depth;
+        if (!splat_test(V, i, j, c, nn, R, mode, depth)) continue;
+        unsigned long long key =
+            ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)p;
+        unsigned long long *slot = kv + (int64_t)j * W + i;
+        if (key < __ldcg(slot)) atomicMin(slot, key);
+      }
+  }
+}
+
+__global__ void resolve_kernel(const __grid_constant__ pe_view_batch vb,
+                               const unsigned long long *__restrict__ keys,
+                               const float *__restrict__ nrm, int mode, int64_t per_view,
+                               float4 *__restrict__ nd, uint32_t *__restrict__ hit,
+                               uint8_t *__restrict__ mask) {
+  int64_t total = per_view * vb.n;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long key = keys[g];
+    const pe_view &V = vb.v[g / per_view];
+    float4 o4 = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+    uint32_t idx = PE_NONE;
+    if (key != ~0ull) {
+      idx = (uint32_t)(key & 0xffffffffull);
+      o4.w = __uint_as_float((uint32_t)(key >> 32));
+      if (mode == 0) {
+        pe_f3 n = {__ldg(nrm + 3 * (int64_t)idx), __ldg(nrm + 3 * (int64_t)idx + 1),
+                   __ldg(nrm + 3 * (int64_t)idx + 2)};
+        if (pe_dot(n, pe_v3(V.d)) > 0.0f) n = pe_neg3(n);
+        o4.x = n.x;
+        o4.y = n.y;
+        o4.z = n.z;
+      }
+    }
+    if (nd) nd[g] = o4;
+    if (hit) hit[g] = idx;
+    if (mask) mask[g] = idx != PE_NONE;
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float *nrm,
+                          const float *rad, int64_t n, int mode, float delta,
+                          unsigned long long *keys, cudaStream_t s) {
+  if (n <= 0) return PE_OK;
+  int64_t blocks_needed = (n + kSplatThreads - 1) / kSplatThreads;
+  // enough blocks to fill the GPU across the batch; points loop grid-stride
+  int64_t per_view = (int64_t)sm_count() * 8 / (vb.n > 0 ? vb.n : 1);
+  if (per_view < 1) per_view = 1;
+  int gx = (int)(blocks_needed < per_view ? blocks_needed : per_view);
+  dim3 grid(gx, vb.n);
+  splat_kernel<<<grid, kSplatThreads, 0, s>>>(vb, pos, nrm, rad, n, mode, delta, keys);
+  PE_TRY_LAUNCH("splat_kernel");
+  return PE_OK;
+}
+
+static bool same_size(const pe_view *views, int32_t n) {
+  for (int i = 1; i < n; ++i)
+    if (views[i].W != views[0].W || views[i].H != views[0].H) return false;
+  return true;
+}
+
+extern "C" size_t pe_build_gfb_workspace(int32_t n_views, const pe_view *views) {
+  if (n_views < 1 || !views) return 0;
+  int64_t tot = 0;
+  for (int i = 0; i < n_views; ++i) tot += (int64_t)views[i].W * views[i].H;
+  pe_carve c{nullptr, 0};
+  c.take<unsigned long long>((size_t)tot);
+  return c.bytes() + 256;
+}
+
+extern "C" pe_status pe_build_gfb(const pe_view *views, int32_t n_views, const float *pos,
+                                  const float *nrm, const float *rad, int64_t n_points,
+                                  int32_t mode, float delta, void *ws, size_t ws_bytes,
+                                  float *gfb_nd, uint32_t *gfb_hit, uint8_t *gfb_mask,
+                                  uint64_t *keys_out, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!views || n_views < 1 || n_views > PE_MAX_BATCH)
+    return pe_fail(PE_EINVAL, "pe_build_gfb: n_views must be in [1, %d]", PE_MAX_BATCH);
+  if (!same_size(views, n_views))
+    return pe_fail(PE_EINVAL, "pe_build_gfb: all views of a call must share W x H");
+  if (views[0].W <= 0 || views[0].H <= 0 || !(views[0].pitch > 0))
+    return pe_fail(PE_EINVAL, "pe_build_gfb: bad screen size or pitch");
+  if (n_points < 0 || n_points >= (int64_t)PE_NONE)
+    return pe_fail(PE_EINVAL, "pe_build_gfb: n_points out of range");
+  if (mode != 0 && mode != 1) return pe_fail(PE_EINVAL, "pe_build_gfb: mode must be 0 or 1");
+  if (n_points > 0 && (!pos || (mode == 0 && (!nrm || !rad))))
+    return pe_fail(PE_EINVAL, "pe_build_gfb: surfel mode needs pos, nrm and rad");
+  if (mode == 1 && !(delta > 0)) return pe_fail(PE_EINVAL, "pe_build_gfb: delta must be > 0");
+  if (gfb_nd && !pe_aligned(gfb_nd, 16))
+    return pe_fail(PE_EINVAL, "pe_build_gfb: gfb_nd must be 16-byte aligned");
+  size_t need = pe_build_gfb_workspace(n_views, views);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_build_gfb: workspace needs %zu bytes (256-aligned)", need);
+
+  pe_view_batch vb;
+  memset(&vb, 0, sizeof(vb));
+  vb.n = n_views;
+  vb.W = views[0].W;
+  vb.H = views[0].H;
+  for (int i = 0; i < n_views; ++i) vb.v[i] = views[i];
+  int64_t per_view = (int64_t)vb.W * vb.H;
+  unsigned long long *keys =
+      keys_out ? reinterpret_cast<unsigned long long *>(keys_out)
+               : reinterpret_cast<unsigned long long *>(
+                     pe_carve{static_cast<char *>(ws), 0}.take<unsigned long long>(
+                         (size_t)(per_view * n_views)));
+  PE_TRY_CUDA(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * per_view * n_views, s));
+  pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, mode, delta, keys, s);
+  if (st != PE_OK) return st;
+  if (gfb_nd || gfb_hit || gfb_mask) {
+    int64_t total = per_view * n_views;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > sm_count() * 16) blocks = sm_count() * 16;
+    resolve_kernel<<<blocks, 256, 0, s>>>(vb, keys, nrm, mode, per_view,
+                                          reinterpret_cast<float4 *>(gfb_nd), gfb_hit,
+                                          gfb_mask);
+    PE_TRY_LAUNCH("resolve_kernel");
+  }
+  return PE_OK;
+}

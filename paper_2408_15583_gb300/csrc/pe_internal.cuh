@@ -1,0 +1,178 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstddef>
+
+#include "pointemray.h"
+
+#define PE_MAX_LEVELS 6
+#define PE_LEAF 8          // leaf tile edge in pixels
+#define PE_FAN 4           // tiles per pyramid level edge
+#define PE_NONE 0xFFFFFFFFu
+
+// Device error word bits (pe_stream_check maps them to pe_status).
+#define PE_ERR_OVERFLOW 1u
+#define PE_ERR_TIMEOUT 2u
+
+// ---------------------------------------------------------------------------
+// Host helpers (defined in api.cu)
+// ---------------------------------------------------------------------------
+pe_status pe_fail(pe_status s, const char *fmt, ...);
+unsigned int *pe_err_word();  // device address of the error word, current device
+
+#define PE_TRY_CUDA(call)                                                    \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return pe_fail(PE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+void pe_count_launch();
+
+#define PE_TRY_LAUNCH(what)                                                  \
+  do {                                                                       \
+    pe_count_launch();                                                       \
+    cudaError_t e_ = cudaGetLastError();                                     \
+    if (e_ != cudaSuccess)                                                   \
+      return pe_fail(PE_ECUDA, "%s launch: %s", what, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Bump allocator over a caller buffer (base may be null to measure).
+struct pe_carve {
+  char *base;
+  size_t off;
+  template <class T>
+  T *take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+  size_t bytes() const { return (off + 255) & ~size_t(255); }
+};
+
+inline bool pe_aligned(const void *p, size_t a) {
+  return (reinterpret_cast<uintptr_t>(p) % a) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Views of a batch (kernel parameter, passed __grid_constant__)
+// ---------------------------------------------------------------------------
+struct pe_view_batch {
+  int32_t n;
+  int32_t W, H;            // common screen size (all views of the batch)
+  pe_view v[PE_MAX_BATCH];
+};
+
+// Geometry layout: splat planes and bounding pyramids of the aggregated views.
+struct pe_geom_layout {
+  int32_t nv;
+  pe_view view[PE_MAX_VIEWS];
+  int64_t pix_off[PE_MAX_VIEWS + 1];
+  int32_t nlev[PE_MAX_VIEWS];
+  int32_t tw[PE_MAX_VIEWS][PE_MAX_LEVELS];
+  int32_t th[PE_MAX_VIEWS][PE_MAX_LEVELS];
+  int64_t node_off[PE_MAX_VIEWS][PE_MAX_LEVELS];  // in nodes (2 float4 each)
+  int64_t n_nodes;
+  float pad[PE_MAX_VIEWS];  // absolute box padding per view (metres)
+  const float4 *cr;         // splat centre, radius
+  const float4 *nf;         // splat normal, count
+  const float4 *nodes;      // [n_nodes][2] lo, hi in (u, v, d) frame
+};
+
+// Fills everything but the pointers; returns false on bad views.
+bool pe_make_layout(int32_t nv, const pe_view *views, pe_geom_layout *L);
+// Blob byte offsets of the three arrays for a layout.
+void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
+                       size_t *off_nodes, size_t *total);
+
+// ---------------------------------------------------------------------------
+// Launchers shared between entry points
+// ---------------------------------------------------------------------------
+pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float *nrm,
+                          const float *rad, int64_t n, int mode, float delta,
+                          unsigned long long *keys, cudaStream_t s);
+
+struct pe_trace_ws {
+  uint32_t *q0, *q1;        // ray slot queues
+  uint32_t *counts;         // [4]: queue sizes
+};
+size_t pe_trace_ws_bytes(int64_t n_rays);
+pe_trace_ws pe_trace_ws_carve(pe_carve &c, int64_t n_rays);
+
+pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,
+                          const float *nrm, const pe_geom *geom, int32_t mb,
+                          const pe_params &prm, const pe_trace_ws &tw, const pe_hits &h,
+                          int64_t *stats, cudaStream_t s);
+
+size_t pe_po_ws_bytes(int32_t n_groups, int64_t rays_per_group, int32_t n_freq);
+pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rays_per_group,
+                       const float *ks, const double *freqs, int32_t n_freq, void *ws,
+                       size_t ws_bytes, double *E, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers: IEEE binary32 without contraction, left to right.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+struct pe_f3 {
+  float x, y, z;
+};
+__device__ __forceinline__ float pe_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float pe_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float pe_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float pe_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float pe_sqrt(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float pe_dot(pe_f3 a, pe_f3 b) {
+  return pe_add(pe_add(pe_mul(a.x, b.x), pe_mul(a.y, b.y)), pe_mul(a.z, b.z));
+}
+__device__ __forceinline__ pe_f3 pe_sub3(pe_f3 a, pe_f3 b) {
+  return {pe_sub(a.x, b.x), pe_sub(a.y, b.y), pe_sub(a.z, b.z)};
+}
+// o + t d
+__device__ __forceinline__ pe_f3 pe_ray_at(pe_f3 o, float t, pe_f3 d) {
+  return {pe_add(o.x, pe_mul(t, d.x)), pe_add(o.y, pe_mul(t, d.y)),
+          pe_add(o.z, pe_mul(t, d.z))};
+}
+__device__ __forceinline__ pe_f3 pe_neg3(pe_f3 a) { return {-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ pe_f3 pe_v3(const float *p) { return {p[0], p[1], p[2]}; }
+
+// Centre of pixel (i, j): ((o + a u) + b v), a = ((i + 0.5) - W/2) L.
+__device__ __forceinline__ pe_f3 pe_pixel_origin(const pe_view &V, int i, int j) {
+  float fi = pe_sub(pe_add((float)i, 0.5f), pe_mul(0.5f, (float)V.W));
+  float fj = pe_sub(pe_add((float)j, 0.5f), pe_mul(0.5f, (float)V.H));
+  float a = pe_mul(fi, V.pitch), b = pe_mul(fj, V.pitch);
+  return {pe_add(pe_add(V.o[0], pe_mul(a, V.u[0])), pe_mul(b, V.v[0])),
+          pe_add(pe_add(V.o[1], pe_mul(a, V.u[1])), pe_mul(b, V.v[1])),
+          pe_add(pe_add(V.o[2], pe_mul(a, V.u[2])), pe_mul(b, V.v[2]))};
+}
+
+// Ray o + t d against a two-sided disk (c, n, R): plane not parallel, hit
+// point inside the disk, t > tmin.  Returns t (and x, e = x - c) on a hit.
+__device__ __forceinline__ bool pe_hit_disk(pe_f3 o, pe_f3 d, pe_f3 c, pe_f3 n, float R,
+                                            float tmin, float &t, pe_f3 &x, pe_f3 &e) {
+  float den = pe_dot(d, n);
+  if (den == 0.0f) return false;
+  pe_f3 q = pe_sub3(c, o);
+  t = pe_div(pe_dot(q, n), den);
+  x = pe_ray_at(o, t, d);
+  e = pe_sub3(x, c);
+  if (!(pe_dot(e, e) <= pe_mul(R, R))) return false;
+  if (!(t > tmin)) return false;
+  return true;
+}
+
+// Reflection a - (2 (a . n)) n (Eq. 4; also H and the tube vectors).
+__device__ __forceinline__ pe_f3 pe_reflect(pe_f3 a, pe_f3 n) {
+  float s = pe_mul(2.0f, pe_dot(a, n));
+  return {pe_sub(a.x, pe_mul(s, n.x)), pe_sub(a.y, pe_mul(s, n.y)),
+          pe_sub(a.z, pe_mul(s, n.z))};
+}
+
+__device__ __forceinline__ void pe_raise(unsigned int *err, unsigned int bit) {
+  if (err) atomicOr(err, bit);
+}
+#endif

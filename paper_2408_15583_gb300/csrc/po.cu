@@ -1,0 +1,335 @@
+// a6: physical-optics aperture field sum (Eq. 5-14) over rays x frequencies.
+//
+// Per ray, the frequency-independent parts of Eq. 14 are computed once and
+// staged in shared memory: the projected tube vectors of Eq. 12-13, the
+// parallelogram area |u' x v'|, the sinc arguments per unit wavenumber, the
+// two polarisations' vector factors [(n x h) x ks] x ks, and the phase path
+// d - ks . p (FP64, split into a float hi/lo pair).  Threads then run one
+// frequency each over the staged rays: sinc x sinc, the phase k (d - ks.p) as a
+// double-float product reduced modulo 2 pi, one sincos, twelve
+// multiply-adds.  Each thread keeps float sums compensated with TwoSum every
+// few terms; the block reduces the threads' (hi + lo) in FP64 in a fixed
+// order and a second kernel sums the blocks in a fixed order, so the field
+// is deterministic.
+#include <cstring>
+
+#include "pe_internal.cuh"
+
+namespace {
+
+constexpr int kPoThreads = 256;
+constexpr int kPoGroups = 64;    // groups (angles) per launch
+constexpr int kPoFreqs = 256;    // frequencies per launch
+constexpr int kFlush = 8;        // terms between TwoSum flushes
+
+struct po_consts {
+  int32_t ng, nf;
+  int32_t fl;            // frequency lanes per block (power of two <= 64)
+  int32_t n_chunks;
+  int64_t rpg, chunk;    // rays per group, rays per block (multiple of 256)
+  int32_t g0;            // first group of this launch (slot offset g0 * rpg)
+  float c1, c2, c3, inv2pi;
+  float ks[kPoGroups][3];
+  float k[kPoFreqs], khi[kPoFreqs], klo[kPoFreqs];
+};
+
+// sin(x)/x: Taylor series through x^8 for |x| < 0.5 (truncation < 3e-11),
+// otherwise the hardware sine divided by x.
+__device__ __forceinline__ float sincf_(float x) {
+  float ax = fabsf(x);
+  if (ax < 0.5f) {
+    float x2 = x * x;
+    return 1.0f + x2 * (-1.0f / 6.0f + x2 * (1.0f / 120.0f + x2 * (-1.0f / 5040.0f +
+                                                                  x2 * (1.0f / 362880.0f))));
+  }
+  return __sinf(x) / x;
+}
+
+__device__ __forceinline__ void two_sum_into(float &hi, float &lo, float b) {
+  float s = hi + b;
+  float bp = s - hi;
+  float e = (hi - (s - bp)) + (b - bp);
+  hi = s;
+  lo += e;
+}
+
+__device__ __forceinline__ pe_f3 cross(pe_f3 a, pe_f3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float dotf(pe_f3 a, pe_f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+__global__ void __launch_bounds__(kPoThreads)
+    po_kernel(const pe_hits h, const __grid_constant__ po_consts C, double *__restrict__ part) {
+  __shared__ float s_au[kPoThreads], s_av[kPoThreads], s_dh[kPoThreads], s_dl[kPoThreads];
+  __shared__ float s_V[6][kPoThreads];
+  __shared__ int s_warp[kPoThreads / 32];
+  __shared__ double s_red[kPoThreads][12];
+
+  const int g = blockIdx.y;  // group within this launch
+  const int chunk = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int FL = C.fl, RL = kPoThreads / FL;
+  const int lane_f = tid % FL, lane_r = tid / FL;
+  const pe_f3 ks = {C.ks[g][0], C.ks[g][1], C.ks[g][2]};
+  const int64_t r_begin = (int64_t)chunk * C.chunk;
+  int64_t r_end = r_begin + C.chunk;
+  if (r_end > C.rpg) r_end = C.rpg;
+  const int64_t slot0 = (int64_t)(C.g0 + g) * C.rpg;
+
+  for (int f0 = 0; f0 < C.nf; f0 += FL) {
+    const int f = f0 + lane_f;
+    const bool f_ok = f < C.nf;
+    const float kf = f_ok ? C.k[f] : 0.0f, khi = f_ok ? C.khi[f] : 0.0f,
+                klo = f_ok ? C.klo[f] : 0.0f;
+    float hi[12], lo[12], b[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) hi[i] = lo[i] = b[i] = 0.0f;
+    int pending = 0;
+
+    for (int64_t sb = r_begin; sb < r_end; sb += kPoThreads) {
+      // ---- stage the frequency-independent per-ray factors ----------------
+      int64_t r = sb + tid;
+      bool valid = false;
+      float au = 0, av = 0, dh = 0, dl = 0, V[6] = {0, 0, 0, 0, 0, 0};
+      if (r < r_end) {
+        int64_t slot = slot0 + r;
+        valid = h.M[slot] >= 1 && h.psi[slot] != 0;
+        if (valid) {
+          pe_f3 kk = {h.k[3 * slot], h.k[3 * slot + 1], h.k[3 * slot + 2]};
+          pe_f3 n = {h.n[3 * slot], h.n[3 * slot + 1], h.n[3 * slot + 2]};
+          pe_f3 u = {h.u[3 * slot], h.u[3 * slot + 1], h.u[3 * slot + 2]};
+          pe_f3 v = {h.v[3 * slot], h.v[3 * slot + 1], h.v[3 * slot + 2]};
+          pe_f3 p = {h.p[3 * slot], h.p[3 * slot + 1], h.p[3 * slot + 2]};
+          float nk = dotf(n, kk);
+          if (nk == 0.0f) {
+            valid = false;
+          } else {
+            float su = dotf(n, u) / nk, sv = dotf(n, v) / nk;
+            pe_f3 up = {u.x - kk.x * su, u.y - kk.y * su, u.z - kk.z * su};
+            pe_f3 vp = {v.x - kk.x * sv, v.y - kk.y * sv, v.z - kk.z * sv};
+            pe_f3 cr = cross(up, vp);
+            float area = sqrtf(dotf(cr, cr));
+            pe_f3 q = {kk.x - ks.x, kk.y - ks.y, kk.z - ks.z};
+            au = 0.5f * dotf(q, up);
+            av = 0.5f * dotf(q, vp);
+            float lu = sqrtf(dotf(u, u)), lv = sqrtf(dotf(v, v));
+            pe_f3 hv = {-v.x / lv, -v.y / lv, -v.z / lv};
+            pe_f3 hh = {u.x / lu, u.y / lu, u.z / lu};
+            pe_f3 a = cross(cross(cross(n, hv), ks), ks);
+            pe_f3 c = cross(cross(cross(n, hh), ks), ks);
+            V[0] = area * a.x;
+            V[1] = area * a.y;
+            V[2] = area * a.z;
+            V[3] = area * c.x;
+            V[4] = area * c.y;
+            V[5] = area * c.z;
+            double ksp = (double)ks.x * (double)p.x + (double)ks.y * (double)p.y +
+                         (double)ks.z * (double)p.z;
+            double delta = h.path[slot] - ksp;
+            dh = (float)delta;
+            dl = (float)(delta - (double)dh);
+          }
+        }
+      }
+      // stable compaction of the valid rays (order = slot order)
+      unsigned m = __ballot_sync(0xffffffffu, valid);
+      int wid = tid >> 5, lane = tid & 31;
+      __syncthreads();  // previous sub-batch's readers are done
+      if (lane == 0) s_warp[wid] = __popc(m);
+      __syncthreads();
+      int before = 0, total = 0;
+      for (int w = 0; w < kPoThreads / 32; ++w) {
+        if (w < wid) before += s_warp[w];
+        total += s_warp[w];
+      }
+      if (valid) {
+        int at = before + __popc(m & ((1u << lane) - 1u));
+        s_au[at] = au;
+        s_av[at] = av;
+        s_dh[at] = dh;
+        s_dl[at] = dl;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s_V[i][at] = V[i];
+      }
+      __syncthreads();
+      // ---- one frequency per thread over the staged rays -----------------
+      if (f_ok) {
+        for (int j = lane_r; j < total; j += RL) {
+          float s = sincf_(kf * s_au[j]) * sincf_(kf * s_av[j]);
+          float dhi = s_dh[j], dlo = s_dl[j];
+          float ph = khi * dhi;
+          float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
+          float nq = rintf(ph * C.inv2pi);
+          float red = fmaf(-nq, C.c1, ph);
+          red = fmaf(-nq, C.c2, red);
+          red = fmaf(-nq, C.c3, red);
+          red += er;
+          float sn, cs;
+          __sincosf(red, &sn, &cs);
+          float re = s * cs, im = -s * sn;
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            float Vi = s_V[i][j];
+            b[2 * i] = fmaf(Vi, re, b[2 * i]);
+            b[2 * i + 1] = fmaf(Vi, im, b[2 * i + 1]);
+          }
+          if (++pending == kFlush) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+              two_sum_into(hi[i], lo[i], b[i]);
+              b[i] = 0.0f;
+            }
+            pending = 0;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) two_sum_into(hi[i], lo[i], b[i]);
+    // ---- fixed-order FP64 reduction over the ray lanes -------------------
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 12; ++i) s_red[tid][i] = (double)hi[i] + (double)lo[i];
+    __syncthreads();
+    if (tid < FL && f0 + tid < C.nf) {
+      double acc[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+      for (int rl = 0; rl < RL; ++rl)
+#pragma unroll
+        for (int i = 0; i < 12; ++i) acc[i] += s_red[rl * FL + tid][i];
+      int64_t o = (((int64_t)g * C.n_chunks + chunk) * C.nf + (f0 + tid)) * 12;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) part[o + i] = acc[i];
+    }
+    __syncthreads();
+  }
+}
+
+// E[g0+g][f][12] = sum over chunks (fixed order).
+__global__ void po_reduce_kernel(const double *__restrict__ part, int ng, int nf, int n_chunks,
+                                 int g0, int nf_total, int f_base, double *__restrict__ E) {
+  int64_t n = (int64_t)ng * nf * 12;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % 12);
+    int f = (int)((t / 12) % nf);
+    int g = (int)(t / (12 * (int64_t)nf));
+    double s = 0.0;
+    for (int c = 0; c < n_chunks; ++c) s += part[(((int64_t)g * n_chunks + c) * nf + f) * 12 + i];
+    E[(((int64_t)(g0 + g) * nf_total) + f_base + f) * 12 + i] = s;
+  }
+}
+
+int sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+void po_shape(int32_t ng, int64_t rpg, int32_t nf, int *fl, int *n_chunks, int64_t *chunk) {
+  int f = 1;
+  while (f < nf && f < 64) f <<= 1;
+  *fl = f;
+  int64_t max_chunks = (rpg + kPoThreads - 1) / kPoThreads;
+  int64_t target = ((int64_t)sms() * 8 + ng - 1) / (ng > 0 ? ng : 1);
+  if (target < 1) target = 1;
+  int64_t nc = target < max_chunks ? target : max_chunks;
+  if (nc < 1) nc = 1;
+  int64_t ch = (rpg + nc - 1) / nc;
+  ch = (ch + kPoThreads - 1) / kPoThreads * kPoThreads;
+  nc = (rpg + ch - 1) / ch;
+  if (nc < 1) nc = 1;
+  *n_chunks = (int)nc;
+  *chunk = ch;
+}
+
+}  // namespace
+
+size_t pe_po_ws_bytes(int32_t n_groups, int64_t rpg, int32_t n_freq) {
+  // the partial sums of the largest launch (any group count up to 64)
+  int nf = n_freq < kPoFreqs ? n_freq : kPoFreqs;
+  int gmax = n_groups < kPoGroups ? n_groups : kPoGroups;
+  size_t most = 0;
+  for (int ng = 1; ng <= gmax; ++ng) {
+    int fl, nc;
+    int64_t ch;
+    po_shape(ng, rpg, nf, &fl, &nc, &ch);
+    size_t b = (size_t)ng * nc * nf * 12;
+    if (b > most) most = b;
+  }
+  pe_carve c{nullptr, 0};
+  c.take<double>(most);
+  return c.bytes();
+}
+
+pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const float *ks,
+                       const double *freqs, int32_t n_freq, void *ws, size_t ws_bytes,
+                       double *E, cudaStream_t s) {
+  if (n_groups < 1 || rpg < 1 || n_freq < 1) return PE_OK;
+  if (ws_bytes < pe_po_ws_bytes(n_groups, rpg, n_freq))
+    return pe_fail(PE_ENOMEM, "po: workspace too small");
+  double *part = static_cast<double *>(ws);
+  const double two_pi = 2.0 * M_PI;
+  const double c0 = 299792458.0;
+  for (int g0 = 0; g0 < n_groups; g0 += kPoGroups) {
+    int ng = n_groups - g0 < kPoGroups ? n_groups - g0 : kPoGroups;
+    for (int fb = 0; fb < n_freq; fb += kPoFreqs) {
+      int nf = n_freq - fb < kPoFreqs ? n_freq - fb : kPoFreqs;
+      po_consts C;
+      memset(&C, 0, sizeof(C));
+      C.ng = ng;
+      C.nf = nf;
+      po_shape(ng, rpg, nf, &C.fl, &C.n_chunks, &C.chunk);
+      C.rpg = rpg;
+      C.g0 = g0;
+      C.c1 = (float)two_pi;
+      C.c2 = (float)(two_pi - (double)C.c1);
+      C.c3 = (float)(two_pi - (double)C.c1 - (double)C.c2);
+      C.inv2pi = (float)(1.0 / two_pi);
+      for (int g = 0; g < ng; ++g)
+        for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];
+      for (int f = 0; f < nf; ++f) {
+        double kd = two_pi * freqs[fb + f] / c0;
+        C.k[f] = (float)kd;
+        C.khi[f] = (float)kd;
+        C.klo[f] = (float)(kd - (double)C.khi[f]);
+      }
+      dim3 grid(C.n_chunks, ng);
+      po_kernel<<<grid, kPoThreads, 0, s>>>(h, C, part);
+      PE_TRY_LAUNCH("po_kernel");
+      int64_t n = (int64_t)ng * nf * 12;
+      int blocks = (int)((n + 255) / 256);
+      po_reduce_kernel<<<blocks, 256, 0, s>>>(part, ng, nf, C.n_chunks, g0, n_freq, fb, E);
+      PE_TRY_LAUNCH("po_reduce_kernel");
+    }
+  }
+  return PE_OK;
+}
+
+extern "C" size_t pe_po_workspace(int32_t n_groups, int64_t rays_per_group, int32_t n_freq) {
+  if (n_groups < 1 || rays_per_group < 1 || n_freq < 1) return 0;
+  return pe_po_ws_bytes(n_groups, rays_per_group, n_freq) + 256;
+}
+
+extern "C" pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t rays_per_group,
+                                 const float *ks, const double *freqs, int32_t n_freq, void *ws,
+                                 size_t ws_bytes, double *E, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!hits || !ks || !freqs || !E || n_groups < 1 || rays_per_group < 1 || n_freq < 1)
+    return pe_fail(PE_EINVAL, "pe_po_field: bad arguments");
+  if (hits->n_rays < (int64_t)n_groups * rays_per_group || !hits->p || !hits->n || !hits->k ||
+      !hits->u || !hits->v || !hits->path || !hits->M || !hits->psi)
+    return pe_fail(PE_EINVAL, "pe_po_field: hits must hold n_groups * rays_per_group records");
+  for (int f = 0; f < n_freq; ++f)
+    if (!(freqs[f] > 0)) return pe_fail(PE_EINVAL, "pe_po_field: frequencies must be > 0");
+  size_t need = pe_po_workspace(n_groups, rays_per_group, n_freq);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_po_field: workspace needs %zu bytes", need);
+  return pe_launch_po(*hits, n_groups, rays_per_group, ks, freqs, n_freq, ws, ws_bytes, E, s);
+}

@@ -1,0 +1,156 @@
+// a1/a7: monostatic RCS sweep -- the whole path per batch of angles:
+// incidence screens (a1) -> splat the points (a2, bounce 1) -> bounces 2..mb
+// and Psi through the aggregated splats (a5) -> PO field (a6) -> sigma.
+#include <cstring>
+
+#include "pe_internal.cuh"
+
+namespace {
+
+// sigma[a][f][tx][rx] = k^2/pi |e_rx . Sigma_tx|^2, e_V = u (theta_hat),
+// e_H = v (phi_hat) of the angle's screen.
+__global__ void sigma_kernel(const __grid_constant__ pe_view_batch vb, const double *__restrict__ E,
+                             const double *__restrict__ kw, int nf, int a0,
+                             double *__restrict__ sigma) {
+  int n = vb.n * nf;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int a = t / nf, f = t % nf;
+    const pe_view &V = vb.v[a];
+    const double *e = E + ((int64_t)(a0 + a) * nf + f) * 12;
+    double k = kw[f];
+    double c = k * k / M_PI;
+    for (int tx = 0; tx < 2; ++tx)
+      for (int rx = 0; rx < 2; ++rx) {
+        const float *er = rx == 0 ? V.u : V.v;
+        double re = 0, im = 0;
+        for (int q = 0; q < 3; ++q) {
+          re += (double)er[q] * e[(tx * 3 + q) * 2];
+          im += (double)er[q] * e[(tx * 3 + q) * 2 + 1];
+        }
+        sigma[(((int64_t)(a0 + a) * nf + f) * 2 + tx) * 2 + rx] = c * (re * re + im * im);
+      }
+  }
+}
+
+struct sweep_ws {
+  unsigned long long *keys;
+  pe_hits h;
+  pe_trace_ws tw;
+  double *kw;
+  void *po;
+  size_t po_bytes;
+};
+
+int batch_of(const pe_sweep *sw) {
+  if (sw->angle_batch > 0) return sw->angle_batch < PE_MAX_BATCH ? sw->angle_batch : PE_MAX_BATCH;
+  int64_t per = (int64_t)sw->W * sw->H;
+  int64_t bytes = per * (8 + 60 + 8 + 4 + 1 + 8) + 4096;
+  int64_t b = ((int64_t)2 << 30) / bytes;
+  if (b < 1) b = 1;
+  if (b > PE_MAX_BATCH) b = PE_MAX_BATCH;
+  if (b > sw->n_angles) b = sw->n_angles;
+  return (int)b;
+}
+
+sweep_ws carve_sweep(pe_carve &c, const pe_sweep *sw, int B) {
+  sweep_ws w;
+  memset(&w, 0, sizeof(w));
+  int64_t n = (int64_t)sw->W * sw->H * B;
+  w.keys = c.take<unsigned long long>((size_t)n);
+  w.h.p = c.take<float>((size_t)n * 3);
+  w.h.n = c.take<float>((size_t)n * 3);
+  w.h.k = c.take<float>((size_t)n * 3);
+  w.h.u = c.take<float>((size_t)n * 3);
+  w.h.v = c.take<float>((size_t)n * 3);
+  w.h.path = c.take<double>((size_t)n);
+  w.h.M = c.take<int32_t>((size_t)n);
+  w.h.psi = c.take<uint8_t>((size_t)n);
+  w.h.ids = nullptr;
+  w.h.n_rays = n;
+  w.h.max_bounces = sw->max_bounces;
+  w.tw = pe_trace_ws_carve(c, n);
+  w.kw = c.take<double>((size_t)sw->n_freq);
+  w.po_bytes = pe_po_ws_bytes(B, (int64_t)sw->W * sw->H, sw->n_freq);
+  w.po = c.take<char>(w.po_bytes);
+  return w;
+}
+
+bool sweep_ok(const pe_sweep *sw) {
+  return sw && sw->n_angles >= 1 && sw->theta_deg && sw->phi_deg && sw->W > 0 && sw->H > 0 &&
+         (int64_t)sw->W * sw->H * PE_MAX_BATCH < (int64_t)PE_NONE && sw->extent > 0 &&
+         sw->n_freq >= 1 && sw->freqs_hz && sw->max_bounces >= 1 && sw->max_bounces <= 64;
+}
+
+}  // namespace
+
+extern "C" size_t pe_rcs_sweep_workspace(const pe_sweep *sw) {
+  if (!sweep_ok(sw)) return 0;
+  pe_carve c{nullptr, 0};
+  carve_sweep(c, sw, batch_of(sw));
+  return c.bytes() + 256;
+}
+
+extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const float *nrm,
+                                  const float *rad, int64_t n_points, const pe_geom *geom,
+                                  const pe_params *prm, void *ws, size_t ws_bytes, double *E,
+                                  double *sigma, int64_t *stats, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!sweep_ok(sw) || !prm || !E) return pe_fail(PE_EINVAL, "pe_rcs_sweep: bad sweep");
+  if (n_points < 0 || n_points >= (int64_t)PE_NONE || (n_points > 0 && (!pos || !nrm || !rad)))
+    return pe_fail(PE_EINVAL, "pe_rcs_sweep: points");
+  for (int f = 0; f < sw->n_freq; ++f)
+    if (!(sw->freqs_hz[f] > 0)) return pe_fail(PE_EINVAL, "pe_rcs_sweep: frequencies must be > 0");
+  if (sw->max_bounces > 1 && !geom)
+    return pe_fail(PE_EINVAL, "pe_rcs_sweep: max_bounces > 1 needs the aggregated geometry");
+  size_t need = pe_rcs_sweep_workspace(sw);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_rcs_sweep: workspace needs %zu bytes", need);
+  const int B = batch_of(sw);
+  pe_carve c{static_cast<char *>(ws), 0};
+  sweep_ws w = carve_sweep(c, sw, B);
+  const int64_t per = (int64_t)sw->W * sw->H;
+
+  double kw_h[4096];
+  const double two_pi = 2.0 * M_PI;
+  for (int f0 = 0; f0 < sw->n_freq; f0 += 4096) {
+    int nf = sw->n_freq - f0 < 4096 ? sw->n_freq - f0 : 4096;
+    for (int f = 0; f < nf; ++f) kw_h[f] = two_pi * sw->freqs_hz[f0 + f] / 299792458.0;
+    // pageable source: the call returns once kw_h has been staged
+    PE_TRY_CUDA(cudaMemcpyAsync(w.kw + f0, kw_h, sizeof(double) * nf, cudaMemcpyHostToDevice, s));
+  }
+
+  for (int a0 = 0; a0 < sw->n_angles; a0 += B) {
+    int nb = sw->n_angles - a0 < B ? sw->n_angles - a0 : B;
+    pe_view_batch vb;
+    memset(&vb, 0, sizeof(vb));
+    vb.n = nb;
+    vb.W = sw->W;
+    vb.H = sw->H;
+    float ks[PE_MAX_BATCH * 3];
+    for (int a = 0; a < nb; ++a) {
+      pe_status st = pe_view_from_angles(sw->theta_deg[a0 + a], sw->phi_deg[a0 + a], sw->centre,
+                                         sw->extent, sw->W, sw->H, &vb.v[a]);
+      if (st != PE_OK) return st;
+      for (int k = 0; k < 3; ++k) ks[3 * a + k] = -vb.v[a].d[k];
+    }
+    pe_hits h = w.h;
+    h.n_rays = per * nb;
+    if (!prm->first_bounce_from_geom) {
+      PE_TRY_CUDA(cudaMemsetAsync(w.keys, 0xff, sizeof(unsigned long long) * per * nb, s));
+      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.keys, s);
+      if (st != PE_OK) return st;
+    }
+    pe_status st = pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, w.tw, h, stats, s);
+    if (st != PE_OK) return st;
+    // PO: E rows [a0, a0 + nb)
+    st = pe_launch_po(h, nb, per, ks, sw->freqs_hz, sw->n_freq, w.po, w.po_bytes,
+                      E + (int64_t)a0 * sw->n_freq * 12, s);
+    if (st != PE_OK) return st;
+    if (sigma) {
+      int n = nb * sw->n_freq;
+      sigma_kernel<<<(n + 127) / 128, 128, 0, s>>>(vb, E, w.kw, sw->n_freq, a0, sigma);
+      PE_TRY_LAUNCH("sigma_kernel");
+    }
+  }
+  return PE_OK;
+}

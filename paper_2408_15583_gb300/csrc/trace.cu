@@ -1,0 +1,529 @@
+// a5: GFB-assisted multiple-bounce computation (Alg. 3 lines 4-9).
+//
+// Rays march through the aggregated splats of every view.  Each splat lives
+// at its owner pixel of one view, and every view keeps a pyramid of
+// conservative bounding boxes in its own (u, v, d) frame (8x8-pixel leaves,
+// 4x4 fan-out).  A query descends each view's pyramid with the box test
+// limited to t <= t_best + r, tests the splats of the leaves it reaches with
+// the exact float32 ray/disk test, and finally applies Eq. 23 to the
+// candidates within r of the nearest hit.  Because the boxes only cull and
+// the candidate set and its selection do not depend on visiting order, the
+// hit ids equal those of a brute-force search over all splats.
+//
+// Between bounces the live rays are compacted into a queue with one atomic
+// per warp (ballot + popc); per-ray state lives in the last-hit records, so a
+// ray that misses simply keeps its previous record.
+#include <cstring>
+
+#include "pe_internal.cuh"
+
+namespace {
+
+constexpr int kTraceThreads = 128;
+constexpr int kStack = 96;
+
+struct march_args {
+  pe_geom_layout L;
+  pe_view_batch vb;
+  pe_hits h;
+  const unsigned long long *keys;
+  const float *nrm;
+  const uint32_t *q_in;
+  const uint32_t *n_in;
+  uint32_t *q_out;
+  uint32_t *n_out;
+  int32_t bounce;
+  int32_t mb;
+  float eps;
+  float r_ov;
+  unsigned int *err;
+  long long *stats;
+};
+
+struct vray {
+  float ox, oy, oz, ix, iy, iz;
+};
+
+struct qstate {
+  float tb;
+  uint32_t ib;
+  int nc;
+  float ct[PE_MAX_CAND];
+  uint32_t cid[PE_MAX_CAND];
+};
+
+__device__ __forceinline__ bool box_hit(float4 lo, float4 hi, const vray &r, float t0, float t1) {
+  if (lo.x > hi.x) return false;
+  float ax = (lo.x - r.ox) * r.ix, bx = (hi.x - r.ox) * r.ix;
+  float ay = (lo.y - r.oy) * r.iy, by = (hi.y - r.oy) * r.iy;
+  float az = (lo.z - r.oz) * r.iz, bz = (hi.z - r.oz) * r.iz;
+  float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), t0));
+  float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), t1));
+  return tn <= tf;
+}
+
+__device__ __forceinline__ void note_hit(qstate &S, float t, uint32_t id, float r_ov,
+                                         unsigned int *err) {
+  if (t < S.tb || (t == S.tb && id < S.ib)) {
+    S.tb = t;
+    S.ib = id;
+  }
+  float lim = pe_add(S.tb, r_ov);
+  if (!(t <= lim)) return;
+  if (S.nc == PE_MAX_CAND) {  // drop entries the shrinking limit excludes
+    int k = 0;
+    for (int m = 0; m < S.nc; ++m)
+      if (S.ct[m] <= lim) {
+        S.ct[k] = S.ct[m];
+        S.cid[k] = S.cid[m];
+        ++k;
+      }
+    S.nc = k;
+  }
+  if (S.nc < PE_MAX_CAND) {
+    S.ct[S.nc] = t;
+    S.cid[S.nc] = id;
+    ++S.nc;
+  } else {
+    pe_raise(err, PE_ERR_OVERFLOW);
+  }
+}
+
+// Walk every view's pyramid.  ANY: return at the first hit with t > tmin.
+template <bool ANY>
+__device__ bool walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
+                     qstate &S, unsigned int *err, long long &n_splat, long long &n_node) {
+  uint32_t stack[kStack];
+  for (int v = 0; v < L.nv; ++v) {
+    const pe_view &V = L.view[v];
+    const float pad = L.pad[v];
+    pe_f3 q = {o.x - V.o[0], o.y - V.o[1], o.z - V.o[2]};
+    vray r;
+    r.ox = q.x * V.u[0] + q.y * V.u[1] + q.z * V.u[2];
+    r.oy = q.x * V.v[0] + q.y * V.v[1] + q.z * V.v[2];
+    r.oz = q.x * V.d[0] + q.y * V.d[1] + q.z * V.d[2];
+    r.ix = 1.0f / (d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2]);
+    r.iy = 1.0f / (d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2]);
+    r.iz = 1.0f / (d.x * V.d[0] + d.y * V.d[1] + d.z * V.d[2]);
+    const int top = L.nlev[v] - 1;
+    int sp = 0;
+    stack[sp++] = (uint32_t)top << 28;
+    const int64_t poff = L.pix_off[v];
+    while (sp > 0) {
+      uint32_t e = stack[--sp];
+      int l = (int)(e >> 28);
+      int idx = (int)(e & 0x0fffffffu);
+      int64_t nid = L.node_off[v][l] + idx;
+      float4 lo = __ldg(L.nodes + 2 * nid), hi = __ldg(L.nodes + 2 * nid + 1);
+      ++n_node;
+      float t1 = ANY ? INFINITY : fmaf(fabsf(pe_add(S.tb, r_ov)), 1e-6f, pe_add(S.tb, r_ov)) + pad;
+      float t0 = tmin - pad - 1e-6f * fabsf(tmin);
+      if (!box_hit(lo, hi, r, t0, t1)) continue;
+      int tw = L.tw[v][l];
+      int tx = idx % tw, ty = idx / tw;
+      if (l == 0) {
+        for (int jj = 0; jj < PE_LEAF; ++jj) {
+          int j = ty * PE_LEAF + jj;
+          if (j >= V.H) break;
+          for (int ii = 0; ii < PE_LEAF; ++ii) {
+            int i = tx * PE_LEAF + ii;
+            if (i >= V.W) break;
+            int64_t g = poff + (int64_t)j * V.W + i;
+            float4 c = __ldg(L.cr + g);
+            if (!(c.w > 0.0f)) continue;
+            float4 n = __ldg(L.nf + g);
+            ++n_splat;
+            float t;
+            pe_f3 x, ee;
+            if (!pe_hit_disk(o, d, {c.x, c.y, c.z}, {n.x, n.y, n.z}, c.w, tmin, t, x, ee)) continue;
+            if (ANY) return true;
+            note_hit(S, t, (uint32_t)g, r_ov, err);
+          }
+        }
+      } else {
+        int cw = L.tw[v][l - 1], ch = L.th[v][l - 1];
+        for (int j = PE_FAN - 1; j >= 0; --j)
+          for (int i = PE_FAN - 1; i >= 0; --i) {
+            int cx = tx * PE_FAN + i, cy = ty * PE_FAN + j;
+            if (cx >= cw || cy >= ch) continue;
+            if (sp >= kStack) {
+              pe_raise(err, PE_ERR_OVERFLOW);
+              continue;
+            }
+            stack[sp++] = ((uint32_t)(l - 1) << 28) | (uint32_t)(cy * cw + cx);
+          }
+      }
+    }
+  }
+  return false;
+}
+
+// Eq. 23 on the final candidate set: select the hit closest to its splat's
+// centre relative to R (ties: smaller t, smaller id); blend the normals in
+// splat-id order with weights 1 - rho, normalise, turn against the ray.
+__device__ bool nearest(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
+                        unsigned int *err, pe_f3 &xo, pe_f3 &no, uint32_t &ido,
+                        long long &n_splat, long long &n_node) {
+  qstate S;
+  S.tb = INFINITY;
+  S.ib = PE_NONE;
+  S.nc = 0;
+  walk<false>(L, o, d, tmin, r_ov, S, err, n_splat, n_node);
+  if (S.ib == PE_NONE) return false;
+  float lim = pe_add(S.tb, r_ov);
+  int k = 0;
+  for (int m = 0; m < S.nc; ++m)
+    if (S.ct[m] <= lim) S.cid[k++] = S.cid[m];
+  for (int a = 1; a < k; ++a) {  // insertion sort by id
+    uint32_t x = S.cid[a];
+    int b = a;
+    while (b > 0 && S.cid[b - 1] > x) {
+      S.cid[b] = S.cid[b - 1];
+      --b;
+    }
+    S.cid[b] = x;
+  }
+  pe_f3 m = {0.f, 0.f, 0.f}, nsel = {0.f, 0.f, 0.f}, xsel = {0.f, 0.f, 0.f};
+  float best_rho = INFINITY, best_t = INFINITY;
+  uint32_t sel = PE_NONE;
+  for (int a = 0; a < k; ++a) {
+    uint32_t g = S.cid[a];
+    float4 c = __ldg(L.cr + g), n4 = __ldg(L.nf + g);
+    float t;
+    pe_f3 x, e;
+    pe_hit_disk(o, d, {c.x, c.y, c.z}, {n4.x, n4.y, n4.z}, c.w, tmin, t, x, e);
+    float rho = pe_div(pe_sqrt(pe_dot(e, e)), c.w);
+    pe_f3 nn = {n4.x, n4.y, n4.z};
+    if (pe_dot(nn, d) > 0.0f) nn = pe_neg3(nn);
+    float w = pe_sub(1.0f, rho);
+    m.x = pe_add(m.x, pe_mul(w, nn.x));
+    m.y = pe_add(m.y, pe_mul(w, nn.y));
+    m.z = pe_add(m.z, pe_mul(w, nn.z));
+    if (rho < best_rho || (rho == best_rho && t < best_t)) {
+      best_rho = rho;
+      best_t = t;
+      sel = g;
+      xsel = x;
+      nsel = nn;
+    }
+  }
+  float mm = pe_dot(m, m);
+  if (mm == 0.0f) {
+    no = nsel;
+  } else {
+    float s = pe_sqrt(mm);
+    no = {pe_div(m.x, s), pe_div(m.y, s), pe_div(m.z, s)};
+    if (pe_dot(no, d) > 0.0f) no = pe_neg3(no);
+  }
+  xo = xsel;
+  ido = sel;
+  return true;
+}
+
+__device__ __forceinline__ double path_start(pe_f3 d, pe_f3 p) {
+  return __dadd_rn(__dadd_rn(__dmul_rn((double)d.x, (double)p.x), __dmul_rn((double)d.y, (double)p.y)),
+                   __dmul_rn((double)d.z, (double)p.z));
+}
+
+__device__ __forceinline__ double seg_len(pe_f3 a, pe_f3 b) {
+  double dx = __dsub_rn((double)b.x, (double)a.x);
+  double dy = __dsub_rn((double)b.y, (double)a.y);
+  double dz = __dsub_rn((double)b.z, (double)a.z);
+  return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+__device__ __forceinline__ void st3(float *a, int64_t i, pe_f3 v) {
+  a[3 * i] = v.x;
+  a[3 * i + 1] = v.y;
+  a[3 * i + 2] = v.z;
+}
+__device__ __forceinline__ pe_f3 ld3(const float *a, int64_t i) {
+  return {a[3 * i], a[3 * i + 1], a[3 * i + 2]};
+}
+
+// Warp-cooperative append of `slot` to a queue when `keep`.
+__device__ __forceinline__ void warp_append(bool keep, uint32_t slot, uint32_t *q, uint32_t *n) {
+  unsigned mask = __ballot_sync(0xffffffffu, keep);
+  if (!mask) return;
+  int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(n, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (keep) q[base + __popc(mask & ((1u << lane) - 1u))] = slot;
+}
+
+__device__ __forceinline__ void flush_stats(long long *stats, long long a, long long b,
+                                            long long c, long long d) {
+  if (!stats) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+    d += __shfl_down_sync(0xffffffffu, d, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (a) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 0), (unsigned long long)a);
+    if (b) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 1), (unsigned long long)b);
+    if (c) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 2), (unsigned long long)c);
+    if (d) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 3), (unsigned long long)d);
+  }
+}
+
+// Bounce 1 from the incidence screen's GFB keys (or, geom_first, by marching
+// the splats from the screen).  Writes every slot's record.
+__global__ void __launch_bounds__(kTraceThreads)
+    primary_kernel(const __grid_constant__ march_args A, int geom_first) {
+  const int64_t per_view = (int64_t)A.vb.W * A.vb.H;
+  const int64_t n_rays = per_view * A.vb.n;
+  long long nq = 0, ns = 0, nn = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_rays;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    int64_t slot = base + threadIdx.x;
+    bool active = slot < n_rays;
+    bool live = false;
+    if (active) {
+      const pe_view &V = A.vb.v[slot / per_view];
+      int64_t p = slot % per_view;
+      int i = (int)(p % V.W), j = (int)(p / V.W);
+      pe_f3 o = pe_pixel_origin(V, i, j);
+      pe_f3 d = pe_v3(V.d);
+      pe_f3 u = {pe_mul(V.pitch, V.u[0]), pe_mul(V.pitch, V.u[1]), pe_mul(V.pitch, V.u[2])};
+      pe_f3 v = {pe_mul(V.pitch, V.v[0]), pe_mul(V.pitch, V.v[1]), pe_mul(V.pitch, V.v[2])};
+      bool hit = false;
+      pe_f3 x = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 0.f};
+      uint32_t id = PE_NONE;
+      ++nq;
+      if (geom_first) {
+        hit = nearest(A.L, o, d, 0.0f, A.r_ov, A.err, x, n, id, ns, nn);
+      } else {
+        unsigned long long key = A.keys[slot];
+        if (key != ~0ull) {
+          hit = true;
+          float t = __uint_as_float((uint32_t)(key >> 32));
+          id = (uint32_t)(key & 0xffffffffull);
+          x = pe_ray_at(o, t, d);
+          n = {__ldg(A.nrm + 3 * (int64_t)id), __ldg(A.nrm + 3 * (int64_t)id + 1),
+               __ldg(A.nrm + 3 * (int64_t)id + 2)};
+          if (pe_dot(n, d) > 0.0f) n = pe_neg3(n);
+        }
+      }
+      A.h.M[slot] = hit ? 1 : 0;
+      A.h.psi[slot] = 1;
+      if (A.h.ids) A.h.ids[slot] = id;
+      st3(A.h.p, slot, x);
+      st3(A.h.n, slot, n);
+      st3(A.h.k, slot, d);
+      st3(A.h.u, slot, u);
+      st3(A.h.v, slot, v);
+      A.h.path[slot] = hit ? path_start(d, x) : 0.0;
+      live = hit && A.mb >= 2;
+    }
+    if (A.q_out) warp_append(live, (uint32_t)slot, A.q_out, A.n_out);
+  }
+  flush_stats(A.stats, nq, 0, ns, nn);
+}
+
+// One bounce (b >= 2) for the rays of q_in.
+__global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_constant__ march_args A) {
+  const uint32_t n_in = *A.n_in;
+  const int64_t n_rays = A.h.n_rays;
+  long long nq = 0, ns = 0, nn = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_in;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    int64_t qi = base + threadIdx.x;
+    bool active = qi < n_in;
+    bool live = false;
+    uint32_t slot = 0;
+    if (active) {
+      slot = A.q_in[qi];
+      pe_f3 p = ld3(A.h.p, slot), n = ld3(A.h.n, slot), d = ld3(A.h.k, slot);
+      pe_f3 u = ld3(A.h.u, slot), v = ld3(A.h.v, slot);
+      pe_f3 rd = pe_reflect(d, n);
+      float len = pe_sqrt(pe_dot(rd, rd));
+      d = {pe_div(rd.x, len), pe_div(rd.y, len), pe_div(rd.z, len)};
+      u = pe_reflect(u, n);
+      v = pe_reflect(v, n);
+      pe_f3 x, n2;
+      uint32_t id;
+      ++nq;
+      if (nearest(A.L, p, d, A.eps, A.r_ov, A.err, x, n2, id, ns, nn)) {
+        A.h.path[slot] = __dadd_rn(A.h.path[slot], seg_len(p, x));
+        st3(A.h.p, slot, x);
+        st3(A.h.n, slot, n2);
+        st3(A.h.k, slot, d);
+        st3(A.h.u, slot, u);
+        st3(A.h.v, slot, v);
+        A.h.M[slot] = A.bounce;
+        if (A.h.ids) A.h.ids[(int64_t)(A.bounce - 1) * n_rays + slot] = id;
+        live = A.bounce < A.mb;
+      }
+    }
+    if (A.q_out) warp_append(live, slot, A.q_out, A.n_out);
+  }
+  flush_stats(A.stats, nq, 0, ns, nn);
+}
+
+// Psi: shadow ray from the last hit toward the receiver (monostatic: w).
+__global__ void __launch_bounds__(kTraceThreads) shadow_kernel(const __grid_constant__ march_args A) {
+  const int64_t per_view = (int64_t)A.vb.W * A.vb.H;
+  const int64_t n_rays = A.h.n_rays;
+  long long nsh = 0, ns = 0, nn = 0;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < n_rays;
+       slot += (int64_t)gridDim.x * blockDim.x) {
+    if (A.h.M[slot] < 2) continue;
+    const pe_view &V = A.vb.v[slot / per_view];
+    pe_f3 w = {-V.d[0], -V.d[1], -V.d[2]};
+    qstate S;
+    S.tb = INFINITY;
+    S.ib = PE_NONE;
+    S.nc = 0;
+    ++nsh;
+    bool blocked = walk<true>(A.L, ld3(A.h.p, slot), w, A.eps, A.r_ov, S, A.err, ns, nn);
+    A.h.psi[slot] = blocked ? 0 : 1;
+  }
+  flush_stats(A.stats, 0, nsh, ns, nn);
+}
+
+int sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + kTraceThreads - 1) / kTraceThreads;
+  int64_t cap = (int64_t)sms() * 16;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
+  if (!g || !g->blob_dev) return false;
+  if (!pe_make_layout(g->n_views, g->views, L)) return false;
+  size_t a, b, c, t;
+  pe_layout_offsets(*L, &a, &b, &c, &t);
+  if (g->blob_bytes < t) return false;
+  char *blob = static_cast<char *>(g->blob_dev);
+  L->cr = reinterpret_cast<const float4 *>(blob + a);
+  L->nf = reinterpret_cast<const float4 *>(blob + b);
+  L->nodes = reinterpret_cast<const float4 *>(blob + c);
+  return true;
+}
+
+}  // namespace
+
+size_t pe_trace_ws_bytes(int64_t n_rays) {
+  pe_carve c{nullptr, 0};
+  pe_trace_ws_carve(c, n_rays);
+  return c.bytes();
+}
+
+pe_trace_ws pe_trace_ws_carve(pe_carve &c, int64_t n_rays) {
+  pe_trace_ws w;
+  w.q0 = c.take<uint32_t>((size_t)n_rays);
+  w.q1 = c.take<uint32_t>((size_t)n_rays);
+  w.counts = c.take<uint32_t>(PE_MAX_BATCH);
+  return w;
+}
+
+pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,
+                          const float *nrm, const pe_geom *geom, int32_t mb,
+                          const pe_params &prm, const pe_trace_ws &tw, const pe_hits &h,
+                          int64_t *stats, cudaStream_t s) {
+  march_args A;
+  memset(&A, 0, sizeof(A));
+  bool have_geom = geom != nullptr;
+  if (have_geom && !geom_layout(geom, &A.L))
+    return pe_fail(PE_EINVAL, "trace: invalid geometry (views or blob size)");
+  if (!have_geom && (mb > 1 || prm.first_bounce_from_geom))
+    return pe_fail(PE_EINVAL, "trace: bounces beyond the first need the aggregated geometry");
+  A.vb = vb;
+  A.h = h;
+  A.keys = keys;
+  A.nrm = nrm;
+  A.mb = mb;
+  A.eps = prm.eps;
+  A.r_ov = prm.overlap_r;
+  A.err = pe_err_word();
+  A.stats = reinterpret_cast<long long *>(stats);
+  const int64_t n_rays = (int64_t)vb.W * vb.H * vb.n;
+  if (h.ids) PE_TRY_CUDA(cudaMemsetAsync(h.ids, 0xff, sizeof(uint32_t) * n_rays * mb, s));
+  PE_TRY_CUDA(cudaMemsetAsync(tw.counts, 0, sizeof(uint32_t) * PE_MAX_BATCH, s));
+  uint32_t *qa = tw.q0, *qb = tw.q1;
+  uint32_t *na = tw.counts, *nb = tw.counts + 1;
+  A.q_out = mb >= 2 ? qa : nullptr;
+  A.n_out = na;
+  A.bounce = 1;
+  primary_kernel<<<grid_for(n_rays), kTraceThreads, 0, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
+  PE_TRY_LAUNCH("primary_kernel");
+  for (int b = 2; b <= mb; ++b) {
+    A.bounce = b;
+    A.q_in = qa;
+    A.n_in = na;
+    A.q_out = b < mb ? qb : nullptr;
+    A.n_out = nb;
+    PE_TRY_CUDA(cudaMemsetAsync(nb, 0, sizeof(uint32_t), s));
+    march_kernel<<<grid_for(n_rays), kTraceThreads, 0, s>>>(A);
+    PE_TRY_LAUNCH("march_kernel");
+    uint32_t *t = qa;
+    qa = qb;
+    qb = t;
+    t = na;
+    na = nb;
+    nb = t;
+  }
+  if (mb >= 2) {
+    shadow_kernel<<<grid_for(n_rays), kTraceThreads, 0, s>>>(A);
+    PE_TRY_LAUNCH("shadow_kernel");
+  }
+  return PE_OK;
+}
+
+extern "C" size_t pe_trace_workspace(int32_t n_views, const pe_view *views) {
+  if (n_views < 1 || !views) return 0;
+  int64_t n = (int64_t)views[0].W * views[0].H * n_views;
+  return pe_trace_ws_bytes(n) + 256;
+}
+
+extern "C" pe_status pe_trace_bounces(const pe_view *views, int32_t n_views,
+                                      const uint64_t *keys, const float *nrm,
+                                      const pe_geom *geom, int32_t max_bounces,
+                                      const pe_params *prm, void *ws, size_t ws_bytes,
+                                      const pe_hits *hits, int64_t *stats, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!views || n_views < 1 || n_views > PE_MAX_BATCH || !prm || !hits)
+    return pe_fail(PE_EINVAL, "pe_trace_bounces: bad arguments");
+  for (int i = 1; i < n_views; ++i)
+    if (views[i].W != views[0].W || views[i].H != views[0].H)
+      return pe_fail(PE_EINVAL, "pe_trace_bounces: all screens must share W x H");
+  if (max_bounces < 1 || max_bounces > 64)
+    return pe_fail(PE_EINVAL, "pe_trace_bounces: max_bounces in [1, 64]");
+  int64_t n_rays = (int64_t)views[0].W * views[0].H * n_views;
+  if (n_rays >= (int64_t)PE_NONE) return pe_fail(PE_EINVAL, "pe_trace_bounces: too many rays");
+  if (hits->n_rays != n_rays || !hits->p || !hits->n || !hits->k || !hits->u || !hits->v ||
+      !hits->path || !hits->M || !hits->psi)
+    return pe_fail(PE_EINVAL, "pe_trace_bounces: hits must hold n_views*W*H records");
+  if (!prm->first_bounce_from_geom && (!keys || !nrm))
+    return pe_fail(PE_EINVAL, "pe_trace_bounces: bounce 1 from the GFB needs keys and nrm");
+  size_t need = pe_trace_workspace(n_views, views);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_trace_bounces: workspace needs %zu bytes", need);
+  pe_view_batch vb;
+  memset(&vb, 0, sizeof(vb));
+  vb.n = n_views;
+  vb.W = views[0].W;
+  vb.H = views[0].H;
+  for (int i = 0; i < n_views; ++i) vb.v[i] = views[i];
+  pe_carve c{static_cast<char *>(ws), 0};
+  pe_trace_ws tw = pe_trace_ws_carve(c, n_rays);
+  pe_hits h = *hits;
+  h.max_bounces = max_bounces;
+  return pe_launch_trace(vb, reinterpret_cast<const unsigned long long *>(keys), nrm, geom,
+                         max_bounces, *prm, tw, h, stats, s);
+}

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every symbol the header declares, computes views exactly as
+the oracle does, sizes workspaces, and rejects bad arguments before touching
+the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pointemray.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2408_15583_gb300 import _lib
+    from paper_2408_15583_gb300.build import build
+    build()
+    return _lib.load()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pe_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("pe_build_gfb", "pe_aggregate_views", "pe_trace_bounces", "pe_po_field",
+                     "pe_rcs_sweep", "pe_stream_check", "pe_last_error", "pe_abi_version"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2408_15583_gb300 import _lib
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+    assert lib.pe_abi_version() == 1
+
+
+def test_view_setup_matches_oracle_bitwise(lib):
+    from paper_2408_15583_gb300 import api
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        th, ph = float(rng.uniform(0, 180)), float(rng.uniform(-360, 360))
+        c = rng.normal(size=3) * 3
+        ext = float(rng.uniform(0.05, 30))
+        W = int(rng.integers(1, 4097))
+        v = api.view_from_angles(th, ph, c, ext, W, W)
+        o = oracle.view_from_angles(th, ph, c, ext, W, W, "fp32")
+        a = np.array(list(v.o) + list(v.u) + list(v.v) + list(v.d) + [v.pitch], np.float32)
+        b = np.array(list(o.o) + list(o.u) + list(o.v) + list(o.d) + [o.pitch], np.float32)
+        assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_workspace_queries(lib):
+    from paper_2408_15583_gb300 import api
+    vs = [api.view_from_angles(60, 45 + 90 * i, [0, 0, 0], 1.0, 512, 512) for i in range(8)]
+    arr = api.views_to_array(vs)
+    assert lib.pe_build_gfb_workspace(8, arr) >= 8 * 512 * 512 * 8
+    g = lib.pe_geom_bytes(8, arr)
+    assert g >= 8 * 512 * 512 * 32
+    assert lib.pe_aggregate_workspace(8, arr, 256) >= 256 ** 3 * 8
+    assert lib.pe_aggregate_workspace(8, arr, 257) == 0
+    assert lib.pe_trace_workspace(8, arr) >= 8 * 512 * 512 * 8
+    assert lib.pe_po_workspace(4, 1 << 20, 64) > 0
+    assert lib.pe_po_workspace(0, 1 << 20, 64) == 0
+    sw = api.SweepArgs([90.0] * 3, [0.0, 1.0, 2.0], 1024, 1024, [0, 0, 0], 1.1,
+                       np.linspace(8e9, 12e9, 64), 2)
+    assert sw.workspace_bytes() > 3 * 1024 * 1024 * 80
+    bad = api.SweepArgs([90.0], [0.0], 1024, 1024, [0, 0, 0], -1.0, [1e9], 2)
+    assert bad.workspace_bytes() == 0
+
+
+def test_argument_errors_before_any_device_work(lib):
+    from paper_2408_15583_gb300 import api
+    v = api.views_to_array([api.view_from_angles(0, 0, [0, 0, 0], 1.0, 8, 8)])
+    # zero views, too many views, bad mode: rejected synchronously
+    assert lib.pe_build_gfb(v, 0, None, None, None, 0, 0, 0.0, None, 0, None, None, None,
+                            None, None) == 1
+    assert lib.pe_build_gfb(v, 65, None, None, None, 0, 0, 0.0, None, 0, None, None, None,
+                            None, None) == 1
+    assert lib.pe_build_gfb(v, 1, None, None, None, 0, 7, 0.0, None, 0, None, None, None,
+                            None, None) == 1
+    assert b"mode" in lib.pe_last_error()
+    # workspace too small
+    assert lib.pe_build_gfb(v, 1, None, None, None, 0, 0, 0.0, None, 0, None, None, None,
+                            None, None) == 2
+    assert lib.pe_view_from_angles(0.0, 0.0, None, 1.0, 8, 8, None) == 1
+    assert lib.pe_trace_bounces(v, 1, None, None, None, 0, None, None, 0, None, None, None) == 1
+    assert lib.pe_po_field(None, 1, 1, None, None, 1, None, 0, None, None) == 1

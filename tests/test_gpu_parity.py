@@ -1,0 +1,331 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: hit-index buffers, bounce counts, splats and every value that decides a
+hit are bit-exact against the oracle's FP32-geometry mode; the PO field is
+within 1e-3 relative per sample (||E - E_ref|| / max(||E_ref||, 1e-3 max
+||E_ref||)) and sigma within 0.1 dB where sigma_ref >= peak - 40 dB.  The
+oracle computes every expected value from the same seeded inputs; nothing it
+uses comes from the CUDA path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _mods():
+    from paper_2408_15583_gb300 import api, pipeline
+    return api, pipeline
+
+
+def _oracle_view(v):
+    return oracle.View(o=np.array(v.o[:], np.float64), u=np.array(v.u[:], np.float64),
+                       v=np.array(v.v[:], np.float64), d=np.array(v.d[:], np.float64),
+                       pitch=float(v.pitch), W=v.W, H=v.H)
+
+
+def _keys_oracle(sc, v, tube=False, delta=0.0):
+    return oracle.gfb(sc, v, "fp32", tube=tube, delta=delta).keys()
+
+
+def field_err(E, Eref):
+    """Per-sample relative error of c24: ||E - Eref|| / max(||Eref||, 1e-3 max||Eref||),
+    over [..., pol, xyz] complex arrays, per polarisation."""
+    d = np.sqrt((np.abs(E - Eref) ** 2).sum(axis=-1))
+    r = np.sqrt((np.abs(Eref) ** 2).sum(axis=-1))
+    floor = 1e-3 * r.max()
+    return d / np.maximum(r, floor)
+
+
+def _cplx(E):
+    E = E.detach().cpu().numpy()
+    return E[..., 0] + 1j * E[..., 1]
+
+
+# ----------------------------------------------------------------------------
+# a1/a2/a3
+# ----------------------------------------------------------------------------
+
+SCENES = {
+    "dihedral": lambda: scenes.dihedral(2000, seed=31),
+    "sphere": lambda: scenes.sphere(3000, 1.0),
+    "composite": lambda: scenes.composite(6000, seed=9, pca=True),
+}
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+@pytest.mark.parametrize("WH", [(72, 72), (70, 45)])
+def test_gfb_keys_bitexact(name, WH):
+    api, pipe = _mods()
+    sc = SCENES[name]()
+    c, r = scenes.bounding_sphere(sc.pos)
+    views = pipe.views_from_angles([90.0, 60.0, 133.0], [20.0, 200.0, 311.0], c, r * 1.05, *WH)
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    out = api.build_gfb(views, pos, nrm, rad, 0)
+    api.stream_check()
+    keys = out["keys"].cpu().numpy().view(np.uint64).reshape(3, -1)
+    nd = out["nd"].cpu().numpy().reshape(3, -1, 4)
+    for i, v in enumerate(views):
+        g = oracle.gfb(sc, _oracle_view(v), "fp32")
+        assert np.array_equal(keys[i], g.keys()), f"view {i}"
+        hit = g.idx >= 0
+        assert np.array_equal(nd[i][hit, :3].astype(np.float64), g.nrm[hit])
+        assert np.array_equal(nd[i][hit, 3].astype(np.float64), g.depth[hit])
+        assert np.all(np.isinf(nd[i][~hit, 3]))
+    assert np.array_equal(out["mask"].cpu().numpy(), (keys.ravel() != np.uint64(2 ** 64 - 1)))
+    hits = out["hit"].cpu().numpy().view(np.uint32)
+    assert np.array_equal(hits, (keys.ravel() & np.uint64(0xFFFFFFFF)).astype(np.uint32))
+
+
+def test_gfb_tube_mode_bitexact():
+    api, pipe = _mods()
+    sc = scenes.dihedral(3000, seed=4)
+    c, r = scenes.bounding_sphere(sc.pos)
+    views = pipe.views_from_angles([60.0, 120.0], [45.0, 135.0], c, r * 1.05, 64, 64)
+    delta = 2.0 * views[0].pitch
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    out = api.build_gfb(views, pos, None, None, 1, delta)
+    keys = out["keys"].cpu().numpy().view(np.uint64).reshape(2, -1)
+    for i, v in enumerate(views):
+        g = oracle.gfb(sc, _oracle_view(v), "fp32", tube=True, delta=float(np.float32(delta)))
+        assert np.array_equal(keys[i], g.keys())
+
+
+def test_gfb_edge_cases():
+    api, pipe = _mods()
+    views = pipe.views_from_angles([0.0], [0.0], [0, 0, 0], 1.0, 17, 9)
+    # no points: every pixel misses
+    z = torch.zeros((0, 3), dtype=torch.float32, device=DEV)
+    out = api.build_gfb(views, z, z, torch.zeros(0, device=DEV), 0)
+    assert torch.all(out["mask"] == 0)
+    # a single point, and one behind the screen (t < 0), and a NaN point
+    sc = scenes.Scene(pos=np.array([[0.05, -0.02, 0.0], [0.0, 0.0, 5.0], [np.nan, 0, 0]], np.float32),
+                      nrm=np.array([[0, 0, 1], [0, 0, 1], [0, 0, 1]], np.float32),
+                      rad=np.array([0.3, 0.5, 0.3], np.float32))
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    out = api.build_gfb(views, pos, nrm, rad, 0)
+    keys = out["keys"].cpu().numpy().view(np.uint64)
+    g = oracle.gfb(sc, _oracle_view(views[0]), "fp32")
+    assert np.array_equal(keys, g.keys())
+    assert set(np.unique(g.idx)) <= {-1, 0}
+    with pytest.raises(RuntimeError):
+        api.build_gfb(views, pos, None, rad, 0)     # surfel mode needs normals
+
+
+# ----------------------------------------------------------------------------
+# a4 / a5 on a shared small geometry
+# ----------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small_geom():
+    api, pipe = _mods()
+    sc = scenes.dihedral(3000, seed=12)
+    vd = scenes.aggregation_views(sc, 80, 80)
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    gv = pipe.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, vd.W, vd.H)
+    prm = pipe.default_params(sc.pos, gv)
+    geom, g = pipe.build_geometry(pos, nrm, rad, gv, prm)
+    api.stream_check()
+    ogv = [_oracle_view(v) for v in gv]
+    ogf = [oracle.gfb(sc, v, "fp32") for v in ogv]
+    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
+                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
+    S = oracle.aggregate(ogf, fp, "fp32")
+    return dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, S=S, ogv=ogv)
+
+
+def test_aggregate_splats_bitexact(small_geom):
+    geom, S = small_geom["geom"], small_geom["S"]
+    cr, nf = geom.planes()
+    cr = cr.cpu().numpy()
+    nf = nf.cpu().numpy()
+    ids = np.flatnonzero(cr[:, 3] > 0)
+    assert S.ns > 1000
+    assert np.array_equal(ids, S.id)
+    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
+    assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
+    assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
+    assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
+
+
+@pytest.mark.parametrize("geom_first", [False, True])
+def test_trace_bounces_bitexact(small_geom, geom_first):
+    api, pipe = _mods()
+    d = small_geom
+    sc = d["sc"]
+    c, r = scenes.bounding_sphere(sc.pos)
+    th, ph = [90.0, 90.0, 75.0], [45.0, 10.0, 58.0]
+    views = pipe.views_from_angles(th, ph, c, r * 1.02, 40, 40)
+    prm = pipe.default_params(sc.pos, d["gv"], first_bounce_from_geom=geom_first)
+    mb = 3
+    keys = None
+    if not geom_first:
+        keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    stats = torch.zeros(8, dtype=torch.int64, device=DEV)
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, prm, stats=stats)
+    api.stream_check()
+    per = 40 * 40
+    for a, v in enumerate(views):
+        ov = _oracle_view(v)
+        first = None if geom_first else oracle.gfb(sc, ov, "fp32")
+        tr = oracle.trace(ov, d["S"], mb, float(prm.eps), float(prm.overlap_r), first=first,
+                          mode="fp32")
+        sl = slice(a * per, (a + 1) * per)
+        assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), f"angle {a}"
+        ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
+        ids[ids == 0xFFFFFFFF] = -1
+        assert np.array_equal(ids.T, tr.ids), f"angle {a}"
+        assert np.array_equal(h.psi[sl].cpu().numpy(), tr.psi)
+        live = tr.M > 0
+        for name in ("p", "n", "k", "u", "v"):
+            got = getattr(h, name)[sl].cpu().numpy().astype(np.float64)
+            assert np.array_equal(got[live], getattr(tr, name)[live]), name
+        path = h.path[sl].cpu().numpy()
+        assert np.allclose(path[live], tr.path[live], rtol=1e-13, atol=1e-13)
+    if not geom_first:
+        assert (h.M.cpu().numpy() >= 2).sum() > 100   # the case exercises bounces
+    st = stats.cpu().numpy()
+    assert st[0] >= 3 * per and st[2] > 0 and st[3] > 0
+
+
+# ----------------------------------------------------------------------------
+# a6
+# ----------------------------------------------------------------------------
+
+def _hits_from_trace(api, tr):
+    n = tr.M.shape[0]
+    h = api.alloc_hits(n, 1, DEV, ids=False)
+    for name in ("p", "n", "k", "u", "v"):
+        getattr(h, name).copy_(torch.from_numpy(getattr(tr, name).astype(np.float32)))
+    h.path.copy_(torch.from_numpy(tr.path))
+    h.M.copy_(torch.from_numpy(tr.M))
+    h.psi.copy_(torch.from_numpy(tr.psi))
+    return h
+
+
+def test_po_field_synthetic_plate_many_freqs():
+    # synthetic (oracle-free) inputs: a plate tiled by projected screen cells
+    # at oblique incidence; 64 frequencies 8-12 GHz.
+    api, _ = _mods()
+    th = math.radians(25.0)
+    w = np.array([math.sin(th), 0, math.cos(th)])
+    u = np.array([math.cos(th), 0, -math.sin(th)])
+    v = np.array([0, 1.0, 0])
+    d = -w
+    a, b, nu, nv = 0.3, 0.2, 60, 40
+    us = (a / nu * math.cos(th)) * u
+    vs = (b / nv) * v
+    up = us - d * (us[2] / d[2])
+    vp = vs - d * (vs[2] / d[2])
+    ii, jj = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    ps = (ii.ravel()[:, None] - (nu - 1) / 2) * up[None] + (jj.ravel()[:, None] - (nv - 1) / 2) * vp[None]
+    ps = (ps + np.array([0.1, -0.05, 0.02])).astype(np.float32).astype(np.float64)
+    n = ps.shape[0]
+    f32 = lambda x: np.asarray(x, np.float32).astype(np.float64)
+    tr = oracle.Trace(M=np.ones(n, np.int32), ids=np.zeros((n, 1), np.int64), p=ps,
+                      n=np.tile([0, 0, 1.0], (n, 1)), k=np.tile(f32(d), (n, 1)),
+                      u=np.tile(f32(us), (n, 1)), v=np.tile(f32(vs), (n, 1)),
+                      path=ps @ f32(d), psi=np.ones(n, np.uint8))
+    freqs = scenes.freq_grid(8e9, 12e9, 64)
+    Eo = oracle.po_field(tr, freqs, f32(w))[0]
+    h = _hits_from_trace(api, tr)
+    E = _cplx(api.po_field(h, 1, n, f32(w)[None], freqs))[0]
+    assert field_err(E, Eo).max() < 1e-4
+
+
+def test_po_field_matches_oracle_on_traced_hits(small_geom):
+    api, pipe = _mods()
+    d = small_geom
+    sc = d["sc"]
+    c, r = scenes.bounding_sphere(sc.pos)
+    th, ph = [90.0, 80.0], [45.0, 20.0]
+    views = pipe.views_from_angles(th, ph, c, r * 1.02, 48, 48)
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], 2, d["prm"])
+    freqs = scenes.freq_grid(2.5e9, 3.5e9, 5)
+    ks = np.array([[-x for x in v.d] for v in views], np.float32)
+    E = _cplx(api.po_field(h, 2, 48 * 48, ks, freqs))
+    api.stream_check()
+    for a, v in enumerate(views):
+        ov = _oracle_view(v)
+        tr = oracle.trace(ov, d["S"], 2, float(d["prm"].eps), float(d["prm"].overlap_r),
+                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+        Eo = oracle.po_field(tr, freqs, ks[a].astype(np.float64))[0]
+        assert field_err(E[a], Eo).max() < 1e-3
+
+
+# ----------------------------------------------------------------------------
+# a7: the whole sweep
+# ----------------------------------------------------------------------------
+
+def _sigma_check(sig, ref, peak_db=40.0, tol_db=0.1):
+    sd, so = oracle.db(sig), oracle.db(ref)
+    keep = so >= so.max() - peak_db
+    return np.abs(sd - so)[keep].max()
+
+
+def test_rcs_sweep_matches_oracle(small_geom):
+    api, pipe = _mods()
+    d = small_geom
+    sc = d["sc"]
+    sw = scenes._sweep_over(sc, [90.0] * 5 + [70.0], [0.0, 13.0, 45.0, 62.0, 90.0, 30.0], 48,
+                            [2.9e9, 3.0e9, 3.3e9], 2)
+    args = api.SweepArgs.from_sweep(sw, angle_batch=4)     # two batches, ragged tail
+    E, sig = api.rcs_sweep(args, d["pos"], d["nrm"], d["rad"], d["geom"], d["prm"])
+    api.stream_check()
+    eps = float(d["prm"].eps)
+    ref = oracle.rcs_sweep(sc, sw, d["S"], eps, eps, mode="fp32")
+    Eg = _cplx(E)
+    assert field_err(Eg, ref.E).max() < 1e-3
+    s = sig.cpu().numpy()
+    assert _sigma_check(s[..., 0, 0], ref.sigma[..., 0, 0]) < 0.1
+    assert _sigma_check(s[..., 1, 1], ref.sigma[..., 1, 1]) < 0.1
+    # determinism: a second run is bit-identical
+    E2, _ = api.rcs_sweep(args, d["pos"], d["nrm"], d["rad"], d["geom"], d["prm"])
+    assert torch.equal(E, E2)
+
+
+def test_rcs_sweep_vs_fp64_physics_oracle(small_geom):
+    # The FP64 oracle traces in double precision: a handful of grazing rays
+    # can fall on the other side of a disk edge, so the bar is sigma within
+    # 0.1 dB where sigma >= peak - 20 dB.
+    api, pipe = _mods()
+    d = small_geom
+    sc = d["sc"]
+    sw = scenes._sweep_over(sc, [90.0] * 3, [0.0, 45.0, 90.0], 48, [3.0e9], 2)
+    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), d["pos"], d["nrm"], d["rad"],
+                           d["geom"], d["prm"])
+    vd = scenes.aggregation_views(sc, 80, 80)
+    S64, gv64, _, _ = oracle.build_geometry(sc, vd, "fp64")
+    eps = float(d["prm"].eps)
+    ref = oracle.rcs_sweep(sc, sw, S64, eps, eps, mode="fp64")
+    s = sig.cpu().numpy()
+    assert _sigma_check(s[..., 0, 0], ref.sigma[..., 0, 0], peak_db=20.0) < 0.1
+
+
+def test_rcs_sweep_single_bounce_without_geometry():
+    api, pipe = _mods()
+    sc = scenes.sphere(4000, 1.0)
+    sw = scenes._sweep_over(sc, [90.0, 30.0], [0.0, 100.0], 40, [3e9, 3.2e9], 1)
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    prm = api.make_params(sc.pos, 0.01, 0.01)
+    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), pos, nrm, rad, None, prm)
+    ref = oracle.rcs_sweep(sc, sw, None, 0.01, 0.01, mode="fp32")
+    assert field_err(_cplx(E), ref.E).max() < 1e-3
