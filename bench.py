@@ -243,7 +243,8 @@ def run_gpu(args, rank, world, local_rank):
         "data": "synthetic",
         "config": dict(desc, l2="flushed between steps (512 MB write outside the timed events)",
                        ray_bounces_per_step=bounces_per_step,
-                       shadow_queries_per_step=int(st[1]), parallelism=f"replicas{world}"),
+                       shadow_queries_per_step=int(st[1]), splat_tests_per_step=int(st[2]),
+                       node_tests_per_step=int(st[3]), parallelism=f"replicas{world}"),
         "rcs_samples_per_s": samples / (t_ms / 1e3),
         "e2e": {"value": per_gpu_units * world / (e2e_ms / 1e3), "unit": "ray-bounces/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -9,9 +9,11 @@
 
 #include "pointemray.h"
 
-#define PE_MAX_LEVELS 6
+#define PE_MAX_LEVELS 12
 #define PE_LEAF 8          // leaf tile edge in pixels
-#define PE_FAN 4           // tiles per pyramid level edge
+#ifndef PE_FAN
+#define PE_FAN 2           // tiles per pyramid level edge
+#endif
 #define PE_NONE 0xFFFFFFFFu
 
 // Device error word bits (pe_stream_check maps them to pe_status).

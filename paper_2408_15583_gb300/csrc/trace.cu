@@ -20,7 +20,6 @@
 namespace {
 
 constexpr int kTraceThreads = 128;
-constexpr int kStack = 96;
 
 struct march_args {
   pe_geom_layout L;
@@ -89,12 +88,23 @@ __device__ __forceinline__ void note_hit(qstate &S, float t, uint32_t id, float 
   }
 }
 
-// Walk every view's pyramid.  ANY: return at the first hit with t > tmin.
+// Walk every view's pyramid with the whole warp (packet traversal).  The 32
+// rays of a warp are neighbours on the ray screen, so they need nearly the
+// same nodes: the warp descends the union of the nodes any active lane's
+// box test accepts, box and splat data are loaded once per warp (uniform
+// addresses), and each lane tests its own ray exactly.  Extra tests never
+// change a lane's result (the minimum and the candidate set are
+// order-independent), so hits stay bit-exact.  Per-level child masks replace
+// a stack.  ANY: a lane stops at its first hit with t > tmin (shadow rays).
+// Every lane of the warp must call this together.
 template <bool ANY>
-__device__ bool walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
-                     qstate &S, unsigned int *err, long long &n_splat, long long &n_node) {
-  uint32_t stack[kStack];
+__device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
+                     bool active, qstate &S, bool &hit_any, unsigned int *err,
+                     long long &n_splat, long long &n_node) {
+  const unsigned FULL = 0xffffffffu;
   for (int v = 0; v < L.nv; ++v) {
+    bool live = active && !(ANY && hit_any);
+    if (!__any_sync(FULL, live)) return;
     const pe_view &V = L.view[v];
     const float pad = L.pad[v];
     pe_f3 q = {o.x - V.o[0], o.y - V.o[1], o.z - V.o[2]};
@@ -105,71 +115,125 @@ __device__ bool walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
     r.ix = 1.0f / (d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2]);
     r.iy = 1.0f / (d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2]);
     r.iz = 1.0f / (d.x * V.d[0] + d.y * V.d[1] + d.z * V.d[2]);
+    const float t0 = tmin - pad - 1e-6f * fabsf(tmin);
     const int top = L.nlev[v] - 1;
-    int sp = 0;
-    stack[sp++] = (uint32_t)top << 28;
     const int64_t poff = L.pix_off[v];
-    while (sp > 0) {
-      uint32_t e = stack[--sp];
-      int l = (int)(e >> 28);
-      int idx = (int)(e & 0x0fffffffu);
+    uint32_t mask[PE_MAX_LEVELS];
+    int node[PE_MAX_LEVELS];
+    // node test for the current lane limits
+    auto test_node = [&](int l, int idx) -> bool {
       int64_t nid = L.node_off[v][l] + idx;
       float4 lo = __ldg(L.nodes + 2 * nid), hi = __ldg(L.nodes + 2 * nid + 1);
-      ++n_node;
-      float t1 = ANY ? INFINITY : fmaf(fabsf(pe_add(S.tb, r_ov)), 1e-6f, pe_add(S.tb, r_ov)) + pad;
-      float t0 = tmin - pad - 1e-6f * fabsf(tmin);
-      if (!box_hit(lo, hi, r, t0, t1)) continue;
-      int tw = L.tw[v][l];
+      bool lv = active && !(ANY && hit_any);
+      float lim = pe_add(S.tb, r_ov);
+      float t1 = ANY ? INFINITY : fmaf(fabsf(lim), 1e-6f, lim) + pad;
+      bool h = lv && box_hit(lo, hi, r, t0, t1);
+      n_node += lv;
+      return __any_sync(FULL, h);
+    };
+    auto children = [&](int l, int idx) -> uint32_t {
+      // existing children (level l-1) of node idx at level l, as a 16-bit mask
+      int tw = L.tw[v][l], cw = L.tw[v][l - 1], ch = L.th[v][l - 1];
       int tx = idx % tw, ty = idx / tw;
-      if (l == 0) {
-        for (int jj = 0; jj < PE_LEAF; ++jj) {
-          int j = ty * PE_LEAF + jj;
-          if (j >= V.H) break;
-          for (int ii = 0; ii < PE_LEAF; ++ii) {
-            int i = tx * PE_LEAF + ii;
-            if (i >= V.W) break;
-            int64_t g = poff + (int64_t)j * V.W + i;
-            float4 c = __ldg(L.cr + g);
-            if (!(c.w > 0.0f)) continue;
-            float4 n = __ldg(L.nf + g);
-            ++n_splat;
-            float t;
-            pe_f3 x, ee;
-            if (!pe_hit_disk(o, d, {c.x, c.y, c.z}, {n.x, n.y, n.z}, c.w, tmin, t, x, ee)) continue;
-            if (ANY) return true;
+      int nx = cw - tx * PE_FAN, ny = ch - ty * PE_FAN;
+      nx = nx > PE_FAN ? PE_FAN : nx;
+      ny = ny > PE_FAN ? PE_FAN : ny;
+      uint32_t row = (1u << nx) - 1u, m = 0;
+      for (int j = 0; j < ny; ++j) m |= row << (j * PE_FAN);
+      return m;
+    };
+    if (!test_node(top, 0)) continue;
+    if (top == 0) {
+      mask[0] = 0;
+    }
+    int l = top;
+    node[top] = 0;
+    mask[top] = top > 0 ? children(top, 0) : 0u;
+    bool leaf_root = top == 0;
+    for (;;) {
+      int leaf = -1;
+      if (leaf_root) {
+        leaf = 0;
+        leaf_root = false;
+      } else {
+        while (l <= top && mask[l] == 0) ++l;
+        if (l > top) break;
+        int c = __ffs(mask[l]) - 1;
+        mask[l] &= mask[l] - 1;
+        int tw = L.tw[v][l], cw = L.tw[v][l - 1];
+        int tx = node[l] % tw, ty = node[l] / tw;
+        int child = (ty * PE_FAN + c / PE_FAN) * cw + tx * PE_FAN + (c % PE_FAN);
+        if (!test_node(l - 1, child)) continue;
+        if (l - 1 > 0) {
+          node[l - 1] = child;
+          mask[l - 1] = children(l - 1, child);
+          --l;
+          continue;
+        }
+        leaf = child;
+      }
+      // leaf tile: test its splats.  A conservative pre-test in plain float
+      // arithmetic (distance of the centre to the ray line <= R, and the hit
+      // parameter window [tc - R, tc + R] reaching (tmin, t_best + r]) skips
+      // the exact test for splats no lane can hit; its slack covers the
+      // rounding of both tests, so it never drops a hit the exact test takes.
+      int tw0 = L.tw[v][0];
+      int tx = leaf % tw0, ty = leaf / tw0;
+      bool lv = active && !(ANY && hit_any);
+      for (int jj = 0; jj < PE_LEAF; ++jj) {
+        int j = ty * PE_LEAF + jj;
+        if (j >= V.H) break;
+        for (int ii = 0; ii < PE_LEAF; ++ii) {
+          int i = tx * PE_LEAF + ii;
+          if (i >= V.W) break;
+          int64_t g = poff + (int64_t)j * V.W + i;
+          float4 c = __ldg(L.cr + g);
+          if (!(c.w > 0.0f)) continue;
+          float qx = c.x - o.x, qy = c.y - o.y, qz = c.z - o.z;
+          float tc = qx * d.x + qy * d.y + qz * d.z;
+          float qq = qx * qx + qy * qy + qz * qz;
+          float ll = qq - tc * tc;
+          float Rs = c.w * 1.0001f + 1e-3f * pad;
+          float sl = 1e-5f * (fabsf(tc) + c.w) + pad;
+          bool pass = lv && ll <= Rs * Rs + 1e-6f * qq && tc + Rs + sl > tmin;
+          if (!ANY) {
+            float lim = pe_add(S.tb, r_ov);
+            pass = pass && tc - Rs - sl <= fmaf(fabsf(lim), 1e-6f, lim);
+          }
+          if (!__any_sync(FULL, pass)) continue;
+          float4 n = __ldg(L.nf + g);
+          if (!pass) continue;
+          ++n_splat;
+          float t;
+          pe_f3 x, ee;
+          if (!pe_hit_disk(o, d, {c.x, c.y, c.z}, {n.x, n.y, n.z}, c.w, tmin, t, x, ee)) continue;
+          if (ANY) {
+            hit_any = true;
+            lv = false;
+          } else {
             note_hit(S, t, (uint32_t)g, r_ov, err);
           }
         }
-      } else {
-        int cw = L.tw[v][l - 1], ch = L.th[v][l - 1];
-        for (int j = PE_FAN - 1; j >= 0; --j)
-          for (int i = PE_FAN - 1; i >= 0; --i) {
-            int cx = tx * PE_FAN + i, cy = ty * PE_FAN + j;
-            if (cx >= cw || cy >= ch) continue;
-            if (sp >= kStack) {
-              pe_raise(err, PE_ERR_OVERFLOW);
-              continue;
-            }
-            stack[sp++] = ((uint32_t)(l - 1) << 28) | (uint32_t)(cy * cw + cx);
-          }
       }
+      if (ANY && !__any_sync(FULL, active && !hit_any)) return;
     }
   }
-  return false;
 }
 
 // Eq. 23 on the final candidate set: select the hit closest to its splat's
 // centre relative to R (ties: smaller t, smaller id); blend the normals in
 // splat-id order with weights 1 - rho, normalise, turn against the ray.
+// Every lane of the warp must call this together (inactive lanes: active=0).
 __device__ bool nearest(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
-                        unsigned int *err, pe_f3 &xo, pe_f3 &no, uint32_t &ido,
+                        bool active, unsigned int *err, pe_f3 &xo, pe_f3 &no, uint32_t &ido,
                         long long &n_splat, long long &n_node) {
   qstate S;
   S.tb = INFINITY;
   S.ib = PE_NONE;
   S.nc = 0;
-  walk<false>(L, o, d, tmin, r_ov, S, err, n_splat, n_node);
-  if (S.ib == PE_NONE) return false;
+  bool unused = false;
+  walk<false>(L, o, d, tmin, r_ov, active, S, unused, err, n_splat, n_node);
+  if (!active || S.ib == PE_NONE) return false;
   float lim = pe_add(S.tb, r_ov);
   int k = 0;
   for (int m = 0; m < S.nc; ++m)
@@ -270,44 +334,69 @@ __device__ __forceinline__ void flush_stats(long long *stats, long long a, long 
   }
 }
 
+// Thread t of a batch -> (view, pixel) so that each warp covers an 8x4 tile
+// of one screen (neighbouring rays in a warp).
+struct tile_map {
+  int tiles_x, tiles_y;
+  int64_t per_view_threads, n_threads;
+};
+__host__ __device__ __forceinline__ tile_map make_tile_map(int W, int H, int n_views) {
+  tile_map m;
+  m.tiles_x = (W + 7) / 8;
+  m.tiles_y = (H + 3) / 4;
+  m.per_view_threads = (int64_t)m.tiles_x * m.tiles_y * 32;
+  m.n_threads = m.per_view_threads * n_views;
+  return m;
+}
+__device__ __forceinline__ bool tile_pixel(const tile_map &m, int W, int H, int64_t t, int &view,
+                                           int &i, int &j) {
+  view = (int)(t / m.per_view_threads);
+  int64_t r = t % m.per_view_threads;
+  int tile = (int)(r >> 5), lane = (int)(r & 31);
+  i = (tile % m.tiles_x) * 8 + (lane & 7);
+  j = (tile / m.tiles_x) * 4 + (lane >> 3);
+  return i < W && j < H;
+}
+
 // Bounce 1 from the incidence screen's GFB keys (or, geom_first, by marching
 // the splats from the screen).  Writes every slot's record.
 __global__ void __launch_bounds__(kTraceThreads)
     primary_kernel(const __grid_constant__ march_args A, int geom_first) {
-  const int64_t per_view = (int64_t)A.vb.W * A.vb.H;
-  const int64_t n_rays = per_view * A.vb.n;
+  const int W = A.vb.W, H = A.vb.H;
+  const int64_t per_view = (int64_t)W * H;
+  const tile_map tm = make_tile_map(W, H, A.vb.n);
   long long nq = 0, ns = 0, nn = 0;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_rays;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
-    int64_t slot = base + threadIdx.x;
-    bool active = slot < n_rays;
-    bool live = false;
-    if (active) {
-      const pe_view &V = A.vb.v[slot / per_view];
-      int64_t p = slot % per_view;
-      int i = (int)(p % V.W), j = (int)(p / V.W);
-      pe_f3 o = pe_pixel_origin(V, i, j);
-      pe_f3 d = pe_v3(V.d);
-      pe_f3 u = {pe_mul(V.pitch, V.u[0]), pe_mul(V.pitch, V.u[1]), pe_mul(V.pitch, V.u[2])};
-      pe_f3 v = {pe_mul(V.pitch, V.v[0]), pe_mul(V.pitch, V.v[1]), pe_mul(V.pitch, V.v[2])};
-      bool hit = false;
-      pe_f3 x = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 0.f};
-      uint32_t id = PE_NONE;
-      ++nq;
-      if (geom_first) {
-        hit = nearest(A.L, o, d, 0.0f, A.r_ov, A.err, x, n, id, ns, nn);
-      } else {
-        unsigned long long key = A.keys[slot];
-        if (key != ~0ull) {
-          hit = true;
-          float t = __uint_as_float((uint32_t)(key >> 32));
-          id = (uint32_t)(key & 0xffffffffull);
-          x = pe_ray_at(o, t, d);
-          n = {__ldg(A.nrm + 3 * (int64_t)id), __ldg(A.nrm + 3 * (int64_t)id + 1),
-               __ldg(A.nrm + 3 * (int64_t)id + 2)};
-          if (pe_dot(n, d) > 0.0f) n = pe_neg3(n);
-        }
+    int64_t t = base + threadIdx.x;
+    int vi = 0, i = 0, j = 0;
+    bool active = t < tm.n_threads && tile_pixel(tm, W, H, t, vi, i, j);
+    if (!active) vi = 0;
+    const pe_view &V = A.vb.v[vi];
+    const int64_t slot = (int64_t)vi * per_view + (int64_t)j * W + i;
+    pe_f3 o = pe_pixel_origin(V, i, j);
+    pe_f3 d = pe_v3(V.d);
+    pe_f3 u = {pe_mul(V.pitch, V.u[0]), pe_mul(V.pitch, V.u[1]), pe_mul(V.pitch, V.u[2])};
+    pe_f3 v = {pe_mul(V.pitch, V.v[0]), pe_mul(V.pitch, V.v[1]), pe_mul(V.pitch, V.v[2])};
+    bool hit = false;
+    pe_f3 x = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 0.f};
+    uint32_t id = PE_NONE;
+    nq += active;
+    if (geom_first) {
+      hit = nearest(A.L, o, d, 0.0f, A.r_ov, active, A.err, x, n, id, ns, nn);
+    } else if (active) {
+      unsigned long long key = A.keys[slot];
+      if (key != ~0ull) {
+        hit = true;
+        float tt = __uint_as_float((uint32_t)(key >> 32));
+        id = (uint32_t)(key & 0xffffffffull);
+        x = pe_ray_at(o, tt, d);
+        n = {__ldg(A.nrm + 3 * (int64_t)id), __ldg(A.nrm + 3 * (int64_t)id + 1),
+             __ldg(A.nrm + 3 * (int64_t)id + 2)};
+        if (pe_dot(n, d) > 0.0f) n = pe_neg3(n);
       }
+    }
+    if (active) {
       A.h.M[slot] = hit ? 1 : 0;
       A.h.psi[slot] = 1;
       if (A.h.ids) A.h.ids[slot] = id;
@@ -317,14 +406,14 @@ __global__ void __launch_bounds__(kTraceThreads)
       st3(A.h.u, slot, u);
       st3(A.h.v, slot, v);
       A.h.path[slot] = hit ? path_start(d, x) : 0.0;
-      live = hit && A.mb >= 2;
     }
+    bool live = active && hit && A.mb >= 2;
     if (A.q_out) warp_append(live, (uint32_t)slot, A.q_out, A.n_out);
   }
   flush_stats(A.stats, nq, 0, ns, nn);
 }
 
-// One bounce (b >= 2) for the rays of q_in.
+// One bounce (b >= 2) for the rays of q_in (queue order keeps warps coherent).
 __global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_constant__ march_args A) {
   const uint32_t n_in = *A.n_in;
   const int64_t n_rays = A.h.n_rays;
@@ -333,31 +422,36 @@ __global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_const
        base += (int64_t)gridDim.x * blockDim.x) {
     int64_t qi = base + threadIdx.x;
     bool active = qi < n_in;
-    bool live = false;
-    uint32_t slot = 0;
+    uint32_t slot = active ? A.q_in[qi] : 0u;
+    pe_f3 p = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 1.f}, d = {0.f, 0.f, 1.f};
+    pe_f3 u = {0.f, 0.f, 0.f}, v = {0.f, 0.f, 0.f};
     if (active) {
-      slot = A.q_in[qi];
-      pe_f3 p = ld3(A.h.p, slot), n = ld3(A.h.n, slot), d = ld3(A.h.k, slot);
-      pe_f3 u = ld3(A.h.u, slot), v = ld3(A.h.v, slot);
+      p = ld3(A.h.p, slot);
+      n = ld3(A.h.n, slot);
+      d = ld3(A.h.k, slot);
+      u = ld3(A.h.u, slot);
+      v = ld3(A.h.v, slot);
       pe_f3 rd = pe_reflect(d, n);
       float len = pe_sqrt(pe_dot(rd, rd));
       d = {pe_div(rd.x, len), pe_div(rd.y, len), pe_div(rd.z, len)};
       u = pe_reflect(u, n);
       v = pe_reflect(v, n);
-      pe_f3 x, n2;
-      uint32_t id;
-      ++nq;
-      if (nearest(A.L, p, d, A.eps, A.r_ov, A.err, x, n2, id, ns, nn)) {
-        A.h.path[slot] = __dadd_rn(A.h.path[slot], seg_len(p, x));
-        st3(A.h.p, slot, x);
-        st3(A.h.n, slot, n2);
-        st3(A.h.k, slot, d);
-        st3(A.h.u, slot, u);
-        st3(A.h.v, slot, v);
-        A.h.M[slot] = A.bounce;
-        if (A.h.ids) A.h.ids[(int64_t)(A.bounce - 1) * n_rays + slot] = id;
-        live = A.bounce < A.mb;
-      }
+    }
+    pe_f3 x, n2;
+    uint32_t id;
+    nq += active;
+    bool hit = nearest(A.L, p, d, A.eps, A.r_ov, active, A.err, x, n2, id, ns, nn);
+    bool live = false;
+    if (hit) {
+      A.h.path[slot] = __dadd_rn(A.h.path[slot], seg_len(p, x));
+      st3(A.h.p, slot, x);
+      st3(A.h.n, slot, n2);
+      st3(A.h.k, slot, d);
+      st3(A.h.u, slot, u);
+      st3(A.h.v, slot, v);
+      A.h.M[slot] = A.bounce;
+      if (A.h.ids) A.h.ids[(int64_t)(A.bounce - 1) * n_rays + slot] = id;
+      live = A.bounce < A.mb;
     }
     if (A.q_out) warp_append(live, slot, A.q_out, A.n_out);
   }
@@ -366,21 +460,30 @@ __global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_const
 
 // Psi: shadow ray from the last hit toward the receiver (monostatic: w).
 __global__ void __launch_bounds__(kTraceThreads) shadow_kernel(const __grid_constant__ march_args A) {
-  const int64_t per_view = (int64_t)A.vb.W * A.vb.H;
-  const int64_t n_rays = A.h.n_rays;
+  const int W = A.vb.W, H = A.vb.H;
+  const int64_t per_view = (int64_t)W * H;
+  const tile_map tm = make_tile_map(W, H, A.vb.n);
   long long nsh = 0, ns = 0, nn = 0;
-  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < n_rays;
-       slot += (int64_t)gridDim.x * blockDim.x) {
-    if (A.h.M[slot] < 2) continue;
-    const pe_view &V = A.vb.v[slot / per_view];
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = base + threadIdx.x;
+    int vi = 0, i = 0, j = 0;
+    bool active = t < tm.n_threads && tile_pixel(tm, W, H, t, vi, i, j);
+    if (!active) vi = 0;
+    const int64_t slot = (int64_t)vi * per_view + (int64_t)j * W + i;
+    active = active && A.h.M[slot] >= 2;
+    if (!__any_sync(0xffffffffu, active)) continue;
+    const pe_view &V = A.vb.v[vi];
     pe_f3 w = {-V.d[0], -V.d[1], -V.d[2]};
+    pe_f3 p = active ? ld3(A.h.p, slot) : pe_f3{0.f, 0.f, 0.f};
     qstate S;
     S.tb = INFINITY;
     S.ib = PE_NONE;
     S.nc = 0;
-    ++nsh;
-    bool blocked = walk<true>(A.L, ld3(A.h.p, slot), w, A.eps, A.r_ov, S, A.err, ns, nn);
-    A.h.psi[slot] = blocked ? 0 : 1;
+    nsh += active;
+    bool blocked = false;
+    walk<true>(A.L, p, w, A.eps, A.r_ov, active, S, blocked, A.err, ns, nn);
+    if (active) A.h.psi[slot] = blocked ? 0 : 1;
   }
   flush_stats(A.stats, 0, nsh, ns, nn);
 }
@@ -460,7 +563,8 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   A.q_out = mb >= 2 ? qa : nullptr;
   A.n_out = na;
   A.bounce = 1;
-  primary_kernel<<<grid_for(n_rays), kTraceThreads, 0, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
+  const int64_t n_thr = make_tile_map(vb.W, vb.H, vb.n).n_threads;
+  primary_kernel<<<grid_for(n_thr), kTraceThreads, 0, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
   PE_TRY_LAUNCH("primary_kernel");
   for (int b = 2; b <= mb; ++b) {
     A.bounce = b;
@@ -479,7 +583,7 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
     nb = t;
   }
   if (mb >= 2) {
-    shadow_kernel<<<grid_for(n_rays), kTraceThreads, 0, s>>>(A);
+    shadow_kernel<<<grid_for(n_thr), kTraceThreads, 0, s>>>(A);
     PE_TRY_LAUNCH("shadow_kernel");
   }
   return PE_OK;
