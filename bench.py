@@ -18,6 +18,7 @@ number of kernels launched.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -167,11 +168,20 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # timed region: K steps, L2 flushed between steps (outside the events)
+    # timed region: K steps, L2 flushed between steps (outside the events);
+    # the library also records events around every march_kernel launch on
+    # the launching stream (the dominant kernel) for the roofline.
+    max_pairs = 512
+    mev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * max_pairs)]
+    for e in mev:          # torch creates the CUDA event on its first record
+        e.record(stream)
+    torch.cuda.synchronize()
+    mev_ptrs = (ctypes.c_void_p * (2 * max_pairs))(*[e.cuda_event for e in mev])
     clk = ClockSampler(local_rank)
     clk.start()
     l0 = lib.pe_kernel_launches()
     barrier()
+    lib.pe_set_kernel_events(b"march_kernel", mev_ptrs, max_pairs)
     total_ms = 0.0
     for _ in range(args.steps):
         flush.zero_()
@@ -183,9 +193,13 @@ def run_gpu(args, rank, world, local_rank):
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
     barrier()
+    n_march = lib.pe_set_kernel_events(None, None, 0)
     launches = lib.pe_kernel_launches() - l0
     clocks = clk.stop()
     api.stream_check()
+    march_ms = [mev[2 * k].elapsed_time(mev[2 * k + 1]) for k in range(n_march)]
+    march_queries = int(st[0]) - A * sw.W * sw.H          # bounce >= 2 queries per step
+    march_launches_per_step = max(1, n_march // args.steps)
 
     # end to end through the C ABI with host buffers: pinned H2D of the
     # points each step, D2H of the field and sigma
@@ -215,8 +229,10 @@ def run_gpu(args, rank, world, local_rank):
     h2d = int(hp.numel() * 4 + hn.numel() * 4 + hr.numel() * 4)
     d2h = int(hE.numel() * 8 + hS.numel() * 8)
 
-    # roofline of the dominant kernel, timed alone on the launching stream
-    roof = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream)
+    # roofline of the dominant kernel (march_kernel, timed in the steps above)
+    roof = roofline_march(march_ms, march_queries / march_launches_per_step)
+    # the PO field kernel, timed alone on the launching stream
+    roof_po = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream)
 
     t_ms = total_ms
     if world > 1:
@@ -250,10 +266,39 @@ def run_gpu(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "rcs_samples_per_s": samples / (e2e_ms / 1e3)},
         "roofline": roof,
+        "roofline_po": roof_po,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
     return out
+
+
+# Algorithmic bytes of one bounce query of the march: the ray's record is
+# read (hit point, normal, direction, tube vectors: 15 floats; path length:
+# 8 bytes; its queue slot: 4 bytes; 72 + 4 = 76 bytes) and, on a hit,
+# rewritten together with the bounce count and the next queue slot (76 bytes).
+MARCH_BYTES_PER_QUERY = 152
+
+
+def roofline_march(ms_list, queries_per_launch):
+    if not ms_list:
+        return None
+    ms = float(np.mean(ms_list))
+    achieved = queries_per_launch * MARCH_BYTES_PER_QUERY / (ms / 1e3) / 1e9
+    peak, src = hbm_peak()
+    return {"kernel": "march_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": src, "bytes_per_query": MARCH_BYTES_PER_QUERY,
+            "queries_per_launch": queries_per_launch, "ms_per_launch": ms,
+            "launches_timed": len(ms_list)}
+
+
+def hbm_peak():
+    try:
+        m = json.load(open(MEASURED))
+        return float(m["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy bandwidth)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
 
 
 def roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream):

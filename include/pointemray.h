@@ -140,6 +140,15 @@ int pe_abi_version(void);
  * the paper. */
 int64_t pe_kernel_launches(void);
 
+/* Diagnostics (no counterpart in the paper): make the library record CUDA
+ * events around the next launches of one of its kernels on the calling host
+ * thread.  `kernel` names it ("march_kernel", "po_kernel", "splat_kernel",
+ * "primary_kernel", "shadow_kernel"); events[2k] / events[2k+1] (created by the
+ * caller, cudaEvent_t passed as void*) are recorded on the launching stream
+ * immediately before / after the k-th such launch, for k < n_pairs.  Pass
+ * n_pairs = 0 to stop.  Returns the pairs recorded since the last call. */
+int32_t pe_set_kernel_events(const char *kernel, void **events, int32_t n_pairs);
+
 /* Human-readable text of the last error on the calling host thread. */
 const char *pe_last_error(void);
 

@@ -53,6 +53,7 @@ P = C.c_void_p
 SIGNATURES = {
     "pe_abi_version": (C.c_int, []),
     "pe_kernel_launches": (C.c_int64, []),
+    "pe_set_kernel_events": (C.c_int32, [C.c_char_p, P, C.c_int32]),
     "pe_last_error": (C.c_char_p, []),
     "pe_stream_check": (C.c_int, [P]),
     "pe_view_from_angles": (C.c_int, [C.c_double, C.c_double, P, C.c_double, C.c_int32,

@@ -43,6 +43,40 @@ extern "C" int64_t pe_kernel_launches(void) { return (int64_t)g_launches.load();
 
 extern "C" const char *pe_last_error(void) { return g_last_error; }
 
+// Diagnostic event recording (calling host thread only).
+namespace {
+thread_local char t_ev_kernel[64] = "";
+thread_local void **t_ev = nullptr;
+thread_local int32_t t_ev_pairs = 0, t_ev_done = 0;
+}  // namespace
+
+extern "C" int32_t pe_set_kernel_events(const char *kernel, void **events, int32_t n_pairs) {
+  int32_t done = t_ev_done;
+  t_ev_done = 0;
+  if (!kernel || !events || n_pairs <= 0) {
+    t_ev = nullptr;
+    t_ev_pairs = 0;
+    t_ev_kernel[0] = 0;
+    return done;
+  }
+  snprintf(t_ev_kernel, sizeof(t_ev_kernel), "%s", kernel);
+  t_ev = events;
+  t_ev_pairs = n_pairs;
+  return done;
+}
+
+void pe_event_before(const char *kernel, cudaStream_t s) {
+  if (t_ev && t_ev_done < t_ev_pairs && strcmp(kernel, t_ev_kernel) == 0)
+    cudaEventRecord(static_cast<cudaEvent_t>(t_ev[2 * t_ev_done]), s);
+}
+
+void pe_event_after(const char *kernel, cudaStream_t s) {
+  if (t_ev && t_ev_done < t_ev_pairs && strcmp(kernel, t_ev_kernel) == 0) {
+    cudaEventRecord(static_cast<cudaEvent_t>(t_ev[2 * t_ev_done + 1]), s);
+    ++t_ev_done;
+  }
+}
+
 extern "C" pe_status pe_stream_check(void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   PE_TRY_CUDA(cudaStreamSynchronize(s));

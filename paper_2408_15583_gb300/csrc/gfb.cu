@@ -131,7 +131,9 @@ pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float
   if (per_view < 1) per_view = 1;
   int gx = (int)(blocks_needed < per_view ? blocks_needed : per_view);
   dim3 grid(gx, vb.n);
+  pe_event_before("splat_kernel", s);
   splat_kernel<<<grid, kSplatThreads, 0, s>>>(vb, pos, nrm, rad, n, mode, delta, keys);
+  pe_event_after("splat_kernel", s);
   PE_TRY_LAUNCH("splat_kernel");
   return PE_OK;
 }

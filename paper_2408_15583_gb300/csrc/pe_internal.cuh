@@ -34,6 +34,9 @@ unsigned int *pe_err_word();  // device address of the error word, current devic
   } while (0)
 
 void pe_count_launch();
+// Diagnostic event pairs around a named kernel's launches (api.cu).
+void pe_event_before(const char *kernel, cudaStream_t s);
+void pe_event_after(const char *kernel, cudaStream_t s);
 
 #define PE_TRY_LAUNCH(what)                                                  \
   do {                                                                       \

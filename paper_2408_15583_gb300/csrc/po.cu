@@ -301,7 +301,9 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
         C.klo[f] = (float)(kd - (double)C.khi[f]);
       }
       dim3 grid(C.n_chunks, ng);
+      pe_event_before("po_kernel", s);
       po_kernel<<<grid, kPoThreads, 0, s>>>(h, C, part);
+      pe_event_after("po_kernel", s);
       PE_TRY_LAUNCH("po_kernel");
       int64_t n = (int64_t)ng * nf * 12;
       int blocks = (int)((n + 255) / 256);

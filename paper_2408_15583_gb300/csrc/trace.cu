@@ -101,6 +101,7 @@ template <bool ANY>
 __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
                      bool active, qstate &S, bool &hit_any, unsigned int *err,
                      long long &n_splat, long long &n_node) {
+  static_assert(PE_FAN == 2, "the register-resident traversal assumes a 2x2 fan-out");
   const unsigned FULL = 0xffffffffu;
   for (int v = 0; v < L.nv; ++v) {
     bool live = active && !(ANY && hit_any);
@@ -118,67 +119,85 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
     const float t0 = tmin - pad - 1e-6f * fabsf(tmin);
     const int top = L.nlev[v] - 1;
     const int64_t poff = L.pix_off[v];
-    uint32_t mask[PE_MAX_LEVELS];
-    int node[PE_MAX_LEVELS];
-    // node test for the current lane limits
-    auto test_node = [&](int l, int idx) -> bool {
-      int64_t nid = L.node_off[v][l] + idx;
+    auto t_far = [&]() -> float {
+      float lim = pe_add(S.tb, r_ov);
+      return ANY ? INFINITY : fmaf(fabsf(lim), 1e-6f, lim) + pad;
+    };
+    // root
+    {
+      int64_t nid = L.node_off[v][top];
       float4 lo = __ldg(L.nodes + 2 * nid), hi = __ldg(L.nodes + 2 * nid + 1);
       bool lv = active && !(ANY && hit_any);
-      float lim = pe_add(S.tb, r_ov);
-      float t1 = ANY ? INFINITY : fmaf(fabsf(lim), 1e-6f, lim) + pad;
-      bool h = lv && box_hit(lo, hi, r, t0, t1);
       n_node += lv;
-      return __any_sync(FULL, h);
-    };
-    auto children = [&](int l, int idx) -> uint32_t {
-      // existing children (level l-1) of node idx at level l, as a 16-bit mask
-      int tw = L.tw[v][l], cw = L.tw[v][l - 1], ch = L.th[v][l - 1];
-      int tx = idx % tw, ty = idx / tw;
-      int nx = cw - tx * PE_FAN, ny = ch - ty * PE_FAN;
-      nx = nx > PE_FAN ? PE_FAN : nx;
-      ny = ny > PE_FAN ? PE_FAN : ny;
-      uint32_t row = (1u << nx) - 1u, m = 0;
-      for (int j = 0; j < ny; ++j) m |= row << (j * PE_FAN);
-      return m;
-    };
-    if (!test_node(top, 0)) continue;
-    if (top == 0) {
-      mask[0] = 0;
+      if (!__any_sync(FULL, lv && box_hit(lo, hi, r, t0, t_far()))) continue;
     }
-    int l = top;
-    node[top] = 0;
-    mask[top] = top > 0 ? children(top, 0) : 0u;
-    bool leaf_root = top == 0;
+    // Traversal state, all in registers: `expand` asks to expand node
+    // (px, py) of level l (its four children at level l-1 are box-tested
+    // together; the accepted ones become pending bits [4(l-1), 4(l-1)+4) of
+    // `masks`).  Otherwise the pending bits of level l are children of node
+    // (px, py) at level l+1; going up one level halves (px, py).
+    uint64_t masks = 0;
+    int l = top, px = 0, py = 0;
+    bool expand = top > 0;
+    int leaf_x = 0, leaf_y = 0;
+    bool root_leaf = top == 0;
     for (;;) {
-      int leaf = -1;
-      if (leaf_root) {
-        leaf = 0;
-        leaf_root = false;
+      if (root_leaf) {
+        root_leaf = false;
+        leaf_x = 0;
+        leaf_y = 0;
       } else {
-        while (l <= top && mask[l] == 0) ++l;
-        if (l > top) break;
-        int c = __ffs(mask[l]) - 1;
-        mask[l] &= mask[l] - 1;
-        int tw = L.tw[v][l], cw = L.tw[v][l - 1];
-        int tx = node[l] % tw, ty = node[l] / tw;
-        int child = (ty * PE_FAN + c / PE_FAN) * cw + tx * PE_FAN + (c % PE_FAN);
-        if (!test_node(l - 1, child)) continue;
-        if (l - 1 > 0) {
-          node[l - 1] = child;
-          mask[l - 1] = children(l - 1, child);
-          --l;
+        if (expand) {
+          expand = false;
+          const int cl = l - 1;
+          const int cw = L.tw[v][cl], ch = L.th[v][cl];
+          const int64_t base = L.node_off[v][cl];
+          float4 blo[4], bhi[4];
+          bool ex[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            int cx = 2 * px + (c & 1), cy = 2 * py + (c >> 1);
+            ex[c] = cx < cw && cy < ch;
+            int64_t nid = base + (ex[c] ? (int64_t)cy * cw + cx : 0);
+            blo[c] = __ldg(L.nodes + 2 * nid);
+            bhi[c] = __ldg(L.nodes + 2 * nid + 1);
+          }
+          bool lv = active && !(ANY && hit_any);
+          float t1 = t_far();
+          uint32_t m = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            n_node += lv && ex[c];
+            bool h = ex[c] && lv && box_hit(blo[c], bhi[c], r, t0, t1);
+            if (__any_sync(FULL, h)) m |= 1u << c;
+          }
+          masks |= (uint64_t)m << (4 * cl);
+          l = cl;
+        }
+        while (l < top && ((masks >> (4 * l)) & 0xfull) == 0) {
+          ++l;
+          px >>= 1;
+          py >>= 1;
+        }
+        if (l >= top) break;
+        const int c = __ffs((uint32_t)((masks >> (4 * l)) & 0xfull)) - 1;
+        masks &= ~(1ull << (4 * l + c));
+        const int cx = 2 * px + (c & 1), cy = 2 * py + (c >> 1);
+        if (l > 0) {
+          px = cx;
+          py = cy;
+          expand = true;
           continue;
         }
-        leaf = child;
+        leaf_x = cx;
+        leaf_y = cy;
       }
       // leaf tile: test its splats.  A conservative pre-test in plain float
       // arithmetic (distance of the centre to the ray line <= R, and the hit
       // parameter window [tc - R, tc + R] reaching (tmin, t_best + r]) skips
       // the exact test for splats no lane can hit; its slack covers the
       // rounding of both tests, so it never drops a hit the exact test takes.
-      int tw0 = L.tw[v][0];
-      int tx = leaf % tw0, ty = leaf / tw0;
+      const int tx = leaf_x, ty = leaf_y;
       bool lv = active && !(ANY && hit_any);
       for (int jj = 0; jj < PE_LEAF; ++jj) {
         int j = ty * PE_LEAF + jj;
@@ -564,7 +583,9 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   A.n_out = na;
   A.bounce = 1;
   const int64_t n_thr = make_tile_map(vb.W, vb.H, vb.n).n_threads;
+  pe_event_before("primary_kernel", s);
   primary_kernel<<<grid_for(n_thr), kTraceThreads, 0, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
+  pe_event_after("primary_kernel", s);
   PE_TRY_LAUNCH("primary_kernel");
   for (int b = 2; b <= mb; ++b) {
     A.bounce = b;
@@ -573,7 +594,9 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
     A.q_out = b < mb ? qb : nullptr;
     A.n_out = nb;
     PE_TRY_CUDA(cudaMemsetAsync(nb, 0, sizeof(uint32_t), s));
+    pe_event_before("march_kernel", s);
     march_kernel<<<grid_for(n_rays), kTraceThreads, 0, s>>>(A);
+    pe_event_after("march_kernel", s);
     PE_TRY_LAUNCH("march_kernel");
     uint32_t *t = qa;
     qa = qb;
@@ -583,7 +606,9 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
     nb = t;
   }
   if (mb >= 2) {
+    pe_event_before("shadow_kernel", s);
     shadow_kernel<<<grid_for(n_thr), kTraceThreads, 0, s>>>(A);
+    pe_event_after("shadow_kernel", s);
     PE_TRY_LAUNCH("shadow_kernel");
   }
   return PE_OK;

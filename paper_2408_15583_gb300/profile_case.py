@@ -1,0 +1,66 @@
+"""Small, representative cases of the hot kernels for profiling (ncu).
+
+    python -m paper_2408_15583_gb300.profile_case march [reps]   # one traced batch
+    python -m paper_2408_15583_gb300.profile_case po [reps]      # PO over that batch
+    python -m paper_2408_15583_gb300.profile_case splat [reps]   # incidence splats
+
+Each case is the sphere workload's geometry (200k points, 8 fused 512^2
+views) with one batch of 8 incidence angles at 1024^2 rays and 64
+frequencies: a few GB on the device, inputs larger than L2, a handful of
+launches -- small enough for a full ncu capture of one launch.
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv):
+    import torch
+
+    import scenes
+    from paper_2408_15583_gb300 import api, build, pipeline
+
+    build()
+    case = argv[0] if argv else "march"
+    reps = int(argv[1]) if len(argv) > 1 else 3
+    wl = scenes.workload_sphere()
+    sc, sw, vd = wl.scene, wl.sweep, wl.views
+    dev = "cuda:0"
+    pos, nrm, rad = pipeline.scene_to_device(sc, dev)
+    gv = pipeline.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, vd.W, vd.H)
+    prm = pipeline.default_params(sc.pos, gv)
+    geom, _ = pipeline.build_geometry(pos, nrm, rad, gv, prm)
+    nb = 8
+    views = [api.view_from_angles(sw.theta_deg[a * 45], sw.phi_deg[a * 45], sw.centre, sw.extent,
+                                  sw.W, sw.H) for a in range(nb)]
+    keys = api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))["keys"]
+    stats = torch.zeros(8, dtype=torch.int64, device=dev)
+    h = api.trace_bounces(views, keys, nrm, geom, 2, prm, ids=False, stats=stats)
+    ks = [[-x for x in v.d] for v in views]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        if case == "march":
+            api.trace_bounces(views, keys, nrm, geom, 2, prm, hits=h, ids=False)
+        elif case == "po":
+            api.po_field(h, nb, sw.W * sw.H, ks, sw.freqs_hz)
+        elif case == "splat":
+            api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))
+        else:
+            raise SystemExit(f"unknown case {case}")
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / reps
+    api.stream_check()
+    st = stats.cpu().numpy()
+    print(f"{case}: {dt * 1e3:.2f} ms per call; batch queries {st[0]} shadow {st[1]} "
+          f"exact splat tests {st[2]} node tests {st[3]}")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
