@@ -280,14 +280,39 @@ def run_gpu(args, rank, world, local_rank):
 MARCH_BYTES_PER_QUERY = 152
 
 
+# DRAM bytes (read + write) per bounce query of march_kernel from one ncu
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 646.6 MB
+# over 6,332,964 queries), valid only for the sources it was taken on (their
+# SHA-256 prefixes); scaled to a full launch by the number of queries.
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 102.1,
+                     "sources": {"paper_2408_15583_gb300/csrc/trace.cu": "0c7a4eaec796f98e",
+                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "8388fdd29e24e928"}}
+
+
+def _traffic_valid(rec):
+    import hashlib
+    for path, sha in rec["sources"].items():
+        try:
+            h = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()
+        except OSError:
+            return False
+        if not h.startswith(sha):
+            return False
+    return True
+
+
 def roofline_march(ms_list, queries_per_launch):
     if not ms_list:
         return None
     ms = float(np.mean(ms_list))
     achieved = queries_per_launch * MARCH_BYTES_PER_QUERY / (ms / 1e3) / 1e9
     peak, src = hbm_peak()
+    traffic = None
+    if _traffic_valid(MARCH_NCU_TRAFFIC):
+        traffic = MARCH_NCU_TRAFFIC["bytes_per_query"] * queries_per_launch
     return {"kernel": "march_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": "bytes per launch, scaled by queries from a smaller ncu capture",
             "peak_source": src, "bytes_per_query": MARCH_BYTES_PER_QUERY,
             "queries_per_launch": queries_per_launch, "ms_per_launch": ms,
             "launches_timed": len(ms_list)}
