@@ -280,6 +280,25 @@ pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t rays_per_gr
                       const float *ks, const double *freqs_hz, int32_t n_freq,
                       void *ws, size_t ws_bytes, double *E_dev, void *stream);
 
+/* pe_po_field without a workspace -- for callers that cannot allocate device
+ * memory for the library (their memory belongs to a host application's own
+ * pool, or allocation is not allowed where they call from).  The paper has no
+ * counterpart; this is an interface convenience.  Same arguments, result and
+ * arithmetic as pe_po_field, minus ws/ws_bytes: the partial sums live in a
+ * fixed 16 MiB device array inside the library, which every GPU that loads
+ * the library keeps until the process exits.  Requests whose partial sums
+ * need more than 16 MiB (pe_po_workspace() - 256 > 16 MiB) return PE_EINVAL
+ * with a message.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device, with that device current);
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads on the same device) race and corrupt each other's
+ * results; serialise them.  Nothing in the array needs clearing between
+ * calls. */
+pe_status pe_po_field_static(const pe_hits *hits, int32_t n_groups, int64_t rays_per_group,
+                             const float *ks, const double *freqs_hz, int32_t n_freq,
+                             double *E_dev, void *stream);
+
 /* ---------------------------------------------------------------------------
  * a1/a7  Monostatic RCS sweep (whole path: a1-a6 per batch of angles).
  * ------------------------------------------------------------------------- */

@@ -69,6 +69,7 @@ SIGNATURES = {
                                    P]),
     "pe_po_workspace": (C.c_size_t, [C.c_int32, C.c_int64, C.c_int32]),
     "pe_po_field": (C.c_int, [P, C.c_int32, C.c_int64, P, P, C.c_int32, P, C.c_size_t, P, P]),
+    "pe_po_field_static": (C.c_int, [P, C.c_int32, C.c_int64, P, P, C.c_int32, P, P]),
     "pe_rcs_sweep_workspace": (C.c_size_t, [P]),
     "pe_rcs_sweep": (C.c_int, [P, P, P, P, C.c_int64, P, P, P, C.c_size_t, P, P, P, P]),
 }
