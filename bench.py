@@ -412,6 +412,45 @@ def oracle_sample(wl, n_pix=1024, view_px=64, seed=0):
     return queries, dt, len(pix), view_px
 
 
+# ----------------------------------------------------------------------------
+# serving (continuous batching vs one request at a time)
+# ----------------------------------------------------------------------------
+
+def run_serving(n_requests=100, slots=4, budget_gb=150.0, seed=5):
+    """C5-shaped request mix, scaled to a bench-sized window: targets from
+    the dihedral / sphere / trihedral / composite generators (10k-120k
+    points), screens 128^2-512^2, 1-32 angles, 1-16 frequencies, 1-3 bounces,
+    fused geometry from 8 views at 256^2.  Poisson arrivals at 70% of the
+    one-at-a-time service rate measured first on the same requests."""
+    import torch
+    from paper_2408_15583_gb300 import serve
+    pool = [("dihedral", scenes.dihedral(10_000, seed=1)),
+            ("sphere", scenes.sphere(120_000)),
+            ("trihedral", scenes.trihedral(30_000, a=0.6)),
+            ("composite", scenes.composite(60_000, seed=7, pca=True))]
+    budget = int(budget_gb * (1 << 30))
+    # service rate, one at a time, back to back (also warms the geometry cache)
+    reqs = serve.make_requests(pool, n_requests, rate_hz=1e9, seed=seed, view_W=256)
+    cal = serve.Scheduler(serve.GpuExecutor(n_slots=1), budget, n_slots=1)
+    t0 = time.perf_counter()
+    cal.run(reqs)
+    torch.cuda.synchronize()
+    busy = time.perf_counter() - t0
+    rate = 0.7 * n_requests / busy
+    reqs = serve.make_requests(pool, n_requests, rate_hz=rate, seed=seed, view_W=256)
+    out = {"requests": n_requests, "rate_hz": rate, "slots": slots, "hbm_budget_gb": budget_gb,
+           "workload": "Poisson arrivals at 70% of the one-at-a-time service rate; per request "
+                       "a target of 10k-120k points, screen 128^2-512^2, 1-32 angles, 1-16 "
+                       "freqs, 1-3 bounces, fused geometry 8 x 256^2 kept resident"}
+    for name, n_slots in (("plain_batched", 1), ("continuous", slots)):
+        sch = serve.Scheduler(serve.GpuExecutor(n_slots=n_slots), budget, n_slots=n_slots)
+        res = sch.run(reqs)
+        st = serve.latency_stats(res)
+        st["max_concurrent"] = sch.max_running
+        out[name] = st
+    return out
+
+
 def cpu_baseline(wl):
     q, dt, npix, vpx = oracle_sample(wl)
     return {"value": q / dt, "unit": "ray-bounces/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -453,6 +492,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sphere", choices=["sphere", "dihedral", "composite"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -469,6 +509,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     out = run_gpu(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_serving:
+        out["serving"] = run_serving()
     if rank == 0 and not args.no_cpu_baseline:
         wl, _ = make_workload(args.workload)
         out["cpu_baseline"] = cpu_baseline(wl)
