@@ -422,3 +422,73 @@ def workload_small(seed: int = 11) -> Workload:
     phi = np.array([0.0, 17.0, 45.0, 71.0])
     sw = _sweep_over(sc, np.full(4, 90.0), phi, 48, [3e9, 3.5e9, 4e9], 2)
     return Workload(sc, sw, aggregation_views(sc, 96, 96), "dihedral-small")
+
+
+# ----------------------------------------------------------------------------
+# Network parameters for the learned GFB completion (seeded random init)
+# ----------------------------------------------------------------------------
+
+UNET_HEADS = (("depth", 1), ("normal", 3), ("mask", 1))
+
+
+def unet_param_shapes(widths=(32, 64, 128, 256), blocks=(2, 2, 2, 2)):
+    """Names and shapes of the U-Net parameters (layout used by both sides):
+    3x3 convs [Cout, 3, 3, Cin]; 1x1 convs [Cout, Cin]; depthwise 7x7 [7, 7, C];
+    vectors [C].  ConvNeXt block p: dw 7x7 -> LayerNorm -> 1x1 C->4C -> GELU ->
+    1x1 4C->C, residual."""
+    shp = {}
+
+    def block(p, c):
+        shp[p + ".dw.w"] = (7, 7, c)
+        shp[p + ".dw.b"] = (c,)
+        shp[p + ".ln.g"] = (c,)
+        shp[p + ".ln.b"] = (c,)
+        shp[p + ".pw1.w"] = (4 * c, c)
+        shp[p + ".pw1.b"] = (4 * c,)
+        shp[p + ".pw2.w"] = (c, 4 * c)
+        shp[p + ".pw2.b"] = (c,)
+
+    c = widths
+    shp["stem.w"] = (c[0], 3, 3, 1)
+    shp["stem.b"] = (c[0],)
+    for lvl in range(len(c)):
+        if lvl > 0:
+            shp[f"down{lvl}.w"] = (c[lvl], c[lvl - 1])
+            shp[f"down{lvl}.b"] = (c[lvl],)
+        for k in range(blocks[lvl]):
+            block(f"enc{lvl}.{k}", c[lvl])
+    for head, nout in UNET_HEADS:
+        for lvl in range(len(c) - 2, -1, -1):
+            p = f"{head}.up{lvl}"
+            shp[p + ".w"] = (4 * c[lvl], 3, 3, c[lvl + 1])
+            shp[p + ".b"] = (4 * c[lvl],)
+            shp[f"{head}.fuse{lvl}.w"] = (c[lvl], 2 * c[lvl])
+            shp[f"{head}.fuse{lvl}.b"] = (c[lvl],)
+            block(f"{head}.blk{lvl}", c[lvl])
+        shp[f"{head}.head.w"] = (nout, c[0])
+        shp[f"{head}.head.b"] = (nout,)
+    return shp
+
+
+def unet_init(seed: int = 0, widths=(32, 64, 128, 256), blocks=(2, 2, 2, 2)):
+    """Seeded float32 initial parameters: weights ~ N(0, 1/fan_in) (scaled
+    down on the residual branch's last 1x1), biases 0, LayerNorm gain 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for name, shp in unet_param_shapes(widths, blocks).items():
+        if name.endswith(".b"):
+            a = np.zeros(shp)
+        elif name.endswith(".ln.g"):
+            a = np.ones(shp)
+        else:
+            if name.endswith(".dw.w"):
+                fan_in = 49
+            elif len(shp) == 4:
+                fan_in = shp[1] * shp[2] * shp[3]
+            else:
+                fan_in = shp[-1]
+            a = rng.normal(0.0, 1.0 / math.sqrt(fan_in), size=shp)
+            if name.endswith(".pw2.w"):
+                a *= 0.1
+        out[name] = a.astype(np.float32)
+    return out
