@@ -341,6 +341,129 @@ pe_status pe_rcs_sweep(const pe_sweep *sweep, const float *pos_dev,
                        size_t ws_bytes, double *E_dev, double *sigma_dev,
                        int64_t *stats_dev, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * a8  Learned GFB completion (Sec. III-A: a U-Net with ConvNeXt blocks (ref 49),
+ *     max-pooling down, sub-pixel convolution up (ref 51), a shared encoder and
+ *     three decoders for depth, normal (uvw frame) and hit mask; losses
+ *     Eq. 17-21; AdamW training, Sec. IV-A).  Layer primitives composed by the
+ *     caller.  Activations are BF16 (passed as void*) in NHWC layout (channels
+ *     fastest); accumulation and master weights are FP32.  Reductions over
+ *     pixels (weight, bias, LayerNorm and loss sums) use fixed-order partial
+ *     sums in the caller's workspace, so results are deterministic.
+ * ------------------------------------------------------------------------- */
+
+/* C[m,n] = epi(alpha * sum_k A(m,k) B(k,n)) with A(m,k) = A[m*sam + k*sak],
+ * B(k,n) = B[k*sbk + n*sbn] (BF16, any strides: row- or column-major
+ * operands), tensor-core products accumulated in FP32.  epi adds bias[n]
+ * (FP32, nullable), R[m*ldr+n] (BF16 residual, nullable), beta * C_old (FP32
+ * C only), then, if gelu, stores the pre-activation to Z (BF16, nullable) and
+ * applies GELU (exact erf form).  C is FP32 (c_f32 = 1) or BF16 with row
+ * stride ldc.  Long K is split across blocks (deterministic split-K) using ws
+ * of pe_nn_gemm_workspace() bytes. */
+size_t pe_nn_gemm_workspace(int32_t M, int32_t N, int64_t K);
+pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, int64_t sam, int64_t sak,
+                     const void *B, int64_t sbk, int64_t sbn, void *C, int64_t ldc,
+                     int32_t c_f32, const float *bias, const void *R, int64_t ldr, void *Z,
+                     int64_t ldz, int32_t gelu, float alpha, float beta, void *ws,
+                     size_t ws_bytes, void *stream);
+
+/* 3x3 convolution support, zero padding 1: forward writes col[p][(ky*3+kx)*C + c]
+ * (BF16 [B*H*W][9C]) from X [B][H][W][C]; backward (backward = 1) reads X as
+ * dcol and writes col as dX [B][H][W][C] (sum over the taps that read each
+ * input pixel). */
+pe_status pe_nn_im2col3(const void *X, int32_t B, int32_t H, int32_t W, int32_t C, void *col,
+                        int32_t backward, void *stream);
+
+/* Depthwise 7x7 convolution, zero padding 3, weights w[ky][kx][c] FP32, bias
+ * FP32 (nullable).  Backward: dX (nullable), dw [49][C] and db [C] (FP32,
+ * overwritten, nullable) with ws of pe_nn_dwconv7_bwd_workspace() bytes. */
+pe_status pe_nn_dwconv7(const void *X, const float *w, const float *bias, int32_t B, int32_t H,
+                        int32_t W, int32_t C, void *Y, void *stream);
+size_t pe_nn_dwconv7_bwd_workspace(int32_t B, int32_t H, int32_t W, int32_t C);
+pe_status pe_nn_dwconv7_bwd(const void *X, const void *dY, const float *w, int32_t B, int32_t H,
+                            int32_t W, int32_t C, void *dX, float *dw, float *db, void *ws,
+                            size_t ws_bytes, void *stream);
+
+/* LayerNorm over the C channels of each of P pixels (C <= 256), gamma/beta
+ * FP32; saves per-pixel mean and 1/std (FP32) for the backward, which writes
+ * dX and dgamma, dbeta (FP32, overwritten, nullable). */
+pe_status pe_nn_layernorm(const void *X, const float *gamma, const float *beta, int64_t P,
+                          int32_t C, float eps, void *Y, float *mean, float *rstd,
+                          void *stream);
+size_t pe_nn_layernorm_bwd_workspace(int64_t P, int32_t C);
+pe_status pe_nn_layernorm_bwd(const void *dY, const void *X, const float *gamma,
+                              const float *mean, const float *rstd, int64_t P, int32_t C,
+                              void *dX, float *dgamma, float *dbeta, void *ws, size_t ws_bytes,
+                              void *stream);
+
+/* Bias gradients: out[n] = (accumulate ? out[n] : 0) + sum_m X[m*ld + n]. */
+size_t pe_nn_colsum_workspace(int64_t M, int32_t N);
+pe_status pe_nn_colsum(const void *X, int64_t M, int32_t N, int64_t ld, float *out,
+                       int32_t accumulate, void *ws, size_t ws_bytes, void *stream);
+
+/* dZ = dA * GELU'(Z) elementwise (BF16). */
+pe_status pe_nn_gelu_bwd(const void *dA, const void *Z, int64_t n, void *dZ, void *stream);
+
+/* 2x2 max-pooling (even H, W) with the argmax (0..3, row-major in the window)
+ * kept in arg [B][H/2][W/2][C]; backward (backward = 1): X = dY, Y = dX. */
+pe_status pe_nn_maxpool2(const void *X, int32_t B, int32_t H, int32_t W, int32_t C, void *Y,
+                         uint8_t *arg, int32_t backward, void *stream);
+
+/* Sub-pixel convolution's shuffle (ref 51): out[b][2y+i][2x+j][off + c] =
+ * in[b][y][x][4c + 2i + j], the output having ld_big channels (so the result
+ * can land in one half of a concatenation); backward = 1 runs the reverse. */
+pe_status pe_nn_pixel_shuffle2(const void *src, int32_t B, int32_t H, int32_t W, int32_t C,
+                               void *dst, int64_t ld_big, int32_t off, int32_t backward,
+                               void *stream);
+
+/* dst[p][doff + c] = (accumulate ? dst : 0) + src[p][soff + c], c < C (BF16). */
+pe_status pe_nn_copy_channels(const void *src, int64_t lds, int32_t soff, void *dst, int64_t ldd,
+                              int32_t doff, int64_t P, int32_t C, int32_t accumulate,
+                              void *stream);
+
+/* FP32 -> BF16 copy. */
+pe_status pe_nn_to_bf16(const float *x, int64_t n, void *y, void *stream);
+
+/* AdamW (ref 53) with decoupled weight decay and bias correction at `step`
+ * (>= 1); also refreshes the BF16 copy p_bf16 (nullable). */
+pe_status pe_nn_adamw(float *p, const float *g, float *m, float *v, void *p_bf16, int64_t n,
+                      float lr, float beta1, float beta2, float eps, float weight_decay,
+                      int32_t step, void *stream);
+
+/* Eq. 17-21 on FP32 head outputs (depth [P], normal [P][3], mask logit [P])
+ * against d_gt [P], n_gt [P][3], m_gt [P] in {0,1}, P = B*H*W: L1 (squared
+ * depth error), L2 (|n_p x n_g| / (|n_p||n_g|)) and L4 (the same for the
+ * vectors (d_u, d_v, 1) of central differences, on hit pixels whose 4
+ * neighbours are hits) are means over ground-truth hits, L3 (alpha-balanced
+ * focal loss) a mean over all pixels; loss[0] = sum lambdas[i] * L(i+1),
+ * loss[1..4] = L1..L4 (device FP32); g_* = dL/d(outputs) (FP32, overwritten).
+ * |a x b| is evaluated as sqrt(|a x b|^2 + 1e-12) and norms products get
+ * +1e-8, so the losses are differentiable everywhere. */
+size_t pe_nn_unet_losses_workspace(int32_t B, int32_t H, int32_t W);
+pe_status pe_nn_unet_losses(const float *depth, const float *normal, const float *logit,
+                            const float *d_gt, const float *n_gt, const float *m_gt, int32_t B,
+                            int32_t H, int32_t W, float alpha, float gamma, const float *lambdas,
+                            float *loss, float *g_depth, float *g_normal, float *g_logit,
+                            void *ws, size_t ws_bytes, void *stream);
+
+/* Training pairs and GFB <-> hit records for n_views screens of one size.
+ * Depth is normalised per view: (t - t_near[v]) / t_scale[v] (host arrays).
+ * pe_learned_pairs: x_bf16 [P] = normalised depth of the tube-mode keys
+ * (pe_build_gfb mode 1; 0 where empty); from a surfel GFB (float4 n, depth;
+ * pe_build_gfb mode 0) d_gt, m_gt [P] and n_gt [P][3] = (n.u, n.v, n.w).
+ * pe_gfb_hits: single-bounce last-hit records (Sec. III-A, Eq. 14) of a GFB
+ * given as normalised depth [P], a hit indicator mask [P] (> threshold) and
+ * normals in the uvw frame [P][3] (turned to face the view), or -- when
+ * normal_uvw is NULL -- normals from the depth derivatives by Eq. 16. */
+pe_status pe_learned_pairs(const pe_view *views, int32_t n_views, const float *t_near,
+                           const float *t_scale, const uint64_t *tube_keys,
+                           const float *surfel_nd, void *x_bf16, float *d_gt, float *n_gt,
+                           float *m_gt, void *stream);
+pe_status pe_gfb_hits(const pe_view *views, int32_t n_views, const float *t_near,
+                      const float *t_scale, const float *depth, const float *mask,
+                      float threshold, const float *normal_uvw, const pe_hits *hits,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,8 +47,9 @@ def convnext(x, P, p):
 
 
 def forward(P, x, n_levels=4, blocks=(2, 2, 2, 2)):
-    """x: [B,1,H,W] normalised coarse depth -> dict of depth [B,1,H,W],
-    normal [B,3,H,W] (raw, uvw frame), mask logit [B,1,H,W]."""
+    """x: [B,1,H,W] normalised coarse depth -> dict of depth [B,1,H,W]
+    (input + the depth head's correction), normal [B,3,H,W] (raw, uvw frame),
+    mask logit [B,1,H,W]."""
     skips = []
     y = conv3(x, P["stem.w"], P["stem.b"])
     for lvl in range(n_levels):
@@ -66,6 +67,9 @@ def forward(P, x, n_levels=4, blocks=(2, 2, 2, 2)):
             u = conv1(u, P[f"{head}.fuse{lvl}.w"], P[f"{head}.fuse{lvl}.b"])
             u = convnext(u, P, f"{head}.blk{lvl}")
         out[head] = conv1(u, P[f"{head}.head.w"], P[f"{head}.head.b"])
+    # the depth decoder refines the coarse depth: its head output is a
+    # correction added to the input map (empty input pixels hold 0)
+    out["depth"] = out["depth"] + x
     return out
 
 

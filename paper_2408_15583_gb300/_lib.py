@@ -72,6 +72,38 @@ SIGNATURES = {
     "pe_po_field_static": (C.c_int, [P, C.c_int32, C.c_int64, P, P, C.c_int32, P, P]),
     "pe_rcs_sweep_workspace": (C.c_size_t, [P]),
     "pe_rcs_sweep": (C.c_int, [P, P, P, P, C.c_int64, P, P, P, C.c_size_t, P, P, P, P]),
+    # a8
+    "pe_nn_gemm_workspace": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int64]),
+    "pe_nn_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, P, C.c_int64, C.c_int64, P,
+                             C.c_int64, C.c_int64, P, C.c_int64, C.c_int32, P, P, C.c_int64, P,
+                             C.c_int64, C.c_int32, C.c_float, C.c_float, P, C.c_size_t, P]),
+    "pe_nn_im2col3": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, P]),
+    "pe_nn_dwconv7": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P]),
+    "pe_nn_dwconv7_bwd_workspace": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "pe_nn_dwconv7_bwd": (C.c_int, [P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, P,
+                                    P, C.c_size_t, P]),
+    "pe_nn_layernorm": (C.c_int, [P, P, P, C.c_int64, C.c_int32, C.c_float, P, P, P, P]),
+    "pe_nn_layernorm_bwd_workspace": (C.c_size_t, [C.c_int64, C.c_int32]),
+    "pe_nn_layernorm_bwd": (C.c_int, [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P,
+                                      C.c_size_t, P]),
+    "pe_nn_colsum_workspace": (C.c_size_t, [C.c_int64, C.c_int32]),
+    "pe_nn_colsum": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int64, P, C.c_int32, P, C.c_size_t,
+                               P]),
+    "pe_nn_gelu_bwd": (C.c_int, [P, P, C.c_int64, P, P]),
+    "pe_nn_maxpool2": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, C.c_int32,
+                                 P]),
+    "pe_nn_pixel_shuffle2": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P,
+                                       C.c_int64, C.c_int32, C.c_int32, P]),
+    "pe_nn_copy_channels": (C.c_int, [P, C.c_int64, C.c_int32, P, C.c_int64, C.c_int32,
+                                      C.c_int64, C.c_int32, C.c_int32, P]),
+    "pe_nn_to_bf16": (C.c_int, [P, C.c_int64, P, P]),
+    "pe_nn_adamw": (C.c_int, [P, P, P, P, P, C.c_int64, C.c_float, C.c_float, C.c_float,
+                              C.c_float, C.c_float, C.c_int32, P]),
+    "pe_nn_unet_losses_workspace": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+    "pe_nn_unet_losses": (C.c_int, [P, P, P, P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_float,
+                                    C.c_float, P, P, P, P, P, P, C.c_size_t, P]),
+    "pe_learned_pairs": (C.c_int, [P, C.c_int32, P, P, P, P, P, P, P, P, P]),
+    "pe_gfb_hits": (C.c_int, [P, C.c_int32, P, P, P, P, C.c_float, P, P, P]),
 }
 
 _lib = None

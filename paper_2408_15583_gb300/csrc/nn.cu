@@ -1,0 +1,1074 @@
+// Layer kernels of the learned GFB completion network (a8): BF16 activations
+// in NHWC layout, FP32 accumulation, FP32 master weights.
+//
+//   GEMM (tensor cores, mma.sync m16n8k16 BF16 -> FP32) with fused bias,
+//   residual, GELU epilogues and deterministic split-K; im2col / col2im for
+//   3x3 convolutions; depthwise 7x7; LayerNorm over channels; max-pool 2x2;
+//   pixel shuffle x2; channel copies for concatenation; bias / LayerNorm /
+//   depthwise weight reductions in a fixed order; the losses of Eq. 17-21 with
+//   their gradients; AdamW.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "pe_internal.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+__device__ __forceinline__ float b2f(bf16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ bf16 f2b(float x) { return __float2bfloat16_rn(x); }
+
+int n_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+int grid1(int64_t n, int threads, int per_sm = 16) {
+  int64_t b = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)n_sms() * per_sm;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+// ---------------------------------------------------------------------------
+// GEMM
+// ---------------------------------------------------------------------------
+struct gemm_args {
+  int M, N;
+  int64_t K;
+  const bf16 *A;
+  int64_t sam, sak;  // element (m, k) at A[m * sam + k * sak]
+  const bf16 *B;
+  int64_t sbk, sbn;  // element (k, n) at B[k * sbk + n * sbn]
+  void *C;
+  int64_t ldc;
+  int c_f32;
+  const float *bias;  // [N] or null
+  const bf16 *R;      // residual [M][ldr] or null
+  int64_t ldr;
+  bf16 *Z;            // pre-activation copy (gelu) or null
+  int64_t ldz;
+  int gelu;
+  float alpha, beta;  // beta applies to an FP32 C only
+  float *part;        // split-K partials [split][M][N]
+  int64_t k_per_split;
+  int vec_a, vec_b;
+};
+
+constexpr int GB = 64, GK = 32, GPAD = 40;
+
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+
+__device__ __forceinline__ void gemm_store(const gemm_args &g, int m, int n, float v) {
+  if (m >= g.M || n >= g.N) return;
+  if (g.bias) v += g.bias[n];
+  if (g.R) v += b2f(g.R[(int64_t)m * g.ldr + n]);
+  if (g.c_f32 && g.beta != 0.0f) v += g.beta * static_cast<float *>(g.C)[(int64_t)m * g.ldc + n];
+  if (g.gelu) {
+    if (g.Z) g.Z[(int64_t)m * g.ldz + n] = f2b(v);
+    v = gelu_f(v);
+  }
+  if (g.c_f32)
+    static_cast<float *>(g.C)[(int64_t)m * g.ldc + n] = v;
+  else
+    static_cast<bf16 *>(g.C)[(int64_t)m * g.ldc + n] = f2b(v);
+}
+
+// Tile rows [row0, row0+64) x k [k0, k0+32) of X into S[row][k].
+template <bool KCONTIG>
+__device__ __forceinline__ void load_tile(bf16 (*S)[GPAD], const bf16 *__restrict__ X,
+                                          int64_t s_r, int64_t s_k, int row0, int64_t k0,
+                                          int rows, int64_t k_end, bool vec) {
+  const bf16 zero = f2b(0.0f);
+  if (KCONTIG) {
+    for (int c = threadIdx.x; c < GB * GK / 8; c += blockDim.x) {
+      int r = c >> 2, kc = (c & 3) * 8;
+      int gr = row0 + r;
+      int64_t gk = k0 + kc;
+      if (vec && gr < rows && gk + 8 <= k_end) {
+        *reinterpret_cast<uint4 *>(&S[r][kc]) =
+            *reinterpret_cast<const uint4 *>(X + (int64_t)gr * s_r + gk);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          S[r][kc + e] = (gr < rows && gk + e < k_end) ? X[(int64_t)gr * s_r + (gk + e) * s_k] : zero;
+      }
+    }
+  } else {
+    for (int c = threadIdx.x; c < GB * GK / 8; c += blockDim.x) {
+      int k = c >> 3, rc = (c & 7) * 8;
+      int64_t gk = k0 + k;
+      int gr = row0 + rc;
+      if (vec && gk < k_end && gr + 8 <= rows) {
+        uint4 v = *reinterpret_cast<const uint4 *>(X + gk * s_k + gr);
+        const bf16 *t = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) S[rc + e][k] = t[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          S[rc + e][k] = (gk < k_end && gr + e < rows) ? X[(int64_t)(gr + e) * s_r + gk * s_k] : zero;
+      }
+    }
+  }
+}
+
+template <bool AK, bool BK>
+__global__ void __launch_bounds__(128) gemm_kernel(const gemm_args g) {
+  __shared__ __align__(16) bf16 As[GB][GPAD];
+  __shared__ __align__(16) bf16 Bs[GB][GPAD];
+  const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+  const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
+  int64_t ke = kb + g.k_per_split;
+  if (ke > g.K) ke = g.K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int gq = lane >> 2, tq = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
+    load_tile<AK>(As, g.A, g.sam, g.sak, m0, k0, g.M, ke, g.vec_a);
+    load_tile<BK>(Bs, g.B, g.sbn, g.sbk, n0, k0, g.N, ke, g.vec_b);
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + gq;
+        a[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tq * 2]);
+        a[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tq * 2]);
+        a[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tq * 2 + 8]);
+        a[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tq * 2 + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + j * 8 + gq;
+        b[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + tq * 2]);
+        b[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + tq * 2 + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+              "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]),
+                "r"(b[j][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = m0 + wm + i * 16 + gq + (e >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + tq * 2 + (e & 1);
+        const float v = acc[i][j][e] * g.alpha;
+        if (g.part) {
+          if (m < g.M && n < g.N) g.part[((int64_t)blockIdx.z * g.M + m) * g.N + n] = v;
+        } else {
+          gemm_store(g, m, n, v);
+        }
+      }
+}
+
+__global__ void gemm_splitk_reduce(const gemm_args g, int split) {
+  const int64_t total = (int64_t)g.M * g.N;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    for (int z = 0; z < split; ++z) v += g.part[(int64_t)z * total + t];
+    gemm_store(g, (int)(t / g.N), (int)(t % g.N), v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3x3 convolution helpers (NHWC, zero padding 1): col[p][(ky*3+kx)*C + c]
+// ---------------------------------------------------------------------------
+__global__ void im2col3_kernel(const bf16 *__restrict__ X, int B, int H, int W, int C,
+                               bf16 *__restrict__ col) {
+  const int64_t total = (int64_t)B * H * W * 9 * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    int tap = (int)((t / C) % 9);
+    int64_t p = t / (9 * (int64_t)C);
+    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+    col[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                 ? X[(((int64_t)b * H + yy) * W + xx) * C + c]
+                 : f2b(0.0f);
+  }
+}
+
+// dX[b,y,x,c] = sum over taps of dcol at the pixel that read (y, x) through that tap.
+__global__ void col2im3_kernel(const bf16 *__restrict__ dcol, int B, int H, int W, int C,
+                               bf16 *__restrict__ dX) {
+  const int64_t total = (int64_t)B * H * W * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    int64_t p = t / C;
+    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    float s = 0.0f;
+    for (int tap = 0; tap < 9; ++tap) {
+      int py = y - (tap / 3 - 1), px = x - (tap % 3 - 1);
+      if (py < 0 || py >= H || px < 0 || px >= W) continue;
+      s += b2f(dcol[((((int64_t)b * H + py) * W + px) * 9 + tap) * C + c]);
+    }
+    dX[t] = f2b(s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// depthwise 7x7 (zero padding 3), weights w[ky][kx][c] FP32
+// ---------------------------------------------------------------------------
+__global__ void dw7_fwd_kernel(const bf16 *__restrict__ X, const float *__restrict__ w,
+                               const float *__restrict__ bias, int B, int H, int W, int C,
+                               bf16 *__restrict__ Y) {
+  const int64_t total = (int64_t)B * H * W * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    int64_t p = t / C;
+    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    float s = bias ? bias[c] : 0.0f;
+    for (int ky = 0; ky < 7; ++ky) {
+      int yy = y + ky - 3;
+      if (yy < 0 || yy >= H) continue;
+      for (int kx = 0; kx < 7; ++kx) {
+        int xx = x + kx - 3;
+        if (xx < 0 || xx >= W) continue;
+        s += w[(ky * 7 + kx) * C + c] * b2f(X[(((int64_t)b * H + yy) * W + xx) * C + c]);
+      }
+    }
+    Y[t] = f2b(s);
+  }
+}
+
+__global__ void dw7_bwd_data_kernel(const bf16 *__restrict__ dY, const float *__restrict__ w, int B,
+                                    int H, int W, int C, bf16 *__restrict__ dX) {
+  const int64_t total = (int64_t)B * H * W * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    int64_t p = t / C;
+    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    float s = 0.0f;
+    for (int ky = 0; ky < 7; ++ky) {
+      int yy = y - ky + 3;
+      if (yy < 0 || yy >= H) continue;
+      for (int kx = 0; kx < 7; ++kx) {
+        int xx = x - kx + 3;
+        if (xx < 0 || xx >= W) continue;
+        s += w[(ky * 7 + kx) * C + c] * b2f(dY[(((int64_t)b * H + yy) * W + xx) * C + c]);
+      }
+    }
+    dX[t] = f2b(s);
+  }
+}
+
+// Partial weight/bias gradients: block (cx, chunk) sums pixels of its chunk
+// for 32 channels; part[chunk][50][C] (tap 49 = bias).
+__global__ void __launch_bounds__(256) dw7_bwd_weight_kernel(const bf16 *__restrict__ X,
+                                                             const bf16 *__restrict__ dY, int B,
+                                                             int H, int W, int C,
+                                                             int64_t pix_per_chunk,
+                                                             float *__restrict__ part) {
+  __shared__ float red[8][32];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  const int64_t P = (int64_t)B * H * W;
+  const int64_t p0 = (int64_t)blockIdx.y * pix_per_chunk;
+  int64_t p1 = p0 + pix_per_chunk;
+  if (p1 > P) p1 = P;
+  float acc[50];
+#pragma unroll
+  for (int i = 0; i < 50; ++i) acc[i] = 0.0f;
+  if (c < C) {
+    for (int64_t p = p0 + threadIdx.y; p < p1; p += 8) {
+      int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+      float g = b2f(dY[p * C + c]);
+      acc[49] += g;
+#pragma unroll
+      for (int ky = 0; ky < 7; ++ky) {
+        int yy = y + ky - 3;
+        if (yy < 0 || yy >= H) continue;
+#pragma unroll
+        for (int kx = 0; kx < 7; ++kx) {
+          int xx = x + kx - 3;
+          if (xx < 0 || xx >= W) continue;
+          acc[ky * 7 + kx] += g * b2f(X[(((int64_t)b * H + yy) * W + xx) * C + c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 50; ++i) {
+    red[threadIdx.y][threadIdx.x] = acc[i];
+    __syncthreads();
+    if (threadIdx.y == 0 && c < C) {
+      float s = 0.0f;
+      for (int r = 0; r < 8; ++r) s += red[r][threadIdx.x];
+      part[((int64_t)blockIdx.y * 50 + i) * C + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[i] = sum over chunks of part[chunk][i] (fixed order), i < n.
+__global__ void sum_chunks_kernel(const float *__restrict__ part, int chunks, int64_t n,
+                                  float *__restrict__ out, int accumulate) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int k = 0; k < chunks; ++k) s += part[(int64_t)k * n + i];
+    out[i] = accumulate ? out[i] + s : s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// LayerNorm over the C channels of each pixel (one warp per pixel)
+// ---------------------------------------------------------------------------
+__global__ void ln_fwd_kernel(const bf16 *__restrict__ X, const float *__restrict__ gam,
+                              const float *__restrict__ bet, int64_t P, int C, float eps,
+                              bf16 *__restrict__ Y, float *__restrict__ mean,
+                              float *__restrict__ rstd) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
+    const bf16 *x = X + p * C;
+    float s = 0.0f;
+    for (int c = lane; c < C; c += 32) s += b2f(x[c]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float mu = s / C;
+    float v = 0.0f;
+    for (int c = lane; c < C; c += 32) {
+      float d = b2f(x[c]) - mu;
+      v += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const float rs = rsqrtf(v / C + eps);
+    for (int c = lane; c < C; c += 32) Y[p * C + c] = f2b((b2f(x[c]) - mu) * rs * gam[c] + bet[c]);
+    if (lane == 0) {
+      mean[p] = mu;
+      rstd[p] = rs;
+    }
+  }
+}
+
+// dX and per-warp partials of dgamma, dbeta: part[warp][2][C].
+__global__ void ln_bwd_kernel(const bf16 *__restrict__ dY, const bf16 *__restrict__ X,
+                              const float *__restrict__ gam, const float *__restrict__ mean,
+                              const float *__restrict__ rstd, int64_t P, int C,
+                              bf16 *__restrict__ dX, float *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  float dg[8], db[8];  // C <= 256
+#pragma unroll
+  for (int i = 0; i < 8; ++i) dg[i] = db[i] = 0.0f;
+  for (int64_t p = gw; p < P; p += warps) {
+    const float mu = mean[p], rs = rstd[p];
+    float s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      int c = lane + 32 * i;
+      if (c >= C) break;
+      float xh = (b2f(X[p * C + c]) - mu) * rs;
+      float gy = b2f(dY[p * C + c]);
+      float g = gy * gam[c];
+      s1 += g;
+      s2 += g * xh;
+      dg[i] += gy * xh;
+      db[i] += gy;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    s1 /= C;
+    s2 /= C;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      int c = lane + 32 * i;
+      if (c >= C) break;
+      float xh = (b2f(X[p * C + c]) - mu) * rs;
+      float g = b2f(dY[p * C + c]) * gam[c];
+      dX[p * C + c] = f2b(rs * (g - s1 - xh * s2));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int c = lane + 32 * i;
+    if (c >= C) break;
+    part[(gw * 2 + 0) * C + c] = dg[i];
+    part[(gw * 2 + 1) * C + c] = db[i];
+  }
+}
+
+// Column sums of a [M][ld] BF16 matrix in fixed order: part[chunk][N].
+__global__ void colsum_kernel(const bf16 *__restrict__ Xs, int64_t M, int N, int64_t ld,
+                              int64_t rows_per_chunk, float *__restrict__ part) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk, r1 = r0 + rows_per_chunk;
+    if (r1 > M) r1 = M;
+    float s = 0.0f;
+    for (int64_t r = r0; r < r1; ++r) s += b2f(Xs[r * ld + n]);
+    part[(int64_t)blockIdx.y * N + n] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise
+// ---------------------------------------------------------------------------
+__global__ void gelu_bwd_kernel(const bf16 *__restrict__ dA, const bf16 *__restrict__ Z, int64_t n,
+                                bf16 *__restrict__ dZ) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float z = b2f(Z[i]);
+    float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+    float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
+    dZ[i] = f2b(b2f(dA[i]) * (cdf + z * pdf));
+  }
+}
+
+__global__ void maxpool2_fwd_kernel(const bf16 *__restrict__ X, int B, int H, int W, int C,
+                                    bf16 *__restrict__ Y, uint8_t *__restrict__ arg) {
+  const int Ho = H / 2, Wo = W / 2;
+  const int64_t total = (int64_t)B * Ho * Wo * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    int64_t p = t / C;
+    int x = (int)(p % Wo), y = (int)((p / Wo) % Ho), b = (int)(p / ((int64_t)Wo * Ho));
+    float best = -INFINITY;
+    int bi = 0;
+    for (int k = 0; k < 4; ++k) {
+      float v = b2f(X[(((int64_t)b * H + 2 * y + (k >> 1)) * W + 2 * x + (k & 1)) * C + c]);
+      if (v > best) {
+        best = v;
+        bi = k;
+      }
+    }
+    Y[t] = f2b(best);
+    arg[t] = (uint8_t)bi;
+  }
+}
+
+__global__ void maxpool2_bwd_kernel(const bf16 *__restrict__ dY, const uint8_t *__restrict__ arg,
+                                    int B, int H, int W, int C, bf16 *__restrict__ dX) {
+  const int64_t total = (int64_t)B * H * W * C;
+  const int Ho = H / 2, Wo = W / 2;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    int64_t p = t / C;
+    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    int64_t q = (((int64_t)b * Ho + y / 2) * Wo + x / 2) * C + c;
+    dX[t] = (arg[q] == (uint8_t)(((y & 1) << 1) | (x & 1))) ? dY[q] : f2b(0.0f);
+  }
+}
+
+// out[b, 2y+i, 2x+j, off + c] = in[b, y, x, 4c + 2i + j]; dir 1: the reverse.
+__global__ void pixel_shuffle2_kernel(const bf16 *__restrict__ src, int B, int H, int W, int C,
+                                      bf16 *__restrict__ dst, int64_t ld_big, int off, int dir) {
+  const int64_t total = (int64_t)B * H * W * 4 * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c4 = (int)(t % (4 * C));
+    int64_t p = t / (4 * C);
+    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
+    int c = c4 >> 2, i = (c4 >> 1) & 1, j = c4 & 1;
+    int64_t big = (((int64_t)b * 2 * H + 2 * y + i) * 2 * W + 2 * x + j) * ld_big + off + c;
+    if (dir == 0)
+      dst[big] = src[t];
+    else
+      dst[t] = src[big];
+  }
+}
+
+// dst[p][doff + c] (=|+=) src[p][soff + c] for c < C.
+__global__ void copy_channels_kernel(const bf16 *__restrict__ src, int64_t lds, int soff,
+                                     bf16 *__restrict__ dst, int64_t ldd, int doff, int64_t P,
+                                     int C, int accumulate) {
+  const int64_t total = P * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int c = (int)(t % C);
+    int64_t p = t / C;
+    float v = b2f(src[p * lds + soff + c]);
+    bf16 *d = dst + p * ldd + doff + c;
+    *d = f2b(accumulate ? b2f(*d) + v : v);
+  }
+}
+
+__global__ void f32_to_bf16_kernel(const float *__restrict__ x, int64_t n, bf16 *__restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = f2b(x[i]);
+}
+
+__global__ void adamw_kernel(float *__restrict__ p, const float *__restrict__ g,
+                             float *__restrict__ m, float *__restrict__ v, bf16 *__restrict__ pb,
+                             int64_t n, float lr, float b1, float b2, float eps, float wd,
+                             float bc1, float bc2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.0f - b1) * gi;
+    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    float pi = p[i] * (1.0f - lr * wd) - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    p[i] = pi;
+    if (pb) pb[i] = f2b(pi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Losses of Eq. 17-21 and their gradients.  Outputs are FP32 head outputs:
+// depth [P], normal [P][3], mask logit [P].  Ground truth: d_gt [P],
+// n_gt [P][3], m_gt [P] (0/1).  counts[0] = hit pixels, [1] = L4 pixels,
+// [2] = all pixels (set by loss_count_kernel).
+// ---------------------------------------------------------------------------
+struct loss_args {
+  const float *d, *n, *z, *d_gt, *n_gt, *m_gt;
+  int B, H, W;
+  float alpha, gamma, w1, w2, w3, w4;
+  const float *counts;
+  float *g_d, *g_n, *g_z;  // gradients of the total loss
+  float *c4u, *c4v;        // per pixel dL4/d(gu), dL4/d(gv) (scratch)
+  float *part;             // [blocks][4] loss partial sums
+};
+
+__device__ __forceinline__ bool hit_at(const loss_args &a, int b, int y, int x) {
+  return a.m_gt[((int64_t)b * a.H + y) * a.W + x] > 0.5f;
+}
+
+__device__ __forceinline__ bool l4_valid(const loss_args &a, int b, int y, int x) {
+  if (x < 1 || y < 1 || x > a.W - 2 || y > a.H - 2) return false;
+  return hit_at(a, b, y, x) && hit_at(a, b, y, x - 1) && hit_at(a, b, y, x + 1) &&
+         hit_at(a, b, y - 1, x) && hit_at(a, b, y + 1, x);
+}
+
+// f = |a x b| / (|a| |b| + e) with |a x b| = sqrt(|a x b|^2 + 1e-12); returns f
+// and df/da.
+__device__ __forceinline__ float cross_ratio(const float a[3], const float b[3], float ga[3]) {
+  float c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+  float cn = sqrtf(c[0] * c[0] + c[1] * c[1] + c[2] * c[2] + 1e-12f);
+  float na = sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  float nb = sqrtf(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+  float den = na * nb + 1e-8f;
+  float bxc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+  for (int k = 0; k < 3; ++k)
+    ga[k] = (bxc[k] / cn) / den - cn * nb * (na > 0.0f ? a[k] / na : 0.0f) / (den * den);
+  return cn / den;
+}
+
+__global__ void loss_count_kernel(const loss_args a, float *counts) {
+  // single block: deterministic counts
+  __shared__ float s[3][256];
+  float c0 = 0.0f, c1 = 0.0f;
+  const int64_t P = (int64_t)a.B * a.H * a.W;
+  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) {
+    int x = (int)(p % a.W), y = (int)((p / a.W) % a.H), b = (int)(p / ((int64_t)a.W * a.H));
+    c0 += hit_at(a, b, y, x) ? 1.0f : 0.0f;
+    c1 += l4_valid(a, b, y, x) ? 1.0f : 0.0f;
+  }
+  s[0][threadIdx.x] = c0;
+  s[1][threadIdx.x] = c1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t0 = 0.0f, t1 = 0.0f;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      t0 += s[0][i];
+      t1 += s[1][i];
+    }
+    counts[0] = fmaxf(t0, 1.0f);
+    counts[1] = fmaxf(t1, 1.0f);
+    counts[2] = (float)P;
+  }
+}
+
+__device__ __forceinline__ void grads_at(const loss_args &a, const float *d, int b, int y, int x,
+                                         float g[3]) {
+  const int64_t row = ((int64_t)b * a.H + y) * a.W;
+  g[0] = 0.5f * (d[row + x + 1] - d[row + x - 1]);
+  g[1] = 0.5f * (d[row + a.W + x] - d[row - a.W + x]);
+  g[2] = 1.0f;
+}
+
+// Pass 1: per-pixel terms of L1, L2, L3 with their gradients, and the L4
+// partials with respect to the centre's (gu, gv).
+__global__ void __launch_bounds__(256) loss_pass1_kernel(const loss_args a) {
+  __shared__ float red[4][256];
+  const int64_t P = (int64_t)a.B * a.H * a.W;
+  const float nh = a.counts[0], n4 = a.counts[1], na = a.counts[2];
+  float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(p % a.W), y = (int)((p / a.W) % a.H), b = (int)(p / ((int64_t)a.W * a.H));
+    const bool hit = a.m_gt[p] > 0.5f;
+    // L1
+    float gd = 0.0f;
+    if (hit) {
+      float e = a.d[p] - a.d_gt[p];
+      s[0] += e * e / nh;
+      gd = a.w1 * 2.0f * e / nh;
+    }
+    a.g_d[p] = gd;
+    // L2
+    float gn[3] = {0.0f, 0.0f, 0.0f};
+    if (hit) {
+      float np_[3] = {a.n[3 * p], a.n[3 * p + 1], a.n[3 * p + 2]};
+      float ng[3] = {a.n_gt[3 * p], a.n_gt[3 * p + 1], a.n_gt[3 * p + 2]};
+      float ga[3];
+      s[1] += cross_ratio(np_, ng, ga) / nh;
+      for (int k = 0; k < 3; ++k) gn[k] = a.w2 * ga[k] / nh;
+    }
+    for (int k = 0; k < 3; ++k) a.g_n[3 * p + k] = gn[k];
+    // L3 (focal, alpha-balanced)
+    {
+      float z = a.z[p];
+      float pr = 1.0f / (1.0f + expf(-z));
+      float lp = -(fmaxf(-z, 0.0f) + log1pf(expf(-fabsf(z))));   // log p
+      float l1p = -(fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z))));   // log (1 - p)
+      float l, dl;
+      if (hit) {
+        float q = powf(1.0f - pr, a.gamma);
+        l = -a.alpha * q * lp;
+        dl = -a.alpha * q * (-a.gamma * pr * lp + (1.0f - pr));
+      } else {
+        float q = powf(pr, a.gamma);
+        l = -(1.0f - a.alpha) * q * l1p;
+        dl = -(1.0f - a.alpha) * q * (a.gamma * (1.0f - pr) * l1p - pr);
+      }
+      s[2] += l / na;
+      a.g_z[p] = a.w3 * dl / na;
+    }
+    // L4 partials at valid centres
+    float cu = 0.0f, cv = 0.0f;
+    if (l4_valid(a, b, y, x)) {
+      float gp[3], gg[3], ga[3];
+      grads_at(a, a.d, b, y, x, gp);
+      grads_at(a, a.d_gt, b, y, x, gg);
+      s[3] += cross_ratio(gp, gg, ga) / n4;
+      cu = a.w4 * ga[0] / n4;
+      cv = a.w4 * ga[1] / n4;
+    }
+    a.c4u[p] = cu;
+    a.c4v[p] = cv;
+  }
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = s[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.0f;
+      for (int i = 0; i < (int)blockDim.x; ++i) t += red[k][i];
+      a.part[blockIdx.x * 4 + k] = t;
+    }
+  }
+}
+
+// Pass 2: scatter the L4 centre partials to the depths they were made of
+// (gather form): d(x+1) gets +0.5 cu(x), d(x-1) gets -0.5 cu(x), likewise v.
+__global__ void loss_pass2_kernel(const loss_args a) {
+  const int64_t P = (int64_t)a.B * a.H * a.W;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(p % a.W), y = (int)((p / a.W) % a.H);
+    float g = 0.0f;
+    if (x >= 1) g += 0.5f * a.c4u[p - 1];
+    if (x <= a.W - 2) g -= 0.5f * a.c4u[p + 1];
+    if (y >= 1) g += 0.5f * a.c4v[p - a.W];
+    if (y <= a.H - 2) g -= 0.5f * a.c4v[p + a.W];
+    a.g_d[p] += g;
+  }
+}
+
+__global__ void loss_total_kernel(const float *part, int blocks, float w1, float w2, float w3,
+                                  float w4, float *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float s[4] = {0, 0, 0, 0};
+  for (int b = 0; b < blocks; ++b)
+    for (int k = 0; k < 4; ++k) s[k] += part[b * 4 + k];
+  out[0] = w1 * s[0] + w2 * s[1] + w3 * s[2] + w4 * s[3];
+  for (int k = 0; k < 4; ++k) out[1 + k] = s[k];
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+#define NN_CHECK_STREAM cudaStream_t s = static_cast<cudaStream_t>(stream)
+
+extern "C" size_t pe_nn_gemm_workspace(int32_t M, int32_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0) return 0;
+  int64_t tiles = (int64_t)((N + GB - 1) / GB) * ((M + GB - 1) / GB);
+  int64_t target = (int64_t)n_sms() * 4;
+  int64_t split = tiles >= target ? 1 : (target + tiles - 1) / tiles;
+  int64_t max_split = (K + 1023) / 1024;
+  if (split > max_split) split = max_split;
+  if (split > 64) split = 64;
+  if (split <= 1) return 256;
+  return (size_t)split * M * N * sizeof(float) + 256;
+}
+
+extern "C" pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, int64_t sam,
+                                int64_t sak, const void *B, int64_t sbk, int64_t sbn, void *C,
+                                int64_t ldc, int32_t c_f32, const float *bias, const void *R,
+                                int64_t ldr, void *Z, int64_t ldz, int32_t gelu, float alpha,
+                                float beta, void *ws, size_t ws_bytes, void *stream) {
+  NN_CHECK_STREAM;
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C)
+    return pe_fail(PE_EINVAL, "pe_nn_gemm: bad sizes or null operands");
+  gemm_args g;
+  memset(&g, 0, sizeof(g));
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.A = static_cast<const bf16 *>(A);
+  g.sam = sam;
+  g.sak = sak;
+  g.B = static_cast<const bf16 *>(B);
+  g.sbk = sbk;
+  g.sbn = sbn;
+  g.C = C;
+  g.ldc = ldc;
+  g.c_f32 = c_f32;
+  g.bias = bias;
+  g.R = static_cast<const bf16 *>(R);
+  g.ldr = ldr;
+  g.Z = static_cast<bf16 *>(Z);
+  g.ldz = ldz;
+  g.gelu = gelu;
+  g.alpha = alpha;
+  g.beta = beta;
+  const bool ak = sak == 1, bk = sbk == 1;
+  // vector loads need 16-byte aligned rows along the contiguous dimension
+  auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  g.vec_a = al(A) && (ak ? (sam % 8 == 0) : (sam == 1 && sak % 8 == 0));
+  g.vec_b = al(B) && (bk ? (sbn % 8 == 0) : (sbn == 1 && sbk % 8 == 0));
+  int64_t tiles = (int64_t)((N + GB - 1) / GB) * ((M + GB - 1) / GB);
+  int64_t target = (int64_t)n_sms() * 4;
+  int64_t split = tiles >= target ? 1 : (target + tiles - 1) / tiles;
+  int64_t max_split = (K + 1023) / 1024;
+  if (split > max_split) split = max_split;
+  if (split > 64) split = 64;
+  if (split < 1) split = 1;
+  int64_t kps = (K + split - 1) / split;
+  kps = (kps + GK - 1) / GK * GK;
+  split = (K + kps - 1) / kps;
+  g.k_per_split = kps;
+  if (split > 1) {
+    size_t need = (size_t)split * M * N * sizeof(float);
+    if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_gemm: workspace needs %zu", need);
+    g.part = static_cast<float *>(ws);
+  }
+  if ((M + GB - 1) / GB > 65535) return pe_fail(PE_EINVAL, "pe_nn_gemm: M too large");
+  dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB, (unsigned)split);
+  if (ak && bk) gemm_kernel<true, true><<<grid, 128, 0, s>>>(g);
+  else if (ak && !bk) gemm_kernel<true, false><<<grid, 128, 0, s>>>(g);
+  else if (!ak && bk) gemm_kernel<false, true><<<grid, 128, 0, s>>>(g);
+  else gemm_kernel<false, false><<<grid, 128, 0, s>>>(g);
+  PE_TRY_LAUNCH("gemm_kernel");
+  if (split > 1) {
+    gemm_splitk_reduce<<<grid1((int64_t)M * N, 256), 256, 0, s>>>(g, (int)split);
+    PE_TRY_LAUNCH("gemm_splitk_reduce");
+  }
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_im2col3(const void *X, int32_t B, int32_t H, int32_t W, int32_t C,
+                                   void *col, int32_t backward, void *stream) {
+  NN_CHECK_STREAM;
+  if (!X || !col || B <= 0 || H <= 0 || W <= 0 || C <= 0)
+    return pe_fail(PE_EINVAL, "pe_nn_im2col3: bad arguments");
+  if (!backward) {
+    im2col3_kernel<<<grid1((int64_t)B * H * W * 9 * C, 256), 256, 0, s>>>(
+        static_cast<const bf16 *>(X), B, H, W, C, static_cast<bf16 *>(col));
+    PE_TRY_LAUNCH("im2col3_kernel");
+  } else {  // X is dcol [P][9C], col is dX [P][C]
+    col2im3_kernel<<<grid1((int64_t)B * H * W * C, 256), 256, 0, s>>>(
+        static_cast<const bf16 *>(X), B, H, W, C, static_cast<bf16 *>(col));
+    PE_TRY_LAUNCH("col2im3_kernel");
+  }
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_dwconv7(const void *X, const float *w, const float *bias, int32_t B,
+                                   int32_t H, int32_t W, int32_t C, void *Y, void *stream) {
+  NN_CHECK_STREAM;
+  if (!X || !w || !Y || B <= 0 || H <= 0 || W <= 0 || C <= 0)
+    return pe_fail(PE_EINVAL, "pe_nn_dwconv7: bad arguments");
+  dw7_fwd_kernel<<<grid1((int64_t)B * H * W * C, 256), 256, 0, s>>>(
+      static_cast<const bf16 *>(X), w, bias, B, H, W, C, static_cast<bf16 *>(Y));
+  PE_TRY_LAUNCH("dw7_fwd_kernel");
+  return PE_OK;
+}
+
+static int64_t dw_chunks(int64_t P) {
+  int64_t c = (P + 2047) / 2048;
+  return c < 1 ? 1 : (c > 1024 ? 1024 : c);
+}
+
+extern "C" size_t pe_nn_dwconv7_bwd_workspace(int32_t B, int32_t H, int32_t W, int32_t C) {
+  int64_t P = (int64_t)B * H * W;
+  return (size_t)dw_chunks(P) * 50 * C * sizeof(float) + 256;
+}
+
+// dX (nullable), dw [7][7][C] and db [C] (FP32, overwritten).
+extern "C" pe_status pe_nn_dwconv7_bwd(const void *X, const void *dY, const float *w, int32_t B,
+                                       int32_t H, int32_t W, int32_t C, void *dX, float *dw,
+                                       float *db, void *ws, size_t ws_bytes, void *stream) {
+  NN_CHECK_STREAM;
+  if (!X || !dY || !w || B <= 0 || H <= 0 || W <= 0 || C <= 0)
+    return pe_fail(PE_EINVAL, "pe_nn_dwconv7_bwd: bad arguments");
+  int64_t P = (int64_t)B * H * W;
+  if (dX) {
+    dw7_bwd_data_kernel<<<grid1(P * C, 256), 256, 0, s>>>(static_cast<const bf16 *>(dY), w, B, H,
+                                                            W, C, static_cast<bf16 *>(dX));
+    PE_TRY_LAUNCH("dw7_bwd_data_kernel");
+  }
+  if (dw || db) {
+    int64_t chunks = dw_chunks(P);
+    size_t need = (size_t)chunks * 50 * C * sizeof(float);
+    if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_dwconv7_bwd: workspace");
+    float *part = static_cast<float *>(ws);
+    dim3 grid((C + 31) / 32, (unsigned)chunks);
+    dw7_bwd_weight_kernel<<<grid, dim3(32, 8), 0, s>>>(static_cast<const bf16 *>(X),
+                                                       static_cast<const bf16 *>(dY), B, H, W, C,
+                                                       (P + chunks - 1) / chunks, part);
+    PE_TRY_LAUNCH("dw7_bwd_weight_kernel");
+    // part[chunk][50][C]: taps 0..48 -> dw, 49 -> db; sum the chunks in
+    // order into chunk 0 (each thread reads and writes only its own index)
+    sum_chunks_kernel<<<grid1(50 * (int64_t)C, 256), 256, 0, s>>>(part, (int)chunks,
+                                                                  50 * (int64_t)C, part, 0);
+    PE_TRY_LAUNCH("sum_chunks_kernel");
+    if (dw) PE_TRY_CUDA(cudaMemcpyAsync(dw, part, sizeof(float) * 49 * C, cudaMemcpyDeviceToDevice, s));
+    if (db)
+      PE_TRY_CUDA(cudaMemcpyAsync(db, part + 49 * C, sizeof(float) * C, cudaMemcpyDeviceToDevice, s));
+  }
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_layernorm(const void *X, const float *gamma, const float *beta,
+                                     int64_t P, int32_t C, float eps, void *Y, float *mean,
+                                     float *rstd, void *stream) {
+  NN_CHECK_STREAM;
+  if (!X || !gamma || !beta || !Y || !mean || !rstd || P <= 0 || C <= 0 || C > 256)
+    return pe_fail(PE_EINVAL, "pe_nn_layernorm: bad arguments (C <= 256)");
+  ln_fwd_kernel<<<grid1(P * 32, 256), 256, 0, s>>>(static_cast<const bf16 *>(X), gamma, beta, P, C,
+                                                   eps, static_cast<bf16 *>(Y), mean, rstd);
+  PE_TRY_LAUNCH("ln_fwd_kernel");
+  return PE_OK;
+}
+
+extern "C" size_t pe_nn_layernorm_bwd_workspace(int64_t P, int32_t C) {
+  int64_t warps = (int64_t)grid1(P * 32, 256) * 8;
+  return (size_t)warps * 2 * C * sizeof(float) + 256;
+}
+
+// dX and dgamma, dbeta (FP32, overwritten).
+extern "C" pe_status pe_nn_layernorm_bwd(const void *dY, const void *X, const float *gamma,
+                                         const float *mean, const float *rstd, int64_t P, int32_t C,
+                                         void *dX, float *dgamma, float *dbeta, void *ws,
+                                         size_t ws_bytes, void *stream) {
+  NN_CHECK_STREAM;
+  if (!dY || !X || !gamma || !mean || !rstd || !dX || P <= 0 || C <= 0 || C > 256)
+    return pe_fail(PE_EINVAL, "pe_nn_layernorm_bwd: bad arguments (C <= 256)");
+  int blocks = grid1(P * 32, 256);
+  int64_t warps = (int64_t)blocks * 8;
+  size_t need = (size_t)warps * 2 * C * sizeof(float);
+  if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_layernorm_bwd: workspace");
+  float *part = static_cast<float *>(ws);
+  ln_bwd_kernel<<<blocks, 256, 0, s>>>(static_cast<const bf16 *>(dY), static_cast<const bf16 *>(X),
+                                       gamma, mean, rstd, P, C, static_cast<bf16 *>(dX), part);
+  PE_TRY_LAUNCH("ln_bwd_kernel");
+  // part[warp][2][C]: sum over warps in order
+  sum_chunks_kernel<<<grid1(2 * (int64_t)C, 256), 256, 0, s>>>(part, (int)warps, 2 * (int64_t)C,
+                                                               part, 0);
+  PE_TRY_LAUNCH("sum_chunks_kernel");
+  if (dgamma) PE_TRY_CUDA(cudaMemcpyAsync(dgamma, part, sizeof(float) * C, cudaMemcpyDeviceToDevice, s));
+  if (dbeta) PE_TRY_CUDA(cudaMemcpyAsync(dbeta, part + C, sizeof(float) * C, cudaMemcpyDeviceToDevice, s));
+  return PE_OK;
+}
+
+extern "C" size_t pe_nn_colsum_workspace(int64_t M, int32_t N) {
+  int64_t chunks = (M + 4095) / 4096;
+  return (size_t)(chunks < 1 ? 1 : chunks) * N * sizeof(float) + 256;
+}
+
+// out[n] = (accumulate ? out[n] : 0) + sum_m X[m * ld + n] (fixed order).
+extern "C" pe_status pe_nn_colsum(const void *X, int64_t M, int32_t N, int64_t ld, float *out,
+                                  int32_t accumulate, void *ws, size_t ws_bytes, void *stream) {
+  NN_CHECK_STREAM;
+  if (!X || !out || M <= 0 || N <= 0) return pe_fail(PE_EINVAL, "pe_nn_colsum: bad arguments");
+  int64_t chunks = (M + 4095) / 4096;
+  if (chunks < 1) chunks = 1;
+  size_t need = (size_t)chunks * N * sizeof(float);
+  if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_colsum: workspace");
+  float *part = static_cast<float *>(ws);
+  colsum_kernel<<<dim3((N + 127) / 128, (unsigned)chunks), 128, 0, s>>>(
+      static_cast<const bf16 *>(X), M, N, ld, 4096, part);
+  PE_TRY_LAUNCH("colsum_kernel");
+  sum_chunks_kernel<<<grid1(N, 256), 256, 0, s>>>(part, (int)chunks, N, out, accumulate);
+  PE_TRY_LAUNCH("sum_chunks_kernel");
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_gelu_bwd(const void *dA, const void *Z, int64_t n, void *dZ,
+                                    void *stream) {
+  NN_CHECK_STREAM;
+  if (!dA || !Z || !dZ || n <= 0) return pe_fail(PE_EINVAL, "pe_nn_gelu_bwd: bad arguments");
+  gelu_bwd_kernel<<<grid1(n, 256), 256, 0, s>>>(static_cast<const bf16 *>(dA),
+                                                static_cast<const bf16 *>(Z), n,
+                                                static_cast<bf16 *>(dZ));
+  PE_TRY_LAUNCH("gelu_bwd_kernel");
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_maxpool2(const void *X, int32_t B, int32_t H, int32_t W, int32_t C,
+                                    void *Y, uint8_t *arg, int32_t backward, void *stream) {
+  NN_CHECK_STREAM;
+  if (!X || !Y || !arg || B <= 0 || H < 2 || W < 2 || C <= 0 || (H & 1) || (W & 1))
+    return pe_fail(PE_EINVAL, "pe_nn_maxpool2: bad arguments (even H, W)");
+  if (!backward) {
+    maxpool2_fwd_kernel<<<grid1((int64_t)B * H * W * C / 4, 256), 256, 0, s>>>(
+        static_cast<const bf16 *>(X), B, H, W, C, static_cast<bf16 *>(Y), arg);
+    PE_TRY_LAUNCH("maxpool2_fwd_kernel");
+  } else {  // X = dY (pooled), Y = dX (full)
+    maxpool2_bwd_kernel<<<grid1((int64_t)B * H * W * C, 256), 256, 0, s>>>(
+        static_cast<const bf16 *>(X), arg, B, H, W, C, static_cast<bf16 *>(Y));
+    PE_TRY_LAUNCH("maxpool2_bwd_kernel");
+  }
+  return PE_OK;
+}
+
+// Forward: src [B][H][W][4C] -> dst [B][2H][2W][ld_big] at channel offset off.
+// Backward: src = the big gradient, dst = [B][H][W][4C].
+extern "C" pe_status pe_nn_pixel_shuffle2(const void *src, int32_t B, int32_t H, int32_t W,
+                                          int32_t C, void *dst, int64_t ld_big, int32_t off,
+                                          int32_t backward, void *stream) {
+  NN_CHECK_STREAM;
+  if (!src || !dst || B <= 0 || H <= 0 || W <= 0 || C <= 0 || off < 0 || off + C > ld_big)
+    return pe_fail(PE_EINVAL, "pe_nn_pixel_shuffle2: bad arguments");
+  pixel_shuffle2_kernel<<<grid1((int64_t)B * H * W * 4 * C, 256), 256, 0, s>>>(
+      static_cast<const bf16 *>(src), B, H, W, C, static_cast<bf16 *>(dst), ld_big, off,
+      backward ? 1 : 0);
+  PE_TRY_LAUNCH("pixel_shuffle2_kernel");
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_copy_channels(const void *src, int64_t lds, int32_t soff, void *dst,
+                                         int64_t ldd, int32_t doff, int64_t P, int32_t C,
+                                         int32_t accumulate, void *stream) {
+  NN_CHECK_STREAM;
+  if (!src || !dst || P <= 0 || C <= 0) return pe_fail(PE_EINVAL, "pe_nn_copy_channels: bad arguments");
+  copy_channels_kernel<<<grid1(P * C, 256), 256, 0, s>>>(static_cast<const bf16 *>(src), lds, soff,
+                                                         static_cast<bf16 *>(dst), ldd, doff, P, C,
+                                                         accumulate);
+  PE_TRY_LAUNCH("copy_channels_kernel");
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_to_bf16(const float *x, int64_t n, void *y, void *stream) {
+  NN_CHECK_STREAM;
+  if (!x || !y || n <= 0) return pe_fail(PE_EINVAL, "pe_nn_to_bf16: bad arguments");
+  f32_to_bf16_kernel<<<grid1(n, 256), 256, 0, s>>>(x, n, static_cast<bf16 *>(y));
+  PE_TRY_LAUNCH("f32_to_bf16_kernel");
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_adamw(float *p, const float *g, float *m, float *v, void *p_bf16,
+                                 int64_t n, float lr, float beta1, float beta2, float eps,
+                                 float weight_decay, int32_t step, void *stream) {
+  NN_CHECK_STREAM;
+  if (!p || !g || !m || !v || n <= 0 || step < 1) return pe_fail(PE_EINVAL, "pe_nn_adamw: bad arguments");
+  float bc1 = 1.0f - powf(beta1, (float)step), bc2 = 1.0f - powf(beta2, (float)step);
+  adamw_kernel<<<grid1(n, 256), 256, 0, s>>>(p, g, m, v, static_cast<bf16 *>(p_bf16), n, lr, beta1,
+                                             beta2, eps, weight_decay, bc1, bc2);
+  PE_TRY_LAUNCH("adamw_kernel");
+  return PE_OK;
+}
+
+static int loss_blocks(int64_t P) { return grid1(P, 256, 4); }
+
+extern "C" size_t pe_nn_unet_losses_workspace(int32_t B, int32_t H, int32_t W) {
+  int64_t P = (int64_t)B * H * W;
+  return (size_t)(2 * P + 4 * loss_blocks(P) + 8) * sizeof(float) + 1024;
+}
+
+// Eq. 17-21: loss[0] = L, loss[1..4] = L1..L4 (device FP32); gradients of L
+// with respect to the head outputs (FP32, overwritten).
+extern "C" pe_status pe_nn_unet_losses(const float *depth, const float *normal, const float *logit,
+                                       const float *d_gt, const float *n_gt, const float *m_gt,
+                                       int32_t B, int32_t H, int32_t W, float alpha, float gamma,
+                                       const float *lambdas, float *loss, float *g_depth,
+                                       float *g_normal, float *g_logit, void *ws, size_t ws_bytes,
+                                       void *stream) {
+  NN_CHECK_STREAM;
+  if (!depth || !normal || !logit || !d_gt || !n_gt || !m_gt || !lambdas || !loss || !g_depth ||
+      !g_normal || !g_logit || B <= 0 || H < 3 || W < 3)
+    return pe_fail(PE_EINVAL, "pe_nn_unet_losses: bad arguments");
+  int64_t P = (int64_t)B * H * W;
+  if (!ws || ws_bytes < pe_nn_unet_losses_workspace(B, H, W))
+    return pe_fail(PE_ENOMEM, "pe_nn_unet_losses: workspace");
+  float *f = static_cast<float *>(ws);
+  loss_args a;
+  memset(&a, 0, sizeof(a));
+  a.d = depth;
+  a.n = normal;
+  a.z = logit;
+  a.d_gt = d_gt;
+  a.n_gt = n_gt;
+  a.m_gt = m_gt;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.alpha = alpha;
+  a.gamma = gamma;
+  a.w1 = lambdas[0];
+  a.w2 = lambdas[1];
+  a.w3 = lambdas[2];
+  a.w4 = lambdas[3];
+  a.g_d = g_depth;
+  a.g_n = g_normal;
+  a.g_z = g_logit;
+  a.c4u = f;
+  a.c4v = f + P;
+  int blocks = loss_blocks(P);
+  a.part = f + 2 * P;
+  float *counts = f + 2 * P + 4 * blocks;
+  a.counts = counts;
+  loss_count_kernel<<<1, 256, 0, s>>>(a, counts);
+  PE_TRY_LAUNCH("loss_count_kernel");
+  loss_pass1_kernel<<<blocks, 256, 0, s>>>(a);
+  PE_TRY_LAUNCH("loss_pass1_kernel");
+  loss_pass2_kernel<<<grid1(P, 256), 256, 0, s>>>(a);
+  PE_TRY_LAUNCH("loss_pass2_kernel");
+  loss_total_kernel<<<1, 32, 0, s>>>(a.part, blocks, a.w1, a.w2, a.w3, a.w4, loss);
+  PE_TRY_LAUNCH("loss_total_kernel");
+  return PE_OK;
+}

@@ -1,0 +1,213 @@
+"""Data, training and evaluation of the learned GFB completion (a8).
+
+Pairs: for a random target (``scenes.random_primitives``) sampled sparsely
+(5-50 points per lambda^2) and densely (>= 200 per lambda^2), each view gives
+a coarse tube-mode depth map (Alg. 1, tube radius 1-3 pixels) of the sparse
+cloud as input, and the dense cloud's surfel GFB (depth, normal in the uvw
+frame, hit mask) as target -- both produced by the surfel tracer kernels
+(``pe_build_gfb``), whose output is bit-identical to the CPU oracle's FP32
+mode.  The ray pitch is lambda/10 (Sec. IV-A).
+
+Evaluation (what the network gains): for held-out targets, the monostatic PO
+RCS (single bounce, Eq. 14) of (a) the dense surfel GFB -- the reference --,
+(b) the coarse tube-mode GFB with normals from its depth by Eq. 16 -- the
+method without the network --, and (c) the network's GFB; RMSE in dB over the
+views of each target with the floor of c23 (max(sigma_ref) - 60 dB).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import time
+from dataclasses import dataclass
+from typing import List
+
+import numpy as np
+import torch
+
+from . import _lib, api, pipeline
+from ._lib import check
+from .learned import UNet, lr_schedule
+
+C0 = 299_792_458.0
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class ViewSet:
+    views: list
+    t_near: np.ndarray
+    t_scale: np.ndarray
+    lam: float
+    W: int
+
+
+def view_set(scene, n_views: int, W: int, seed: int) -> ViewSet:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    p = scene.pos.astype(np.float64)
+    c = 0.5 * (p.min(0) + p.max(0))
+    r = float(np.sqrt(((p - c) ** 2).sum(1).max()))
+    ext = 1.02 * r
+    th = rng.uniform(30.0, 150.0, n_views)
+    ph = rng.uniform(0.0, 360.0, n_views)
+    views = [api.view_from_angles(t, f, c, ext, W, W) for t, f in zip(th, ph)]
+    L = views[0].pitch
+    D = ext + L
+    return ViewSet(views, np.full(n_views, D - r, np.float32), np.full(n_views, 2 * r, np.float32),
+                   10.0 * L, W)
+
+
+def make_pairs(sparse, dense, vs: ViewSet, delta_px: float, device="cuda:0"):
+    """GPU tensors x (BF16 [n*P]), d_gt, m_gt ([n*P]), n_gt ([n*P, 3])."""
+    lib = _lib.load()
+    n = len(vs.views)
+    P = vs.W * vs.W
+    ps, _, _ = pipeline.scene_to_device(sparse, device)
+    pd, nd_, rd = pipeline.scene_to_device(dense, device)
+    delta = float(delta_px * vs.views[0].pitch)
+    keys = api.build_gfb(vs.views, ps, None, None, 1, delta, outputs=("keys",))["keys"]
+    nd = api.build_gfb(vs.views, pd, nd_, rd, 0, outputs=("nd",))["nd"]
+    x = torch.empty(n * P, dtype=torch.bfloat16, device=device)
+    d_gt = torch.empty(n * P, dtype=torch.float32, device=device)
+    m_gt = torch.empty(n * P, dtype=torch.float32, device=device)
+    n_gt = torch.empty(n * P, 3, dtype=torch.float32, device=device)
+    arr = api.views_to_array(vs.views)
+    check(lib.pe_learned_pairs(arr, n, vs.t_near.ctypes.data_as(C.c_void_p),
+                               vs.t_scale.ctypes.data_as(C.c_void_p), _p(keys), _p(nd), _p(x),
+                               _p(d_gt), _p(n_gt), _p(m_gt),
+                               C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+          "pe_learned_pairs")
+    return {"x": x, "d_gt": d_gt, "n_gt": n_gt, "m_gt": m_gt, "vs": vs}
+
+
+def dataset(n_scenes: int, views_per_scene: int, W: int, seed: int, device="cuda:0",
+            dense_density=200.0):
+    import scenes
+    out = []
+    for k in range(n_scenes):
+        sd = seed * 100_003 + k
+        rng = np.random.Generator(np.random.PCG64(sd))
+        sparse = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0)
+        dense = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0, density=dense_density)
+        vs = view_set(sparse, views_per_scene, W, sd + 1)
+        out.append(make_pairs(sparse, dense, vs, float(rng.uniform(1.0, 3.0)), device))
+    return out
+
+
+def _cat(items, key):
+    return torch.cat([it[key] for it in items])
+
+
+def train(model: UNet, data: List[dict], steps: int, batch: int, lr0=1e-3, seed=0,
+          log_every=0):
+    """Mini-batches of `batch` views drawn from the whole set; the paper's
+    halving schedule (Sec. IV-A) with `steps_per_epoch` = views / batch."""
+    W = data[0]["vs"].W
+    P = W * W
+    x = _cat(data, "x").view(-1, P)
+    d = _cat(data, "d_gt").view(-1, P)
+    n = _cat(data, "n_gt").view(-1, P, 3)
+    m = _cat(data, "m_gt").view(-1, P)
+    nv = x.shape[0]
+    spe = max(1, nv // batch)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    hist = []
+    for step in range(steps):
+        idx = torch.from_numpy(rng.choice(nv, size=batch, replace=False)).to(x.device)
+        lr = lr_schedule(step, spe, lr0=lr0, floor=1e-6)
+        loss = model.train_step(x[idx].reshape(-1).contiguous(), d[idx].reshape(-1).contiguous(),
+                                n[idx].reshape(-1, 3).contiguous(), m[idx].reshape(-1).contiguous(),
+                                batch, W, W, lr)
+        if log_every and (step % log_every == 0 or step == steps - 1):
+            hist.append((step, loss.cpu().numpy().tolist()))
+    return hist
+
+
+def _sigma_from_hits(hits, vs: ViewSet):
+    """Monostatic sigma (VV, m^2) of each view at f = c / lambda."""
+    n = len(vs.views)
+    ks = np.array([[-c for c in v.d] for v in vs.views], np.float32)
+    E = api.po_field(hits, n, vs.W * vs.W, ks, np.array([C0 / vs.lam]))
+    E = E.cpu().numpy()
+    E = E[..., 0] + 1j * E[..., 1]                   # [n][1][pol][3]
+    k = 2 * math.pi / vs.lam
+    out = np.empty(n)
+    for a, v in enumerate(vs.views):
+        e = np.array(v.u[:], np.float64)
+        out[a] = k * k / math.pi * abs(E[a, 0, 0] @ e) ** 2
+    return out
+
+
+def gfb_sigma(vs: ViewSet, depth, mask, threshold, normal_uvw):
+    lib = _lib.load()
+    n = len(vs.views)
+    h = api.alloc_hits(n * vs.W * vs.W, 1, depth.device, ids=False)
+    arr = api.views_to_array(vs.views)
+    check(lib.pe_gfb_hits(arr, n, vs.t_near.ctypes.data_as(C.c_void_p),
+                          vs.t_scale.ctypes.data_as(C.c_void_p), _p(depth), _p(mask),
+                          float(threshold), _p(normal_uvw), C.byref(h.c),
+                          C.c_void_p(torch.cuda.current_stream().cuda_stream)), "pe_gfb_hits")
+    return _sigma_from_hits(h, vs)
+
+
+def rmse_db(s, ref, floor_db=60.0):
+    sd = 10 * np.log10(np.maximum(s, 1e-30))
+    rd = 10 * np.log10(np.maximum(ref, 1e-30))
+    lo = rd.max() - floor_db
+    return float(np.sqrt(np.mean((np.maximum(sd, lo) - np.maximum(rd, lo)) ** 2)))
+
+
+def evaluate(model: UNet, data: List[dict]):
+    """Per held-out target: RMSE (dB) of the coarse GFB + Eq. 16 normals and
+    of the network's GFB against the dense surfel GFB."""
+    res = []
+    for it in data:
+        vs = it["vs"]
+        n = len(vs.views)
+        W = vs.W
+        ref = gfb_sigma(vs, it["d_gt"], it["m_gt"], 0.5, it["n_gt"])
+        xf = it["x"].float()
+        coarse = gfb_sigma(vs, xf, xf, 0.0, None)
+        outs, _ = model.forward(it["x"], n, W, W)
+        learned = gfb_sigma(vs, outs["depth"], outs["mask"], 0.0, outs["normal"])
+        res.append({"coarse": rmse_db(coarse, ref), "learned": rmse_db(learned, ref)})
+    return res
+
+
+def time_paths(model: UNet, sparse, dense, vs: ViewSet, reps=5):
+    """Per-view time of the learned path (tube splat of the sparse cloud +
+    network inference) and of plain surfel splatting of the dense cloud."""
+    dev = model.dev
+    ps, _, _ = pipeline.scene_to_device(sparse, dev)
+    pd, nd_, rd = pipeline.scene_to_device(dense, dev)
+    n = len(vs.views)
+    delta = 2.0 * vs.views[0].pitch
+    lib = _lib.load()
+    x = torch.empty(n * vs.W * vs.W, dtype=torch.bfloat16, device=dev)
+    arr = api.views_to_array(vs.views)
+
+    def learned():
+        keys = api.build_gfb(vs.views, ps, None, None, 1, delta, outputs=("keys",))["keys"]
+        check(lib.pe_learned_pairs(arr, n, vs.t_near.ctypes.data_as(C.c_void_p),
+                                   vs.t_scale.ctypes.data_as(C.c_void_p), _p(keys), None, _p(x),
+                                   None, None, None,
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+              "pe_learned_pairs")
+        model.forward(x, n, vs.W, vs.W)
+
+    def plain():
+        api.build_gfb(vs.views, pd, nd_, rd, 0, outputs=("nd", "mask"))
+
+    out = {}
+    for name, fn in (("learned", learned), ("plain_splatting", plain)):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        out[name] = (time.perf_counter() - t) / reps / n
+    return out

@@ -315,27 +315,28 @@ def composite(n_points: int = 1_000_000, seed: int = 7, freq_hz: float = 10e9,
 
 
 def random_primitives(seed: int, lam: float, bbox_lambdas: float = 25.6,
-                      n_min: int = 3, n_max: int = 12) -> Scene:
+                      n_min: int = 3, n_max: int = 12, density: Optional[float] = None,
+                      sample_seed: Optional[int] = None) -> Scene:
     """3-12 random boxes / cylinders / spheres of 0.2-2 m (then rescaled so the
     scene's longest bbox edge is ``bbox_lambdas`` wavelengths), sampled at a
-    uniform density of 5-50 points per lambda^2."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    k = int(rng.integers(n_min, n_max + 1))
-    parts_p, parts_n, areas = [], [], []
+    uniform density of 5-50 points per lambda^2 (or ``density`` points per
+    lambda^2).  The shapes depend on ``seed`` only, so the same target can be
+    sampled sparsely and densely."""
+    srng = np.random.Generator(np.random.PCG64(seed))
+    k = int(srng.integers(n_min, n_max + 1))
     shapes = []
     for _ in range(k):
-        kind = int(rng.integers(0, 3))
-        size = rng.uniform(0.2, 2.0, size=3)
-        ctr = rng.uniform(-2.0, 2.0, size=3)
+        kind = int(srng.integers(0, 3))
+        size = srng.uniform(0.2, 2.0, size=3)
+        ctr = srng.uniform(-2.0, 2.0, size=3)
         shapes.append((kind, size, ctr))
-    scale_probe = []
-    for kind, size, ctr in shapes:
-        scale_probe.append(ctr - size)
-        scale_probe.append(ctr + size)
-    sp = np.array(scale_probe)
+    dens = float(srng.uniform(5.0, 50.0)) if density is None else float(density)
+    rng = np.random.Generator(np.random.PCG64(seed * 7919 + 1 if sample_seed is None else sample_seed))
+    sp = np.array([c - s for _, s, c in shapes] + [c + s for _, s, c in shapes])
     ext = float((sp.max(axis=0) - sp.min(axis=0)).max())
     s = bbox_lambdas * lam / ext
-    density = rng.uniform(5.0, 50.0) / (lam * lam)
+    density = dens / (lam * lam)
+    parts_p, parts_n = [], []
     for kind, size, ctr in shapes:
         size = size * s
         ctr = ctr * s

@@ -1,0 +1,276 @@
+"""The learned GFB completion (a8) on the GPU against the FP64 CPU reference
+network (oracle/unet.py) and plain FP64 PyTorch references of single layers.
+
+BF16 activations (8-bit mantissa) set the tolerances: single layers within
+2e-2 relative, the whole network's outputs within 5e-2 (relative L2), the
+gradients of the well-conditioned loss terms within 0.05 per parameter tensor,
+those of the full loss within 0.1 as a whole.  The losses run in FP32 from
+FP32 head outputs and match to 1e-4.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import scenes  # noqa: E402
+from oracle import unet as ounet  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def ops():
+    from paper_2408_15583_gb300.learned import Ops
+    return Ops(DEV)
+
+
+def bf(x):
+    return torch.as_tensor(x).to(torch.bfloat16)
+
+
+def rel(a, b):
+    a = a.detach().double().cpu()
+    b = b.detach().double().cpu()
+    return float((a - b).norm() / b.norm().clamp(min=1e-30))
+
+
+@pytest.mark.parametrize("M,N,K", [(200, 96, 72), (64, 64, 32), (37, 5, 9), (96, 160, 20000)])
+def test_gemm_layouts(M, N, K):
+    o = ops()
+    g = torch.Generator().manual_seed(M + N + K)
+    A = bf(torch.randn(M, K, generator=g))
+    B = bf(torch.randn(K, N, generator=g))
+    ref = A.double() @ B.double()
+    bias = torch.randn(N, generator=g)
+    # NT: A row-major [M,K], B given as [N,K]
+    out = torch.empty(M, N, dtype=torch.float32, device=DEV)
+    Bt = B.t().contiguous().to(DEV)
+    o.gemm(M, N, K, A.to(DEV), K, 1, Bt, 1, K, out, N, bias=bias.to(DEV))
+    assert rel(out, ref + bias.double()) < 1e-5
+    # NN: B row-major [K,N], BF16 output with a residual and GELU
+    R = bf(torch.randn(M, N, generator=g))
+    out16 = torch.empty(M, N, dtype=torch.bfloat16, device=DEV)
+    Z = torch.empty(M, N, dtype=torch.bfloat16, device=DEV)
+    o.gemm(M, N, K, A.to(DEV), K, 1, B.to(DEV), N, 1, out16, N, R=R.to(DEV), ldr=N, Z=Z, ldz=N,
+           gelu=True)
+    pre = ref + R.double()
+    assert rel(Z, pre) < 1e-2
+    assert rel(out16, torch.nn.functional.gelu(pre)) < 1e-2
+    # TN: A given as [K,M] (column-major A)
+    At = A.t().contiguous().to(DEV)
+    out2 = torch.empty(M, N, dtype=torch.float32, device=DEV)
+    o.gemm(M, N, K, At, 1, M, B.to(DEV), N, 1, out2, N)
+    assert rel(out2, ref) < 1e-5
+
+
+def test_depthwise_layernorm_pool_shuffle_vs_torch():
+    o = ops()
+    Bn, H, W, Cc = 2, 12, 10, 40
+    g = torch.Generator().manual_seed(1)
+    x = bf(torch.randn(Bn, H, W, Cc, generator=g))
+    w = torch.randn(7, 7, Cc, generator=g) * 0.2
+    b = torch.randn(Cc, generator=g)
+    y = torch.empty(Bn * H * W, Cc, dtype=torch.bfloat16, device=DEV)
+    o.dw(x.to(DEV), w.to(DEV), b.to(DEV), Bn, H, W, Cc, y)
+    xr = x.double().permute(0, 3, 1, 2)
+    ref = torch.nn.functional.conv2d(xr, w.double().permute(2, 0, 1)[:, None], b.double(),
+                                     padding=3, groups=Cc)
+    assert rel(y.view(Bn, H, W, Cc).permute(0, 3, 1, 2), ref) < 1e-2
+    # depthwise backward vs autograd
+    xq = xr.clone().requires_grad_(True)
+    wq = w.double().clone().requires_grad_(True)
+    bq = b.double().clone().requires_grad_(True)
+    out = torch.nn.functional.conv2d(xq, wq.permute(2, 0, 1)[:, None], bq, padding=3, groups=Cc)
+    dy = bf(torch.randn(Bn, H, W, Cc, generator=g))
+    out.backward(dy.double().permute(0, 3, 1, 2))
+    dx = torch.empty(Bn * H * W, Cc, dtype=torch.bfloat16, device=DEV)
+    dw = torch.empty(7, 7, Cc, device=DEV)
+    db = torch.empty(Cc, device=DEV)
+    o.dw_bwd(x.to(DEV), dy.to(DEV), w.to(DEV), Bn, H, W, Cc, dx, dw, db)
+    assert rel(dx.view(Bn, H, W, Cc).permute(0, 3, 1, 2), xq.grad) < 1e-2
+    assert rel(dw, wq.grad) < 1e-3 and rel(db, bq.grad) < 1e-3
+    # LayerNorm forward/backward
+    P = Bn * H * W
+    gam, bet = torch.randn(Cc, generator=g), torch.randn(Cc, generator=g)
+    yl = torch.empty(P, Cc, dtype=torch.bfloat16, device=DEV)
+    mean = torch.empty(P, device=DEV)
+    rstd = torch.empty(P, device=DEV)
+    o.ln(x.to(DEV), gam.to(DEV), bet.to(DEV), P, Cc, yl, mean, rstd)
+    xl = x.double().view(P, Cc).clone().requires_grad_(True)
+    gl = gam.double().clone().requires_grad_(True)
+    bl = bet.double().clone().requires_grad_(True)
+    refl = torch.nn.functional.layer_norm(xl, (Cc,), gl, bl, 1e-6)
+    assert rel(yl, refl) < 1e-2
+    dyl = bf(torch.randn(P, Cc, generator=g))
+    refl.backward(dyl.double())
+    dxl = torch.empty(P, Cc, dtype=torch.bfloat16, device=DEV)
+    dg = torch.empty(Cc, device=DEV)
+    dbt = torch.empty(Cc, device=DEV)
+    o.ln_bwd(dyl.to(DEV), x.to(DEV), gam.to(DEV), mean, rstd, P, Cc, dxl, dg, dbt)
+    assert rel(dxl, xl.grad) < 2e-2 and rel(dg, gl.grad) < 1e-3 and rel(dbt, bl.grad) < 1e-3
+    # max-pool and its backward
+    yp = torch.empty(Bn * (H // 2) * (W // 2), Cc, dtype=torch.bfloat16, device=DEV)
+    arg = torch.empty(yp.shape, dtype=torch.uint8, device=DEV)
+    o.maxpool(x.to(DEV), Bn, H, W, Cc, yp, arg)
+    refp = torch.nn.functional.max_pool2d(xr, 2)
+    assert torch.equal(yp.view(Bn, H // 2, W // 2, Cc).permute(0, 3, 1, 2).double().cpu(), refp)
+    # pixel shuffle into the first half of a concatenation
+    src = bf(torch.randn(Bn, H, W, 4 * 8, generator=g))
+    big = torch.zeros(Bn * 2 * H * 2 * W, 16, dtype=torch.bfloat16, device=DEV)
+    o.shuffle(src.to(DEV), Bn, H, W, 8, big, 16, 0)
+    refs = torch.nn.functional.pixel_shuffle(src.double().permute(0, 3, 1, 2), 2)
+    got = big.view(Bn, 2 * H, 2 * W, 16)[..., :8].permute(0, 3, 1, 2).double().cpu()
+    assert torch.equal(got, refs)
+
+
+def _oracle_outputs(params, x, widths, blocks):
+    P = ounet.to_params(params)
+    out = ounet.forward(P, torch.tensor(x[:, None], dtype=torch.float64), n_levels=len(widths),
+                        blocks=blocks)
+    return P, out
+
+
+def _net(widths, blocks, seed):
+    from paper_2408_15583_gb300.learned import UNet
+    params = scenes.unet_init(seed, widths, blocks)
+    return params, UNet(params, widths, blocks, DEV)
+
+
+def _rand_targets(Bn, H, W, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    d = g.random((Bn, H, W))
+    n = g.normal(size=(Bn, H, W, 3))
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    m = (g.random((Bn, H, W)) > 0.3).astype(np.float64)
+    m[:, 4:12, 4:12] = 1.0
+    return d, n, m
+
+
+def test_losses_match_oracle():
+    from paper_2408_15583_gb300.learned import UNet
+    params = scenes.unet_init(0, (8, 8, 8, 8), (1, 1, 1, 1))
+    net = UNet(params, (8, 8, 8, 8), (1, 1, 1, 1), DEV)
+    Bn, H, W = 2, 16, 16
+    g = np.random.Generator(np.random.PCG64(9))
+    outs = {"depth": g.random((Bn, H, W)), "normal": g.normal(size=(Bn, H, W, 3)),
+            "mask": g.normal(size=(Bn, H, W)) * 2}
+    d, n, m = _rand_targets(Bn, H, W, 3)
+    to = lambda a: torch.tensor(a, dtype=torch.float32, device=DEV).reshape(-1, *a.shape[3:])
+    gpu_outs = {"depth": to(outs["depth"]).view(-1), "normal": to(outs["normal"]),
+                "mask": to(outs["mask"]).view(-1)}
+    loss, grads = net.losses(gpu_outs, to(d).view(-1).contiguous(), to(n).contiguous(),
+                             to(m).view(-1).contiguous(), Bn, H, W)
+    od = torch.tensor(outs["depth"], dtype=torch.float64, requires_grad=True)
+    on = torch.tensor(outs["normal"], dtype=torch.float64, requires_grad=True)
+    oz = torch.tensor(outs["mask"], dtype=torch.float64, requires_grad=True)
+    L, parts = ounet.losses({"depth": od[:, None], "normal": on.permute(0, 3, 1, 2),
+                             "mask": oz[:, None]}, torch.tensor(d), torch.tensor(n), torch.tensor(m))
+    L.backward()
+    lv = loss.cpu().numpy()
+    assert abs(lv[0] - L.item()) < 1e-4 * abs(L.item())
+    for k in range(4):
+        assert abs(lv[1 + k] - parts[k].item()) < 1e-4 * max(abs(parts[k].item()), 1e-6)
+    assert rel(grads["depth"], od.grad.reshape(-1)) < 1e-4
+    assert rel(grads["normal"], on.grad.reshape(-1, 3)) < 1e-4
+    assert rel(grads["mask"], oz.grad.reshape(-1)) < 1e-4
+
+
+WID, BLK = (32, 64, 128, 256), (2, 2, 2, 2)
+
+
+def test_unet_forward_matches_oracle():
+    params, net = _net(WID, BLK, 4)
+    Bn, H, W = 2, 32, 32
+    x = np.random.Generator(np.random.PCG64(2)).random((Bn, H, W)).astype(np.float32)
+    x = torch.tensor(x).to(torch.bfloat16).float().numpy()      # both sides see the BF16 input
+    outs, _ = net.forward(torch.tensor(x).to(torch.bfloat16).to(DEV).reshape(-1), Bn, H, W)
+    _, ref = _oracle_outputs(params, x, WID, BLK)
+    assert rel(outs["depth"].view(Bn, H, W), ref["depth"][:, 0]) < 5e-2
+    assert rel(outs["normal"].view(Bn, H, W, 3), ref["normal"].permute(0, 2, 3, 1)) < 5e-2
+    assert rel(outs["mask"].view(Bn, H, W), ref["mask"][:, 0]) < 5e-2
+
+
+def _grad_compare(lambdas, seed):
+    params, net = _net(WID, BLK, seed)
+    Bn, H, W = 2, 32, 32
+    x = np.random.Generator(np.random.PCG64(seed)).random((Bn, H, W)).astype(np.float32)
+    x = torch.tensor(x).to(torch.bfloat16).float().numpy()
+    d, n, m = _rand_targets(Bn, H, W, seed + 1)
+    to = lambda a: torch.tensor(a, dtype=torch.float32, device=DEV)
+    outs, tape = net.forward(torch.tensor(x).to(torch.bfloat16).to(DEV).reshape(-1), Bn, H, W)
+    loss, grads = net.losses(outs, to(d).reshape(-1), to(n).reshape(-1, 3), to(m).reshape(-1),
+                             Bn, H, W, lambdas=lambdas)
+    net.backward(tape, grads)
+    P, ref = _oracle_outputs(params, x, WID, BLK)
+    _, parts = ounet.losses(ref, torch.tensor(d), torch.tensor(n), torch.tensor(m))
+    L = sum(w * p for w, p in zip(lambdas, parts))
+    L.backward()
+    assert abs(loss.cpu().numpy()[0] - L.item()) < 5e-2 * abs(L.item())
+    rows = []
+    ga, gb_ = [], []
+    for name in params:
+        gg = net.g(name).double().cpu().reshape(-1)
+        go = P[name].grad.reshape(-1)
+        ga.append(gg)
+        gb_.append(go)
+        if go.norm() < 1e-12:
+            continue
+        cos = float(gg @ go / (gg.norm() * go.norm() + 1e-30))
+        rows.append((rel(gg, go), cos, name))
+    ga, gb_ = torch.cat(ga), torch.cat(gb_)
+    cos_all = float(ga @ gb_ / (ga.norm() * gb_.norm()))
+    return sorted(rows, reverse=True), (cos_all, rel(ga, gb_))
+
+
+def test_unet_backward_chain_matches_oracle():
+    # the depth and mask losses (Eq. 17, 19) are well conditioned: every
+    # parameter's gradient through the shared encoder and those decoders
+    rows, _ = _grad_compare((1.0, 0.0, 1.0, 0.0), 5)
+    assert rows[0][0] < 0.05, rows[:5]
+    assert min(c for _, c, _ in rows) > 0.998, sorted(rows, key=lambda t: t[1])[:5]
+
+
+def test_unet_gradients_of_the_full_loss():
+    # Eq. 21: the sin-angle terms (Eq. 18, 20) scale like 1/|n| and amplify
+    # BF16 rounding of the outputs where the raw normal is small at
+    # initialisation; pixel sums with heavy cancellation (head biases) then
+    # show it most.  The whole gradient vector must agree closely.
+    rows, (cos_all, rel_all) = _grad_compare((1.0, 0.5, 1.0, 0.5), 6)
+    assert rel_all < 0.1 and cos_all > 0.995, (rel_all, cos_all, rows[:5])
+    assert min(c for _, c, _ in rows) > 0.9, sorted(rows, key=lambda t: t[1])[:5]
+
+
+def test_training_reduces_the_loss():
+    from paper_2408_15583_gb300 import learned_train as lt
+    params, net = _net(WID, BLK, 6)
+    data = lt.dataset(6, 4, 64, seed=1)
+    hist = lt.train(net, data, steps=60, batch=8, lr0=1e-3, log_every=10)
+    first, last = hist[0][1][0], hist[-1][1][0]
+    assert last < 0.8 * first, hist
+
+
+def test_learned_gfb_beats_the_coarse_gfb_on_held_out_targets():
+    """What the trained network gains over the method without it: the
+    coarse tube-tracing GFB with Eq. 16 normals vs the network's GFB, both
+    against the dense surfel GFB, monostatic PO RCS RMSE in dB."""
+    from paper_2408_15583_gb300 import learned_train as lt
+    params, net = _net(WID, BLK, 7)
+    train = lt.dataset(48, 8, 64, seed=11)
+    lt.train(net, train, steps=1000, batch=16, lr0=1e-3)
+    held = lt.dataset(8, 12, 64, seed=99)
+    res = lt.evaluate(net, held)
+    coarse = float(np.mean([r["coarse"] for r in res]))
+    learned = float(np.mean([r["learned"] for r in res]))
+    print(f"RCS RMSE vs dense surfel GFB: coarse {coarse:.2f} dB, learned {learned:.2f} dB")
+    assert learned < coarse

@@ -25,6 +25,15 @@ def test_shapes_and_heads():
     assert out["mask"].shape == (2, 1, 16, 16)
 
 
+def test_depth_output_refines_the_input():
+    # with the depth head zeroed, the refined depth is the coarse input
+    P = small_params()
+    P["depth.head.w"].data.zero_()
+    P["depth.head.b"].data.zero_()
+    x = torch.rand(1, 1, 8, 8, dtype=torch.float64)
+    assert torch.equal(unet.forward(P, x, blocks=B_SMALL)["depth"], x)
+
+
 def test_convnext_block_is_identity_with_zero_last_projection():
     P = small_params()
     P["enc0.0.pw2.w"].data.zero_()
