@@ -451,6 +451,56 @@ def run_serving(n_requests=100, slots=4, budget_gb=150.0, seed=5):
     return out
 
 
+# ----------------------------------------------------------------------------
+# learned GFB completion (training throughput, inference vs plain splatting)
+# ----------------------------------------------------------------------------
+
+def run_learned(W=256, batch=64, steps=8, warmup=2):
+    """Training steps of the U-Net at the C4 shape (256^2 coarse depth,
+    batch 64, widths 32-256), timed with CUDA events; per-view time of the
+    learned path (tube splat of the sparse cloud + inference) vs plain surfel
+    splatting of the dense cloud."""
+    import torch
+    from paper_2408_15583_gb300 import learned_train as lt
+    from paper_2408_15583_gb300.learned import UNet
+    widths, blocks = (32, 64, 128, 256), (2, 2, 2, 2)
+    data = lt.dataset(4, 16, W, seed=21, keep_scenes=True)
+    net = UNet(scenes.unet_init(0, widths, blocks), widths, blocks, "cuda:0")
+    P = W * W
+    x = torch.cat([d["x"] for d in data]).view(-1, P)[:batch].reshape(-1).contiguous()
+    dg = torch.cat([d["d_gt"] for d in data]).view(-1, P)[:batch].reshape(-1).contiguous()
+    ng = torch.cat([d["n_gt"] for d in data]).view(-1, P, 3)[:batch].reshape(-1, 3).contiguous()
+    mg = torch.cat([d["m_gt"] for d in data]).view(-1, P)[:batch].reshape(-1).contiguous()
+    for _ in range(warmup):
+        net.train_step(x, dg, ng, mg, batch, W, W, 1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        loss = net.train_step(x, dg, ng, mg, batch, W, W, 1e-4)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flops = 3.0 * lt.forward_flops(widths, blocks, W, W) * batch
+    peak = 1708.8
+    try:
+        peak = float(json.load(open(MEASURED))["bf16_tflops_sustained"])
+    except (OSError, ValueError, KeyError):
+        pass
+    t = lt.time_paths(net, data[0]["sparse"], data[0]["dense"], data[0]["vs"])
+    return {"workload": f"U-Net widths 32-256, {W}^2 coarse depth, batch {batch}, BF16 "
+                        "activations, FP32 accumulation; pairs from the surfel tracer",
+            "train_ms_per_step": ms, "train_images_per_s": batch / (ms / 1e3),
+            "train_tflops": flops / (ms / 1e3) / 1e12,
+            "tensor_roofline": {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12,
+                                "peak": peak, "unit": "TFLOP/s",
+                                "frac": flops / (ms / 1e3) / 1e12 / peak,
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
+            "last_loss": float(loss.cpu()[0]),
+            "ms_per_view_learned_path": t["learned"] * 1e3,
+            "ms_per_view_plain_splatting": t["plain_splatting"] * 1e3}
+
+
 def cpu_baseline(wl):
     q, dt, npix, vpx = oracle_sample(wl)
     return {"value": q / dt, "unit": "ray-bounces/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -493,6 +543,7 @@ def main():
     ap.add_argument("--workload", default="sphere", choices=["sphere", "dihedral", "composite"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -511,6 +562,8 @@ def main():
     out = run_gpu(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_serving:
         out["serving"] = run_serving()
+    if rank == 0 and world == 1 and not args.no_learned:
+        out["learned"] = run_learned()
     if rank == 0 and not args.no_cpu_baseline:
         wl, _ = make_workload(args.workload)
         out["cpu_baseline"] = cpu_baseline(wl)

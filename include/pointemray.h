@@ -96,12 +96,21 @@ typedef struct {
  * and a conservative bounding-box pyramid per view (leaf tiles of 8x8 pixels,
  * each level 4x4 tiles of the one below) in that view's (u, v, d) frame.
  * A splat's id is its owner pixel's global index off_v + p.
- * Layout is fully determined by the views; use pe_geom_bytes() to size it. */
+ * The blob also holds a coarse 32^3 grid over the fusion bounding box: per
+ * cell, a bit mask of the views that own a splat whose (padded) sphere
+ * overlaps the cell, plus one mask of views with splats outside the grid;
+ * rays only descend the pyramids of views met along their path.
+ * Layout is fully determined by the views; use pe_geom_bytes() to size it.
+ * vgrid_* are written by pe_aggregate_views (callers leave them zero). */
+#define PE_VGRID 32
 typedef struct {
   int32_t n_views;
   pe_view views[PE_MAX_VIEWS];
   void *blob_dev;          /* caller-owned, pe_geom_bytes() bytes, 256-aligned */
   size_t blob_bytes;
+  float vgrid_min[3];      /* grid origin (metres); 0 cells = no grid */
+  float vgrid_cell;        /* cell edge (metres) */
+  int32_t vgrid_n;         /* cells per axis (PE_VGRID) or 0 */
 } pe_geom;
 
 /* Per-ray last-hit records (Alg. 3 hitRecord; Eq. 14 inputs), indexed by ray
@@ -129,7 +138,8 @@ typedef struct {
 
 /* Device counters of a trace (int64): [0] executed intersection queries
  * (primary GFB lookups + march queries, misses included), [1] shadow queries,
- * [2] splat tests, [3] pyramid node tests. */
+ * [2] exact ray/splat tests, [3] pyramid node tests, [4] view pyramids
+ * walked (after the coarse occupancy grid's culling). */
 #define PE_STATS_WORDS 8
 
 /* Library version of this header's ABI. */

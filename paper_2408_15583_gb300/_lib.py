@@ -32,7 +32,8 @@ class PeParams(C.Structure):
 
 class PeGeom(C.Structure):
     _fields_ = [("n_views", C.c_int32), ("views", PeView * PE_MAX_VIEWS),
-                ("blob_dev", C.c_void_p), ("blob_bytes", C.c_size_t)]
+                ("blob_dev", C.c_void_p), ("blob_bytes", C.c_size_t),
+                ("vgrid_min", C.c_float * 3), ("vgrid_cell", C.c_float), ("vgrid_n", C.c_int32)]
 
 
 class PeHits(C.Structure):

@@ -346,6 +346,37 @@ __global__ void pyramid_up_kernel(const __grid_constant__ pe_geom_layout L, int 
   }
 }
 
+// Coarse view-occupancy grid: every splat marks, with its owner view's bit,
+// the cells its sphere (padded for rounding) overlaps; splats reaching outside
+// the grid mark the extra word vmask[n^3].
+__global__ void vgrid_kernel(const __grid_constant__ pe_geom_layout L, uint32_t *__restrict__ vmask) {
+  const int n = L.vg_n;
+  const float cell = L.vg_cell;
+  const int64_t total = L.pix_off[L.nv];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    float4 c = L.cr[g];
+    if (!(c.w > 0.0f)) continue;
+    const int v = view_of(L, g);
+    const uint32_t bit = 1u << v;
+    const float pad = c.w * 1.00001f + 1e-3f * cell + L.pad[v];
+    const float cc[3] = {c.x, c.y, c.z};
+    int lo[3], hi[3];
+    bool outside = false;
+    for (int k = 0; k < 3; ++k) {
+      float a = floorf((cc[k] - pad - L.vg_min[k]) / cell);
+      float b = floorf((cc[k] + pad - L.vg_min[k]) / cell);
+      if (!(a >= 0.0f) || !(b <= (float)(n - 1))) outside = true;
+      lo[k] = (int)fminf(fmaxf(a, 0.0f), (float)(n - 1));
+      hi[k] = (int)fminf(fmaxf(b, 0.0f), (float)(n - 1));
+    }
+    if (outside) atomicOr(vmask + (int64_t)n * n * n, bit);
+    for (int x = lo[0]; x <= hi[0]; ++x)
+      for (int y = lo[1]; y <= hi[1]; ++y)
+        for (int z = lo[2]; z <= hi[2]; ++z) atomicOr(vmask + ((int64_t)x * n + y) * n + z, bit);
+  }
+}
+
 int grid_for(int64_t n, int threads, int cap) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -409,8 +440,8 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   for (int v = 0; v < n_views; ++v)
     if (memcmp(&out->views[v], &views[v], sizeof(pe_view)) != 0)
       return pe_fail(PE_EINVAL, "pe_aggregate_views: out->views differ from views");
-  size_t o_cr, o_nf, o_nodes, tot;
-  pe_layout_offsets(L, &o_cr, &o_nf, &o_nodes, &tot);
+  size_t o_cr, o_nf, o_nodes, o_vm, tot;
+  pe_layout_offsets(L, &o_cr, &o_nf, &o_nodes, &o_vm, &tot);
   if (out->blob_bytes < tot || !pe_aligned(out->blob_dev, 256))
     return pe_fail(PE_ENOMEM, "pe_aggregate_views: geometry blob needs %zu bytes", tot);
   size_t need = pe_aggregate_workspace(n_views, views, G);
@@ -421,9 +452,16 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   float4 *cr = reinterpret_cast<float4 *>(blob + o_cr);
   float4 *nf = reinterpret_cast<float4 *>(blob + o_nf);
   float4 *nodes = reinterpret_cast<float4 *>(blob + o_nodes);
+  uint32_t *vmask = reinterpret_cast<uint32_t *>(blob + o_vm);
   L.cr = cr;
   L.nf = nf;
   L.nodes = nodes;
+  // the coarse grid covers the fusion box with one spare cell on each side
+  const float ext = (float)((double)G / (double)prm->inv_voxel);
+  L.vg_n = PE_VGRID;
+  L.vg_cell = ext / (float)(PE_VGRID - 2);
+  for (int k = 0; k < 3; ++k) L.vg_min[k] = prm->bbox_min[k] - L.vg_cell;
+  L.vmask = vmask;
 
   int64_t total_pix = L.pix_off[n_views];
   int64_t nvox = (int64_t)G * G * G;
@@ -455,6 +493,12 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   fuse_segment_kernel<<<grid_for(total_pix, 128, cap), 128, 0, s>>>(L, nd, w.entries, w.offs,
                                                                      nvox, cr, nf);
   PE_TRY_LAUNCH("fuse_segment_kernel");
+  PE_TRY_CUDA(cudaMemsetAsync(vmask, 0, sizeof(uint32_t) * ((size_t)PE_VGRID * PE_VGRID * PE_VGRID + 1), s));
+  vgrid_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, vmask);
+  PE_TRY_LAUNCH("vgrid_kernel");
+  out->vgrid_n = L.vg_n;
+  out->vgrid_cell = L.vg_cell;
+  for (int k = 0; k < 3; ++k) out->vgrid_min[k] = L.vg_min[k];
   for (int v = 0; v < n_views; ++v) {
     pyramid_leaf_kernel<<<grid_for((int64_t)L.tw[v][0] * L.th[v][0], 128, cap), 128, 0, s>>>(
         L, v, nodes);

@@ -158,7 +158,7 @@ bool pe_make_layout(int32_t nv, const pe_view *views, pe_geom_layout *L) {
 }
 
 void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
-                       size_t *off_nodes, size_t *total) {
+                       size_t *off_nodes, size_t *off_vmask, size_t *total) {
   pe_carve c{nullptr, 0};
   int64_t np = L.pix_off[L.nv];
   c.take<float4>((size_t)np);
@@ -169,13 +169,16 @@ void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
   size_t b = c.bytes();
   c.take<float4>((size_t)L.n_nodes * 2);
   *off_nodes = b;
+  size_t d = c.bytes();
+  c.take<uint32_t>((size_t)PE_VGRID * PE_VGRID * PE_VGRID + 1);
+  *off_vmask = d;
   *total = c.bytes();
 }
 
 extern "C" size_t pe_geom_bytes(int32_t n_views, const pe_view *views) {
   pe_geom_layout L;
   if (!pe_make_layout(n_views, views, &L)) return 0;
-  size_t a, b, c, t;
-  pe_layout_offsets(L, &a, &b, &c, &t);
+  size_t a, b, c, d, t;
+  pe_layout_offsets(L, &a, &b, &c, &d, &t);
   return t;
 }

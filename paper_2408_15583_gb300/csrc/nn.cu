@@ -127,7 +127,7 @@ template <bool AK, bool BK>
 __global__ void __launch_bounds__(128) gemm_kernel(const gemm_args g) {
   __shared__ __align__(16) bf16 As[GB][GPAD];
   __shared__ __align__(16) bf16 Bs[GB][GPAD];
-  const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+  const int m0 = blockIdx.x * GB, n0 = blockIdx.y * GB;
   const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
   int64_t ke = kb + g.k_per_split;
   if (ke > g.K) ke = g.K;
@@ -786,8 +786,8 @@ extern "C" pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, 
     if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_gemm: workspace needs %zu", need);
     g.part = static_cast<float *>(ws);
   }
-  if ((M + GB - 1) / GB > 65535) return pe_fail(PE_EINVAL, "pe_nn_gemm: M too large");
-  dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB, (unsigned)split);
+  if ((N + GB - 1) / GB > 65535) return pe_fail(PE_EINVAL, "pe_nn_gemm: N too large");
+  dim3 grid((M + GB - 1) / GB, (N + GB - 1) / GB, (unsigned)split);
   if (ak && bk) gemm_kernel<true, true><<<grid, 128, 0, s>>>(g);
   else if (ak && !bk) gemm_kernel<true, false><<<grid, 128, 0, s>>>(g);
   else if (!ak && bk) gemm_kernel<false, true><<<grid, 128, 0, s>>>(g);

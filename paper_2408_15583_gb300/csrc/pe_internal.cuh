@@ -10,7 +10,7 @@
 #include "pointemray.h"
 
 #define PE_MAX_LEVELS 12
-#define PE_LEAF 8          // leaf tile edge in pixels
+#define PE_LEAF 4          // leaf tile edge in pixels
 #ifndef PE_FAN
 #define PE_FAN 2           // tiles per pyramid level edge
 #endif
@@ -87,13 +87,19 @@ struct pe_geom_layout {
   const float4 *cr;         // splat centre, radius
   const float4 *nf;         // splat normal, count
   const float4 *nodes;      // [n_nodes][2] lo, hi in (u, v, d) frame
+  // coarse view-occupancy grid: vmask[(ix*n + iy)*n + iz], vmask[n^3] = views
+  // with splats outside the grid; n = 0: no grid (walk every view)
+  const uint32_t *vmask;
+  float vg_min[3];
+  float vg_cell;
+  int32_t vg_n;
 };
 
 // Fills everything but the pointers; returns false on bad views.
 bool pe_make_layout(int32_t nv, const pe_view *views, pe_geom_layout *L);
-// Blob byte offsets of the three arrays for a layout.
+// Blob byte offsets of the arrays for a layout.
 void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
-                       size_t *off_nodes, size_t *total);
+                       size_t *off_nodes, size_t *off_vmask, size_t *total);
 
 // ---------------------------------------------------------------------------
 // Launchers shared between entry points

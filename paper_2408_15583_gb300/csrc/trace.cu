@@ -88,6 +88,62 @@ __device__ __forceinline__ void note_hit(qstate &S, float t, uint32_t id, float 
   }
 }
 
+// Views owning splats along the ray (t > tmin), from the coarse occupancy
+// grid by a 3D DDA; all views when there is no grid.  The splats were marked
+// in every cell their padded sphere overlaps, so a cell the ray crosses
+// carries the bit of every splat it can hit there.
+__device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin) {
+  const int n = L.vg_n;
+  if (n == 0) return 0xffffffffu;
+  uint32_t m = __ldg(L.vmask + (int64_t)n * n * n);
+  const float cell = L.vg_cell;
+  const float oo[3] = {o.x - L.vg_min[0], o.y - L.vg_min[1], o.z - L.vg_min[2]};
+  const float dd[3] = {d.x, d.y, d.z};
+  const float size = cell * n;
+  float t0 = tmin - 1e-3f * cell, t1 = INFINITY;
+  float inv[3];
+  for (int k = 0; k < 3; ++k) {
+    inv[k] = 1.0f / dd[k];
+    float a = (0.0f - oo[k]) * inv[k], b = (size - oo[k]) * inv[k];
+    if (dd[k] == 0.0f) {
+      if (oo[k] < 0.0f || oo[k] > size) return m;
+      continue;
+    }
+    t0 = fmaxf(t0, fminf(a, b));
+    t1 = fminf(t1, fmaxf(a, b));
+  }
+  if (!(t0 <= t1)) return m;
+  int ix[3], st[3];
+  float tmax[3], tdel[3];
+  for (int k = 0; k < 3; ++k) {
+    float p = oo[k] + t0 * dd[k];
+    int c = (int)floorf(p / cell);
+    ix[k] = c < 0 ? 0 : (c > n - 1 ? n - 1 : c);
+    if (dd[k] > 0.0f) {
+      st[k] = 1;
+      tmax[k] = ((ix[k] + 1) * cell - oo[k]) * inv[k];
+      tdel[k] = cell * inv[k];
+    } else if (dd[k] < 0.0f) {
+      st[k] = -1;
+      tmax[k] = (ix[k] * cell - oo[k]) * inv[k];
+      tdel[k] = -cell * inv[k];
+    } else {
+      st[k] = 0;
+      tmax[k] = INFINITY;
+      tdel[k] = INFINITY;
+    }
+  }
+  for (int it = 0; it < 3 * n + 3; ++it) {
+    m |= __ldg(L.vmask + ((int64_t)ix[0] * n + ix[1]) * n + ix[2]);
+    int k = tmax[0] < tmax[1] ? (tmax[0] < tmax[2] ? 0 : 2) : (tmax[1] < tmax[2] ? 1 : 2);
+    if (tmax[k] > t1) break;
+    ix[k] += st[k];
+    if (ix[k] < 0 || ix[k] >= n) break;
+    tmax[k] += tdel[k];
+  }
+  return m;
+}
+
 // Walk every view's pyramid with the whole warp (packet traversal).  The 32
 // rays of a warp are neighbours on the ray screen, so they need nearly the
 // same nodes: the warp descends the union of the nodes any active lane's
@@ -100,10 +156,13 @@ __device__ __forceinline__ void note_hit(qstate &S, float t, uint32_t id, float 
 template <bool ANY>
 __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
                      bool active, qstate &S, bool &hit_any, unsigned int *err,
-                     long long &n_splat, long long &n_node) {
+                     long long &n_splat, long long &n_node, long long &n_view) {
   static_assert(PE_FAN == 2, "the register-resident traversal assumes a 2x2 fan-out");
   const unsigned FULL = 0xffffffffu;
+  const uint32_t vm = __reduce_or_sync(FULL, active ? view_mask(L, o, d, tmin) : 0u);
+  if (active) n_view += __popc(vm & ((L.nv >= 32) ? 0xffffffffu : ((1u << L.nv) - 1u)));
   for (int v = 0; v < L.nv; ++v) {
+    if (!((vm >> v) & 1u)) continue;
     bool live = active && !(ANY && hit_any);
     if (!__any_sync(FULL, live)) return;
     const pe_view &V = L.view[v];
@@ -245,13 +304,13 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
 // Every lane of the warp must call this together (inactive lanes: active=0).
 __device__ bool nearest(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
                         bool active, unsigned int *err, pe_f3 &xo, pe_f3 &no, uint32_t &ido,
-                        long long &n_splat, long long &n_node) {
+                        long long &n_splat, long long &n_node, long long &n_view) {
   qstate S;
   S.tb = INFINITY;
   S.ib = PE_NONE;
   S.nc = 0;
   bool unused = false;
-  walk<false>(L, o, d, tmin, r_ov, active, S, unused, err, n_splat, n_node);
+  walk<false>(L, o, d, tmin, r_ov, active, S, unused, err, n_splat, n_node, n_view);
   if (!active || S.ib == PE_NONE) return false;
   float lim = pe_add(S.tb, r_ov);
   int k = 0;
@@ -336,20 +395,15 @@ __device__ __forceinline__ void warp_append(bool keep, uint32_t slot, uint32_t *
 }
 
 __device__ __forceinline__ void flush_stats(long long *stats, long long a, long long b,
-                                            long long c, long long d) {
+                                            long long c, long long d, long long e) {
   if (!stats) return;
+  long long v[5] = {a, b, c, d, e};
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
-    d += __shfl_down_sync(0xffffffffu, d, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (a) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 0), (unsigned long long)a);
-    if (b) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 1), (unsigned long long)b);
-    if (c) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 2), (unsigned long long)c);
-    if (d) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 3), (unsigned long long)d);
+  for (int k = 0; k < 5; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if ((threadIdx.x & 31) == 0 && v[k])
+      atomicAdd(reinterpret_cast<unsigned long long *>(stats + k), (unsigned long long)v[k]);
   }
 }
 
@@ -384,7 +438,7 @@ __global__ void __launch_bounds__(kTraceThreads)
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
   const tile_map tm = make_tile_map(W, H, A.vb.n);
-  long long nq = 0, ns = 0, nn = 0;
+  long long nq = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
     int64_t t = base + threadIdx.x;
@@ -402,7 +456,7 @@ __global__ void __launch_bounds__(kTraceThreads)
     uint32_t id = PE_NONE;
     nq += active;
     if (geom_first) {
-      hit = nearest(A.L, o, d, 0.0f, A.r_ov, active, A.err, x, n, id, ns, nn);
+      hit = nearest(A.L, o, d, 0.0f, A.r_ov, active, A.err, x, n, id, ns, nn, nv);
     } else if (active) {
       unsigned long long key = A.keys[slot];
       if (key != ~0ull) {
@@ -429,14 +483,14 @@ __global__ void __launch_bounds__(kTraceThreads)
     bool live = active && hit && A.mb >= 2;
     if (A.q_out) warp_append(live, (uint32_t)slot, A.q_out, A.n_out);
   }
-  flush_stats(A.stats, nq, 0, ns, nn);
+  flush_stats(A.stats, nq, 0, ns, nn, nv);
 }
 
 // One bounce (b >= 2) for the rays of q_in (queue order keeps warps coherent).
 __global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_constant__ march_args A) {
   const uint32_t n_in = *A.n_in;
   const int64_t n_rays = A.h.n_rays;
-  long long nq = 0, ns = 0, nn = 0;
+  long long nq = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_in;
        base += (int64_t)gridDim.x * blockDim.x) {
     int64_t qi = base + threadIdx.x;
@@ -459,7 +513,7 @@ __global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_const
     pe_f3 x, n2;
     uint32_t id;
     nq += active;
-    bool hit = nearest(A.L, p, d, A.eps, A.r_ov, active, A.err, x, n2, id, ns, nn);
+    bool hit = nearest(A.L, p, d, A.eps, A.r_ov, active, A.err, x, n2, id, ns, nn, nv);
     bool live = false;
     if (hit) {
       A.h.path[slot] = __dadd_rn(A.h.path[slot], seg_len(p, x));
@@ -474,7 +528,7 @@ __global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_const
     }
     if (A.q_out) warp_append(live, slot, A.q_out, A.n_out);
   }
-  flush_stats(A.stats, nq, 0, ns, nn);
+  flush_stats(A.stats, nq, 0, ns, nn, nv);
 }
 
 // Psi: shadow ray from the last hit toward the receiver (monostatic: w).
@@ -482,7 +536,7 @@ __global__ void __launch_bounds__(kTraceThreads) shadow_kernel(const __grid_cons
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
   const tile_map tm = make_tile_map(W, H, A.vb.n);
-  long long nsh = 0, ns = 0, nn = 0;
+  long long nsh = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
     int64_t t = base + threadIdx.x;
@@ -501,10 +555,10 @@ __global__ void __launch_bounds__(kTraceThreads) shadow_kernel(const __grid_cons
     S.nc = 0;
     nsh += active;
     bool blocked = false;
-    walk<true>(A.L, p, w, A.eps, A.r_ov, active, S, blocked, A.err, ns, nn);
+    walk<true>(A.L, p, w, A.eps, A.r_ov, active, S, blocked, A.err, ns, nn, nv);
     if (active) A.h.psi[slot] = blocked ? 0 : 1;
   }
-  flush_stats(A.stats, 0, nsh, ns, nn);
+  flush_stats(A.stats, 0, nsh, ns, nn, nv);
 }
 
 int sms() {
@@ -528,13 +582,21 @@ int grid_for(int64_t n) {
 bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
   if (!g || !g->blob_dev) return false;
   if (!pe_make_layout(g->n_views, g->views, L)) return false;
-  size_t a, b, c, t;
-  pe_layout_offsets(*L, &a, &b, &c, &t);
+  size_t a, b, c, d, t;
+  pe_layout_offsets(*L, &a, &b, &c, &d, &t);
   if (g->blob_bytes < t) return false;
   char *blob = static_cast<char *>(g->blob_dev);
   L->cr = reinterpret_cast<const float4 *>(blob + a);
   L->nf = reinterpret_cast<const float4 *>(blob + b);
   L->nodes = reinterpret_cast<const float4 *>(blob + c);
+  L->vmask = reinterpret_cast<const uint32_t *>(blob + d);
+  if (g->vgrid_n == PE_VGRID && g->vgrid_cell > 0.0f) {
+    L->vg_n = g->vgrid_n;
+    L->vg_cell = g->vgrid_cell;
+    for (int k = 0; k < 3; ++k) L->vg_min[k] = g->vgrid_min[k];
+  } else {
+    L->vg_n = 0;      // no grid: every view is walked
+  }
   return true;
 }
 

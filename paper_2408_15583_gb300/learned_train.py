@@ -84,7 +84,7 @@ def make_pairs(sparse, dense, vs: ViewSet, delta_px: float, device="cuda:0"):
 
 
 def dataset(n_scenes: int, views_per_scene: int, W: int, seed: int, device="cuda:0",
-            dense_density=200.0):
+            dense_density=200.0, keep_scenes=False):
     import scenes
     out = []
     for k in range(n_scenes):
@@ -93,8 +93,31 @@ def dataset(n_scenes: int, views_per_scene: int, W: int, seed: int, device="cuda
         sparse = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0)
         dense = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0, density=dense_density)
         vs = view_set(sparse, views_per_scene, W, sd + 1)
-        out.append(make_pairs(sparse, dense, vs, float(rng.uniform(1.0, 3.0)), device))
+        item = make_pairs(sparse, dense, vs, float(rng.uniform(1.0, 3.0)), device)
+        if keep_scenes:
+            item["sparse"], item["dense"] = sparse, dense
+        out.append(item)
     return out
+
+
+def forward_flops(widths, blocks, H, W):
+    """FP ops of one forward pass on an H x W image (multiply-add = 2)."""
+    f = 0.0
+    c = widths
+    L = len(widths)
+    px = [H * W / 4 ** l for l in range(L)]
+    f += 2 * px[0] * 9 * 1 * c[0]                              # stem
+    blk = lambda p, ch: 2 * p * (49 * ch + 8 * ch * ch)        # dw 7x7 + two 1x1
+    for l in range(L):
+        if l > 0:
+            f += 2 * px[l] * c[l - 1] * c[l]
+        f += blocks[l] * blk(px[l], c[l])
+    for nout in (1, 3, 1):
+        for l in range(L - 2, -1, -1):
+            f += 2 * px[l + 1] * 9 * c[l + 1] * 4 * c[l]          # up 3x3
+            f += 2 * px[l] * 2 * c[l] * c[l] + blk(px[l], c[l])  # fuse + block
+        f += 2 * px[0] * c[0] * nout
+    return f
 
 
 def _cat(items, key):

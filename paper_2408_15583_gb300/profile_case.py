@@ -59,7 +59,7 @@ def main(argv):
     api.stream_check()
     st = stats.cpu().numpy()
     print(f"{case}: {dt * 1e3:.2f} ms per call; batch queries {st[0]} shadow {st[1]} "
-          f"exact splat tests {st[2]} node tests {st[3]}")
+          f"exact splat tests {st[2]} node tests {st[3]} views walked {st[4]}")
 
 
 if __name__ == "__main__":
