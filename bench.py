@@ -281,12 +281,12 @@ MARCH_BYTES_PER_QUERY = 152
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 646.6 MB
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 723.6 MB
 # over 6,332,964 queries), valid only for the sources it was taken on (their
 # SHA-256 prefixes); scaled to a full launch by the number of queries.
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 102.1,
-                     "sources": {"paper_2408_15583_gb300/csrc/trace.cu": "0c7a4eaec796f98e",
-                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "8388fdd29e24e928"}}
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 114.3,
+                     "sources": {"paper_2408_15583_gb300/csrc/trace.cu": "42445b23eaf994d5",
+                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "e5600a88c6aa3647"}}
 
 
 def _traffic_valid(rec):
