@@ -138,8 +138,10 @@ typedef struct {
 
 /* Device counters of a trace (int64): [0] executed intersection queries
  * (primary GFB lookups + march queries, misses included), [1] shadow queries,
- * [2] exact ray/splat tests, [3] pyramid node tests, [4] view pyramids
- * walked (after the coarse occupancy grid's culling). */
+ * [2] exact ray/splat tests, [3] pyramid node tests, [4] views whose
+ * splats lie along the query's ray per the coarse occupancy grid (the
+ * pyramids its walk searches, each over the stretch of the ray crossing
+ * that view's occupied cells). */
 #define PE_STATS_WORDS 8
 
 /* Library version of this header's ABI. */

@@ -284,6 +284,9 @@ __global__ void fuse_segment_kernel(const __grid_constant__ pe_geom_layout L,
 
 // Leaf boxes: bounds of the owned splats' spheres in the view's (u, v, d)
 // frame, padded for rounding.  Empty tiles get lo = +inf, hi = -inf.
+// Leaf boxes; a leaf's lo.w holds the bit pattern of its occupancy mask
+// (bit jj * PE_LEAF + ii set when slot (ii, jj) holds a splat).
+static_assert(PE_LEAF * PE_LEAF <= 32, "leaf occupancy mask is one 32-bit word");
 __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, int v,
                                     float4 *__restrict__ nodes) {
   const pe_view &V = L.view[v];
@@ -293,6 +296,7 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tw * th; t += gridDim.x * blockDim.x) {
     int tx = t % tw, ty = t / tw;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    uint32_t occ = 0;
     for (int jj = 0; jj < PE_LEAF; ++jj) {
       int j = ty * PE_LEAF + jj;
       if (j >= V.H) break;
@@ -301,6 +305,7 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
         if (i >= V.W) break;
         float4 c = cr[(int64_t)j * V.W + i];
         if (!(c.w > 0.0f)) continue;
+        occ |= 1u << (jj * PE_LEAF + ii);
         float qx = c.x - V.o[0], qy = c.y - V.o[1], qz = c.z - V.o[2];
         float a[3] = {qx * V.u[0] + qy * V.u[1] + qz * V.u[2],
                       qx * V.v[0] + qy * V.v[1] + qz * V.v[2],
@@ -314,7 +319,7 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
       }
     }
     int64_t nid = L.node_off[v][0] + t;
-    nodes[2 * nid] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    nodes[2 * nid] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(occ));
     nodes[2 * nid + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
   }
 }
@@ -359,7 +364,7 @@ __global__ void vgrid_kernel(const __grid_constant__ pe_geom_layout L, uint32_t 
     if (!(c.w > 0.0f)) continue;
     const int v = view_of(L, g);
     const uint32_t bit = 1u << v;
-    const float pad = c.w * 1.00001f + 1e-3f * cell + L.pad[v];
+    const float pad = c.w * 1.00001f + 1e-2f * cell + L.pad[v];
     const float cc[3] = {c.x, c.y, c.z};
     int lo[3], hi[3];
     bool outside = false;

@@ -2,9 +2,11 @@
 //
 // Rays march through the aggregated splats of every view.  Each splat lives
 // at its owner pixel of one view, and every view keeps a pyramid of
-// conservative bounding boxes in its own (u, v, d) frame (8x8-pixel leaves,
-// 4x4 fan-out).  A query descends each view's pyramid with the box test
-// limited to t <= t_best + r, tests the splats of the leaves it reaches with
+// conservative bounding boxes in its own (u, v, d) frame (4x4-pixel leaves,
+// 2x2 fan-out).  A coarse 3D occupancy grid gives each query the views whose
+// splats lie along it and, per view, the stretch of the ray that passes
+// through their cells.  A query descends each of those views' pyramids with
+// the box test limited to that stretch and to t <= t_best + r, tests the splats of the leaves it reaches with
 // the exact float32 ray/disk test, and finally applies Eq. 23 to the
 // candidates within r of the nearest hit.  Because the boxes only cull and
 // the candidate set and its selection do not depend on visiting order, the
@@ -39,8 +41,10 @@ struct march_args {
   long long *stats;
 };
 
+// A ray in a view's (u, v, d) frame: reciprocal direction and -origin/dir,
+// so a slab bound is one FMA.
 struct vray {
-  float ox, oy, oz, ix, iy, iz;
+  float ix, iy, iz, nx, ny, nz;
 };
 
 struct qstate {
@@ -53,9 +57,9 @@ struct qstate {
 
 __device__ __forceinline__ bool box_hit(float4 lo, float4 hi, const vray &r, float t0, float t1) {
   if (lo.x > hi.x) return false;
-  float ax = (lo.x - r.ox) * r.ix, bx = (hi.x - r.ox) * r.ix;
-  float ay = (lo.y - r.oy) * r.iy, by = (hi.y - r.oy) * r.iy;
-  float az = (lo.z - r.oz) * r.iz, bz = (hi.z - r.oz) * r.iz;
+  float ax = fmaf(lo.x, r.ix, r.nx), bx = fmaf(hi.x, r.ix, r.nx);
+  float ay = fmaf(lo.y, r.iy, r.ny), by = fmaf(hi.y, r.iy, r.ny);
+  float az = fmaf(lo.z, r.iz, r.nz), bz = fmaf(hi.z, r.iz, r.nz);
   float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), t0));
   float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), t1));
   return tn <= tf;
@@ -91,11 +95,23 @@ __device__ __forceinline__ void note_hit(qstate &S, float t, uint32_t id, float 
 // Views owning splats along the ray (t > tmin), from the coarse occupancy
 // grid by a 3D DDA; all views when there is no grid.  The splats were marked
 // in every cell their padded sphere overlaps, so a cell the ray crosses
-// carries the bit of every splat it can hit there.
-__device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin) {
+// carries the bit of every splat it can hit there.  Per view, tv[v] gets the
+// ray-parameter interval from the entry of the first to the exit of the last
+// cell carrying its bit (unbounded for views marked outside the grid, empty
+// for views not crossed): a hit on that view's splats lies inside it, since
+// the points of the ray within the marking pad of the hit point all lie in
+// marked cells.  tv is indexed [v * stride].
+__device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float2 *tv,
+                              int stride) {
   const int n = L.vg_n;
-  if (n == 0) return 0xffffffffu;
-  uint32_t m = __ldg(L.vmask + (int64_t)n * n * n);
+  for (int v = 0; v < L.nv; ++v) tv[v * stride] = make_float2(INFINITY, -INFINITY);
+  if (n == 0) {
+    for (int v = 0; v < L.nv; ++v) tv[v * stride] = make_float2(-INFINITY, INFINITY);
+    return 0xffffffffu;
+  }
+  const uint32_t outside = __ldg(L.vmask + (int64_t)n * n * n);
+  for (uint32_t b = outside; b; b &= b - 1) tv[(__ffs(b) - 1) * stride] = make_float2(-INFINITY, INFINITY);
+  uint32_t m = outside;
   const float cell = L.vg_cell;
   const float oo[3] = {o.x - L.vg_min[0], o.y - L.vg_min[1], o.z - L.vg_min[2]};
   const float dd[3] = {d.x, d.y, d.z};
@@ -133,14 +149,33 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
       tdel[k] = INFINITY;
     }
   }
+  float t_in = t0;
+  bool ended = false;
   for (int it = 0; it < 3 * n + 3; ++it) {
-    m |= __ldg(L.vmask + ((int64_t)ix[0] * n + ix[1]) * n + ix[2]);
-    int k = tmax[0] < tmax[1] ? (tmax[0] < tmax[2] ? 0 : 2) : (tmax[1] < tmax[2] ? 1 : 2);
-    if (tmax[k] > t1) break;
+    const int k = tmax[0] < tmax[1] ? (tmax[0] < tmax[2] ? 0 : 2) : (tmax[1] < tmax[2] ? 1 : 2);
+    const float t_out = tmax[k];
+    const uint32_t b = __ldg(L.vmask + ((int64_t)ix[0] * n + ix[1]) * n + ix[2]) & ~outside;
+    for (uint32_t r = b; r; r &= r - 1) {
+      const int v = __ffs(r) - 1;
+      float2 &T = tv[v * stride];
+      if (!((m >> v) & 1u)) T.x = t_in;
+      T.y = t_out;
+    }
+    m |= b;
+    if (t_out > t1) {
+      ended = true;
+      break;
+    }
     ix[k] += st[k];
-    if (ix[k] < 0 || ix[k] >= n) break;
+    if (ix[k] < 0 || ix[k] >= n) {
+      ended = true;
+      break;
+    }
     tmax[k] += tdel[k];
+    t_in = t_out;
   }
+  if (!ended)  // cannot happen for a line through an n^3 grid; stay conservative
+    for (uint32_t r = m; r; r &= r - 1) tv[(__ffs(r) - 1) * stride].y = INFINITY;
   return m;
 }
 
@@ -153,34 +188,48 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
 // order-independent), so hits stay bit-exact.  Per-level child masks replace
 // a stack.  ANY: a lane stops at its first hit with t > tmin (shadow rays).
 // Every lane of the warp must call this together.
+// The walk of view v is limited to the lane's interval tv[v] from the grid,
+// widened by a slack far above the rounding of both parameterisations.
+// `tv` is the block's dynamic shared memory, L.nv x blockDim.x entries.
 template <bool ANY>
 __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, float r_ov,
                      bool active, qstate &S, bool &hit_any, unsigned int *err,
                      long long &n_splat, long long &n_node, long long &n_view) {
   static_assert(PE_FAN == 2, "the register-resident traversal assumes a 2x2 fan-out");
   const unsigned FULL = 0xffffffffu;
-  const uint32_t vm = __reduce_or_sync(FULL, active ? view_mask(L, o, d, tmin) : 0u);
-  if (active) n_view += __popc(vm & ((L.nv >= 32) ? 0xffffffffu : ((1u << L.nv) - 1u)));
+  extern __shared__ float2 tv_all[];
+  float2 *tv = tv_all + threadIdx.x;
+  const int stride = blockDim.x;
+  const uint32_t mine = active ? view_mask(L, o, d, tmin, tv, stride) : 0u;
+  const uint32_t vm = __reduce_or_sync(FULL, mine);
+  const uint32_t all_views = (L.nv >= 32) ? 0xffffffffu : ((1u << L.nv) - 1u);
+  if (active) n_view += __popc(mine & all_views);
+  const float t_slack = L.vg_n ? 1e-2f * L.vg_cell : 0.0f;
   for (int v = 0; v < L.nv; ++v) {
     if (!((vm >> v) & 1u)) continue;
     bool live = active && !(ANY && hit_any);
     if (!__any_sync(FULL, live)) return;
     const pe_view &V = L.view[v];
     const float pad = L.pad[v];
+    float2 T = active ? tv[v * stride] : make_float2(INFINITY, -INFINITY);
+    T.x = T.x - (t_slack + 1e-5f * fminf(fabsf(T.x), 1e30f));  // infinities stay
+    T.y = T.y + (t_slack + 1e-5f * fminf(fabsf(T.y), 1e30f));
     pe_f3 q = {o.x - V.o[0], o.y - V.o[1], o.z - V.o[2]};
+    // (the FMA slab form moves a face by ~1e-7 |origin|, far inside the
+    // boxes' padding of 1e-5 of the view's span)
     vray r;
-    r.ox = q.x * V.u[0] + q.y * V.u[1] + q.z * V.u[2];
-    r.oy = q.x * V.v[0] + q.y * V.v[1] + q.z * V.v[2];
-    r.oz = q.x * V.d[0] + q.y * V.d[1] + q.z * V.d[2];
     r.ix = 1.0f / (d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2]);
     r.iy = 1.0f / (d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2]);
     r.iz = 1.0f / (d.x * V.d[0] + d.y * V.d[1] + d.z * V.d[2]);
-    const float t0 = tmin - pad - 1e-6f * fabsf(tmin);
+    r.nx = -(q.x * V.u[0] + q.y * V.u[1] + q.z * V.u[2]) * r.ix;
+    r.ny = -(q.x * V.v[0] + q.y * V.v[1] + q.z * V.v[2]) * r.iy;
+    r.nz = -(q.x * V.d[0] + q.y * V.d[1] + q.z * V.d[2]) * r.iz;
+    const float t0 = fmaxf(tmin - pad - 1e-6f * fabsf(tmin), T.x);
     const int top = L.nlev[v] - 1;
     const int64_t poff = L.pix_off[v];
     auto t_far = [&]() -> float {
       float lim = pe_add(S.tb, r_ov);
-      return ANY ? INFINITY : fmaf(fabsf(lim), 1e-6f, lim) + pad;
+      return ANY ? T.y : fminf(fmaf(fabsf(lim), 1e-6f, lim) + pad, T.y);
     };
     // root
     {
@@ -251,29 +300,29 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
         leaf_x = cx;
         leaf_y = cy;
       }
-      // leaf tile: test its splats.  A conservative pre-test in plain float
+      // leaf tile: test its splats (the occupied slots of the leaf's mask).
+      // A conservative pre-test in plain float
       // arithmetic (distance of the centre to the ray line <= R, and the hit
       // parameter window [tc - R, tc + R] reaching (tmin, t_best + r]) skips
       // the exact test for splats no lane can hit; its slack covers the
       // rounding of both tests, so it never drops a hit the exact test takes.
       const int tx = leaf_x, ty = leaf_y;
       bool lv = active && !(ANY && hit_any);
-      for (int jj = 0; jj < PE_LEAF; ++jj) {
-        int j = ty * PE_LEAF + jj;
-        if (j >= V.H) break;
-        for (int ii = 0; ii < PE_LEAF; ++ii) {
-          int i = tx * PE_LEAF + ii;
-          if (i >= V.W) break;
+      const int64_t leaf = L.node_off[v][0] + (int64_t)ty * L.tw[v][0] + tx;
+      for (uint32_t occ = __float_as_uint(__ldg(&L.nodes[2 * leaf].w)); occ; occ &= occ - 1) {
+        const int b = __ffs(occ) - 1;
+        const int i = tx * PE_LEAF + b % PE_LEAF, j = ty * PE_LEAF + b / PE_LEAF;
+        {
           int64_t g = poff + (int64_t)j * V.W + i;
           float4 c = __ldg(L.cr + g);
-          if (!(c.w > 0.0f)) continue;
           float qx = c.x - o.x, qy = c.y - o.y, qz = c.z - o.z;
           float tc = qx * d.x + qy * d.y + qz * d.z;
           float qq = qx * qx + qy * qy + qz * qz;
           float ll = qq - tc * tc;
           float Rs = c.w * 1.0001f + 1e-3f * pad;
           float sl = 1e-5f * (fabsf(tc) + c.w) + pad;
-          bool pass = lv && ll <= Rs * Rs + 1e-6f * qq && tc + Rs + sl > tmin;
+          bool pass = lv && ll <= Rs * Rs + 1e-6f * qq && tc + Rs + sl > tmin &&
+                      tc + Rs + sl >= T.x && tc - Rs - sl <= T.y;
           if (!ANY) {
             float lim = pe_add(S.tb, r_ov);
             pass = pass && tc - Rs - sl <= fmaf(fabsf(lim), 1e-6f, lim);
@@ -487,7 +536,7 @@ __global__ void __launch_bounds__(kTraceThreads)
 }
 
 // One bounce (b >= 2) for the rays of q_in (queue order keeps warps coherent).
-__global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_constant__ march_args A) {
+__global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_constant__ march_args A) {
   const uint32_t n_in = *A.n_in;
   const int64_t n_rays = A.h.n_rays;
   long long nq = 0, ns = 0, nn = 0, nv = 0;
@@ -532,7 +581,7 @@ __global__ void __launch_bounds__(kTraceThreads) march_kernel(const __grid_const
 }
 
 // Psi: shadow ray from the last hit toward the receiver (monostatic: w).
-__global__ void __launch_bounds__(kTraceThreads) shadow_kernel(const __grid_constant__ march_args A) {
+__global__ void __launch_bounds__(kTraceThreads, 8) shadow_kernel(const __grid_constant__ march_args A) {
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
   const tile_map tm = make_tile_map(W, H, A.vb.n);
@@ -645,8 +694,10 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   A.n_out = na;
   A.bounce = 1;
   const int64_t n_thr = make_tile_map(vb.W, vb.H, vb.n).n_threads;
+  // per-lane ray intervals of every view (walk's shared memory)
+  const size_t tv_bytes = have_geom ? (size_t)A.L.nv * kTraceThreads * sizeof(float2) : 0;
   pe_event_before("primary_kernel", s);
-  primary_kernel<<<grid_for(n_thr), kTraceThreads, 0, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
+  primary_kernel<<<grid_for(n_thr), kTraceThreads, tv_bytes, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
   pe_event_after("primary_kernel", s);
   PE_TRY_LAUNCH("primary_kernel");
   for (int b = 2; b <= mb; ++b) {
@@ -657,7 +708,7 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
     A.n_out = nb;
     PE_TRY_CUDA(cudaMemsetAsync(nb, 0, sizeof(uint32_t), s));
     pe_event_before("march_kernel", s);
-    march_kernel<<<grid_for(n_rays), kTraceThreads, 0, s>>>(A);
+    march_kernel<<<grid_for(n_rays), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("march_kernel", s);
     PE_TRY_LAUNCH("march_kernel");
     uint32_t *t = qa;
@@ -669,7 +720,7 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   }
   if (mb >= 2) {
     pe_event_before("shadow_kernel", s);
-    shadow_kernel<<<grid_for(n_thr), kTraceThreads, 0, s>>>(A);
+    shadow_kernel<<<grid_for(n_thr), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("shadow_kernel", s);
     PE_TRY_LAUNCH("shadow_kernel");
   }

@@ -1,13 +1,15 @@
 """Small, representative cases of the hot kernels for profiling (ncu).
 
-    python -m paper_2408_15583_gb300.profile_case march [reps]   # one traced batch
-    python -m paper_2408_15583_gb300.profile_case po [reps]      # PO over that batch
-    python -m paper_2408_15583_gb300.profile_case splat [reps]   # incidence splats
+    python -m paper_2408_15583_gb300.profile_case march [reps] [workload]  # one traced batch
+    python -m paper_2408_15583_gb300.profile_case po [reps] [workload]     # PO over that batch
+    python -m paper_2408_15583_gb300.profile_case splat [reps] [workload]  # incidence splats
 
-Each case is the sphere workload's geometry (200k points, 8 fused 512^2
-views) with one batch of 8 incidence angles at 1024^2 rays and 64
+By default each case is the sphere workload's geometry (200k points, 8 fused
+512^2 views) with one batch of 8 incidence angles at 1024^2 rays and 64
 frequencies: a few GB on the device, inputs larger than L2, a handful of
-launches -- small enough for a full ncu capture of one launch.
+launches -- small enough for a full ncu capture of one launch.  `workload`
+= dihedral or composite takes that workload's scene, screen and bounce
+count instead (for timing; the composite batch holds ~3 GB of ray records).
 """
 from __future__ import annotations
 
@@ -29,7 +31,9 @@ def main(argv):
     build()
     case = argv[0] if argv else "march"
     reps = int(argv[1]) if len(argv) > 1 else 3
-    wl = scenes.workload_sphere()
+    name = argv[2] if len(argv) > 2 else "sphere"
+    wl = {"sphere": scenes.workload_sphere, "dihedral": scenes.workload_dihedral,
+          "composite": scenes.workload_composite}[name]()
     sc, sw, vd = wl.scene, wl.sweep, wl.views
     dev = "cuda:0"
     pos, nrm, rad = pipeline.scene_to_device(sc, dev)
@@ -37,17 +41,19 @@ def main(argv):
     prm = pipeline.default_params(sc.pos, gv)
     geom, _ = pipeline.build_geometry(pos, nrm, rad, gv, prm)
     nb = 8
-    views = [api.view_from_angles(sw.theta_deg[a * 45], sw.phi_deg[a * 45], sw.centre, sw.extent,
-                                  sw.W, sw.H) for a in range(nb)]
+    na = len(sw.phi_deg)
+    mb = max(2, sw.max_bounces)
+    views = [api.view_from_angles(sw.theta_deg[a * na // nb], sw.phi_deg[a * na // nb], sw.centre,
+                                  sw.extent, sw.W, sw.H) for a in range(nb)]
     keys = api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))["keys"]
     stats = torch.zeros(8, dtype=torch.int64, device=dev)
-    h = api.trace_bounces(views, keys, nrm, geom, 2, prm, ids=False, stats=stats)
+    h = api.trace_bounces(views, keys, nrm, geom, mb, prm, ids=False, stats=stats)
     ks = [[-x for x in v.d] for v in views]
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(reps):
         if case == "march":
-            api.trace_bounces(views, keys, nrm, geom, 2, prm, hits=h, ids=False)
+            api.trace_bounces(views, keys, nrm, geom, mb, prm, hits=h, ids=False)
         elif case == "po":
             api.po_field(h, nb, sw.W * sw.H, ks, sw.freqs_hz)
         elif case == "splat":
