@@ -241,108 +241,130 @@ __global__ void col2im3_kernel(const bf16 *__restrict__ dcol, int B, int H, int 
 }
 
 // ---------------------------------------------------------------------------
-// depthwise 7x7 (zero padding 3), weights w[ky][kx][c] FP32
+// depthwise 7x7 (zero padding 3), weights w[ky][kx][c] FP32; C even, rows of
+// channel pairs (bf16x2).
 // ---------------------------------------------------------------------------
-__global__ void dw7_fwd_kernel(const bf16 *__restrict__ X, const float *__restrict__ w,
-                               const float *__restrict__ bias, int B, int H, int W, int C,
-                               bf16 *__restrict__ Y) {
-  const int64_t total = (int64_t)B * H * W * C;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % C);
-    int64_t p = t / C;
-    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-    float s = bias ? bias[c] : 0.0f;
-    for (int ky = 0; ky < 7; ++ky) {
-      int yy = y + ky - 3;
-      if (yy < 0 || yy >= H) continue;
-      for (int kx = 0; kx < 7; ++kx) {
-        int xx = x + kx - 3;
-        if (xx < 0 || xx >= W) continue;
-        s += w[(ky * 7 + kx) * C + c] * b2f(X[(((int64_t)b * H + yy) * W + xx) * C + c]);
-      }
-    }
-    Y[t] = f2b(s);
-  }
-}
+typedef __nv_bfloat162 bf162;
 
-__global__ void dw7_bwd_data_kernel(const bf16 *__restrict__ dY, const float *__restrict__ w, int B,
-                                    int H, int W, int C, bf16 *__restrict__ dX) {
-  const int64_t total = (int64_t)B * H * W * C;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % C);
-    int64_t p = t / C;
-    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-    float s = 0.0f;
-    for (int ky = 0; ky < 7; ++ky) {
-      int yy = y - ky + 3;
-      if (yy < 0 || yy >= H) continue;
-      for (int kx = 0; kx < 7; ++kx) {
-        int xx = x - kx + 3;
-        if (xx < 0 || xx >= W) continue;
-        s += w[(ky * 7 + kx) * C + c] * b2f(dY[(((int64_t)b * H + yy) * W + xx) * C + c]);
-      }
-    }
-    dX[t] = f2b(s);
-  }
-}
+__device__ __forceinline__ float2 ld2(const bf162 *p) { return __bfloat1622float2(*p); }
 
-// Partial weight/bias gradients: block (cx, chunk) sums pixels of its chunk
-// for 32 channels; part[chunk][50][C] (tap 49 = bias).
-__global__ void __launch_bounds__(256) dw7_bwd_weight_kernel(const bf16 *__restrict__ X,
-                                                             const bf16 *__restrict__ dY, int B,
-                                                             int H, int W, int C,
-                                                             int64_t pix_per_chunk,
-                                                             float *__restrict__ part) {
-  __shared__ float red[8][32];
-  const int c = blockIdx.x * 32 + threadIdx.x;
-  const int64_t P = (int64_t)B * H * W;
-  const int64_t p0 = (int64_t)blockIdx.y * pix_per_chunk;
-  int64_t p1 = p0 + pix_per_chunk;
-  if (p1 > P) p1 = P;
-  float acc[50];
+// Y = bias + sum_taps w * X (FLIP = 0), or the data gradient dX = sum_taps
+// w[6-ky][6-kx] * dY[y+ky-3][x+kx-3] (FLIP = 1, X = dY, no bias).  A thread
+// owns one channel pair and four consecutive pixels of one row; block row y
+// = image row (b, y).
+template <bool FLIP>
+__global__ void __launch_bounds__(256) dw7_kernel(const bf162 *__restrict__ X,
+                                                  const float *__restrict__ w,
+                                                  const float *__restrict__ bias, int B, int H,
+                                                  int W, int C, bf162 *__restrict__ Y) {
+  const int cp2 = C >> 1, groups = (W + 3) >> 2, per_row = groups * cp2, rows = B * H;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int b = r / H, y = r - b * H;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < per_row; t += gridDim.x * blockDim.x) {
+      const int cp = t % cp2, x0 = (t / cp2) * 4;
+      float2 acc[4];
+      const float2 b0 = bias ? make_float2(bias[2 * cp], bias[2 * cp + 1]) : make_float2(0.f, 0.f);
 #pragma unroll
-  for (int i = 0; i < 50; ++i) acc[i] = 0.0f;
-  if (c < C) {
-    for (int64_t p = p0 + threadIdx.y; p < p1; p += 8) {
-      int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-      float g = b2f(dY[p * C + c]);
-      acc[49] += g;
-#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = b0;
+#pragma unroll 1
       for (int ky = 0; ky < 7; ++ky) {
-        int yy = y + ky - 3;
+        const int yy = y + ky - 3;
         if (yy < 0 || yy >= H) continue;
+        const bf162 *row = X + (size_t)(b * H + yy) * W * cp2 + cp;
+        float2 in[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+          const int xx = x0 + k - 3;
+          in[k] = (xx >= 0 && xx < W) ? ld2(row + (size_t)xx * cp2) : make_float2(0.f, 0.f);
+        }
+        const int wy = FLIP ? 6 - ky : ky;
 #pragma unroll
         for (int kx = 0; kx < 7; ++kx) {
-          int xx = x + kx - 3;
-          if (xx < 0 || xx >= W) continue;
-          acc[ky * 7 + kx] += g * b2f(X[(((int64_t)b * H + yy) * W + xx) * C + c]);
+          const int wx = FLIP ? 6 - kx : kx;
+          const float2 wv = __ldg(reinterpret_cast<const float2 *>(w + (wy * 7 + wx) * C) + cp);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i].x = fmaf(wv.x, in[i + kx].x, acc[i].x);
+            acc[i].y = fmaf(wv.y, in[i + kx].y, acc[i].y);
+          }
         }
       }
-    }
-  }
+      bf162 *out = Y + (size_t)r * W * cp2 + cp;
 #pragma unroll
-  for (int i = 0; i < 50; ++i) {
-    red[threadIdx.y][threadIdx.x] = acc[i];
-    __syncthreads();
-    if (threadIdx.y == 0 && c < C) {
-      float s = 0.0f;
-      for (int r = 0; r < 8; ++r) s += red[r][threadIdx.x];
-      part[((int64_t)blockIdx.y * 50 + i) * C + c] = s;
+      for (int i = 0; i < 4; ++i)
+        if (x0 + i < W) out[(size_t)(x0 + i) * cp2] = __floats2bfloat162_rn(acc[i].x, acc[i].y);
     }
-    __syncthreads();
   }
 }
 
-// out[i] = sum over chunks of part[chunk][i] (fixed order), i < n.
+// Partial weight/bias gradients: part[chunk][50][C] (tap 49 = bias) with
+// chunk = blockIdx.x over image rows r = chunk, chunk + gridDim.x, ...  A
+// thread owns channel pair cp and tap row ky and slides a 7-pixel window of X
+// along each row, so every load is used by seven taps.
+__global__ void dw7_wgrad_kernel(const bf162 *__restrict__ X, const bf162 *__restrict__ dY,
+                                 int B, int H, int W, int C, float *__restrict__ part) {
+  const int cp2 = C >> 1;
+  const int cp = blockIdx.y * blockDim.x + threadIdx.x, ky = threadIdx.y;
+  if (cp >= cp2) return;
+  float2 acc[7], accb = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) acc[k] = make_float2(0.f, 0.f);
+  for (int r = blockIdx.x; r < B * H; r += gridDim.x) {
+    const int b = r / H, y = r - b * H, yy = y + ky - 3;
+    const bool rowok = yy >= 0 && yy < H;
+    if (!rowok && ky != 3) continue;
+    const bf162 *g = dY + (size_t)r * W * cp2 + cp;
+    const bf162 *xr = X + (size_t)(b * H + (rowok ? yy : y)) * W * cp2 + cp;
+    float2 win[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int xx = k - 3;
+      win[k] = (xx >= 0 && xx < W) ? ld2(xr + (size_t)xx * cp2) : make_float2(0.f, 0.f);
+    }
+    for (int x = 0; x < W; ++x) {
+      const float2 gv = ld2(g + (size_t)x * cp2);
+      accb.x += gv.x;
+      accb.y += gv.y;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        acc[k].x = fmaf(gv.x, win[k].x, acc[k].x);
+        acc[k].y = fmaf(gv.y, win[k].y, acc[k].y);
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) win[k] = win[k + 1];
+      const int xn = x + 4;
+      win[6] = xn < W ? ld2(xr + (size_t)xn * cp2) : make_float2(0.f, 0.f);
+    }
+  }
+  float *pb = part + (size_t)blockIdx.x * 50 * C + 2 * cp;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    pb[(ky * 7 + k) * C] = acc[k].x;
+    pb[(ky * 7 + k) * C + 1] = acc[k].y;
+  }
+  if (ky == 3) {
+    pb[49 * C] = accb.x;
+    pb[49 * C + 1] = accb.y;
+  }
+}
+
+// out[i] = (accumulate ? out[i] : 0) + sum over chunks of part[chunk][i],
+// i < n, in a fixed order: lane ty of the block sums chunks ty, ty + 8, ...
+// and the eight partial sums are added in order.  Block (32, 8).
 __global__ void sum_chunks_kernel(const float *__restrict__ part, int chunks, int64_t n,
                                   float *__restrict__ out, int accumulate) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float s = 0.0f;
-    for (int k = 0; k < chunks; ++k) s += part[(int64_t)k * n + i];
-    out[i] = accumulate ? out[i] + s : s;
+  __shared__ float red[8][33];
+  const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  float s = 0.0f;
+  if (i < n)
+    for (int k = threadIdx.y; k < chunks; k += 8) s += part[(int64_t)k * n + i];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+    out[i] = accumulate ? out[i] + t : t;
   }
 }
 
@@ -357,18 +379,29 @@ __global__ void ln_fwd_kernel(const bf16 *__restrict__ X, const float *__restric
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < P; p += warps) {
     const bf16 *x = X + p * C;
+    float v[8];  // C <= 256: channel lane + 32 i
     float s = 0.0f;
-    for (int c = lane; c < C; c += 32) s += b2f(x[c]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = lane + 32 * i;
+      v[i] = c < C ? b2f(x[c]) : 0.0f;
+      s += v[i];
+    }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const float mu = s / C;
-    float v = 0.0f;
-    for (int c = lane; c < C; c += 32) {
-      float d = b2f(x[c]) - mu;
-      v += d * d;
+    float var = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float d = lane + 32 * i < C ? v[i] - mu : 0.0f;
+      var += d * d;
     }
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const float rs = rsqrtf(v / C + eps);
-    for (int c = lane; c < C; c += 32) Y[p * C + c] = f2b((b2f(x[c]) - mu) * rs * gam[c] + bet[c]);
+    for (int o = 16; o > 0; o >>= 1) var += __shfl_xor_sync(0xffffffffu, var, o);
+    const float rs = rsqrtf(var / C + eps);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = lane + 32 * i;
+      if (c < C) Y[p * C + c] = f2b((v[i] - mu) * rs * gam[c] + bet[c]);
+    }
     if (lane == 0) {
       mean[p] = mu;
       rstd[p] = rs;
@@ -389,17 +422,19 @@ __global__ void ln_bwd_kernel(const bf16 *__restrict__ dY, const bf16 *__restric
   for (int i = 0; i < 8; ++i) dg[i] = db[i] = 0.0f;
   for (int64_t p = gw; p < P; p += warps) {
     const float mu = mean[p], rs = rstd[p];
+    float xh[8], gg[8];
     float s1 = 0.0f, s2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       int c = lane + 32 * i;
-      if (c >= C) break;
-      float xh = (b2f(X[p * C + c]) - mu) * rs;
+      xh[i] = gg[i] = 0.0f;
+      if (c >= C) continue;
+      xh[i] = (b2f(X[p * C + c]) - mu) * rs;
       float gy = b2f(dY[p * C + c]);
-      float g = gy * gam[c];
-      s1 += g;
-      s2 += g * xh;
-      dg[i] += gy * xh;
+      gg[i] = gy * gam[c];
+      s1 += gg[i];
+      s2 += gg[i] * xh[i];
+      dg[i] += gy * xh[i];
       db[i] += gy;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -411,10 +446,7 @@ __global__ void ln_bwd_kernel(const bf16 *__restrict__ dY, const bf16 *__restric
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       int c = lane + 32 * i;
-      if (c >= C) break;
-      float xh = (b2f(X[p * C + c]) - mu) * rs;
-      float g = b2f(dY[p * C + c]) * gam[c];
-      dX[p * C + c] = f2b(rs * (g - s1 - xh * s2));
+      if (c < C) dX[p * C + c] = f2b(rs * (gg[i] - s1 - xh[i] * s2));
     }
   }
 #pragma unroll
@@ -426,15 +458,41 @@ __global__ void ln_bwd_kernel(const bf16 *__restrict__ dY, const bf16 *__restric
   }
 }
 
-// Column sums of a [M][ld] BF16 matrix in fixed order: part[chunk][N].
+// Column sums of a [M][ld] BF16 matrix in a fixed order: block (32, 8) owns
+// 32 columns (PAIR: 32 column pairs) of chunk blockIdx.y; lane ty sums rows
+// r0 + ty, r0 + ty + 8, ...; the eight lanes are added in order into
+// part[chunk][N].
+template <bool PAIR>
 __global__ void colsum_kernel(const bf16 *__restrict__ Xs, int64_t M, int N, int64_t ld,
                               int64_t rows_per_chunk, float *__restrict__ part) {
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
-    int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk, r1 = r0 + rows_per_chunk;
-    if (r1 > M) r1 = M;
-    float s = 0.0f;
-    for (int64_t r = r0; r < r1; ++r) s += b2f(Xs[r * ld + n]);
-    part[(int64_t)blockIdx.y * N + n] = s;
+  __shared__ float2 red[8][33];
+  const int c = (blockIdx.x * 32 + threadIdx.x) * (PAIR ? 2 : 1);
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  int64_t r1 = r0 + rows_per_chunk;
+  if (r1 > M) r1 = M;
+  float2 s = make_float2(0.f, 0.f);
+  if (c < N) {
+    for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) {
+      if (PAIR) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const bf162 *>(Xs + r * ld + c));
+        s.x += v.x;
+        s.y += v.y;
+      } else {
+        s.x += b2f(Xs[r * ld + c]);
+      }
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < N) {
+    float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      t.x += red[k][threadIdx.x].x;
+      t.y += red[k][threadIdx.x].y;
+    }
+    part[(int64_t)blockIdx.y * N + c] = t.x;
+    if (PAIR) part[(int64_t)blockIdx.y * N + c + 1] = t.y;
   }
 }
 
@@ -585,29 +643,30 @@ __device__ __forceinline__ float cross_ratio(const float a[3], const float b[3],
   return cn / den;
 }
 
-__global__ void loss_count_kernel(const loss_args a, float *counts) {
-  // single block: deterministic counts
-  __shared__ float s[3][256];
-  float c0 = 0.0f, c1 = 0.0f;
+// Hit pixels and valid L4 centres, as exact integer counts (cnt zeroed first).
+__global__ void loss_count_kernel(const loss_args a, unsigned long long *cnt) {
   const int64_t P = (int64_t)a.B * a.H * a.W;
-  for (int64_t p = threadIdx.x; p < P; p += blockDim.x) {
-    int x = (int)(p % a.W), y = (int)((p / a.W) % a.H), b = (int)(p / ((int64_t)a.W * a.H));
-    c0 += hit_at(a, b, y, x) ? 1.0f : 0.0f;
-    c1 += l4_valid(a, b, y, x) ? 1.0f : 0.0f;
+  unsigned c0 = 0, c1 = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(p % a.W), y = (int)((p / a.W) % a.H), b = (int)(p / ((int64_t)a.W * a.H));
+    c0 += hit_at(a, b, y, x) ? 1u : 0u;
+    c1 += l4_valid(a, b, y, x) ? 1u : 0u;
   }
-  s[0][threadIdx.x] = c0;
-  s[1][threadIdx.x] = c1;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float t0 = 0.0f, t1 = 0.0f;
-    for (int i = 0; i < (int)blockDim.x; ++i) {
-      t0 += s[0][i];
-      t1 += s[1][i];
-    }
-    counts[0] = fmaxf(t0, 1.0f);
-    counts[1] = fmaxf(t1, 1.0f);
-    counts[2] = (float)P;
+  for (int o = 16; o > 0; o >>= 1) {
+    c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+    c1 += __shfl_xor_sync(0xffffffffu, c1, o);
   }
+  if ((threadIdx.x & 31) == 0) {
+    if (c0) atomicAdd(cnt, (unsigned long long)c0);
+    if (c1) atomicAdd(cnt + 1, (unsigned long long)c1);
+  }
+}
+
+__global__ void loss_count_finish(const unsigned long long *cnt, int64_t P, float *counts) {
+  counts[0] = fmaxf((float)cnt[0], 1.0f);
+  counts[1] = fmaxf((float)cnt[1], 1.0f);
+  counts[2] = (float)P;
 }
 
 __device__ __forceinline__ void grads_at(const loss_args &a, const float *d, int b, int y, int x,
@@ -817,25 +876,31 @@ extern "C" pe_status pe_nn_im2col3(const void *X, int32_t B, int32_t H, int32_t 
   return PE_OK;
 }
 
+static bool al4(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
 extern "C" pe_status pe_nn_dwconv7(const void *X, const float *w, const float *bias, int32_t B,
                                    int32_t H, int32_t W, int32_t C, void *Y, void *stream) {
   NN_CHECK_STREAM;
-  if (!X || !w || !Y || B <= 0 || H <= 0 || W <= 0 || C <= 0)
-    return pe_fail(PE_EINVAL, "pe_nn_dwconv7: bad arguments");
-  dw7_fwd_kernel<<<grid1((int64_t)B * H * W * C, 256), 256, 0, s>>>(
-      static_cast<const bf16 *>(X), w, bias, B, H, W, C, static_cast<bf16 *>(Y));
-  PE_TRY_LAUNCH("dw7_fwd_kernel");
+  if (!X || !w || !Y || B <= 0 || H <= 0 || W <= 0 || C <= 0 || (C & 1) || !al4(X) || !al4(Y) ||
+      (reinterpret_cast<uintptr_t>(w) & 7))
+    return pe_fail(PE_EINVAL, "pe_nn_dwconv7: bad arguments (C even, aligned buffers)");
+  const int per_row = ((W + 3) / 4) * (C / 2);
+  dim3 grid((per_row + 255) / 256, (unsigned)(B * H < 65535 ? B * H : 65535));
+  dw7_kernel<false><<<grid, 256, 0, s>>>(static_cast<const bf162 *>(X), w, bias, B, H, W, C,
+                                         static_cast<bf162 *>(Y));
+  PE_TRY_LAUNCH("dw7_kernel");
   return PE_OK;
 }
 
-static int64_t dw_chunks(int64_t P) {
-  int64_t c = (P + 2047) / 2048;
-  return c < 1 ? 1 : (c > 1024 ? 1024 : c);
+// Chunks (image rows per partial) of the weight gradient: fixed by the shape.
+static int dw_chunks(int32_t B, int32_t H) {
+  int64_t r = (int64_t)B * H;
+  return (int)(r < 1024 ? (r < 1 ? 1 : r) : 1024);
 }
 
 extern "C" size_t pe_nn_dwconv7_bwd_workspace(int32_t B, int32_t H, int32_t W, int32_t C) {
-  int64_t P = (int64_t)B * H * W;
-  return (size_t)dw_chunks(P) * 50 * C * sizeof(float) + 256;
+  (void)W;
+  return (size_t)dw_chunks(B, H) * 50 * C * sizeof(float) + 256;
 }
 
 // dX (nullable), dw [7][7][C] and db [C] (FP32, overwritten).
@@ -843,28 +908,30 @@ extern "C" pe_status pe_nn_dwconv7_bwd(const void *X, const void *dY, const floa
                                        int32_t H, int32_t W, int32_t C, void *dX, float *dw,
                                        float *db, void *ws, size_t ws_bytes, void *stream) {
   NN_CHECK_STREAM;
-  if (!X || !dY || !w || B <= 0 || H <= 0 || W <= 0 || C <= 0)
-    return pe_fail(PE_EINVAL, "pe_nn_dwconv7_bwd: bad arguments");
-  int64_t P = (int64_t)B * H * W;
+  if (!X || !dY || !w || B <= 0 || H <= 0 || W <= 0 || C <= 0 || (C & 1) || !al4(X) ||
+      !al4(dY) || (dX && !al4(dX)) || (reinterpret_cast<uintptr_t>(w) & 7))
+    return pe_fail(PE_EINVAL, "pe_nn_dwconv7_bwd: bad arguments (C even, aligned buffers)");
   if (dX) {
-    dw7_bwd_data_kernel<<<grid1(P * C, 256), 256, 0, s>>>(static_cast<const bf16 *>(dY), w, B, H,
-                                                            W, C, static_cast<bf16 *>(dX));
-    PE_TRY_LAUNCH("dw7_bwd_data_kernel");
+    const int per_row = ((W + 3) / 4) * (C / 2);
+    dim3 grid((per_row + 255) / 256, (unsigned)(B * H < 65535 ? B * H : 65535));
+    dw7_kernel<true><<<grid, 256, 0, s>>>(static_cast<const bf162 *>(dY), w, nullptr, B, H, W, C,
+                                          static_cast<bf162 *>(dX));
+    PE_TRY_LAUNCH("dw7_kernel");
   }
   if (dw || db) {
-    int64_t chunks = dw_chunks(P);
+    const int chunks = dw_chunks(B, H);
     size_t need = (size_t)chunks * 50 * C * sizeof(float);
     if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_dwconv7_bwd: workspace");
     float *part = static_cast<float *>(ws);
-    dim3 grid((C + 31) / 32, (unsigned)chunks);
-    dw7_bwd_weight_kernel<<<grid, dim3(32, 8), 0, s>>>(static_cast<const bf16 *>(X),
-                                                       static_cast<const bf16 *>(dY), B, H, W, C,
-                                                       (P + chunks - 1) / chunks, part);
-    PE_TRY_LAUNCH("dw7_bwd_weight_kernel");
+    const int cp2 = C / 2, bx = cp2 < 32 ? cp2 : 32;
+    dim3 grid((unsigned)chunks, (unsigned)((cp2 + bx - 1) / bx));
+    dw7_wgrad_kernel<<<grid, dim3(bx, 7), 0, s>>>(static_cast<const bf162 *>(X),
+                                                  static_cast<const bf162 *>(dY), B, H, W, C, part);
+    PE_TRY_LAUNCH("dw7_wgrad_kernel");
     // part[chunk][50][C]: taps 0..48 -> dw, 49 -> db; sum the chunks in
-    // order into chunk 0 (each thread reads and writes only its own index)
-    sum_chunks_kernel<<<grid1(50 * (int64_t)C, 256), 256, 0, s>>>(part, (int)chunks,
-                                                                  50 * (int64_t)C, part, 0);
+    // order into chunk 0 (a block reads only the columns it writes)
+    sum_chunks_kernel<<<(unsigned)((50 * C + 31) / 32), dim3(32, 8), 0, s>>>(part, chunks,
+                                                                          50 * (int64_t)C, part, 0);
     PE_TRY_LAUNCH("sum_chunks_kernel");
     if (dw) PE_TRY_CUDA(cudaMemcpyAsync(dw, part, sizeof(float) * 49 * C, cudaMemcpyDeviceToDevice, s));
     if (db)
@@ -907,33 +974,46 @@ extern "C" pe_status pe_nn_layernorm_bwd(const void *dY, const void *X, const fl
                                        gamma, mean, rstd, P, C, static_cast<bf16 *>(dX), part);
   PE_TRY_LAUNCH("ln_bwd_kernel");
   // part[warp][2][C]: sum over warps in order
-  sum_chunks_kernel<<<grid1(2 * (int64_t)C, 256), 256, 0, s>>>(part, (int)warps, 2 * (int64_t)C,
-                                                               part, 0);
+  sum_chunks_kernel<<<(unsigned)((2 * C + 31) / 32), dim3(32, 8), 0, s>>>(part, (int)warps,
+                                                                        2 * (int64_t)C, part, 0);
   PE_TRY_LAUNCH("sum_chunks_kernel");
   if (dgamma) PE_TRY_CUDA(cudaMemcpyAsync(dgamma, part, sizeof(float) * C, cudaMemcpyDeviceToDevice, s));
   if (dbeta) PE_TRY_CUDA(cudaMemcpyAsync(dbeta, part + C, sizeof(float) * C, cudaMemcpyDeviceToDevice, s));
   return PE_OK;
 }
 
+// Row chunks of a column sum: fixed by M.
+static int64_t colsum_chunks(int64_t M) {
+  int64_t c = (M + 255) / 256;
+  return c < 1 ? 1 : (c > 1024 ? 1024 : c);
+}
+
 extern "C" size_t pe_nn_colsum_workspace(int64_t M, int32_t N) {
-  int64_t chunks = (M + 4095) / 4096;
-  return (size_t)(chunks < 1 ? 1 : chunks) * N * sizeof(float) + 256;
+  return (size_t)colsum_chunks(M) * N * sizeof(float) + 256;
 }
 
 // out[n] = (accumulate ? out[n] : 0) + sum_m X[m * ld + n] (fixed order).
 extern "C" pe_status pe_nn_colsum(const void *X, int64_t M, int32_t N, int64_t ld, float *out,
                                   int32_t accumulate, void *ws, size_t ws_bytes, void *stream) {
   NN_CHECK_STREAM;
-  if (!X || !out || M <= 0 || N <= 0) return pe_fail(PE_EINVAL, "pe_nn_colsum: bad arguments");
-  int64_t chunks = (M + 4095) / 4096;
-  if (chunks < 1) chunks = 1;
+  if (!X || !out || M <= 0 || N <= 0 || ld < N) return pe_fail(PE_EINVAL, "pe_nn_colsum: bad arguments");
+  const int64_t chunks = colsum_chunks(M);
   size_t need = (size_t)chunks * N * sizeof(float);
   if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_colsum: workspace");
   float *part = static_cast<float *>(ws);
-  colsum_kernel<<<dim3((N + 127) / 128, (unsigned)chunks), 128, 0, s>>>(
-      static_cast<const bf16 *>(X), M, N, ld, 4096, part);
+  const int64_t rpc = (M + chunks - 1) / chunks;
+  const bool pair = (N % 2 == 0) && (ld % 2 == 0) && al4(X);
+  const bf16 *x = static_cast<const bf16 *>(X);
+  if (pair) {
+    colsum_kernel<true><<<dim3((N / 2 + 31) / 32, (unsigned)chunks), dim3(32, 8), 0, s>>>(
+        x, M, N, ld, rpc, part);
+  } else {
+    colsum_kernel<false><<<dim3((N + 31) / 32, (unsigned)chunks), dim3(32, 8), 0, s>>>(
+        x, M, N, ld, rpc, part);
+  }
   PE_TRY_LAUNCH("colsum_kernel");
-  sum_chunks_kernel<<<grid1(N, 256), 256, 0, s>>>(part, (int)chunks, N, out, accumulate);
+  sum_chunks_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 8), 0, s>>>(part, (int)chunks, N, out,
+                                                                      accumulate);
   PE_TRY_LAUNCH("sum_chunks_kernel");
   return PE_OK;
 }
@@ -1062,8 +1142,13 @@ extern "C" pe_status pe_nn_unet_losses(const float *depth, const float *normal, 
   a.part = f + 2 * P;
   float *counts = f + 2 * P + 4 * blocks;
   a.counts = counts;
-  loss_count_kernel<<<1, 256, 0, s>>>(a, counts);
+  // two 64-bit counters after the three counts (the offset is a multiple of 8 bytes)
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(counts + 4);
+  PE_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+  loss_count_kernel<<<grid1(P, 256), 256, 0, s>>>(a, cnt);
   PE_TRY_LAUNCH("loss_count_kernel");
+  loss_count_finish<<<1, 1, 0, s>>>(cnt, P, counts);
+  PE_TRY_LAUNCH("loss_count_finish");
   loss_pass1_kernel<<<blocks, 256, 0, s>>>(a);
   PE_TRY_LAUNCH("loss_pass1_kernel");
   loss_pass2_kernel<<<grid1(P, 256), 256, 0, s>>>(a);

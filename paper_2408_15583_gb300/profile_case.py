@@ -3,6 +3,7 @@
     python -m paper_2408_15583_gb300.profile_case march [reps] [workload]  # one traced batch
     python -m paper_2408_15583_gb300.profile_case po [reps] [workload]     # PO over that batch
     python -m paper_2408_15583_gb300.profile_case splat [reps] [workload]  # incidence splats
+    python -m paper_2408_15583_gb300.profile_case unet [reps] [batch]     # U-Net training steps
 
 By default each case is the sphere workload's geometry (200k points, 8 fused
 512^2 views) with one batch of 8 incidence angles at 1024^2 rays and 64
@@ -31,6 +32,8 @@ def main(argv):
     build()
     case = argv[0] if argv else "march"
     reps = int(argv[1]) if len(argv) > 1 else 3
+    if case == "unet":
+        return unet_case(reps, int(argv[2]) if len(argv) > 2 else 64)
     name = argv[2] if len(argv) > 2 else "sphere"
     wl = {"sphere": scenes.workload_sphere, "dihedral": scenes.workload_dihedral,
           "composite": scenes.workload_composite}[name]()
@@ -66,6 +69,34 @@ def main(argv):
     st = stats.cpu().numpy()
     print(f"{case}: {dt * 1e3:.2f} ms per call; batch queries {st[0]} shadow {st[1]} "
           f"exact splat tests {st[2]} node tests {st[3]} views walked {st[4]}")
+
+
+def unet_case(reps, batch, W=256):
+    """Training steps of the completion U-Net (widths 32-256, two blocks per
+    level) at W x W on seeded random maps (one warm-up step first)."""
+    import numpy as np
+    import torch
+
+    import scenes
+    from paper_2408_15583_gb300.learned import UNet
+
+    widths, blocks = (32, 64, 128, 256), (2, 2, 2, 2)
+    net = UNet(scenes.unet_init(0, widths, blocks), widths, blocks, "cuda:0")
+    g = torch.Generator().manual_seed(3)
+    P = batch * W * W
+    x = torch.rand(P, generator=g).to("cuda:0", torch.bfloat16)
+    m = (torch.rand(P, generator=g) > 0.5).float().cuda()
+    d = torch.rand(P, generator=g).cuda() * m
+    n = torch.nn.functional.normalize(torch.randn(P, 3, generator=g), dim=1).cuda()
+    net.train_step(x, d, n, m, batch, W, W, 1e-4)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        loss = net.train_step(x, d, n, m, batch, W, W, 1e-4)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / reps
+    print(f"unet: {dt * 1e3:.2f} ms per training step (batch {batch}, {W}^2); "
+          f"loss {np.round(loss.cpu().numpy(), 5).tolist()}")
 
 
 if __name__ == "__main__":
