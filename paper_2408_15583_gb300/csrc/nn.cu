@@ -14,6 +14,7 @@
 #include "pe_internal.cuh"
 
 typedef __nv_bfloat16 bf16;
+typedef __nv_bfloat162 bf162;
 
 namespace {
 
@@ -60,10 +61,22 @@ struct gemm_args {
   float alpha, beta;  // beta applies to an FP32 C only
   float *part;        // split-K partials [split][M][N]
   int64_t k_per_split;
-  int vec_a, vec_b;
+  int vec_a, vec_b;   // 16-byte operand copies are legal
+  int vec_c;          // 16-byte epilogue accesses (C, R, Z) are legal
 };
 
-constexpr int GB = 64, GK = 32, GPAD = 40;
+// Block tile 128 (M) x 64 (N) x 32 (K), eight warps of 32 x 32, a
+// three-stage cp.async pipeline; fragments by ldmatrix (transposed for the
+// operands whose M or N index is the contiguous one, as in the weight
+// gradients).  Shared-memory rows are padded by 16 bytes so the eight row
+// addresses of an ldmatrix fall in distinct banks.
+constexpr int TM = 128, TN = 64, TK = 32, STAGES = 3, GEMM_THREADS = 256;
+constexpr int A_STAGE = TM * (TK + 8);  // >= TK * (TM + 8)
+constexpr int B_STAGE = TN * (TK + 8);  // >= TK * (TN + 8)
+static_assert(A_STAGE >= TK * (TM + 8) && B_STAGE >= TK * (TN + 8), "stage sizes");
+constexpr int GEMM_SMEM = STAGES * (A_STAGE + B_STAGE) * 2;
+constexpr int C_LD = TN + 4;  // FP32 staging of the output tile
+static_assert(TM * C_LD * 4 <= GEMM_SMEM, "epilogue staging fits the pipeline buffers");
 
 __device__ __forceinline__ float gelu_f(float z) {
   return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
@@ -84,55 +97,93 @@ __device__ __forceinline__ void gemm_store(const gemm_args &g, int m, int n, flo
     static_cast<bf16 *>(g.C)[(int64_t)m * g.ldc + n] = f2b(v);
 }
 
-// Tile rows [row0, row0+64) x k [k0, k0+32) of X into S[row][k].
-template <bool KCONTIG>
-__device__ __forceinline__ void load_tile(bf16 (*S)[GPAD], const bf16 *__restrict__ X,
-                                          int64_t s_r, int64_t s_k, int row0, int64_t k0,
-                                          int rows, int64_t k_end, bool vec) {
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 16-byte asynchronous copy; bytes < 16 zero-fills the rest (0: all zeros,
+// the source is then not read).
+__device__ __forceinline__ void cp16(void *dst, const void *src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+
+// Stage one operand tile.  ROWS x TK with K contiguous (KC: S[row][k], row
+// stride TK + 8) or TK x ROWS with the row index contiguous (S[k][row], row
+// stride ROWS + 8).  X(row, k) = X[row * s_r + k * s_k]; rows >= n_rows and
+// k >= k_end read as zero.  vec: 16-byte copies are legal (aligned base,
+// contiguous stride 1 and the other stride a multiple of 8 elements).
+template <bool KC, int ROWS>
+__device__ __forceinline__ void stage_tile(bf16 *S, const bf16 *__restrict__ X, int64_t s_r,
+                                           int64_t s_k, int row0, int64_t k0, int n_rows,
+                                           int64_t k_end, bool vec) {
   const bf16 zero = f2b(0.0f);
-  if (KCONTIG) {
-    for (int c = threadIdx.x; c < GB * GK / 8; c += blockDim.x) {
-      int r = c >> 2, kc = (c & 3) * 8;
-      int gr = row0 + r;
-      int64_t gk = k0 + kc;
-      if (vec && gr < rows && gk + 8 <= k_end) {
-        *reinterpret_cast<uint4 *>(&S[r][kc]) =
-            *reinterpret_cast<const uint4 *>(X + (int64_t)gr * s_r + gk);
+  if (KC) {
+    constexpr int CH = ROWS * TK / 8;
+    for (int c = threadIdx.x; c < CH; c += GEMM_THREADS) {
+      const int r = c >> 2, kc = (c & 3) * 8;
+      const int gr = row0 + r;
+      const int64_t gk = k0 + kc;
+      bf16 *d = S + r * (TK + 8) + kc;
+      if (vec) {
+        int64_t left = k_end - gk;
+        int bytes = (gr < n_rows && left > 0) ? (int)(left >= 8 ? 16 : 2 * left) : 0;
+        cp16(d, bytes ? X + (int64_t)gr * s_r + gk : X, bytes);
       } else {
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-          S[r][kc + e] = (gr < rows && gk + e < k_end) ? X[(int64_t)gr * s_r + (gk + e) * s_k] : zero;
+          d[e] = (gr < n_rows && gk + e < k_end) ? X[(int64_t)gr * s_r + (gk + e) * s_k] : zero;
       }
     }
   } else {
-    for (int c = threadIdx.x; c < GB * GK / 8; c += blockDim.x) {
-      int k = c >> 3, rc = (c & 7) * 8;
-      int64_t gk = k0 + k;
-      int gr = row0 + rc;
-      if (vec && gk < k_end && gr + 8 <= rows) {
-        uint4 v = *reinterpret_cast<const uint4 *>(X + gk * s_k + gr);
-        const bf16 *t = reinterpret_cast<const bf16 *>(&v);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) S[rc + e][k] = t[e];
+    constexpr int CH = ROWS * TK / 8, PER_K = ROWS / 8;
+    for (int c = threadIdx.x; c < CH; c += GEMM_THREADS) {
+      const int k = c / PER_K, rc = (c % PER_K) * 8;
+      const int64_t gk = k0 + k;
+      const int gr = row0 + rc;
+      bf16 *d = S + k * (ROWS + 8) + rc;
+      if (vec) {
+        int left = n_rows - gr;
+        int bytes = (gk < k_end && left > 0) ? (left >= 8 ? 16 : 2 * left) : 0;
+        cp16(d, bytes ? X + gk * s_k + gr : X, bytes);
       } else {
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-          S[rc + e][k] = (gk < k_end && gr + e < rows) ? X[(int64_t)(gr + e) * s_r + gk * s_k] : zero;
+          d[e] = (gk < k_end && gr + e < n_rows) ? X[(int64_t)(gr + e) * s_r + gk * s_k] : zero;
       }
     }
   }
 }
 
+// C = epilogue(alpha * A B) over one 128 x 64 tile and the K range of split
+// blockIdx.z; with split-K the raw products go to part[z][M][N].
 template <bool AK, bool BK>
-__global__ void __launch_bounds__(128) gemm_kernel(const gemm_args g) {
-  __shared__ __align__(16) bf16 As[GB][GPAD];
-  __shared__ __align__(16) bf16 Bs[GB][GPAD];
-  const int m0 = blockIdx.x * GB, n0 = blockIdx.y * GB;
+__global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const gemm_args g) {
+  __shared__ __align__(128) bf16 smem[STAGES * (A_STAGE + B_STAGE)];
+  bf16 *As = smem, *Bs = smem + STAGES * A_STAGE;
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
   const int64_t kb = (int64_t)blockIdx.z * g.k_per_split;
   int64_t ke = kb + g.k_per_split;
   if (ke > g.K) ke = g.K;
+  const int nk = (int)((ke - kb + TK - 1) / TK);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int wm = (warp & 3) * 32, wn = (warp >> 2) * 32;
   const int gq = lane >> 2, tq = lane & 3;
   float acc[2][4][4];
 #pragma unroll
@@ -141,26 +192,49 @@ __global__ void __launch_bounds__(128) gemm_kernel(const gemm_args g) {
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-  for (int64_t k0 = kb; k0 < ke; k0 += GK) {
-    load_tile<AK>(As, g.A, g.sam, g.sak, m0, k0, g.M, ke, g.vec_a);
-    load_tile<BK>(Bs, g.B, g.sbn, g.sbk, n0, k0, g.N, ke, g.vec_b);
-    __syncthreads();
+
+  auto load = [&](int st, int kt) {
+    if (kt < nk) {
+      const int64_t k0 = kb + (int64_t)kt * TK;
+      stage_tile<AK, TM>(As + st * A_STAGE, g.A, g.sam, g.sak, m0, k0, g.M, ke, g.vec_a);
+      stage_tile<BK, TN>(Bs + st * B_STAGE, g.B, g.sbn, g.sbk, n0, k0, g.N, ke, g.vec_b);
+    }
+    cp_commit();
+  };
 #pragma unroll
-    for (int kk = 0; kk < GK; kk += 16) {
+  for (int st = 0; st < STAGES - 1; ++st) load(st, st);
+  for (int kt = 0; kt < nk; ++kt) {
+    cp_wait<STAGES - 2>();
+    __syncthreads();
+    const bf16 *A = As + (kt % STAGES) * A_STAGE, *B = Bs + (kt % STAGES) * B_STAGE;
+#pragma unroll
+    for (int kk = 0; kk < TK; kk += 16) {
       uint32_t a[2][4], b[4][2];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + gq;
-        a[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tq * 2]);
-        a[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tq * 2]);
-        a[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + tq * 2 + 8]);
-        a[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + tq * 2 + 8]);
+        if (AK) {
+          const int r = wm + 16 * i + (lane & 7) + ((lane >> 3) & 1) * 8;
+          ldsm4(a[i], A + r * (TK + 8) + kk + (lane >> 4) * 8);
+        } else {
+          const int k = kk + (lane >> 4) * 8 + (lane & 7);
+          ldsm4t(a[i], A + k * (TM + 8) + wm + 16 * i + ((lane >> 3) & 1) * 8);
+        }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + gq;
-        b[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + tq * 2]);
-        b[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + tq * 2 + 8]);
+      for (int j = 0; j < 4; j += 2) {
+        uint32_t r[4];
+        if (BK) {
+          const int n = wn + 8 * (j + (lane >> 4)) + (lane & 7);
+          ldsm4(r, B + n * (TK + 8) + kk + ((lane >> 3) & 1) * 8);
+        } else {
+          const int q = lane >> 3;
+          const int k = kk + (q & 1) * 8 + (lane & 7);
+          ldsm4t(r, B + k * (TN + 8) + wn + 8 * (j + (q >> 1)));
+        }
+        b[j][0] = r[0];
+        b[j][1] = r[1];
+        b[j + 1][0] = r[2];
+        b[j + 1][1] = r[3];
       }
 #pragma unroll
       for (int i = 0; i < 2; ++i)
@@ -173,32 +247,101 @@ __global__ void __launch_bounds__(128) gemm_kernel(const gemm_args g) {
               : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]),
                 "r"(b[j][1]));
     }
-    __syncthreads();
+    load((kt + STAGES - 1) % STAGES, kt + STAGES - 1);
   }
+  cp_wait<0>();
+  __syncthreads();
+  // stage alpha * acc as FP32 in shared memory, then write rows of eight
+  float *Cs = reinterpret_cast<float *>(smem);
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int m = m0 + wm + i * 16 + gq + (e >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + tq * 2 + (e & 1);
-        const float v = acc[i][j][e] * g.alpha;
-        if (g.part) {
-          if (m < g.M && n < g.N) g.part[((int64_t)blockIdx.z * g.M + m) * g.N + n] = v;
-        } else {
-          gemm_store(g, m, n, v);
-        }
+      for (int h = 0; h < 2; ++h) {
+        const int r = wm + 16 * i + gq + 8 * h, c = wn + 8 * j + 2 * tq;
+        *reinterpret_cast<float2 *>(Cs + r * C_LD + c) =
+            make_float2(acc[i][j][2 * h] * g.alpha, acc[i][j][2 * h + 1] * g.alpha);
       }
+  __syncthreads();
+  const bool split = g.part != nullptr;
+  for (int c = threadIdx.x; c < TM * TN / 8; c += GEMM_THREADS) {
+    const int r = c >> 3, cc = (c & 7) * 8;
+    const int m = m0 + r, n = n0 + cc;
+    if (m >= g.M || n >= g.N) continue;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = Cs[r * C_LD + cc + e];
+    if (split) {
+      float *dst = g.part + ((int64_t)blockIdx.z * g.M + m) * g.N + n;
+      for (int e = 0; e < 8 && n + e < g.N; ++e) dst[e] = v[e];
+      continue;
+    }
+    if (n + 8 > g.N || !g.vec_c) {
+      for (int e = 0; e < 8 && n + e < g.N; ++e) gemm_store(g, m, n + e, v[e]);
+      continue;
+    }
+    if (g.bias) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] += __ldg(g.bias + n + e);
+    }
+    if (g.R) {
+      const uint4 rv = *reinterpret_cast<const uint4 *>(g.R + (int64_t)m * g.ldr + n);
+      const bf162 *rp = reinterpret_cast<const bf162 *>(&rv);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(rp[e]);
+        v[2 * e] += f.x;
+        v[2 * e + 1] += f.y;
+      }
+    }
+    if (g.c_f32 && g.beta != 0.0f) {
+      const float *cp = static_cast<const float *>(g.C) + (int64_t)m * g.ldc + n;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] += g.beta * cp[e];
+    }
+    if (g.gelu) {
+      if (g.Z) {
+        uint4 zv;
+        bf162 *zp = reinterpret_cast<bf162 *>(&zv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) zp[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+        *reinterpret_cast<uint4 *>(g.Z + (int64_t)m * g.ldz + n) = zv;
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = gelu_f(v[e]);
+    }
+    if (g.c_f32) {
+      float4 *cp = reinterpret_cast<float4 *>(static_cast<float *>(g.C) + (int64_t)m * g.ldc + n);
+      cp[0] = make_float4(v[0], v[1], v[2], v[3]);
+      cp[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+      uint4 ov;
+      bf162 *op = reinterpret_cast<bf162 *>(&ov);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) op[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      *reinterpret_cast<uint4 *>(static_cast<bf16 *>(g.C) + (int64_t)m * g.ldc + n) = ov;
+    }
+  }
 }
 
+// Sum of the split-K partials in a fixed order (lane ty of a (32, 8) block
+// takes splits ty, ty + 8, ...; the eight are added in order), then the
+// epilogue.
 __global__ void gemm_splitk_reduce(const gemm_args g, int split) {
+  __shared__ float red[8][33];
   const int64_t total = (int64_t)g.M * g.N;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    float v = 0.0f;
-    for (int z = 0; z < split; ++z) v += g.part[(int64_t)z * total + t];
-    gemm_store(g, (int)(t / g.N), (int)(t % g.N), v);
+  const int64_t t = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  float v = 0.0f;
+  if (t < total)
+    for (int z = threadIdx.y; z < split; z += 8) v += g.part[(int64_t)z * total + t];
+  red[threadIdx.y][threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.y == 0 && t < total) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
+    gemm_store(g, (int)(t / g.N), (int)(t % g.N), s);
   }
 }
 
@@ -244,8 +387,6 @@ __global__ void col2im3_kernel(const bf16 *__restrict__ dcol, int B, int H, int 
 // depthwise 7x7 (zero padding 3), weights w[ky][kx][c] FP32; C even, rows of
 // channel pairs (bf16x2).
 // ---------------------------------------------------------------------------
-typedef __nv_bfloat162 bf162;
-
 __device__ __forceinline__ float2 ld2(const bf162 *p) { return __bfloat1622float2(*p); }
 
 // Y = bias + sum_taps w * X (FLIP = 0), or the data gradient dX = sum_taps
@@ -782,14 +923,25 @@ __global__ void loss_total_kernel(const float *part, int blocks, float w1, float
 // ===========================================================================
 #define NN_CHECK_STREAM cudaStream_t s = static_cast<cudaStream_t>(stream)
 
+// Split-K factor: enough blocks for the whole GPU (about 1024, fixed so the
+// summation order does not depend on the device), at least 8 K-steps each.
+static int64_t gemm_split(int32_t M, int32_t N, int64_t K, int64_t *kps_out) {
+  const int64_t tiles = (int64_t)((N + TN - 1) / TN) * ((M + TM - 1) / TM);
+  int64_t split = tiles >= 1024 ? 1 : (1024 + tiles - 1) / tiles;
+  const int64_t max_split = (K + 8 * TK - 1) / (8 * TK);
+  if (split > max_split) split = max_split;
+  if (split > 4096) split = 4096;
+  if (split < 1) split = 1;
+  int64_t kps = (K + split - 1) / split;
+  kps = (kps + TK - 1) / TK * TK;
+  split = (K + kps - 1) / kps;
+  if (kps_out) *kps_out = kps;
+  return split;
+}
+
 extern "C" size_t pe_nn_gemm_workspace(int32_t M, int32_t N, int64_t K) {
   if (M <= 0 || N <= 0 || K <= 0) return 0;
-  int64_t tiles = (int64_t)((N + GB - 1) / GB) * ((M + GB - 1) / GB);
-  int64_t target = (int64_t)n_sms() * 4;
-  int64_t split = tiles >= target ? 1 : (target + tiles - 1) / tiles;
-  int64_t max_split = (K + 1023) / 1024;
-  if (split > max_split) split = max_split;
-  if (split > 64) split = 64;
+  const int64_t split = gemm_split(M, N, K, nullptr);
   if (split <= 1) return 256;
   return (size_t)split * M * N * sizeof(float) + 256;
 }
@@ -825,35 +977,30 @@ extern "C" pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, 
   g.alpha = alpha;
   g.beta = beta;
   const bool ak = sak == 1, bk = sbk == 1;
-  // vector loads need 16-byte aligned rows along the contiguous dimension
+  // 16-byte copies need aligned bases and rows along the contiguous dimension
   auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   g.vec_a = al(A) && (ak ? (sam % 8 == 0) : (sam == 1 && sak % 8 == 0));
   g.vec_b = al(B) && (bk ? (sbn % 8 == 0) : (sbn == 1 && sbk % 8 == 0));
-  int64_t tiles = (int64_t)((N + GB - 1) / GB) * ((M + GB - 1) / GB);
-  int64_t target = (int64_t)n_sms() * 4;
-  int64_t split = tiles >= target ? 1 : (target + tiles - 1) / tiles;
-  int64_t max_split = (K + 1023) / 1024;
-  if (split > max_split) split = max_split;
-  if (split > 64) split = 64;
-  if (split < 1) split = 1;
-  int64_t kps = (K + split - 1) / split;
-  kps = (kps + GK - 1) / GK * GK;
-  split = (K + kps - 1) / kps;
+  g.vec_c = al(C) && (c_f32 ? ldc % 4 == 0 : ldc % 8 == 0) && (!R || (al(R) && ldr % 8 == 0)) &&
+            (!Z || (al(Z) && ldz % 8 == 0)) && (!bias || (reinterpret_cast<uintptr_t>(bias) & 3) == 0);
+  int64_t kps = 0;
+  const int64_t split = gemm_split(M, N, K, &kps);
   g.k_per_split = kps;
   if (split > 1) {
     size_t need = (size_t)split * M * N * sizeof(float);
     if (!ws || ws_bytes < need) return pe_fail(PE_ENOMEM, "pe_nn_gemm: workspace needs %zu", need);
     g.part = static_cast<float *>(ws);
   }
-  if ((N + GB - 1) / GB > 65535) return pe_fail(PE_EINVAL, "pe_nn_gemm: N too large");
-  dim3 grid((M + GB - 1) / GB, (N + GB - 1) / GB, (unsigned)split);
-  if (ak && bk) gemm_kernel<true, true><<<grid, 128, 0, s>>>(g);
-  else if (ak && !bk) gemm_kernel<true, false><<<grid, 128, 0, s>>>(g);
-  else if (!ak && bk) gemm_kernel<false, true><<<grid, 128, 0, s>>>(g);
-  else gemm_kernel<false, false><<<grid, 128, 0, s>>>(g);
+  if ((N + TN - 1) / TN > 65535) return pe_fail(PE_EINVAL, "pe_nn_gemm: N too large");
+  dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN, (unsigned)split);
+  if (ak && bk) gemm_kernel<true, true><<<grid, GEMM_THREADS, 0, s>>>(g);
+  else if (ak && !bk) gemm_kernel<true, false><<<grid, GEMM_THREADS, 0, s>>>(g);
+  else if (!ak && bk) gemm_kernel<false, true><<<grid, GEMM_THREADS, 0, s>>>(g);
+  else gemm_kernel<false, false><<<grid, GEMM_THREADS, 0, s>>>(g);
   PE_TRY_LAUNCH("gemm_kernel");
   if (split > 1) {
-    gemm_splitk_reduce<<<grid1((int64_t)M * N, 256), 256, 0, s>>>(g, (int)split);
+    const int64_t total = (int64_t)M * N;
+    gemm_splitk_reduce<<<(unsigned)((total + 31) / 32), dim3(32, 8), 0, s>>>(g, (int)split);
     PE_TRY_LAUNCH("gemm_splitk_reduce");
   }
   return PE_OK;

@@ -74,6 +74,40 @@ def test_gemm_layouts(M, N, K):
     assert rel(out2, ref) < 1e-5
 
 
+@pytest.mark.parametrize("ak,bk", [(True, True), (True, False), (False, True), (False, False)])
+@pytest.mark.parametrize("M,N,K", [(300, 200, 136), (100, 72, 5000)])
+def test_gemm_padded_strides(ak, bk, M, N, K):
+    """Every operand layout with padded leading dimensions: ragged M and N
+    tiles, partial 16-byte rows along a contiguous M or N, and (K = 5000)
+    split-K with a short last split."""
+    o = ops()
+    g = torch.Generator().manual_seed(M * 7 + N + K + 2 * ak + bk)
+    A = bf(torch.randn(M, K, generator=g))
+    B = bf(torch.randn(K, N, generator=g))
+    ref = A.double() @ B.double()
+    pad = lambda n: n + (8 - n % 8) % 8 + 8
+    if ak:
+        As = torch.zeros(M, pad(K), dtype=torch.bfloat16)
+        As[:, :K] = A
+        sam, sak = As.shape[1], 1
+    else:
+        As = torch.zeros(K, pad(M), dtype=torch.bfloat16)
+        As[:, :M] = A.t()
+        sam, sak = 1, As.shape[1]
+    if bk:
+        Bs = torch.zeros(N, pad(K), dtype=torch.bfloat16)
+        Bs[:, :K] = B.t()
+        sbk, sbn = 1, Bs.shape[1]
+    else:
+        Bs = torch.zeros(K, pad(N), dtype=torch.bfloat16)
+        Bs[:, :N] = B
+        sbk, sbn = Bs.shape[1], 1
+    out = torch.full((M, N + 4), 7.0, dtype=torch.float32, device=DEV)
+    o.gemm(M, N, K, As.to(DEV), sam, sak, Bs.to(DEV), sbk, sbn, out, N + 4)
+    assert rel(out[:, :N], ref) < 1e-5
+    assert bool((out[:, N:] == 7.0).all())      # nothing written past N
+
+
 def test_depthwise_layernorm_pool_shuffle_vs_torch():
     o = ops()
     Bn, H, W, Cc = 2, 12, 10, 40
@@ -141,9 +175,11 @@ def _oracle_outputs(params, x, widths, blocks):
     return P, out
 
 
-def _net(widths, blocks, seed):
+def _net(widths, blocks, seed, normal_bias=None):
     from paper_2408_15583_gb300.learned import UNet
     params = scenes.unet_init(seed, widths, blocks)
+    if normal_bias is not None:
+        params["normal.head.b"] = np.asarray(normal_bias, params["normal.head.b"].dtype)
     return params, UNet(params, widths, blocks, DEV)
 
 
@@ -201,8 +237,8 @@ def test_unet_forward_matches_oracle():
     assert rel(outs["mask"].view(Bn, H, W), ref["mask"][:, 0]) < 5e-2
 
 
-def _grad_compare(lambdas, seed):
-    params, net = _net(WID, BLK, seed)
+def _grad_compare(lambdas, seed, normal_bias=None):
+    params, net = _net(WID, BLK, seed, normal_bias)
     Bn, H, W = 2, 32, 32
     x = np.random.Generator(np.random.PCG64(seed)).random((Bn, H, W)).astype(np.float32)
     x = torch.tensor(x).to(torch.bfloat16).float().numpy()
@@ -242,13 +278,15 @@ def test_unet_backward_chain_matches_oracle():
 
 
 def test_unet_gradients_of_the_full_loss():
-    # Eq. 21: the sin-angle terms (Eq. 18, 20) scale like 1/|n| and amplify
-    # BF16 rounding of the outputs where the raw normal is small at
-    # initialisation; pixel sums with heavy cancellation (head biases) then
-    # show it most.  The whole gradient vector must agree closely.
-    rows, (cos_all, rel_all) = _grad_compare((1.0, 0.5, 1.0, 0.5), 6)
+    # Eq. 21 with every term.  The sin-angle term of Eq. 18 scales like 1/|n|
+    # in the raw predicted normal, which a fresh initialisation leaves near
+    # zero, where any BF16 rounding of the outputs turns the normal head's
+    # gradient sums around.  The comparison is made where that term is
+    # conditioned like the others: the normal head's bias points along w, so
+    # |n| ~ 1 (Eq. 20 uses (d_u, d_v, 1), whose length is at least 1).
+    rows, (cos_all, rel_all) = _grad_compare((1.0, 0.5, 1.0, 0.5), 6, normal_bias=(0.0, 0.0, 1.0))
     assert rel_all < 0.1 and cos_all > 0.995, (rel_all, cos_all, rows[:5])
-    assert min(c for _, c, _ in rows) > 0.9, sorted(rows, key=lambda t: t[1])[:5]
+    assert min(c for _, c, _ in rows) > 0.99, sorted(rows, key=lambda t: t[1])[:5]
 
 
 def test_training_reduces_the_loss():
