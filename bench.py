@@ -57,6 +57,15 @@ def make_workload(name):
                              "PCA normals), 2048^2 rays, 10 GHz, 72 azimuths, mb=5, "
                              "8 GFB views 512^2",
                     points=1_000_000, rays=2048 * 2048, freqs=1, angles=72, max_bounces=5)
+    elif name == "octar":
+        wl = scenes.workload_octar()
+        W = wl.sweep.W
+        desc = dict(workload=f"OctAR (three orthogonal 20 m plates = 8 trihedrals), 50k points, "
+                             f"{W}^2 rays (lambda/10), 500 MHz, theta 60 deg, 360 azimuths, mb=3, "
+                             "8 GFB views 512^2",
+                    points=wl.scene.n, rays=W * W, freqs=1, angles=360, max_bounces=3,
+                    paper_context="3-bounce MBC about 30 ms per angle, EM field under 1 ms per "
+                                  "angle, GFB preprocessing 2.44 s (hardware not stated)")
     else:
         raise SystemExit(f"unknown workload {name}")
     return wl, desc
@@ -229,6 +238,27 @@ def run_gpu(args, rank, world, local_rank):
     h2d = int(hp.numel() * 4 + hn.numel() * 4 + hr.numel() * 4)
     d2h = int(hE.numel() * 8 + hS.numel() * 8)
 
+    # phase split (outside the timed steps): GFB views + fusion vs the sweep
+    def _time(fn, reps=2):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def _geometry():
+        g = api.build_gfb(gv, pos, nrm, rad, 0, 0.0, outputs=("nd", "mask"))
+        api.aggregate_views(gv, g["nd"], g["mask"], prm, geom=geom)
+
+    geom_ms = _time(_geometry)
+    sweep_ms = _time(lambda: api.rcs_sweep(sargs, pos, nrm, rad, geom, prm, ws=ws, E=E, sigma=sig))
+    api.stream_check()
+    phases = {"gfb_views_and_fusion_ms": geom_ms, "sweep_ms": sweep_ms,
+              "sweep_ms_per_angle": sweep_ms / A}
+
     # roofline of the dominant kernel (march_kernel, timed in the steps above)
     roof = roofline_march(march_ms, march_queries / march_launches_per_step)
     # the PO field kernel, timed alone on the launching stream
@@ -265,6 +295,7 @@ def run_gpu(args, rank, world, local_rank):
         "e2e": {"value": per_gpu_units * world / (e2e_ms / 1e3), "unit": "ray-bounces/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "rcs_samples_per_s": samples / (e2e_ms / 1e3)},
+        "phases": phases,
         "roofline": roof,
         "roofline_po": roof_po,
         "gpu_launches": int(launches),
@@ -541,7 +572,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "dihedral", "composite"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "dihedral", "composite", "octar"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-learned", action="store_true")

@@ -9,7 +9,7 @@ By default each case is the sphere workload's geometry (200k points, 8 fused
 512^2 views) with one batch of 8 incidence angles at 1024^2 rays and 64
 frequencies: a few GB on the device, inputs larger than L2, a handful of
 launches -- small enough for a full ncu capture of one launch.  `workload`
-= dihedral or composite takes that workload's scene, screen and bounce
+= dihedral, composite or octar takes that workload's scene, screen and bounce
 count instead (for timing; the composite batch holds ~3 GB of ray records).
 """
 from __future__ import annotations
@@ -36,7 +36,7 @@ def main(argv):
         return unet_case(reps, int(argv[2]) if len(argv) > 2 else 64)
     name = argv[2] if len(argv) > 2 else "sphere"
     wl = {"sphere": scenes.workload_sphere, "dihedral": scenes.workload_dihedral,
-          "composite": scenes.workload_composite}[name]()
+          "composite": scenes.workload_composite, "octar": scenes.workload_octar}[name]()
     sc, sw, vd = wl.scene, wl.sweep, wl.views
     dev = "cuda:0"
     pos, nrm, rad = pipeline.scene_to_device(sc, dev)

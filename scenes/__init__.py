@@ -29,9 +29,10 @@ C0 = 299_792_458.0  # speed of light, m/s
 __all__ = [
     "C0", "Scene", "Sweep", "GfbViews", "Workload",
     "knn_radius", "pca_normals", "bounding_sphere",
-    "plate", "dihedral", "trihedral", "sphere", "cylinder", "composite",
+    "plate", "dihedral", "trihedral", "sphere", "cylinder", "composite", "octar",
     "random_primitives", "aggregation_views", "freq_grid",
-    "workload_dihedral", "workload_sphere", "workload_composite", "workload_small",
+    "workload_dihedral", "workload_sphere", "workload_composite", "workload_octar",
+    "workload_small",
 ]
 
 
@@ -215,6 +216,29 @@ def dihedral(n_points: int = 10_000, a: float = 0.5, seed: int = 1, jitter: bool
     p2 = np.stack([np.zeros_like(su), su, sv - a / 2], axis=1)
     n2 = np.tile([1.0, 0.0, 0.0], (p2.shape[0], 1))
     return _finish(np.concatenate([p1, p2]), np.concatenate([n1, n2]), "dihedral", seed)
+
+
+def octar(n_points: int = 50_000, size: float = 20.0, seed: int = 8) -> Scene:
+    """The paper's OctAR target (Sec. IV-B, Fig. 11): eight trihedral corner
+    reflectors formed by three mutually orthogonal square plates of side
+    `size` crossing at the origin (the planes x=0, y=0, z=0).  n/3 points per
+    plate, one uniform point per cell of a square grid; exact normals along
+    each plate's axis (the plates are two-sided)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    per = n_points // 3
+    n_u = max(1, int(round(math.sqrt(per))))
+    n_v = max(1, per // n_u)
+    ps, ns = [], []
+    for axis in range(3):
+        su, sv = _stratified_rect(rng, n_u, n_v, size, size)
+        p = np.zeros((su.size, 3))
+        p[:, (axis + 1) % 3] = su - size / 2
+        p[:, (axis + 2) % 3] = sv - size / 2
+        n = np.zeros_like(p)
+        n[:, axis] = 1.0
+        ps.append(p)
+        ns.append(n)
+    return _finish(np.concatenate(ps), np.concatenate(ns), "octar", seed)
 
 
 def trihedral(n_points: int = 30_000, a: float = 0.6, seed: int = 4,
@@ -415,6 +439,21 @@ def workload_composite(n_points=1_000_000, W=2048, view_W=512, n_angles=72, pca=
     phi = np.arange(n_angles, dtype=np.float64) * (360.0 / n_angles)
     sw = _sweep_over(sc, np.full(n_angles, 60.0), phi, W, [10e9], 5)
     return Workload(sc, sw, aggregation_views(sc, view_W, view_W), "composite")
+
+
+def workload_octar(n_points=50_000, size=20.0, view_W=512, n_angles=360, freq_hz=500e6,
+                   W=None) -> Workload:
+    """OctAR at the paper's settings (Sec. IV-B): 50k points, longest bbox edge
+    20 m, 500 MHz, monostatic theta = 60 deg over phi 0..359, three bounces,
+    ray pitch lambda/10 (W x W rays over the bounding sphere)."""
+    sc = octar(n_points, size)
+    phi = np.arange(n_angles, dtype=np.float64) * (360.0 / n_angles)
+    if W is None:
+        _, r = bounding_sphere(sc.pos)
+        pitch = C0 / freq_hz / 10.0
+        W = int(math.ceil(2.0 * r * 1.02 / pitch / 8.0)) * 8
+    sw = _sweep_over(sc, np.full(n_angles, 60.0), phi, W, [freq_hz], 3)
+    return Workload(sc, sw, aggregation_views(sc, view_W, view_W), "octar")
 
 
 def workload_small(seed: int = 11) -> Workload:

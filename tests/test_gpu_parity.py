@@ -133,10 +133,8 @@ def test_gfb_edge_cases():
 # a4 / a5 on a shared small geometry
 # ----------------------------------------------------------------------------
 
-@pytest.fixture(scope="module")
-def small_geom():
+def _geom_case(sc):
     api, pipe = _mods()
-    sc = scenes.dihedral(3000, seed=12)
     vd = scenes.aggregation_views(sc, 80, 80)
     pos, nrm, rad = pipe.scene_to_device(sc, DEV)
     gv = pipe.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, vd.W, vd.H)
@@ -151,7 +149,24 @@ def small_geom():
     return dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, S=S, ogv=ogv)
 
 
-def test_aggregate_splats_bitexact(small_geom):
+@pytest.fixture(scope="module")
+def small_geom():
+    return _geom_case(scenes.dihedral(3000, seed=12))
+
+
+@pytest.fixture(scope="module")
+def octar_geom():
+    # the OctAR shape at 2 m: eight trihedral corners, rays of up to 3 bounces
+    # crossing the splats of several views
+    return _geom_case(scenes.octar(3000, size=2.0, seed=13))
+
+
+GEOMS = ["small_geom", "octar_geom"]
+
+
+@pytest.mark.parametrize("case", GEOMS)
+def test_aggregate_splats_bitexact(case, request):
+    small_geom = request.getfixturevalue(case)
     geom, S = small_geom["geom"], small_geom["S"]
     cr, nf = geom.planes()
     cr = cr.cpu().numpy()
@@ -165,13 +180,15 @@ def test_aggregate_splats_bitexact(small_geom):
     assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
 
 
+@pytest.mark.parametrize("case", GEOMS)
 @pytest.mark.parametrize("geom_first", [False, True])
-def test_trace_bounces_bitexact(small_geom, geom_first):
+def test_trace_bounces_bitexact(case, geom_first, request):
     api, pipe = _mods()
-    d = small_geom
+    d = request.getfixturevalue(case)
     sc = d["sc"]
     c, r = scenes.bounding_sphere(sc.pos)
-    th, ph = [90.0, 90.0, 75.0], [45.0, 10.0, 58.0]
+    th, ph = ([90.0, 90.0, 75.0], [45.0, 10.0, 58.0]) if case == "small_geom" else \
+        ([60.0, 54.7356, 120.0], [45.0, 45.0, 200.0])
     views = pipe.views_from_angles(th, ph, c, r * 1.02, 40, 40)
     prm = pipe.default_params(sc.pos, d["gv"], first_bounce_from_geom=geom_first)
     mb = 3
@@ -284,12 +301,14 @@ def _sigma_check(sig, ref, peak_db=40.0, tol_db=0.1):
     return np.abs(sd - so)[keep].max()
 
 
-def test_rcs_sweep_matches_oracle(small_geom):
+@pytest.mark.parametrize("case", GEOMS)
+def test_rcs_sweep_matches_oracle(case, request):
     api, pipe = _mods()
-    d = small_geom
+    d = request.getfixturevalue(case)
     sc = d["sc"]
-    sw = scenes._sweep_over(sc, [90.0] * 5 + [70.0], [0.0, 13.0, 45.0, 62.0, 90.0, 30.0], 48,
-                            [2.9e9, 3.0e9, 3.3e9], 2)
+    th = [90.0] * 5 + [70.0] if case == "small_geom" else [60.0] * 5 + [54.7356]
+    sw = scenes._sweep_over(sc, th, [0.0, 13.0, 45.0, 62.0, 90.0, 30.0], 48,
+                            [2.9e9, 3.0e9, 3.3e9], 2 if case == "small_geom" else 3)
     args = api.SweepArgs.from_sweep(sw, angle_batch=4)     # two batches, ragged tail
     E, sig = api.rcs_sweep(args, d["pos"], d["nrm"], d["rad"], d["geom"], d["prm"])
     api.stream_check()
