@@ -93,8 +93,9 @@ typedef struct {
  * blob holds, for each view v (pixel offset off_v = sum of earlier W*H):
  *   splat_cr[off_v + p] = {cx, cy, cz, R}   (R = 0: no splat owned here)
  *   splat_nf[off_v + p] = {nx, ny, nz, count}
- * and a conservative bounding-box pyramid per view (leaf tiles of 8x8 pixels,
- * each level 4x4 tiles of the one below) in that view's (u, v, d) frame.
+ * and a conservative bounding-box pyramid per view (leaf tiles of 4x4 pixels,
+ * each level 2x2 tiles of the one below; a leaf's lo.w holds the bit pattern
+ * of its occupancy mask) in that view's (u, v, d) frame.
  * A splat's id is its owner pixel's global index off_v + p.
  * The blob also holds a coarse 32^3 grid over the fusion bounding box: per
  * cell, a bit mask of the views that own a splat whose (padded) sphere
@@ -223,7 +224,11 @@ size_t pe_aggregate_workspace(int32_t n_views, const pe_view *views,
  * contributor), both summed in FP64 in (view, pixel) order, and whose radius
  * is the largest Eq. 22 value over its contributors (L = the contributor's
  * view pitch, p = its view direction).  The splat is stored at its owner
- * pixel: the first contributor in (view, pixel) order.  Then the bounding
+ * pixel: among the contributing views the one facing the fused normal most
+ * directly (largest floor(4 |n . d_v|), FP32; the lower view on a tie), at
+ * its first pixel in (view, pixel) order (the first contributor if the
+ * normal vanishes).
+ * Then the bounding
  * pyramids are built.  out->views/n_views/blob_dev must be set by the caller
  * (views identical to `views`).  Requires n_views <= PE_MAX_VIEWS,
  * fuse_grid <= 256. */

@@ -256,7 +256,7 @@ static int64_t SFX(aggregate)(int nv, const or_view *views, const double *depth_
     uint64_t vox = ent[a].key >> 40;
     int64_t b = a;
     while (b < ne && (ent[b].key >> 40) == vox) ++b;
-    /* segment [a, b) in (view, pixel) order; the first entry owns the splat */
+    /* segment [a, b) in (view, pixel) order */
     const SFX(entry) *E0 = &ent[a];
     double sp3[3] = {0, 0, 0}, sn3[3] = {0, 0, 0}, rmax = 0.0;
     for (int64_t e = a; e < b; ++e) {
@@ -276,12 +276,31 @@ static int64_t SFX(aggregate)(int nv, const or_view *views, const double *depth_
     double cnt = (double)(b - a);
     double m = sqrt((sn3[0] * sn3[0] + sn3[1] * sn3[1]) + sn3[2] * sn3[2]);
     SFX(splat) *S = &sp[ns++];
-    int v0 = (int)((E0->key >> 32) & 0xff);
-    S->id = voff[v0] + (int64_t)(E0->key & 0xffffffffu);
     for (int k = 0; k < 3; ++k) {
       S->c[k] = (R)(sp3[k] / cnt);
       S->n[k] = (R)(sn3[k] / m);
     }
+    /* owner: among the contributing views, the one facing the fused normal
+     * most directly, by |n . d_v| in quarters (floor(4 |n . d_v|), so that
+     * near-equal views tie), the lower view on a tie, and within it its
+     * first (lowest) pixel; the first entry if the normal vanishes */
+    const SFX(entry) *Eo = E0;
+    if (m > 0.0) {
+      R best = (R)-1;
+      for (int64_t e = a; e < b; ++e) {
+        SFX(view) V;
+        SFX(load_view)(&views[ent[e].view], &V);
+        R sc = SFX(dot)(S->n, V.d);
+        if (sc < (R)0) sc = -sc;
+        sc = FLOOR(sc * (R)4);
+        if (sc > best) {
+          best = sc;
+          Eo = &ent[e];
+        }
+      }
+    }
+    int v0 = (int)((Eo->key >> 32) & 0xff);
+    S->id = voff[v0] + (int64_t)(Eo->key & 0xffffffffu);
     S->r = (R)rmax;
     S->count = (int32_t)(b - a);
     a = b;

@@ -271,14 +271,34 @@ __global__ void fuse_segment_kernel(const __grid_constant__ pe_geom_layout L,
     double cnt = (double)len;
     double m = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a.sn[0], a.sn[0]), __dmul_rn(a.sn[1], a.sn[1])),
                                     __dmul_rn(a.sn[2], a.sn[2])));
+    const pe_f3 nrm = {__double2float_rn(__ddiv_rn(a.sn[0], m)),
+                       __double2float_rn(__ddiv_rn(a.sn[1], m)),
+                       __double2float_rn(__ddiv_rn(a.sn[2], m))};
+    // Owner: the contributing view facing the fused normal most directly, by
+    // |n . d_v| in quarters (floor(4 |n . d_v|), so near-equal views tie),
+    // the smaller (view, pixel) key on a tie; the first entry if the normal
+    // vanishes.  Owners of neighbouring voxels then mostly come from the same
+    // view, which keeps each stretch of surface in few pyramids.
+    if (m > 0.0) {
+      float bs = -1.0f;
+      unsigned long long bk = owner;
+      auto consider = [&](unsigned long long k) {
+        const pe_view &V = L.view[(int)((k >> 32) & 0xff)];
+        const float sc = floorf(__fmul_rn(fabsf(pe_dot(nrm, pe_f3{V.d[0], V.d[1], V.d[2]})), 4.0f));
+        if (sc > bs || (sc == bs && k < bk)) {
+          bs = sc;
+          bk = k;
+        }
+      };
+      for (int64_t e = 0; e < len; ++e) consider(entries[s + e]);
+      owner = bk;
+    }
     int v0 = (int)((owner >> 32) & 0xff);
     int64_t id = L.pix_off[v0] + (int64_t)(owner & 0xffffffffull);
     cr[id] = make_float4(__double2float_rn(__ddiv_rn(a.sp[0], cnt)),
                          __double2float_rn(__ddiv_rn(a.sp[1], cnt)),
                          __double2float_rn(__ddiv_rn(a.sp[2], cnt)), __double2float_rn(a.rmax));
-    nf[id] = make_float4(__double2float_rn(__ddiv_rn(a.sn[0], m)),
-                         __double2float_rn(__ddiv_rn(a.sn[1], m)),
-                         __double2float_rn(__ddiv_rn(a.sn[2], m)), (float)len);
+    nf[id] = make_float4(nrm.x, nrm.y, nrm.z, (float)len);
   }
 }
 

@@ -42,7 +42,7 @@ __device__ __forceinline__ float sincf_(float x) {
     return 1.0f + x2 * (-1.0f / 6.0f + x2 * (1.0f / 120.0f + x2 * (-1.0f / 5040.0f +
                                                                   x2 * (1.0f / 362880.0f))));
   }
-  return __sinf(x) / x;
+  return __fdividef(__sinf(x), x);
 }
 
 __device__ __forceinline__ void two_sum_into(float &hi, float &lo, float b) {
@@ -58,10 +58,11 @@ __device__ __forceinline__ pe_f3 cross(pe_f3 a, pe_f3 b) {
 }
 __device__ __forceinline__ float dotf(pe_f3 a, pe_f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-__global__ void __launch_bounds__(kPoThreads)
+__global__ void __launch_bounds__(kPoThreads, 3)
     po_kernel(const pe_hits h, const __grid_constant__ po_consts C, double *__restrict__ part) {
-  __shared__ float s_au[kPoThreads], s_av[kPoThreads], s_dh[kPoThreads], s_dl[kPoThreads];
-  __shared__ float s_V[6][kPoThreads];
+  // per staged ray: {au, av, dh, dl}, {V0..V3}, {V4, V5, -, -}: three
+  // broadcast 16-byte loads per term
+  __shared__ float4 s_ray[3][kPoThreads];
   __shared__ int s_warp[kPoThreads / 32];
   __shared__ double s_red[kPoThreads][12];
 
@@ -144,19 +145,17 @@ __global__ void __launch_bounds__(kPoThreads)
       }
       if (valid) {
         int at = before + __popc(m & ((1u << lane) - 1u));
-        s_au[at] = au;
-        s_av[at] = av;
-        s_dh[at] = dh;
-        s_dl[at] = dl;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) s_V[i][at] = V[i];
+        s_ray[0][at] = make_float4(au, av, dh, dl);
+        s_ray[1][at] = make_float4(V[0], V[1], V[2], V[3]);
+        s_ray[2][at] = make_float4(V[4], V[5], 0.0f, 0.0f);
       }
       __syncthreads();
       // ---- one frequency per thread over the staged rays -----------------
       if (f_ok) {
         for (int j = lane_r; j < total; j += RL) {
-          float s = sincf_(kf * s_au[j]) * sincf_(kf * s_av[j]);
-          float dhi = s_dh[j], dlo = s_dl[j];
+          const float4 r0 = s_ray[0][j], r1 = s_ray[1][j], r2 = s_ray[2][j];
+          float s = sincf_(kf * r0.x) * sincf_(kf * r0.y);
+          float dhi = r0.z, dlo = r0.w;
           float ph = khi * dhi;
           float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
           float nq = rintf(ph * C.inv2pi);
@@ -167,11 +166,11 @@ __global__ void __launch_bounds__(kPoThreads)
           float sn, cs;
           __sincosf(red, &sn, &cs);
           float re = s * cs, im = -s * sn;
+          const float Vs[6] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
 #pragma unroll
           for (int i = 0; i < 6; ++i) {
-            float Vi = s_V[i][j];
-            b[2 * i] = fmaf(Vi, re, b[2 * i]);
-            b[2 * i + 1] = fmaf(Vi, im, b[2 * i + 1]);
+            b[2 * i] = fmaf(Vs[i], re, b[2 * i]);
+            b[2 * i + 1] = fmaf(Vs[i], im, b[2 * i + 1]);
           }
           if (++pending == kFlush) {
 #pragma unroll

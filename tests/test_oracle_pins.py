@@ -217,6 +217,28 @@ def test_fusion_average_over_views(mode):
     assert np.allclose(s.n, n[None], atol=1e-7)
 
 
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_fusion_owner_is_the_most_frontal_view(mode):
+    # view 0 looks down -z; view 1 looks along (0.6, 0, -0.8) from a screen
+    # placed so its pixels land on the same surface points (x_i, y_j, 0).
+    # With both normals (-0.6, 0, 0.8): |n.d0| = 0.8 < |n.d1| = 1, so view 1
+    # owns every splat (ids 25 + pixel); with (0.6, 0, 0.8): 0.8 > 0.28 and
+    # view 0 owns them.
+    L = 0.125
+    v0 = down_view(5, 5, L)
+    v1 = oracle.View(o=np.array([-3.0, 0.0, 4.0]), u=np.array([1.0, 0.0, 0.0]),
+                     v=np.array([0.0, 1.0, 0.0]), d=np.array([0.6, 0.0, -0.8]), pitch=L, W=5, H=5)
+    inner = [6, 7, 8, 11, 12, 13, 16, 17, 18]
+    for n, owner_off in (([-0.6, 0.0, 0.8], 25), ([0.6, 0.0, 0.8], 0)):
+        n = np.array(n)
+        g0 = _handmade_gfb(v0, np.full(25, 5.0), np.tile(n, (25, 1)), np.ones(25))
+        g1 = _handmade_gfb(v1, np.full(25, 5.0), np.tile(n, (25, 1)), np.ones(25))
+        s = oracle.aggregate([g0, g1], _exact_fuse(), mode)
+        assert list(s.id) == [owner_off + i for i in inner]
+        assert np.all(s.count == 2)
+        assert np.allclose(s.n, n[None], atol=1e-7)
+
+
 # ----------------------------------------------------------------------------
 # a5: Eq. 23 overlap selection / blend, epsilon, mirror paths
 # ----------------------------------------------------------------------------
