@@ -378,6 +378,13 @@ pe_status pe_rcs_sweep(const pe_sweep *sweep, const float *pos_dev,
  * stride ldc.  Long K is split across blocks (deterministic split-K) using ws
  * of pe_nn_gemm_workspace() bytes. */
 size_t pe_nn_gemm_workspace(int32_t M, int32_t N, int64_t K);
+/* Which contraction kernel pe_nn_gemm uses (process-wide; returns the
+ * previous setting; other values only query): 0 = the tcgen05 tensor-core
+ * kernel (TMA-staged operands, accumulator in tensor memory) whenever both
+ * operands are K-contiguous with 16-byte aligned rows and no split-K is
+ * needed, else the mma.sync kernel (default); 1 = the mma.sync kernel only.
+ * Both give the same result up to FP32 summation order. */
+int32_t pe_nn_gemm_path(int32_t path);
 pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, int64_t sam, int64_t sak,
                      const void *B, int64_t sbk, int64_t sbn, void *C, int64_t ldc,
                      int32_t c_f32, const float *bias, const void *R, int64_t ldr, void *Z,

@@ -75,6 +75,7 @@ SIGNATURES = {
     "pe_rcs_sweep": (C.c_int, [P, P, P, P, C.c_int64, P, P, P, C.c_size_t, P, P, P, P]),
     # a8
     "pe_nn_gemm_workspace": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int64]),
+    "pe_nn_gemm_path": (C.c_int32, [C.c_int32]),
     "pe_nn_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, P, C.c_int64, C.c_int64, P,
                              C.c_int64, C.c_int64, P, C.c_int64, C.c_int32, P, P, C.c_int64, P,
                              C.c_int64, C.c_int32, C.c_float, C.c_float, P, C.c_size_t, P]),

@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include "pe_internal.cuh"
+#include "nn_gemm.cuh"
 
 typedef __nv_bfloat16 bf16;
 typedef __nv_bfloat162 bf162;
@@ -42,28 +43,7 @@ int grid1(int64_t n, int threads, int per_sm = 16) {
 // ---------------------------------------------------------------------------
 // GEMM
 // ---------------------------------------------------------------------------
-struct gemm_args {
-  int M, N;
-  int64_t K;
-  const bf16 *A;
-  int64_t sam, sak;  // element (m, k) at A[m * sam + k * sak]
-  const bf16 *B;
-  int64_t sbk, sbn;  // element (k, n) at B[k * sbk + n * sbn]
-  void *C;
-  int64_t ldc;
-  int c_f32;
-  const float *bias;  // [N] or null
-  const bf16 *R;      // residual [M][ldr] or null
-  int64_t ldr;
-  bf16 *Z;            // pre-activation copy (gelu) or null
-  int64_t ldz;
-  int gelu;
-  float alpha, beta;  // beta applies to an FP32 C only
-  float *part;        // split-K partials [split][M][N]
-  int64_t k_per_split;
-  int vec_a, vec_b;   // 16-byte operand copies are legal
-  int vec_c;          // 16-byte epilogue accesses (C, R, Z) are legal
-};
+
 
 // Block tile 128 (M) x 64 (N) x 32 (K), eight warps of 32 x 32, a
 // three-stage cp.async pipeline; fragments by ldmatrix (transposed for the
@@ -82,7 +62,7 @@ __device__ __forceinline__ float gelu_f(float z) {
   return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
 }
 
-__device__ __forceinline__ void gemm_store(const gemm_args &g, int m, int n, float v) {
+__device__ __forceinline__ void gemm_store(const pe_gemm_args &g, int m, int n, float v) {
   if (m >= g.M || n >= g.N) return;
   if (g.bias) v += g.bias[n];
   if (g.R) v += b2f(g.R[(int64_t)m * g.ldr + n]);
@@ -174,7 +154,7 @@ __device__ __forceinline__ void stage_tile(bf16 *S, const bf16 *__restrict__ X, 
 // C = epilogue(alpha * A B) over one 128 x 64 tile and the K range of split
 // blockIdx.z; with split-K the raw products go to part[z][M][N].
 template <bool AK, bool BK>
-__global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const gemm_args g) {
+__global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const pe_gemm_args g) {
   __shared__ __align__(128) bf16 smem[STAGES * (A_STAGE + B_STAGE)];
   bf16 *As = smem, *Bs = smem + STAGES * A_STAGE;
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
@@ -328,7 +308,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const gemm_args g) {
 // Sum of the split-K partials in a fixed order (lane ty of a (32, 8) block
 // takes splits ty, ty + 8, ...; the eight are added in order), then the
 // epilogue.
-__global__ void gemm_splitk_reduce(const gemm_args g, int split) {
+__global__ void gemm_splitk_reduce(const pe_gemm_args g, int split) {
   __shared__ float red[8][33];
   const int64_t total = (int64_t)g.M * g.N;
   const int64_t t = (int64_t)blockIdx.x * 32 + threadIdx.x;
@@ -923,6 +903,16 @@ __global__ void loss_total_kernel(const float *part, int blocks, float w1, float
 // ===========================================================================
 #define NN_CHECK_STREAM cudaStream_t s = static_cast<cudaStream_t>(stream)
 
+// 0: tcgen05 kernel where it applies (K-contiguous operands, no split-K),
+// else the mma.sync kernel; 1: the mma.sync kernel only.
+static int g_gemm_path = 0;
+
+extern "C" int32_t pe_nn_gemm_path(int32_t path) {
+  const int prev = g_gemm_path;
+  if (path == 0 || path == 1) g_gemm_path = path;
+  return prev;
+}
+
 // Split-K factor: enough blocks for the whole GPU (about 1024, fixed so the
 // summation order does not depend on the device), at least 8 K-steps each.
 static int64_t gemm_split(int32_t M, int32_t N, int64_t K, int64_t *kps_out) {
@@ -954,7 +944,7 @@ extern "C" pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, 
   NN_CHECK_STREAM;
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C)
     return pe_fail(PE_EINVAL, "pe_nn_gemm: bad sizes or null operands");
-  gemm_args g;
+  pe_gemm_args g;
   memset(&g, 0, sizeof(g));
   g.M = M;
   g.N = N;
@@ -992,6 +982,10 @@ extern "C" pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, 
     g.part = static_cast<float *>(ws);
   }
   if ((N + TN - 1) / TN > 65535) return pe_fail(PE_EINVAL, "pe_nn_gemm: N too large");
+  if (split == 1 && g_gemm_path == 0 && pe_gemm_tc_eligible(g)) {
+    const pe_status st = pe_gemm_tc(g, s);
+    if (st != PE_EUNSUPPORTED) return st;
+  }
   dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN, (unsigned)split);
   if (ak && bk) gemm_kernel<true, true><<<grid, GEMM_THREADS, 0, s>>>(g);
   else if (ak && !bk) gemm_kernel<true, false><<<grid, GEMM_THREADS, 0, s>>>(g);

@@ -3,7 +3,7 @@
     python -m paper_2408_15583_gb300.profile_case march [reps] [workload]  # one traced batch
     python -m paper_2408_15583_gb300.profile_case po [reps] [workload]     # PO over that batch
     python -m paper_2408_15583_gb300.profile_case splat [reps] [workload]  # incidence splats
-    python -m paper_2408_15583_gb300.profile_case unet [reps] [batch]     # U-Net training steps
+    python -m paper_2408_15583_gb300.profile_case unet [reps] [batch] [mma]  # U-Net training steps
 
 By default each case is the sphere workload's geometry (200k points, 8 fused
 512^2 views) with one batch of 8 incidence angles at 1024^2 rays and 64
@@ -33,6 +33,9 @@ def main(argv):
     case = argv[0] if argv else "march"
     reps = int(argv[1]) if len(argv) > 1 else 3
     if case == "unet":
+        if len(argv) > 3 and argv[3] == "mma":     # the mma.sync contraction kernel only
+            from paper_2408_15583_gb300 import _lib
+            _lib.load().pe_nn_gemm_path(1)
         return unet_case(reps, int(argv[2]) if len(argv) > 2 else 64)
     name = argv[2] if len(argv) > 2 else "sphere"
     wl = {"sphere": scenes.workload_sphere, "dihedral": scenes.workload_dihedral,

@@ -45,8 +45,9 @@ def rel(a, b):
     return float((a - b).norm() / b.norm().clamp(min=1e-30))
 
 
-@pytest.mark.parametrize("M,N,K", [(200, 96, 72), (64, 64, 32), (37, 5, 9), (96, 160, 20000)])
-def test_gemm_layouts(M, N, K):
+@pytest.mark.parametrize("M,N,K", [(200, 96, 72), (64, 64, 32), (37, 5, 9), (96, 160, 20000),
+                                   (520, 3, 32), (2000, 256, 576)])
+def test_gemm_layouts(M, N, K, gemm_path):
     o = ops()
     g = torch.Generator().manual_seed(M + N + K)
     A = bf(torch.randn(M, K, generator=g))
@@ -74,9 +75,18 @@ def test_gemm_layouts(M, N, K):
     assert rel(out2, ref) < 1e-5
 
 
+@pytest.fixture(params=[0, 1], ids=["tcgen05-where-it-applies", "mma.sync-only"])
+def gemm_path(request):
+    from paper_2408_15583_gb300 import _lib
+    lib = _lib.load()
+    prev = lib.pe_nn_gemm_path(request.param)
+    yield request.param
+    lib.pe_nn_gemm_path(prev)
+
+
 @pytest.mark.parametrize("ak,bk", [(True, True), (True, False), (False, True), (False, False)])
-@pytest.mark.parametrize("M,N,K", [(300, 200, 136), (100, 72, 5000)])
-def test_gemm_padded_strides(ak, bk, M, N, K):
+@pytest.mark.parametrize("M,N,K", [(300, 200, 136), (100, 72, 5000), (1000, 520, 72)])
+def test_gemm_padded_strides(ak, bk, M, N, K, gemm_path):
     """Every operand layout with padded leading dimensions: ragged M and N
     tiles, partial 16-byte rows along a contiguous M or N, and (K = 5000)
     split-K with a short last split."""
