@@ -373,8 +373,10 @@ pe_status pe_rcs_sweep(const pe_sweep *sweep, const float *pos_dev,
  * B(k,n) = B[k*sbk + n*sbn] (BF16, any strides: row- or column-major
  * operands), tensor-core products accumulated in FP32.  epi adds bias[n]
  * (FP32, nullable), R[m*ldr+n] (BF16 residual, nullable), beta * C_old (FP32
- * C only), then, if gelu, stores the pre-activation to Z (BF16, nullable) and
- * applies GELU (exact erf form).  C is FP32 (c_f32 = 1) or BF16 with row
+ * C only), then, if gelu = 1, stores the pre-activation to Z (BF16, nullable)
+ * and applies GELU (exact erf form); if gelu = 2, multiplies by GELU'(Z[m*ldz
+ * + n]) (Z read, required: the backward of GELU fused into the data
+ * gradient).  C is FP32 (c_f32 = 1) or BF16 with row
  * stride ldc.  Long K is split across blocks (deterministic split-K) using ws
  * of pe_nn_gemm_workspace() bytes. */
 size_t pe_nn_gemm_workspace(int32_t M, int32_t N, int64_t K);
@@ -424,6 +426,9 @@ pe_status pe_nn_layernorm_bwd(const void *dY, const void *X, const float *gamma,
 size_t pe_nn_colsum_workspace(int64_t M, int32_t N);
 pe_status pe_nn_colsum(const void *X, int64_t M, int32_t N, int64_t ld, float *out,
                        int32_t accumulate, void *ws, size_t ws_bytes, void *stream);
+
+/* dst [Cc][R] = transpose of src [R][Cc] (BF16, row-major, distinct buffers). */
+pe_status pe_nn_transpose(const void *src, int32_t R, int32_t Cc, void *dst, void *stream);
 
 /* dZ = dA * GELU'(Z) elementwise (BF16). */
 pe_status pe_nn_gelu_bwd(const void *dA, const void *Z, int64_t n, void *dZ, void *stream);

@@ -58,25 +58,6 @@ constexpr int GEMM_SMEM = STAGES * (A_STAGE + B_STAGE) * 2;
 constexpr int C_LD = TN + 4;  // FP32 staging of the output tile
 static_assert(TM * C_LD * 4 <= GEMM_SMEM, "epilogue staging fits the pipeline buffers");
 
-__device__ __forceinline__ float gelu_f(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
-}
-
-__device__ __forceinline__ void gemm_store(const pe_gemm_args &g, int m, int n, float v) {
-  if (m >= g.M || n >= g.N) return;
-  if (g.bias) v += g.bias[n];
-  if (g.R) v += b2f(g.R[(int64_t)m * g.ldr + n]);
-  if (g.c_f32 && g.beta != 0.0f) v += g.beta * static_cast<float *>(g.C)[(int64_t)m * g.ldc + n];
-  if (g.gelu) {
-    if (g.Z) g.Z[(int64_t)m * g.ldz + n] = f2b(v);
-    v = gelu_f(v);
-  }
-  if (g.c_f32)
-    static_cast<float *>(g.C)[(int64_t)m * g.ldc + n] = v;
-  else
-    static_cast<bf16 *>(g.C)[(int64_t)m * g.ldc + n] = f2b(v);
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -257,51 +238,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const pe_gemm_args g
       for (int e = 0; e < 8 && n + e < g.N; ++e) dst[e] = v[e];
       continue;
     }
-    if (n + 8 > g.N || !g.vec_c) {
-      for (int e = 0; e < 8 && n + e < g.N; ++e) gemm_store(g, m, n + e, v[e]);
-      continue;
-    }
-    if (g.bias) {
-#pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] += __ldg(g.bias + n + e);
-    }
-    if (g.R) {
-      const uint4 rv = *reinterpret_cast<const uint4 *>(g.R + (int64_t)m * g.ldr + n);
-      const bf162 *rp = reinterpret_cast<const bf162 *>(&rv);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(rp[e]);
-        v[2 * e] += f.x;
-        v[2 * e + 1] += f.y;
-      }
-    }
-    if (g.c_f32 && g.beta != 0.0f) {
-      const float *cp = static_cast<const float *>(g.C) + (int64_t)m * g.ldc + n;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] += g.beta * cp[e];
-    }
-    if (g.gelu) {
-      if (g.Z) {
-        uint4 zv;
-        bf162 *zp = reinterpret_cast<bf162 *>(&zv);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) zp[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-        *reinterpret_cast<uint4 *>(g.Z + (int64_t)m * g.ldz + n) = zv;
-      }
-#pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = gelu_f(v[e]);
-    }
-    if (g.c_f32) {
-      float4 *cp = reinterpret_cast<float4 *>(static_cast<float *>(g.C) + (int64_t)m * g.ldc + n);
-      cp[0] = make_float4(v[0], v[1], v[2], v[3]);
-      cp[1] = make_float4(v[4], v[5], v[6], v[7]);
-    } else {
-      uint4 ov;
-      bf162 *op = reinterpret_cast<bf162 *>(&ov);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) op[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-      *reinterpret_cast<uint4 *>(static_cast<bf16 *>(g.C) + (int64_t)m * g.ldc + n) = ov;
-    }
+    pe_gemm_store8(g, m, n, v);
   }
 }
 
@@ -321,7 +258,7 @@ __global__ void gemm_splitk_reduce(const pe_gemm_args g, int split) {
     float s = 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x];
-    gemm_store(g, (int)(t / g.N), (int)(t % g.N), s);
+    pe_gemm_store(g, (int)(t / g.N), (int)(t % g.N), s);
   }
 }
 
@@ -624,10 +561,7 @@ __global__ void gelu_bwd_kernel(const bf16 *__restrict__ dA, const bf16 *__restr
                                 bf16 *__restrict__ dZ) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float z = b2f(Z[i]);
-    float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
-    float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
-    dZ[i] = f2b(b2f(dA[i]) * (cdf + z * pdf));
+    dZ[i] = f2b(b2f(dA[i]) * pe_gelu_grad(b2f(Z[i])));
   }
 }
 
@@ -698,6 +632,22 @@ __global__ void copy_channels_kernel(const bf16 *__restrict__ src, int64_t lds, 
     float v = b2f(src[p * lds + soff + c]);
     bf16 *d = dst + p * ldd + doff + c;
     *d = f2b(accumulate ? b2f(*d) + v : v);
+  }
+}
+
+// dst[c][r] = src[r][c] (BF16), 32 x 32 tiles through shared memory.
+__global__ void transpose_kernel(const bf16 *__restrict__ src, int R, int Cc,
+                                 bf16 *__restrict__ dst) {
+  __shared__ bf16 t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < Cc) t[i][threadIdx.x] = src[(int64_t)r * Cc + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < Cc && r < R) dst[(int64_t)c * R + r] = t[threadIdx.x][i];
   }
 }
 
@@ -942,8 +892,8 @@ extern "C" pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, 
                                 int64_t ldr, void *Z, int64_t ldz, int32_t gelu, float alpha,
                                 float beta, void *ws, size_t ws_bytes, void *stream) {
   NN_CHECK_STREAM;
-  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C)
-    return pe_fail(PE_EINVAL, "pe_nn_gemm: bad sizes or null operands");
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || gelu < 0 || gelu > 2 || (gelu == 2 && !Z))
+    return pe_fail(PE_EINVAL, "pe_nn_gemm: bad sizes, null operands or gelu mode");
   pe_gemm_args g;
   memset(&g, 0, sizeof(g));
   g.M = M;
@@ -1211,6 +1161,18 @@ extern "C" pe_status pe_nn_copy_channels(const void *src, int64_t lds, int32_t s
                                                          static_cast<bf16 *>(dst), ldd, doff, P, C,
                                                          accumulate);
   PE_TRY_LAUNCH("copy_channels_kernel");
+  return PE_OK;
+}
+
+extern "C" pe_status pe_nn_transpose(const void *src, int32_t R, int32_t Cc, void *dst,
+                                     void *stream) {
+  NN_CHECK_STREAM;
+  if (!src || !dst || R <= 0 || Cc <= 0) return pe_fail(PE_EINVAL, "pe_nn_transpose: bad arguments");
+  if ((R + 31) / 32 > 65535) return pe_fail(PE_EINVAL, "pe_nn_transpose: too many rows");
+  dim3 grid((unsigned)((Cc + 31) / 32), (unsigned)((R + 31) / 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(static_cast<const bf16 *>(src), R, Cc,
+                                                static_cast<bf16 *>(dst));
+  PE_TRY_LAUNCH("transpose_kernel");
   return PE_OK;
 }
 

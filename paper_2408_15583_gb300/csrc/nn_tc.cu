@@ -3,17 +3,19 @@
 //   C[m][n] = epilogue(alpha * sum_k A[m][k] * B[n][k])
 // (A: activations [M][lda], B: weights [N][ldb], BF16, FP32 accumulation).
 //
-// One CTA computes a 128 x BN tile (BN = 64, 128 or 256) with four warps:
+// One CTA computes a 128 x BN tile (BN = 64, 128 or 256) with eight warps:
 //   warp 0 (one lane)  streams 128 x 64 and BN x 64 operand tiles into a
-//                      four-stage shared-memory ring with TMA (128-byte
-//                      swizzle, zero fill outside the matrices);
+//                      shared-memory ring of up to four stages with TMA
+//                      (128-byte swizzle, zero fill outside the matrices);
 //   warp 1 (one lane)  issues tcgen05.mma (kind::f16, M = 128, N = BN,
 //                      K = 16 per instruction) accumulating in tensor memory
 //                      and releases each stage with tcgen05.commit;
 //   warp 2             allocates and frees the BN tensor-memory columns;
-//   all four warps     read the accumulator back (tcgen05.ld, 32 rows per
-//                      warp) and apply the epilogue (bias, residual, GELU with
-//                      the pre-activation copy, FP32 or BF16 output).
+//   all eight warps    read the accumulator back (tcgen05.ld, 32 rows and
+//                      half the columns per warp) into shared memory, then
+//                      write coalesced rows through the epilogue (bias,
+//                      residual, GELU with the pre-activation copy or GELU',
+//                      FP32 or BF16 output).
 // Every wait on an mbarrier has an iteration limit; on expiry the kernel sets
 // the library's timeout flag, skips its stores, waits (again bounded) for its
 // own copies and products still in flight and frees its tensor memory.
@@ -30,7 +32,7 @@ namespace {
 typedef __nv_bfloat16 bf16;
 typedef __nv_bfloat162 bf162;
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 128;
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 256;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <int BN>
@@ -38,7 +40,14 @@ struct tc_cfg {
   static constexpr int A_BYTES = TC_BM * TC_BK * 2;  // 16 KB, 1024-byte multiple
   static constexpr int B_BYTES = BN * TC_BK * 2;     // 8/16/32 KB
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int SMEM = TC_STAGES * STAGE + 1024 /* barriers */ + 1024 /* alignment */;
+  static constexpr int C_LD = BN + 4;                        // FP32 staging row (floats)
+  static constexpr int C_BYTES = TC_BM * C_LD * 4;
+  // ring of `stages` operand stages, reused for the FP32 output tile; then
+  // the barriers; plus slack to align the base to 1024 bytes
+  static int smem(int stages) {
+    const int ring = stages * STAGE > C_BYTES ? stages * STAGE : C_BYTES;
+    return ((ring + 1023) / 1024) * 1024 + 1024 + 1024;
+  }
   // instruction descriptor, kind::f16: D = F32 (bits 4-5), A = B = BF16
   // (bits 7-9, 10-12), both K-major (bits 15, 16 clear), N >> 3 (bits
   // 17-22), M >> 4 (bits 24-28)
@@ -130,95 +139,17 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu_tc(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
-}
-
-// Epilogue of 16 consecutive outputs (m, n .. n+15) of one row.
-__device__ __forceinline__ void store16(const pe_gemm_args &g, int m, int n, float (&v)[16]) {
-  if (m >= g.M) return;
-#pragma unroll
-  for (int e = 0; e < 16; ++e) v[e] *= g.alpha;
-  const bool full = n + 16 <= g.N && g.vec_c;
-  if (!full) {
-    for (int e = 0; e < 16 && n + e < g.N; ++e) {
-      float x = v[e];
-      if (g.bias) x += g.bias[n + e];
-      if (g.R) x += __bfloat162float(g.R[(int64_t)m * g.ldr + n + e]);
-      if (g.c_f32 && g.beta != 0.0f) x += g.beta * static_cast<float *>(g.C)[(int64_t)m * g.ldc + n + e];
-      if (g.gelu) {
-        if (g.Z) g.Z[(int64_t)m * g.ldz + n + e] = __float2bfloat16_rn(x);
-        x = gelu_tc(x);
-      }
-      if (g.c_f32)
-        static_cast<float *>(g.C)[(int64_t)m * g.ldc + n + e] = x;
-      else
-        static_cast<bf16 *>(g.C)[(int64_t)m * g.ldc + n + e] = __float2bfloat16_rn(x);
-    }
-    return;
-  }
-  if (g.bias) {
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] += __ldg(g.bias + n + e);
-  }
-  if (g.R) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint4 rv = *reinterpret_cast<const uint4 *>(g.R + (int64_t)m * g.ldr + n + 8 * h);
-      const bf162 *rp = reinterpret_cast<const bf162 *>(&rv);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(rp[e]);
-        v[8 * h + 2 * e] += f.x;
-        v[8 * h + 2 * e + 1] += f.y;
-      }
-    }
-  }
-  if (g.c_f32 && g.beta != 0.0f) {
-    const float *cp = static_cast<const float *>(g.C) + (int64_t)m * g.ldc + n;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] += g.beta * cp[e];
-  }
-  if (g.gelu) {
-    if (g.Z) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uint4 zv;
-        bf162 *zp = reinterpret_cast<bf162 *>(&zv);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) zp[e] = __floats2bfloat162_rn(v[8 * h + 2 * e], v[8 * h + 2 * e + 1]);
-        *reinterpret_cast<uint4 *>(g.Z + (int64_t)m * g.ldz + n + 8 * h) = zv;
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = gelu_tc(v[e]);
-  }
-  if (g.c_f32) {
-    float4 *cp = reinterpret_cast<float4 *>(static_cast<float *>(g.C) + (int64_t)m * g.ldc + n);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  } else {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      uint4 ov;
-      bf162 *op = reinterpret_cast<bf162 *>(&ov);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) op[e] = __floats2bfloat162_rn(v[8 * h + 2 * e], v[8 * h + 2 * e + 1]);
-      *reinterpret_cast<uint4 *>(static_cast<bf16 *>(g.C) + (int64_t)m * g.ldc + n + 8 * h) = ov;
-    }
-  }
-}
-
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const pe_gemm_args g, unsigned int *err) {
+                   const pe_gemm_args g, int stages, unsigned int *err) {
   using cfg = tc_cfg<BN>;
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   uint8_t *base = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t *full = reinterpret_cast<uint64_t *>(base + TC_STAGES * cfg::STAGE);
+  const int ring = stages * cfg::STAGE > cfg::C_BYTES ? stages * cfg::STAGE : cfg::C_BYTES;
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + ((ring + 1023) / 1024) * 1024);
   uint64_t *empty = full + TC_STAGES;
   uint64_t *accum = empty + TC_STAGES;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accum + 1);
@@ -230,7 +161,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
@@ -254,8 +185,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   int issued = 0;  // k-blocks whose loads were issued (producer lane)
   if (warp == 0 && lane == 0) {
     for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+      const int s = kb % stages;
+      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
       if (!mbar_wait(empty + s, ph ^ 1u)) {
         atomicOr(&s_fail, 1);
         break;
@@ -269,8 +200,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1 && lane == 0) {
     int kb = 0;
     for (; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+      const int s = kb % stages;
+      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
       if (!mbar_wait(full + s, ph)) {
         atomicOr(&s_fail, 1);
         break;
@@ -286,20 +217,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_commit(accum);  // all products issued above are complete
   }
-  // epilogue: every warp reads its 32 accumulator rows
+  // epilogue: the accumulator goes through shared memory (the operand ring
+  // is free once every product has completed), then all threads write
+  // coalesced rows.  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+  // (its rows) for half of the columns.
   const bool ready = mbar_wait(accum, 0u);
   if (!ready) atomicOr(&s_fail, 1);
   tc_fence_after();
   __syncwarp();
   // a warp-uniform decision: tcgen05.ld needs the whole warp
   const bool ok = __all_sync(0xffffffffu, ready && !s_fail);
+  float *Cs = reinterpret_cast<float *>(base);
   if (ok) {
-    const int m = m0 + warp * 32 + lane;
-    const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c = 0; c < BN; c += 16) {
+    const int quad = warp & 3, half = warp >> 2;
+    const int r = quad * 32 + lane;
+    const uint32_t row = tmem + ((uint32_t)(quad * 32) << 16);
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
       float v[16];
       tc_ld16(row + (uint32_t)c, v);
-      if (n0 + c < g.N) store16(g, m, n0 + c, v);
+      float4 *dst = reinterpret_cast<float4 *>(Cs + r * cfg::C_LD + c);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        dst[q] = make_float4(v[4 * q] * g.alpha, v[4 * q + 1] * g.alpha, v[4 * q + 2] * g.alpha,
+                             v[4 * q + 3] * g.alpha);
+    }
+  }
+  __syncthreads();
+  if (!s_fail) {
+    for (int c = threadIdx.x; c < TC_BM * BN / 8; c += TC_THREADS) {
+      const int r = c / (BN / 8), cc = (c % (BN / 8)) * 8;
+      const int m = m0 + r, n = n0 + cc;
+      if (m >= g.M || n >= g.N) continue;
+      float v[8];
+      const float4 a = *reinterpret_cast<const float4 *>(Cs + r * cfg::C_LD + cc);
+      const float4 b = *reinterpret_cast<const float4 *>(Cs + r * cfg::C_LD + cc + 4);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      pe_gemm_store8(g, m, n, v);
     }
   }
   __syncthreads();
@@ -311,8 +265,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       atomicOr(err, PE_ERR_TIMEOUT);
     }
     if (warp == 0 && lane == 0) {
-      for (int kb = (issued > TC_STAGES ? issued - TC_STAGES : 0); kb < issued; ++kb)
-        mbar_wait(full + kb % TC_STAGES, (uint32_t)(kb / TC_STAGES) & 1u);
+      for (int kb = (issued > stages ? issued - stages : 0); kb < issued; ++kb)
+        mbar_wait(full + kb % stages, (uint32_t)(kb / stages) & 1u);
     }
     if (warp == 1 && lane == 0) mbar_wait(accum, 0u);
   }
@@ -366,14 +320,20 @@ pe_status launch_bn(const pe_gemm_args &g, cudaStream_t s) {
   CUtensorMap ma, mb;
   if (!make_map(&ma, g.A, g.M, g.K, g.sam, TC_BM) || !make_map(&mb, g.B, g.N, g.K, g.sbn, BN))
     return PE_EUNSUPPORTED;  // the caller takes the other kernel
+  // as many stages as K-blocks, up to four; the shared memory this takes
+  // also caps the CTAs per SM so their tensor memory (BN columns each)
+  // stays within the SM's 512 columns
+  const int nk = (int)((g.K + TC_BK - 1) / TC_BK);
+  const int stages = nk < TC_STAGES ? nk : TC_STAGES;
+  const int smem = cfg::smem(stages);
   static bool attr = false;
   if (!attr) {
     PE_TRY_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     cfg::SMEM));
+                                     cfg::smem(TC_STAGES)));
     attr = true;
   }
   dim3 grid((unsigned)((g.M + TC_BM - 1) / TC_BM), (unsigned)((g.N + BN - 1) / BN));
-  gemm_tc_kernel<BN><<<grid, TC_THREADS, cfg::SMEM, s>>>(ma, mb, g, pe_err_word());
+  gemm_tc_kernel<BN><<<grid, TC_THREADS, smem, s>>>(ma, mb, g, stages, pe_err_word());
   PE_TRY_LAUNCH("gemm_tc_kernel");
   return PE_OK;
 }

@@ -56,12 +56,13 @@ class Ops:
 
     # C[m,n] = sum_k A(m,k) B(k,n) with explicit element strides
     def gemm(self, M, N, K, A, sam, sak, B, sbk, sbn, Cout, ldc, bias=None, R=None, ldr=0,
-             Z=None, ldz=0, gelu=False, alpha=1.0, beta=0.0):
+             Z=None, ldz=0, gelu=False, alpha=1.0, beta=0.0, dgelu=False):
         nb = self.lib.pe_nn_gemm_workspace(M, N, K)
         ws = self.ws(nb)
         check(self.lib.pe_nn_gemm(M, N, K, _p(A), sam, sak, _p(B), sbk, sbn, _p(Cout), ldc,
                                   1 if Cout.dtype == F32 else 0, _p(bias), _p(R), ldr, _p(Z), ldz,
-                                  1 if gelu else 0, alpha, beta, _p(ws), ws.numel(), self.s()),
+                                  2 if dgelu else (1 if gelu else 0), alpha, beta, _p(ws),
+                                  ws.numel(), self.s()),
               "pe_nn_gemm")
 
     # y[P,N] = x[P,K] . W[N,K]^T (+ bias, + residual, gelu)
@@ -71,12 +72,19 @@ class Ops:
         self.gemm(P, N, K, x, ldx, 1, W, 1, K, out, ldo, bias=bias, R=R, ldr=ldr, Z=Z,
                   ldz=N, gelu=gelu)
 
-    def linear_bwd(self, dy, x, ldx, W, dx, ldd, dW, db, need_dx=True):
-        """dy [P,N] (BF16, contiguous), x [P,K] with row stride ldx."""
+    def linear_bwd(self, dy, x, ldx, W, dx, ldd, dW, db, need_dx=True, gelu_z=None):
+        """dy [P,N] (BF16, contiguous), x [P,K] with row stride ldx.  The data
+        gradient reads W through its transpose, so both of its operands are
+        K-contiguous (the layout of the tensor-core kernel); with gelu_z it
+        is multiplied by GELU'(gelu_z) in the epilogue (the backward of a
+        GELU applied to this layer's input)."""
         P, N = dy.shape
         K = W.shape[1]
         if need_dx:
-            self.gemm(P, K, N, dy, N, 1, W, K, 1, dx, ldd)
+            Wt = torch.empty(K, N, dtype=W.dtype, device=self.dev)
+            check(self.lib.pe_nn_transpose(_p(W), N, K, _p(Wt), self.s()), "pe_nn_transpose")
+            self.gemm(P, K, N, dy, N, 1, Wt, 1, N, dx, ldd, Z=gelu_z, ldz=K,
+                      dgelu=gelu_z is not None)
         self.gemm(N, K, P, dy, 1, N, x, ldx, 1, dW, K)
         self.colsum(dy, P, N, N, db)
 
@@ -209,11 +217,9 @@ class UNet:
         o = self.ops
         p, (x, a, bn, mean, rstd, z1, h, B, H, W, Cc) = rec
         P = B * H * W
-        dh = self._empty(P, 4 * Cc)
-        o.linear_bwd(dy, h, 4 * Cc, self.pb(p + ".pw2.w"), dh, 4 * Cc, self.g(p + ".pw2.w"),
-                     self.g(p + ".pw2.b"))
-        dz1 = self._empty(P, 4 * Cc)
-        o.gelu_bwd(dh, z1, dz1)
+        dz1 = self._empty(P, 4 * Cc)          # dL/dz1 = (dy . W2) * GELU'(z1), one GEMM
+        o.linear_bwd(dy, h, 4 * Cc, self.pb(p + ".pw2.w"), dz1, 4 * Cc, self.g(p + ".pw2.w"),
+                     self.g(p + ".pw2.b"), gelu_z=z1)
         dbn = self._empty(P, Cc)
         o.linear_bwd(dz1, bn, Cc, self.pb(p + ".pw1.w"), dbn, Cc, self.g(p + ".pw1.w"),
                      self.g(p + ".pw1.b"))

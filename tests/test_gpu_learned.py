@@ -68,6 +68,13 @@ def test_gemm_layouts(M, N, K, gemm_path):
     pre = ref + R.double()
     assert rel(Z, pre) < 1e-2
     assert rel(out16, torch.nn.functional.gelu(pre)) < 1e-2
+    # data gradient through a GELU: (A B) * GELU'(Z), Z read in the epilogue
+    Zin = bf(torch.randn(M, N, generator=g))
+    outg = torch.empty(M, N, dtype=torch.bfloat16, device=DEV)
+    o.gemm(M, N, K, A.to(DEV), K, 1, Bt, 1, K, outg, N, Z=Zin.to(DEV), ldz=N, dgelu=True)
+    z = Zin.double()
+    dg = 0.5 * (1 + torch.erf(z / math.sqrt(2))) + z * torch.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+    assert rel(outg, ref * dg) < 1e-2
     # TN: A given as [K,M] (column-major A)
     At = A.t().contiguous().to(DEV)
     out2 = torch.empty(M, N, dtype=torch.float32, device=DEV)
