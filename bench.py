@@ -254,10 +254,12 @@ def run_gpu(args, rank, world, local_rank):
         api.aggregate_views(gv, g["nd"], g["mask"], prm, geom=geom)
 
     geom_ms = _time(_geometry)
+    # surfel radius (8 nearest) and PCA normal (16 nearest) of every point
+    pattr_ms = _time(lambda: api.point_attributes(pos, 8, 16, nrm))
     sweep_ms = _time(lambda: api.rcs_sweep(sargs, pos, nrm, rad, geom, prm, ws=ws, E=E, sigma=sig))
     api.stream_check()
-    phases = {"gfb_views_and_fusion_ms": geom_ms, "sweep_ms": sweep_ms,
-              "sweep_ms_per_angle": sweep_ms / A}
+    phases = {"point_attributes_ms": pattr_ms, "gfb_views_and_fusion_ms": geom_ms,
+              "sweep_ms": sweep_ms, "sweep_ms_per_angle": sweep_ms / A}
 
     # roofline of the dominant kernel (march_kernel, timed in the steps above)
     roof = roofline_march(march_ms, march_queries / march_launches_per_step)

@@ -145,6 +145,25 @@ typedef struct {
  * that view's occupied cells). */
 #define PE_STATS_WORDS 8
 
+/* Surfel attributes (the per-point inputs of Alg. 1 in surfel mode; the
+ * paper's splatting baseline takes a radius from the point spacing and
+ * normals from local PCA, Sec. IV-A), computed on the GPU:
+ *   radius[i] = mean distance from p_i to its k_r nearest other points;
+ *   normal[i] = unit eigenvector of the smallest eigenvalue of the
+ *               covariance of the k_n nearest points (p_i included), turned
+ *               to agree with ref_nrm[i] (nullable) or else to point away
+ *               from the bounding-box centre.
+ * pos_dev: FP32 [n][3]; radius_dev [n], normal_dev [n][3] (FP32, either may
+ * be null).  Neighbours are exact: ordered by the FP32 squared distance
+ * (dx*dx + dy*dy) + dz*dz, ties by index; distances summed in FP64 in that
+ * order; mean and covariance in FP64.  Requires 1 <= k_r <= 31, 3 <= k_n <=
+ * 32, n >= max(k_r + 1, k_n), n < 2^32; ws of
+ * pe_point_attributes_workspace(n) bytes (256-byte aligned). */
+size_t pe_point_attributes_workspace(int64_t n_points);
+pe_status pe_point_attributes(const float *pos_dev, int64_t n_points, int32_t k_r, int32_t k_n,
+                              const float *ref_nrm_dev, void *ws, size_t ws_bytes,
+                              float *radius_dev, float *normal_dev, void *stream);
+
 /* Library version of this header's ABI. */
 int pe_abi_version(void);
 

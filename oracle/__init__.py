@@ -79,6 +79,7 @@ def lib():
                                   P, P, P, P, P, P, P, P, P]
         _lib.or_po_field.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int, P,
                                      C.c_int, P, P]
+        _lib.or_knn.argtypes = [P, C.c_int64, P, C.c_int64, C.c_int, P, P]
     return _lib
 
 
@@ -359,3 +360,67 @@ def rcs_sweep(scene, sweep, splats: Optional[Splats], eps: float, r_ov: float,
         trs.append(tr)
         vs.append(v)
     return SweepResult(np.array(Es), np.array(sig), trs, vs)
+
+
+# ----------------------------------------------------------------------------
+# Surfel attributes: radius from the k nearest other points (mean distance)
+# and the PCA normal of the k nearest points (the smallest principal axis),
+# the per-point inputs of Alg. 1 in surfel mode.
+# ----------------------------------------------------------------------------
+
+def knn(pos: np.ndarray, K: int, queries=None):
+    """Brute-force K nearest points (itself included) of every point, or of
+    the points listed in `queries`: indices [nq][K] and FP32 squared
+    distances, ordered by (d2, index)."""
+    p = np.ascontiguousarray(pos, dtype=np.float32)
+    n = p.shape[0]
+    q = None if queries is None else np.ascontiguousarray(queries, dtype=np.int64)
+    nq = n if q is None else q.shape[0]
+    idx = np.empty((nq, K), np.int64)
+    d2 = np.empty((nq, K), np.float32)
+    lib().or_knn(_p(p), n, _p(q), nq, K, _p(idx), _p(d2))
+    return idx, d2
+
+
+def knn_radius(idx: np.ndarray, d2: np.ndarray, self_idx: np.ndarray, k_r: int) -> np.ndarray:
+    """Mean distance to the first k_r neighbours other than the point itself
+    (square roots and sum in FP64 in list order, rounded once to FP32)."""
+    out = np.empty(idx.shape[0], np.float32)
+    for r in range(idx.shape[0]):
+        s, used = 0.0, 0
+        for e in range(idx.shape[1]):
+            if used == k_r:
+                break
+            if idx[r, e] == self_idx[r]:
+                continue
+            s += math.sqrt(float(d2[r, e]))
+            used += 1
+        out[r] = np.float32(s / k_r)
+    return out
+
+
+def point_attributes(pos: np.ndarray, k_r: int = 8, k_n: int = 16, ref=None):
+    """radius[i] = mean distance to the k_r nearest other points (square
+    roots and sum in FP64, in neighbour order, rounded once to FP32);
+    normal[i] = unit eigenvector of the smallest eigenvalue of the FP64
+    covariance of the k_n nearest points (itself included), turned to agree
+    with ref[i] if given, else to point away from the bounding-box centre.
+    Also returns the three eigenvalues (ascending) per point."""
+    p = np.ascontiguousarray(pos, dtype=np.float32)
+    K = max(k_r + 1, k_n)
+    idx, d2 = knn(p, K)
+    n = p.shape[0]
+    rad = knn_radius(idx, d2, np.arange(n), k_r)
+    nb = p.astype(np.float64)[idx[:, :k_n]]                 # [n, k_n, 3]
+    m = nb.sum(axis=1) / k_n
+    c = nb - m[:, None, :]
+    cov = np.einsum("nki,nkj->nij", c, c)
+    w, vec = np.linalg.eigh(cov)
+    nrm = vec[:, :, 0]
+    if ref is not None:
+        flip = (nrm * np.asarray(ref, np.float64)).sum(axis=1) < 0
+    else:
+        lo, hi = p.astype(np.float64).min(axis=0), p.astype(np.float64).max(axis=0)
+        flip = (nrm * (p.astype(np.float64) - 0.5 * (lo + hi))).sum(axis=1) < 0
+    nrm[flip] *= -1.0
+    return rad, nrm, w, idx

@@ -179,3 +179,40 @@ void or_po_field(int64_t nr, const double *p, const double *n, const double *k,
     }
   }
 }
+
+/* ---------------------------------------------------------------------------
+ * Surfel attributes (the inputs of Alg. 1 in surfel mode): the K nearest
+ * points of every point by brute force.  Squared distance in FP32 as
+ * (dx*dx + dy*dy) + dz*dz with dx = p_j - p_i; neighbours ordered by
+ * (squared distance, index); the point itself is included (distance 0).
+ * For the points queries[0..nq) (all points, nq = n, when queries is null);
+ * out_idx / out_d2: [nq][K].
+ * ------------------------------------------------------------------------- */
+void or_knn(const float *pos, int64_t n, const int64_t *queries, int64_t nq, int K,
+            int64_t *out_idx, float *out_d2) {
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t qi = 0; qi < nq; ++qi) {
+    const int64_t i = queries ? queries[qi] : qi;
+    float bd[64];
+    int64_t bi[64];
+    int cnt = 0;
+    const float qx = pos[3 * i], qy = pos[3 * i + 1], qz = pos[3 * i + 2];
+    for (int64_t j = 0; j < n; ++j) {
+      float dx = pos[3 * j] - qx, dy = pos[3 * j + 1] - qy, dz = pos[3 * j + 2] - qz;
+      float d2 = (dx * dx + dy * dy) + dz * dz;
+      if (cnt == K && !(d2 < bd[K - 1] || (d2 == bd[K - 1] && j < bi[K - 1]))) continue;
+      int at = cnt < K ? cnt++ : K - 1;
+      while (at > 0 && (bd[at - 1] > d2 || (bd[at - 1] == d2 && bi[at - 1] > j))) {
+        bd[at] = bd[at - 1];
+        bi[at] = bi[at - 1];
+        --at;
+      }
+      bd[at] = d2;
+      bi[at] = j;
+    }
+    for (int e = 0; e < K; ++e) {
+      out_idx[qi * K + e] = e < cnt ? bi[e] : -1;
+      out_d2[qi * K + e] = e < cnt ? bd[e] : INFINITY;
+    }
+  }
+}

@@ -76,6 +76,9 @@ SIGNATURES = {
     # a8
     "pe_nn_gemm_workspace": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int64]),
     "pe_nn_gemm_path": (C.c_int32, [C.c_int32]),
+    "pe_point_attributes_workspace": (C.c_size_t, [C.c_int64]),
+    "pe_point_attributes": (C.c_int, [P, C.c_int64, C.c_int32, C.c_int32, P, P, C.c_size_t, P, P,
+                                      P]),
     "pe_nn_transpose": (C.c_int, [P, C.c_int32, C.c_int32, P, P]),
     "pe_nn_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, P, C.c_int64, C.c_int64, P,
                              C.c_int64, C.c_int64, P, C.c_int64, C.c_int32, P, P, C.c_int64, P,

@@ -18,6 +18,7 @@ from ._lib import PeGeom, PeHits, PeParams, PeSweep, PeView, check
 
 __all__ = ["view_from_angles", "make_params", "build_gfb", "aggregate_views", "alloc_hits",
            "trace_bounces", "po_field", "rcs_sweep", "stream_check", "Geom", "Hits",
+           "point_attributes",
            "views_to_array", "workspace"]
 
 
@@ -133,6 +134,24 @@ class Geom:
         f = self.blob.view(torch.float32)
         nf_off = ((tot * 16 + 255) // 256) * 256 // 4
         return f[:tot * 4].view(tot, 4), f[nf_off:nf_off + tot * 4].view(tot, 4)
+
+
+def point_attributes(pos: torch.Tensor, k_r: int = 8, k_n: int = 16,
+                     ref: Optional[torch.Tensor] = None, radius: bool = True, normal: bool = True,
+                     stream=None):
+    """Surfel radius (mean distance to the k_r nearest other points) and PCA
+    normal (k_n nearest points) of every point, on the GPU
+    (``pe_point_attributes``).  Returns (radius [n] or None, normal [n,3] or
+    None), FP32 on pos's device."""
+    lib = _lib()
+    n = int(pos.shape[0])
+    dev = pos.device
+    ws = workspace(lib.pe_point_attributes_workspace(n), dev)
+    r = torch.empty(n, dtype=torch.float32, device=dev) if radius else None
+    nr = torch.empty(n, 3, dtype=torch.float32, device=dev) if normal else None
+    check(lib.pe_point_attributes(_p(pos), n, k_r, k_n, _p(ref), _p(ws), ws.numel(), _p(r), _p(nr),
+                                  _s(stream)), "pe_point_attributes")
+    return r, nr
 
 
 def alloc_geom(views: Sequence[PeView], device) -> Geom:

@@ -437,6 +437,21 @@ agg_ws carve_agg(pe_carve &c, int64_t total_pix, int G) {
 
 }  // namespace
 
+// out[i] = sum of in[0..i) for i in [0, n] (n + 1 entries; n <= 2^24) with
+// tile scratch of (n + 4095) / 4096 uint32.
+pe_status pe_exclusive_scan_u32(const uint32_t *in, int64_t n, uint32_t *tile, uint32_t *out,
+                                cudaStream_t s) {
+  const int64_t n_tiles = (n + kScanTile - 1) / kScanTile;
+  if (n < 1 || n_tiles > kScanTile) return pe_fail(PE_EUNSUPPORTED, "scan: too many entries");
+  scan_tile_sums<<<(int)n_tiles, kScanThreads, 0, s>>>(in, n, tile);
+  PE_TRY_LAUNCH("scan_tile_sums");
+  scan_tile_offsets<<<1, kScanThreads, 0, s>>>(tile, n_tiles);
+  PE_TRY_LAUNCH("scan_tile_offsets");
+  scan_apply<<<(int)n_tiles, kScanThreads, 0, s>>>(in, n, tile, out);
+  PE_TRY_LAUNCH("scan_apply");
+  return PE_OK;
+}
+
 extern "C" size_t pe_aggregate_workspace(int32_t n_views, const pe_view *views,
                                          int32_t fuse_grid) {
   pe_geom_layout L;

@@ -97,6 +97,11 @@ struct pe_geom_layout {
 
 // Fills everything but the pointers; returns false on bad views.
 bool pe_make_layout(int32_t nv, const pe_view *views, pe_geom_layout *L);
+
+// Exclusive scan of n uint32 into out[0..n] (out[n] = total), n <= 2^24;
+// tile holds (n + 4095) / 4096 entries of scratch.
+pe_status pe_exclusive_scan_u32(const uint32_t *in, int64_t n, uint32_t *tile, uint32_t *out,
+                                cudaStream_t s);
 // Blob byte offsets of the arrays for a layout.
 void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
                        size_t *off_nodes, size_t *off_vmask, size_t *total);

@@ -546,3 +546,51 @@ def test_golden_closed_forms():
                "sphere": lambda r: math.pi * r["a"] ** 2,
                "trihedral": lambda r: 12 * math.pi * r["a"] ** 4 / lam ** 2}[row["kind"]](row)
         assert abs(10 * math.log10(val) - row["dbsm"]) < 0.01, row
+
+
+# ----------------------------------------------------------------------------
+# surfel attributes (radius from the k nearest points, PCA normals)
+# ----------------------------------------------------------------------------
+
+def test_knn_radius_and_normal_on_a_square_lattice():
+    # 9 x 9 lattice of pitch 1/8 in z = 0: an interior point's 8 nearest
+    # other points are 4 at 1/8 and 4 at sqrt(2)/8, so R = (1 + sqrt 2)/16;
+    # the plane's normal is +z (turned to agree with the reference)
+    a = 0.125
+    g = np.stack(np.meshgrid(np.arange(9), np.arange(9), indexing="ij"), -1).reshape(-1, 2) * a
+    pos = np.concatenate([g, np.zeros((81, 1))], axis=1).astype(np.float32)
+    ref = np.tile([0.0, 0.0, 1.0], (81, 1))
+    r, n, w, _ = oracle.point_attributes(pos, 8, 9, ref=ref)
+    inner = [i for i in range(81) if 2 <= i // 9 <= 6 and 2 <= i % 9 <= 6]
+    expect = np.float32(a * (1.0 + math.sqrt(2.0)) / 2.0)
+    assert np.all(np.abs(r[inner] - expect) <= 1e-7 * expect)
+    assert np.allclose(n, ref, atol=1e-12)
+    assert np.allclose(w[:, 0], 0.0, atol=1e-12)
+
+
+def test_knn_distances_match_an_independent_kd_tree():
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(4)
+    pos = rng.random((2000, 3)).astype(np.float32)
+    idx, d2 = oracle.knn(pos, 12)
+    dk, _ = cKDTree(pos.astype(np.float64)).query(pos.astype(np.float64), k=12)
+    assert np.allclose(np.sqrt(d2.astype(np.float64)), dk, rtol=2e-6, atol=1e-7)
+    assert np.all(idx[:, 0] == np.arange(2000))        # itself first (distance 0)
+
+
+def test_pca_normal_of_a_tilted_plane_and_duplicates():
+    rng = np.random.default_rng(5)
+    nrm = np.array([1.0, 2.0, 2.0]) / 3.0
+    t1 = np.array([2.0, -1.0, 0.0]) / math.sqrt(5.0)
+    t2 = np.cross(nrm, t1)
+    uv = rng.random((3000, 2)) * 4.0 - 2.0
+    pos = (uv[:, :1] * t1 + uv[:, 1:] * t2 + 0.5).astype(np.float32)
+    _, n, _, _ = oracle.point_attributes(pos, 8, 16, ref=np.tile(nrm, (3000, 1)))
+    assert np.max(np.arccos(np.clip(n @ nrm, -1, 1))) < 2e-5
+    # a duplicated point: its twin is a neighbour at distance 0; only the
+    # point itself is left out of its radius
+    dup = np.concatenate([pos[:50], pos[:1]]).astype(np.float32)
+    r, _, _, idx = oracle.point_attributes(dup, 4, 8)
+    d = np.sqrt(((dup[:, None, :].astype(np.float64) - dup[None]) ** 2).sum(-1))
+    d0 = np.sort(np.delete(d[0], 0))[:4]
+    assert d0[0] == 0.0 and abs(r[0] - d0.mean()) < 1e-6 * max(d0.mean(), 1e-9)
