@@ -305,7 +305,10 @@ __global__ void fuse_segment_kernel(const __grid_constant__ pe_geom_layout L,
 // Leaf boxes: bounds of the owned splats' spheres in the view's (u, v, d)
 // frame, padded for rounding.  Empty tiles get lo = +inf, hi = -inf.
 // Leaf boxes; a leaf's lo.w holds the bit pattern of its occupancy mask
-// (bit jj * PE_LEAF + ii set when slot (ii, jj) holds a splat).
+// (bit jj * PE_LEAF + ii set when slot (ii, jj) holds a splat) and hi.w its
+// reach: the largest pixel distance from a slot to its splat's projected
+// centre plus the splat's (padded) radius in pixels, so that a ray hitting a
+// splat passes within `reach` pixels of the splat's slot.
 static_assert(PE_LEAF * PE_LEAF <= 32, "leaf occupancy mask is one 32-bit word");
 __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, int v,
                                     float4 *__restrict__ nodes) {
@@ -317,6 +320,8 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
     int tx = t % tw, ty = t / tw;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     uint32_t occ = 0;
+    float reach = 0.0f;
+    const float inv_pitch = 1.0f / V.pitch;
     for (int jj = 0; jj < PE_LEAF; ++jj) {
       int j = ty * PE_LEAF + jj;
       if (j >= V.H) break;
@@ -331,6 +336,10 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
                       qx * V.v[0] + qy * V.v[1] + qz * V.v[2],
                       qx * V.d[0] + qy * V.d[1] + qz * V.d[2]};
         float r = c.w * 1.000001f + pad;
+        // reach: pixel distance (Chebyshev) from this slot to the splat's
+        // projected centre plus its radius in pixels
+        const float ci = a[0] * inv_pitch + 0.5f * V.W - 0.5f, cj = a[1] * inv_pitch + 0.5f * V.H - 0.5f;
+        reach = fmaxf(reach, fmaxf(fabsf(ci - (float)i), fabsf(cj - (float)j)) + r * inv_pitch);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           lo[k] = fminf(lo[k], a[k] - r);
@@ -340,7 +349,7 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
     }
     int64_t nid = L.node_off[v][0] + t;
     nodes[2 * nid] = make_float4(lo[0], lo[1], lo[2], __uint_as_float(occ));
-    nodes[2 * nid + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    nodes[2 * nid + 1] = make_float4(hi[0], hi[1], hi[2], reach);
   }
 }
 
@@ -364,6 +373,7 @@ __global__ void pyramid_up_kernel(const __grid_constant__ pe_geom_layout L, int 
         hi.x = fmaxf(hi.x, b.x);
         hi.y = fmaxf(hi.y, b.y);
         hi.z = fmaxf(hi.z, b.z);
+        hi.w = fmaxf(hi.w, b.w);  // largest reach below
       }
     int64_t nid = L.node_off[v][l] + t;
     nodes[2 * nid] = lo;

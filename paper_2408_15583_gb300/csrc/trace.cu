@@ -231,10 +231,58 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       float lim = pe_add(S.tb, r_ov);
       return ANY ? T.y : fminf(fmaf(fabsf(lim), 1e-6f, lim) + pad, T.y);
     };
-    // root
+    // Start node: the lowest node holding every leaf slot that a lane's
+    // ray can reach in this view.  A ray hitting a splat passes within the
+    // view's reach (root hi.w, in pixels) of the splat's slot, and the hit
+    // lies on the lane's stretch [t0, T.y] of the ray, so the slots lie in
+    // the projection of that stretch widened by the reach.  Lanes whose
+    // stretch is unbounded keep the root.
+    const int64_t rid = L.node_off[v][top];
+    const float4 rlo = __ldg(L.nodes + 2 * rid), rhi = __ldg(L.nodes + 2 * rid + 1);
+    int ls = top, sx = 0, sy = 0;
     {
-      int64_t nid = L.node_off[v][top];
-      float4 lo = __ldg(L.nodes + 2 * nid), hi = __ldg(L.nodes + 2 * nid + 1);
+      const bool lv = active && !(ANY && hit_any) && T.x <= T.y;
+      const bool fin = isfinite(t0) && isfinite(T.y);
+      if (top > 0 && __all_sync(FULL, !lv || fin)) {
+        int lx0 = 0x7fffffff, ly0 = 0x7fffffff, lx1 = -1, ly1 = -1;
+        if (lv) {
+          const float il = 1.0f / V.pitch, reach = rhi.w + 2.0f;
+          const float au = q.x * V.u[0] + q.y * V.u[1] + q.z * V.u[2];
+          const float av = q.x * V.v[0] + q.y * V.v[1] + q.z * V.v[2];
+          const float du = d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2];
+          const float dv = d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2];
+          const float cu = 0.5f * V.W - 0.5f, cv = 0.5f * V.H - 0.5f;
+          const float u0 = fmaf(t0, du, au) * il + cu, u1 = fmaf(T.y, du, au) * il + cu;
+          const float v0 = fmaf(t0, dv, av) * il + cv, v1 = fmaf(T.y, dv, av) * il + cv;
+          const float tw0 = (float)L.tw[v][0], th0 = (float)L.th[v][0];
+          const float fx0 = fminf(fmaxf(floorf((fminf(u0, u1) - reach) / PE_LEAF), -1.0f), tw0);
+          const float fx1 = fminf(fmaxf(floorf((fmaxf(u0, u1) + reach) / PE_LEAF), -1.0f), tw0);
+          const float fy0 = fminf(fmaxf(floorf((fminf(v0, v1) - reach) / PE_LEAF), -1.0f), th0);
+          const float fy1 = fminf(fmaxf(floorf((fmaxf(v0, v1) + reach) / PE_LEAF), -1.0f), th0);
+          // a stretch whose slots all lie off the screen reaches no splat
+          if (fx1 >= 0.0f && fx0 < tw0 && fy1 >= 0.0f && fy0 < th0) {
+            lx0 = (int)fmaxf(fx0, 0.0f);
+            lx1 = (int)fminf(fx1, tw0 - 1.0f);
+            ly0 = (int)fmaxf(fy0, 0.0f);
+            ly1 = (int)fminf(fy1, th0 - 1.0f);
+          }
+        }
+        lx0 = __reduce_min_sync(FULL, lx0);
+        ly0 = __reduce_min_sync(FULL, ly0);
+        lx1 = __reduce_max_sync(FULL, lx1);
+        ly1 = __reduce_max_sync(FULL, ly1);
+        if (lx1 < 0) continue;  // no lane reaches a slot of this view
+        ls = 0;
+        while (ls < top && ((lx0 >> ls) != (lx1 >> ls) || (ly0 >> ls) != (ly1 >> ls))) ++ls;
+        sx = lx0 >> ls;
+        sy = ly0 >> ls;
+      }
+    }
+    // the start node's box
+    {
+      const int64_t nid = L.node_off[v][ls] + (int64_t)sy * L.tw[v][ls] + sx;
+      const float4 lo = ls == top ? rlo : __ldg(L.nodes + 2 * nid);
+      const float4 hi = ls == top ? rhi : __ldg(L.nodes + 2 * nid + 1);
       bool lv = active && !(ANY && hit_any);
       n_node += lv;
       if (!__any_sync(FULL, lv && box_hit(lo, hi, r, t0, t_far()))) continue;
@@ -243,17 +291,18 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
     // (px, py) of level l (its four children at level l-1 are box-tested
     // together; the accepted ones become pending bits [4(l-1), 4(l-1)+4) of
     // `masks`).  Otherwise the pending bits of level l are children of node
-    // (px, py) at level l+1; going up one level halves (px, py).
+    // (px, py) at level l+1; going up one level halves (px, py).  The walk
+    // ends when it climbs back to the start level.
     uint64_t masks = 0;
-    int l = top, px = 0, py = 0;
-    bool expand = top > 0;
+    int l = ls, px = sx, py = sy;
+    bool expand = ls > 0;
     int leaf_x = 0, leaf_y = 0;
-    bool root_leaf = top == 0;
+    bool root_leaf = ls == 0;
     for (;;) {
       if (root_leaf) {
         root_leaf = false;
-        leaf_x = 0;
-        leaf_y = 0;
+        leaf_x = sx;
+        leaf_y = sy;
       } else {
         if (expand) {
           expand = false;
@@ -282,12 +331,12 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
           masks |= (uint64_t)m << (4 * cl);
           l = cl;
         }
-        while (l < top && ((masks >> (4 * l)) & 0xfull) == 0) {
+        while (l < ls && ((masks >> (4 * l)) & 0xfull) == 0) {
           ++l;
           px >>= 1;
           py >>= 1;
         }
-        if (l >= top) break;
+        if (l >= ls) break;
         const int c = __ffs((uint32_t)((masks >> (4 * l)) & 0xfull)) - 1;
         masks &= ~(1ull << (4 * l + c));
         const int cx = 2 * px + (c & 1), cy = 2 * py + (c >> 1);
