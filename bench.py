@@ -522,6 +522,7 @@ def run_learned(W=256, batch=64, steps=8, warmup=2):
     except (OSError, ValueError, KeyError):
         pass
     t = lt.time_paths(net, data[0]["sparse"], data[0]["dense"], data[0]["vs"])
+    fk = lt.finite_k_study(data)
     return {"workload": f"U-Net widths 32-256, {W}^2 coarse depth, batch {batch}, BF16 "
                         "activations, FP32 accumulation; pairs from the surfel tracer",
             "train_ms_per_step": ms, "train_images_per_s": batch / (ms / 1e3),
@@ -532,7 +533,8 @@ def run_learned(W=256, batch=64, steps=8, warmup=2):
                                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
             "last_loss": float(loss.cpu()[0]),
             "ms_per_view_learned_path": t["learned"] * 1e3,
-            "ms_per_view_plain_splatting": t["plain_splatting"] * 1e3}
+            "ms_per_view_plain_splatting": t["plain_splatting"] * 1e3,
+            "alg1_finite_k_vs_unbounded": fk}
 
 
 def cpu_baseline(wl):

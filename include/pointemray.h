@@ -145,6 +145,24 @@ typedef struct {
  * that view's occupied cells). */
 #define PE_STATS_WORDS 8
 
+/* Alg. 1 (screen-based PRI, tube mode) with a finite heap of K points per
+ * ray tube, as the paper writes it: of the candidates of pixel (i, j)'s tube
+ * (points within delta of its central ray, in front of the screen) the K
+ * nearest the central ray (squared distance in FP32, ties: smaller index)
+ * are kept, and of those the one nearest the tube's origin (Length(p - o),
+ * ties: smaller index) gives the pixel's key, in pe_build_gfb's format
+ * (float bits of the depth << 32 | point index; all ones = no candidate).
+ * pe_build_gfb's tube mode is the unbounded heap (K >= every candidate
+ * count gives the same keys).  pos_dev FP32 [n][3]; keys_dev [n_views][H][W]
+ * uint64 (caller-allocated); 1 <= K <= 64; n_views * W * H < 2^24; ws of
+ * pe_build_gfb_topk_workspace() bytes (0: the candidate list would exceed
+ * 2^32 entries, PE_EUNSUPPORTED). */
+size_t pe_build_gfb_topk_workspace(int32_t n_views, const pe_view *views, int64_t n_points,
+                                   float delta);
+pe_status pe_build_gfb_topk(const pe_view *views, int32_t n_views, const float *pos_dev,
+                            int64_t n_points, float delta, int32_t K, void *ws, size_t ws_bytes,
+                            uint64_t *keys_dev, void *stream);
+
 /* Surfel attributes (the per-point inputs of Alg. 1 in surfel mode; the
  * paper's splatting baseline takes a radius from the point spacing and
  * normals from local PCA, Sec. IV-A), computed on the GPU:

@@ -80,6 +80,8 @@ def lib():
         _lib.or_po_field.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int, P,
                                      C.c_int, P, P]
         _lib.or_knn.argtypes = [P, C.c_int64, P, C.c_int64, C.c_int, P, P]
+        _lib.or_gfb_topk.argtypes = [C.c_int, P, P, C.c_int64, C.c_double, C.c_int, P, C.c_int64,
+                                     P, P]
     return _lib
 
 
@@ -173,6 +175,23 @@ def gfb(scene, view: View, mode: str = "fp32", tube: bool = False, delta: float 
                  1 if tube else 0, float(delta), _p(pixa), npix, _p(depth), _p(idx),
                  _p(nout))
     return Gfb(depth, idx, nout, view, pixa)
+
+
+def gfb_topk(pos: np.ndarray, view: View, delta: float, K: int, mode: str = "fp32",
+             pix: Optional[np.ndarray] = None) -> Gfb:
+    """Alg. 1 with a finite heap of K points per ray tube (1 <= K <= 64):
+    the K candidates nearest the central ray, then the one nearest the
+    tube's origin."""
+    assert 1 <= K <= 64
+    p = np.ascontiguousarray(pos, dtype=np.float32)
+    npix = view.W * view.H if pix is None else len(pix)
+    pixa = None if pix is None else np.ascontiguousarray(pix, dtype=np.int64)
+    depth = np.empty(npix, np.float64)
+    idx = np.empty(npix, np.int64)
+    vc = view.c()
+    lib().or_gfb_topk(_fp(mode), C.byref(vc), _p(p), p.shape[0], float(delta), int(K), _p(pixa),
+                      npix, _p(depth), _p(idx))
+    return Gfb(depth, idx, np.zeros((npix, 3)), view, pixa)
 
 
 # ----------------------------------------------------------------------------

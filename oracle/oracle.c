@@ -55,6 +55,14 @@ void or_gfb(int fp64, const or_view *v, const float *pos, const float *nrm,
     gfb_f32(v, pos, nrm, rad, n, mode, delta, pix, npix, depth, idx, nrm_out);
 }
 
+void or_gfb_topk(int fp64, const or_view *v, const float *pos, int64_t n, double delta, int K,
+                 const int64_t *pix, int64_t npix, double *depth, int64_t *idx) {
+  if (fp64)
+    gfb_topk_f64(v, pos, n, delta, K, pix, npix, depth, idx);
+  else
+    gfb_topk_f32(v, pos, n, delta, K, pix, npix, depth, idx);
+}
+
 int64_t or_aggregate(int fp64, int nv, const or_view *views, const double *depth,
                      const double *nrm, const uint8_t *mask, double tau,
                      const double *bmin, double inv_vox, int G, int64_t *out_id,

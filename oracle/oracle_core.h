@@ -134,6 +134,61 @@ static void SFX(gfb)(const or_view *vin, const float *pos, const float *nrm,
   }
 }
 
+/* Alg. 1 with a finite heap of K points per ray tube, as written: the
+ * candidates (points within delta of the central ray, in front of the
+ * screen) are ranked by their squared distance to the central ray (ties:
+ * smaller point index); of the K best, the one nearest the tube's origin
+ * (Length(p - o), ties: smaller index) gives the depth.  Same arithmetic as
+ * hit_tube.  Outputs as gfb in tube mode. */
+static void SFX(gfb_topk)(const or_view *vin, const float *pos, int64_t n, double delta, int K,
+                          const int64_t *pix, int64_t npix, double *depth_out,
+                          int64_t *idx_out) {
+  SFX(view) v;
+  SFX(load_view)(vin, &v);
+  R dl = (R)delta;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < npix; ++q) {
+    int64_t p = pix ? pix[q] : q;
+    int i = (int)(p % v.W), j = (int)(p / v.W);
+    R o[3];
+    SFX(pixel_origin)(&v, i, j, o);
+    R ka[64], ks[64];
+    int64_t ki[64];
+    int cnt = 0;
+    for (int64_t s = 0; s < n; ++s) {
+      R c[3] = {(R)pos[3 * s], (R)pos[3 * s + 1], (R)pos[3 * s + 2]};
+      R qv[3] = {c[0] - o[0], c[1] - o[1], c[2] - o[2]};
+      R t = SFX(dot)(qv, v.d);
+      R x[3], e[3];
+      for (int k = 0; k < 3; ++k) x[k] = o[k] + t * v.d[k];
+      for (int k = 0; k < 3; ++k) e[k] = x[k] - c[k];
+      R a = SFX(dot)(e, e);
+      if (!(a < dl * dl)) continue;
+      if (!(t > (R)0)) continue;
+      if (cnt == K && !(a < ka[K - 1])) continue; /* equal a: the smaller index stays */
+      int at = cnt < K ? cnt++ : K - 1;
+      while (at > 0 && ka[at - 1] > a) {
+        ka[at] = ka[at - 1];
+        ki[at] = ki[at - 1];
+        ks[at] = ks[at - 1];
+        --at;
+      }
+      ka[at] = a;
+      ki[at] = s;
+      ks[at] = SQRT(SFX(dot)(qv, qv));
+    }
+    R best = (R)INFINITY;
+    int64_t bi = -1;
+    for (int e = 0; e < cnt; ++e)
+      if (ks[e] < best || (ks[e] == best && ki[e] < bi)) {
+        best = ks[e];
+        bi = ki[e];
+      }
+    depth_out[q] = (double)best;
+    idx_out[q] = bi;
+  }
+}
+
 /* ---------------------------------------------------------------------------
  * Alg. 3 lines 1-2: edge filtering, voxel fusion, conversion to splats.
  * ------------------------------------------------------------------------- */

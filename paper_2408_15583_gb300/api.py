@@ -18,7 +18,7 @@ from ._lib import PeGeom, PeHits, PeParams, PeSweep, PeView, check
 
 __all__ = ["view_from_angles", "make_params", "build_gfb", "aggregate_views", "alloc_hits",
            "trace_bounces", "po_field", "rcs_sweep", "stream_check", "Geom", "Hits",
-           "point_attributes",
+           "point_attributes", "build_gfb_topk",
            "views_to_array", "workspace"]
 
 
@@ -116,6 +116,23 @@ def build_gfb(views: Sequence[PeView], pos: torch.Tensor, nrm: Optional[torch.Te
         if t is not None:
             out[k] = t
     return out
+
+
+def build_gfb_topk(views: Sequence[PeView], pos: torch.Tensor, delta: float, K: int,
+                   stream=None) -> torch.Tensor:
+    """Alg. 1 with a finite heap of K points per ray tube
+    (``pe_build_gfb_topk``): depth keys [n_views * W * H] (int64 holding the
+    uint64 (float bits of depth << 32 | point index), all ones = empty)."""
+    n = len(views)
+    arr = views_to_array(views)
+    ws_bytes = _lib().pe_build_gfb_topk_workspace(n, arr, pos.shape[0], float(delta))
+    if ws_bytes == 0:
+        raise RuntimeError("pe_build_gfb_topk: unsupported size")
+    ws = workspace(ws_bytes, pos.device)
+    keys = torch.empty(n * views[0].W * views[0].H, dtype=torch.int64, device=pos.device)
+    check(_lib().pe_build_gfb_topk(arr, n, _p(pos), pos.shape[0], float(delta), int(K), _p(ws),
+                                   ws_bytes, _p(keys), _s(stream)), "pe_build_gfb_topk")
+    return keys
 
 
 # ----------------------------------------------------------------------------

@@ -234,3 +234,29 @@ def time_paths(model: UNet, sparse, dense, vs: ViewSet, reps=5):
         torch.cuda.synchronize()
         out[name] = (time.perf_counter() - t) / reps / n
     return out
+
+
+def finite_k_study(items: List[dict], Ks=(4, 8, 16), delta_px=2.0, device="cuda:0"):
+    """How far the unbounded heap (K = all candidates, the default tube mode)
+    is from Alg. 1 with a finite K on the coarse-depth inputs: over the
+    targets' views, the fraction of covered pixels whose chosen point
+    differs and the RMS depth difference (in units of the ray pitch)."""
+    out = {}
+    for K in Ks:
+        diff, n_hit, sq = 0, 0, 0.0
+        for it in items:
+            vs = it["vs"]
+            pos, _, _ = pipeline.scene_to_device(it["sparse"], device)
+            delta = float(delta_px * vs.views[0].pitch)
+            kinf = api.build_gfb(vs.views, pos, None, None, 1, delta, outputs=("keys",))["keys"]
+            kk = api.build_gfb_topk(vs.views, pos, delta, K)
+            hit = kinf != -1
+            di = (kinf[hit] & 0xFFFFFFFF) != (kk[hit] & 0xFFFFFFFF)
+            dinf = ((kinf[hit] >> 32) & 0xFFFFFFFF).to(torch.int32).view(torch.float32)
+            dk = ((kk[hit] >> 32) & 0xFFFFFFFF).to(torch.int32).view(torch.float32)
+            diff += int(di.sum())
+            n_hit += int(hit.sum())
+            sq += float(((dk - dinf).double() / vs.views[0].pitch).pow(2).sum())
+        out[f"K={K}"] = {"changed_point_fraction": diff / max(n_hit, 1),
+                         "rms_depth_change_pitches": math.sqrt(sq / max(n_hit, 1))}
+    return out

@@ -594,3 +594,37 @@ def test_pca_normal_of_a_tilted_plane_and_duplicates():
     d = np.sqrt(((dup[:, None, :].astype(np.float64) - dup[None]) ** 2).sum(-1))
     d0 = np.sort(np.delete(d[0], 0))[:4]
     assert d0[0] == 0.0 and abs(r[0] - d0.mean()) < 1e-6 * max(d0.mean(), 1e-9)
+
+
+# ----------------------------------------------------------------------------
+# Alg. 1 with a finite K (the heap of K points nearest the central ray)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_alg1_finite_k_hand_case(mode):
+    # one pixel looking down -z from z = 5; delta = 0.1.  A: depth 4 (z = 1),
+    # 0.03 off the axis; C: depth 3, 0.05 off; B: depth 2, 0.08 off.
+    # K = 1 keeps A (most central): 4; K = 2 keeps A, C: 3; K >= 3: 2.
+    v = down_view(1, 1, 1.0)
+    pos = np.array([[0.03, 0.0, 1.0], [0.0, 0.08, 3.0], [0.0, -0.05, 2.0]], np.float32)
+    for K, i in {1: 0, 2: 2, 3: 1, 8: 1}.items():
+        g = oracle.gfb_topk(pos, v, 0.1, K, mode)
+        assert g.idx[0] == i
+        # the score is Length(p - o), o = (0, 0, 5) the pixel's origin
+        expect = np.linalg.norm(pos[i].astype(np.float64) - [0.0, 0.0, 5.0])
+        assert abs(g.depth[0] - expect) < 1e-6
+
+
+def test_alg1_large_k_equals_the_unbounded_heap():
+    rng = np.random.default_rng(9)
+    sc = mk_scene(rng.random((400, 3)) * [1.0, 1.0, 0.2], np.tile([0, 0, 1.0], (400, 1)),
+                  np.full(400, 0.05))
+    v = down_view(24, 24, 1.0 / 24, z=3.0)
+    v.o = v.o + np.array([0.5, 0.5, 0.0])
+    g_inf = oracle.gfb(sc, v, "fp32", tube=True, delta=0.06)
+    g_k = oracle.gfb_topk(sc.pos, v, 0.06, 64, "fp32")
+    assert np.array_equal(g_inf.idx, g_k.idx) and np.array_equal(g_inf.depth, g_k.depth)
+    assert (g_inf.idx >= 0).mean() > 0.5
+    g1 = oracle.gfb_topk(sc.pos, v, 0.06, 1, "fp32")
+    assert np.array_equal(g1.idx >= 0, g_inf.idx >= 0)      # same hit pixels
+    assert (g1.idx != g_inf.idx).mean() > 0.05               # but other points chosen
