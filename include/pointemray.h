@@ -334,6 +334,23 @@ pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t rays_per_gr
                       const float *ks, const double *freqs_hz, int32_t n_freq,
                       void *ws, size_t ws_bytes, double *E_dev, void *stream);
 
+/* Bistatic observation grids: for each group g (rays_per_group slots, as in
+ * pe_po_field) and each of n_obs receiver directions obs_dirs[g][o] (unit,
+ * toward the receiver; host float32 [n_groups][n_obs][3]), Psi is tested per
+ * ray toward that receiver -- a shadow ray from the ray's last hit (M >= 1)
+ * against the aggregated splats of `geom`, blocked by any hit with t > eps
+ * (Eq. 14's Psi, Sec. II-C) -- and the Eq. 14 sum of pe_po_field is formed
+ * with ks = obs_dirs[g][o].  hits->psi is not read.  E_dev: float64
+ * [n_groups][n_obs][n_freq][2][3][2].  n_groups <= PE_MAX_BATCH; ws of
+ * pe_po_field_bistatic_workspace() bytes.  The monostatic receiver
+ * (obs = -d of the group's view) gives pe_po_field's result except that
+ * single-bounce rays are shadow-tested too. */
+size_t pe_po_field_bistatic_workspace(int32_t n_groups, int64_t rays_per_group, int32_t n_freq);
+pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups, int64_t rays_per_group,
+                               const float *obs_dirs, int32_t n_obs, const pe_geom *geom,
+                               float eps, const double *freqs_hz, int32_t n_freq, void *ws,
+                               size_t ws_bytes, double *E_dev, void *stream);
+
 /* pe_po_field without a workspace -- for callers that cannot allocate device
  * memory for the library (their memory belongs to a host application's own
  * pool, or allocation is not allowed where they call from).  The paper has no

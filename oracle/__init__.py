@@ -80,6 +80,8 @@ def lib():
         _lib.or_po_field.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int, P,
                                      C.c_int, P, P]
         _lib.or_knn.argtypes = [P, C.c_int64, P, C.c_int64, C.c_int, P, P]
+        _lib.or_shadow_dirs.argtypes = [C.c_int, P, P, P, P, C.c_int64, P, P, C.c_int64, P,
+                                        C.c_int, C.c_double, P]
         _lib.or_gfb_topk.argtypes = [C.c_int, P, P, C.c_int64, C.c_double, C.c_int, P, C.c_int64,
                                      P, P]
     return _lib
@@ -313,6 +315,33 @@ def po_field(tr: Trace, freqs_hz, ks_dirs) -> np.ndarray:
     lib().or_po_field(nr, *[_p(a) for a in arr], _p(use), freqs.shape[0], _p(freqs),
                       ks.shape[0], _p(ks), _p(E))
     return E[..., 0] + 1j * E[..., 1]
+
+
+def shadow_dirs(tr: Trace, splats: Splats, dirs, eps: float, mode: str = "fp32") -> np.ndarray:
+    """Psi toward other receivers (bistatic): [nobs][nr] uint8, 1 unless a
+    splat is hit from the ray's last hit point along dirs[o] (t > eps); 0 for
+    rays without a hit."""
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    nr = tr.M.shape[0]
+    psi = np.empty((d.shape[0], nr), np.uint8)
+    arr = [np.ascontiguousarray(a) for a in (splats.c, splats.n, splats.r, splats.id)]
+    lib().or_shadow_dirs(_fp(mode), *[_p(a) for a in arr], arr[3].shape[0],
+                         _p(np.ascontiguousarray(tr.p)), _p(np.ascontiguousarray(tr.M)), nr,
+                         _p(d), d.shape[0], float(eps), _p(psi))
+    return psi
+
+
+def po_field_bistatic(tr: Trace, splats: Splats, freqs_hz, obs_dirs, eps: float,
+                      mode: str = "fp32") -> np.ndarray:
+    """Eq. 14 toward each receiver direction of obs_dirs, with Psi tested
+    toward that receiver: complex [obs][F][pol][3]."""
+    obs = np.atleast_2d(np.asarray(obs_dirs, np.float64))
+    psi = shadow_dirs(tr, splats, obs, eps, mode)
+    out = []
+    for o in range(obs.shape[0]):
+        t = Trace(tr.M, tr.ids, tr.p, tr.n, tr.k, tr.u, tr.v, tr.path, psi[o])
+        out.append(po_field(t, freqs_hz, obs[o])[0])
+    return np.array(out)
 
 
 def sigma_from_field(E: np.ndarray, freqs_hz, u_hat, v_hat) -> np.ndarray:

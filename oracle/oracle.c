@@ -90,6 +90,15 @@ void or_trace(int fp64, const or_view *v, const int64_t *pix, int64_t nr,
               eps, r_ov, do_shadow, M, ids, p, n, k, u, vv, path, psi);
 }
 
+void or_shadow_dirs(int fp64, const double *sc, const double *sn, const double *sr,
+                    const int64_t *sid, int64_t ns, const double *p, const int32_t *M, int64_t nr,
+                    const double *dirs, int nobs, double eps, uint8_t *psi) {
+  if (fp64)
+    shadow_dirs_f64(sc, sn, sr, sid, ns, p, M, nr, dirs, nobs, eps, psi);
+  else
+    shadow_dirs_f32(sc, sn, sr, sid, ns, p, M, nr, dirs, nobs, eps, psi);
+}
+
 /* ---------------------------------------------------------------------------
  * Physical optics (Sec. II-B, II-C).
  * ------------------------------------------------------------------------- */

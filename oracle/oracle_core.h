@@ -577,3 +577,39 @@ static void SFX(trace)(const or_view *vin, const int64_t *pix, int64_t nr,
   free(n);
   free(r);
 }
+
+/* Psi for other receivers (bistatic observation, Eq. 14): for each ray with
+ * at least one hit and each direction dirs[o] toward a receiver, 1 unless a
+ * splat is hit along that direction from the ray's last hit point with
+ * t > eps.  p: [nr][3] last-hit points, M: [nr] hit counts; psi_out:
+ * [nobs][nr] (0 for rays without a hit). */
+static void SFX(shadow_dirs)(const double *sc, const double *sn, const double *sr,
+                             const int64_t *sid, int64_t ns, const double *p, const int32_t *M,
+                             int64_t nr, const double *dirs, int nobs, double eps,
+                             uint8_t *psi_out) {
+  R *c = (R *)malloc(sizeof(R) * (size_t)(3 * ns + 1));
+  R *n = (R *)malloc(sizeof(R) * (size_t)(3 * ns + 1));
+  R *r = (R *)malloc(sizeof(R) * (size_t)(ns + 1));
+  for (int64_t s = 0; s < 3 * ns; ++s) {
+    c[s] = (R)sc[s];
+    n[s] = (R)sn[s];
+  }
+  for (int64_t s = 0; s < ns; ++s) r[s] = (R)sr[s];
+  SFX(splatset) S = {c, n, r, sid, ns};
+  const R E = (R)eps;
+  for (int o = 0; o < nobs; ++o) {
+    const R w[3] = {(R)dirs[3 * o], (R)dirs[3 * o + 1], (R)dirs[3 * o + 2]};
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < nr; ++q) {
+      uint8_t psi = 0;
+      if (M[q] >= 1) {
+        const R pq[3] = {(R)p[3 * q], (R)p[3 * q + 1], (R)p[3 * q + 2]};
+        psi = SFX(any_hit)(&S, pq, w, E) ? 0 : 1;
+      }
+      psi_out[(int64_t)o * nr + q] = psi;
+    }
+  }
+  free(c);
+  free(n);
+  free(r);
+}

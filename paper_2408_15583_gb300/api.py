@@ -18,7 +18,7 @@ from ._lib import PeGeom, PeHits, PeParams, PeSweep, PeView, check
 
 __all__ = ["view_from_angles", "make_params", "build_gfb", "aggregate_views", "alloc_hits",
            "trace_bounces", "po_field", "rcs_sweep", "stream_check", "Geom", "Hits",
-           "point_attributes", "build_gfb_topk",
+           "point_attributes", "build_gfb_topk", "po_field_bistatic",
            "views_to_array", "workspace"]
 
 
@@ -267,6 +267,25 @@ def po_field(hits: Hits, n_groups: int, rays_per_group: int, ks: np.ndarray,
     check(_lib().pe_po_field(C.byref(hits.c), n_groups, rays_per_group,
                              ks.ctypes.data_as(C.c_void_p), fr.ctypes.data_as(C.c_void_p),
                              fr.shape[0], _p(ws), ws_bytes, _p(E), _s(stream)), "pe_po_field")
+    return E
+
+
+def po_field_bistatic(hits: Hits, n_groups: int, rays_per_group: int, obs_dirs: np.ndarray,
+                      geom: "Geom", eps: float, freqs_hz: np.ndarray, stream=None) -> torch.Tensor:
+    """Eq. 14 toward n_obs receivers per group, Psi tested toward each
+    (``pe_po_field_bistatic``).  obs_dirs: [n_groups, n_obs, 3].  Returns
+    float64 [n_groups, n_obs, F, 2 pol, 3, re/im]."""
+    obs = np.ascontiguousarray(obs_dirs, dtype=np.float32)
+    n_obs = obs.shape[1]
+    fr = np.ascontiguousarray(freqs_hz, dtype=np.float64).ravel()
+    dev = hits.M.device
+    E = torch.empty((n_groups, n_obs, fr.shape[0], 2, 3, 2), dtype=torch.float64, device=dev)
+    ws_bytes = _lib().pe_po_field_bistatic_workspace(n_groups, rays_per_group, fr.shape[0])
+    ws = workspace(ws_bytes, dev)
+    check(_lib().pe_po_field_bistatic(C.byref(hits.c), n_groups, rays_per_group,
+                                      obs.ctypes.data_as(C.c_void_p), n_obs, C.byref(geom.c),
+                                      float(eps), fr.ctypes.data_as(C.c_void_p), fr.shape[0],
+                                      _p(ws), ws_bytes, _p(E), _s(stream)), "pe_po_field_bistatic")
     return E
 
 

@@ -334,3 +334,72 @@ extern "C" pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t 
     return pe_fail(PE_ENOMEM, "pe_po_field: workspace needs %zu bytes", need);
   return pe_launch_po(*hits, n_groups, rays_per_group, ks, freqs, n_freq, ws, ws_bytes, E, s);
 }
+
+// ---------------------------------------------------------------------------
+// Bistatic observation: the Eq. 14 sum toward n_obs receiver directions per
+// group, each with Psi tested toward its own receiver.
+// ---------------------------------------------------------------------------
+
+namespace {
+struct bistatic_ws {
+  uint8_t *psi;
+  double *Eo;
+  char *po;
+  size_t po_bytes;
+};
+
+bistatic_ws carve_bistatic(pe_carve &c, int32_t n_groups, int64_t rpg, int32_t n_freq) {
+  bistatic_ws w;
+  w.psi = c.take<uint8_t>((size_t)(n_groups * rpg));
+  w.Eo = c.take<double>((size_t)n_groups * n_freq * 12);
+  w.po_bytes = pe_po_ws_bytes(n_groups, rpg, n_freq);
+  w.po = c.take<char>(w.po_bytes);
+  return w;
+}
+}  // namespace
+
+extern "C" size_t pe_po_field_bistatic_workspace(int32_t n_groups, int64_t rays_per_group,
+                                                 int32_t n_freq) {
+  if (n_groups < 1 || rays_per_group < 1 || n_freq < 1) return 0;
+  pe_carve c{nullptr, 0};
+  carve_bistatic(c, n_groups, rays_per_group, n_freq);
+  return c.bytes() + 256;
+}
+
+extern "C" pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups,
+                                          int64_t rays_per_group, const float *obs_dirs,
+                                          int32_t n_obs, const pe_geom *geom, float eps,
+                                          const double *freqs, int32_t n_freq, void *ws,
+                                          size_t ws_bytes, double *E, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!hits || !obs_dirs || !freqs || !E || !geom || n_groups < 1 || n_groups > PE_MAX_BATCH ||
+      rays_per_group < 1 || n_obs < 1 || n_freq < 1 || !(eps >= 0.0f))
+    return pe_fail(PE_EINVAL, "pe_po_field_bistatic: bad arguments (1..%d groups)", PE_MAX_BATCH);
+  if (hits->n_rays < (int64_t)n_groups * rays_per_group || !hits->p || !hits->n || !hits->k ||
+      !hits->u || !hits->v || !hits->path || !hits->M)
+    return pe_fail(PE_EINVAL, "pe_po_field_bistatic: hits must hold n_groups * rays_per_group records");
+  for (int f = 0; f < n_freq; ++f)
+    if (!(freqs[f] > 0)) return pe_fail(PE_EINVAL, "pe_po_field_bistatic: frequencies must be > 0");
+  const size_t need = pe_po_field_bistatic_workspace(n_groups, rays_per_group, n_freq);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_po_field_bistatic: workspace needs %zu bytes", need);
+  pe_carve c{static_cast<char *>(ws), 0};
+  bistatic_ws w = carve_bistatic(c, n_groups, rays_per_group, n_freq);
+  float dirs[PE_MAX_BATCH * 3];
+  const size_t row = sizeof(double) * 12 * n_freq;
+  for (int o = 0; o < n_obs; ++o) {
+    for (int g = 0; g < n_groups; ++g)
+      for (int k = 0; k < 3; ++k) dirs[3 * g + k] = obs_dirs[((int64_t)g * n_obs + o) * 3 + k];
+    pe_status st = pe_launch_shadow_dirs(geom, *hits, n_groups, rays_per_group, dirs, eps, w.psi,
+                                         nullptr, s);
+    if (st != PE_OK) return st;
+    pe_hits h = *hits;
+    h.psi = w.psi;
+    st = pe_launch_po(h, n_groups, rays_per_group, dirs, freqs, n_freq, w.po, w.po_bytes, w.Eo, s);
+    if (st != PE_OK) return st;
+    // E[g][o][f][12] <- Eo[g][f][12]
+    PE_TRY_CUDA(cudaMemcpy2DAsync(E + (int64_t)o * n_freq * 12, row * n_obs, w.Eo, row, row,
+                                  (size_t)n_groups, cudaMemcpyDeviceToDevice, s));
+  }
+  return PE_OK;
+}

@@ -659,6 +659,46 @@ __global__ void __launch_bounds__(kTraceThreads, 8) shadow_kernel(const __grid_c
   flush_stats(A.stats, 0, nsh, ns, nn, nv);
 }
 
+// Psi toward other receivers (bistatic Eq. 14): a shadow ray from each
+// ray's last hit along its group's receiver direction; slots in raster order.
+struct shadow_dirs_args {
+  pe_geom_layout L;
+  const float *p;
+  const int32_t *M;
+  int64_t rpg;
+  int32_t n_groups;
+  float eps;
+  float dir[PE_MAX_BATCH][3];
+  uint8_t *psi;
+  unsigned int *err;
+  long long *stats;
+};
+
+__global__ void __launch_bounds__(kTraceThreads, 8)
+    shadow_dirs_kernel(const __grid_constant__ shadow_dirs_args A) {
+  const int64_t total = A.rpg * A.n_groups;
+  long long nsh = 0, ns = 0, nn = 0, nv = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    const bool in = t < total;
+    const bool active = in && A.M[t] >= 1;
+    const int g = in ? (int)(t / A.rpg) : 0;
+    const pe_f3 w = {A.dir[g][0], A.dir[g][1], A.dir[g][2]};
+    const pe_f3 p = active ? pe_f3{A.p[3 * t], A.p[3 * t + 1], A.p[3 * t + 2]}
+                           : pe_f3{0.f, 0.f, 0.f};
+    qstate S;
+    S.tb = INFINITY;
+    S.ib = PE_NONE;
+    S.nc = 0;
+    nsh += active;
+    bool blocked = false;
+    walk<true>(A.L, p, w, A.eps, 0.0f, active, S, blocked, A.err, ns, nn, nv);
+    if (in) A.psi[t] = (active && !blocked) ? 1 : 0;
+  }
+  flush_stats(A.stats, 0, nsh, ns, nn, nv);
+}
+
 int sms() {
   static int n = 0;
   if (!n) {
@@ -773,6 +813,30 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
     pe_event_after("shadow_kernel", s);
     PE_TRY_LAUNCH("shadow_kernel");
   }
+  return PE_OK;
+}
+
+pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n_groups,
+                                int64_t rpg, const float *dirs, float eps, uint8_t *psi,
+                                int64_t *stats, cudaStream_t s) {
+  if (n_groups < 1 || n_groups > PE_MAX_BATCH || rpg < 1)
+    return pe_fail(PE_EINVAL, "shadow: 1..%d groups", PE_MAX_BATCH);
+  shadow_dirs_args A;
+  memset(&A, 0, sizeof(A));
+  if (!geom_layout(geom, &A.L)) return pe_fail(PE_EINVAL, "shadow: invalid geometry");
+  A.p = h.p;
+  A.M = h.M;
+  A.rpg = rpg;
+  A.n_groups = n_groups;
+  A.eps = eps;
+  for (int g = 0; g < n_groups; ++g)
+    for (int k = 0; k < 3; ++k) A.dir[g][k] = dirs[3 * g + k];
+  A.psi = psi;
+  A.err = pe_err_word();
+  A.stats = reinterpret_cast<long long *>(stats);
+  const size_t tv_bytes = (size_t)A.L.nv * kTraceThreads * sizeof(float2);
+  shadow_dirs_kernel<<<grid_for(rpg * n_groups), kTraceThreads, tv_bytes, s>>>(A);
+  PE_TRY_LAUNCH("shadow_dirs_kernel");
   return PE_OK;
 }
 

@@ -291,6 +291,45 @@ def test_po_field_matches_oracle_on_traced_hits(small_geom):
         assert field_err(E[a], Eo).max() < 1e-3
 
 
+@pytest.mark.parametrize("case", GEOMS)
+def test_po_field_bistatic_matches_oracle(case, request):
+    # three incidence angles, four receivers each (the transmitter's own
+    # direction and three others); Psi per receiver against the splats
+    api, pipe = _mods()
+    d = request.getfixturevalue(case)
+    sc = d["sc"]
+    c, r = scenes.bounding_sphere(sc.pos)
+    th, ph = [90.0, 70.0, 60.0], [45.0, 20.0, 200.0]
+    views = pipe.views_from_angles(th, ph, c, r * 1.02, 40, 40)
+    mb = 2 if case == "small_geom" else 3
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, d["prm"])
+    freqs = scenes.freq_grid(2.5e9, 3.5e9, 3)
+    obs = []
+    for v in views:
+        w = -np.asarray(v.d[:], np.float64)
+        rows = [w]
+        for dphi, dth in ((25.0, 0.0), (60.0, 10.0), (140.0, -20.0)):
+            t0 = math.acos(np.clip(w[2], -1, 1)) + math.radians(dth)
+            p0 = math.atan2(w[1], w[0]) + math.radians(dphi)
+            rows.append([math.sin(t0) * math.cos(p0), math.sin(t0) * math.sin(p0), math.cos(t0)])
+        obs.append(rows)
+    obs = np.asarray(obs, np.float32)
+    eps = float(d["prm"].eps)
+    E = _cplx(api.po_field_bistatic(h, 3, 40 * 40, obs, d["geom"], eps, freqs))
+    api.stream_check()
+    blocked = 0
+    for a, v in enumerate(views):
+        ov = _oracle_view(v)
+        tr = oracle.trace(ov, d["S"], mb, eps, float(d["prm"].overlap_r),
+                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+        o64 = obs[a].astype(np.float64)
+        Eo = oracle.po_field_bistatic(tr, d["S"], freqs, o64, eps)
+        blocked += int((oracle.shadow_dirs(tr, d["S"], o64, eps) == 0)[:, tr.M > 0].sum())
+        assert field_err(E[a], Eo).max() < 1e-3, f"angle {a}"
+    assert blocked > 0          # the case exercises receiver shadowing
+
+
 # ----------------------------------------------------------------------------
 # a7: the whole sweep
 # ----------------------------------------------------------------------------

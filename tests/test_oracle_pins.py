@@ -628,3 +628,58 @@ def test_alg1_large_k_equals_the_unbounded_heap():
     g1 = oracle.gfb_topk(sc.pos, v, 0.06, 1, "fp32")
     assert np.array_equal(g1.idx >= 0, g_inf.idx >= 0)      # same hit pixels
     assert (g1.idx != g_inf.idx).mean() > 0.05               # but other points chosen
+
+
+# ----------------------------------------------------------------------------
+# bistatic observation (Eq. 14 toward other receivers, Psi per receiver)
+# ----------------------------------------------------------------------------
+
+def _splats_of(rows):
+    if not rows:
+        z = np.zeros((0, 3))
+        return oracle.Splats(id=np.zeros(0, np.int64), c=z, n=z, r=np.zeros(0),
+                             count=np.zeros(0, np.int32), keep=np.zeros(0, np.uint8))
+    return _splats(rows)
+
+
+@pytest.mark.parametrize("beta", [0.0, 15.0, 40.0])
+def test_bistatic_plate_exact_integral_and_receiver_shadowing(beta):
+    # a 0.5 x 0.3 plate lit at normal incidence, received at beta from the
+    # normal in the xz-plane: the sum of the cells' Eq. 11 terms is the exact
+    # plate integral |U x V| sinc(q.U/2) sinc(q.V/2), q = k (k_in - k_s),
+    # times [(n x h) x k_s] x k_s for each transmit polarisation
+    f = 3e9
+    k = 2 * math.pi * f / C0
+    tr, w, u, v, U, V = _plate_cells(0.0, 0.5, 0.3, 40, 30)
+    ks = np.array([math.sin(math.radians(beta)), 0.0, math.cos(math.radians(beta))])
+    E = oracle.po_field_bistatic(tr, _splats_of([]), [f], [ks], 1e-3)[0, 0]   # [pol][3]
+    q = k * (-w - ks)
+    sinc = lambda x: math.sin(x) / x if x else 1.0
+    I = np.linalg.norm(np.cross(U, V)) * sinc(q @ U / 2) * sinc(q @ V / 2)
+    n = np.array([0.0, 0.0, 1.0])
+    us, vs = tr.u[0], tr.v[0]
+    for pol, h in ((0, -vs / np.linalg.norm(vs)), (1, us / np.linalg.norm(us))):
+        vec = np.cross(np.cross(np.cross(n, h), ks), ks)
+        assert np.allclose(E[pol].real, I * vec, rtol=1e-9, atol=1e-12 * abs(I))
+        assert np.allclose(E[pol].imag, 0.0, atol=1e-9 * abs(I))
+    # a large disk above the plate blocks every receiver on that side
+    lid = _splats_of([(0, [0.0, 0.0, 0.5], [0.0, 0.0, 1.0], 10.0)])
+    assert np.all(oracle.shadow_dirs(tr, lid, [ks], 1e-3) == 0)
+    assert np.all(oracle.po_field_bistatic(tr, lid, [f], [ks], 1e-3) == 0)
+
+
+def test_bistatic_psi_toward_the_transmitter_is_the_monostatic_psi():
+    # dihedral rays that bounce twice: the receiver at the transmitter sees
+    # the monostatic shadow test exactly; single-bounce rays are unblocked
+    sc = scenes.dihedral(2000, seed=5)
+    vd = scenes.aggregation_views(sc, 64, 64)
+    S, gv, _, _ = oracle.build_geometry(sc, vd, "fp32")
+    eps = oracle.default_eps(gv)
+    c, r = scenes.bounding_sphere(sc.pos)
+    v = oracle.view_from_angles(90.0, 40.0, c, r * 1.02, 32, 32, "fp32")
+    tr = oracle.trace(v, S, 2, eps, eps, first=oracle.gfb(sc, v, "fp32"), mode="fp32")
+    psi = oracle.shadow_dirs(tr, S, [-np.asarray(v.d)], eps)[0]
+    two = tr.M >= 2
+    assert two.sum() > 50
+    assert np.array_equal(psi[two], tr.psi[two])
+    assert psi[tr.M == 1].mean() > 0.95
