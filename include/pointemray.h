@@ -340,7 +340,10 @@ pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t rays_per_gr
  * ray toward that receiver -- a shadow ray from the ray's last hit (M >= 1)
  * against the aggregated splats of `geom`, blocked by any hit with t > eps
  * (Eq. 14's Psi, Sec. II-C) -- and the Eq. 14 sum of pe_po_field is formed
- * with ks = obs_dirs[g][o].  hits->psi is not read.  E_dev: float64
+ * with ks = obs_dirs[g][o].  With only_bounce > 0 only rays whose last hit
+ * is that bounce (M == only_bounce) contribute: tracing with max_bounces =
+ * b for b = 1..mb and summing gives PO at every bounce (Eq. 14 applied at
+ * each hit instead of the last).  hits->psi is not read.  E_dev: float64
  * [n_groups][n_obs][n_freq][2][3][2].  n_groups <= PE_MAX_BATCH; ws of
  * pe_po_field_bistatic_workspace() bytes.  The monostatic receiver
  * (obs = -d of the group's view) gives pe_po_field's result except that
@@ -348,8 +351,9 @@ pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t rays_per_gr
 size_t pe_po_field_bistatic_workspace(int32_t n_groups, int64_t rays_per_group, int32_t n_freq);
 pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups, int64_t rays_per_group,
                                const float *obs_dirs, int32_t n_obs, const pe_geom *geom,
-                               float eps, const double *freqs_hz, int32_t n_freq, void *ws,
-                               size_t ws_bytes, double *E_dev, void *stream);
+                               float eps, int32_t only_bounce, const double *freqs_hz,
+                               int32_t n_freq, void *ws, size_t ws_bytes, double *E_dev,
+                               void *stream);
 
 /* pe_po_field without a workspace -- for callers that cannot allocate device
  * memory for the library (their memory belongs to a host application's own

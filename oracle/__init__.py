@@ -332,16 +332,35 @@ def shadow_dirs(tr: Trace, splats: Splats, dirs, eps: float, mode: str = "fp32")
 
 
 def po_field_bistatic(tr: Trace, splats: Splats, freqs_hz, obs_dirs, eps: float,
-                      mode: str = "fp32") -> np.ndarray:
+                      mode: str = "fp32", only_bounce: int = 0) -> np.ndarray:
     """Eq. 14 toward each receiver direction of obs_dirs, with Psi tested
-    toward that receiver: complex [obs][F][pol][3]."""
+    toward that receiver (only rays with M == only_bounce if > 0):
+    complex [obs][F][pol][3]."""
     obs = np.atleast_2d(np.asarray(obs_dirs, np.float64))
     psi = shadow_dirs(tr, splats, obs, eps, mode)
+    if only_bounce > 0:
+        psi = psi * (tr.M == only_bounce).astype(np.uint8)[None]
     out = []
     for o in range(obs.shape[0]):
         t = Trace(tr.M, tr.ids, tr.p, tr.n, tr.k, tr.u, tr.v, tr.path, psi[o])
         out.append(po_field(t, freqs_hz, obs[o])[0])
     return np.array(out)
+
+
+def po_field_every_bounce(view: View, splats: Splats, first: Gfb, mb: int, eps: float,
+                          r_ov: float, freqs_hz, mode: str = "fp32") -> np.ndarray:
+    """PO at every bounce instead of Eq. 14's last hit: for b = 1..mb, the
+    rays traced to b bounces whose b-th hit is their last contribute Eq. 14
+    at that hit, with Psi toward the (monostatic) receiver; the fields are
+    summed.  complex [F][pol][3]."""
+    w = -np.asarray(view.d, np.float64)
+    E = 0.0
+    for b in range(1, mb + 1):
+        tr = trace(view, splats, b, eps, r_ov, first=first, mode=mode)
+        psi = shadow_dirs(tr, splats, [w], eps, mode)[0] * (tr.M == b).astype(np.uint8)
+        t = Trace(tr.M, tr.ids, tr.p, tr.n, tr.k, tr.u, tr.v, tr.path, psi)
+        E = E + po_field(t, freqs_hz, w)[0]
+    return E
 
 
 def sigma_from_field(E: np.ndarray, freqs_hz, u_hat, v_hat) -> np.ndarray:

@@ -78,8 +78,8 @@ SIGNATURES = {
     "pe_nn_gemm_path": (C.c_int32, [C.c_int32]),
     "pe_point_attributes_workspace": (C.c_size_t, [C.c_int64]),
     "pe_po_field_bistatic_workspace": (C.c_size_t, [C.c_int32, C.c_int64, C.c_int32]),
-    "pe_po_field_bistatic": (C.c_int, [P, C.c_int32, C.c_int64, P, C.c_int32, P, C.c_float, P,
-                                       C.c_int32, P, C.c_size_t, P, P]),
+    "pe_po_field_bistatic": (C.c_int, [P, C.c_int32, C.c_int64, P, C.c_int32, P, C.c_float,
+                                       C.c_int32, P, C.c_int32, P, C.c_size_t, P, P]),
     "pe_build_gfb_topk_workspace": (C.c_size_t, [C.c_int32, P, C.c_int64, C.c_float]),
     "pe_build_gfb_topk": (C.c_int, [P, C.c_int32, P, C.c_int64, C.c_float, C.c_int32, P, C.c_size_t,
                                     P, P]),

@@ -271,7 +271,8 @@ def po_field(hits: Hits, n_groups: int, rays_per_group: int, ks: np.ndarray,
 
 
 def po_field_bistatic(hits: Hits, n_groups: int, rays_per_group: int, obs_dirs: np.ndarray,
-                      geom: "Geom", eps: float, freqs_hz: np.ndarray, stream=None) -> torch.Tensor:
+                      geom: "Geom", eps: float, freqs_hz: np.ndarray, only_bounce: int = 0,
+                      stream=None) -> torch.Tensor:
     """Eq. 14 toward n_obs receivers per group, Psi tested toward each
     (``pe_po_field_bistatic``).  obs_dirs: [n_groups, n_obs, 3].  Returns
     float64 [n_groups, n_obs, F, 2 pol, 3, re/im]."""
@@ -284,7 +285,8 @@ def po_field_bistatic(hits: Hits, n_groups: int, rays_per_group: int, obs_dirs: 
     ws = workspace(ws_bytes, dev)
     check(_lib().pe_po_field_bistatic(C.byref(hits.c), n_groups, rays_per_group,
                                       obs.ctypes.data_as(C.c_void_p), n_obs, C.byref(geom.c),
-                                      float(eps), fr.ctypes.data_as(C.c_void_p), fr.shape[0],
+                                      float(eps), int(only_bounce), fr.ctypes.data_as(C.c_void_p),
+                                      fr.shape[0],
                                       _p(ws), ws_bytes, _p(E), _s(stream)), "pe_po_field_bistatic")
     return E
 

@@ -127,10 +127,12 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
 
 // Psi toward receiver direction dirs[g] (host [n_groups][3]) for every slot
 // of group g (rays_per_group consecutive slots): 1 unless a splat is hit from
-// the slot's last hit (M >= 1) along dirs[g] with t > eps; 0 without a hit.
+// the slot's last hit (M >= 1; M == only_bounce if only_bounce > 0) along
+// dirs[g] with t > eps; 0 for the other slots.
 pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n_groups,
                                 int64_t rays_per_group, const float *dirs, float eps,
-                                uint8_t *psi, int64_t *stats, cudaStream_t s);
+                                int32_t only_bounce, uint8_t *psi, int64_t *stats,
+                                cudaStream_t s);
 size_t pe_po_ws_bytes(int32_t n_groups, int64_t rays_per_group, int32_t n_freq);
 pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rays_per_group,
                        const float *ks, const double *freqs, int32_t n_freq, void *ws,

@@ -369,8 +369,9 @@ extern "C" size_t pe_po_field_bistatic_workspace(int32_t n_groups, int64_t rays_
 extern "C" pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups,
                                           int64_t rays_per_group, const float *obs_dirs,
                                           int32_t n_obs, const pe_geom *geom, float eps,
-                                          const double *freqs, int32_t n_freq, void *ws,
-                                          size_t ws_bytes, double *E, void *stream) {
+                                          int32_t only_bounce, const double *freqs,
+                                          int32_t n_freq, void *ws, size_t ws_bytes, double *E,
+                                          void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!hits || !obs_dirs || !freqs || !E || !geom || n_groups < 1 || n_groups > PE_MAX_BATCH ||
       rays_per_group < 1 || n_obs < 1 || n_freq < 1 || !(eps >= 0.0f))
@@ -390,8 +391,8 @@ extern "C" pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups,
   for (int o = 0; o < n_obs; ++o) {
     for (int g = 0; g < n_groups; ++g)
       for (int k = 0; k < 3; ++k) dirs[3 * g + k] = obs_dirs[((int64_t)g * n_obs + o) * 3 + k];
-    pe_status st = pe_launch_shadow_dirs(geom, *hits, n_groups, rays_per_group, dirs, eps, w.psi,
-                                         nullptr, s);
+    pe_status st = pe_launch_shadow_dirs(geom, *hits, n_groups, rays_per_group, dirs, eps,
+                                         only_bounce, w.psi, nullptr, s);
     if (st != PE_OK) return st;
     pe_hits h = *hits;
     h.psi = w.psi;

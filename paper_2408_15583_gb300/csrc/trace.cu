@@ -672,6 +672,7 @@ struct shadow_dirs_args {
   uint8_t *psi;
   unsigned int *err;
   long long *stats;
+  int32_t only_bounce;  // > 0: only rays whose last hit is that bounce
 };
 
 __global__ void __launch_bounds__(kTraceThreads, 8)
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
        base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = base + threadIdx.x;
     const bool in = t < total;
-    const bool active = in && A.M[t] >= 1;
+    const bool active = in && A.M[t] >= 1 && (A.only_bounce <= 0 || A.M[t] == A.only_bounce);
     const int g = in ? (int)(t / A.rpg) : 0;
     const pe_f3 w = {A.dir[g][0], A.dir[g][1], A.dir[g][2]};
     const pe_f3 p = active ? pe_f3{A.p[3 * t], A.p[3 * t + 1], A.p[3 * t + 2]}
@@ -817,8 +818,8 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
 }
 
 pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n_groups,
-                                int64_t rpg, const float *dirs, float eps, uint8_t *psi,
-                                int64_t *stats, cudaStream_t s) {
+                                int64_t rpg, const float *dirs, float eps, int32_t only_bounce,
+                                uint8_t *psi, int64_t *stats, cudaStream_t s) {
   if (n_groups < 1 || n_groups > PE_MAX_BATCH || rpg < 1)
     return pe_fail(PE_EINVAL, "shadow: 1..%d groups", PE_MAX_BATCH);
   shadow_dirs_args A;
@@ -834,6 +835,7 @@ pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n
   A.psi = psi;
   A.err = pe_err_word();
   A.stats = reinterpret_cast<long long *>(stats);
+  A.only_bounce = only_bounce;
   const size_t tv_bytes = (size_t)A.L.nv * kTraceThreads * sizeof(float2);
   shadow_dirs_kernel<<<grid_for(rpg * n_groups), kTraceThreads, tv_bytes, s>>>(A);
   PE_TRY_LAUNCH("shadow_dirs_kernel");

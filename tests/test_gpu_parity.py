@@ -330,6 +330,26 @@ def test_po_field_bistatic_matches_oracle(case, request):
     assert blocked > 0          # the case exercises receiver shadowing
 
 
+@pytest.mark.parametrize("case", GEOMS)
+def test_po_at_every_bounce_matches_oracle(case, request):
+    api, pipe = _mods()
+    d = request.getfixturevalue(case)
+    sc = d["sc"]
+    c, r = scenes.bounding_sphere(sc.pos)
+    views = pipe.views_from_angles([90.0, 60.0], [45.0, 30.0], c, r * 1.02, 40, 40)
+    mb = 2 if case == "small_geom" else 3
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    freqs = scenes.freq_grid(2.5e9, 3.5e9, 3)
+    E = _cplx(pipe.field_every_bounce(views, keys, d["nrm"], d["geom"], d["prm"], mb, freqs))
+    api.stream_check()
+    eps = float(d["prm"].eps)
+    for a, v in enumerate(views):
+        ov = _oracle_view(v)
+        Eo = oracle.po_field_every_bounce(ov, d["S"], oracle.gfb(sc, ov, "fp32"), mb, eps,
+                                          float(d["prm"].overlap_r), freqs)
+        assert field_err(E[a], Eo).max() < 1e-3, f"angle {a}"
+
+
 # ----------------------------------------------------------------------------
 # a7: the whole sweep
 # ----------------------------------------------------------------------------
