@@ -66,8 +66,35 @@ __global__ void __launch_bounds__(kSplatThreads)
     float fj0 = fmaxf(floorf(cj - rp), 0.0f), fj1 = fminf(ceilf(cj + rp), (float)(H - 1));
     if (!(fi0 <= fi1) || !(fj0 <= fj1)) continue;
     int i0 = (int)fi0, i1 = (int)fi1, j0 = (int)fj0, j1 = (int)fj1;
-    for (int j = j0; j <= j1; ++j)
-      for (int i = i0; i <= i1; ++i) {
+    // Per row, the columns whose ray can hit: the screen points (a, b)
+    // (metres from c's projection along u, v) hitting the disk satisfy
+    //   a^2 nw^2 + (a nu + b nv)^2 + b^2 nw^2 <= R^2 nw^2
+    // (n in the view frame; the tube is the circle nu = nv = 0, nw = 1),
+    // solved for a with R widened far beyond the rounding of the exact test,
+    // which still decides every pixel.  Near edge-on disks keep the square.
+    float nu = 0.0f, nv = 0.0f, nw = 1.0f;
+    if (mode == 0) {
+      nu = nn.x * V.u[0] + nn.y * V.u[1] + nn.z * V.u[2];
+      nv = nn.x * V.v[0] + nn.y * V.v[1] + nn.z * V.v[2];
+      nw = -(nn.x * V.d[0] + nn.y * V.d[1] + nn.z * V.d[2]);
+    }
+    const float Rw = R * 1.0001f + 0.02f * V.pitch;
+    const float qa = nw * nw + nu * nu;
+    const bool rows = qa > 1e-3f;
+    for (int j = j0; j <= j1; ++j) {
+      int ia = i0, ib = i1;
+      if (rows) {
+        const float b = ((float)j - cj) * V.pitch;
+        const float qb = 2.0f * b * nu * nv;
+        const float qc = b * b * (nw * nw + nv * nv) - Rw * Rw * nw * nw;
+        const float disc = qb * qb - 4.0f * qa * qc;
+        if (disc < 0.0f) continue;
+        const float sq = sqrtf(disc), inv2a = 0.5f / qa;
+        const float alo = (-qb - sq) * inv2a, ahi = (-qb + sq) * inv2a;
+        ia = max(ia, (int)floorf(ci + alo * inv - 0.05f));
+        ib = min(ib, (int)ceilf(ci + ahi * inv + 0.05f));
+      }
+      for (int i = ia; i <= ib; ++i) {
         float depth;
         if (!splat_test(V, i, j, c, nn, R, mode, depth)) continue;
         unsigned long long key =
@@ -75,6 +102,7 @@ __global__ void __launch_bounds__(kSplatThreads)
         unsigned long long *slot = kv + (int64_t)j * W + i;
         if (key < __ldcg(slot)) atomicMin(slot, key);
       }
+    }
   }
 }
 
