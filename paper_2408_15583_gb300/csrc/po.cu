@@ -58,7 +58,7 @@ __device__ __forceinline__ pe_f3 cross(pe_f3 a, pe_f3 b) {
 }
 __device__ __forceinline__ float dotf(pe_f3 a, pe_f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-__global__ void __launch_bounds__(kPoThreads, 3)
+__global__ void __launch_bounds__(kPoThreads, 4)
     po_kernel(const pe_hits h, const __grid_constant__ po_consts C, double *__restrict__ part) {
   // per staged ray: {au, av, dh, dl}, {V0..V3}, {V4, V5, -, -}: three
   // broadcast 16-byte loads per term
