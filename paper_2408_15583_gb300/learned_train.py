@@ -125,7 +125,7 @@ def _cat(items, key):
 
 
 def train(model: UNet, data: List[dict], steps: int, batch: int, lr0=1e-3, seed=0,
-          log_every=0):
+          log_every=0, step0=0):
     """Mini-batches of `batch` views drawn from the whole set; the paper's
     halving schedule (Sec. IV-A) with `steps_per_epoch` = views / batch."""
     W = data[0]["vs"].W
@@ -140,7 +140,7 @@ def train(model: UNet, data: List[dict], steps: int, batch: int, lr0=1e-3, seed=
     hist = []
     for step in range(steps):
         idx = torch.from_numpy(rng.choice(nv, size=batch, replace=False)).to(x.device)
-        lr = lr_schedule(step, spe, lr0=lr0, floor=1e-6)
+        lr = lr_schedule(step0 + step, spe, lr0=lr0, floor=1e-6)
         loss = model.train_step(x[idx].reshape(-1).contiguous(), d[idx].reshape(-1).contiguous(),
                                 n[idx].reshape(-1, 3).contiguous(), m[idx].reshape(-1).contiguous(),
                                 batch, W, W, lr)
@@ -260,3 +260,42 @@ def finite_k_study(items: List[dict], Ks=(4, 8, 16), delta_px=2.0, device="cuda:
         out[f"K={K}"] = {"changed_point_fraction": diff / max(n_hit, 1),
                          "rms_depth_change_pitches": math.sqrt(sq / max(n_hit, 1))}
     return out
+
+
+def study(n_train=160, n_held=16, views_train=16, views_held=12, W=256, steps=(500, 1500, 3000),
+          batch=32, lr0=1e-3, seed=5):
+    """Train on pairs from n_train random targets and report, at each step
+    count in `steps`, the held-out RCS RMSE (dB) of the network's GFB and of
+    the coarse GFB, both against the dense surfel GFB."""
+    import scenes
+    widths, blocks = (32, 64, 128, 256), (2, 2, 2, 2)
+    net = UNet(scenes.unet_init(seed, widths, blocks), widths, blocks, "cuda:0")
+    t0 = time.perf_counter()
+    train_set = dataset(n_train, views_train, W, seed=seed * 7 + 1)
+    held = dataset(n_held, views_held, W, seed=seed * 7 + 2)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    rows, done = [], 0
+    for target in steps:
+        t1 = time.perf_counter()
+        train(net, train_set, target - done, batch, lr0=lr0, seed=seed + done, step0=done)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        done = target
+        res = evaluate(net, held)
+        rows.append({"steps": target, "train_s": dt,
+                     "rmse_db_learned": float(np.mean([r["learned"] for r in res])),
+                     "rmse_db_coarse": float(np.mean([r["coarse"] for r in res]))})
+    return {"pairs": len(train_set) * views_train, "held_out_views": n_held * views_held,
+            "W": W, "batch": batch, "data_s": t_data, "checkpoints": rows}
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "study":
+        kw = {}
+        for a in sys.argv[2:]:
+            k, v = a.split("=")
+            kw[k] = tuple(int(x) for x in v.split(",")) if k == "steps" else int(v)
+        print(json.dumps(study(**kw)))
