@@ -314,13 +314,13 @@ MARCH_BYTES_PER_QUERY = 152
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 635.9 MB
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 648.0 MB
 # over 6,332,964 queries), valid only for the sources it was taken on (their
 # SHA-256 prefixes); scaled to a full launch by the number of queries.
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 100.4,
-                     "sources": {"paper_2408_15583_gb300/csrc/trace.cu": "7d636cca27545afb",
-                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "e5600a88c6aa3647",
-                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "b7a48171c06d6030"}}
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 102.3,
+                     "sources": {"paper_2408_15583_gb300/csrc/trace.cu": "fc23d4983b37e979",
+                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "5f323e9a219af691",
+                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "d18e0da1ebb1e0df"}}
 
 
 def _traffic_valid(rec):
