@@ -255,6 +255,16 @@ class GpuExecutor:
         self.dev = torch.device(device)
         self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(n_slots)]
         self.geo: "OrderedDict[str, dict]" = OrderedDict()
+        # the bounding sphere depends on the scene alone: computed once per
+        # scene key (it is the largest host-side cost of a request)
+        self.spheres: Dict[str, tuple] = {}
+
+    def _sphere(self, req: RcsRequest):
+        sp = self.spheres.get(req.scene_key)
+        if sp is None:
+            sp = _bounding_sphere(req.pos)
+            self.spheres[req.scene_key] = sp
+        return sp
 
     # geometry cache
     def geometry_cached(self, key: str) -> bool:
@@ -282,8 +292,8 @@ class GpuExecutor:
         with torch.cuda.stream(s):
             pos, nrm, rad = [t.to(self.dev, non_blocking=True) for t in hp]
             g = self.geo.get(req.scene_key)
+            c, r = self._sphere(req)
             if g is None:
-                c, r = _bounding_sphere(req.pos)
                 th = [60.0] * 4 + [120.0] * 4
                 ph = [45.0, 135.0, 225.0, 315.0] * 2
                 gv = pipe.views_from_angles(th, ph, c, r * 1.02, req.view_W, req.view_W)
@@ -298,7 +308,6 @@ class GpuExecutor:
                 s.wait_event(g["ready"])
                 self.geo.move_to_end(req.scene_key)
             g["users"] += 1
-            c, r = _bounding_sphere(req.pos)
             args = api.SweepArgs(req.theta_deg, req.phi_deg, req.W, req.W, c, r * 1.02,
                                  req.freqs_hz, req.max_bounces)
             stats = torch.zeros(8, dtype=torch.int64, device=self.dev)
