@@ -71,7 +71,7 @@ def lib():
         P = C.c_void_p
         _lib.or_gfb.argtypes = [C.c_int, P, P, P, P, C.c_int64, C.c_int, C.c_double,
                                 P, C.c_int64, P, P, P]
-        _lib.or_aggregate.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_double, P,
+        _lib.or_aggregate.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_double, C.c_int, P,
                                       C.c_double, C.c_int, P, P, P, P, P, P]
         _lib.or_aggregate.restype = C.c_int64
         _lib.or_trace.argtypes = [C.c_int, P, P, C.c_int64, P, P, P, P, P, P, P,
@@ -220,6 +220,7 @@ class FuseParams:
     bmin: np.ndarray    # float32-representable
     inv_vox: float      # float32-representable
     G: int = 256
+    edge_mode: int = 0  # 0: the edge rule of c14; 1: Canny on the depth map
 
 
 def fuse_params(scene, G: int = 256, tau: float = 3.0) -> FuseParams:
@@ -246,7 +247,8 @@ def aggregate(gfbs, fp: FuseParams, mode: str = "fp32") -> Splats:
     keep = np.empty(tot, np.uint8)
     bmin = np.ascontiguousarray(fp.bmin, dtype=np.float64)
     ns = lib().or_aggregate(_fp(mode), len(gfbs), views, _p(depth), _p(nrm), _p(mask),
-                            fp.tau, _p(bmin), fp.inv_vox, fp.G, _p(oid), _p(oc), _p(on),
+                            fp.tau, int(fp.edge_mode), _p(bmin), fp.inv_vox, fp.G, _p(oid),
+                            _p(oc), _p(on),
                             _p(orr), _p(ocnt), _p(keep))
     return Splats(oid[:ns].copy(), oc[:ns].copy(), on[:ns].copy(), orr[:ns].copy(),
                   ocnt[:ns].copy(), keep)

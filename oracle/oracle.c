@@ -64,14 +64,14 @@ void or_gfb_topk(int fp64, const or_view *v, const float *pos, int64_t n, double
 }
 
 int64_t or_aggregate(int fp64, int nv, const or_view *views, const double *depth,
-                     const double *nrm, const uint8_t *mask, double tau,
+                     const double *nrm, const uint8_t *mask, double tau, int edge_mode,
                      const double *bmin, double inv_vox, int G, int64_t *out_id,
                      double *out_c, double *out_n, double *out_r,
                      int32_t *out_count, uint8_t *keep) {
   if (fp64)
-    return aggregate_f64(nv, views, depth, nrm, mask, tau, bmin, inv_vox, G,
+    return aggregate_f64(nv, views, depth, nrm, mask, tau, edge_mode, bmin, inv_vox, G,
                          out_id, out_c, out_n, out_r, out_count, keep);
-  return aggregate_f32(nv, views, depth, nrm, mask, tau, bmin, inv_vox, G, out_id,
+  return aggregate_f32(nv, views, depth, nrm, mask, tau, edge_mode, bmin, inv_vox, G, out_id,
                        out_c, out_n, out_r, out_count, keep);
 }
 

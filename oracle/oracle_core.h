@@ -196,6 +196,99 @@ static void SFX(gfb_topk)(const or_view *vin, const float *pos, int64_t n, doubl
 /* Edge rule (the paper names a Canny operator without thresholds): a hit
  * pixel is an edge if a 4-neighbour is outside the image or empty, or if a
  * neighbour's depth differs by more than tau * L. */
+/* Canny edges of one view's depth map (edge mode 1; the paper removes GFB
+ * edges with a Canny filter before fusion, Sec. III-B, without its
+ * parameters).  On valid pixels only: 5x5 binomial smoothing ([1 4 6 4 1]^2 /
+ * 256; samples outside the image or empty take the centre's depth), Sobel
+ * gradient of the smoothed map (samples outside/empty take the centre's
+ * value), magnitude sqrt(gx^2 + gy^2), non-maximum suppression along the
+ * gradient's sector (0, 45, 90, 135 degrees by tan 22.5 and tan 67.5; absent
+ * neighbours count 0; ties kept), thresholds high = 8 tau L (the Sobel
+ * response to a slope of tau pitches per pixel) and low = high / 2,
+ * hysteresis over the 8 neighbours.  edge[p] = 1 for Canny edge pixels. */
+static R SFX(cs)(const R *S, const uint8_t *mask, int W, int H, int i, int j, int di, int dj) {
+  int ii = i + di, jj = j + dj;
+  if (ii < 0 || jj < 0 || ii >= W || jj >= H || !mask[(int64_t)jj * W + ii])
+    return S[(int64_t)j * W + i];
+  return S[(int64_t)jj * W + ii];
+}
+
+static void SFX(canny)(const R *depth, const uint8_t *mask, int W, int H, R L, R tau,
+                       uint8_t *edge) {
+  const int64_t n = (int64_t)W * H;
+  R *S = (R *)calloc((size_t)n + 1, sizeof(R));
+  R *Gm = (R *)calloc((size_t)n + 1, sizeof(R));
+  uint8_t *sec = (uint8_t *)calloc((size_t)n + 1, 1);
+  uint8_t *st = (uint8_t *)calloc((size_t)n + 1, 1);
+  int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  static const int b[5] = {1, 4, 6, 4, 1};
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < W; ++i) {
+      int64_t p = (int64_t)j * W + i;
+      if (!mask[p]) continue;
+      R acc = (R)0;
+      for (int dj = -2; dj <= 2; ++dj)
+        for (int di = -2; di <= 2; ++di) {
+          int ii = i + di, jj = j + dj;
+          int in = ii >= 0 && jj >= 0 && ii < W && jj < H && mask[(int64_t)jj * W + ii];
+          R dq = in ? depth[(int64_t)jj * W + ii] : depth[p];
+          R w = (R)(b[dj + 2] * b[di + 2]) / (R)256;
+          acc = acc + w * dq;
+        }
+      S[p] = acc;
+    }
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < W; ++i) {
+      int64_t p = (int64_t)j * W + i;
+      if (!mask[p]) continue;
+#define CS(a, c) SFX(cs)(S, mask, W, H, i, j, a, c)
+      R gx = ((CS(1, -1) - CS(-1, -1)) + (R)2 * (CS(1, 0) - CS(-1, 0))) + (CS(1, 1) - CS(-1, 1));
+      R gy = ((CS(-1, 1) - CS(-1, -1)) + (R)2 * (CS(0, 1) - CS(0, -1))) + (CS(1, 1) - CS(1, -1));
+#undef CS
+      Gm[p] = SQRT(gx * gx + gy * gy);
+      R ax = gx < (R)0 ? -gx : gx, ay = gy < (R)0 ? -gy : gy;
+      if (ay <= (R)0.41421356f * ax) sec[p] = 0;
+      else if (ay >= (R)2.41421356f * ax) sec[p] = 2;
+      else sec[p] = ((gx > (R)0) == (gy > (R)0)) ? 1 : 3;
+    }
+  const R high = ((R)8 * tau) * L, low = (R)0.5 * high;
+  static const int nx[4] = {1, 1, 0, 1}, ny[4] = {0, 1, 1, -1};
+  int64_t top = 0;
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < W; ++i) {
+      int64_t p = (int64_t)j * W + i;
+      if (!mask[p]) continue;
+      R g = Gm[p], g1 = (R)0, g2 = (R)0;
+      int a = sec[p];
+      int i1 = i + nx[a], j1 = j + ny[a], i2 = i - nx[a], j2 = j - ny[a];
+      if (i1 >= 0 && j1 >= 0 && i1 < W && j1 < H && mask[(int64_t)j1 * W + i1]) g1 = Gm[(int64_t)j1 * W + i1];
+      if (i2 >= 0 && j2 >= 0 && i2 < W && j2 < H && mask[(int64_t)j2 * W + i2]) g2 = Gm[(int64_t)j2 * W + i2];
+      if (!(g > (R)0 && g >= g1 && g >= g2)) continue;
+      st[p] = g >= high ? 2 : (g >= low ? 1 : 0);
+      if (st[p] == 2) stack[top++] = p;
+    }
+  while (top > 0) { /* hysteresis: weak pixels connected to a strong one */
+    int64_t p = stack[--top];
+    int i = (int)(p % W), j = (int)(p / W);
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        int ii = i + di, jj = j + dj;
+        if (ii < 0 || jj < 0 || ii >= W || jj >= H) continue;
+        int64_t q = (int64_t)jj * W + ii;
+        if (st[q] == 1) {
+          st[q] = 2;
+          stack[top++] = q;
+        }
+      }
+  }
+  for (int64_t p = 0; p < n; ++p) edge[p] = st[p] == 2;
+  free(S);
+  free(Gm);
+  free(sec);
+  free(st);
+  free(stack);
+}
+
 static int SFX(is_edge)(const R *depth, const uint8_t *mask, int W, int H, int i,
                         int j, R tauL) {
   static const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
@@ -254,7 +347,7 @@ static double SFX(eq22)(const R *n, const R *p, double L) {
  * splats written (sorted by splat id = global owner pixel index). */
 static int64_t SFX(aggregate)(int nv, const or_view *views, const double *depth_in,
                               const double *nrm_in, const uint8_t *mask,
-                              double tau, const double *bmin, double inv_vox,
+                              double tau, int edge_mode, const double *bmin, double inv_vox,
                               int G, int64_t *out_id, double *out_c,
                               double *out_n, double *out_r, int32_t *out_count,
                               uint8_t *keep_out) {
@@ -270,11 +363,18 @@ static int64_t SFX(aggregate)(int nv, const or_view *views, const double *depth_
     SFX(view) V;
     SFX(load_view)(&views[v], &V);
     R tauL = (R)tau * V.L;
+    uint8_t *cedge = NULL;
+    if (edge_mode == 1) {
+      cedge = (uint8_t *)calloc((size_t)V.W * V.H + 1, 1);
+      SFX(canny)(depth + off, mask + off, V.W, V.H, V.L, (R)tau, cedge);
+      tauL = (R)INFINITY; /* the border part of the edge rule stays */
+    }
     for (int j = 0; j < V.H; ++j)
       for (int i = 0; i < V.W; ++i) {
         int64_t q = off + (int64_t)j * V.W + i;
         uint8_t keep = 0;
-        if (mask[q] && !SFX(is_edge)(depth + off, mask + off, V.W, V.H, i, j, tauL)) {
+        if (mask[q] && !SFX(is_edge)(depth + off, mask + off, V.W, V.H, i, j, tauL) &&
+            !(cedge && cedge[(int64_t)j * V.W + i])) {
           keep = 1;
           R o[3], p[3];
           SFX(pixel_origin)(&V, i, j, o);
@@ -299,6 +399,7 @@ static int64_t SFX(aggregate)(int nv, const or_view *views, const double *depth_
         }
         if (keep_out) keep_out[q] = keep;
       }
+    free(cedge);
     off += (int64_t)V.W * V.H;
   }
   qsort(ent, (size_t)ne, sizeof(SFX(entry)), SFX(cmp_entry));

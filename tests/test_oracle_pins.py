@@ -683,3 +683,48 @@ def test_bistatic_psi_toward_the_transmitter_is_the_monostatic_psi():
     assert two.sum() > 50
     assert np.array_equal(psi[two], tr.psi[two])
     assert psi[tr.M == 1].mean() > 0.95
+
+
+# ----------------------------------------------------------------------------
+# Canny edge mode of the fusion (edge_mode 1)
+# ----------------------------------------------------------------------------
+
+def _canny_keep(depth, mode="fp32", tau=3.0):
+    W = H = depth.shape[0]
+    v = down_view(W, H, 0.125)
+    g = _handmade_gfb(v, depth.ravel(), np.tile([0.0, 0.0, 1.0], (W * H, 1)), np.ones(W * H))
+    fp = oracle.FuseParams(tau=tau, bmin=np.array([-2.0, -2.0, -40.0]), inv_vox=8.0, G=256,
+                           edge_mode=1)
+    return oracle.aggregate([g], fp, mode).keep.reshape(H, W)
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_canny_ramp_threshold_and_flat_map(mode):
+    # a linear ramp of slope s metres per pixel: smoothing keeps it, Sobel
+    # gives 8 s, so interior pixels are strong iff 8 s >= 8 tau L = 3 (all
+    # equal: the suppression keeps them); below low = 1.5 nothing survives.
+    # Dyadic slopes keep every step exact in both precisions.
+    tau, n = 3.0, 24
+    ii = np.arange(n)[None, :] * np.ones((n, 1))
+    inner = (slice(3, n - 3), slice(3, n - 3))
+    keep_hi = _canny_keep(5.0 + 0.5 * ii, mode, tau)      # 8 s = 4 >= 3
+    keep_lo = _canny_keep(5.0 + 0.125 * ii, mode, tau)    # 8 s = 1 < 1.5
+    keep_flat = _canny_keep(np.full((n, n), 5.0), mode, tau)
+    assert not keep_hi[inner].any()                 # every interior pixel an edge
+    assert keep_lo[inner].all() and keep_flat[1:-1, 1:-1].all()
+    assert not keep_flat[0].any()                   # the border rule still applies
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_canny_step_gives_the_two_columns_beside_it(mode):
+    # a depth step between columns 9 and 10: the smoothed profile is
+    # symmetric about 9.5, the two columns beside the step tie in gradient and
+    # both survive suppression; everything else keeps (besides the border)
+    n = 24
+    d = np.full((n, n), 5.0)
+    d[:, 10:] = 5.0 + 20 * 0.125
+    keep = _canny_keep(d, mode)
+    interior = keep[1:-1, 1:-1]
+    cols = np.flatnonzero(~interior.any(axis=0)) + 1
+    assert list(cols) == [9, 10]
+    assert interior[:, [c - 1 for c in range(1, n - 1) if c not in (9, 10)]].all()
