@@ -69,15 +69,22 @@ typedef struct {
  *   delta      ray-tube radius of Alg. 1 (tube mode), metres;
  *   eps        minimum travel distance of reflected rays (Sec. III-B, Fig. 4b);
  *   overlap_r  radius r of the Eq. 23 overlap sphere, metres;
- *   edge_tau   edge rule: a GFB pixel is an edge if a 4-neighbour is outside
- *              the image or empty, or differs in depth by more than
- *              edge_tau * pitch (stands in for the paper's Canny filter);
+ *   edge_tau   edge rule (edge_mode 0): a GFB pixel is an edge if a
+ *              4-neighbour is outside the image or empty, or differs in depth
+ *              by more than edge_tau * pitch;
  *   fuse_grid  voxel grid size G of the fusion step (Sec. III-B: 256);
  *   bbox_min   voxel grid origin (float32), inv_voxel = G / (longest bbox edge)
  *              as float32;
  *   first_bounce_from_geom  0: bounce 1 from the incidence view's GFB
  *              (PO path of Sec. III-A); 1: bounce 1 traced against the
- *              aggregated splats as in Alg. 3. */
+ *              aggregated splats as in Alg. 3;
+ *   edge_mode  0: the edge rule above; 1: a Canny filter on each view's depth
+ *              map (the paper's choice, Sec. III-B): 5x5 binomial smoothing,
+ *              Sobel gradient, suppression across the gradient, thresholds
+ *              8 edge_tau pitch (high) and half of it (low), hysteresis over 8
+ *              neighbours; a pixel next to the image border or an empty pixel
+ *              is an edge in both modes.  Mode 1 synchronises the stream
+ *              while the hysteresis converges. */
 typedef struct {
   float delta;
   float eps;
@@ -87,6 +94,7 @@ typedef struct {
   float bbox_min[3];
   float inv_voxel;
   int32_t first_bounce_from_geom;
+  int32_t edge_mode;
 } pe_params;
 
 /* Aggregated splat geometry (Alg. 3 lines 1-3).  One caller-allocated device

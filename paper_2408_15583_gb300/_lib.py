@@ -27,7 +27,8 @@ class PeView(C.Structure):
 class PeParams(C.Structure):
     _fields_ = [("delta", C.c_float), ("eps", C.c_float), ("overlap_r", C.c_float),
                 ("edge_tau", C.c_float), ("fuse_grid", C.c_int32), ("bbox_min", C.c_float * 3),
-                ("inv_voxel", C.c_float), ("first_bounce_from_geom", C.c_int32)]
+                ("inv_voxel", C.c_float), ("first_bounce_from_geom", C.c_int32),
+                ("edge_mode", C.c_int32)]
 
 
 class PeGeom(C.Structure):

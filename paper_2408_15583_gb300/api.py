@@ -67,7 +67,8 @@ def view_from_struct(o, u, v, d, pitch, W, H) -> PeView:
 
 
 def make_params(pos: np.ndarray, eps: float, overlap_r: float, G: int = 256, tau: float = 3.0,
-                delta: float = 0.0, first_bounce_from_geom: bool = False) -> PeParams:
+                delta: float = 0.0, first_bounce_from_geom: bool = False,
+                edge_mode: int = 0) -> PeParams:
     """pe_params for a point set: voxel grid over its bounding box with cubic
     voxels of (longest edge)/G, origin and inverse voxel size rounded to FP32."""
     p = np.asarray(pos, dtype=np.float64)
@@ -83,6 +84,7 @@ def make_params(pos: np.ndarray, eps: float, overlap_r: float, G: int = 256, tau
         prm.bbox_min[k] = float(np.float32(lo[k]))
     prm.inv_voxel = float(np.float32(G / ext))
     prm.first_bounce_from_geom = 1 if first_bounce_from_geom else 0
+    prm.edge_mode = int(edge_mode)
     return prm
 
 

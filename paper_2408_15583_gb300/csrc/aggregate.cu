@@ -25,10 +25,137 @@ __device__ __forceinline__ int view_of(const pe_geom_layout &L, int64_t g) {
   return v;
 }
 
+// ---- Canny edges of the views' depth maps (edge mode 1) --------------------
+// The same arithmetic, in the same order, as the reference statement: 5x5
+// binomial smoothing over valid pixels (absent samples take the centre's
+// depth), Sobel on the smoothed map, suppression across the gradient's
+// sector, thresholds 8 tau L and half of it, hysteresis over 8 neighbours.
+__device__ __forceinline__ bool canny_in(const pe_geom_layout &L, const uint8_t *mask, int64_t off,
+                                         const pe_view &V, int i, int j) {
+  return i >= 0 && j >= 0 && i < V.W && j < V.H && mask[off + (int64_t)j * V.W + i];
+}
+
+__global__ void canny_smooth_kernel(const __grid_constant__ pe_geom_layout L,
+                                    const float4 *__restrict__ nd,
+                                    const uint8_t *__restrict__ mask, float *__restrict__ S) {
+  const int64_t total = L.pix_off[L.nv];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    if (!mask[g]) continue;
+    const int v = view_of(L, g);
+    const pe_view &V = L.view[v];
+    const int64_t off = L.pix_off[v], p = g - off;
+    const int i = (int)(p % V.W), j = (int)(p / V.W);
+    const float t = nd[g].w;
+    const int b[5] = {1, 4, 6, 4, 1};
+    float acc = 0.0f;
+    for (int dj = -2; dj <= 2; ++dj)
+      for (int di = -2; di <= 2; ++di) {
+        const float dq = canny_in(L, mask, off, V, i + di, j + dj)
+                             ? nd[off + (int64_t)(j + dj) * V.W + (i + di)].w
+                             : t;
+        const float w = pe_div((float)(b[dj + 2] * b[di + 2]), 256.0f);
+        acc = pe_add(acc, pe_mul(w, dq));
+      }
+    S[g] = acc;
+  }
+}
+
+__global__ void canny_grad_kernel(const __grid_constant__ pe_geom_layout L,
+                                  const uint8_t *__restrict__ mask, const float *__restrict__ S,
+                                  float *__restrict__ Gm, uint8_t *__restrict__ sec) {
+  const int64_t total = L.pix_off[L.nv];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    if (!mask[g]) continue;
+    const int v = view_of(L, g);
+    const pe_view &V = L.view[v];
+    const int64_t off = L.pix_off[v], p = g - off;
+    const int i = (int)(p % V.W), j = (int)(p / V.W);
+    auto cs = [&](int di, int dj) -> float {
+      return canny_in(L, mask, off, V, i + di, j + dj) ? S[off + (int64_t)(j + dj) * V.W + (i + di)]
+                                                        : S[g];
+    };
+    const float gx = pe_add(pe_add(pe_sub(cs(1, -1), cs(-1, -1)), pe_mul(2.0f, pe_sub(cs(1, 0), cs(-1, 0)))),
+                            pe_sub(cs(1, 1), cs(-1, 1)));
+    const float gy = pe_add(pe_add(pe_sub(cs(-1, 1), cs(-1, -1)), pe_mul(2.0f, pe_sub(cs(0, 1), cs(0, -1)))),
+                            pe_sub(cs(1, 1), cs(1, -1)));
+    Gm[g] = pe_sqrt(pe_add(pe_mul(gx, gx), pe_mul(gy, gy)));
+    const float ax = fabsf(gx), ay = fabsf(gy);
+    uint8_t sc;
+    if (ay <= pe_mul(0.41421356f, ax)) sc = 0;
+    else if (ay >= pe_mul(2.41421356f, ax)) sc = 2;
+    else sc = ((gx > 0.0f) == (gy > 0.0f)) ? 1 : 3;
+    sec[g] = sc;
+  }
+}
+
+__global__ void canny_nms_kernel(const __grid_constant__ pe_geom_layout L,
+                                 const uint8_t *__restrict__ mask, const float *__restrict__ Gm,
+                                 const uint8_t *__restrict__ sec, float tau,
+                                 uint8_t *__restrict__ state) {
+  const int64_t total = L.pix_off[L.nv];
+  const int nx[4] = {1, 1, 0, 1}, ny[4] = {0, 1, 1, -1};
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t st = 0;
+    if (mask[g]) {
+      const int v = view_of(L, g);
+      const pe_view &V = L.view[v];
+      const int64_t off = L.pix_off[v], p = g - off;
+      const int i = (int)(p % V.W), j = (int)(p / V.W);
+      const int a = sec[g];
+      const float gm = Gm[g];
+      const float g1 = canny_in(L, mask, off, V, i + nx[a], j + ny[a])
+                           ? Gm[off + (int64_t)(j + ny[a]) * V.W + (i + nx[a])] : 0.0f;
+      const float g2 = canny_in(L, mask, off, V, i - nx[a], j - ny[a])
+                           ? Gm[off + (int64_t)(j - ny[a]) * V.W + (i - nx[a])] : 0.0f;
+      if (gm > 0.0f && gm >= g1 && gm >= g2) {
+        const float high = pe_mul(pe_mul(8.0f, tau), V.pitch), low = pe_mul(0.5f, high);
+        st = gm >= high ? 2 : (gm >= low ? 1 : 0);
+      }
+    }
+    state[g] = st;
+  }
+}
+
+// One hysteresis pass: a weak pixel with a strong 8-neighbour becomes strong.
+// Passes repeat until none changes; the fixed point is the set of weak pixels
+// connected to a strong one, whatever the order of the updates.
+__global__ void canny_hyst_kernel(const __grid_constant__ pe_geom_layout L,
+                                  uint8_t *__restrict__ state, unsigned int *changed) {
+  const int64_t total = L.pix_off[L.nv];
+  unsigned int ch = 0;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    if (state[g] != 1) continue;
+    const int v = view_of(L, g);
+    const pe_view &V = L.view[v];
+    const int64_t off = L.pix_off[v], p = g - off;
+    const int i = (int)(p % V.W), j = (int)(p / V.W);
+    bool up = false;
+    for (int dj = -1; dj <= 1 && !up; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di, jj = j + dj;
+        if (ii < 0 || jj < 0 || ii >= V.W || jj >= V.H) continue;
+        if (state[off + (int64_t)jj * V.W + ii] == 2) {
+          up = true;
+          break;
+        }
+      }
+    if (up) {
+      state[g] = 2;
+      ++ch;
+    }
+  }
+  if (ch) atomicAdd(changed, ch);
+}
+
 // Edge rule + voxel of the pixel's surface point; counts contributors.
 __global__ void fuse_classify_kernel(const __grid_constant__ pe_geom_layout L,
                                      const float4 *__restrict__ nd,
                                      const uint8_t *__restrict__ mask, float tau,
+                                     const uint8_t *__restrict__ canny_state,
                                      float bx, float by, float bz, float inv_vox, int G,
                                      uint32_t *__restrict__ vox_of, uint32_t *__restrict__ count) {
   int64_t total = L.pix_off[L.nv];
@@ -41,8 +168,9 @@ __global__ void fuse_classify_kernel(const __grid_constant__ pe_geom_layout L,
       int64_t off = L.pix_off[v], p = g - off;
       int i = (int)(p % V.W), j = (int)(p / V.W);
       float t = nd[g].w;
-      float tauL = pe_mul(tau, V.pitch);
-      bool edge = false;
+      // edge mode 1: Canny edges replace the depth-jump part of the rule
+      float tauL = canny_state ? INFINITY : pe_mul(tau, V.pitch);
+      bool edge = canny_state && canny_state[g] == 2;
       const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -432,6 +560,8 @@ int sms() {
 struct agg_ws {
   uint32_t *count, *offs, *tile, *vox_of;
   unsigned long long *entries;
+  uint8_t *canny_state;     // edge mode 1 (the other Canny buffers alias
+  unsigned int *changed;    // entries and vox_of, which the fusion fills later)
 };
 
 agg_ws carve_agg(pe_carve &c, int64_t total_pix, int G) {
@@ -442,6 +572,8 @@ agg_ws carve_agg(pe_carve &c, int64_t total_pix, int G) {
   w.tile = c.take<uint32_t>((size_t)((nv + kScanTile - 1) / kScanTile));
   w.vox_of = c.take<uint32_t>((size_t)total_pix);
   w.entries = c.take<unsigned long long>((size_t)total_pix);
+  w.canny_state = c.take<uint8_t>((size_t)total_pix);
+  w.changed = c.take<unsigned int>(1);
   return w;
 }
 
@@ -523,9 +655,39 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   PE_TRY_CUDA(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * nvox, s));
   PE_TRY_CUDA(cudaMemsetAsync(cr, 0, sizeof(float4) * total_pix, s));
   PE_TRY_CUDA(cudaMemsetAsync(nf, 0, sizeof(float4) * total_pix, s));
+  const uint8_t *cstate = nullptr;
+  if (prm->edge_mode == 1) {
+    float *S = reinterpret_cast<float *>(w.entries), *Gm = S + total_pix;
+    uint8_t *sec = reinterpret_cast<uint8_t *>(w.vox_of);
+    canny_smooth_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, nd, gfb_mask, S);
+    PE_TRY_LAUNCH("canny_smooth_kernel");
+    canny_grad_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, gfb_mask, S, Gm, sec);
+    PE_TRY_LAUNCH("canny_grad_kernel");
+    canny_nms_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, gfb_mask, Gm, sec,
+                                                                    prm->edge_tau, w.canny_state);
+    PE_TRY_LAUNCH("canny_nms_kernel");
+    // hysteresis: batches of passes until a batch changes nothing
+    bool converged = false;
+    for (int batch = 0; batch < 4096 && !converged; ++batch) {
+      PE_TRY_CUDA(cudaMemsetAsync(w.changed, 0, sizeof(unsigned int), s));
+      for (int k = 0; k < 8; ++k) {
+        canny_hyst_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, w.canny_state,
+                                                                         w.changed);
+        PE_TRY_LAUNCH("canny_hyst_kernel");
+      }
+      unsigned int h = 0;
+      PE_TRY_CUDA(cudaMemcpyAsync(&h, w.changed, sizeof(h), cudaMemcpyDeviceToHost, s));
+      PE_TRY_CUDA(cudaStreamSynchronize(s));
+      converged = h == 0;
+    }
+    if (!converged) return pe_fail(PE_EOVERFLOW, "pe_aggregate_views: Canny hysteresis did not converge");
+    cstate = w.canny_state;
+  } else if (prm->edge_mode != 0) {
+    return pe_fail(PE_EINVAL, "pe_aggregate_views: edge_mode must be 0 or 1");
+  }
   fuse_classify_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(
-      L, nd, gfb_mask, prm->edge_tau, prm->bbox_min[0], prm->bbox_min[1], prm->bbox_min[2],
-      prm->inv_voxel, G, w.vox_of, w.count);
+      L, nd, gfb_mask, prm->edge_tau, cstate, prm->bbox_min[0], prm->bbox_min[1],
+      prm->bbox_min[2], prm->inv_voxel, G, w.vox_of, w.count);
   PE_TRY_LAUNCH("fuse_classify_kernel");
   int64_t n_tiles = (nvox + kScanTile - 1) / kScanTile;
   if (n_tiles > kScanTile) return pe_fail(PE_EUNSUPPORTED, "voxel grid too large for the scan");

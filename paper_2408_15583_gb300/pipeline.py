@@ -24,12 +24,12 @@ def views_from_angles(theta_deg: Sequence[float], phi_deg: Sequence[float], cent
 
 
 def default_params(pos: np.ndarray, gviews: Sequence[PeView], G: int = 256, tau: float = 3.0,
-                   first_bounce_from_geom: bool = False) -> PeParams:
+                   first_bounce_from_geom: bool = False, edge_mode: int = 0) -> PeParams:
     """epsilon = r = the smallest aggregation-view pitch (values the paper
     leaves open)."""
     lmin = float(min(v.pitch for v in gviews))
     return api.make_params(pos, lmin, lmin, G=G, tau=tau,
-                           first_bounce_from_geom=first_bounce_from_geom)
+                           first_bounce_from_geom=first_bounce_from_geom, edge_mode=edge_mode)
 
 
 def build_geometry(pos, nrm, rad, gviews: Sequence[PeView], params: PeParams, stream=None):

@@ -146,7 +146,8 @@ def _geom_case(sc):
     fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
                            inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
     S = oracle.aggregate(ogf, fp, "fp32")
-    return dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, S=S, ogv=ogv)
+    return dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, S=S, ogv=ogv,
+                ogf=ogf, fp=fp)
 
 
 @pytest.fixture(scope="module")
@@ -178,6 +179,30 @@ def test_aggregate_splats_bitexact(case, request):
     assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
     assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
     assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
+
+
+@pytest.mark.parametrize("case", GEOMS)
+def test_aggregate_canny_edges_bitexact(case, request):
+    # edge mode 1 (Canny on each view's depth map): the same splats as the
+    # oracle's statement, bit for bit, and a different set from mode 0
+    api, pipe = _mods()
+    d = request.getfixturevalue(case)
+    prm = pipe.default_params(d["sc"].pos, d["gv"], edge_mode=1)
+    geom, _ = pipe.build_geometry(d["pos"], d["nrm"], d["rad"], d["gv"], prm)
+    api.stream_check()
+    fp = oracle.FuseParams(tau=d["fp"].tau, bmin=d["fp"].bmin, inv_vox=d["fp"].inv_vox,
+                           G=d["fp"].G, edge_mode=1)
+    S = oracle.aggregate(d["ogf"], fp, "fp32")
+    cr, nf = geom.planes()
+    cr = cr.cpu().numpy()
+    nf = nf.cpu().numpy()
+    ids = np.flatnonzero(cr[:, 3] > 0)
+    assert S.ns > 500
+    assert np.array_equal(ids, S.id)
+    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
+    assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
+    assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
+    assert not np.array_equal(S.id, d["S"].id)
 
 
 @pytest.mark.parametrize("case", GEOMS)
