@@ -288,7 +288,7 @@ pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
  * ------------------------------------------------------------------------- */
 
 /* Workspace bytes for pe_trace_bounces over n_views ray screens of this size
- * (two ray queues of uint32 slots + counters). */
+ * (currently a constant 256: the bounce state lives in the hit records). */
 size_t pe_trace_workspace(int32_t n_views, const pe_view *views);
 
 /* Trace every pixel ray of n_views ray screens (e.g. one per monostatic

@@ -113,16 +113,9 @@ pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float
                           const float *rad, int64_t n, int mode, float delta,
                           unsigned long long *keys, cudaStream_t s);
 
-struct pe_trace_ws {
-  uint32_t *q0, *q1;        // ray slot queues
-  uint32_t *counts;         // [4]: queue sizes
-};
-size_t pe_trace_ws_bytes(int64_t n_rays);
-pe_trace_ws pe_trace_ws_carve(pe_carve &c, int64_t n_rays);
-
 pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,
                           const float *nrm, const pe_geom *geom, int32_t mb,
-                          const pe_params &prm, const pe_trace_ws &tw, const pe_hits &h,
+                          const pe_params &prm, const pe_hits &h,
                           int64_t *stats, cudaStream_t s);
 
 // Psi toward receiver direction dirs[g] (host [n_groups][3]) for every slot

@@ -4,13 +4,16 @@
 // staged in shared memory: the projected tube vectors of Eq. 12-13, the
 // parallelogram area |u' x v'|, the sinc arguments per unit wavenumber, the
 // two polarisations' vector factors [(n x h) x ks] x ks, and the phase path
-// d - ks . p (FP64, split into a float hi/lo pair).  Threads then run one
-// frequency each over the staged rays: sinc x sinc, the phase k (d - ks.p) as a
-// double-float product reduced modulo 2 pi, one sincos, twelve
-// multiply-adds.  Each thread keeps float sums compensated with TwoSum every
-// few terms; the block reduces the threads' (hi + lo) in FP64 in a fixed
-// order and a second kernel sums the blocks in a fixed order, so the field
-// is deterministic.
+// d - ks . p (FP64, split into a float hi/lo pair).  The vector factor is
+// perpendicular to ks (it is minus the part of n x h across ks), so it is
+// kept as its two coordinates in an orthonormal basis (e1, e2) of the plane
+// across ks.  Threads then run one frequency each over the staged rays:
+// sinc x sinc, the phase k (d - ks.p) as a double-float product reduced
+// modulo 2 pi, one sincos, eight multiply-adds.  Each thread keeps float sums
+// compensated with TwoSum every few terms; the block reduces the threads'
+// (hi + lo) in FP64 in a fixed order and a second kernel sums the blocks in a
+// fixed order and turns the two coordinates back into the field's three
+// Cartesian components, so the field is deterministic.
 #include <cstring>
 
 #include "pe_internal.cuh"
@@ -20,7 +23,8 @@ namespace {
 constexpr int kPoThreads = 256;
 constexpr int kPoGroups = 64;    // groups (angles) per launch
 constexpr int kPoFreqs = 256;    // frequencies per launch
-constexpr int kFlush = 8;        // terms between TwoSum flushes
+constexpr int kFlush = 16;       // terms between TwoSum flushes
+constexpr int kAcc = 8;          // sums per (ray, frequency): 2 pol x (e1, e2) x (re, im)
 
 struct po_consts {
   int32_t ng, nf;
@@ -30,6 +34,7 @@ struct po_consts {
   int32_t g0;            // first group of this launch (slot offset g0 * rpg)
   float c1, c2, c3, inv2pi;
   float ks[kPoGroups][3];
+  float e1[kPoGroups][3], e2[kPoGroups][3];  // orthonormal basis across ks
   float k[kPoFreqs], khi[kPoFreqs], klo[kPoFreqs];
 };
 
@@ -60,11 +65,11 @@ __device__ __forceinline__ float dotf(pe_f3 a, pe_f3 b) { return a.x * b.x + a.y
 
 __global__ void __launch_bounds__(kPoThreads, 4)
     po_kernel(const pe_hits h, const __grid_constant__ po_consts C, double *__restrict__ part) {
-  // per staged ray: {au, av, dh, dl}, {V0..V3}, {V4, V5, -, -}: three
+  // per staged ray: {au, av, dh, dl}, {Va.e1, Va.e2, Vc.e1, Vc.e2}: two
   // broadcast 16-byte loads per term
-  __shared__ float4 s_ray[3][kPoThreads];
+  __shared__ float4 s_ray[2][kPoThreads];
   __shared__ int s_warp[kPoThreads / 32];
-  __shared__ double s_red[kPoThreads][12];
+  __shared__ double s_red[kPoThreads][kAcc];
 
   const int g = blockIdx.y;  // group within this launch
   const int chunk = blockIdx.x;
@@ -72,6 +77,8 @@ __global__ void __launch_bounds__(kPoThreads, 4)
   const int FL = C.fl, RL = kPoThreads / FL;
   const int lane_f = tid % FL, lane_r = tid / FL;
   const pe_f3 ks = {C.ks[g][0], C.ks[g][1], C.ks[g][2]};
+  const pe_f3 e1 = {C.e1[g][0], C.e1[g][1], C.e1[g][2]};
+  const pe_f3 e2 = {C.e2[g][0], C.e2[g][1], C.e2[g][2]};
   const int64_t r_begin = (int64_t)chunk * C.chunk;
   int64_t r_end = r_begin + C.chunk;
   if (r_end > C.rpg) r_end = C.rpg;
@@ -82,16 +89,16 @@ __global__ void __launch_bounds__(kPoThreads, 4)
     const bool f_ok = f < C.nf;
     const float kf = f_ok ? C.k[f] : 0.0f, khi = f_ok ? C.khi[f] : 0.0f,
                 klo = f_ok ? C.klo[f] : 0.0f;
-    float hi[12], lo[12], b[12];
+    float hi[kAcc], lo[kAcc], b[kAcc];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) hi[i] = lo[i] = b[i] = 0.0f;
+    for (int i = 0; i < kAcc; ++i) hi[i] = lo[i] = b[i] = 0.0f;
     int pending = 0;
 
     for (int64_t sb = r_begin; sb < r_end; sb += kPoThreads) {
       // ---- stage the frequency-independent per-ray factors ----------------
       int64_t r = sb + tid;
       bool valid = false;
-      float au = 0, av = 0, dh = 0, dl = 0, V[6] = {0, 0, 0, 0, 0, 0};
+      float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
       if (r < r_end) {
         int64_t slot = slot0 + r;
         valid = h.M[slot] >= 1 && h.psi[slot] != 0;
@@ -118,12 +125,10 @@ __global__ void __launch_bounds__(kPoThreads, 4)
             pe_f3 hh = {u.x / lu, u.y / lu, u.z / lu};
             pe_f3 a = cross(cross(cross(n, hv), ks), ks);
             pe_f3 c = cross(cross(cross(n, hh), ks), ks);
-            V[0] = area * a.x;
-            V[1] = area * a.y;
-            V[2] = area * a.z;
-            V[3] = area * c.x;
-            V[4] = area * c.y;
-            V[5] = area * c.z;
+            V[0] = area * dotf(a, e1);
+            V[1] = area * dotf(a, e2);
+            V[2] = area * dotf(c, e1);
+            V[3] = area * dotf(c, e2);
             double ksp = (double)ks.x * (double)p.x + (double)ks.y * (double)p.y +
                          (double)ks.z * (double)p.z;
             double delta = h.path[slot] - ksp;
@@ -147,13 +152,12 @@ __global__ void __launch_bounds__(kPoThreads, 4)
         int at = before + __popc(m & ((1u << lane) - 1u));
         s_ray[0][at] = make_float4(au, av, dh, dl);
         s_ray[1][at] = make_float4(V[0], V[1], V[2], V[3]);
-        s_ray[2][at] = make_float4(V[4], V[5], 0.0f, 0.0f);
       }
       __syncthreads();
       // ---- one frequency per thread over the staged rays -----------------
       if (f_ok) {
         for (int j = lane_r; j < total; j += RL) {
-          const float4 r0 = s_ray[0][j], r1 = s_ray[1][j], r2 = s_ray[2][j];
+          const float4 r0 = s_ray[0][j], r1 = s_ray[1][j];
           float s = sincf_(kf * r0.x) * sincf_(kf * r0.y);
           float dhi = r0.z, dlo = r0.w;
           float ph = khi * dhi;
@@ -166,15 +170,15 @@ __global__ void __launch_bounds__(kPoThreads, 4)
           float sn, cs;
           __sincosf(red, &sn, &cs);
           float re = s * cs, im = -s * sn;
-          const float Vs[6] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y};
+          const float Vs[4] = {r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-          for (int i = 0; i < 6; ++i) {
+          for (int i = 0; i < 4; ++i) {
             b[2 * i] = fmaf(Vs[i], re, b[2 * i]);
             b[2 * i + 1] = fmaf(Vs[i], im, b[2 * i + 1]);
           }
           if (++pending == kFlush) {
 #pragma unroll
-            for (int i = 0; i < 12; ++i) {
+            for (int i = 0; i < kAcc; ++i) {
               two_sum_into(hi[i], lo[i], b[i]);
               b[i] = 0.0f;
             }
@@ -184,39 +188,54 @@ __global__ void __launch_bounds__(kPoThreads, 4)
       }
     }
 #pragma unroll
-    for (int i = 0; i < 12; ++i) two_sum_into(hi[i], lo[i], b[i]);
+    for (int i = 0; i < kAcc; ++i) two_sum_into(hi[i], lo[i], b[i]);
     // ---- fixed-order FP64 reduction over the ray lanes -------------------
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < 12; ++i) s_red[tid][i] = (double)hi[i] + (double)lo[i];
+    for (int i = 0; i < kAcc; ++i) s_red[tid][i] = (double)hi[i] + (double)lo[i];
     __syncthreads();
     if (tid < FL && f0 + tid < C.nf) {
-      double acc[12];
+      double acc[kAcc];
 #pragma unroll
-      for (int i = 0; i < 12; ++i) acc[i] = 0.0;
+      for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
       for (int rl = 0; rl < RL; ++rl)
 #pragma unroll
-        for (int i = 0; i < 12; ++i) acc[i] += s_red[rl * FL + tid][i];
-      int64_t o = (((int64_t)g * C.n_chunks + chunk) * C.nf + (f0 + tid)) * 12;
+        for (int i = 0; i < kAcc; ++i) acc[i] += s_red[rl * FL + tid][i];
+      int64_t o = (((int64_t)g * C.n_chunks + chunk) * C.nf + (f0 + tid)) * kAcc;
 #pragma unroll
-      for (int i = 0; i < 12; ++i) part[o + i] = acc[i];
+      for (int i = 0; i < kAcc; ++i) part[o + i] = acc[i];
     }
     __syncthreads();
   }
 }
 
-// E[g0+g][f][12] = sum over chunks (fixed order).
-__global__ void po_reduce_kernel(const double *__restrict__ part, int ng, int nf, int n_chunks,
-                                 int g0, int nf_total, int f_base, double *__restrict__ E) {
-  int64_t n = (int64_t)ng * nf * 12;
+// E[g0+g][f][12] = the chunks' sums (fixed order) taken back from the basis
+// (e1, e2) across ks to Cartesian components: for polarisation p, component
+// x and re/im r, E = e1[x] S[p][e1][r] + e2[x] S[p][e2][r].
+__global__ void po_reduce_kernel(const double *__restrict__ part, const __grid_constant__ po_consts C,
+                                 int nf_total, int f_base, double *__restrict__ E) {
+  const int64_t n = (int64_t)C.ng * C.nf;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int i = (int)(t % 12);
-    int f = (int)((t / 12) % nf);
-    int g = (int)(t / (12 * (int64_t)nf));
-    double s = 0.0;
-    for (int c = 0; c < n_chunks; ++c) s += part[(((int64_t)g * n_chunks + c) * nf + f) * 12 + i];
-    E[(((int64_t)(g0 + g) * nf_total) + f_base + f) * 12 + i] = s;
+    const int f = (int)(t % C.nf);
+    const int g = (int)(t / C.nf);
+    double S[kAcc];
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) S[i] = 0.0;
+    for (int c = 0; c < C.n_chunks; ++c) {
+      const double *q = part + (((int64_t)g * C.n_chunks + c) * C.nf + f) * kAcc;
+#pragma unroll
+      for (int i = 0; i < kAcc; ++i) S[i] += q[i];
+    }
+    double *e = E + (((int64_t)(C.g0 + g) * nf_total) + f_base + f) * 12;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+          e[(p * 3 + x) * 2 + r] = __dadd_rn(__dmul_rn((double)C.e1[g][x], S[(p * 2) * 2 + r]),
+                                             __dmul_rn((double)C.e2[g][x], S[(p * 2 + 1) * 2 + r]));
   }
 }
 
@@ -229,6 +248,31 @@ int sms() {
     if (n <= 0) n = 1;
   }
   return n;
+}
+
+// An orthonormal basis (e1, e2) of the plane across the unit vector ks, in
+// FP64, rounded to float (both the kernel's projection and the reduction's
+// reconstruction use these float values).  e1 is the coordinate axis least
+// aligned with ks with its ks part removed; e2 = ks x e1.
+void transverse_basis(const float ksf[3], float e1f[3], float e2f[3]) {
+  double k[3] = {ksf[0], ksf[1], ksf[2]};
+  const double kn = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+  for (int i = 0; i < 3; ++i) k[i] = kn > 0 ? k[i] / kn : (i == 2 ? 1.0 : 0.0);
+  int m = 0;
+  for (int i = 1; i < 3; ++i)
+    if (fabs(k[i]) < fabs(k[m])) m = i;
+  double a[3] = {0.0, 0.0, 0.0};
+  a[m] = 1.0;
+  const double ak = a[0] * k[0] + a[1] * k[1] + a[2] * k[2];
+  double e1[3] = {a[0] - ak * k[0], a[1] - ak * k[1], a[2] - ak * k[2]};
+  const double n1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (int i = 0; i < 3; ++i) e1[i] /= n1;
+  const double e2[3] = {k[1] * e1[2] - k[2] * e1[1], k[2] * e1[0] - k[0] * e1[2],
+                        k[0] * e1[1] - k[1] * e1[0]};
+  for (int i = 0; i < 3; ++i) {
+    e1f[i] = (float)e1[i];
+    e2f[i] = (float)e2[i];
+  }
 }
 
 void po_shape(int32_t ng, int64_t rpg, int32_t nf, int *fl, int *n_chunks, int64_t *chunk) {
@@ -259,7 +303,7 @@ size_t pe_po_ws_bytes(int32_t n_groups, int64_t rpg, int32_t n_freq) {
     int fl, nc;
     int64_t ch;
     po_shape(ng, rpg, nf, &fl, &nc, &ch);
-    size_t b = (size_t)ng * nc * nf * 12;
+    size_t b = (size_t)ng * nc * nf * kAcc;
     if (b > most) most = b;
   }
   pe_carve c{nullptr, 0};
@@ -291,8 +335,10 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
       C.c2 = (float)(two_pi - (double)C.c1);
       C.c3 = (float)(two_pi - (double)C.c1 - (double)C.c2);
       C.inv2pi = (float)(1.0 / two_pi);
-      for (int g = 0; g < ng; ++g)
+      for (int g = 0; g < ng; ++g) {
         for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];
+        transverse_basis(C.ks[g], C.e1[g], C.e2[g]);
+      }
       for (int f = 0; f < nf; ++f) {
         double kd = two_pi * freqs[fb + f] / c0;
         C.k[f] = (float)kd;
@@ -304,9 +350,9 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
       po_kernel<<<grid, kPoThreads, 0, s>>>(h, C, part);
       pe_event_after("po_kernel", s);
       PE_TRY_LAUNCH("po_kernel");
-      int64_t n = (int64_t)ng * nf * 12;
-      int blocks = (int)((n + 255) / 256);
-      po_reduce_kernel<<<blocks, 256, 0, s>>>(part, ng, nf, C.n_chunks, g0, n_freq, fb, E);
+      int64_t n = (int64_t)ng * nf;
+      int blocks = (int)((n + 127) / 128);
+      po_reduce_kernel<<<blocks, 128, 0, s>>>(part, C, n_freq, fb, E);
       PE_TRY_LAUNCH("po_reduce_kernel");
     }
   }

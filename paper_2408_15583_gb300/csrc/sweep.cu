@@ -35,7 +35,6 @@ __global__ void sigma_kernel(const __grid_constant__ pe_view_batch vb, const dou
 struct sweep_ws {
   unsigned long long *keys;
   pe_hits h;
-  pe_trace_ws tw;
   double *kw;
   void *po;
   size_t po_bytes;
@@ -68,7 +67,6 @@ sweep_ws carve_sweep(pe_carve &c, const pe_sweep *sw, int B) {
   w.h.ids = nullptr;
   w.h.n_rays = n;
   w.h.max_bounces = sw->max_bounces;
-  w.tw = pe_trace_ws_carve(c, n);
   w.kw = c.take<double>((size_t)sw->n_freq);
   w.po_bytes = pe_po_ws_bytes(B, (int64_t)sw->W * sw->H, sw->n_freq);
   w.po = c.take<char>(w.po_bytes);
@@ -140,7 +138,7 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
       pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.keys, s);
       if (st != PE_OK) return st;
     }
-    pe_status st = pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, w.tw, h, stats, s);
+    pe_status st = pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, h, stats, s);
     if (st != PE_OK) return st;
     // PO: E rows [a0, a0 + nb)
     st = pe_launch_po(h, nb, per, ks, sw->freqs_hz, sw->n_freq, w.po, w.po_bytes,

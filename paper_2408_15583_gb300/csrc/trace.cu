@@ -29,10 +29,6 @@ struct march_args {
   pe_hits h;
   const unsigned long long *keys;
   const float *nrm;
-  const uint32_t *q_in;
-  const uint32_t *n_in;
-  uint32_t *q_out;
-  uint32_t *n_out;
   int32_t bounce;
   int32_t mb;
   float eps;
@@ -481,17 +477,6 @@ __device__ __forceinline__ pe_f3 ld3(const float *a, int64_t i) {
   return {a[3 * i], a[3 * i + 1], a[3 * i + 2]};
 }
 
-// Warp-cooperative append of `slot` to a queue when `keep`.
-__device__ __forceinline__ void warp_append(bool keep, uint32_t slot, uint32_t *q, uint32_t *n) {
-  unsigned mask = __ballot_sync(0xffffffffu, keep);
-  if (!mask) return;
-  int lane = threadIdx.x & 31;
-  uint32_t base = 0;
-  if (lane == 0) base = atomicAdd(n, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (keep) q[base + __popc(mask & ((1u << lane) - 1u))] = slot;
-}
-
 __device__ __forceinline__ void flush_stats(long long *stats, long long a, long long b,
                                             long long c, long long d, long long e) {
   if (!stats) return;
@@ -578,22 +563,31 @@ __global__ void __launch_bounds__(kTraceThreads)
       st3(A.h.v, slot, v);
       A.h.path[slot] = hit ? path_start(d, x) : 0.0;
     }
-    bool live = active && hit && A.mb >= 2;
-    if (A.q_out) warp_append(live, (uint32_t)slot, A.q_out, A.n_out);
   }
   flush_stats(A.stats, nq, 0, ns, nn, nv);
 }
 
-// One bounce (b >= 2) for the rays of q_in (queue order keeps warps coherent).
+// One bounce (b >= 2).  Threads map to slots by the same 8x4 tiles as bounce
+// 1, and a lane is live when its ray hit at bounce b - 1 (M = b - 1).  A warp
+// is thus always one tile of one screen: its rays are neighbours whose
+// reflections stay close, so the warp's union walk is nearly each lane's own.
+// (A compacted queue of live rays would mix tiles from anywhere on the
+// screen into one warp; the per-lane results are the same either way.)
+// Warps with no live lane only read M.
 __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_constant__ march_args A) {
-  const uint32_t n_in = *A.n_in;
+  const int W = A.vb.W, H = A.vb.H;
+  const int64_t per_view = (int64_t)W * H;
+  const tile_map tm = make_tile_map(W, H, A.vb.n);
   const int64_t n_rays = A.h.n_rays;
   long long nq = 0, ns = 0, nn = 0, nv = 0;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_in;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
-    int64_t qi = base + threadIdx.x;
-    bool active = qi < n_in;
-    uint32_t slot = active ? A.q_in[qi] : 0u;
+    int64_t t = base + threadIdx.x;
+    int vi = 0, i = 0, j = 0;
+    bool active = t < tm.n_threads && tile_pixel(tm, W, H, t, vi, i, j);
+    const uint32_t slot = active ? (uint32_t)((int64_t)vi * per_view + (int64_t)j * W + i) : 0u;
+    active = active && A.h.M[slot] == A.bounce - 1;
+    if (!__any_sync(0xffffffffu, active)) continue;
     pe_f3 p = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 1.f}, d = {0.f, 0.f, 1.f};
     pe_f3 u = {0.f, 0.f, 0.f}, v = {0.f, 0.f, 0.f};
     if (active) {
@@ -612,7 +606,6 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
     uint32_t id;
     nq += active;
     bool hit = nearest(A.L, p, d, A.eps, A.r_ov, active, A.err, x, n2, id, ns, nn, nv);
-    bool live = false;
     if (hit) {
       A.h.path[slot] = __dadd_rn(A.h.path[slot], seg_len(p, x));
       st3(A.h.p, slot, x);
@@ -622,9 +615,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
       st3(A.h.v, slot, v);
       A.h.M[slot] = A.bounce;
       if (A.h.ids) A.h.ids[(int64_t)(A.bounce - 1) * n_rays + slot] = id;
-      live = A.bounce < A.mb;
     }
-    if (A.q_out) warp_append(live, slot, A.q_out, A.n_out);
   }
   flush_stats(A.stats, nq, 0, ns, nn, nv);
 }
@@ -741,24 +732,10 @@ bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
 
 }  // namespace
 
-size_t pe_trace_ws_bytes(int64_t n_rays) {
-  pe_carve c{nullptr, 0};
-  pe_trace_ws_carve(c, n_rays);
-  return c.bytes();
-}
-
-pe_trace_ws pe_trace_ws_carve(pe_carve &c, int64_t n_rays) {
-  pe_trace_ws w;
-  w.q0 = c.take<uint32_t>((size_t)n_rays);
-  w.q1 = c.take<uint32_t>((size_t)n_rays);
-  w.counts = c.take<uint32_t>(PE_MAX_BATCH);
-  return w;
-}
-
 pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,
                           const float *nrm, const pe_geom *geom, int32_t mb,
-                          const pe_params &prm, const pe_trace_ws &tw, const pe_hits &h,
-                          int64_t *stats, cudaStream_t s) {
+                          const pe_params &prm, const pe_hits &h, int64_t *stats,
+                          cudaStream_t s) {
   march_args A;
   memset(&A, 0, sizeof(A));
   bool have_geom = geom != nullptr;
@@ -777,11 +754,6 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   A.stats = reinterpret_cast<long long *>(stats);
   const int64_t n_rays = (int64_t)vb.W * vb.H * vb.n;
   if (h.ids) PE_TRY_CUDA(cudaMemsetAsync(h.ids, 0xff, sizeof(uint32_t) * n_rays * mb, s));
-  PE_TRY_CUDA(cudaMemsetAsync(tw.counts, 0, sizeof(uint32_t) * PE_MAX_BATCH, s));
-  uint32_t *qa = tw.q0, *qb = tw.q1;
-  uint32_t *na = tw.counts, *nb = tw.counts + 1;
-  A.q_out = mb >= 2 ? qa : nullptr;
-  A.n_out = na;
   A.bounce = 1;
   const int64_t n_thr = make_tile_map(vb.W, vb.H, vb.n).n_threads;
   // per-lane ray intervals of every view (walk's shared memory)
@@ -792,21 +764,10 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   PE_TRY_LAUNCH("primary_kernel");
   for (int b = 2; b <= mb; ++b) {
     A.bounce = b;
-    A.q_in = qa;
-    A.n_in = na;
-    A.q_out = b < mb ? qb : nullptr;
-    A.n_out = nb;
-    PE_TRY_CUDA(cudaMemsetAsync(nb, 0, sizeof(uint32_t), s));
     pe_event_before("march_kernel", s);
-    march_kernel<<<grid_for(n_rays), kTraceThreads, tv_bytes, s>>>(A);
+    march_kernel<<<grid_for(n_thr), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("march_kernel", s);
     PE_TRY_LAUNCH("march_kernel");
-    uint32_t *t = qa;
-    qa = qb;
-    qb = t;
-    t = na;
-    na = nb;
-    nb = t;
   }
   if (mb >= 2) {
     pe_event_before("shadow_kernel", s);
@@ -844,8 +805,7 @@ pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n
 
 extern "C" size_t pe_trace_workspace(int32_t n_views, const pe_view *views) {
   if (n_views < 1 || !views) return 0;
-  int64_t n = (int64_t)views[0].W * views[0].H * n_views;
-  return pe_trace_ws_bytes(n) + 256;
+  return 256;  // nothing beyond the record buffers is needed at present
 }
 
 extern "C" pe_status pe_trace_bounces(const pe_view *views, int32_t n_views,
@@ -877,10 +837,8 @@ extern "C" pe_status pe_trace_bounces(const pe_view *views, int32_t n_views,
   vb.W = views[0].W;
   vb.H = views[0].H;
   for (int i = 0; i < n_views; ++i) vb.v[i] = views[i];
-  pe_carve c{static_cast<char *>(ws), 0};
-  pe_trace_ws tw = pe_trace_ws_carve(c, n_rays);
   pe_hits h = *hits;
   h.max_bounces = max_bounces;
   return pe_launch_trace(vb, reinterpret_cast<const unsigned long long *>(keys), nrm, geom,
-                         max_bounces, *prm, tw, h, stats, s);
+                         max_bounces, *prm, h, stats, s);
 }

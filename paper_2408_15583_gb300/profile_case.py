@@ -14,6 +14,7 @@ count instead (for timing; the composite batch holds ~3 GB of ray records).
 """
 from __future__ import annotations
 
+import ctypes
 import os
 import sys
 import time
@@ -72,6 +73,22 @@ def main(argv):
     st = stats.cpu().numpy()
     print(f"{case}: {dt * 1e3:.2f} ms per call; batch queries {st[0]} shadow {st[1]} "
           f"exact splat tests {st[2]} node tests {st[3]} views walked {st[4]}")
+    if case == "march":
+        # per-launch times of the trace's kernels (CUDA events on the stream)
+        from paper_2408_15583_gb300 import _lib
+        lib = _lib.load()
+        for kname in ("primary_kernel", "march_kernel", "shadow_kernel"):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * 16)]
+            for e in ev:       # torch creates the CUDA event on its first record
+                e.record()
+            torch.cuda.synchronize()
+            ptrs = (ctypes.c_void_p * len(ev))(*[e.cuda_event for e in ev])
+            lib.pe_set_kernel_events(kname.encode(), ptrs, 16)
+            api.trace_bounces(views, keys, nrm, geom, mb, prm, hits=h, ids=False)
+            n = lib.pe_set_kernel_events(None, None, 0)
+            torch.cuda.synchronize()
+            ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n)]
+            print(f"  {kname}: " + " ".join(f"{m:.3f}" for m in ms) + " ms")
 
 
 def unet_case(reps, batch, W=256):
