@@ -192,6 +192,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
                      bool active, qstate &S, bool &hit_any, unsigned int *err,
                      long long &n_splat, long long &n_node, long long &n_view) {
   static_assert(PE_FAN == 2, "the register-resident traversal assumes a 2x2 fan-out");
+  static_assert(2 * PE_LEAF * PE_LEAF == 32, "a leaf is fetched by one warp: 16 centres + 16 normals");
   const unsigned FULL = 0xffffffffu;
   extern __shared__ float2 tv_all[];
   float2 *tv = tv_all + threadIdx.x;
@@ -346,7 +347,10 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
         leaf_y = cy;
       }
       // leaf tile: test its splats (the occupied slots of the leaf's mask).
-      // A conservative pre-test in plain float
+      // The warp fetches the whole leaf at once: lane b loads slot b's
+      // centre/radius and lane 16 + b its normal (one memory round trip per
+      // leaf, not one per slot); each slot is then broadcast by shuffles,
+      // which move bits unchanged.  A conservative pre-test in plain float
       // arithmetic (distance of the centre to the ray line <= R, and the hit
       // parameter window [tc - R, tc + R] reaching (tmin, t_best + r]) skips
       // the exact test for splats no lane can hit; its slack covers the
@@ -354,12 +358,26 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       const int tx = leaf_x, ty = leaf_y;
       bool lv = active && !(ANY && hit_any);
       const int64_t leaf = L.node_off[v][0] + (int64_t)ty * L.tw[v][0] + tx;
-      for (uint32_t occ = __float_as_uint(__ldg(&L.nodes[2 * leaf].w)); occ; occ &= occ - 1) {
+      const uint32_t occ0 = __float_as_uint(__ldg(&L.nodes[2 * leaf].w));
+      float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
+      {
+        const int lane = threadIdx.x & 31, b = lane & (PE_LEAF * PE_LEAF - 1);
+        if ((occ0 >> b) & 1u) {
+          const int i = tx * PE_LEAF + b % PE_LEAF, j = ty * PE_LEAF + b / PE_LEAF;
+          const int64_t g = poff + (int64_t)j * V.W + i;
+          mine = __ldg((lane < PE_LEAF * PE_LEAF ? L.cr : L.nf) + g);
+        }
+      }
+      for (uint32_t occ = occ0; occ; occ &= occ - 1) {
         const int b = __ffs(occ) - 1;
         const int i = tx * PE_LEAF + b % PE_LEAF, j = ty * PE_LEAF + b / PE_LEAF;
         {
           int64_t g = poff + (int64_t)j * V.W + i;
-          float4 c = __ldg(L.cr + g);
+          float4 c;
+          c.x = __shfl_sync(FULL, mine.x, b);
+          c.y = __shfl_sync(FULL, mine.y, b);
+          c.z = __shfl_sync(FULL, mine.z, b);
+          c.w = __shfl_sync(FULL, mine.w, b);
           float qx = c.x - o.x, qy = c.y - o.y, qz = c.z - o.z;
           float tc = qx * d.x + qy * d.y + qz * d.z;
           float qq = qx * qx + qy * qy + qz * qz;
@@ -373,7 +391,11 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
             pass = pass && tc - Rs - sl <= fmaf(fabsf(lim), 1e-6f, lim);
           }
           if (!__any_sync(FULL, pass)) continue;
-          float4 n = __ldg(L.nf + g);
+          float4 n;
+          n.x = __shfl_sync(FULL, mine.x, PE_LEAF * PE_LEAF + b);
+          n.y = __shfl_sync(FULL, mine.y, PE_LEAF * PE_LEAF + b);
+          n.z = __shfl_sync(FULL, mine.z, PE_LEAF * PE_LEAF + b);
+          n.w = __shfl_sync(FULL, mine.w, PE_LEAF * PE_LEAF + b);
           if (!pass) continue;
           ++n_splat;
           float t;
