@@ -432,7 +432,9 @@ __global__ void fuse_segment_kernel(const __grid_constant__ pe_geom_layout L,
 
 // Leaf boxes: bounds of the owned splats' spheres in the view's (u, v, d)
 // frame, padded for rounding.  Empty tiles get lo = +inf, hi = -inf.
-// Leaf boxes; a leaf's lo.w holds the bit pattern of its occupancy mask
+// Leaf boxes: per axis of the view frame, the union of the splats' disk
+// extents (a disk, not its bounding sphere: thin along the axes its normal
+// faces), padded; a leaf's lo.w holds the bit pattern of its occupancy mask
 // (bit jj * PE_LEAF + ii set when slot (ii, jj) holds a splat) and hi.w its
 // reach: the largest pixel distance from a slot to its splat's projected
 // centre plus the splat's (padded) radius in pixels, so that a ray hitting a
@@ -443,6 +445,7 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
   const pe_view &V = L.view[v];
   int tw = L.tw[v][0], th = L.th[v][0];
   const float4 *cr = L.cr + L.pix_off[v];
+  const float4 *nf = L.nf + L.pix_off[v];
   float pad = L.pad[v];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tw * th; t += gridDim.x * blockDim.x) {
     int tx = t % tw, ty = t / tw;
@@ -468,10 +471,18 @@ __global__ void pyramid_leaf_kernel(const __grid_constant__ pe_geom_layout L, in
         // projected centre plus its radius in pixels
         const float ci = a[0] * inv_pitch + 0.5f * V.W - 0.5f, cj = a[1] * inv_pitch + 0.5f * V.H - 0.5f;
         reach = fmaxf(reach, fmaxf(fabsf(ci - (float)i), fabsf(cj - (float)j)) + r * inv_pitch);
+        // the disk's extent along axis e is R sqrt(1 - (n.e)^2) (its points
+        // are c + y with y across n, |y| <= R); the 1e-6 under the root
+        // (1e-3 R at a face-on axis) covers the rounding of n
+        const float4 n = nf[(int64_t)j * V.W + i];
+        const float ne[3] = {n.x * V.u[0] + n.y * V.u[1] + n.z * V.u[2],
+                             n.x * V.v[0] + n.y * V.v[1] + n.z * V.v[2],
+                             n.x * V.d[0] + n.y * V.d[1] + n.z * V.d[2]};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          lo[k] = fminf(lo[k], a[k] - r);
-          hi[k] = fmaxf(hi[k], a[k] + r);
+          const float ek = c.w * 1.000001f * sqrtf(fmaxf(1.0f - ne[k] * ne[k], 0.0f) + 1e-6f) + pad;
+          lo[k] = fminf(lo[k], a[k] - ek);
+          hi[k] = fmaxf(hi[k], a[k] + ek);
         }
       }
     }

@@ -276,6 +276,10 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       }
     }
     // the start node's box
+    // occ4: the occupancy masks (lo.w, 16 bits each) of the four children
+    // of the last expanded level-1 node, i.e. of the leaves pending at level
+    // 0, so a leaf visit needs no reload of its node
+    uint64_t occ4 = 0;
     {
       const int64_t nid = L.node_off[v][ls] + (int64_t)sy * L.tw[v][ls] + sx;
       const float4 lo = ls == top ? rlo : __ldg(L.nodes + 2 * nid);
@@ -283,6 +287,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       bool lv = active && !(ANY && hit_any);
       n_node += lv;
       if (!__any_sync(FULL, lv && box_hit(lo, hi, r, t0, t_far()))) continue;
+      occ4 = __float_as_uint(lo.w) & 0xffffu;  // the start node when it is a leaf
     }
     // Traversal state, all in registers: `expand` asks to expand node
     // (px, py) of level l (its four children at level l-1 are box-tested
@@ -293,7 +298,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
     uint64_t masks = 0;
     int l = ls, px = sx, py = sy;
     bool expand = ls > 0;
-    int leaf_x = 0, leaf_y = 0;
+    int leaf_x = 0, leaf_y = 0, leaf_c = 0;
     bool root_leaf = ls == 0;
     for (;;) {
       if (root_leaf) {
@@ -325,6 +330,12 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
             bool h = ex[c] && lv && box_hit(blo[c], bhi[c], r, t0, t1);
             if (__any_sync(FULL, h)) m |= 1u << c;
           }
+          if (cl == 0) {
+            occ4 = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              occ4 |= (uint64_t)(__float_as_uint(blo[c].w) & 0xffffu) << (16 * c);
+          }
           masks |= (uint64_t)m << (4 * cl);
           l = cl;
         }
@@ -345,6 +356,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
         }
         leaf_x = cx;
         leaf_y = cy;
+        leaf_c = c;
       }
       // leaf tile: test its splats (the occupied slots of the leaf's mask).
       // The warp fetches the whole leaf at once: lane b loads slot b's
@@ -357,8 +369,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       // rounding of both tests, so it never drops a hit the exact test takes.
       const int tx = leaf_x, ty = leaf_y;
       bool lv = active && !(ANY && hit_any);
-      const int64_t leaf = L.node_off[v][0] + (int64_t)ty * L.tw[v][0] + tx;
-      const uint32_t occ0 = __float_as_uint(__ldg(&L.nodes[2 * leaf].w));
+      const uint32_t occ0 = (uint32_t)(occ4 >> (16 * leaf_c)) & 0xffffu;
       float4 mine = make_float4(0.f, 0.f, 0.f, 0.f);
       {
         const int lane = threadIdx.x & 31, b = lane & (PE_LEAF * PE_LEAF - 1);
