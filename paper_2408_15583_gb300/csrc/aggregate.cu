@@ -521,8 +521,9 @@ __global__ void pyramid_up_kernel(const __grid_constant__ pe_geom_layout L, int 
 }
 
 // Coarse view-occupancy grid: every splat marks, with its owner view's bit,
-// the cells its sphere (padded for rounding) overlaps; splats reaching outside
-// the grid mark the extra word vmask[n^3].
+// the cells its disk's bounding box overlaps (per world axis k the disk
+// reaches R sqrt(1 - n_k^2) from its centre), padded by 1 % of a cell and for
+// rounding; splats reaching outside the grid mark the extra word vmask[n^3].
 __global__ void vgrid_kernel(const __grid_constant__ pe_geom_layout L, uint32_t *__restrict__ vmask) {
   const int n = L.vg_n;
   const float cell = L.vg_cell;
@@ -533,11 +534,13 @@ __global__ void vgrid_kernel(const __grid_constant__ pe_geom_layout L, uint32_t 
     if (!(c.w > 0.0f)) continue;
     const int v = view_of(L, g);
     const uint32_t bit = 1u << v;
-    const float pad = c.w * 1.00001f + 1e-2f * cell + L.pad[v];
-    const float cc[3] = {c.x, c.y, c.z};
+    const float4 nn = L.nf[g];
+    const float cc[3] = {c.x, c.y, c.z}, nk[3] = {nn.x, nn.y, nn.z};
     int lo[3], hi[3];
     bool outside = false;
     for (int k = 0; k < 3; ++k) {
+      const float pad = c.w * 1.00001f * sqrtf(fmaxf(1.0f - nk[k] * nk[k], 0.0f) + 1e-6f) +
+                        1e-2f * cell + L.pad[v];
       float a = floorf((cc[k] - pad - L.vg_min[k]) / cell);
       float b = floorf((cc[k] + pad - L.vg_min[k]) / cell);
       if (!(a >= 0.0f) || !(b <= (float)(n - 1))) outside = true;
