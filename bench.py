@@ -306,21 +306,21 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-# Algorithmic bytes of one bounce query of the march: the ray's record is
+# Algorithmic bytes of one bounce query of the march: the ray's state is
 # read (hit point, normal, direction, tube vectors: 15 floats; path length:
-# 8 bytes; its queue slot: 4 bytes; 72 + 4 = 76 bytes) and, on a hit,
-# rewritten together with the bounce count and the next queue slot (76 bytes).
+# 8 bytes; bounce count: 4 bytes; hit splat id: 4 bytes; 76 bytes) and, on a
+# hit, rewritten (76 bytes).
 MARCH_BYTES_PER_QUERY = 152
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 648.0 MB
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 507.3 MB
 # over 6,332,964 queries), valid only for the sources it was taken on (their
 # SHA-256 prefixes); scaled to a full launch by the number of queries.
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 102.3,
-                     "sources": {"paper_2408_15583_gb300/csrc/trace.cu": "fc23d4983b37e979",
-                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "5f323e9a219af691",
-                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "d18e0da1ebb1e0df"}}
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 80.1,
+                     "sources": {"paper_2408_15583_gb300/csrc/trace.cu": "21f480225b89409a",
+                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "76d8a06e2e9d487f",
+                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "2174324c3f294368"}}
 
 
 def _traffic_valid(rec):
