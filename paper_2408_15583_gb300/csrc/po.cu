@@ -25,6 +25,7 @@ constexpr int kPoGroups = 64;    // groups (angles) per launch
 constexpr int kPoFreqs = 256;    // frequencies per launch
 constexpr int kFlush = 16;       // terms between TwoSum flushes
 constexpr int kAcc = 8;          // sums per (ray, frequency): 2 pol x (e1, e2) x (re, im)
+constexpr float kTwoPi = 6.28318530717958647692f;
 
 struct po_consts {
   int32_t ng, nf;
@@ -32,10 +33,11 @@ struct po_consts {
   int32_t n_chunks;
   int64_t rpg, chunk;    // rays per group, rays per block (multiple of 256)
   int32_t g0;            // first group of this launch (slot offset g0 * rpg)
-  float c1, c2, c3, inv2pi;
+  int32_t rl_shift;      // log2 of the ray lanes per block (256 / fl)
   float ks[kPoGroups][3];
   float e1[kPoGroups][3], e2[kPoGroups][3];  // orthonormal basis across ks
-  float k[kPoFreqs], khi[kPoFreqs], klo[kPoFreqs];
+  float k[kPoFreqs];                  // wavenumber (rad/m), for the sinc arguments
+  float khi[kPoFreqs], klo[kPoFreqs];  // k / 2 pi = f / c (revolutions/m) as a float pair
 };
 
 // sin(x)/x: Taylor series through x^8 for |x| < 0.5 (truncation < 3e-11),
@@ -155,28 +157,34 @@ __global__ void __launch_bounds__(kPoThreads, 4)
       }
       __syncthreads();
       // ---- one frequency per thread over the staged rays -----------------
+      // chunks of at most kFlush terms; the compensated flush is checked per
+      // chunk (between flushes a float sum holds fewer than 2 kFlush terms)
       if (f_ok) {
-        for (int j = lane_r; j < total; j += RL) {
-          const float4 r0 = s_ray[0][j], r1 = s_ray[1][j];
-          float s = sincf_(kf * r0.x) * sincf_(kf * r0.y);
-          float dhi = r0.z, dlo = r0.w;
-          float ph = khi * dhi;
-          float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
-          float nq = rintf(ph * C.inv2pi);
-          float red = fmaf(-nq, C.c1, ph);
-          red = fmaf(-nq, C.c2, red);
-          red = fmaf(-nq, C.c3, red);
-          red += er;
-          float sn, cs;
-          __sincosf(red, &sn, &cs);
-          float re = s * cs, im = -s * sn;
-          const float Vs[4] = {r1.x, r1.y, r1.z, r1.w};
+        for (int j0 = lane_r; j0 < total; j0 += kFlush * RL) {
+          const int jn = min(total, j0 + kFlush * RL);
+#pragma unroll 2
+          for (int j = j0; j < jn; j += RL) {
+            const float4 r0 = s_ray[0][j], r1 = s_ray[1][j];
+            const float s = sincf_(kf * r0.x) * sincf_(kf * r0.y);
+            // phase in revolutions: (k / 2 pi) (d - ks.p) as a double-float
+            // product; ph - rint(ph) is exact (|ph| < 2^23), the correction
+            // er carries the low parts
+            const float dhi = r0.z, dlo = r0.w;
+            const float ph = khi * dhi;
+            const float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
+            const float red = (ph - rintf(ph)) + er;
+            float sn, cs;
+            __sincosf(red * kTwoPi, &sn, &cs);
+            const float re = s * cs, im = -s * sn;
+            const float Vs[4] = {r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            b[2 * i] = fmaf(Vs[i], re, b[2 * i]);
-            b[2 * i + 1] = fmaf(Vs[i], im, b[2 * i + 1]);
+            for (int i = 0; i < 4; ++i) {
+              b[2 * i] = fmaf(Vs[i], re, b[2 * i]);
+              b[2 * i + 1] = fmaf(Vs[i], im, b[2 * i + 1]);
+            }
           }
-          if (++pending == kFlush) {
+          pending += ((jn - j0 - 1) >> C.rl_shift) + 1;
+          if (pending >= kFlush) {
 #pragma unroll
             for (int i = 0; i < kAcc; ++i) {
               two_sum_into(hi[i], lo[i], b[i]);
@@ -331,19 +339,17 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
       po_shape(ng, rpg, nf, &C.fl, &C.n_chunks, &C.chunk);
       C.rpg = rpg;
       C.g0 = g0;
-      C.c1 = (float)two_pi;
-      C.c2 = (float)(two_pi - (double)C.c1);
-      C.c3 = (float)(two_pi - (double)C.c1 - (double)C.c2);
-      C.inv2pi = (float)(1.0 / two_pi);
+      C.rl_shift = __builtin_ctz((unsigned)(kPoThreads / C.fl));
       for (int g = 0; g < ng; ++g) {
         for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];
         transverse_basis(C.ks[g], C.e1[g], C.e2[g]);
       }
       for (int f = 0; f < nf; ++f) {
-        double kd = two_pi * freqs[fb + f] / c0;
+        const double kd = two_pi * freqs[fb + f] / c0;
+        const double kr = freqs[fb + f] / c0;  // k / 2 pi
         C.k[f] = (float)kd;
-        C.khi[f] = (float)kd;
-        C.klo[f] = (float)(kd - (double)C.khi[f]);
+        C.khi[f] = (float)kr;
+        C.klo[f] = (float)(kr - (double)C.khi[f]);
       }
       dim3 grid(C.n_chunks, ng);
       pe_event_before("po_kernel", s);
