@@ -131,13 +131,19 @@ def run_gpu(args, rank, world, local_rank):
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2408_15583_gb300 import _lib, api, pipeline
+    from paper_2408_15583_gb300 import _lib, api, pipeline, shard
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     lib = _lib.load()
     wl, desc = make_workload(args.workload)
     sc, sw, vd = wl.scene, wl.sweep, wl.views
+    if world > 1:
+        # weak scaling: this rank's interleave of a sweep `world` times
+        # denser in phi (angles are independent; nothing is exchanged)
+        import dataclasses
+        th, ph = shard.rank_angles(sw.theta_deg, sw.phi_deg, rank, world)
+        sw = dataclasses.replace(sw, theta_deg=th, phi_deg=ph)
     stream = torch.cuda.current_stream()
 
     pos, nrm, rad = pipeline.scene_to_device(sc, dev)
@@ -266,15 +272,9 @@ def run_gpu(args, rank, world, local_rank):
     # the PO field kernel, timed alone on the launching stream
     roof_po = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream)
 
-    t_ms = total_ms
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        t = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms, e2e_ms = float(t[0]), float(t[1])
-    per_gpu_units = bounces_per_step * args.steps
-    value = per_gpu_units * world / (t_ms / 1e3)
+    # the job: units of all ranks over the slowest rank's time
+    job_units, t_ms, value = shard.job_throughput(bounces_per_step * args.steps, total_ms, dev)
+    _, e2e_ms, e2e_value = shard.job_throughput(bounces_per_step * args.steps, e2e_ms, dev)
     samples = A * F * 2 * args.steps * world
     out = {
         "metric": "ray-bounces/s",
@@ -292,9 +292,11 @@ def run_gpu(args, rank, world, local_rank):
         "config": dict(desc, l2="flushed between steps (512 MB write outside the timed events)",
                        ray_bounces_per_step=bounces_per_step,
                        shadow_queries_per_step=int(st[1]), splat_tests_per_step=int(st[2]),
-                       node_tests_per_step=int(st[3]), parallelism=f"replicas{world}"),
+                       node_tests_per_step=int(st[3]),
+                       parallelism=(f"angles sharded over {world} GPUs (rank r: phi + r/{world} step)"
+                                    if world > 1 else "1 GPU")),
         "rcs_samples_per_s": samples / (t_ms / 1e3),
-        "e2e": {"value": per_gpu_units * world / (e2e_ms / 1e3), "unit": "ray-bounces/s",
+        "e2e": {"value": e2e_value, "unit": "ray-bounces/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "rcs_samples_per_s": samples / (e2e_ms / 1e3)},
         "phases": phases,
@@ -600,7 +602,7 @@ def main():
         out["serving"] = run_serving()
     if rank == 0 and world == 1 and not args.no_learned:
         out["learned"] = run_learned()
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl, _ = make_workload(args.workload)
         out["cpu_baseline"] = cpu_baseline(wl)
     if world > 1:
