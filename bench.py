@@ -518,6 +518,7 @@ def run_learned(W=256, batch=64, steps=8, warmup=2):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     flops = 3.0 * lt.forward_flops(widths, blocks, W, W) * batch
+    hbm_bytes = 3.0 * lt.forward_bytes(widths, blocks, W, W) * batch
     peak = 1708.8
     try:
         peak = float(json.load(open(MEASURED))["bf16_tflops_sustained"])
@@ -533,6 +534,16 @@ def run_learned(W=256, batch=64, steps=8, warmup=2):
                                 "peak": peak, "unit": "TFLOP/s",
                                 "frac": flops / (ms / 1e3) / 1e12 / peak,
                                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"},
+            # widths 32-256 make most layers stream activations (1x1 GEMMs
+            # with K <= 256, depthwise, LayerNorm, GELU): the same step
+            # against HBM, with layer-wise algorithmic bytes (each layer
+            # reads its inputs and writes its outputs once; a training step
+            # taken as 3 forward passes, like its FLOPs)
+            "hbm_roofline": {"bound": "hbm", "achieved": hbm_bytes / (ms / 1e3) / 1e9,
+                             "peak": hbm_peak()[0], "unit": "GB/s",
+                             "frac": hbm_bytes / (ms / 1e3) / 1e9 / hbm_peak()[0],
+                             "bytes_per_step": hbm_bytes,
+                             "peak_source": hbm_peak()[1]},
             "last_loss": float(loss.cpu()[0]),
             "ms_per_view_learned_path": t["learned"] * 1e3,
             "ms_per_view_plain_splatting": t["plain_splatting"] * 1e3,

@@ -120,6 +120,32 @@ def forward_flops(widths, blocks, H, W):
     return f
 
 
+def forward_bytes(widths, blocks, H, W, elem=2):
+    """Layer-wise algorithmic bytes of one forward pass on an H x W image:
+    every layer reads its inputs and writes its outputs once (activations of
+    `elem` bytes; weights and im2col columns not counted).  A ConvNeXt block
+    moves 16 C values per pixel: depthwise 7x7 (C in, C out), LayerNorm (C,
+    C), 1x1 expansion (C, 4C), 1x1 projection with the residual (4C + C, C)."""
+    c = widths
+    L = len(widths)
+    px = [H * W / 4 ** l for l in range(L)]
+    v = px[0] * (1 + c[0])                                     # stem
+    blk = lambda p, ch: 16 * p * ch
+    for l in range(L):
+        if l > 0:
+            v += px[l - 1] * c[l - 1] + px[l] * c[l - 1]       # max-pool
+            v += px[l] * (c[l - 1] + c[l])                     # 1x1 down
+        v += blocks[l] * blk(px[l], c[l])
+    for nout in (1, 3, 1):
+        for l in range(L - 2, -1, -1):
+            v += px[l + 1] * (c[l + 1] + 4 * c[l])             # up 3x3
+            v += 2 * px[l] * c[l]                              # sub-pixel shuffle
+            v += 2 * px[l] * c[l]                              # skip copy
+            v += px[l] * 3 * c[l] + blk(px[l], c[l])           # fuse 1x1 + block
+        v += px[0] * (c[0] + nout + 1)                         # head (+ residual)
+    return v * elem
+
+
 def _cat(items, key):
     return torch.cat([it[key] for it in items])
 
