@@ -143,7 +143,7 @@ def test_dihedral_full_sweep_and_traces(dihedral_full):
     per = sw.W * sw.H
     multi = 0
     for k, ref in enumerate(refs):
-        tr = ref.trs[0]
+        tr = ref.traces[0]
         sl = slice(k * per, (k + 1) * per)
         assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), f"angle {angles[k]}"
         ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
