@@ -99,8 +99,11 @@ __global__ void __launch_bounds__(kSplatThreads)
         if (!splat_test(V, i, j, c, nn, R, mode, depth)) continue;
         unsigned long long key =
             ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)p;
-        unsigned long long *slot = kv + (int64_t)j * W + i;
-        if (key < __ldcg(slot)) atomicMin(slot, key);
+        // the result is unused, so the atomic is a fire-and-forget
+        // reduction in L2: the thread does not wait for it (reading the key
+        // first to skip losing updates made every covered pixel wait on an
+        // L2 round trip)
+        atomicMin(kv + (int64_t)j * W + i, key);
       }
     }
   }
