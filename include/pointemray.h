@@ -50,7 +50,7 @@ typedef enum {
   PE_ECUDA = 3,         /* a CUDA runtime call failed (see pe_last_error)   */
   PE_ETIMEOUT = 4,      /* a bounded device wait gave up                    */
   PE_EOVERFLOW = 5,     /* a fixed-capacity device list overflowed          */
-  PE_EUNSUPPORTED = 6   /* valid request outside what this build supports   */
+  PE_EUNSUPPORTED = 6   /* valid request outside what the library supports */
 } pe_status;
 
 /* An orthographic ray screen (the paper's uvwo frame, Sec. III-A around
