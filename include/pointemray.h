@@ -134,7 +134,9 @@ typedef struct {
  *   psi           : uint8 [n]       visibility of the receiver (Psi);
  *   ids           : uint32 [mb][n]  hit id per bounce (point index for a
  *                   GFB bounce, splat id for a splat bounce, 0xFFFFFFFF after
- *                   the last); may be NULL. */
+ *                   the last); may be NULL.
+ * M, psi (and ids) are written for every slot; p, n, k, u, v and path only
+ * for rays that hit (M >= 1) and are undefined where M = 0. */
 typedef struct {
   float *p, *n, *k, *u, *v;
   double *path;

@@ -65,6 +65,66 @@ __device__ __forceinline__ pe_f3 cross(pe_f3 a, pe_f3 b) {
 }
 __device__ __forceinline__ float dotf(pe_f3 a, pe_f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// The frequency-independent factors of ray `slot` (Eq. 12-14): the sinc
+// arguments per unit wavenumber (au, av), the phase path d - ks.p as a float
+// pair (dh, dl) and the area-weighted vector factors of both polarisations in
+// the basis (e1, e2).  False for a ray without a contribution (a miss,
+// Psi = 0, or a tube edge-on to the surface).
+__device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f3 ks, pe_f3 e1,
+                                            pe_f3 e2, float &au, float &av, float &dh,
+                                            float &dl, float V[4]) {
+  if (!(h.M[slot] >= 1 && h.psi[slot] != 0)) return false;
+  pe_f3 kk = {h.k[3 * slot], h.k[3 * slot + 1], h.k[3 * slot + 2]};
+  pe_f3 n = {h.n[3 * slot], h.n[3 * slot + 1], h.n[3 * slot + 2]};
+  pe_f3 u = {h.u[3 * slot], h.u[3 * slot + 1], h.u[3 * slot + 2]};
+  pe_f3 v = {h.v[3 * slot], h.v[3 * slot + 1], h.v[3 * slot + 2]};
+  pe_f3 p = {h.p[3 * slot], h.p[3 * slot + 1], h.p[3 * slot + 2]};
+  float nk = dotf(n, kk);
+  if (nk == 0.0f) return false;
+  float su = dotf(n, u) / nk, sv = dotf(n, v) / nk;
+  pe_f3 up = {u.x - kk.x * su, u.y - kk.y * su, u.z - kk.z * su};
+  pe_f3 vp = {v.x - kk.x * sv, v.y - kk.y * sv, v.z - kk.z * sv};
+  pe_f3 cr = cross(up, vp);
+  float area = sqrtf(dotf(cr, cr));
+  pe_f3 q = {kk.x - ks.x, kk.y - ks.y, kk.z - ks.z};
+  au = 0.5f * dotf(q, up);
+  av = 0.5f * dotf(q, vp);
+  float lu = sqrtf(dotf(u, u)), lv = sqrtf(dotf(v, v));
+  pe_f3 hv = {-v.x / lv, -v.y / lv, -v.z / lv};
+  pe_f3 hh = {u.x / lu, u.y / lu, u.z / lu};
+  pe_f3 a = cross(cross(cross(n, hv), ks), ks);
+  pe_f3 c = cross(cross(cross(n, hh), ks), ks);
+  V[0] = area * dotf(a, e1);
+  V[1] = area * dotf(a, e2);
+  V[2] = area * dotf(c, e1);
+  V[3] = area * dotf(c, e2);
+  double ksp = (double)ks.x * (double)p.x + (double)ks.y * (double)p.y + (double)ks.z * (double)p.z;
+  double delta = h.path[slot] - ksp;
+  dh = (float)delta;
+  dl = (float)(delta - (double)dh);
+  return true;
+}
+
+// One (ray, frequency) term of Eq. 14 added to the float sums b: sinc x sinc,
+// the phase in revolutions (k / 2 pi) (d - ks.p) as a double-float product
+// (ph - rint(ph) is exact for |ph| < 2^23; er carries the low parts), one
+// sincos, eight multiply-adds.
+__device__ __forceinline__ void add_term(float kf, float khi, float klo, float au, float av,
+                                         float dhi, float dlo, const float V[4], float b[kAcc]) {
+  const float s = sincf_(kf * au) * sincf_(kf * av);
+  const float ph = khi * dhi;
+  const float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
+  const float red = (ph - rintf(ph)) + er;
+  float sn, cs;
+  __sincosf(red * kTwoPi, &sn, &cs);
+  const float re = s * cs, im = -s * sn;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    b[2 * i] = fmaf(V[i], re, b[2 * i]);
+    b[2 * i + 1] = fmaf(V[i], im, b[2 * i + 1]);
+  }
+}
+
 __global__ void __launch_bounds__(kPoThreads, 4)
     po_kernel(const pe_hits h, const __grid_constant__ po_consts C, double *__restrict__ part) {
   // per staged ray: {au, av, dh, dl}, {Va.e1, Va.e2, Vc.e1, Vc.e2}: two
@@ -96,101 +156,66 @@ __global__ void __launch_bounds__(kPoThreads, 4)
     for (int i = 0; i < kAcc; ++i) hi[i] = lo[i] = b[i] = 0.0f;
     int pending = 0;
 
-    for (int64_t sb = r_begin; sb < r_end; sb += kPoThreads) {
-      // ---- stage the frequency-independent per-ray factors ----------------
-      int64_t r = sb + tid;
-      bool valid = false;
-      float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
-      if (r < r_end) {
-        int64_t slot = slot0 + r;
-        valid = h.M[slot] >= 1 && h.psi[slot] != 0;
-        if (valid) {
-          pe_f3 kk = {h.k[3 * slot], h.k[3 * slot + 1], h.k[3 * slot + 2]};
-          pe_f3 n = {h.n[3 * slot], h.n[3 * slot + 1], h.n[3 * slot + 2]};
-          pe_f3 u = {h.u[3 * slot], h.u[3 * slot + 1], h.u[3 * slot + 2]};
-          pe_f3 v = {h.v[3 * slot], h.v[3 * slot + 1], h.v[3 * slot + 2]};
-          pe_f3 p = {h.p[3 * slot], h.p[3 * slot + 1], h.p[3 * slot + 2]};
-          float nk = dotf(n, kk);
-          if (nk == 0.0f) {
-            valid = false;
-          } else {
-            float su = dotf(n, u) / nk, sv = dotf(n, v) / nk;
-            pe_f3 up = {u.x - kk.x * su, u.y - kk.y * su, u.z - kk.z * su};
-            pe_f3 vp = {v.x - kk.x * sv, v.y - kk.y * sv, v.z - kk.z * sv};
-            pe_f3 cr = cross(up, vp);
-            float area = sqrtf(dotf(cr, cr));
-            pe_f3 q = {kk.x - ks.x, kk.y - ks.y, kk.z - ks.z};
-            au = 0.5f * dotf(q, up);
-            av = 0.5f * dotf(q, vp);
-            float lu = sqrtf(dotf(u, u)), lv = sqrtf(dotf(v, v));
-            pe_f3 hv = {-v.x / lv, -v.y / lv, -v.z / lv};
-            pe_f3 hh = {u.x / lu, u.y / lu, u.z / lu};
-            pe_f3 a = cross(cross(cross(n, hv), ks), ks);
-            pe_f3 c = cross(cross(cross(n, hh), ks), ks);
-            V[0] = area * dotf(a, e1);
-            V[1] = area * dotf(a, e2);
-            V[2] = area * dotf(c, e1);
-            V[3] = area * dotf(c, e2);
-            double ksp = (double)ks.x * (double)p.x + (double)ks.y * (double)p.y +
-                         (double)ks.z * (double)p.z;
-            double delta = h.path[slot] - ksp;
-            dh = (float)delta;
-            dl = (float)(delta - (double)dh);
+    if (FL == 1) {
+      // one frequency: each thread takes its own rays, nothing to share
+      for (int64_t r = r_begin + tid; r < r_end; r += kPoThreads) {
+        float au, av, dh, dl, V[4];
+        if (!ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V)) continue;
+        add_term(kf, khi, klo, au, av, dh, dl, V, b);
+        if (++pending == kFlush) {
+#pragma unroll
+          for (int i = 0; i < kAcc; ++i) {
+            two_sum_into(hi[i], lo[i], b[i]);
+            b[i] = 0.0f;
           }
+          pending = 0;
         }
       }
-      // stable compaction of the valid rays (order = slot order)
-      unsigned m = __ballot_sync(0xffffffffu, valid);
-      int wid = tid >> 5, lane = tid & 31;
-      __syncthreads();  // previous sub-batch's readers are done
-      if (lane == 0) s_warp[wid] = __popc(m);
-      __syncthreads();
-      int before = 0, total = 0;
-      for (int w = 0; w < kPoThreads / 32; ++w) {
-        if (w < wid) before += s_warp[w];
-        total += s_warp[w];
-      }
-      if (valid) {
-        int at = before + __popc(m & ((1u << lane) - 1u));
-        s_ray[0][at] = make_float4(au, av, dh, dl);
-        s_ray[1][at] = make_float4(V[0], V[1], V[2], V[3]);
-      }
-      __syncthreads();
-      // ---- one frequency per thread over the staged rays -----------------
-      // chunks of at most kFlush terms; the compensated flush is checked per
-      // chunk (between flushes a float sum holds fewer than 2 kFlush terms)
-      if (f_ok) {
-        for (int j0 = lane_r; j0 < total; j0 += kFlush * RL) {
-          const int jn = min(total, j0 + kFlush * RL);
+    } else {
+      for (int64_t sb = r_begin; sb < r_end; sb += kPoThreads) {
+        // ---- stage the frequency-independent per-ray factors --------------
+        const int64_t r = sb + tid;
+        float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
+        const bool valid = r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V);
+        // stable compaction of the valid rays (order = slot order)
+        unsigned m = __ballot_sync(0xffffffffu, valid);
+        int wid = tid >> 5, lane = tid & 31;
+        __syncthreads();  // previous sub-batch's readers are done
+        if (lane == 0) s_warp[wid] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < kPoThreads / 32; ++w) {
+          if (w < wid) before += s_warp[w];
+          total += s_warp[w];
+        }
+        if (valid) {
+          int at = before + __popc(m & ((1u << lane) - 1u));
+          s_ray[0][at] = make_float4(au, av, dh, dl);
+          s_ray[1][at] = make_float4(V[0], V[1], V[2], V[3]);
+        }
+        __syncthreads();
+        // ---- one frequency per thread over the staged rays ---------------
+        // chunks of at most kFlush terms; the compensated flush is checked
+        // per chunk (between flushes a float sum holds fewer than 2 kFlush
+        // terms)
+        if (f_ok) {
+          for (int j0 = lane_r; j0 < total; j0 += kFlush * RL) {
+            const int jn = min(total, j0 + kFlush * RL);
 #pragma unroll 2
-          for (int j = j0; j < jn; j += RL) {
-            const float4 r0 = s_ray[0][j], r1 = s_ray[1][j];
-            const float s = sincf_(kf * r0.x) * sincf_(kf * r0.y);
-            // phase in revolutions: (k / 2 pi) (d - ks.p) as a double-float
-            // product; ph - rint(ph) is exact (|ph| < 2^23), the correction
-            // er carries the low parts
-            const float dhi = r0.z, dlo = r0.w;
-            const float ph = khi * dhi;
-            const float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
-            const float red = (ph - rintf(ph)) + er;
-            float sn, cs;
-            __sincosf(red * kTwoPi, &sn, &cs);
-            const float re = s * cs, im = -s * sn;
-            const float Vs[4] = {r1.x, r1.y, r1.z, r1.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              b[2 * i] = fmaf(Vs[i], re, b[2 * i]);
-              b[2 * i + 1] = fmaf(Vs[i], im, b[2 * i + 1]);
+            for (int j = j0; j < jn; j += RL) {
+              const float4 r0 = s_ray[0][j], r1 = s_ray[1][j];
+              const float Vs[4] = {r1.x, r1.y, r1.z, r1.w};
+              add_term(kf, khi, klo, r0.x, r0.y, r0.z, r0.w, Vs, b);
             }
-          }
-          pending += ((jn - j0 - 1) >> C.rl_shift) + 1;
-          if (pending >= kFlush) {
+            pending += ((jn - j0 - 1) >> C.rl_shift) + 1;
+            if (pending >= kFlush) {
 #pragma unroll
-            for (int i = 0; i < kAcc; ++i) {
-              two_sum_into(hi[i], lo[i], b[i]);
-              b[i] = 0.0f;
+              for (int i = 0; i < kAcc; ++i) {
+                two_sum_into(hi[i], lo[i], b[i]);
+                b[i] = 0.0f;
+              }
+              pending = 0;
             }
-            pending = 0;
           }
         }
       }

@@ -548,7 +548,8 @@ __device__ __forceinline__ bool tile_pixel(const tile_map &m, int W, int H, int6
 }
 
 // Bounce 1 from the incidence screen's GFB keys (or, geom_first, by marching
-// the splats from the screen).  Writes every slot's record.
+// the splats from the screen).  Writes every slot's M and Psi, and the rest
+// of the record for the rays that hit.
 __global__ void __launch_bounds__(kTraceThreads)
     primary_kernel(const __grid_constant__ march_args A, int geom_first) {
   const int W = A.vb.W, H = A.vb.H;
@@ -589,12 +590,15 @@ __global__ void __launch_bounds__(kTraceThreads)
       A.h.M[slot] = hit ? 1 : 0;
       A.h.psi[slot] = 1;
       if (A.h.ids) A.h.ids[slot] = id;
-      st3(A.h.p, slot, x);
-      st3(A.h.n, slot, n);
-      st3(A.h.k, slot, d);
-      st3(A.h.u, slot, u);
-      st3(A.h.v, slot, v);
-      A.h.path[slot] = hit ? path_start(d, x) : 0.0;
+      // a miss (M = 0) ends the ray: nothing reads the rest of its record
+      if (hit) {
+        st3(A.h.p, slot, x);
+        st3(A.h.n, slot, n);
+        st3(A.h.k, slot, d);
+        st3(A.h.u, slot, u);
+        st3(A.h.v, slot, v);
+        A.h.path[slot] = path_start(d, x);
+      }
     }
   }
   flush_stats(A.stats, nq, 0, ns, nn, nv);
