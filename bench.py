@@ -270,7 +270,8 @@ def run_gpu(args, rank, world, local_rank):
     # roofline of the dominant kernel (march_kernel, timed in the steps above)
     roof = roofline_march(march_ms, march_queries / march_launches_per_step)
     # the PO field kernel, timed alone on the launching stream
-    roof_po = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream)
+    roof_po = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream,
+                          clocks.get("sm_mhz") if isinstance(clocks, dict) else None)
 
     # the job: units of all ranks over the slowest rank's time
     job_units, t_ms, value = shard.job_throughput(bounces_per_step * args.steps, total_ms, dev)
@@ -362,7 +363,7 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream):
+def roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream, sm_mhz=None):
     """Time pe_po_field alone (same kernel and launch shape as inside the
     sweep) on one batch of traced angles; ALU roofline."""
     import torch
@@ -387,36 +388,33 @@ def roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream):
     ms = e0.elapsed_time(e1) / reps
     flops_per_term = PO_FLOPS_PER_TERM
     achieved = terms * flops_per_term / (ms / 1e3) / 1e12
-    peak, src = alu_peak()
+    peak, src = alu_peak(sm_mhz)
     return {"kernel": "po_kernel (+po_reduce_kernel)", "bound": "alu", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
             "peak_source": src, "flops_per_term": flops_per_term, "terms_per_launch": terms,
             "ms_per_launch": ms}
 
 
-# Algorithmic FP32 work of one (ray, frequency) term of Eq. 14 as the kernel
-# evaluates it (FMA = 2): two sinc arguments (2), two sinc evaluations
-# (Taylor, 5 FMA each: 20), their product and the amplitude split (3),
-# double-float phase k*delta and its reduction mod 2 pi (2 mul + 5 FMA + 1
-# add: 13), e^{-j phi} (2 special-function ops, counted 1 each: 2), and 12
-# complex-vector multiply-adds (24).
+# Algorithmic FP32 work of one (ray, frequency) term of Eq. 14 (FMA = 2): two
+# sinc arguments (2), two sinc evaluations (Taylor, 5 FMA each: 20), their
+# product and the amplitude split (3), double-float phase k*delta and its
+# reduction mod 2 pi (2 mul + 5 FMA + 1 add: 13), e^{-j phi} (2
+# special-function ops, counted 1 each: 2), and the field's 3 Cartesian
+# components x 2 polarisations, complex: 12 multiply-adds (24).  (The kernel
+# needs 8 of those 12, in a basis across ks.)
 PO_FLOPS_PER_TERM = 64
 
 
-def alu_peak():
-    """FP32 peak = 152 SMs x 128 FP32 lanes x 2 (FMA) x SM clock.  With the
-    measured median SM clock under load when MEASURED_PEAKS.json has it."""
-    mhz = 2070.0
-    src = "152 SM x 128 FP32 lanes x 2 x 2070 MHz (max clock)"
-    try:
-        m = json.load(open(MEASURED))
-        c = m.get("clocks_under_load", {}).get("sm_mhz_median")
-        if c:
-            mhz = float(c)
-            src = f"152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz (measured median SM clock under load)"
-    except (OSError, ValueError):
-        pass
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12, src
+def alu_peak(sm_mhz=None):
+    """FP32 peak = 152 SMs x 128 FP32 lanes x 2 (FMA) x SM clock, at the SM
+    clock sampled during this run's timed region (the kernel runs at that
+    clock; the slower median clock in MEASURED_PEAKS.json is the power-capped
+    GEMM's), else at the maximum clock, 2070 MHz."""
+    if sm_mhz and sm_mhz > 0:
+        mhz, how = float(sm_mhz), "median SM clock sampled during the timed region"
+    else:
+        mhz, how = 2070.0, "maximum SM clock"
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, f"152 SM x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({how})"
 
 
 # ----------------------------------------------------------------------------
