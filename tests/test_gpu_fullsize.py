@@ -223,3 +223,26 @@ def test_sphere_full_sweep_vs_exact_po(sphere_full):
     # the cross-polarised return of a sphere vanishes (up to the surfel
     # sampling): 20 dB below the co-polarised one
     assert np.all(s[:, :, 0, 1] < 1e-2 * s[:, :, 0, 0])
+
+
+# ----------------------------------------------------------------------------
+# composite workload: sampled GFB keys at full size
+# ----------------------------------------------------------------------------
+
+def test_composite_full_gfb_keys_sampled():
+    # 1M noisy points with PCA normals; the 8 fused views at 512^2 and one
+    # 8-angle batch of the sweep's 2048^2 ray screens, sampled pixels against
+    # the oracle's per-pixel search over all points
+    api, pipe = _mods()
+    wl = scenes.workload_composite()
+    sc, sw, vd = wl.scene, wl.sweep, wl.views
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    gv = pipe.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, vd.W, vd.H)
+    kg = api.build_gfb(gv, pos, nrm, rad, 0, outputs=("keys",))["keys"]
+    angles = [0, 9, 18, 27, 36, 45, 54, 71]
+    views = [api.view_from_angles(sw.theta_deg[a], sw.phi_deg[a], sw.centre, sw.extent,
+                                  sw.W, sw.H) for a in angles]
+    ks = api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))["keys"]
+    api.stream_check()
+    assert _sampled_keys_match(sc, gv, kg, 200, 3) > 200
+    assert _sampled_keys_match(sc, views, ks, 200, 4) > 100
