@@ -74,7 +74,8 @@ typedef struct {
  *              by more than edge_tau * pitch;
  *   fuse_grid  voxel grid size G of the fusion step (Sec. III-B: 256);
  *   bbox_min   voxel grid origin (float32), inv_voxel = G / (longest bbox edge)
- *              as float32;
+ *              as float32 (finite and > 0: a point set of zero extent has no
+ *              grid, and pe_aggregate_views returns PE_EINVAL);
  *   first_bounce_from_geom  0: bounce 1 from the incidence view's GFB
  *              (PO path of Sec. III-A); 1: bounce 1 traced against the
  *              aggregated splats as in Alg. 3;
@@ -278,7 +279,8 @@ size_t pe_aggregate_workspace(int32_t n_views, const pe_view *views,
  * Then the bounding
  * pyramids are built.  out->views/n_views/blob_dev must be set by the caller
  * (views identical to `views`).  Requires n_views <= PE_MAX_VIEWS,
- * fuse_grid <= 256. */
+ * fuse_grid <= 256, a finite bbox_min and a finite inv_voxel > 0
+ * (PE_EINVAL otherwise). */
 pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
                              const float *gfb_nd_dev, const uint8_t *gfb_mask_dev,
                              const pe_params *params, void *ws, size_t ws_bytes,

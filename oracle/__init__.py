@@ -228,6 +228,10 @@ def fuse_params(scene, G: int = 256, tau: float = 3.0) -> FuseParams:
     bbox edge / G (Sec. III-B); values rounded to FP32."""
     lo, hi = scene.bbox()
     ext = float((hi - lo).max())
+    if not (ext > 0.0 and np.isfinite(ext)):
+        # the grid over the bounding box (Sec. III-B) is undefined for a box
+        # of zero extent
+        raise ValueError("fusion grid: the points' bounding box has zero extent")
     return FuseParams(tau=float(np.float32(tau)),
                       bmin=lo.astype(np.float32).astype(np.float64),
                       inv_vox=float(np.float32(G / ext)), G=G)

@@ -7,6 +7,7 @@ stream.  Names follow ``include/pointemray.h``.
 from __future__ import annotations
 
 import ctypes as C
+import math
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
 
@@ -74,6 +75,9 @@ def make_params(pos: np.ndarray, eps: float, overlap_r: float, G: int = 256, tau
     p = np.asarray(pos, dtype=np.float64)
     lo, hi = p.min(axis=0), p.max(axis=0)
     ext = float((hi - lo).max())
+    if not (ext > 0.0 and math.isfinite(ext)):
+        raise ValueError("the fusion grid spans the points' bounding box: it needs points "
+                         "of positive, finite extent")
     prm = PeParams()
     prm.delta = float(delta)
     prm.eps = float(eps)

@@ -630,6 +630,10 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
                    PE_MAX_VIEWS);
   int G = prm->fuse_grid;
   if (G < 1 || G > 256) return pe_fail(PE_EINVAL, "pe_aggregate_views: fuse_grid in [1, 256]");
+  if (!(prm->inv_voxel > 0.0f) || !isfinite(prm->inv_voxel) || !isfinite(prm->bbox_min[0]) ||
+      !isfinite(prm->bbox_min[1]) || !isfinite(prm->bbox_min[2]))
+    return pe_fail(PE_EINVAL, "pe_aggregate_views: the fusion grid needs a finite origin and "
+                              "inv_voxel > 0 (a point set of positive extent)");
   if (!pe_aligned(gfb_nd, 16)) return pe_fail(PE_EINVAL, "pe_aggregate_views: gfb_nd alignment");
   if (out->n_views != n_views || !out->blob_dev)
     return pe_fail(PE_EINVAL, "pe_aggregate_views: out must name the same views and a blob");

@@ -435,3 +435,121 @@ def test_rcs_sweep_single_bounce_without_geometry():
     E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), pos, nrm, rad, None, prm)
     ref = oracle.rcs_sweep(sc, sw, None, 0.01, 0.01, mode="fp32")
     assert field_err(_cplx(E), ref.E).max() < 1e-3
+
+
+# ----------------------------------------------------------------------------
+# degenerate and ragged inputs through the whole path
+# ----------------------------------------------------------------------------
+
+def test_trace_ragged_screen_bitexact(small_geom):
+    # a screen whose size is not a multiple of the kernels' 8 x 4 ray tiles:
+    # partial tiles at the right and bottom edges, three bounces
+    api, pipe = _mods()
+    d = small_geom
+    sc = d["sc"]
+    c, r = scenes.bounding_sphere(sc.pos)
+    views = pipe.views_from_angles([90.0, 80.0], [45.0, 30.0], c, r * 1.02, 37, 23)
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], 3, d["prm"])
+    api.stream_check()
+    per = 37 * 23
+    multi = 0
+    for a, v in enumerate(views):
+        ov = _oracle_view(v)
+        tr = oracle.trace(ov, d["S"], 3, float(d["prm"].eps), float(d["prm"].overlap_r),
+                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+        sl = slice(a * per, (a + 1) * per)
+        assert np.array_equal(h.M[sl].cpu().numpy(), tr.M)
+        ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
+        ids[ids == 0xFFFFFFFF] = -1
+        assert np.array_equal(ids.T, tr.ids)
+        assert np.array_equal(h.psi[sl].cpu().numpy(), tr.psi)
+        multi += int((tr.M >= 2).sum())
+    assert multi > 20
+
+
+def test_empty_geometry_and_missing_screen_give_zero_field():
+    # (1) GFB views that see nothing: no splats, every bounce query misses;
+    # (2) a ray screen beside the target: every ray misses; the field and
+    # sigma are exactly zero, as in the oracle
+    api, pipe = _mods()
+    sc = scenes.dihedral(1500, seed=7)
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    c, r = scenes.bounding_sphere(sc.pos)
+    far = np.asarray(c) + np.array([10.0, 0.0, 0.0])
+    gv = pipe.views_from_angles([60.0, 120.0], [45.0, 135.0], far, r, 32, 32)
+    prm = pipe.default_params(sc.pos, gv)
+    geom, g = pipe.build_geometry(pos, nrm, rad, gv, prm)
+    api.stream_check()
+    cr, _ = geom.planes()
+    assert int((cr[:, 3] > 0).sum()) == 0
+    sw = scenes._sweep_over(sc, [90.0, 70.0], [0.0, 30.0], 24, [3e9, 3.1e9], 3)
+    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), pos, nrm, rad, geom, prm)
+    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
+    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
+                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
+    S = oracle.aggregate(ogf, fp, "fp32")
+    assert S.ns == 0
+    ref = oracle.rcs_sweep(sc, sw, S, float(prm.eps), float(prm.overlap_r), mode="fp32")
+    # with no splats only the primary bounce contributes
+    assert field_err(_cplx(E), ref.E).max() < 1e-3
+    sw2 = scenes.Sweep(theta_deg=np.array([90.0]), phi_deg=np.array([0.0]), W=16, H=16,
+                       centre=np.asarray(c) + np.array([0.0, 0.0, 10.0]), extent=0.2,
+                       freqs_hz=np.array([3e9]), max_bounces=2)
+    E2, sig2 = api.rcs_sweep(api.SweepArgs.from_sweep(sw2), pos, nrm, rad, geom, prm)
+    api.stream_check()
+    assert torch.count_nonzero(E2) == 0 and torch.count_nonzero(sig2) == 0
+
+
+def test_two_point_scene_through_the_path():
+    # two surfels: a handful of GFB pixels, a few voxels, a few splats; three
+    # bounces.  (One point alone spans no box, so it has no fusion grid:
+    # both sides reject it.)
+    api, pipe = _mods()
+    sc = scenes.Scene(pos=np.array([[0.01, -0.02, 0.03], [0.06, 0.01, -0.02]], np.float32),
+                      nrm=np.array([[0.0, 0.6, 0.8], [0.8, 0.0, 0.6]], np.float32),
+                      rad=np.array([0.05, 0.04], np.float32))
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    centre = sc.pos.mean(axis=0).astype(np.float64)
+    gv = pipe.views_from_angles([60.0, 60.0, 120.0, 120.0], [45.0, 225.0, 135.0, 315.0],
+                                centre, 0.12, 48, 48)
+    prm = pipe.default_params(sc.pos, gv)
+    geom, g = pipe.build_geometry(pos, nrm, rad, gv, prm)
+    api.stream_check()
+    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
+    S = oracle.aggregate(ogf, oracle.fuse_params(sc, prm.fuse_grid, float(prm.edge_tau)), "fp32")
+    cr, nf = geom.planes()
+    cr = cr.cpu().numpy()
+    ids = np.flatnonzero(cr[:, 3] > 0)
+    assert np.array_equal(ids, S.id) and S.ns >= 2
+    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
+    sw = scenes.Sweep(theta_deg=np.array([0.0, 37.0]), phi_deg=np.array([0.0, 90.0]), W=20, H=20,
+                      centre=centre, extent=0.12, freqs_hz=np.array([5e9]), max_bounces=3)
+    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), pos, nrm, rad, geom, prm)
+    api.stream_check()
+    ref = oracle.rcs_sweep(sc, sw, S, float(prm.eps), float(prm.overlap_r), mode="fp32")
+    assert field_err(_cplx(E), ref.E).max() < 1e-3
+
+
+def test_zero_extent_fusion_grid_is_rejected():
+    api, pipe = _mods()
+    sc = scenes.Scene(pos=np.array([[0.01, -0.02, 0.03]], np.float32),
+                      nrm=np.array([[0.0, 0.6, 0.8]], np.float32),
+                      rad=np.array([0.05], np.float32))
+    with pytest.raises(ValueError):
+        api.make_params(sc.pos, 0.01, 0.01)
+    with pytest.raises(ValueError):
+        oracle.fuse_params(sc)
+    # through the ABI: a grid with inv_voxel = inf or NaN origin is refused
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    gv = pipe.views_from_angles([60.0], [45.0], sc.pos[0].astype(np.float64), 0.1, 16, 16)
+    g = api.build_gfb(gv, pos, nrm, rad, 0, outputs=("nd", "mask"))
+    prm = api.make_params(np.array([[0, 0, 0], [1, 1, 1]], np.float32), 0.01, 0.01)
+    prm.inv_voxel = float("inf")
+    with pytest.raises(RuntimeError):
+        api.aggregate_views(gv, g["nd"], g["mask"], prm)
+    prm = api.make_params(np.array([[0, 0, 0], [1, 1, 1]], np.float32), 0.01, 0.01)
+    prm.bbox_min[1] = float("nan")
+    with pytest.raises(RuntimeError):
+        api.aggregate_views(gv, g["nd"], g["mask"], prm)
+    api.stream_check()
