@@ -728,23 +728,18 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
   flush_stats(A.stats, 0, nsh, ns, nn, nv);
 }
 
-int sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
+
+// One block per 128 threads of the pass, no grid-stride cap: the walks of
+// the bounce and shadow passes are long and live rays cluster on the
+// target, so a capped grid (each warp revisiting the same tile column down
+// the screen) left most warps idle while a few carried the target's tiles;
+// with one warp per tile the block scheduler fills the SMs as blocks finish.
+int grid_all(int64_t n) {
+  int64_t b = (n + kTraceThreads - 1) / kTraceThreads;
+  if (b < 1) b = 1;
+  return (int)(b < 0x7fffffff ? b : 0x7fffffff);
 }
 
-int grid_for(int64_t n) {
-  int64_t b = (n + kTraceThreads - 1) / kTraceThreads;
-  int64_t cap = (int64_t)sms() * 16;
-  if (b < 1) b = 1;
-  return (int)(b < cap ? b : cap);
-}
 
 bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
   if (!g || !g->blob_dev) return false;
@@ -796,19 +791,19 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   // per-lane ray intervals of every view (walk's shared memory)
   const size_t tv_bytes = have_geom ? (size_t)A.L.nv * kTraceThreads * sizeof(float2) : 0;
   pe_event_before("primary_kernel", s);
-  primary_kernel<<<grid_for(n_thr), kTraceThreads, tv_bytes, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
+  primary_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
   pe_event_after("primary_kernel", s);
   PE_TRY_LAUNCH("primary_kernel");
   for (int b = 2; b <= mb; ++b) {
     A.bounce = b;
     pe_event_before("march_kernel", s);
-    march_kernel<<<grid_for(n_thr), kTraceThreads, tv_bytes, s>>>(A);
+    march_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("march_kernel", s);
     PE_TRY_LAUNCH("march_kernel");
   }
   if (mb >= 2) {
     pe_event_before("shadow_kernel", s);
-    shadow_kernel<<<grid_for(n_thr), kTraceThreads, tv_bytes, s>>>(A);
+    shadow_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("shadow_kernel", s);
     PE_TRY_LAUNCH("shadow_kernel");
   }
@@ -835,7 +830,7 @@ pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n
   A.stats = reinterpret_cast<long long *>(stats);
   A.only_bounce = only_bounce;
   const size_t tv_bytes = (size_t)A.L.nv * kTraceThreads * sizeof(float2);
-  shadow_dirs_kernel<<<grid_for(rpg * n_groups), kTraceThreads, tv_bytes, s>>>(A);
+  shadow_dirs_kernel<<<grid_all(rpg * n_groups), kTraceThreads, tv_bytes, s>>>(A);
   PE_TRY_LAUNCH("shadow_dirs_kernel");
   return PE_OK;
 }
