@@ -510,16 +510,27 @@ __device__ __forceinline__ pe_f3 ld3(const float *a, int64_t i) {
   return {a[3 * i], a[3 * i + 1], a[3 * i + 2]};
 }
 
+// Add the thread's counters to stats[0..4]: a warp reduction, then a block
+// reduction in shared memory, then one atomic per non-zero counter per
+// block (a grid of one block per 128 rays would otherwise pile millions of
+// atomics onto five addresses).  Every thread of the block calls it, last.
 __device__ __forceinline__ void flush_stats(long long *stats, long long a, long long b,
                                             long long c, long long d, long long e) {
-  if (!stats) return;
+  if (!stats) return;  // a kernel argument: uniform over the block
+  __shared__ long long s_st[kTraceThreads / 32][5];
   long long v[5] = {a, b, c, d, e};
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if ((threadIdx.x & 31) == 0 && v[k])
-      atomicAdd(reinterpret_cast<unsigned long long *>(stats + k), (unsigned long long)v[k]);
+    if (lane == 0) s_st[w][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) {
+    long long t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_st[i][threadIdx.x];
+    if (t) atomicAdd(reinterpret_cast<unsigned long long *>(stats + threadIdx.x), (unsigned long long)t);
   }
 }
 
