@@ -510,27 +510,45 @@ __device__ __forceinline__ pe_f3 ld3(const float *a, int64_t i) {
   return {a[3 * i], a[3 * i + 1], a[3 * i + 2]};
 }
 
-// Add the thread's counters to stats[0..4]: a warp reduction, then a block
-// reduction in shared memory, then one atomic per non-zero counter per
-// block (a grid of one block per 128 rays would otherwise pile millions of
-// atomics onto five addresses).  Every thread of the block calls it, last.
-__device__ __forceinline__ void flush_stats(long long *stats, long long a, long long b,
-                                            long long c, long long d, long long e) {
+// Per-block partial counters: each warp adds its own, and the last warp of
+// the block to finish sums them and issues one atomic per non-zero counter
+// (a grid of one block per 128 rays would otherwise pile millions of atomics
+// onto five addresses; no barrier at the end, so a warp done with its walk
+// does not wait for the block's slowest).  stats_begin() runs first in the
+// kernel, by every thread.
+struct stats_acc {
+  long long v[kTraceThreads / 32][5];
+  unsigned int done;
+};
+
+__device__ __forceinline__ void stats_begin(stats_acc &acc) {
+  if (threadIdx.x == 0) acc.done = 0u;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void flush_stats(long long *stats, stats_acc &acc, long long a,
+                                            long long b, long long c, long long d, long long e) {
   if (!stats) return;  // a kernel argument: uniform over the block
-  __shared__ long long s_st[kTraceThreads / 32][5];
   long long v[5] = {a, b, c, d, e};
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < 5; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0) s_st[w][k] = v[k];
+  unsigned int last = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc.v[w][k] = v[k];
+    __threadfence_block();
+    last = atomicAdd(&acc.done, 1u) == (blockDim.x >> 5) - 1u;
   }
-  __syncthreads();
-  if (threadIdx.x < 5) {
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence_block();
+  if (lane < 5) {
     long long t = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_st[i][threadIdx.x];
-    if (t) atomicAdd(reinterpret_cast<unsigned long long *>(stats + threadIdx.x), (unsigned long long)t);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += ((volatile long long *)acc.v[i])[lane];
+    if (t) atomicAdd(reinterpret_cast<unsigned long long *>(stats + lane), (unsigned long long)t);
   }
 }
 
@@ -566,6 +584,8 @@ __global__ void __launch_bounds__(kTraceThreads)
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
   const tile_map tm = make_tile_map(W, H, A.vb.n);
+  __shared__ stats_acc sacc;
+  stats_begin(sacc);
   long long nq = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
@@ -612,7 +632,7 @@ __global__ void __launch_bounds__(kTraceThreads)
       }
     }
   }
-  flush_stats(A.stats, nq, 0, ns, nn, nv);
+  flush_stats(A.stats, sacc, nq, 0, ns, nn, nv);
 }
 
 // One bounce (b >= 2).  Threads map to slots by the same 8x4 tiles as bounce
@@ -627,6 +647,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
   const int64_t per_view = (int64_t)W * H;
   const tile_map tm = make_tile_map(W, H, A.vb.n);
   const int64_t n_rays = A.h.n_rays;
+  __shared__ stats_acc sacc;
+  stats_begin(sacc);
   long long nq = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
@@ -665,7 +687,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
       if (A.h.ids) A.h.ids[(int64_t)(A.bounce - 1) * n_rays + slot] = id;
     }
   }
-  flush_stats(A.stats, nq, 0, ns, nn, nv);
+  flush_stats(A.stats, sacc, nq, 0, ns, nn, nv);
 }
 
 // Psi: shadow ray from the last hit toward the receiver (monostatic: w).
@@ -673,6 +695,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8) shadow_kernel(const __grid_c
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
   const tile_map tm = make_tile_map(W, H, A.vb.n);
+  __shared__ stats_acc sacc;
+  stats_begin(sacc);
   long long nsh = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
@@ -695,7 +719,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) shadow_kernel(const __grid_c
     walk<true>(A.L, p, w, A.eps, A.r_ov, active, S, blocked, A.err, ns, nn, nv);
     if (active) A.h.psi[slot] = blocked ? 0 : 1;
   }
-  flush_stats(A.stats, 0, nsh, ns, nn, nv);
+  flush_stats(A.stats, sacc, 0, nsh, ns, nn, nv);
 }
 
 // Psi toward other receivers (bistatic Eq. 14): a shadow ray from each
@@ -717,6 +741,8 @@ struct shadow_dirs_args {
 __global__ void __launch_bounds__(kTraceThreads, 8)
     shadow_dirs_kernel(const __grid_constant__ shadow_dirs_args A) {
   const int64_t total = A.rpg * A.n_groups;
+  __shared__ stats_acc sacc;
+  stats_begin(sacc);
   long long nsh = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total;
        base += (int64_t)gridDim.x * blockDim.x) {
@@ -736,7 +762,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
     walk<true>(A.L, p, w, A.eps, 0.0f, active, S, blocked, A.err, ns, nn, nv);
     if (in) A.psi[t] = (active && !blocked) ? 1 : 0;
   }
-  flush_stats(A.stats, 0, nsh, ns, nn, nv);
+  flush_stats(A.stats, sacc, 0, nsh, ns, nn, nv);
 }
 
 

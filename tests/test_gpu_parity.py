@@ -450,9 +450,17 @@ def test_trace_ragged_screen_bitexact(small_geom):
     c, r = scenes.bounding_sphere(sc.pos)
     views = pipe.views_from_angles([90.0, 80.0], [45.0, 30.0], c, r * 1.02, 37, 23)
     keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
-    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], 3, d["prm"])
+    stats = torch.zeros(8, dtype=torch.int64, device=DEV)
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], 3, d["prm"], stats=stats)
     api.stream_check()
     per = 37 * 23
+    # the device counters, exactly: every screen ray is a query, bounce b
+    # queries the rays that hit at b - 1, a shadow ray leaves every ray that
+    # ended after two or more bounces
+    M = h.M.cpu().numpy()
+    st = stats.cpu().numpy()
+    assert st[0] == 2 * per + int((M >= 1).sum()) + int((M >= 2).sum())
+    assert st[1] == int((M >= 2).sum())
     multi = 0
     for a, v in enumerate(views):
         ov = _oracle_view(v)
