@@ -403,7 +403,8 @@ typedef struct {
   int32_t n_freq;
   const double *freqs_hz;    /* host [n_freq] */
   int32_t max_bounces;
-  int32_t angle_batch;       /* angles per batch (1..PE_MAX_BATCH), 0 = auto */
+  int32_t angle_batch;       /* angles per batch (1..PE_MAX_BATCH), 0 = auto
+                                (as many as fit ~16 GB of ray records) */
 } pe_sweep;
 
 /* The view of a monostatic incidence (a1): w = (sin t cos p, sin t sin p,

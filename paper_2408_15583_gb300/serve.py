@@ -90,7 +90,7 @@ def estimate(req: RcsRequest, geometry_cached: bool):
     while it runs, and the fused geometry it leaves resident if not cached."""
     n = req.n_points
     per_angle = req.W * req.W * (8 + 60 + 8 + 4 + 1 + 8)
-    batch = max(1, min(64, len(req.theta_deg), (2 << 30) // max(per_angle, 1)))
+    batch = max(1, min(64, len(req.theta_deg), (16 << 30) // max(per_angle, 1)))  # the library's rule
     b = 28 * n                                   # points
     b += batch * per_angle                       # sweep workspace
     b += len(req.theta_deg) * len(req.freqs_hz) * 12 * 8 * 2   # field + sigma
