@@ -111,7 +111,24 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f
 // sincos, eight multiply-adds.
 __device__ __forceinline__ void add_term(float kf, float khi, float klo, float au, float av,
                                          float dhi, float dlo, const float V[4], float b[kAcc]) {
-  const float s = sincf_(kf * au) * sincf_(kf * av);
+  // the common case, both arguments small, as one branch: the product of the
+  // two Taylor series of sin(x)/x in x^2 (through x^8, truncation < 3e-11)
+  const float xa = kf * au, xb = kf * av;
+  float s;
+  if (fmaxf(fabsf(xa), fabsf(xb)) < 0.5f) {
+    const float ta = xa * xa, tb = xb * xb;
+    float pa = fmaf(ta, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    float pb = fmaf(tb, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    pa = fmaf(pa, ta, 1.0f / 120.0f);
+    pb = fmaf(pb, tb, 1.0f / 120.0f);
+    pa = fmaf(pa, ta, -1.0f / 6.0f);
+    pb = fmaf(pb, tb, -1.0f / 6.0f);
+    pa = fmaf(pa, ta, 1.0f);
+    pb = fmaf(pb, tb, 1.0f);
+    s = pa * pb;
+  } else {
+    s = sincf_(xa) * sincf_(xb);
+  }
   const float ph = khi * dhi;
   const float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
   const float red = (ph - rintf(ph)) + er;
