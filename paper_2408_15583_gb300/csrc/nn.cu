@@ -265,38 +265,88 @@ __global__ void gemm_splitk_reduce(const pe_gemm_args g, int split) {
 // ---------------------------------------------------------------------------
 // 3x3 convolution helpers (NHWC, zero padding 1): col[p][(ky*3+kx)*C + c]
 // ---------------------------------------------------------------------------
+// VEC channels per thread: 8 (one 16-byte load and store) when C is a
+// multiple of 8 and the buffers are 16-byte aligned, else 1.  The index
+// arithmetic runs once per VEC channels.
+template <int VEC>
+struct chunk_of;
+template <>
+struct chunk_of<1> {
+  using T = bf16;
+};
+template <>
+struct chunk_of<8> {
+  using T = uint4;
+};
+
+template <int VEC>
 __global__ void im2col3_kernel(const bf16 *__restrict__ X, int B, int H, int W, int C,
                                bf16 *__restrict__ col) {
-  const int64_t total = (int64_t)B * H * W * 9 * C;
+  using T = typename chunk_of<VEC>::T;
+  const int CV = C / VEC;
+  const T *Xv = reinterpret_cast<const T *>(X);
+  T *colv = reinterpret_cast<T *>(col);
+  const int64_t total = (int64_t)B * H * W * 9 * CV;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % C);
-    int tap = (int)((t / C) % 9);
-    int64_t p = t / (9 * (int64_t)C);
-    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-    int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-    col[t] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                 ? X[(((int64_t)b * H + yy) * W + xx) * C + c]
-                 : f2b(0.0f);
+    const int cv = (int)(t % CV);
+    const int64_t r = t / CV;
+    const int tap = (int)(r % 9);
+    const int64_t p = r / 9;
+    const int x = (int)(p % W);
+    const int64_t q = p / W;
+    const int y = (int)(q % H), b = (int)(q / H);
+    const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+    T v;
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+      v = Xv[(((int64_t)b * H + yy) * W + xx) * CV + cv];
+    } else {
+      memset(&v, 0, sizeof(T));  // bf16 zero is all-zero bits
+    }
+    colv[t] = v;
   }
 }
 
-// dX[b,y,x,c] = sum over taps of dcol at the pixel that read (y, x) through that tap.
+// dX[b,y,x,c] = sum over taps of dcol at the pixel that read (y, x) through
+// that tap (taps in order 0..8, FP32 sums).
+template <int VEC>
 __global__ void col2im3_kernel(const bf16 *__restrict__ dcol, int B, int H, int W, int C,
                                bf16 *__restrict__ dX) {
-  const int64_t total = (int64_t)B * H * W * C;
+  const int CV = C / VEC;
+  const int64_t total = (int64_t)B * H * W * CV;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % C);
-    int64_t p = t / C;
-    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-    float s = 0.0f;
+    const int cv = (int)(t % CV);
+    const int64_t p = t / CV;
+    const int x = (int)(p % W);
+    const int64_t q = p / W;
+    const int y = (int)(q % H), b = (int)(q / H);
+    float s[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) s[k] = 0.0f;
     for (int tap = 0; tap < 9; ++tap) {
-      int py = y - (tap / 3 - 1), px = x - (tap % 3 - 1);
+      const int py = y - (tap / 3 - 1), px = x - (tap % 3 - 1);
       if (py < 0 || py >= H || px < 0 || px >= W) continue;
-      s += b2f(dcol[((((int64_t)b * H + py) * W + px) * 9 + tap) * C + c]);
+      const bf16 *src = dcol + ((((int64_t)b * H + py) * W + px) * 9 + tap) * C + (int64_t)cv * VEC;
+      if (VEC == 8) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(src);
+        const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) s[k] += b2f(e[k]);
+      } else {
+        s[0] += b2f(src[0]);
+      }
     }
-    dX[t] = f2b(s);
+    bf16 *dst = dX + p * C + (int64_t)cv * VEC;
+    if (VEC == 8) {
+      uint4 u;
+      bf16 *e = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) e[k] = f2b(s[k]);
+      *reinterpret_cast<uint4 *>(dst) = u;
+    } else {
+      dst[0] = f2b(s[0]);
+    }
   }
 }
 
@@ -955,13 +1005,19 @@ extern "C" pe_status pe_nn_im2col3(const void *X, int32_t B, int32_t H, int32_t 
   NN_CHECK_STREAM;
   if (!X || !col || B <= 0 || H <= 0 || W <= 0 || C <= 0)
     return pe_fail(PE_EINVAL, "pe_nn_im2col3: bad arguments");
+  const bool v8 = (C % 8) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                  (reinterpret_cast<uintptr_t>(col) & 15) == 0;
+  const bf16 *x = static_cast<const bf16 *>(X);
+  bf16 *y = static_cast<bf16 *>(col);
   if (!backward) {
-    im2col3_kernel<<<grid1((int64_t)B * H * W * 9 * C, 256), 256, 0, s>>>(
-        static_cast<const bf16 *>(X), B, H, W, C, static_cast<bf16 *>(col));
+    const int64_t n = (int64_t)B * H * W * 9 * (v8 ? C / 8 : C);
+    if (v8) im2col3_kernel<8><<<grid1(n, 256), 256, 0, s>>>(x, B, H, W, C, y);
+    else im2col3_kernel<1><<<grid1(n, 256), 256, 0, s>>>(x, B, H, W, C, y);
     PE_TRY_LAUNCH("im2col3_kernel");
   } else {  // X is dcol [P][9C], col is dX [P][C]
-    col2im3_kernel<<<grid1((int64_t)B * H * W * C, 256), 256, 0, s>>>(
-        static_cast<const bf16 *>(X), B, H, W, C, static_cast<bf16 *>(col));
+    const int64_t n = (int64_t)B * H * W * (v8 ? C / 8 : C);
+    if (v8) col2im3_kernel<8><<<grid1(n, 256), 256, 0, s>>>(x, B, H, W, C, y);
+    else col2im3_kernel<1><<<grid1(n, 256), 256, 0, s>>>(x, B, H, W, C, y);
     PE_TRY_LAUNCH("col2im3_kernel");
   }
   return PE_OK;
