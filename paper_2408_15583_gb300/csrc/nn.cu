@@ -653,35 +653,77 @@ __global__ void maxpool2_bwd_kernel(const bf16 *__restrict__ dY, const uint8_t *
 }
 
 // out[b, 2y+i, 2x+j, off + c] = in[b, y, x, 4c + 2i + j]; dir 1: the reverse.
+// One thread per pixel (Y, X) of the 2H x 2W image and VEC consecutive
+// channels c: the small image's element [b, Y/2, X/2][4c + 2(Y&1) + (X&1)]
+// moves to / from the large image's [b, Y, X][off + c] (VEC = 8: the large
+// side as one 16-byte access).
+template <int VEC>
 __global__ void pixel_shuffle2_kernel(const bf16 *__restrict__ src, int B, int H, int W, int C,
                                       bf16 *__restrict__ dst, int64_t ld_big, int off, int dir) {
-  const int64_t total = (int64_t)B * H * W * 4 * C;
+  const int CV = C / VEC;
+  const int W2 = 2 * W, H2 = 2 * H;
+  const int64_t total = (int64_t)B * H2 * W2 * CV;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int c4 = (int)(t % (4 * C));
-    int64_t p = t / (4 * C);
-    int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((int64_t)W * H));
-    int c = c4 >> 2, i = (c4 >> 1) & 1, j = c4 & 1;
-    int64_t big = (((int64_t)b * 2 * H + 2 * y + i) * 2 * W + 2 * x + j) * ld_big + off + c;
-    if (dir == 0)
-      dst[big] = src[t];
-    else
-      dst[t] = src[big];
+    const int c0 = (int)(t % CV) * VEC;
+    const int64_t P = t / CV;                 // large-image pixel
+    const int X = (int)(P % W2);
+    const int64_t q = P / W2;
+    const int Y = (int)(q % H2), b = (int)(q / H2);
+    const int sub = 2 * (Y & 1) + (X & 1);
+    const int64_t small = ((int64_t)b * H + (Y >> 1)) * W + (X >> 1);
+    const int64_t sbase = small * 4 * C + 4 * (int64_t)c0 + sub;   // stride 4 over c
+    const int64_t bbase = P * ld_big + off + c0;
+    if (VEC == 8) {
+      if (dir == 0) {
+        uint4 u;
+        bf16 *e = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) e[k] = src[sbase + 4 * k];
+        *reinterpret_cast<uint4 *>(dst + bbase) = u;
+      } else {
+        const uint4 u = *reinterpret_cast<const uint4 *>(src + bbase);
+        const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dst[sbase + 4 * k] = e[k];
+      }
+    } else {
+      if (dir == 0)
+        dst[bbase] = src[sbase];
+      else
+        dst[sbase] = src[bbase];
+    }
   }
 }
 
-// dst[p][doff + c] (=|+=) src[p][soff + c] for c < C.
+// dst[p][doff + c] (=|+=) src[p][soff + c] for c < C; VEC = 8: 16-byte
+// chunks (sums per element in FP32, as for VEC = 1).
+template <int VEC>
 __global__ void copy_channels_kernel(const bf16 *__restrict__ src, int64_t lds, int soff,
                                      bf16 *__restrict__ dst, int64_t ldd, int doff, int64_t P,
                                      int C, int accumulate) {
-  const int64_t total = P * C;
+  const int CV = C / VEC;
+  const int64_t total = P * CV;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int c = (int)(t % C);
-    int64_t p = t / C;
-    float v = b2f(src[p * lds + soff + c]);
+    const int c = (int)(t % CV) * VEC;
+    const int64_t p = t / CV;
+    const bf16 *sp = src + p * lds + soff + c;
     bf16 *d = dst + p * ldd + doff + c;
-    *d = f2b(accumulate ? b2f(*d) + v : v);
+    if (VEC == 8) {
+      uint4 u = *reinterpret_cast<const uint4 *>(sp);
+      if (accumulate) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(d);
+        bf16 *e = reinterpret_cast<bf16 *>(&u);
+        const bf16 *f = reinterpret_cast<const bf16 *>(&w);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) e[k] = f2b(b2f(f[k]) + b2f(e[k]));
+      }
+      *reinterpret_cast<uint4 *>(d) = u;
+    } else {
+      const float v = b2f(*sp);
+      *d = f2b(accumulate ? b2f(*d) + v : v);
+    }
   }
 }
 
@@ -1201,9 +1243,20 @@ extern "C" pe_status pe_nn_pixel_shuffle2(const void *src, int32_t B, int32_t H,
   NN_CHECK_STREAM;
   if (!src || !dst || B <= 0 || H <= 0 || W <= 0 || C <= 0 || off < 0 || off + C > ld_big)
     return pe_fail(PE_EINVAL, "pe_nn_pixel_shuffle2: bad arguments");
-  pixel_shuffle2_kernel<<<grid1((int64_t)B * H * W * 4 * C, 256), 256, 0, s>>>(
-      static_cast<const bf16 *>(src), B, H, W, C, static_cast<bf16 *>(dst), ld_big, off,
-      backward ? 1 : 0);
+  {
+    const bf16 *big = static_cast<const bf16 *>(backward ? src : dst);
+    const bool v8 = C % 8 == 0 && off % 8 == 0 && ld_big % 8 == 0 &&
+                    (reinterpret_cast<uintptr_t>(big) & 15) == 0;
+    const int64_t n = (int64_t)B * 4 * H * W * (v8 ? C / 8 : C);
+    if (v8)
+      pixel_shuffle2_kernel<8><<<grid1(n, 256), 256, 0, s>>>(
+          static_cast<const bf16 *>(src), B, H, W, C, static_cast<bf16 *>(dst), ld_big, off,
+          backward ? 1 : 0);
+    else
+      pixel_shuffle2_kernel<1><<<grid1(n, 256), 256, 0, s>>>(
+          static_cast<const bf16 *>(src), B, H, W, C, static_cast<bf16 *>(dst), ld_big, off,
+          backward ? 1 : 0);
+  }
   PE_TRY_LAUNCH("pixel_shuffle2_kernel");
   return PE_OK;
 }
@@ -1213,9 +1266,17 @@ extern "C" pe_status pe_nn_copy_channels(const void *src, int64_t lds, int32_t s
                                          int32_t accumulate, void *stream) {
   NN_CHECK_STREAM;
   if (!src || !dst || P <= 0 || C <= 0) return pe_fail(PE_EINVAL, "pe_nn_copy_channels: bad arguments");
-  copy_channels_kernel<<<grid1(P * C, 256), 256, 0, s>>>(static_cast<const bf16 *>(src), lds, soff,
-                                                         static_cast<bf16 *>(dst), ldd, doff, P, C,
-                                                         accumulate);
+  const bool v8 = C % 8 == 0 && soff % 8 == 0 && doff % 8 == 0 && lds % 8 == 0 && ldd % 8 == 0 &&
+                  (reinterpret_cast<uintptr_t>(src) & 15) == 0 &&
+                  (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+  if (v8)
+    copy_channels_kernel<8><<<grid1(P * (C / 8), 256), 256, 0, s>>>(
+        static_cast<const bf16 *>(src), lds, soff, static_cast<bf16 *>(dst), ldd, doff, P, C,
+        accumulate);
+  else
+    copy_channels_kernel<1><<<grid1(P * C, 256), 256, 0, s>>>(
+        static_cast<const bf16 *>(src), lds, soff, static_cast<bf16 *>(dst), ldd, doff, P, C,
+        accumulate);
   PE_TRY_LAUNCH("copy_channels_kernel");
   return PE_OK;
 }
