@@ -517,6 +517,54 @@ __global__ void ln_fwd_kernel(const bf16 *__restrict__ X, const float *__restric
   }
 }
 
+// LayerNorm for narrow pixels (C a multiple of 8, used for C = 32): one thread per
+// pixel, its C channels in registers through 16-byte loads and stores, the
+// mean and variance summed in channel order (no shuffles).
+template <int C>
+__global__ void __launch_bounds__(256) ln_fwd_narrow_kernel(
+    const bf16 *__restrict__ X, const float *__restrict__ gam, const float *__restrict__ bet,
+    int64_t P, float eps, bf16 *__restrict__ Y, float *__restrict__ mean,
+    float *__restrict__ rstd) {
+  static_assert(C % 8 == 0 && C <= 64, "narrow LayerNorm: C a multiple of 8, at most 64");
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float v[C];
+    const uint4 *x = reinterpret_cast<const uint4 *>(X + p * C);
+#pragma unroll
+    for (int k = 0; k < C / 8; ++k) {
+      const uint4 u = x[k];
+      const bf16 *e = reinterpret_cast<const bf16 *>(&u);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[8 * k + m] = b2f(e[m]);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) s += v[c];
+    const float mu = s / C;
+    float var = 0.0f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const float d = v[c] - mu;
+      var += d * d;
+    }
+    const float rs = rsqrtf(var / C + eps);
+    uint4 *y = reinterpret_cast<uint4 *>(Y + p * C);
+#pragma unroll
+    for (int k = 0; k < C / 8; ++k) {
+      uint4 u;
+      bf16 *e = reinterpret_cast<bf16 *>(&u);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int c = 8 * k + m;
+        e[m] = f2b((v[c] - mu) * rs * __ldg(gam + c) + __ldg(bet + c));
+      }
+      y[k] = u;
+    }
+    mean[p] = mu;
+    rstd[p] = rs;
+  }
+}
+
 // dX and per-warp partials of dgamma, dbeta: part[warp][2][C].
 __global__ void ln_bwd_kernel(const bf16 *__restrict__ dY, const bf16 *__restrict__ X,
                               const float *__restrict__ gam, const float *__restrict__ mean,
@@ -1135,9 +1183,17 @@ extern "C" pe_status pe_nn_layernorm(const void *X, const float *gamma, const fl
   NN_CHECK_STREAM;
   if (!X || !gamma || !beta || !Y || !mean || !rstd || P <= 0 || C <= 0 || C > 256)
     return pe_fail(PE_EINVAL, "pe_nn_layernorm: bad arguments (C <= 256)");
-  ln_fwd_kernel<<<grid1(P * 32, 256), 256, 0, s>>>(static_cast<const bf16 *>(X), gamma, beta, P, C,
-                                                   eps, static_cast<bf16 *>(Y), mean, rstd);
-  PE_TRY_LAUNCH("ln_fwd_kernel");
+  const bool al16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+  if (al16 && C == 32) {   // (64 channels in registers would cap a thread at 255 registers)
+    ln_fwd_narrow_kernel<32><<<grid1(P, 256), 256, 0, s>>>(
+        static_cast<const bf16 *>(X), gamma, beta, P, eps, static_cast<bf16 *>(Y), mean, rstd);
+    PE_TRY_LAUNCH("ln_fwd_narrow_kernel");
+  } else {
+    ln_fwd_kernel<<<grid1(P * 32, 256), 256, 0, s>>>(static_cast<const bf16 *>(X), gamma, beta, P,
+                                                     C, eps, static_cast<bf16 *>(Y), mean, rstd);
+    PE_TRY_LAUNCH("ln_fwd_kernel");
+  }
   return PE_OK;
 }
 
