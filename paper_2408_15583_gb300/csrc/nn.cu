@@ -358,30 +358,31 @@ __device__ __forceinline__ float2 ld2(const bf162 *p) { return __bfloat1622float
 
 // Y = bias + sum_taps w * X (FLIP = 0), or the data gradient dX = sum_taps
 // w[6-ky][6-kx] * dY[y+ky-3][x+kx-3] (FLIP = 1, X = dY, no bias).  A thread
-// owns one channel pair and four consecutive pixels of one row; block row y
+// owns one channel pair and eight consecutive pixels of one row; block row y
 // = image row (b, y).
 template <bool FLIP>
 __global__ void __launch_bounds__(256) dw7_kernel(const bf162 *__restrict__ X,
                                                   const float *__restrict__ w,
                                                   const float *__restrict__ bias, int B, int H,
                                                   int W, int C, bf162 *__restrict__ Y) {
-  const int cp2 = C >> 1, groups = (W + 3) >> 2, per_row = groups * cp2, rows = B * H;
+  constexpr int NPX = 8;  // pixels per thread
+  const int cp2 = C >> 1, groups = (W + NPX - 1) / NPX, per_row = groups * cp2, rows = B * H;
   for (int r = blockIdx.y; r < rows; r += gridDim.y) {
     const int b = r / H, y = r - b * H;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < per_row; t += gridDim.x * blockDim.x) {
-      const int cp = t % cp2, x0 = (t / cp2) * 4;
-      float2 acc[4];
+      const int cp = t % cp2, x0 = (t / cp2) * NPX;
+      float2 acc[NPX];
       const float2 b0 = bias ? make_float2(bias[2 * cp], bias[2 * cp + 1]) : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) acc[i] = b0;
+      for (int i = 0; i < NPX; ++i) acc[i] = b0;
 #pragma unroll 1
       for (int ky = 0; ky < 7; ++ky) {
         const int yy = y + ky - 3;
         if (yy < 0 || yy >= H) continue;
         const bf162 *row = X + (size_t)(b * H + yy) * W * cp2 + cp;
-        float2 in[10];
+        float2 in[NPX + 6];
 #pragma unroll
-        for (int k = 0; k < 10; ++k) {
+        for (int k = 0; k < NPX + 6; ++k) {
           const int xx = x0 + k - 3;
           in[k] = (xx >= 0 && xx < W) ? ld2(row + (size_t)xx * cp2) : make_float2(0.f, 0.f);
         }
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(256) dw7_kernel(const bf162 *__restrict__ X,
           const int wx = FLIP ? 6 - kx : kx;
           const float2 wv = __ldg(reinterpret_cast<const float2 *>(w + (wy * 7 + wx) * C) + cp);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < NPX; ++i) {
             acc[i].x = fmaf(wv.x, in[i + kx].x, acc[i].x);
             acc[i].y = fmaf(wv.y, in[i + kx].y, acc[i].y);
           }
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(256) dw7_kernel(const bf162 *__restrict__ X,
       }
       bf162 *out = Y + (size_t)r * W * cp2 + cp;
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < NPX; ++i)
         if (x0 + i < W) out[(size_t)(x0 + i) * cp2] = __floats2bfloat162_rn(acc[i].x, acc[i].y);
     }
   }
@@ -1121,7 +1122,7 @@ extern "C" pe_status pe_nn_dwconv7(const void *X, const float *w, const float *b
   if (!X || !w || !Y || B <= 0 || H <= 0 || W <= 0 || C <= 0 || (C & 1) || !al4(X) || !al4(Y) ||
       (reinterpret_cast<uintptr_t>(w) & 7))
     return pe_fail(PE_EINVAL, "pe_nn_dwconv7: bad arguments (C even, aligned buffers)");
-  const int per_row = ((W + 3) / 4) * (C / 2);
+  const int per_row = ((W + 7) / 8) * (C / 2);
   dim3 grid((per_row + 255) / 256, (unsigned)(B * H < 65535 ? B * H : 65535));
   dw7_kernel<false><<<grid, 256, 0, s>>>(static_cast<const bf162 *>(X), w, bias, B, H, W, C,
                                          static_cast<bf162 *>(Y));
@@ -1149,7 +1150,7 @@ extern "C" pe_status pe_nn_dwconv7_bwd(const void *X, const void *dY, const floa
       !al4(dY) || (dX && !al4(dX)) || (reinterpret_cast<uintptr_t>(w) & 7))
     return pe_fail(PE_EINVAL, "pe_nn_dwconv7_bwd: bad arguments (C even, aligned buffers)");
   if (dX) {
-    const int per_row = ((W + 3) / 4) * (C / 2);
+    const int per_row = ((W + 7) / 8) * (C / 2);
     dim3 grid((per_row + 255) / 256, (unsigned)(B * H < 65535 ? B * H : 65535));
     dw7_kernel<true><<<grid, 256, 0, s>>>(static_cast<const bf162 *>(dY), w, nullptr, B, H, W, C,
                                           static_cast<bf162 *>(dX));
