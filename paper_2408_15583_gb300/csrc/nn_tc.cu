@@ -140,7 +140,7 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 3)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const pe_gemm_args g, int stages, unsigned int *err) {
   using cfg = tc_cfg<BN>;
@@ -330,6 +330,10 @@ pe_status launch_bn(const pe_gemm_args &g, cudaStream_t s) {
   if (!attr) {
     PE_TRY_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      cfg::smem(TC_STAGES)));
+    // the whole unified L1 as shared memory: up to three CTAs of the
+    // narrow shapes side by side (registers are capped for three as well)
+    PE_TRY_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
     attr = true;
   }
   dim3 grid((unsigned)((g.M + TC_BM - 1) / TC_BM), (unsigned)((g.N + BN - 1) / BN));
