@@ -135,7 +135,7 @@ __device__ __forceinline__ void stage_tile(bf16 *S, const bf16 *__restrict__ X, 
 // C = epilogue(alpha * A B) over one 128 x 64 tile and the K range of split
 // blockIdx.z; with split-K the raw products go to part[z][M][N].
 template <bool AK, bool BK>
-__global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(const pe_gemm_args g) {
+__global__ void __launch_bounds__(GEMM_THREADS, 3) gemm_kernel(const pe_gemm_args g) {
   __shared__ __align__(128) bf16 smem[STAGES * (A_STAGE + B_STAGE)];
   bf16 *As = smem, *Bs = smem + STAGES * A_STAGE;
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
