@@ -361,7 +361,7 @@ __device__ __forceinline__ float2 ld2(const bf162 *p) { return __bfloat1622float
 // owns one channel pair and eight consecutive pixels of one row; block row y
 // = image row (b, y).
 template <bool FLIP>
-__global__ void __launch_bounds__(256) dw7_kernel(const bf162 *__restrict__ X,
+__global__ void __launch_bounds__(256, 4) dw7_kernel(const bf162 *__restrict__ X,
                                                   const float *__restrict__ w,
                                                   const float *__restrict__ bias, int B, int H,
                                                   int W, int C, bf162 *__restrict__ Y) {
@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(256) ln_fwd_narrow_kernel(
 }
 
 // dX and per-warp partials of dgamma, dbeta: part[warp][2][C].
-__global__ void ln_bwd_kernel(const bf16 *__restrict__ dY, const bf16 *__restrict__ X,
+__global__ void __launch_bounds__(256, 4) ln_bwd_kernel(const bf16 *__restrict__ dY, const bf16 *__restrict__ X,
                               const float *__restrict__ gam, const float *__restrict__ mean,
                               const float *__restrict__ rstd, int64_t P, int C,
                               bf16 *__restrict__ dX, float *__restrict__ part) {
