@@ -460,19 +460,22 @@ __global__ void dw7_wgrad_kernel(const bf162 *__restrict__ X, const bf162 *__res
 // out[i] = (accumulate ? out[i] : 0) + sum over chunks of part[chunk][i],
 // i < n, in a fixed order: lane ty of the block sums chunks ty, ty + 8, ...
 // and the eight partial sums are added in order.  Block (32, 8).
-__global__ void sum_chunks_kernel(const float *__restrict__ part, int chunks, int64_t n,
-                                  float *__restrict__ out, int accumulate) {
-  __shared__ float red[8][33];
+__global__ void __launch_bounds__(1024) sum_chunks_kernel(const float *__restrict__ part,
+                                                          int chunks, int64_t n,
+                                                          float *__restrict__ out, int accumulate) {
+  // 32 outputs per block, 32 threads per output walking the chunks in a
+  // fixed interleave, then their 32 sums in a fixed order (deterministic)
+  __shared__ float red[32][33];
   const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
   float s = 0.0f;
   if (i < n)
-    for (int k = threadIdx.y; k < chunks; k += 8) s += part[(int64_t)k * n + i];
+    for (int k = threadIdx.y; k < chunks; k += 32) s += part[(int64_t)k * n + i];
   red[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.y == 0 && i < n) {
     float t = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+    for (int k = 0; k < 32; ++k) t += red[k][threadIdx.x];
     out[i] = accumulate ? out[i] + t : t;
   }
 }
@@ -1168,7 +1171,7 @@ extern "C" pe_status pe_nn_dwconv7_bwd(const void *X, const void *dY, const floa
     PE_TRY_LAUNCH("dw7_wgrad_kernel");
     // part[chunk][50][C]: taps 0..48 -> dw, 49 -> db; sum the chunks in
     // order into chunk 0 (a block reads only the columns it writes)
-    sum_chunks_kernel<<<(unsigned)((50 * C + 31) / 32), dim3(32, 8), 0, s>>>(part, chunks,
+    sum_chunks_kernel<<<(unsigned)((50 * C + 31) / 32), dim3(32, 32), 0, s>>>(part, chunks,
                                                                           50 * (int64_t)C, part, 0);
     PE_TRY_LAUNCH("sum_chunks_kernel");
     if (dw) PE_TRY_CUDA(cudaMemcpyAsync(dw, part, sizeof(float) * 49 * C, cudaMemcpyDeviceToDevice, s));
@@ -1220,7 +1223,7 @@ extern "C" pe_status pe_nn_layernorm_bwd(const void *dY, const void *X, const fl
                                        gamma, mean, rstd, P, C, static_cast<bf16 *>(dX), part);
   PE_TRY_LAUNCH("ln_bwd_kernel");
   // part[warp][2][C]: sum over warps in order
-  sum_chunks_kernel<<<(unsigned)((2 * C + 31) / 32), dim3(32, 8), 0, s>>>(part, (int)warps,
+  sum_chunks_kernel<<<(unsigned)((2 * C + 31) / 32), dim3(32, 32), 0, s>>>(part, (int)warps,
                                                                         2 * (int64_t)C, part, 0);
   PE_TRY_LAUNCH("sum_chunks_kernel");
   if (dgamma) PE_TRY_CUDA(cudaMemcpyAsync(dgamma, part, sizeof(float) * C, cudaMemcpyDeviceToDevice, s));
@@ -1258,7 +1261,7 @@ extern "C" pe_status pe_nn_colsum(const void *X, int64_t M, int32_t N, int64_t l
         x, M, N, ld, rpc, part);
   }
   PE_TRY_LAUNCH("colsum_kernel");
-  sum_chunks_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 8), 0, s>>>(part, (int)chunks, N, out,
+  sum_chunks_kernel<<<(unsigned)((N + 31) / 32), dim3(32, 32), 0, s>>>(part, (int)chunks, N, out,
                                                                       accumulate);
   PE_TRY_LAUNCH("sum_chunks_kernel");
   return PE_OK;
