@@ -15,7 +15,7 @@
  *     *_workspace() query returns (256-byte aligned).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Every call is asynchronous on `stream`.  Argument errors are
- *     returned synchronously; device-side conditions (queue or candidate-list
+ *     returned synchronously; device-side conditions (candidate-list
  *     overflow, bounded waits that timed out) are reported by
  *     pe_stream_check().  No C++ exception crosses the ABI.
  *   - Arrays are row-major.  Points are float32 [N][3] (x,y,z).  A view's

@@ -12,9 +12,10 @@
 // the candidate set and its selection do not depend on visiting order, the
 // hit ids equal those of a brute-force search over all splats.
 //
-// Between bounces the live rays are compacted into a queue with one atomic
-// per warp (ballot + popc); per-ray state lives in the last-hit records, so a
-// ray that misses simply keeps its previous record.
+// Every pass (bounce 1, each later bounce, the shadow rays) runs one warp
+// per 8x4 tile of the incidence screen, one block per 128 rays; a lane is
+// live when its ray's bounce count M says so.  Per-ray state lives in the
+// last-hit records, so a ray that misses simply keeps its previous record.
 #include <cstring>
 
 #include "pe_internal.cuh"
