@@ -3,7 +3,7 @@
 //   C[m][n] = epilogue(alpha * sum_k A[m][k] * B[n][k])
 // (A: activations [M][lda], B: weights [N][ldb], BF16, FP32 accumulation).
 //
-// One CTA computes a 128 x BN tile (BN = 64, 128 or 256) with eight warps:
+// One CTA computes a 128 x BN tile (BN = 32, 64, 128 or 256) with eight warps:
 //   warp 0 (one lane)  streams 128 x 64 and BN x 64 operand tiles into a
 //                      shared-memory ring of up to four stages with TMA
 //                      (128-byte swizzle, zero fill outside the matrices);
@@ -38,7 +38,7 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 template <int BN>
 struct tc_cfg {
   static constexpr int A_BYTES = TC_BM * TC_BK * 2;  // 16 KB, 1024-byte multiple
-  static constexpr int B_BYTES = BN * TC_BK * 2;     // 8/16/32 KB
+  static constexpr int B_BYTES = BN * TC_BK * 2;     // 4/8/16/32 KB
   static constexpr int STAGE = A_BYTES + B_BYTES;
   static constexpr int C_LD = BN + 4;                        // FP32 staging row (floats)
   static constexpr int C_BYTES = TC_BM * C_LD * 4;
@@ -351,6 +351,7 @@ bool pe_gemm_tc_eligible(const pe_gemm_args &g) {
 }
 
 pe_status pe_gemm_tc(const pe_gemm_args &g, cudaStream_t s) {
+  if (g.N <= 32) return launch_bn<32>(g, s);
   if (g.N <= 64) return launch_bn<64>(g, s);
   if (g.N <= 128) return launch_bn<128>(g, s);
   return launch_bn<256>(g, s);

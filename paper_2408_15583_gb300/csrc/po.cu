@@ -23,7 +23,7 @@ namespace {
 constexpr int kPoThreads = 256;
 constexpr int kPoGroups = 64;    // groups (angles) per launch
 constexpr int kPoFreqs = 256;    // frequencies per launch
-constexpr int kFlush = 16;       // terms between TwoSum flushes
+constexpr int kFlush = 32;       // terms between TwoSum flushes
 constexpr int kAcc = 8;          // sums per (ray, frequency): 2 pol x (e1, e2) x (re, im)
 constexpr float kTwoPi = 6.28318530717958647692f;
 
