@@ -460,11 +460,14 @@ __global__ void dw7_wgrad_kernel(const bf162 *__restrict__ X, const bf162 *__res
 // out[i] = (accumulate ? out[i] : 0) + sum over chunks of part[chunk][i],
 // i < n, in a fixed order: lane ty of the block sums chunks ty, ty + 8, ...
 // and the eight partial sums are added in order.  Block (32, 8).
-__global__ void __launch_bounds__(1024) sum_chunks_kernel(const float *__restrict__ part,
-                                                          int chunks, int64_t n,
-                                                          float *__restrict__ out, int accumulate) {
+__global__ void __launch_bounds__(1024) sum_chunks_kernel(const float *part, int chunks,
+                                                          int64_t n, float *out,
+                                                          int accumulate) {
   // 32 outputs per block, 32 threads per output walking the chunks in a
-  // fixed interleave, then their 32 sums in a fixed order (deterministic)
+  // fixed interleave, then their 32 sums in a fixed order (deterministic).
+  // out may be part itself (chunk 0 overwritten): a block reads only its own
+  // 32 columns, all of them before the barrier, and writes them after it
+  // (hence no __restrict__ here).
   __shared__ float red[32][33];
   const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
   float s = 0.0f;
