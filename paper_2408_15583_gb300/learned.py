@@ -16,9 +16,8 @@ frame, hit-mask logit), each: 3x3 conv to 4C -> pixel shuffle -> concat skip
 from __future__ import annotations
 
 import ctypes as C
-import math
 from dataclasses import dataclass
-from typing import Dict, List, Optional
+from typing import Dict, List
 
 import numpy as np
 import torch

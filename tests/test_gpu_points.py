@@ -5,7 +5,6 @@ wherever the normal is well defined (the two smallest covariance eigenvalues
 apart by at least 10 % of the middle one), orientation exact where the
 reference is not near perpendicular.  At the composite workload's full size
 (1M points) a sample of points is checked one by one."""
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ Failures are injected on the host (a start that raises, a poll that raises,
 malformed requests, cancellation); nothing here touches a device.
 """
 import numpy as np
-import pytest
 
 from paper_2408_15583_gb300.serve import (RcsRequest, RcsResult, Scheduler, estimate_bytes,
                                           geometry_bytes, latency_stats, validate)
