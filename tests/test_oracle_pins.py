@@ -686,6 +686,49 @@ def test_bistatic_psi_toward_the_transmitter_is_the_monostatic_psi():
 
 
 # ----------------------------------------------------------------------------
+# PO at every bounce (the variant of Eq. 14 that sums the field of every hit)
+# ----------------------------------------------------------------------------
+
+def test_every_bounce_field_on_the_dihedral(dihedral_geom):
+    # phi = 0: broadside to the plate x = 0 and edge-on to y = 0, so no ray
+    # hits twice and PO at every bounce is the last-hit field exactly.
+    # phi = 45: the last-hit field is the double bounce (pinned above), and the
+    # every-bounce field adds each double-bounce ray's first hit: the two
+    # a x a plates seen 45 deg off their normals.  Each contributes
+    # cos(45) a |integral_0^l exp(j q x) dx|, q = 2 k cos(45), in phase with
+    # the other for both polarisations (the PO currents 2 n x H of the two
+    # plates project onto e_V and e_H with the same sign).  At q a / 2 =
+    # 7.5 pi the integral is at a sidelobe peak, 2 / q; the illuminated
+    # length l is a to within one projected screen cell (pitch / cos 45), so
+    # |sin(q l / 2)| >= cos(q pitch / (2 cos 45)), and the height is a to
+    # within a pitch at each end.
+    sc, S, gv = dihedral_geom
+    eps = oracle.default_eps(gv)
+    a = 0.5
+    q = 15 * math.pi / a
+    f = q / math.sqrt(2) * C0 / (2 * math.pi)
+    for phi in (0.0, 45.0):
+        sw = scenes._sweep_over(sc, [90.0], [phi], 96, [f], 2)
+        v = oracle.sweep_views(sw)[0]
+        Ee = oracle.po_field_every_bounce(v, S, oracle.gfb(sc, v), 2, eps, eps, [f])
+        res = oracle.rcs_sweep(sc, sw, S, eps, eps)
+        El = res.E[0]
+        if phi == 0.0:
+            assert res.traces[0].M.max() == 1
+            assert np.array_equal(Ee, El)
+            continue
+        assert int((res.traces[0].M == 2).sum()) > 4000
+        e = np.stack([v.u, v.v])                    # e_V, e_H
+        d = np.abs(np.einsum("ftc,tc->ft", Ee - El, e)[0])
+        peak = 2 * math.cos(math.pi / 4) * a * 2 / q
+        lo = math.cos(q * v.pitch / (2 * math.cos(math.pi / 4))) * (1 - 2 * v.pitch / a)
+        hi = 1 + 2 * v.pitch / a
+        assert np.all(d > lo * peak) and np.all(d < hi * peak), (d / peak, lo, hi)
+        # and the first hits are a sidelobe: about 28 dB below the double bounce
+        assert np.all(d < 0.06 * np.abs(np.einsum("ftc,tc->ft", El, e)[0]))
+
+
+# ----------------------------------------------------------------------------
 # Canny edge mode of the fusion (edge_mode 1)
 # ----------------------------------------------------------------------------
 
