@@ -44,6 +44,19 @@ struct vray {
   float ix, iy, iz, nx, ny, nz;
 };
 
+// A direction component for the slab form.  An exact zero (a ray
+// perpendicular to a view axis, e.g. d = (0, 0, -1) against a top view)
+// would give a reciprocal of +-inf, and the slab ends lo * inf - a * inf
+// would be NaN or -inf: fminf/fmaxf drop the NaN and keep -inf, which
+// rejects a box that holds the ray.  A magnitude of at least 1e-20 keeps
+// every end finite (|a| * 1e20 is far below FLT_MAX) with the sign of
+// (lo - a), so a box holding the ray spans beyond any parameter the walk
+// uses; only a ray within 1e-17 m of a face sees a shorter slab, far
+// inside the boxes' padding.
+__device__ __forceinline__ float slab_dir(float x) {
+  return fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x;
+}
+
 struct qstate {
   float tb;
   uint32_t ib;
@@ -116,7 +129,7 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
   float t0 = tmin - 1e-3f * cell, t1 = INFINITY;
   float inv[3];
   for (int k = 0; k < 3; ++k) {
-    inv[k] = 1.0f / dd[k];
+    inv[k] = 1.0f / slab_dir(dd[k]);  // finite; exact zeros take the branch below
     float a = (0.0f - oo[k]) * inv[k], b = (size - oo[k]) * inv[k];
     if (dd[k] == 0.0f) {
       if (oo[k] < 0.0f || oo[k] > size) return m;
@@ -216,9 +229,9 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
     // (the FMA slab form moves a face by ~1e-7 |origin|, far inside the
     // boxes' padding of 1e-5 of the view's span)
     vray r;
-    r.ix = 1.0f / (d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2]);
-    r.iy = 1.0f / (d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2]);
-    r.iz = 1.0f / (d.x * V.d[0] + d.y * V.d[1] + d.z * V.d[2]);
+    r.ix = 1.0f / slab_dir(d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2]);
+    r.iy = 1.0f / slab_dir(d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2]);
+    r.iz = 1.0f / slab_dir(d.x * V.d[0] + d.y * V.d[1] + d.z * V.d[2]);
     r.nx = -(q.x * V.u[0] + q.y * V.u[1] + q.z * V.u[2]) * r.ix;
     r.ny = -(q.x * V.v[0] + q.y * V.v[1] + q.z * V.v[2]) * r.iy;
     r.nz = -(q.x * V.d[0] + q.y * V.d[1] + q.z * V.d[2]) * r.iz;

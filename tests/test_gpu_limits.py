@@ -1,0 +1,207 @@
+"""Parity at the limits the C ABI declares, through the whole path.
+
+* PE_MAX_VIEWS: a geometry fused from 16 views, splats bit-exact.
+* Deep bounces: a 30 degree wedge (two plates hinged along the y-axis), where
+  rays from above reflect back and forth up to six times; traced with
+  max_bounces 8 on screens that are not a multiple of the 8 x 4 ray tiles,
+  hit ids, bounce counts and Psi bit-exact, and traced with max_bounces 4
+  (every deeper ray cut at its fourth hit).
+* Frequencies and groups beyond one PO launch: 600 frequencies (launches of
+  256, 256 and 88) over 70 receiver groups (launches of 64 and 6), and a
+  sweep of 4100 frequencies, more than the library stages at once.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import scenes  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _mods():
+    from paper_2408_15583_gb300 import api, pipeline
+    return api, pipeline
+
+
+def _oracle_view(v):
+    return oracle.View(o=np.array(v.o[:], np.float64), u=np.array(v.u[:], np.float64),
+                       v=np.array(v.v[:], np.float64), d=np.array(v.d[:], np.float64),
+                       pitch=float(v.pitch), W=v.W, H=v.H)
+
+
+def _cplx(E):
+    E = E.detach().cpu().numpy()
+    return E[..., 0] + 1j * E[..., 1]
+
+
+def field_err(E, Eref):
+    d = np.sqrt((np.abs(E - Eref) ** 2).sum(axis=-1))
+    r = np.sqrt((np.abs(Eref) ** 2).sum(axis=-1))
+    return d / np.maximum(r, 1e-3 * r.max())
+
+
+def wedge(n_points=3000, L=0.6, half_deg=15.0, seed=17):
+    """Two L x L plates hinged along the y-axis, each at half_deg from +z,
+    opening upward; inner normals.  One uniform point per grid cell."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    per = n_points // 2
+    n_u = int(round(math.sqrt(per)))
+    n_v = per // n_u
+    h = math.radians(half_deg)
+    ps, ns = [], []
+    for sgn in (1.0, -1.0):
+        s, y = scenes._stratified_rect(rng, n_u, n_v, L, L)
+        along = np.array([sgn * math.sin(h), 0.0, math.cos(h)])
+        ps.append(s[:, None] * along[None] + (y - L / 2)[:, None] * np.array([0.0, 1.0, 0.0]))
+        ns.append(np.tile([-sgn * math.cos(h), 0.0, math.sin(h)], (s.size, 1)))
+    return scenes._finish(np.concatenate(ps), np.concatenate(ns), "wedge", seed)
+
+
+@pytest.fixture(scope="module")
+def wedge16():
+    api, pipe = _mods()
+    sc = wedge()
+    c, r = scenes.bounding_sphere(sc.pos)
+    th = np.repeat([0.0, 10.0, 20.0, 30.0], 4)
+    ph = np.tile([0.0, 90.0, 180.0, 270.0], 4)
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    gv = pipe.views_from_angles(th, ph, c, r * 1.02, 64, 64)
+    assert len(gv) == 16
+    prm = pipe.default_params(sc.pos, gv)
+    geom, _ = pipe.build_geometry(pos, nrm, rad, gv, prm)
+    api.stream_check()
+    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
+    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
+                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
+    S = oracle.aggregate(ogf, fp, "fp32")
+    return dict(sc=sc, c=c, r=r, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, S=S,
+                ogf=ogf, fp=fp)
+
+
+def test_sixteen_view_fusion_bitexact(wedge16):
+    d = wedge16
+    cr, nf = d["geom"].planes()
+    cr = cr.cpu().numpy()
+    nf = nf.cpu().numpy()
+    ids = np.flatnonzero(cr[:, 3] > 0)
+    S = d["S"]
+    assert S.ns > 2000
+    assert np.array_equal(ids, S.id)
+    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
+    assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
+    assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
+    assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
+    # views 9-16 change the fused set (they are not ignored)
+    S8 = oracle.aggregate(d["ogf"][:8], d["fp"], "fp32")
+    assert S8.ns != S.ns or not np.array_equal(S8.id, S.id)
+
+
+@pytest.mark.parametrize("mb", [8, 4])
+def test_wedge_deep_bounces_bitexact(wedge16, mb):
+    api, pipe = _mods()
+    d = wedge16
+    sc = d["sc"]
+    W, H = 42, 38
+    views = pipe.views_from_angles([0.0, 5.0, 8.0], [0.0, 90.0, 200.0], d["c"], d["r"] * 1.02,
+                                   W, H)
+    prm = d["prm"]
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, prm)
+    api.stream_check()
+    per = W * H
+    deep = 0
+    for a, v in enumerate(views):
+        ov = _oracle_view(v)
+        tr = oracle.trace(ov, d["S"], mb, float(prm.eps), float(prm.overlap_r),
+                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+        sl = slice(a * per, (a + 1) * per)
+        assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), f"angle {a}"
+        ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
+        ids[ids == 0xFFFFFFFF] = -1
+        assert np.array_equal(ids.T, tr.ids), f"angle {a}"
+        assert np.array_equal(h.psi[sl].cpu().numpy(), tr.psi)
+        live = tr.M > 0
+        for name in ("p", "n", "k", "u", "v"):
+            got = getattr(h, name)[sl].cpu().numpy().astype(np.float64)
+            assert np.array_equal(got[live], getattr(tr, name)[live]), name
+        assert np.allclose(h.path[sl].cpu().numpy()[live], tr.path[live], rtol=1e-13, atol=1e-13)
+        deep += int((tr.M >= 5).sum()) if mb == 8 else int((tr.M == mb).sum())
+    assert deep > 300            # the case reaches the deep bounces (or the cut)
+
+
+def test_wedge_sweep_beyond_the_staged_frequencies(wedge16):
+    # 4100 frequencies: wavenumbers staged in two pieces, PO in 17 launches
+    api, pipe = _mods()
+    d = wedge16
+    sc = d["sc"]
+    sw = scenes._sweep_over(sc, [0.0, 6.0], [0.0, 120.0], 32, scenes.freq_grid(2e9, 4e9, 4100), 8)
+    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), d["pos"], d["nrm"], d["rad"],
+                           d["geom"], d["prm"])
+    api.stream_check()
+    eps = float(d["prm"].eps)
+    ref = oracle.rcs_sweep(sc, sw, d["S"], eps, eps, mode="fp32")
+    assert int(max((t.M >= 5).sum() for t in ref.traces)) > 100
+    assert field_err(_cplx(E), ref.E).max() < 1e-3
+    s = sig.cpu().numpy()
+    for p in (0, 1):
+        sd, so = oracle.db(s[..., p, p]), oracle.db(ref.sigma[..., p, p])
+        keep = so >= so.max() - 40.0
+        assert np.abs(sd - so)[keep].max() < 0.1
+
+
+def test_po_field_beyond_one_launch():
+    # a plate tiled by 20 x 15 projected screen cells, replicated for 70
+    # receiver groups with their own directions; 600 frequencies 2-18 GHz
+    api, _ = _mods()
+    th = math.radians(20.0)
+    w = np.array([math.sin(th), 0, math.cos(th)])
+    u = np.array([math.cos(th), 0, -math.sin(th)])
+    v = np.array([0, 1.0, 0])
+    dd = -w
+    nu, nv = 20, 15
+    us = (0.1 / nu * math.cos(th)) * u
+    vs = (0.075 / nv) * v
+    up = us - dd * (us[2] / dd[2])
+    vp = vs - dd * (vs[2] / dd[2])
+    ii, jj = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    ps = (ii.ravel()[:, None] - (nu - 1) / 2) * up[None] + \
+        (jj.ravel()[:, None] - (nv - 1) / 2) * vp[None]
+    f32 = lambda x: np.asarray(x, np.float32).astype(np.float64)
+    ps = f32(ps + np.array([0.02, -0.01, 0.03]))
+    n = ps.shape[0]
+    tr = oracle.Trace(M=np.ones(n, np.int32), ids=np.zeros((n, 1), np.int64), p=ps,
+                      n=np.tile([0, 0, 1.0], (n, 1)), k=np.tile(f32(dd), (n, 1)),
+                      u=np.tile(f32(us), (n, 1)), v=np.tile(f32(vs), (n, 1)),
+                      path=ps @ f32(dd), psi=np.ones(n, np.uint8))
+    G = 70
+    rng = np.random.default_rng(5)
+    t = np.radians(rng.uniform(0.0, 60.0, G))
+    p = np.radians(rng.uniform(0.0, 360.0, G))
+    ks = f32(np.stack([np.sin(t) * np.cos(p), np.sin(t) * np.sin(p), np.cos(t)], 1))
+    freqs = scenes.freq_grid(2e9, 18e9, 600)
+    Eo = oracle.po_field(tr, freqs, ks)                          # [G][F][pol][3]
+    h = api.alloc_hits(n * G, 1, DEV, ids=False)
+    for name in ("p", "n", "k", "u", "v"):
+        getattr(h, name).copy_(torch.from_numpy(np.tile(getattr(tr, name), (G, 1)).astype(np.float32)))
+    h.path.copy_(torch.from_numpy(np.tile(tr.path, G)))
+    h.M.copy_(torch.from_numpy(np.tile(tr.M, G)))
+    h.psi.copy_(torch.from_numpy(np.tile(tr.psi, G)))
+    E = _cplx(api.po_field(h, G, n, ks, freqs))
+    api.stream_check()
+    assert E.shape == Eo.shape == (G, 600, 2, 3)
+    assert field_err(E, Eo).max() < 1e-3
