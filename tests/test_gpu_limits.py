@@ -3,9 +3,12 @@
 * PE_MAX_VIEWS: a geometry fused from 16 views, splats bit-exact.
 * Deep bounces: a 30 degree wedge (two plates hinged along the y-axis), where
   rays from above reflect back and forth up to six times; traced with
-  max_bounces 8 on screens that are not a multiple of the 8 x 4 ray tiles,
-  hit ids, bounce counts and Psi bit-exact, and traced with max_bounces 4
-  (every deeper ray cut at its fourth hit).
+  max_bounces 8 and 64 (the maximum) on screens that are not a multiple of
+  the 8 x 4 ray tiles, hit ids, bounce counts and Psi bit-exact, with
+  max_bounces 4 (every deeper ray cut at its fourth hit), with the first
+  bounce taken from the geometry, and on one-row, one-column and one-ray
+  screens.  The screens look straight down (ray directions with exact zero
+  components) or nearly so; bistatic receivers along the coordinate axes.
 * Frequencies and groups beyond one PO launch: 600 frequencies (launches of
   256, 256 and 88) over 70 receiver groups (launches of 64 and 6), and a
   sweep of 4100 frequencies, more than the library stages at once.
@@ -111,24 +114,25 @@ def test_sixteen_view_fusion_bitexact(wedge16):
     assert S8.ns != S.ns or not np.array_equal(S8.id, S.id)
 
 
-@pytest.mark.parametrize("mb", [8, 4])
-def test_wedge_deep_bounces_bitexact(wedge16, mb):
+def _trace_vs_oracle(d, views, mb, geom_first=False):
+    """Trace `views` through the ABI and the oracle; every record bit-exact.
+    Returns the oracle traces."""
     api, pipe = _mods()
-    d = wedge16
     sc = d["sc"]
-    W, H = 42, 38
-    views = pipe.views_from_angles([0.0, 5.0, 8.0], [0.0, 90.0, 200.0], d["c"], d["r"] * 1.02,
-                                   W, H)
-    prm = d["prm"]
-    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    W, H = views[0].W, views[0].H
+    prm = pipe.default_params(sc.pos, d["gv"], first_bounce_from_geom=geom_first)
+    keys = None
+    if not geom_first:
+        keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
     h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, prm)
     api.stream_check()
     per = W * H
-    deep = 0
+    trs = []
     for a, v in enumerate(views):
         ov = _oracle_view(v)
-        tr = oracle.trace(ov, d["S"], mb, float(prm.eps), float(prm.overlap_r),
-                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+        first = None if geom_first else oracle.gfb(sc, ov, "fp32")
+        tr = oracle.trace(ov, d["S"], mb, float(prm.eps), float(prm.overlap_r), first=first,
+                          mode="fp32")
         sl = slice(a * per, (a + 1) * per)
         assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), f"angle {a}"
         ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
@@ -140,8 +144,64 @@ def test_wedge_deep_bounces_bitexact(wedge16, mb):
             got = getattr(h, name)[sl].cpu().numpy().astype(np.float64)
             assert np.array_equal(got[live], getattr(tr, name)[live]), name
         assert np.allclose(h.path[sl].cpu().numpy()[live], tr.path[live], rtol=1e-13, atol=1e-13)
-        deep += int((tr.M >= 5).sum()) if mb == 8 else int((tr.M == mb).sum())
+        trs.append(tr)
+    return trs
+
+
+@pytest.mark.parametrize("mb,geom_first", [(8, False), (4, False), (64, False), (8, True)])
+def test_wedge_deep_bounces_bitexact(wedge16, mb, geom_first):
+    # screens from straight above (theta = 0: d = (0, 0, -1), whose
+    # reflections keep d_y = 0 exactly) and slightly off it; 42 x 38 rays
+    api, pipe = _mods()
+    d = wedge16
+    views = pipe.views_from_angles([0.0, 5.0, 8.0], [0.0, 90.0, 200.0], d["c"], d["r"] * 1.02,
+                                   42, 38)
+    trs = _trace_vs_oracle(d, views, mb, geom_first)
+    M = np.concatenate([t.M for t in trs])
+    deep = int((M >= 5).sum()) if mb >= 5 else int((M == mb).sum())
     assert deep > 300            # the case reaches the deep bounces (or the cut)
+    assert M.max() < min(mb, 8) + 1
+
+
+@pytest.mark.parametrize("W,H", [(1, 9), (13, 1), (1, 1)])
+def test_wedge_thin_screens_bitexact(wedge16, W, H):
+    # one-row, one-column and one-ray screens (a single partial 8 x 4 tile);
+    # the pitch is fixed by W, so the 1-column screen is a column of wide
+    # cells down the middle of the wedge
+    api, pipe = _mods()
+    d = wedge16
+    views = pipe.views_from_angles([0.0, 3.0], [0.0, 45.0], d["c"], d["r"] * 1.02, W, H)
+    trs = _trace_vs_oracle(d, views, 8)
+    assert sum(int((t.M > 0).sum()) for t in trs) > 0
+
+
+def test_wedge_bistatic_axis_receivers(wedge16):
+    # receivers along the coordinate axes (shadow rays with two zero
+    # components) and the transmitter's own direction; inside the wedge the
+    # receivers along x are blocked by the plates
+    api, pipe = _mods()
+    d = wedge16
+    sc = d["sc"]
+    views = pipe.views_from_angles([0.0, 5.0], [0.0, 90.0], d["c"], d["r"] * 1.02, 40, 40)
+    mb = 8
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, d["prm"], ids=False)
+    freqs = scenes.freq_grid(2.5e9, 3.5e9, 3)
+    axes = [[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [-1.0, 0.0, 0.0], [0.0, -1.0, 0.0]]
+    obs = np.asarray([[list(-np.asarray(v.d[:], np.float64))] + axes for v in views], np.float32)
+    eps = float(d["prm"].eps)
+    E = _cplx(api.po_field_bistatic(h, 2, 40 * 40, obs, d["geom"], eps, freqs))
+    api.stream_check()
+    blocked = 0
+    for a, v in enumerate(views):
+        ov = _oracle_view(v)
+        tr = oracle.trace(ov, d["S"], mb, eps, float(d["prm"].overlap_r),
+                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+        o64 = obs[a].astype(np.float64)
+        Eo = oracle.po_field_bistatic(tr, d["S"], freqs, o64, eps)
+        blocked += int((oracle.shadow_dirs(tr, d["S"], o64, eps) == 0)[:, tr.M > 0].sum())
+        assert field_err(E[a], Eo).max() < 1e-3, f"angle {a}"
+    assert blocked > 100
 
 
 def test_wedge_sweep_beyond_the_staged_frequencies(wedge16):
