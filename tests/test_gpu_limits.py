@@ -265,3 +265,37 @@ def test_po_field_beyond_one_launch():
     api.stream_check()
     assert E.shape == Eo.shape == (G, 600, 2, 3)
     assert field_err(E, Eo).max() < 1e-3
+
+
+@pytest.mark.parametrize("G", [1, 7, 64])
+def test_small_fusion_grids_bitexact(G):
+    # fuse_grid from 1 (every kept pixel in one voxel: a single splat at the
+    # target's centroid) to a coarse 64^3; splats and a 2-bounce trace
+    # through them bit-exact
+    api, pipe = _mods()
+    sc = scenes.dihedral(2000, seed=41)
+    vd = scenes.aggregation_views(sc, 48, 48)
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    gv = pipe.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, vd.W, vd.H)
+    prm = pipe.default_params(sc.pos, gv, G=G)
+    geom, _ = pipe.build_geometry(pos, nrm, rad, gv, prm)
+    api.stream_check()
+    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
+    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
+                           inv_vox=float(prm.inv_voxel), G=G)
+    S = oracle.aggregate(ogf, fp, "fp32")
+    cr, nf = geom.planes()
+    cr = cr.cpu().numpy()
+    nf = nf.cpu().numpy()
+    ids = np.flatnonzero(cr[:, 3] > 0)
+    assert S.ns >= 1 and (G > 1 or S.ns == 1)
+    assert np.array_equal(ids, S.id)
+    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
+    assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
+    assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
+    assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
+    c, r = scenes.bounding_sphere(sc.pos)
+    views = pipe.views_from_angles([90.0, 70.0], [45.0, 20.0], c, r * 1.02, 32, 32)
+    d = dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, geom=geom, S=S)
+    trs = _trace_vs_oracle(d, views, 2)
+    assert sum(int((t.M > 0).sum()) for t in trs) > 100

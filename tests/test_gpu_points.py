@@ -56,12 +56,28 @@ def _clouds():
 @pytest.mark.parametrize("name", list(_clouds().keys()))
 def test_radius_bitexact_and_normals_vs_oracle(name):
     pos, ref = _clouds()[name]
-    k_r, k_n = 8, 16
+    _check(pos, ref, 8, 16, name != "line")
+
+
+@pytest.mark.parametrize("k_r,k_n", [(31, 32), (1, 3), (31, 3), (1, 32)])
+@pytest.mark.parametrize("cloud", ["octar", "uniform", "exactly_k"])
+def test_neighbour_count_limits(k_r, k_n, cloud):
+    # the smallest and largest neighbour counts the ABI accepts, and a cloud
+    # of exactly max(k_r + 1, k_n) points (every list is the whole cloud)
+    rng = np.random.default_rng(k_r * 100 + k_n)
+    if cloud == "exactly_k":
+        pos, ref = rng.random((max(k_r + 1, k_n), 3)).astype(np.float32), None
+    else:
+        pos, ref = _clouds()[cloud]
+    _check(pos, ref, k_r, k_n, cloud != "exactly_k" and k_n > 3)
+
+
+def _check(pos, ref, k_r, k_n, most_defined):
     r, n = _gpu(pos, k_r, k_n, ref)
     ro, no, w, _ = oracle.point_attributes(pos, k_r, k_n, ref=ref)
     assert np.array_equal(r, ro), f"{np.flatnonzero(r != ro)[:10]}"
     good = (w[:, 1] - w[:, 0]) > 0.1 * np.maximum(w[:, 1], 1e-300)
-    if name != "line":
+    if most_defined:
         assert good.mean() > 0.5
     # angle from atan2(|a x b|, |a . b|): acos of a dot product near 1 would
     # turn the FP32 rounding of the output into ~1e-4 rad
