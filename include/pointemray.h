@@ -41,7 +41,7 @@ extern "C" {
 #define PE_ABI_VERSION 1
 #define PE_MAX_VIEWS 16       /* views per aggregated geometry            */
 #define PE_MAX_BATCH 64       /* views (angles) per pe_build_gfb call      */
-#define PE_MAX_CAND 32        /* Eq. 23 overlap candidates kept per query  */
+#define PE_MAX_CAND 64        /* Eq. 23 overlap candidates kept per query  */
 
 typedef enum {
   PE_OK = 0,
@@ -165,7 +165,8 @@ typedef struct {
  * (float bits of the depth << 32 | point index; all ones = no candidate).
  * pe_build_gfb's tube mode is the unbounded heap (K >= every candidate
  * count gives the same keys).  pos_dev FP32 [n][3]; keys_dev [n_views][H][W]
- * uint64 (caller-allocated); 1 <= K <= 64; n_views * W * H < 2^24; ws of
+ * uint64 (caller-allocated); all views of one W x H; 1 <= K <= 64;
+ * n_views * W * H < 2^24; ws of
  * pe_build_gfb_topk_workspace() bytes (0: the candidate list would exceed
  * 2^32 entries, PE_EUNSUPPORTED). */
 size_t pe_build_gfb_topk_workspace(int32_t n_views, const pe_view *views, int64_t n_points,
@@ -242,7 +243,9 @@ size_t pe_build_gfb_workspace(int32_t n_views, const pe_view *views);
  *   gfb_hit_dev uint32 [pix] point index or 0xFFFFFFFF;
  *   gfb_mask_dev uint8 [pix] 1 on a hit;
  *   keys_dev    uint64 [pix] the raw keys (UINT64_MAX on a miss).
- * Requires 1 <= n_views <= PE_MAX_BATCH, n_points < 2^32 - 1. */
+ * Requires 1 <= n_views <= PE_MAX_BATCH, all views of the call of one W x H
+ * (PE_EINVAL otherwise; views of several sizes take one call per size, and
+ * pe_aggregate_views fuses their outputs concatenated), n_points < 2^32 - 1. */
 pe_status pe_build_gfb(const pe_view *views, int32_t n_views,
                        const float *pos_dev, const float *nrm_dev,
                        const float *rad_dev, int64_t n_points, int32_t mode,

@@ -94,5 +94,17 @@ def test_argument_errors_before_any_device_work(lib):
     assert lib.pe_build_gfb(v, 1, None, None, None, 0, 0, 0.0, None, 0, None, None, None,
                             None, None) == 2
     assert lib.pe_view_from_angles(0.0, 0.0, None, 1.0, 8, 8, None) == 1
+    # the batched entry points take one screen size per call
+    mixed = api.views_to_array([api.view_from_angles(0, 0, [0, 0, 0], 1.0, 8, 8),
+                                api.view_from_angles(0, 0, [0, 0, 0], 1.0, 8, 6)])
+    assert lib.pe_build_gfb(mixed, 2, None, None, None, 0, 0, 0.0, None, 0, None, None, None,
+                            None, None) == 1
+    assert b"W x H" in lib.pe_last_error()
+    assert lib.pe_build_gfb_topk(mixed, 2, None, 0, 0.1, 4, None, 0, None, None) == 1
+    assert b"W x H" in lib.pe_last_error()
+    prm, hits = api.PeParams(), api.PeHits()
+    assert lib.pe_trace_bounces(mixed, 2, None, None, None, 1, C.byref(prm), None, 0,
+                                C.byref(hits), None, None) == 1
+    assert b"W x H" in lib.pe_last_error()
     assert lib.pe_trace_bounces(v, 1, None, None, None, 0, None, None, 0, None, None, None) == 1
     assert lib.pe_po_field(None, 1, 1, None, None, 1, None, 0, None, None) == 1

@@ -9,6 +9,8 @@
   bounce taken from the geometry, and on one-row, one-column and one-ray
   screens.  The screens look straight down (ray directions with exact zero
   components) or nearly so; bistatic receivers along the coordinate axes.
+* Fusion: grids of 1, 7 and 64 voxels per edge, and views of two screen
+  sizes in one geometry.
 * Frequencies and groups beyond one PO launch: 600 frequencies (launches of
   256, 256 and 88) over 70 receiver groups (launches of 64 and 6), and a
   sweep of 4100 frequencies, more than the library stages at once.
@@ -299,3 +301,43 @@ def test_small_fusion_grids_bitexact(G):
     d = dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, geom=geom, S=S)
     trs = _trace_vs_oracle(d, views, 2)
     assert sum(int((t.M > 0).sum()) for t in trs) > 100
+
+
+def test_fusion_of_views_of_different_sizes():
+    # the GFBs of a call share one screen size, but a geometry may fuse views
+    # of several sizes (per-view pixel offsets and pyramids): four 48 x 48
+    # views and four 64 x 40 views, built in two calls and fused in one;
+    # splats and a 3-bounce trace through them bit-exact
+    api, pipe = _mods()
+    sc = scenes.dihedral(2500, seed=43)
+    c, r = scenes.bounding_sphere(sc.pos)
+    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
+    ga = pipe.views_from_angles([60.0] * 4, [45.0, 135.0, 225.0, 315.0], c, r * 1.02, 48, 48)
+    gb = pipe.views_from_angles([120.0] * 4, [45.0, 135.0, 225.0, 315.0], c, r * 1.02, 64, 40)
+    gv = ga + gb
+    prm = pipe.default_params(sc.pos, gv)
+    fa = api.build_gfb(ga, pos, nrm, rad, 0, outputs=("nd", "mask"))
+    fb = api.build_gfb(gb, pos, nrm, rad, 0, outputs=("nd", "mask"))
+    nd = torch.cat([fa["nd"], fb["nd"]])
+    mask = torch.cat([fa["mask"], fb["mask"]])
+    geom = api.aggregate_views(gv, nd, mask, prm)
+    api.stream_check()
+    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
+    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
+                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
+    S = oracle.aggregate(ogf, fp, "fp32")
+    cr, nf = geom.planes()
+    cr = cr.cpu().numpy()
+    nf = nf.cpu().numpy()
+    assert cr.shape[0] == 4 * 48 * 48 + 4 * 64 * 40
+    ids = np.flatnonzero(cr[:, 3] > 0)
+    assert S.ns > 1000 and (S.id >= 4 * 48 * 48).any()       # splats owned by both sizes
+    assert np.array_equal(ids, S.id)
+    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
+    assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
+    assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
+    assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
+    views = pipe.views_from_angles([90.0, 75.0], [45.0, 58.0], c, r * 1.02, 36, 36)
+    d = dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, geom=geom, S=S)
+    trs = _trace_vs_oracle(d, views, 3)
+    assert sum(int((t.M >= 2).sum()) for t in trs) > 100
