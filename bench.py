@@ -318,11 +318,11 @@ MARCH_BYTES_PER_QUERY = 152
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 472.9 MB
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 472.7 MB
 # over 6,332,964 queries), valid only for the sources it was taken on (their
 # SHA-256 prefixes); scaled to a full launch by the number of queries.
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 74.7,
-                     "sources": {"include/pointemray.h": "a852df5773749e93",
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 74.6,
+                     "sources": {"include/pointemray.h": "1940109feadd0e91",
                                  "paper_2408_15583_gb300/csrc/trace.cu": "a3504acfc8ded0a6",
                                  "paper_2408_15583_gb300/csrc/pe_internal.cuh": "76d8a06e2e9d487f",
                                  "paper_2408_15583_gb300/csrc/aggregate.cu": "bf62c78936fbcb0f"}}

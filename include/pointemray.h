@@ -194,6 +194,26 @@ pe_status pe_point_attributes(const float *pos_dev, int64_t n_points, int32_t k_
                               const float *ref_nrm_dev, void *ws, size_t ws_bytes,
                               float *radius_dev, float *normal_dev, void *stream);
 
+/* Unit-throughput probe (no counterpart in the paper): launches one probe
+ * of `blocks` x 256 threads on `stream` and returns the number of operations
+ * it performs (the caller times the launch with events on that stream), or
+ * -1 with pe_last_error set on a bad argument.
+ *   kind 0  FP32 FMA: n_iter x 8 independent fmaf chains per thread (flops,
+ *           an FMA counted as 2);
+ *   kind 1  __sinf: n_iter x 8 independent chains per thread (sines; the
+ *           PO term's sine/cosine path);
+ *   kind 2  FP64 FMA: as kind 0 in double (flops);
+ *   kind 3  L2 reads: n_iter passes of 16-byte loads cached in L2 only over
+ *           the first scratch_bytes - 16 bytes (bytes read; the caller zeroes
+ *           the buffer, sizes it below the L2 and runs a warm-up launch);
+ *   kind 4  64-bit atomicMin, result unused (the splat's form): n_iter per
+ *           thread at hashed addresses of a power-of-two table in scratch
+ *           (atomics).
+ * scratch_dev: device buffer of at least 4096 bytes, 256-byte aligned, that
+ * every kind may write; blocks in [1, 2^20]; n_iter in [1, 2^24]. */
+int64_t pe_probe_units(int32_t kind, int32_t blocks, int32_t n_iter, void *scratch_dev,
+                       size_t scratch_bytes, void *stream);
+
 /* Library version of this header's ABI. */
 int pe_abi_version(void);
 

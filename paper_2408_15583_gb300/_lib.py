@@ -54,6 +54,7 @@ class PeSweep(C.Structure):
 P = C.c_void_p
 SIGNATURES = {
     "pe_abi_version": (C.c_int, []),
+    "pe_probe_units": (C.c_int64, [C.c_int32, C.c_int32, C.c_int32, P, C.c_size_t, P]),
     "pe_kernel_launches": (C.c_int64, []),
     "pe_set_kernel_events": (C.c_int32, [C.c_char_p, P, C.c_int32]),
     "pe_last_error": (C.c_char_p, []),

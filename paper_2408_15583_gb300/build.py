@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libpointemray.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "gfb.cu", "aggregate.cu", "trace.cu", "po.cu", "sweep.cu", "po_static.cu",
            "nn.cu", "nn_tc.cu", "learned_io.cu", "points.cu",
-           "gfb_topk.cu"]
+           "gfb_topk.cu", "probes.cu"]
 
 
 def nvcc() -> str:

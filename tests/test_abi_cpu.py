@@ -108,3 +108,12 @@ def test_argument_errors_before_any_device_work(lib):
     assert b"W x H" in lib.pe_last_error()
     assert lib.pe_trace_bounces(v, 1, None, None, None, 0, None, None, 0, None, None, None) == 1
     assert lib.pe_po_field(None, 1, 1, None, None, 1, None, 0, None, None) == 1
+
+
+def test_probe_arguments_rejected_before_any_device_work(lib):
+    assert lib.pe_probe_units(7, 1, 1, None, 0, None) == -1
+    assert b"kind" in lib.pe_last_error()
+    assert lib.pe_probe_units(0, 0, 1, None, 0, None) == -1
+    assert lib.pe_probe_units(0, 1, 0, None, 0, None) == -1
+    assert lib.pe_probe_units(3, 1, 1, None, 1 << 20, None) == -1
+    assert b"scratch" in lib.pe_last_error()
