@@ -37,20 +37,26 @@ _SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle_core.h")]
 C0 = 299_792_458.0
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle (gcc, -O2 -ffp-contract=off, OpenMP if present)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_SO):
-        so_t = os.path.getmtime(_SO)
-        if all(os.path.getmtime(s) <= so_t for s in _SRC):
-            return _SO
+def _compile(src_c: str, out_so: str) -> None:
+    """gcc -O2 -ffp-contract=off (no fast-math), OpenMP if present, of
+    oracle.c (which includes oracle_core.h from its own directory)."""
     base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-            "-fPIC", "-shared", _SRC[0], "-o", _SO + ".tmp", "-lm"]
+            "-fPIC", "-shared", src_c, "-o", out_so, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_SO):
+        so_t = os.path.getmtime(_SO)
+        if all(os.path.getmtime(s) <= so_t for s in _SRC):
+            return _SO
+    _compile(_SRC[0], _SO + ".tmp")
     os.replace(_SO + ".tmp", _SO)
     return _SO
 
@@ -64,26 +70,32 @@ class OrView(C.Structure):
 _lib = None
 
 
+def _bind(path: str):
+    """Load a build of the C oracle and declare its entry points."""
+    L = C.CDLL(path)
+    P = C.c_void_p
+    L.or_gfb.argtypes = [C.c_int, P, P, P, P, C.c_int64, C.c_int, C.c_double,
+                         P, C.c_int64, P, P, P]
+    L.or_aggregate.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_double, C.c_int, P,
+                               C.c_double, C.c_int, P, P, P, P, P, P]
+    L.or_aggregate.restype = C.c_int64
+    L.or_trace.argtypes = [C.c_int, P, P, C.c_int64, P, P, P, P, P, P, P,
+                           C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int,
+                           P, P, P, P, P, P, P, P, P]
+    L.or_po_field.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int, P,
+                              C.c_int, P, P]
+    L.or_knn.argtypes = [P, C.c_int64, P, C.c_int64, C.c_int, P, P]
+    L.or_shadow_dirs.argtypes = [C.c_int, P, P, P, P, C.c_int64, P, P, C.c_int64, P,
+                                 C.c_int, C.c_double, P]
+    L.or_gfb_topk.argtypes = [C.c_int, P, P, C.c_int64, C.c_double, C.c_int, P, C.c_int64,
+                              P, P]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
-        P = C.c_void_p
-        _lib.or_gfb.argtypes = [C.c_int, P, P, P, P, C.c_int64, C.c_int, C.c_double,
-                                P, C.c_int64, P, P, P]
-        _lib.or_aggregate.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_double, C.c_int, P,
-                                      C.c_double, C.c_int, P, P, P, P, P, P]
-        _lib.or_aggregate.restype = C.c_int64
-        _lib.or_trace.argtypes = [C.c_int, P, P, C.c_int64, P, P, P, P, P, P, P,
-                                  C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int,
-                                  P, P, P, P, P, P, P, P, P]
-        _lib.or_po_field.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int, P,
-                                     C.c_int, P, P]
-        _lib.or_knn.argtypes = [P, C.c_int64, P, C.c_int64, C.c_int, P, P]
-        _lib.or_shadow_dirs.argtypes = [C.c_int, P, P, P, P, C.c_int64, P, P, C.c_int64, P,
-                                        C.c_int, C.c_double, P]
-        _lib.or_gfb_topk.argtypes = [C.c_int, P, P, C.c_int64, C.c_double, C.c_int, P, C.c_int64,
-                                     P, P]
+        _lib = _bind(build())
     return _lib
 
 
