@@ -19,67 +19,125 @@ import oracle
 import scenes
 import test_oracle_pins as P
 
-# name, file, original text, planted text, pins (zero-argument callables)
+# name, file, original text, planted text, pins (callables taking the
+# dihedral geometry built by the unchanged oracle; most ignore it)
 C_MUTANTS = [
+    # PO (Eq. 5-14)
     ("PO: sinc over v' dropped", "oracle.c",
      "double amp = area * sinc(0.5 * dot3(q, up)) * sinc(0.5 * dot3(q, vp));",
      "double amp = area * sinc(0.5 * dot3(q, up));",
-     [P.test_po_parallelogram_cells_use_cross_product_area,
-      lambda: P.test_bistatic_plate_exact_integral_and_receiver_shadowing(40.0)]),
+     [lambda g: P.test_po_parallelogram_cells_use_cross_product_area(),
+      lambda g: P.test_bistatic_plate_exact_integral_and_receiver_shadowing(40.0)]),
     ("PO: cell area as |u'| |v'| instead of |u' x v'|", "oracle.c",
      "double area = sqrt(dot3(cr, cr));",
      "double area = sqrt(dot3(up, up)) * sqrt(dot3(vp, vp));",
-     [P.test_po_parallelogram_cells_use_cross_product_area]),
+     [lambda g: P.test_po_parallelogram_cells_use_cross_product_area()]),
     ("PO: phase sign", "oracle.c",
      "double cre = cos(ph), cim = -sin(ph);",
      "double cre = cos(ph), cim = sin(ph);",
-     [P.test_po_translation_phase_convention]),
+     [lambda g: P.test_po_translation_phase_convention()]),
     ("PO: V-polarisation sign", "oracle.c",
      "h[0][c] = -vl[c] / lv;",
      "h[0][c] = vl[c] / lv;",
-     [lambda: P.test_bistatic_plate_exact_integral_and_receiver_shadowing(15.0)]),
+     [lambda g: P.test_bistatic_plate_exact_integral_and_receiver_shadowing(15.0)]),
     ("PO: u' and v' projections swapped", "oracle.c",
      "nu = dot3(nl, ul) / nk, nv = dot3(nl, vl) / nk;",
      "nu = dot3(nl, vl) / nk, nv = dot3(nl, ul) / nk;",
-     [P.test_po_parallelogram_cells_use_cross_product_area,
-      lambda: P.test_po_plate_pattern_textbook(25.0)]),
+     [lambda g: P.test_po_parallelogram_cells_use_cross_product_area(),
+      lambda g: P.test_po_plate_pattern_textbook(25.0)]),
     ("PO: sign of k_s in q", "oracle.c",
      "q[c] = kw * (kl[c] - ks[c]);",
      "q[c] = kw * (kl[c] + ks[c]);",
-     [lambda: P.test_po_plate_pattern_textbook(25.0)]),
-    ("Eq. 4: reflection sign", "oracle_core.h",
-     "for (int k = 0; k < 3; ++k) out[k] = a[k] - s * n[k];",
-     "for (int k = 0; k < 3; ++k) out[k] = a[k] + s * n[k];",
-     [P.test_trihedral_axis_triple_bounce_aperture]),
+     [lambda g: P.test_po_plate_pattern_textbook(25.0)]),
+    # Alg. 1 and the finite heap
     ("Alg. 1: ties to the larger index", "oracle_core.h",
      "if (t < best) {",
      "if (t <= best) {",
-     [lambda: P.test_gfb_nearest_and_tie_break("fp32")]),
+     [lambda g: P.test_gfb_nearest_and_tie_break("fp32")]),
+    ("finite K: the farthest kept candidate", "oracle_core.h",
+     "if (ks[e] < best || (ks[e] == best && ki[e] < bi)) {",
+     "if (ks[e] > best || best == (R)INFINITY || (ks[e] == best && ki[e] < bi)) {",
+     [lambda g: P.test_alg1_finite_k_hand_case("fp32")]),
+    ("finite K: heap kept in the wrong order", "oracle_core.h",
+     "while (at > 0 && ka[at - 1] > a) {",
+     "while (at > 0 && ka[at - 1] < a) {",
+     [lambda g: P.test_alg1_finite_k_hand_case("fp32")]),
+    # Alg. 3 lines 1-2: edge rule, Canny, fusion, Eq. 22
     ("edge rule dropped", "oracle_core.h",
      "if (dt > tauL) return 1;",
      "if (dt > tauL && 0) return 1;",
-     [P.test_edge_filter_handmade]),
+     [lambda g: P.test_edge_filter_handmade()]),
+    ("Canny: no hysteresis (low threshold = high)", "oracle_core.h",
+     "const R high = ((R)8 * tau) * L, low = (R)0.5 * high;",
+     "const R high = ((R)8 * tau) * L, low = high;",
+     [lambda g: P.test_canny_weak_step_alone_and_joined_to_a_strong_one("fp32")]),
+    ("Canny: high threshold halved", "oracle_core.h",
+     "const R high = ((R)8 * tau) * L, low = (R)0.5 * high;",
+     "const R high = ((R)4 * tau) * L, low = (R)0.5 * high;",
+     [lambda g: P.test_canny_ramp_threshold_and_flat_map("fp32"),
+      lambda g: P.test_canny_weak_step_alone_and_joined_to_a_strong_one("fp32")]),
+    ("fusion: normals not turned into one hemisphere", "oracle_core.h",
+     "if (SFX(dot)(nn, E0->n) < (R)0)",
+     "if (SFX(dot)(nn, E0->n) < (R)0 && 0)",
+     [lambda g: P.test_fusion_average_over_views("fp32")]),
+    ("fusion: radius of the first contributor, not the largest", "oracle_core.h",
+     "if (r > rmax) rmax = r;",
+     "if (rmax == 0.0) rmax = r;",
+     [lambda g: P.test_fusion_owner_is_the_most_frontal_view("fp32")]),
+    ("fusion: centre divided by count + 1", "oracle_core.h",
+     "S->c[k] = (R)(sp3[k] / cnt);",
+     "S->c[k] = (R)(sp3[k] / (cnt + 1.0));",
+     [lambda g: P.test_fusion_average_over_views("fp32")]),
+    ("fusion: owner ties go to the later view", "oracle_core.h",
+     "if (sc > best) {",
+     "if (sc >= best) {",
+     [lambda g: P.test_fusion_owner_is_the_most_frontal_view("fp32")]),
     ("Eq. 22: sqrt(2) replaced by 1.5", "oracle_core.h",
      "if (s < 2.5) return (1.4142135623730951 * L) * s;",
      "if (s < 2.5) return (1.5 * L) * s;",
-     [lambda: P.test_eq22_radius_values("fp64")]),
+     [lambda g: P.test_eq22_radius_values("fp64")]),
+    # Alg. 3 lines 4-9: bounces, Eq. 23, epsilon, Psi
+    ("Eq. 4: reflection sign", "oracle_core.h",
+     "for (int k = 0; k < 3; ++k) out[k] = a[k] - s * n[k];",
+     "for (int k = 0; k < 3; ++k) out[k] = a[k] + s * n[k];",
+     [lambda g: P.test_trihedral_axis_triple_bounce_aperture()]),
+    ("tube vector u not reflected", "oracle_core.h",
+     "SFX(reflect)(u, nn, ru);",
+     "for (int k = 0; k < 3; ++k) ru[k] = u[k];",
+     [lambda g: P.test_trihedral_axis_triple_bounce_aperture(),
+      lambda g: P.test_rcs_dihedral_realised_aperture(g)]),
+    ("path: later segments counted half", "oracle_core.h",
+     "path = path + sqrt((dx * dx + dy * dy) + dz * dz);",
+     "path = path + 0.5 * sqrt((dx * dx + dy * dy) + dz * dz);",
+     [lambda g: P.test_epsilon_minimum_travel("fp32"),
+      lambda g: P.test_rcs_dihedral_realised_aperture(g)]),
+    ("Psi: shadow ray toward the transmitter's back", "oracle_core.h",
+     "R w[3] = {-V.d[0], -V.d[1], -V.d[2]};",
+     "R w[3] = {V.d[0], V.d[1], V.d[2]};",
+     [lambda g: P.test_bistatic_psi_toward_the_transmitter_is_the_monostatic_psi(),
+      lambda g: P.test_dihedral_interior_rays_bounce_twice(g)]),
     ("Eq. 23: no overlap window", "oracle_core.h",
      "R lim = tb + r_ov;",
      "R lim = tb;",
-     [lambda: P.test_eq23_overlap_select_and_blend("fp32")]),
+     [lambda g: P.test_eq23_overlap_select_and_blend("fp32")]),
     ("nearest hit replaced by the farthest", "oracle_core.h",
      "if (t < tb) {",
      "if (tb == (R)INFINITY || t > tb) {",
-     [lambda: P.test_eq23_overlap_select_and_blend("fp32"),
-      lambda: P.test_epsilon_minimum_travel("fp32")]),
+     [lambda g: P.test_eq23_overlap_select_and_blend("fp32"),
+      lambda g: P.test_epsilon_minimum_travel("fp32")]),
     ("Eq. 23: blend weight rho instead of 1 - rho", "oracle_core.h",
      "R w = (R)1 - rho;",
      "R w = rho;",
-     [lambda: P.test_eq23_overlap_select_and_blend("fp32")]),
+     [lambda g: P.test_eq23_overlap_select_and_blend("fp32")]),
     ("epsilon ignored on bounces", "oracle_core.h",
      "R E = (R)eps, RO = (R)r_ov;",
      "R E = (R)0, RO = (R)r_ov;",
-     [lambda: P.test_epsilon_minimum_travel("fp32")]),
+     [lambda g: P.test_epsilon_minimum_travel("fp32")]),
+    # surfel attributes
+    ("k-NN: squared distance without its z term", "oracle.c",
+     "float d2 = (dx * dx + dy * dy) + dz * dz;",
+     "float d2 = (dx * dx + dy * dy) + 0.0f * dz;",
+     [lambda g: P.test_knn_distances_match_an_independent_kd_tree()]),
 ]
 
 
@@ -105,29 +163,29 @@ def plant(tmp_path):
     oracle._lib = saved
 
 
-def _failing(pins):
+def _failing(pins, geom):
     caught = []
     for pin in pins:
         try:
-            pin()
+            pin(geom)
         except AssertionError:
             caught.append(pin)
     return caught
 
 
-def test_an_unchanged_copy_passes_the_pins(plant):
+def test_an_unchanged_copy_passes_the_pins(plant, dihedral_geom):
     # the mechanism itself (copy, flags, binding) changes nothing
     name, fname, old, _, _ = C_MUTANTS[0]
     plant(fname, old, old)
     pins = [p for m in C_MUTANTS for p in m[4]]
-    assert _failing(pins) == []
+    assert _failing(pins, dihedral_geom) == []
 
 
 @pytest.mark.parametrize("mutant", C_MUTANTS, ids=[m[0] for m in C_MUTANTS])
-def test_pins_catch_a_planted_mistake(mutant, plant):
+def test_pins_catch_a_planted_mistake(mutant, plant, dihedral_geom):
     name, fname, old, new, pins = mutant
     plant(fname, old, new)
-    assert _failing(pins), f"no pin caught: {name}"
+    assert _failing(pins, dihedral_geom), f"no pin caught: {name}"
 
 
 # ----------------------------------------------------------------------------
@@ -171,3 +229,48 @@ def test_every_bounce_pin_catches_a_planted_mistake(kind, dihedral_geom, monkeyp
 def test_every_bounce_variant_without_a_mistake_passes(dihedral_geom, monkeypatch):
     monkeypatch.setattr(oracle, "po_field_every_bounce", _every_bounce_variant("none"))
     P.test_every_bounce_field_on_the_dihedral(dihedral_geom)
+
+
+# ----------------------------------------------------------------------------
+# steps written in Python: sigma, the k-NN radius, the normal's orientation
+# ----------------------------------------------------------------------------
+
+def _sigma_quarter(real):
+    return lambda E, freqs_hz, u_hat, v_hat: 0.25 * real(E, freqs_hz, u_hat, v_hat)
+
+
+def _radius_over_k_plus_one(real):
+    def fn(idx, d2, self_idx, k_r):
+        return (real(idx, d2, self_idx, k_r).astype(np.float64) * k_r / (k_r + 1)).astype(np.float32)
+    return fn
+
+
+def _normals_flipped(real):
+    def fn(pos, k_r=8, k_n=16, ref=None):
+        r, n, w, rest = real(pos, k_r, k_n, ref=ref)
+        return r, -n, w, rest
+    return fn
+
+
+PY_MUTANTS = [
+    ("sigma: k^2 / (4 pi) instead of k^2 / pi", "sigma_from_field", _sigma_quarter,
+     [P.test_rcs_sphere_surfels_vs_exact_po]),
+    ("k-NN radius: mean over k_r + 1", "knn_radius", _radius_over_k_plus_one,
+     [P.test_knn_radius_and_normal_on_a_square_lattice]),
+    ("PCA normal: orientation flipped", "point_attributes", _normals_flipped,
+     [P.test_knn_radius_and_normal_on_a_square_lattice,
+      P.test_pca_normal_of_a_tilted_plane_and_duplicates]),
+]
+
+
+@pytest.mark.parametrize("mutant", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_python_steps_catch_a_planted_mistake(mutant, monkeypatch):
+    name, attr, make, pins = mutant
+    monkeypatch.setattr(oracle, attr, make(getattr(oracle, attr)))
+    caught = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught, f"no pin caught: {name}"

@@ -228,8 +228,17 @@ def test_fusion_owner_is_the_most_frontal_view(mode):
     v0 = down_view(5, 5, L)
     v1 = oracle.View(o=np.array([-3.0, 0.0, 4.0]), u=np.array([1.0, 0.0, 0.0]),
                      v=np.array([0.0, 1.0, 0.0]), d=np.array([0.6, 0.0, -0.8]), pitch=L, W=5, H=5)
+    # The radius is the larger Eq. 22 value of the two contributors,
+    # sqrt(2) L / sqrt(|n.d|) here (|n| = |d| = 1, s < 2.5): 1/sqrt(0.8) from
+    # view 0 in the first case, 1/sqrt(0.28) from view 1 in the second.  A
+    # third normal, (-1, 0, 3)/sqrt(10), bisects the two view directions:
+    # |n.d0| = |n.d1| = 3/sqrt(10), a tie that goes to the lower view.
     inner = [6, 7, 8, 11, 12, 13, 16, 17, 18]
-    for n, owner_off in (([-0.6, 0.0, 0.8], 25), ([0.6, 0.0, 0.8], 0)):
+    t = 1.0 / math.sqrt(10.0)
+    cases = (([-0.6, 0.0, 0.8], 25, 1.0 / math.sqrt(0.8)),
+             ([0.6, 0.0, 0.8], 0, 1.0 / math.sqrt(0.28)),
+             ([-t, 0.0, 3.0 * t], 0, 1.0 / math.sqrt(3.0 * t)))
+    for n, owner_off, s_max in cases:
         n = np.array(n)
         g0 = _handmade_gfb(v0, np.full(25, 5.0), np.tile(n, (25, 1)), np.ones(25))
         g1 = _handmade_gfb(v1, np.full(25, 5.0), np.tile(n, (25, 1)), np.ones(25))
@@ -237,6 +246,7 @@ def test_fusion_owner_is_the_most_frontal_view(mode):
         assert list(s.id) == [owner_off + i for i in inner]
         assert np.all(s.count == 2)
         assert np.allclose(s.n, n[None], atol=1e-7)
+        assert np.allclose(s.r, math.sqrt(2.0) * L * s_max, rtol=1e-6)
 
 
 # ----------------------------------------------------------------------------
@@ -771,3 +781,24 @@ def test_canny_step_gives_the_two_columns_beside_it(mode):
     cols = np.flatnonzero(~interior.any(axis=0)) + 1
     assert list(cols) == [9, 10]
     assert interior[:, [c - 1 for c in range(1, n - 1) if c not in (9, 10)]].all()
+
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_canny_weak_step_alone_and_joined_to_a_strong_one(mode):
+    # After the 5 x 5 binomial smoothing a depth step of height h between
+    # columns 9 and 10 reads 1/16, 5/16, 11/16, 15/16 of h on columns 8..11,
+    # so the Sobel response on both columns beside it is 4 (11 - 1) h / 16 =
+    # 2.5 h.  With tau = 3, L = 0.125: high = 8 tau L = 3, low = 1.5.
+    # h = 0.875 gives 2.1875, a weak response: alone, no edge.  Continuing a
+    # strong step (h = 2: 5) along the same columns, the hysteresis carries
+    # it: away from the junction (rows 9-14), both columns are edges in the
+    # strong half and in the weak half.
+    n = 24
+    weak = np.full((n, n), 5.0)
+    weak[:, 10:] = 5.875
+    assert _canny_keep(weak, mode)[1:-1, 1:-1].all()
+    joined = weak.copy()
+    joined[:12, 10:] = 7.0
+    edge = _canny_keep(joined, mode) == 0
+    for r in list(range(1, 9)) + list(range(15, n - 1)):
+        assert edge[r, 9] and edge[r, 10], r
