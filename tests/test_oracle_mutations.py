@@ -6,8 +6,10 @@ when the source moves), the copy is built into its own library with the
 oracle's own compiler flags, and the pins covering that step run against it:
 at least one must fail.  The planted mistakes change arithmetic only (signs,
 comparisons, dropped terms, constants), never an index or a size, so no
-mutant can read or write out of bounds.  The every-bounce composition lives
-in Python and is mutated by replacing the function.  CPU only.
+mutant can read or write out of bounds.  The every-bounce composition and
+the Python steps are mutated by replacing the function; the FP64 reference
+network (oracle/unet.py) by executing its source with one textual change.
+CPU only.
 """
 import os
 import shutil
@@ -18,6 +20,8 @@ import pytest
 import oracle
 import scenes
 import test_oracle_pins as P
+import test_unet_oracle as U
+from oracle import unet
 
 # name, file, original text, planted text, pins (callables taking the
 # dihedral geometry built by the unchanged oracle; most ignore it)
@@ -274,3 +278,73 @@ def test_python_steps_catch_a_planted_mistake(mutant, monkeypatch):
         except AssertionError:
             caught += 1
     assert caught, f"no pin caught: {name}"
+
+
+# ----------------------------------------------------------------------------
+# the FP64 reference network and its losses (oracle/unet.py)
+# ----------------------------------------------------------------------------
+
+UNET_MUTANTS = [
+    ("depth head added to nothing (no residual on the coarse depth)",
+     'out["depth"] = out["depth"] + x', 'out["depth"] = out["depth"]',
+     [U.test_depth_output_refines_the_input]),
+    ("ConvNeXt residual dropped", "    return x + y\n", "    return y\n",
+     [U.test_convnext_block_is_identity_with_zero_last_projection,
+      U.test_convnext_block_closed_form_gelu]),
+    ("ReLU instead of GELU", "y = F.gelu(conv1(", "y = F.relu(conv1(",
+     [U.test_convnext_block_closed_form_gelu]),
+    ("Eq. 19: alpha and 1 - alpha swapped",
+     "foc = torch.where(hit, -alpha * (1 - p) ** gamma * logp, -(1 - alpha) * p ** gamma * log1mp)",
+     "foc = torch.where(hit, -(1 - alpha) * (1 - p) ** gamma * logp, -alpha * p ** gamma * log1mp)",
+     [U.test_focal_loss_closed_values]),
+    ("Eq. 19: gamma - 1", "-alpha * (1 - p) ** gamma * logp", "-alpha * (1 - p) ** (gamma - 1) * logp",
+     [U.test_focal_loss_closed_values]),
+    ("Eq. 21: factors of L2 and L3 swapped",
+     "L = 1.0 * L1 + 0.5 * L2 + 1.0 * L3 + 0.5 * L4",
+     "L = 1.0 * L1 + 1.0 * L2 + 0.5 * L3 + 0.5 * L4",
+     [U.test_normal_depth_and_gradient_losses_closed_values]),
+    ("Eq. 17: absolute instead of squared difference",
+     "L1 = ((d - d_gt) ** 2)[hit].sum() / nh", "L1 = (d - d_gt).abs()[hit].sum() / nh",
+     [U.test_normal_depth_and_gradient_losses_closed_values]),
+    ("Eq. 18: no division by |n| |n_gt|",
+     "cn = _cross_norm(n, n_gt) / (torch.linalg.norm(n, dim=-1) * torch.linalg.norm(n_gt, dim=-1) + DIV_EPS)",
+     "cn = _cross_norm(n, n_gt)",
+     [U.test_normal_depth_and_gradient_losses_closed_values]),
+    ("Eq. 20: central difference without the 1/2",
+     "gu = 0.5 * (dd[:, 1:-1, 2:] - dd[:, 1:-1, :-2])", "gu = (dd[:, 1:-1, 2:] - dd[:, 1:-1, :-2])",
+     [U.test_normal_depth_and_gradient_losses_closed_values]),
+]
+
+
+def _unet_variant(old, new, monkeypatch):
+    """Execute oracle/unet.py with one textual change and route the module's
+    entry points to the changed code."""
+    with open(unet.__file__) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"mutation site not found exactly once: {old!r}"
+    ns = {"__name__": "unet_variant"}
+    exec(compile(src.replace(old, new), unet.__file__ + " (variant)", "exec"), ns)
+    for attr in ("forward", "losses", "convnext"):
+        monkeypatch.setattr(unet, attr, ns[attr])
+
+
+def _caught(pins):
+    n = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            n += 1
+    return n
+
+
+def test_unet_unchanged_variant_passes_the_pins(monkeypatch):
+    _unet_variant("    return x + y\n", "    return x + y\n", monkeypatch)
+    assert _caught([p for m in UNET_MUTANTS for p in m[3]]) == 0
+
+
+@pytest.mark.parametrize("mutant", UNET_MUTANTS, ids=[m[0] for m in UNET_MUTANTS])
+def test_unet_pins_catch_a_planted_mistake(mutant, monkeypatch):
+    name, old, new, pins = mutant
+    _unet_variant(old, new, monkeypatch)
+    assert _caught(pins), f"no pin caught: {name}"

@@ -63,6 +63,27 @@ def _maps(B=1, H=8, W=8):
     return d_gt, n_gt
 
 
+def test_convnext_block_closed_form_gelu():
+    # delta depthwise kernel, LayerNorm (gamma 1, beta 0) over the channel
+    # pair (3, 1) -> (1, -1) (up to its 1e-6 epsilon), identity projections
+    # through the first two of the 8 expansion channels: the block returns
+    # x + GELU(LN(x)) with GELU(t) = t Phi(t), i.e. (3 + Phi(1), 1 - Phi(-1))
+    c, h = 2, 8
+    P = {"b.dw.w": torch.zeros(7, 7, c, dtype=torch.float64), "b.dw.b": torch.zeros(c, dtype=torch.float64),
+         "b.ln.g": torch.ones(c, dtype=torch.float64), "b.ln.b": torch.zeros(c, dtype=torch.float64),
+         "b.pw1.w": torch.zeros(h, c, dtype=torch.float64), "b.pw1.b": torch.zeros(h, dtype=torch.float64),
+         "b.pw2.w": torch.zeros(c, h, dtype=torch.float64), "b.pw2.b": torch.zeros(c, dtype=torch.float64)}
+    P["b.dw.w"][3, 3, :] = 1.0
+    P["b.pw1.w"][0, 0] = P["b.pw1.w"][1, 1] = 1.0
+    P["b.pw2.w"][0, 0] = P["b.pw2.w"][1, 1] = 1.0
+    x = torch.empty(1, c, 5, 5, dtype=torch.float64)
+    x[:, 0], x[:, 1] = 3.0, 1.0
+    y = unet.convnext(x, P, "b")
+    phi = lambda t: 0.5 * (1.0 + math.erf(t / math.sqrt(2.0)))
+    assert torch.allclose(y[:, 0], torch.full_like(y[:, 0], 3.0 + phi(1.0)), atol=2e-6)
+    assert torch.allclose(y[:, 1], torch.full_like(y[:, 1], 1.0 - phi(-1.0)), atol=2e-6)
+
+
 def test_focal_loss_closed_values():
     # Eq. 19 with alpha = 0.5, gamma = 2 at p = 0.5: 0.5 * 0.25 * ln 2 for
     # either label
@@ -80,6 +101,14 @@ def test_focal_loss_closed_values():
     assert parts[2].item() < 1e-15
     _, parts = unet.losses(out, d_gt, n_gt, torch.zeros(1, 8, 8, dtype=torch.float64))
     assert abs(parts[2].item() - 0.5 * 20.0) < 1e-6
+    # alpha weights the hit class and 1 - alpha the empty one (Eq. 19): at
+    # p = 0.5 with alpha = 0.25, 0.25 * 0.25 ln 2 for a hit, 0.75 * 0.25 ln 2
+    # for an empty pixel
+    out["mask"][:] = 0.0
+    for m, a_m in ((1.0, 0.25), (0.0, 0.75)):
+        _, parts = unet.losses(out, d_gt, n_gt, torch.full((1, 8, 8), m, dtype=torch.float64),
+                               alpha=0.25)
+        assert abs(parts[2].item() - a_m * 0.25 * math.log(2)) < 1e-12
 
 
 def test_normal_depth_and_gradient_losses_closed_values():
@@ -93,6 +122,9 @@ def test_normal_depth_and_gradient_losses_closed_values():
     assert abs(parts[0].item() - 0.0625) < 1e-12    # Eq. 17: (0.25 - 0)^2
     assert abs(parts[1].item() - 1.0) < 1e-7        # Eq. 18 (up to the 1e-8 guard)
     assert parts[3].item() < 1e-5                   # Eq. 20: both gradients are (0,0,1)
+    # Eq. 21 with the paper's factors 1, 0.5, 1, 0.5: the mask logit 0 gives
+    # the focal value 0.5 * 0.25 ln 2 on every (hit) pixel
+    assert abs(L.item() - (0.0625 + 0.5 * 1.0 + 0.5 * 0.25 * math.log(2))) < 1e-6
     out["normal"][:, 0] = 0.0
     out["normal"][:, 2] = 3.0                       # parallel: sin = 0
     _, parts = unet.losses(out, d_gt, n_gt, m)
