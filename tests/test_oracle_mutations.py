@@ -54,6 +54,19 @@ C_MUTANTS = [
      "q[c] = kw * (kl[c] + ks[c]);",
      [lambda g: P.test_po_plate_pattern_textbook(25.0)]),
     # Alg. 1 and the finite heap
+    ("pixel rays through pixel corners, not centres", "oracle_core.h",
+     "R fi = ((R)i + (R)0.5) - (R)0.5 * (R)v->W;",
+     "R fi = (R)i - (R)0.5 * (R)v->W;",
+     [lambda g: P.test_gfb_single_disk_handmade("fp32")]),
+    ("Alg. 1 tube: score along the ray instead of Length(p - o)", "oracle_core.h",
+     "*score = SQRT(SFX(dot)(q, q));",
+     "*score = t;",
+     [lambda g: P.test_gfb_tube_mode_handmade("fp32")]),
+    ("Alg. 1 tube: candidates behind the screen kept", "oracle_core.h",
+     "if (!(t > (R)0)) return 0;\n  *score",
+     "if (0) return 0;\n  *score",
+     [lambda g: P.test_gfb_tube_mode_handmade("fp32"),
+      lambda g: P.test_alg1_large_k_equals_the_unbounded_heap()]),
     ("Alg. 1: ties to the larger index", "oracle_core.h",
      "if (t < best) {",
      "if (t <= best) {",

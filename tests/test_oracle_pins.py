@@ -48,6 +48,10 @@ def test_gfb_single_disk_handmade(mode):
     g = oracle.gfb(sc, down_view(8, 8, 0.5), mode)
     hit = g.idx >= 0
     assert hit.sum() == 12
+    # which 12: centres (i + 0.5 - 4) * 0.5 = +-0.25, +-0.75 on both axes,
+    # i, j in 2..5, except the four corners (0.75^2 + 0.75^2 > 1)
+    expect = {(i, j) for i in range(2, 6) for j in range(2, 6)} - {(2, 2), (2, 5), (5, 2), (5, 5)}
+    assert {(int(p % 8), int(p // 8)) for p in np.flatnonzero(hit)} == expect
     assert np.all(g.depth[hit] == 5.0)
     assert np.all(np.isinf(g.depth[~hit]))
     # the stored normal is turned to face the view (n . d < 0)
@@ -111,8 +115,10 @@ def test_gfb_sphere_normals_are_radial():
 def test_gfb_tube_mode_handmade(mode):
     # 4x4 pixels, pitch 0.5; P0 on the axis of pixel (0.25, 0.25) at depth 5,
     # P1 0.05 off that axis but 1 m closer: both inside delta = 0.1, P1 is
-    # nearer the tube origin => depth = |P1 - o| = sqrt(0.05^2 + 4^2).
-    sc = mk_scene([[0.25, 0.25, 0.0], [0.25, 0.30, 1.0]], [[0, 0, 1]] * 2, [0.0, 0.0])
+    # nearer the tube origin => depth = |P1 - o| = sqrt(0.05^2 + 4^2).  P2 on
+    # the same axis 1 m behind the screen (z = 6) is no candidate.
+    sc = mk_scene([[0.25, 0.25, 0.0], [0.25, 0.30, 1.0], [0.25, 0.25, 6.0]], [[0, 0, 1]] * 3,
+                  [0.0, 0.0, 0.0])
     g = oracle.gfb(sc, down_view(4, 4, 0.5), mode, tube=True, delta=0.1)
     hit = np.flatnonzero(g.idx >= 0)
     assert list(hit) == [2 * 4 + 2]
