@@ -361,3 +361,33 @@ def test_unet_pins_catch_a_planted_mistake(mutant, monkeypatch):
     name, old, new, pins = mutant
     _unet_variant(old, new, monkeypatch)
     assert _caught(pins), f"no pin caught: {name}"
+
+
+# ----------------------------------------------------------------------------
+# the view frame (oracle/__init__.py, Python)
+# ----------------------------------------------------------------------------
+
+VIEW_MUTANTS = [
+    ("u = -theta_hat", "u = [ct * cp, ct * sp, -st]", "u = [-ct * cp, -ct * sp, st]"),
+    ("screen one pitch too close", "D = float(extent) + L", "D = float(extent)"),
+    ("phi measured the other way", "w = [st * cp, st * sp, ct]", "w = [st * cp, -st * sp, ct]"),
+]
+
+
+@pytest.mark.parametrize("mutant", VIEW_MUTANTS, ids=[m[0] for m in VIEW_MUTANTS])
+def test_view_frame_pin_catches_a_planted_mistake(mutant, monkeypatch):
+    name, old, new = mutant
+    with open(oracle.__file__) as f:
+        src = f.read()
+    assert src.count(old) == 1, f"mutation site not found exactly once: {old!r}"
+    # under the oracle's own module name: dataclasses look their module up
+    ns = {"__name__": oracle.__name__, "__file__": oracle.__file__}
+    exec(compile(src.replace(old, new), oracle.__file__ + " (variant)", "exec"), ns)
+    monkeypatch.setattr(oracle, "view_from_angles", ns["view_from_angles"])
+    caught = 0
+    for mode in ("fp32", "fp64"):
+        try:
+            P.test_view_frame_is_the_spherical_basis(mode)
+        except AssertionError:
+            caught += 1
+    assert caught == 2, f"not caught in both modes: {name}"

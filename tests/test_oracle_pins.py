@@ -37,6 +37,31 @@ def mk_scene(pos, nrm, rad):
 
 
 # ----------------------------------------------------------------------------
+# a1: view frame
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", ["fp32", "fp64"])
+def test_view_frame_is_the_spherical_basis(mode):
+    # w = r_hat(theta, phi) toward the transmitter, u = theta_hat, v = phi_hat
+    # (u x v = w), rays along d = -w; pitch 2 extent / W; the screen centre
+    # one extent plus one pitch from the target's centre along w
+    tol = 1e-7 if mode == "fp32" else 1e-15
+    for th, ph, w, u, v in ((90.0, 0.0, [1, 0, 0], [0, 0, -1], [0, 1, 0]),
+                            (0.0, 0.0, [0, 0, 1], [1, 0, 0], [0, 1, 0]),
+                            (90.0, 90.0, [0, 1, 0], [0, 0, -1], [-1, 0, 0])):
+        V = oracle.view_from_angles(th, ph, [0.5, -1.0, 2.0], 1.5, 60, 40, mode)
+        assert np.allclose(-V.d, w, atol=tol) and np.allclose(V.u, u, atol=tol)
+        assert np.allclose(V.v, v, atol=tol)
+        assert abs(V.pitch - 2 * 1.5 / 60) < tol
+        assert np.allclose(V.o, np.array([0.5, -1.0, 2.0]) + (1.5 + V.pitch) * np.asarray(w, float),
+                           atol=1e-6)
+    rng = np.random.default_rng(4)
+    for th, ph in zip(rng.uniform(0, 180, 20), rng.uniform(0, 360, 20)):
+        V = oracle.view_from_angles(th, ph, [0, 0, 0], 1.0, 8, 8, mode)
+        assert np.allclose(np.cross(V.u, V.v), -V.d, atol=4 * tol)
+
+
+# ----------------------------------------------------------------------------
 # a2/a3: GFB (Alg. 1)
 # ----------------------------------------------------------------------------
 
