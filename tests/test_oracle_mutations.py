@@ -133,6 +133,15 @@ C_MUTANTS = [
      "R w[3] = {V.d[0], V.d[1], V.d[2]};",
      [lambda g: P.test_bistatic_psi_toward_the_transmitter_is_the_monostatic_psi(),
       lambda g: P.test_dihedral_interior_rays_bounce_twice(g)]),
+    ("bistatic Psi: shadow rays start at t > 0 instead of t > eps", "oracle_core.h",
+     "const R E = (R)eps;\n  for (int o = 0; o < nobs; ++o) {",
+     "const R E = (R)0;\n  for (int o = 0; o < nobs; ++o) {",
+     [lambda g: P.test_bistatic_psi_toward_the_transmitter_is_the_monostatic_psi()]),
+    ("bistatic Psi: blocked and visible swapped", "oracle_core.h",
+     "psi = SFX(any_hit)(&S, pq, w, E) ? 0 : 1;",
+     "psi = SFX(any_hit)(&S, pq, w, E) ? 1 : 0;",
+     [lambda g: P.test_bistatic_plate_exact_integral_and_receiver_shadowing(15.0),
+      lambda g: P.test_bistatic_psi_toward_the_transmitter_is_the_monostatic_psi()]),
     ("Eq. 23: no overlap window", "oracle_core.h",
      "R lim = tb + r_ov;",
      "R lim = tb;",
