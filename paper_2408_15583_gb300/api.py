@@ -60,6 +60,9 @@ def views_to_array(views: Sequence[PeView]):
 
 
 def view_from_struct(o, u, v, d, pitch, W, H) -> PeView:
+    """A pe_view for a screen given by its frame (any orthographic screen,
+    not only one from angles): centre o, unit pixel axes u and v, ray
+    direction d, pixel pitch (m) and size W x H; values rounded to FP32."""
     pv = PeView()
     for k in range(3):
         pv.o[k], pv.u[k], pv.v[k], pv.d[k] = float(o[k]), float(u[k]), float(v[k]), float(d[k])

@@ -117,3 +117,10 @@ def test_probe_arguments_rejected_before_any_device_work(lib):
     assert lib.pe_probe_units(0, 1, 0, None, 0, None) == -1
     assert lib.pe_probe_units(3, 1, 1, None, 1 << 20, None) == -1
     assert b"scratch" in lib.pe_last_error()
+
+
+def test_view_from_struct_round_trips_a_library_view(lib):
+    from paper_2408_15583_gb300 import api
+    a = api.view_from_angles(63.0, 211.0, [0.1, -0.2, 0.3], 1.7, 96, 64)
+    b = api.view_from_struct(a.o, a.u, a.v, a.d, a.pitch, a.W, a.H)
+    assert bytes(a) == bytes(b)
