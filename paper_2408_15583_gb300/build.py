@@ -2,8 +2,9 @@
 
 nvcc compiles each translation unit in parallel and links one shared library
 into ``paper_2408_15583_gb300/_build``.  Host code is compiled with
-``-ffp-contract=off`` (the FP64 view set-up must round like the reference
-arithmetic it is compared with); device code that decides hits uses explicit
+``-ffp-contract=off`` (the FP64 view set-up must round operation by
+operation, with no fused multiply-adds, like the oracle it is checked
+against); device code that decides hits uses explicit
 round-to-nearest intrinsics, so it does not depend on contraction flags.
 """
 from __future__ import annotations
