@@ -122,7 +122,12 @@ C_MUTANTS = [
      "SFX(reflect)(u, nn, ru);",
      "for (int k = 0; k < 3; ++k) ru[k] = u[k];",
      [lambda g: P.test_trihedral_axis_triple_bounce_aperture(),
-      lambda g: P.test_rcs_dihedral_realised_aperture(g)]),
+      lambda g: P.test_rcs_dihedral_realised_aperture(g),
+      lambda g: P.test_rolled_dihedral_twist_and_reciprocity()]),
+    ("tube vector v not reflected", "oracle_core.h",
+     "SFX(reflect)(v, nn, rv);",
+     "for (int k = 0; k < 3; ++k) rv[k] = v[k];",
+     [lambda g: P.test_rolled_dihedral_twist_and_reciprocity()]),
     ("path: later segments counted half", "oracle_core.h",
      "path = path + sqrt((dx * dx + dy * dy) + dz * dz);",
      "path = path + 0.5 * sqrt((dx * dx + dy * dy) + dz * dz);",

@@ -576,6 +576,38 @@ def test_rcs_sphere_surfels_vs_exact_po():
     assert np.max(np.abs(oracle.db(res.sigma[:, 0, 1, 1]) - oracle.db(ref))) < 0.15
 
 
+def _roll(scene, axis, deg):
+    a = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    R = np.eye(3) + math.sin(math.radians(deg)) * K + (1 - math.cos(math.radians(deg))) * K @ K
+    return scenes.Scene(pos=(scene.pos.astype(np.float64) @ R.T).astype(np.float32),
+                        nrm=(scene.nrm.astype(np.float64) @ R.T).astype(np.float32), rad=scene.rad)
+
+
+def test_rolled_dihedral_twist_and_reciprocity():
+    # Seen into its corner, a dihedral's double bounce acts on the (V, H)
+    # amplitudes as diag(1, -1) in the dihedral's own frame; rolled by psi
+    # about the line of sight it becomes [[cos 2psi, sin 2psi], [sin 2psi,
+    # -cos 2psi]]: co- to cross-polarised power cot^2(2 psi) (equal at 22.5
+    # deg, -4.77 dB at 30, all cross-polarised at 45) and sigma_VH = sigma_HV
+    # (monostatic reciprocity).
+    base = scenes.dihedral(6000, seed=21)
+    w = [math.cos(math.pi / 4), math.sin(math.pi / 4), 0.0]
+    for psi in (22.5, 30.0, 45.0):
+        sc = _roll(base, w, psi)
+        S, gv, _, _ = oracle.build_geometry(sc, scenes.aggregation_views(sc, 128, 128), "fp32")
+        eps = oracle.default_eps(gv)
+        sw = scenes._sweep_over(sc, [90.0], [45.0], 96, [3e9, 3.4e9], 2)
+        s = oracle.rcs_sweep(sc, sw, S, eps, eps).sigma[0]       # [F][tx][rx]
+        assert np.all(np.abs(s[:, 0, 1] - s[:, 1, 0]) < 1e-5 * s[:, 0, 1])
+        ratio = oracle.db(s[:, 0, 0]) - oracle.db(s[:, 0, 1])
+        if psi == 45.0:
+            assert np.all(ratio < -30.0), ratio
+        else:
+            expect = 20 * math.log10(1 / math.tan(math.radians(2 * psi)))
+            assert np.all(np.abs(ratio - expect) < 0.3), (psi, ratio, expect)
+
+
 def test_rcs_sphere_converges_with_sampling():
     # the surfel sphere's monostatic sigma approaches the exact PO value as
     # the points and the ray screen are refined together (1500 points on
