@@ -1,0 +1,32 @@
+"""The arithmetic behind bench.py's roofline figures, on hand numbers (CPU;
+the timed runs themselves need a GPU)."""
+import pytest
+
+pytest.importorskip("torch")
+
+import bench  # noqa: E402
+
+
+def test_march_roofline_arithmetic(monkeypatch):
+    # 1e6 queries of 152 algorithmic bytes in 2 ms: 76 GB/s; against a
+    # 7600 GB/s peak, 0.01
+    monkeypatch.setattr(bench, "hbm_peak", lambda: (7600.0, "test"))
+    r = bench.roofline_march([1.5, 2.5], 1_000_000)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["ms_per_launch"] == pytest.approx(2.0)
+    assert r["achieved"] == pytest.approx(1e6 * bench.MARCH_BYTES_PER_QUERY / 2e-3 / 1e9)
+    assert r["achieved"] == pytest.approx(76.0)
+    assert r["frac"] == pytest.approx(0.01)
+    assert r["launches_timed"] == 2
+    if r["traffic"] is not None:
+        assert r["traffic"] == pytest.approx(bench.MARCH_NCU_TRAFFIC["bytes_per_query"] * 1e6)
+    assert bench.roofline_march([], 10) is None
+
+
+def test_alu_peak_from_the_sampled_clock():
+    v, how = bench.alu_peak(2070.0)
+    assert v == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)       # 80.55 TFLOP/s
+    assert "2070" in how
+    v2, how2 = bench.alu_peak(1455.0)
+    assert v2 == pytest.approx(v * 1455.0 / 2070.0)
+    assert bench.alu_peak(None)[0] == pytest.approx(v)             # maximum clock when unsampled
