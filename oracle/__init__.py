@@ -5,7 +5,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
 (``paper_2408_15583_gb300``) never imports it and shares no code with it.
 
 What it computes (PointEMRay, arXiv 2408.15583), step by step and by brute
-force:
+force (large searches take their candidates from a uniform grid instead, with
+the same result bit for bit: ``oracle_grid.h``):
   a1  view / ray screen from (theta, phi)          Sec. III-A (uvwo frame)
   a2  PRI: nearest point per pixel ray (GFB)        Alg. 1, surfel or tube
   a3  GFB resolve (depth, oriented normal, mask)    Alg. 1 output, Eq. 16 frame
@@ -32,7 +33,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle_core.h")]
+_SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "oracle_core.h"),
+        os.path.join(_HERE, "oracle_grid.h")]
 
 C0 = 299_792_458.0
 
@@ -75,18 +77,21 @@ def _bind(path: str):
     L = C.CDLL(path)
     P = C.c_void_p
     L.or_gfb.argtypes = [C.c_int, P, P, P, P, C.c_int64, C.c_int, C.c_double,
-                         P, C.c_int64, P, P, P]
+                         P, C.c_int64, C.c_int, P, P, P]
     L.or_aggregate.argtypes = [C.c_int, C.c_int, P, P, P, P, C.c_double, C.c_int, P,
                                C.c_double, C.c_int, P, P, P, P, P, P]
     L.or_aggregate.restype = C.c_int64
     L.or_trace.argtypes = [C.c_int, P, P, C.c_int64, P, P, P, P, P, P, P,
-                           C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int,
+                           C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
                            P, P, P, P, P, P, P, P, P]
     L.or_po_field.argtypes = [C.c_int64, P, P, P, P, P, P, P, C.c_int, P,
                               C.c_int, P, P]
     L.or_knn.argtypes = [P, C.c_int64, P, C.c_int64, C.c_int, P, P]
     L.or_shadow_dirs.argtypes = [C.c_int, P, P, P, P, C.c_int64, P, P, C.c_int64, P,
-                                 C.c_int, C.c_double, P]
+                                 C.c_int, C.c_double, C.c_int, P]
+    L.or_acc_sum.argtypes = [P, C.c_int64, P]
+    L.or_set_threads.argtypes = [C.c_int]
+    L.or_set_threads.restype = C.c_int
     L.or_gfb_topk.argtypes = [C.c_int, P, P, C.c_int64, C.c_double, C.c_int, P, C.c_int64,
                               P, P]
     return L
@@ -97,6 +102,11 @@ def lib():
     if _lib is None:
         _lib = _bind(build())
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (n >= 1; 0 only queries)."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def _p(a: Optional[np.ndarray]):
@@ -150,7 +160,7 @@ def _fp(mode):
 
 
 # ----------------------------------------------------------------------------
-# a2/a3: GFB by brute force (Alg. 1)
+# a2/a3: GFB (Alg. 1)
 # ----------------------------------------------------------------------------
 
 @dataclass
@@ -174,8 +184,28 @@ class Gfb:
         return k
 
 
+# Searches over more element/ray pairs than this take their candidates from a
+# uniform grid (oracle_grid.h: the same result as brute force, bit for bit).
+GRID_ABOVE = 2_000_000
+
+
+def _use_grid(accel: str, n_elem: int, n_query: int) -> int:
+    """accel: "brute" (every element for every ray), "grid", or "auto"
+    (the grid only for large searches)."""
+    if accel == "brute":
+        return 0
+    if accel == "grid":
+        return 1
+    if accel != "auto":
+        raise ValueError(f"accel must be 'auto', 'grid' or 'brute', not {accel!r}")
+    return 1 if int(n_elem) * int(n_query) > GRID_ABOVE else 0
+
+
 def gfb(scene, view: View, mode: str = "fp32", tube: bool = False, delta: float = 0.0,
-        pix: Optional[np.ndarray] = None) -> Gfb:
+        pix: Optional[np.ndarray] = None, accel: str = "auto") -> Gfb:
+    """Alg. 1 for every pixel of `view` (or the listed ones): the nearest
+    point per pixel ray, surfel mode (disks of radius rad with normal nrm) or
+    tube mode (points within delta of the ray, scored by Length(p - o))."""
     pos = np.ascontiguousarray(scene.pos, dtype=np.float32)
     nrm = np.ascontiguousarray(scene.nrm, dtype=np.float32)
     rad = np.ascontiguousarray(scene.rad, dtype=np.float32)
@@ -186,8 +216,8 @@ def gfb(scene, view: View, mode: str = "fp32", tube: bool = False, delta: float 
     nout = np.empty((npix, 3), np.float64)
     vc = view.c()
     lib().or_gfb(_fp(mode), C.byref(vc), _p(pos), _p(nrm), _p(rad), pos.shape[0],
-                 1 if tube else 0, float(delta), _p(pixa), npix, _p(depth), _p(idx),
-                 _p(nout))
+                 1 if tube else 0, float(delta), _p(pixa), npix,
+                 _use_grid(accel, pos.shape[0], npix), _p(depth), _p(idx), _p(nout))
     return Gfb(depth, idx, nout, view, pixa)
 
 
@@ -289,7 +319,11 @@ class Trace:
 
 def trace(view: View, splats: Optional[Splats], mb: int, eps: float, r_ov: float,
           first: Optional[Gfb] = None, pix: Optional[np.ndarray] = None,
-          mode: str = "fp32", shadow: bool = True) -> Trace:
+          mode: str = "fp32", shadow: bool = True, accel: str = "auto") -> Trace:
+    """Alg. 3's bounce loop for every pixel ray of `view` (or the listed
+    ones): bounce 1 from `first` (the view's GFB) or from the splats, then
+    up to mb - 1 reflections (Eq. 4) through the splats with the Eq. 23
+    overlap rule and minimum travel eps, and Psi toward the transmitter."""
     if pix is None and first is not None:
         pix = first.pix
     nr = view.W * view.H if pix is None else len(pix)
@@ -312,7 +346,9 @@ def trace(view: View, splats: Optional[Splats], mb: int, eps: float, r_ov: float
         fn = np.ascontiguousarray(first.nrm)
     lib().or_trace(_fp(mode), C.byref(vc), _p(pixa), nr, _p(ft), _p(fi), _p(fn),
                    _p(sc), _p(sn), _p(sr), _p(sid), sid.shape[0], mb, float(eps),
-                   float(r_ov), 1 if shadow else 0, _p(M), _p(ids), *[_p(a) for a in out],
+                   float(r_ov), 1 if shadow else 0,
+                   _use_grid(accel, sid.shape[0], nr * max(1, mb)), _p(M), _p(ids),
+                   *[_p(a) for a in out],
                    _p(path), _p(psi))
     return Trace(M, ids, *out, path, psi)
 
@@ -335,7 +371,8 @@ def po_field(tr: Trace, freqs_hz, ks_dirs) -> np.ndarray:
     return E[..., 0] + 1j * E[..., 1]
 
 
-def shadow_dirs(tr: Trace, splats: Splats, dirs, eps: float, mode: str = "fp32") -> np.ndarray:
+def shadow_dirs(tr: Trace, splats: Splats, dirs, eps: float, mode: str = "fp32",
+                accel: str = "auto") -> np.ndarray:
     """Psi toward other receivers (bistatic): [nobs][nr] uint8, 1 unless a
     splat is hit from the ray's last hit point along dirs[o] (t > eps); 0 for
     rays without a hit."""
@@ -345,7 +382,8 @@ def shadow_dirs(tr: Trace, splats: Splats, dirs, eps: float, mode: str = "fp32")
     arr = [np.ascontiguousarray(a) for a in (splats.c, splats.n, splats.r, splats.id)]
     lib().or_shadow_dirs(_fp(mode), *[_p(a) for a in arr], arr[3].shape[0],
                          _p(np.ascontiguousarray(tr.p)), _p(np.ascontiguousarray(tr.M)), nr,
-                         _p(d), d.shape[0], float(eps), _p(psi))
+                         _p(d), d.shape[0], float(eps),
+                         _use_grid(accel, arr[3].shape[0], nr * d.shape[0]), _p(psi))
     return psi
 
 

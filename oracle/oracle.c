@@ -23,6 +23,8 @@ typedef struct {
   int32_t W, H;
 } or_view;
 
+#include "oracle_grid.h"
+
 #define R float
 #define SFX(x) x##_f32
 #define SQRT sqrtf
@@ -45,14 +47,29 @@ typedef struct {
 
 int or_abi_version(void) { return 1; }
 
+/* Threads the oracle's parallel loops use from now on (n >= 1), when built
+ * with OpenMP; returns the number in force (1 without OpenMP). */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 void or_gfb(int fp64, const or_view *v, const float *pos, const float *nrm,
             const float *rad, int64_t n, int mode, double delta,
-            const int64_t *pix, int64_t npix, double *depth, int64_t *idx,
+            const int64_t *pix, int64_t npix, int use_grid, double *depth, int64_t *idx,
             double *nrm_out) {
   if (fp64)
-    gfb_f64(v, pos, nrm, rad, n, mode, delta, pix, npix, depth, idx, nrm_out);
+    gfb_f64(v, pos, nrm, rad, n, mode, delta, pix, npix, use_grid, depth, idx, nrm_out);
   else
-    gfb_f32(v, pos, nrm, rad, n, mode, delta, pix, npix, depth, idx, nrm_out);
+    gfb_f32(v, pos, nrm, rad, n, mode, delta, pix, npix, use_grid, depth, idx, nrm_out);
 }
 
 void or_gfb_topk(int fp64, const or_view *v, const float *pos, int64_t n, double delta, int K,
@@ -79,24 +96,24 @@ void or_trace(int fp64, const or_view *v, const int64_t *pix, int64_t nr,
               const double *first_t, const int64_t *first_idx,
               const double *first_n, const double *sc, const double *sn,
               const double *sr, const int64_t *sid, int64_t ns, int mb, double eps,
-              double r_ov, int do_shadow, int32_t *M, int64_t *ids, double *p,
+              double r_ov, int do_shadow, int use_grid, int32_t *M, int64_t *ids, double *p,
               double *n, double *k, double *u, double *vv, double *path,
               uint8_t *psi) {
   if (fp64)
     trace_f64(v, pix, nr, first_t, first_idx, first_n, sc, sn, sr, sid, ns, mb,
-              eps, r_ov, do_shadow, M, ids, p, n, k, u, vv, path, psi);
+              eps, r_ov, do_shadow, use_grid, M, ids, p, n, k, u, vv, path, psi);
   else
     trace_f32(v, pix, nr, first_t, first_idx, first_n, sc, sn, sr, sid, ns, mb,
-              eps, r_ov, do_shadow, M, ids, p, n, k, u, vv, path, psi);
+              eps, r_ov, do_shadow, use_grid, M, ids, p, n, k, u, vv, path, psi);
 }
 
 void or_shadow_dirs(int fp64, const double *sc, const double *sn, const double *sr,
                     const int64_t *sid, int64_t ns, const double *p, const int32_t *M, int64_t nr,
-                    const double *dirs, int nobs, double eps, uint8_t *psi) {
+                    const double *dirs, int nobs, double eps, int use_grid, uint8_t *psi) {
   if (fp64)
-    shadow_dirs_f64(sc, sn, sr, sid, ns, p, M, nr, dirs, nobs, eps, psi);
+    shadow_dirs_f64(sc, sn, sr, sid, ns, p, M, nr, dirs, nobs, eps, use_grid, psi);
   else
-    shadow_dirs_f32(sc, sn, sr, sid, ns, p, M, nr, dirs, nobs, eps, psi);
+    shadow_dirs_f32(sc, sn, sr, sid, ns, p, M, nr, dirs, nobs, eps, use_grid, psi);
 }
 
 /* ---------------------------------------------------------------------------
@@ -119,7 +136,10 @@ static double dot3(const double *a, const double *b) {
  * integrating exp(-j q u) over an interval of length U (Eq. 10-11). */
 static double sinc(double x) { return x == 0.0 ? 1.0 : sin(x) / x; }
 
-/* Neumaier-compensated accumulator. */
+/* Neumaier-compensated accumulator (Neumaier 1974, the improved Kahan
+ * summation): s carries the running sum, c the rounding errors of its
+ * additions, each recovered exactly by the Fast2Sum of the larger and the
+ * smaller operand; the sum is s + c. */
 typedef struct {
   double s, c;
 } or_acc;
@@ -130,6 +150,15 @@ static void acc_add(or_acc *a, double x) {
   else
     a->c += (x - t) + a->s;
   a->s = t;
+}
+
+/* The field's accumulator over a list of terms, for its pins: out[0] = the
+ * compensated sum s + c, out[1] = s alone (the plain left-to-right sum). */
+void or_acc_sum(const double *x, int64_t n, double *out) {
+  or_acc a = {0.0, 0.0};
+  for (int64_t i = 0; i < n; ++i) acc_add(&a, x[i]);
+  out[0] = a.s + a.c;
+  out[1] = a.s;
 }
 
 /* Eq. 14 without the common factor -j eta0 k0 / (2 pi):
@@ -146,9 +175,12 @@ void or_po_field(int64_t nr, const double *p, const double *n, const double *k,
                  const double *u, const double *v, const double *path,
                  const uint8_t *use, int nf, const double *freqs, int nobs,
                  const double *ks_dirs, double *E) {
+  /* every (receiver, frequency) sample is its own sum over the rays, in ray
+   * order, so the samples can be computed in parallel */
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
   for (int o = 0; o < nobs; ++o) {
-    const double *ks = ks_dirs + 3 * o;
     for (int f = 0; f < nf; ++f) {
+      const double *ks = ks_dirs + 3 * o;
       double kw = 2.0 * OR_PI * freqs[f] / OR_C0;
       or_acc acc[2][3][2];
       memset(acc, 0, sizeof(acc));

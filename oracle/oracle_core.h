@@ -5,7 +5,8 @@
  *   R = double (FP64 physics mode).
  *
  * TEST INFRASTRUCTURE ONLY.  This code is a plain, slow, brute-force statement
- * of the method.  It is compiled with -ffp-contract=off and without fast-math
+ * of the method (the searches can take their candidates from a uniform grid
+ * instead of every element, with the same result: oracle_grid.h).  It is compiled with -ffp-contract=off and without fast-math
  * so every float expression rounds once per operation, left to right.
  *
  * Passages followed (PointEMRay, arXiv 2408.15583):
@@ -83,20 +84,62 @@ static int SFX(hit_tube)(const R *o, const R *d, const R *c, R delta, R *score) 
   return 1;
 }
 
-/* Alg. 1 (PRI) for the listed pixels of one view, by brute force over all
- * points: the nearest candidate (ties: smaller point index).  Surfel mode
- * (mode 0): each point is a disk of radius rad[i] with normal nrm[i];
- * tube mode (mode 1): a tube of radius delta around each pixel's ray.
- * Outputs: depth (t or tube score, +inf on a miss), hit index (-1 on a
- * miss) and, in surfel mode, the hit point's normal turned to face the view
- * (n . d < 0). */
+/* One candidate of Alg. 1 for the pixel ray (o, d): point s as a disk of
+ * radius rad[s] with normal nrm[s] (surfel mode 0) or as a point within a
+ * tube of radius dl around the ray (tube mode 1).  The nearest candidate is
+ * kept; equal depths go to the smaller point index. */
+static void SFX(gfb_consider)(const R *o, const R *d, const float *pos, const float *nrm,
+                              const float *rad, int mode, R dl, int64_t s, R *best,
+                              int64_t *bi) {
+  R c[3] = {(R)pos[3 * s], (R)pos[3 * s + 1], (R)pos[3 * s + 2]};
+  R t;
+  if (mode == 0) {
+    R nn[3] = {(R)nrm[3 * s], (R)nrm[3 * s + 1], (R)nrm[3 * s + 2]};
+    R x[3], e[3];
+    if (!SFX(hit_disk)(o, d, c, nn, (R)rad[s], (R)0, &t, x, e)) return;
+  } else {
+    if (!SFX(hit_tube)(o, d, c, dl, &t)) return;
+  }
+  if (t < *best || (t == *best && s < *bi)) {
+    *best = t;
+    *bi = s;
+  }
+}
+
+/* Alg. 1 (PRI) for the listed pixels of one view: the nearest candidate over
+ * all points (ties: smaller point index), by brute force, or over the points
+ * a uniform grid lists along the pixel's ray (use_grid; same result, see
+ * oracle_grid.h).  Surfel mode (mode 0): each point is a disk of radius
+ * rad[i] with normal nrm[i]; tube mode (mode 1): a tube of radius delta
+ * around each pixel's ray.  Outputs: depth (t or tube score, +inf on a miss),
+ * hit index (-1 on a miss) and, in surfel mode, the hit point's normal turned
+ * to face the view (n . d < 0). */
 static void SFX(gfb)(const or_view *vin, const float *pos, const float *nrm,
                      const float *rad, int64_t n, int mode, double delta,
-                     const int64_t *pix, int64_t npix, double *depth_out,
+                     const int64_t *pix, int64_t npix, int use_grid, double *depth_out,
                      int64_t *idx_out, double *nrm_out) {
   SFX(view) v;
   SFX(load_view)(vin, &v);
   R dl = (R)delta;
+  or_grid grid;
+  memset(&grid, 0, sizeof(grid));
+  if (use_grid) {
+    double *gc = (double *)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double *gr = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double scale = 0.0;
+    for (int64_t s = 0; s < n; ++s) {
+      for (int k = 0; k < 3; ++k) {
+        gc[3 * s + k] = (double)pos[3 * s + k];
+        if (fabs(gc[3 * s + k]) > scale) scale = fabs(gc[3 * s + k]);
+      }
+      gr[s] = mode == 0 ? (double)rad[s] : (double)dl;
+    }
+    scale += fabs(vin->o[0]) + fabs(vin->o[1]) + fabs(vin->o[2]) +
+             (double)(vin->W + vin->H) * vin->pitch;
+    or_grid_build(&grid, gc, gr, n, scale);
+    free(gc);
+    free(gr);
+  }
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t q = 0; q < npix; ++q) {
     int64_t p = pix ? pix[q] : q;
@@ -105,20 +148,18 @@ static void SFX(gfb)(const or_view *vin, const float *pos, const float *nrm,
     SFX(pixel_origin)(&v, i, j, o);
     R best = (R)INFINITY;
     int64_t bi = -1;
-    for (int64_t s = 0; s < n; ++s) {
-      R c[3] = {(R)pos[3 * s], (R)pos[3 * s + 1], (R)pos[3 * s + 2]};
-      R t;
-      if (mode == 0) {
-        R nn[3] = {(R)nrm[3 * s], (R)nrm[3 * s + 1], (R)nrm[3 * s + 2]};
-        R x[3], e[3];
-        if (!SFX(hit_disk)(o, v.d, c, nn, (R)rad[s], (R)0, &t, x, e)) continue;
-      } else {
-        if (!SFX(hit_tube)(o, v.d, c, dl, &t)) continue;
-      }
-      if (t < best) {
-        best = t;
-        bi = s;
-      }
+    if (!use_grid) {
+      for (int64_t s = 0; s < n; ++s) SFX(gfb_consider)(o, v.d, pos, nrm, rad, mode, dl, s, &best, &bi);
+    } else {
+      double od[3] = {(double)o[0], (double)o[1], (double)o[2]};
+      double dd[3] = {(double)v.d[0], (double)v.d[1], (double)v.d[2]};
+      or_walk w;
+      const int32_t *it;
+      int64_t cnt;
+      for (or_walk_begin(&w, &grid, od, dd, 0.0); or_walk_cell(&w, (double)best, &it, &cnt);
+           or_walk_step(&w))
+        for (int64_t e = 0; e < cnt; ++e)
+          SFX(gfb_consider)(o, v.d, pos, nrm, rad, mode, dl, it[e], &best, &bi);
     }
     depth_out[q] = (double)best;
     idx_out[q] = bi;
@@ -132,6 +173,7 @@ static void SFX(gfb)(const or_view *vin, const float *pos, const float *nrm,
       }
     }
   }
+  or_grid_free(&grid);
 }
 
 /* Alg. 1 with a finite heap of K points per ray tube, as written: the
@@ -486,7 +528,42 @@ typedef struct {
   const R *c, *n, *r;
   const int64_t *id;
   int64_t ns;
+  const or_grid *grid; /* NULL: every search is brute force over all splats */
 } SFX(splatset);
+
+/* First pass of the nearest-hit search: splat s against the ray; the nearest
+ * hit with t > tmin is kept (equal t: the smaller storage index, which is the
+ * smaller splat id). */
+static void SFX(first_hit)(const SFX(splatset) *S, const R *o, const R *d, R tmin, int64_t s,
+                           R *tb, int64_t *sb) {
+  R t, x[3], e[3];
+  if (!SFX(hit_disk)(o, d, S->c + 3 * s, S->n + 3 * s, S->r[s], tmin, &t, x, e)) return;
+  if (t < *tb || (t == *tb && s < *sb)) {
+    *tb = t;
+    *sb = s;
+  }
+}
+
+/* The splats the search must consider for the ray o + t d up to t_stop: all
+ * of them (brute force) or those listed in the grid cells the ray crosses
+ * before t_stop, sorted by storage index without repeats. */
+static void SFX(candidates)(const SFX(splatset) *S, const R *o, const R *d, R tmin, R t_stop,
+                            or_list *L) {
+  L->n = 0;
+  if (!S->grid) {
+    for (int64_t s = 0; s < S->ns; ++s) or_list_push(L, (int32_t)s);
+    return;
+  }
+  double od[3] = {(double)o[0], (double)o[1], (double)o[2]};
+  double dd[3] = {(double)d[0], (double)d[1], (double)d[2]};
+  or_walk w;
+  const int32_t *it;
+  int64_t cnt;
+  for (or_walk_begin(&w, S->grid, od, dd, (double)tmin - S->grid->slack);
+       or_walk_cell(&w, (double)t_stop, &it, &cnt); or_walk_step(&w))
+    for (int64_t e = 0; e < cnt; ++e) or_list_push(L, it[e]);
+  or_list_sort_unique(L);
+}
 
 /* Nearest ray-splat hit with t > tmin, then Eq. 23: among the hits whose t is
  * within r_ov of the nearest, pick the one closest (relative to its radius)
@@ -498,25 +575,32 @@ static int SFX(nearest)(const SFX(splatset) *S, const R *o, const R *d, R tmin,
                         R r_ov, R *p_out, R *n_out, int64_t *id_out) {
   R tb = (R)INFINITY;
   int64_t sb = -1;
-  for (int64_t s = 0; s < S->ns; ++s) {
-    R t, x[3], e[3];
-    if (!SFX(hit_disk)(o, d, S->c + 3 * s, S->n + 3 * s, S->r[s], tmin, &t, x, e)) continue;
-    if (t < tb) {
-      tb = t;
-      sb = s;
-    }
+  if (!S->grid) {
+    for (int64_t s = 0; s < S->ns; ++s) SFX(first_hit)(S, o, d, tmin, s, &tb, &sb);
+  } else {
+    double od[3] = {(double)o[0], (double)o[1], (double)o[2]};
+    double dd[3] = {(double)d[0], (double)d[1], (double)d[2]};
+    or_walk w;
+    const int32_t *it;
+    int64_t cnt;
+    for (or_walk_begin(&w, S->grid, od, dd, (double)tmin - S->grid->slack);
+         or_walk_cell(&w, (double)tb, &it, &cnt); or_walk_step(&w))
+      for (int64_t e = 0; e < cnt; ++e) SFX(first_hit)(S, o, d, tmin, it[e], &tb, &sb);
   }
   if (sb < 0) return 0;
   R lim = tb + r_ov;
+  or_list L = {NULL, 0, 0};
+  SFX(candidates)(S, o, d, tmin, lim, &L);
   R m[3] = {0, 0, 0};
   R best_rho = (R)INFINITY, best_t = (R)INFINITY;
   int64_t ssel = -1;
   R xsel[3] = {0, 0, 0}, nsel[3] = {0, 0, 0};
-  for (int64_t s = 0; s < S->ns; ++s) {
-    R t, x[3], e[3];
-    if (!SFX(hit_disk)(o, d, S->c + 3 * s, S->n + 3 * s, S->r[s], tmin, &t, x, e)) continue;
+  for (int64_t e = 0; e < L.n; ++e) {
+    const int64_t s = L.v[e];
+    R t, x[3], ev[3];
+    if (!SFX(hit_disk)(o, d, S->c + 3 * s, S->n + 3 * s, S->r[s], tmin, &t, x, ev)) continue;
     if (!(t <= lim)) continue;
-    R rho = SQRT(SFX(dot)(e, e)) / S->r[s];
+    R rho = SQRT(SFX(dot)(ev, ev)) / S->r[s];
     const R *ns = S->n + 3 * s;
     R nn[3] = {ns[0], ns[1], ns[2]};
     if (SFX(dot)(nn, d) > (R)0)
@@ -533,6 +617,7 @@ static int SFX(nearest)(const SFX(splatset) *S, const R *o, const R *d, R tmin,
       }
     }
   }
+  free(L.v);
   R mm = SFX(dot)(m, m);
   if (mm == (R)0) {
     for (int k = 0; k < 3; ++k) n_out[k] = nsel[k];
@@ -548,11 +633,36 @@ static int SFX(nearest)(const SFX(splatset) *S, const R *o, const R *d, R tmin,
 }
 
 static int SFX(any_hit)(const SFX(splatset) *S, const R *o, const R *d, R tmin) {
-  for (int64_t s = 0; s < S->ns; ++s) {
-    R t, x[3], e[3];
-    if (SFX(hit_disk)(o, d, S->c + 3 * s, S->n + 3 * s, S->r[s], tmin, &t, x, e)) return 1;
+  if (!S->grid) {
+    for (int64_t s = 0; s < S->ns; ++s) {
+      R t, x[3], e[3];
+      if (SFX(hit_disk)(o, d, S->c + 3 * s, S->n + 3 * s, S->r[s], tmin, &t, x, e)) return 1;
+    }
+    return 0;
   }
+  double od[3] = {(double)o[0], (double)o[1], (double)o[2]};
+  double dd[3] = {(double)d[0], (double)d[1], (double)d[2]};
+  or_walk w;
+  const int32_t *it;
+  int64_t cnt;
+  for (or_walk_begin(&w, S->grid, od, dd, (double)tmin - S->grid->slack);
+       or_walk_cell(&w, INFINITY, &it, &cnt); or_walk_step(&w))
+    for (int64_t e = 0; e < cnt; ++e) {
+      R t, x[3], ev[3];
+      const int64_t s = it[e];
+      if (SFX(hit_disk)(o, d, S->c + 3 * s, S->n + 3 * s, S->r[s], tmin, &t, x, ev)) return 1;
+    }
   return 0;
+}
+
+/* Grid over the splats (centres, radii) for searches from rays whose
+ * coordinates stay below `extra` in magnitude beyond the splats' own. */
+static void SFX(splat_grid)(or_grid *g, const double *sc, const double *sr, int64_t ns,
+                            double extra) {
+  double scale = 0.0;
+  for (int64_t s = 0; s < 3 * ns; ++s)
+    if (fabs(sc[s]) > scale && isfinite(sc[s])) scale = fabs(sc[s]);
+  or_grid_build(g, sc, sr, ns, scale + extra);
 }
 
 /* Eq. 4 (and H^r = R H^i, tube vectors likewise): a - 2 (a . n) n. */
@@ -573,7 +683,7 @@ static void SFX(trace)(const or_view *vin, const int64_t *pix, int64_t nr,
                        const double *first_t, const int64_t *first_idx,
                        const double *first_n, const double *sc, const double *sn,
                        const double *sr, const int64_t *sid, int64_t ns, int mb,
-                       double eps, double r_ov, int do_shadow, int32_t *M_out,
+                       double eps, double r_ov, int do_shadow, int use_grid, int32_t *M_out,
                        int64_t *ids_out, double *p_out, double *n_out, double *k_out,
                        double *u_out, double *v_out, double *path_out,
                        uint8_t *psi_out) {
@@ -587,7 +697,13 @@ static void SFX(trace)(const or_view *vin, const int64_t *pix, int64_t nr,
     n[s] = (R)sn[s];
   }
   for (int64_t s = 0; s < ns; ++s) r[s] = (R)sr[s];
-  SFX(splatset) S = {c, n, r, sid, ns};
+  or_grid grid;
+  memset(&grid, 0, sizeof(grid));
+  if (use_grid)
+    SFX(splat_grid)(&grid, sc, sr, ns,
+                    fabs(vin->o[0]) + fabs(vin->o[1]) + fabs(vin->o[2]) +
+                        (double)(vin->W + vin->H) * vin->pitch);
+  SFX(splatset) S = {c, n, r, sid, ns, use_grid ? &grid : NULL};
   R E = (R)eps, RO = (R)r_ov;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t q = 0; q < nr; ++q) {
@@ -674,6 +790,7 @@ static void SFX(trace)(const or_view *vin, const int64_t *pix, int64_t nr,
     }
     path_out[q] = path;
   }
+  or_grid_free(&grid);
   free(c);
   free(n);
   free(r);
@@ -687,7 +804,7 @@ static void SFX(trace)(const or_view *vin, const int64_t *pix, int64_t nr,
 static void SFX(shadow_dirs)(const double *sc, const double *sn, const double *sr,
                              const int64_t *sid, int64_t ns, const double *p, const int32_t *M,
                              int64_t nr, const double *dirs, int nobs, double eps,
-                             uint8_t *psi_out) {
+                             int use_grid, uint8_t *psi_out) {
   R *c = (R *)malloc(sizeof(R) * (size_t)(3 * ns + 1));
   R *n = (R *)malloc(sizeof(R) * (size_t)(3 * ns + 1));
   R *r = (R *)malloc(sizeof(R) * (size_t)(ns + 1));
@@ -696,7 +813,15 @@ static void SFX(shadow_dirs)(const double *sc, const double *sn, const double *s
     n[s] = (R)sn[s];
   }
   for (int64_t s = 0; s < ns; ++s) r[s] = (R)sr[s];
-  SFX(splatset) S = {c, n, r, sid, ns};
+  or_grid grid;
+  memset(&grid, 0, sizeof(grid));
+  if (use_grid) {
+    double extra = 0.0;
+    for (int64_t q = 0; q < 3 * nr; ++q)
+      if (fabs(p[q]) > extra && isfinite(p[q])) extra = fabs(p[q]);
+    SFX(splat_grid)(&grid, sc, sr, ns, extra);
+  }
+  SFX(splatset) S = {c, n, r, sid, ns, use_grid ? &grid : NULL};
   const R E = (R)eps;
   for (int o = 0; o < nobs; ++o) {
     const R w[3] = {(R)dirs[3 * o], (R)dirs[3 * o + 1], (R)dirs[3 * o + 2]};
@@ -710,6 +835,7 @@ static void SFX(shadow_dirs)(const double *sc, const double *sn, const double *s
       psi_out[(int64_t)o * nr + q] = psi;
     }
   }
+  or_grid_free(&grid);
   free(c);
   free(n);
   free(r);

@@ -19,6 +19,7 @@ import pytest
 
 import oracle
 import scenes
+import test_oracle_grid as G
 import test_oracle_pins as P
 import test_unet_oracle as U
 from oracle import unet
@@ -68,8 +69,8 @@ C_MUTANTS = [
      [lambda g: P.test_gfb_tube_mode_handmade("fp32"),
       lambda g: P.test_alg1_large_k_equals_the_unbounded_heap()]),
     ("Alg. 1: ties to the larger index", "oracle_core.h",
-     "if (t < best) {",
-     "if (t <= best) {",
+     "if (t < *best || (t == *best && s < *bi)) {",
+     "if (t < *best || (t == *best && s > *bi)) {",
      [lambda g: P.test_gfb_nearest_and_tie_break("fp32")]),
     ("finite K: the farthest kept candidate", "oracle_core.h",
      "if (ks[e] < best || (ks[e] == best && ki[e] < bi)) {",
@@ -152,8 +153,8 @@ C_MUTANTS = [
      "R lim = tb;",
      [lambda g: P.test_eq23_overlap_select_and_blend("fp32")]),
     ("nearest hit replaced by the farthest", "oracle_core.h",
-     "if (t < tb) {",
-     "if (tb == (R)INFINITY || t > tb) {",
+     "if (t < *tb || (t == *tb && s < *sb)) {",
+     "if (*tb == (R)INFINITY || t > *tb) {",
      [lambda g: P.test_eq23_overlap_select_and_blend("fp32"),
       lambda g: P.test_epsilon_minimum_travel("fp32")]),
     ("Eq. 23: blend weight rho instead of 1 - rho", "oracle_core.h",
@@ -164,6 +165,45 @@ C_MUTANTS = [
      "R E = (R)eps, RO = (R)r_ov;",
      "R E = (R)0, RO = (R)r_ov;",
      [lambda g: P.test_epsilon_minimum_travel("fp32")]),
+    # the field's compensated sum (Neumaier)
+    ("Neumaier: correction of the first branch with its sign flipped", "oracle.c",
+     "a->c += (a->s - t) + x;",
+     "a->c += (t - a->s) + x;",
+     [lambda g: P.test_neumaier_sum_against_exact_rational_sums()]),
+    ("Neumaier: no branch for a term larger than the sum (Kahan's form)", "oracle.c",
+     "if (fabs(a->s) >= fabs(x))",
+     "if (1)",
+     [lambda g: P.test_neumaier_sum_against_exact_rational_sums()]),
+    ("Neumaier: the two branches swapped", "oracle.c",
+     "if (fabs(a->s) >= fabs(x))",
+     "if (fabs(a->s) < fabs(x))",
+     [lambda g: P.test_neumaier_sum_against_exact_rational_sums()]),
+    ("field: the compensation term dropped", "oracle.c",
+     "acc[pol][c][ri].s + acc[pol][c][ri].c;",
+     "acc[pol][c][ri].s;",
+     [lambda g: P.test_po_field_keeps_a_term_below_the_running_sums_ulp()]),
+    # the uniform grid of the large searches (must equal brute force)
+    ("grid: elements listed only in their centre's cell", "oracle_grid.h",
+     "double ri = fabs(r[i]) + pad;",
+     "double ri = pad;",
+     [lambda g: G.grid_equals_brute("dihedral"), lambda g: G.grid_equals_brute("octar")]),
+    ("grid: first boundary of a backward walk one cell off", "oracle_grid.h",
+     "w->tmax[k] = (g->lo[k] + i * g->cell - o[k]) / d[k];",
+     "w->tmax[k] = (g->lo[k] + (i - 1) * g->cell - o[k]) / d[k];",
+     [lambda g: G.grid_equals_brute("dihedral"), lambda g: G.grid_equals_brute("octar")]),
+    ("grid: walk stops a cell before the bound", "oracle_grid.h",
+     "if (!w->live || w->t_in > t_stop + w->g->slack) return 0;",
+     "if (!w->live || w->t_in > t_stop - w->g->cell) return 0;",
+     [lambda g: G.grid_equals_brute("dihedral"), lambda g: G.grid_equals_brute("octar")]),
+    ("grid: Eq. 23 candidates in walk order, with repeats", "oracle_grid.h",
+     "  if (L->n < 2) return;",
+     "  return;",
+     [lambda g: G.grid_equals_brute("dihedral"), lambda g: G.grid_equals_brute("octar")]),
+    ("grid: Eq. 23 candidates only up to the nearest hit", "oracle_core.h",
+     "SFX(candidates)(S, o, d, tmin, lim, &L);",
+     "SFX(candidates)(S, o, d, tmin, tb, &L);",
+     [lambda g: G.grid_equals_brute("dihedral"), lambda g: G.grid_equals_brute("octar"),
+      lambda g: G.grid_equals_brute("composite")]),
     # surfel attributes
     ("k-NN: squared distance without its z term", "oracle.c",
      "float d2 = (dx * dx + dy * dy) + dz * dz;",
@@ -180,7 +220,7 @@ def plant(tmp_path):
     saved = oracle._lib
 
     def _plant(fname, old, new):
-        for f in ("oracle.c", "oracle_core.h"):
+        for f in ("oracle.c", "oracle_core.h", "oracle_grid.h"):
             shutil.copy(os.path.join(src, f), tmp_path / f)
         path = tmp_path / fname
         text = path.read_text()
