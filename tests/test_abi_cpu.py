@@ -124,3 +124,33 @@ def test_view_from_struct_round_trips_a_library_view(lib):
     a = api.view_from_angles(63.0, 211.0, [0.1, -0.2, 0.3], 1.7, 96, 64)
     b = api.view_from_struct(a.o, a.u, a.v, a.d, a.pitch, a.W, a.H)
     assert bytes(a) == bytes(b)
+
+
+@pytest.mark.parametrize("G,tau", [(256, 3.0), (7, 2.5), (1, 3.0)])
+def test_parameters_equal_the_oracles(lib, G, tau):
+    # the library's fusion grid, epsilon and overlap radius (pipeline
+    # default_params over api.make_params) are the oracle's (fuse_params,
+    # default_eps from its own views), bit for bit as FP32 values; the GPU
+    # parity tests build every oracle input on the oracle's side, so this
+    # is where the two parameter paths meet
+    import scenes
+    from paper_2408_15583_gb300 import pipeline
+    f32 = lambda x: np.float32(x).view(np.uint32)
+    for sc in (scenes.dihedral(2000, seed=31), scenes.sphere(3000, 1.0),
+               scenes.octar(3000, size=2.0, seed=13), scenes.plate(0.3, 0.2, 30, 20),
+               scenes.Scene(pos=np.array([[0.01, -0.02, 0.03], [0.06, 0.01, -0.02]], np.float32),
+                            nrm=np.array([[0.0, 0.6, 0.8], [0.8, 0.0, 0.6]], np.float32),
+                            rad=np.array([0.05, 0.04], np.float32))):
+        for W, H in ((80, 80), (64, 40)):
+            vd = scenes.aggregation_views(sc, W, H)
+            gv = pipeline.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, W, H)
+            prm = pipeline.default_params(sc.pos, gv, G=G, tau=tau)
+            fp = oracle.fuse_params(sc, G, tau)
+            eps = oracle.default_eps(oracle.gfb_views(vd, "fp32"))
+            assert prm.fuse_grid == fp.G
+            assert f32(prm.edge_tau) == f32(fp.tau)
+            assert f32(prm.inv_voxel) == f32(fp.inv_vox)
+            for k in range(3):
+                assert f32(prm.bbox_min[k]) == f32(fp.bmin[k])
+            assert f32(prm.eps) == f32(eps) and f32(prm.overlap_r) == f32(eps)
+            assert prm.edge_mode == fp.edge_mode == 0

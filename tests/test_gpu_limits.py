@@ -43,10 +43,10 @@ def _mods():
     return api, pipeline
 
 
-def _oracle_view(v):
-    return oracle.View(o=np.array(v.o[:], np.float64), u=np.array(v.u[:], np.float64),
-                       v=np.array(v.v[:], np.float64), d=np.array(v.d[:], np.float64),
-                       pitch=float(v.pitch), W=v.W, H=v.H)
+def _oviews(th, ph, centre, extent, W, H):
+    """The oracle's own views for the angles the library's views are made
+    from (every oracle input is built on the oracle's side)."""
+    return [oracle.view_from_angles(t, p, centre, extent, W, H, "fp32") for t, p in zip(th, ph)]
 
 
 def _cplx(E):
@@ -90,12 +90,12 @@ def wedge16():
     prm = pipe.default_params(sc.pos, gv)
     geom, _ = pipe.build_geometry(pos, nrm, rad, gv, prm)
     api.stream_check()
-    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
-    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
-                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
+    ogv = _oviews(th, ph, c, r * 1.02, 64, 64)
+    ogf = [oracle.gfb(sc, v, "fp32") for v in ogv]
+    fp = oracle.fuse_params(sc)
     S = oracle.aggregate(ogf, fp, "fp32")
     return dict(sc=sc, c=c, r=r, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, S=S,
-                ogf=ogf, fp=fp)
+                ogf=ogf, fp=fp, eps=oracle.default_eps(ogv))
 
 
 def test_sixteen_view_fusion_bitexact(wedge16):
@@ -116,12 +116,12 @@ def test_sixteen_view_fusion_bitexact(wedge16):
     assert S8.ns != S.ns or not np.array_equal(S8.id, S.id)
 
 
-def _trace_vs_oracle(d, views, mb, geom_first=False):
-    """Trace `views` through the ABI and the oracle; every record bit-exact.
-    Returns the oracle traces."""
+def _trace_vs_oracle(d, th, ph, centre, extent, W, H, mb, geom_first=False):
+    """Trace the screens of angles (th, ph) through the ABI and the oracle;
+    every record bit-exact.  Returns the oracle traces."""
     api, pipe = _mods()
     sc = d["sc"]
-    W, H = views[0].W, views[0].H
+    views = pipe.views_from_angles(th, ph, centre, extent, W, H)
     prm = pipe.default_params(sc.pos, d["gv"], first_bounce_from_geom=geom_first)
     keys = None
     if not geom_first:
@@ -130,11 +130,9 @@ def _trace_vs_oracle(d, views, mb, geom_first=False):
     api.stream_check()
     per = W * H
     trs = []
-    for a, v in enumerate(views):
-        ov = _oracle_view(v)
+    for a, ov in enumerate(_oviews(th, ph, centre, extent, W, H)):
         first = None if geom_first else oracle.gfb(sc, ov, "fp32")
-        tr = oracle.trace(ov, d["S"], mb, float(prm.eps), float(prm.overlap_r), first=first,
-                          mode="fp32")
+        tr = oracle.trace(ov, d["S"], mb, d["eps"], d["eps"], first=first, mode="fp32")
         sl = slice(a * per, (a + 1) * per)
         assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), f"angle {a}"
         ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
@@ -156,9 +154,8 @@ def test_wedge_deep_bounces_bitexact(wedge16, mb, geom_first):
     # reflections keep d_y = 0 exactly) and slightly off it; 42 x 38 rays
     api, pipe = _mods()
     d = wedge16
-    views = pipe.views_from_angles([0.0, 5.0, 8.0], [0.0, 90.0, 200.0], d["c"], d["r"] * 1.02,
-                                   42, 38)
-    trs = _trace_vs_oracle(d, views, mb, geom_first)
+    trs = _trace_vs_oracle(d, [0.0, 5.0, 8.0], [0.0, 90.0, 200.0], d["c"], d["r"] * 1.02,
+                           42, 38, mb, geom_first)
     M = np.concatenate([t.M for t in trs])
     deep = int((M >= 5).sum()) if mb >= 5 else int((M == mb).sum())
     assert deep > 300            # the case reaches the deep bounces (or the cut)
@@ -172,8 +169,7 @@ def test_wedge_thin_screens_bitexact(wedge16, W, H):
     # cells down the middle of the wedge
     api, pipe = _mods()
     d = wedge16
-    views = pipe.views_from_angles([0.0, 3.0], [0.0, 45.0], d["c"], d["r"] * 1.02, W, H)
-    trs = _trace_vs_oracle(d, views, 8)
+    trs = _trace_vs_oracle(d, [0.0, 3.0], [0.0, 45.0], d["c"], d["r"] * 1.02, W, H, 8)
     assert sum(int((t.M > 0).sum()) for t in trs) > 0
 
 
@@ -185,20 +181,19 @@ def test_wedge_bistatic_axis_receivers(wedge16):
     d = wedge16
     sc = d["sc"]
     views = pipe.views_from_angles([0.0, 5.0], [0.0, 90.0], d["c"], d["r"] * 1.02, 40, 40)
+    ovs = _oviews([0.0, 5.0], [0.0, 90.0], d["c"], d["r"] * 1.02, 40, 40)
     mb = 8
     keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
     h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, d["prm"], ids=False)
     freqs = scenes.freq_grid(2.5e9, 3.5e9, 3)
     axes = [[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [-1.0, 0.0, 0.0], [0.0, -1.0, 0.0]]
-    obs = np.asarray([[list(-np.asarray(v.d[:], np.float64))] + axes for v in views], np.float32)
-    eps = float(d["prm"].eps)
-    E = _cplx(api.po_field_bistatic(h, 2, 40 * 40, obs, d["geom"], eps, freqs))
+    obs = np.asarray([[list(-np.asarray(ov.d, np.float64))] + axes for ov in ovs], np.float32)
+    E = _cplx(api.po_field_bistatic(h, 2, 40 * 40, obs, d["geom"], float(d["prm"].eps), freqs))
     api.stream_check()
+    eps = d["eps"]
     blocked = 0
-    for a, v in enumerate(views):
-        ov = _oracle_view(v)
-        tr = oracle.trace(ov, d["S"], mb, eps, float(d["prm"].overlap_r),
-                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+    for a, ov in enumerate(ovs):
+        tr = oracle.trace(ov, d["S"], mb, eps, eps, first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
         o64 = obs[a].astype(np.float64)
         Eo = oracle.po_field_bistatic(tr, d["S"], freqs, o64, eps)
         blocked += int((oracle.shadow_dirs(tr, d["S"], o64, eps) == 0)[:, tr.M > 0].sum())
@@ -215,8 +210,7 @@ def test_wedge_sweep_beyond_the_staged_frequencies(wedge16):
     E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), d["pos"], d["nrm"], d["rad"],
                            d["geom"], d["prm"])
     api.stream_check()
-    eps = float(d["prm"].eps)
-    ref = oracle.rcs_sweep(sc, sw, d["S"], eps, eps, mode="fp32")
+    ref = oracle.rcs_sweep(sc, sw, d["S"], d["eps"], d["eps"], mode="fp32")
     assert int(max((t.M >= 5).sum() for t in ref.traces)) > 100
     assert field_err(_cplx(E), ref.E).max() < 1e-3
     s = sig.cpu().numpy()
@@ -282,10 +276,9 @@ def test_small_fusion_grids_bitexact(G):
     prm = pipe.default_params(sc.pos, gv, G=G)
     geom, _ = pipe.build_geometry(pos, nrm, rad, gv, prm)
     api.stream_check()
-    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
-    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
-                           inv_vox=float(prm.inv_voxel), G=G)
-    S = oracle.aggregate(ogf, fp, "fp32")
+    ogv = oracle.gfb_views(vd, "fp32")
+    ogf = [oracle.gfb(sc, v, "fp32") for v in ogv]
+    S = oracle.aggregate(ogf, oracle.fuse_params(sc, G), "fp32")
     cr, nf = geom.planes()
     cr = cr.cpu().numpy()
     nf = nf.cpu().numpy()
@@ -297,9 +290,9 @@ def test_small_fusion_grids_bitexact(G):
     assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
     assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
     c, r = scenes.bounding_sphere(sc.pos)
-    views = pipe.views_from_angles([90.0, 70.0], [45.0, 20.0], c, r * 1.02, 32, 32)
-    d = dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, geom=geom, S=S)
-    trs = _trace_vs_oracle(d, views, 2)
+    d = dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, geom=geom, S=S,
+             eps=oracle.default_eps(ogv))
+    trs = _trace_vs_oracle(d, [90.0, 70.0], [45.0, 20.0], c, r * 1.02, 32, 32, 2)
     assert sum(int((t.M > 0).sum()) for t in trs) > 100
 
 
@@ -322,10 +315,10 @@ def test_fusion_of_views_of_different_sizes():
     mask = torch.cat([fa["mask"], fb["mask"]])
     geom = api.aggregate_views(gv, nd, mask, prm)
     api.stream_check()
-    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
-    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
-                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
-    S = oracle.aggregate(ogf, fp, "fp32")
+    ogv = (_oviews([60.0] * 4, [45.0, 135.0, 225.0, 315.0], c, r * 1.02, 48, 48) +
+           _oviews([120.0] * 4, [45.0, 135.0, 225.0, 315.0], c, r * 1.02, 64, 40))
+    ogf = [oracle.gfb(sc, v, "fp32") for v in ogv]
+    S = oracle.aggregate(ogf, oracle.fuse_params(sc), "fp32")
     cr, nf = geom.planes()
     cr = cr.cpu().numpy()
     nf = nf.cpu().numpy()
@@ -337,7 +330,7 @@ def test_fusion_of_views_of_different_sizes():
     assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
     assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
     assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
-    views = pipe.views_from_angles([90.0, 75.0], [45.0, 58.0], c, r * 1.02, 36, 36)
-    d = dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, geom=geom, S=S)
-    trs = _trace_vs_oracle(d, views, 3)
+    d = dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, geom=geom, S=S,
+             eps=oracle.default_eps(ogv))
+    trs = _trace_vs_oracle(d, [90.0, 75.0], [45.0, 58.0], c, r * 1.02, 36, 36, 3)
     assert sum(int((t.M >= 2).sum()) for t in trs) > 100

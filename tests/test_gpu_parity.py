@@ -5,7 +5,8 @@ hit are bit-exact against the oracle's FP32-geometry mode; the PO field is
 within 1e-3 relative per sample (||E - E_ref|| / max(||E_ref||, 1e-3 max
 ||E_ref||)) and sigma within 0.1 dB where sigma_ref >= peak - 40 dB.  The
 oracle computes every expected value from the same seeded inputs; nothing it
-uses comes from the CUDA path.
+uses comes from the CUDA path: its views, fusion grid, epsilon and overlap
+radius are built by the oracle from the same angles and points.
 """
 import math
 
@@ -35,10 +36,10 @@ def _mods():
     return api, pipeline
 
 
-def _oracle_view(v):
-    return oracle.View(o=np.array(v.o[:], np.float64), u=np.array(v.u[:], np.float64),
-                       v=np.array(v.v[:], np.float64), d=np.array(v.d[:], np.float64),
-                       pitch=float(v.pitch), W=v.W, H=v.H)
+def _oviews(th, ph, centre, extent, W, H):
+    """The oracle's own views for the angles the library's views were made
+    from (oracle.view_from_angles, rounded to FP32)."""
+    return [oracle.view_from_angles(t, p, centre, extent, W, H, "fp32") for t, p in zip(th, ph)]
 
 
 def _keys_oracle(sc, v, tube=False, delta=0.0):
@@ -76,14 +77,15 @@ def test_gfb_keys_bitexact(name, WH):
     api, pipe = _mods()
     sc = SCENES[name]()
     c, r = scenes.bounding_sphere(sc.pos)
-    views = pipe.views_from_angles([90.0, 60.0, 133.0], [20.0, 200.0, 311.0], c, r * 1.05, *WH)
+    th, ph = [90.0, 60.0, 133.0], [20.0, 200.0, 311.0]
+    views = pipe.views_from_angles(th, ph, c, r * 1.05, *WH)
     pos, nrm, rad = pipe.scene_to_device(sc, DEV)
     out = api.build_gfb(views, pos, nrm, rad, 0)
     api.stream_check()
     keys = out["keys"].cpu().numpy().view(np.uint64).reshape(3, -1)
     nd = out["nd"].cpu().numpy().reshape(3, -1, 4)
-    for i, v in enumerate(views):
-        g = oracle.gfb(sc, _oracle_view(v), "fp32")
+    for i, ov in enumerate(_oviews(th, ph, c, r * 1.05, *WH)):
+        g = oracle.gfb(sc, ov, "fp32")
         assert np.array_equal(keys[i], g.keys()), f"view {i}"
         hit = g.idx >= 0
         assert np.array_equal(nd[i][hit, :3].astype(np.float64), g.nrm[hit])
@@ -99,12 +101,13 @@ def test_gfb_tube_mode_bitexact():
     sc = scenes.dihedral(3000, seed=4)
     c, r = scenes.bounding_sphere(sc.pos)
     views = pipe.views_from_angles([60.0, 120.0], [45.0, 135.0], c, r * 1.05, 64, 64)
-    delta = 2.0 * views[0].pitch
+    ovs = _oviews([60.0, 120.0], [45.0, 135.0], c, r * 1.05, 64, 64)
+    delta = 2.0 * ovs[0].pitch
     pos, nrm, rad = pipe.scene_to_device(sc, DEV)
     out = api.build_gfb(views, pos, None, None, 1, delta)
     keys = out["keys"].cpu().numpy().view(np.uint64).reshape(2, -1)
-    for i, v in enumerate(views):
-        g = oracle.gfb(sc, _oracle_view(v), "fp32", tube=True, delta=float(np.float32(delta)))
+    for i, ov in enumerate(ovs):
+        g = oracle.gfb(sc, ov, "fp32", tube=True, delta=float(np.float32(delta)))
         assert np.array_equal(keys[i], g.keys())
 
 
@@ -122,7 +125,7 @@ def test_gfb_edge_cases():
     pos, nrm, rad = pipe.scene_to_device(sc, DEV)
     out = api.build_gfb(views, pos, nrm, rad, 0)
     keys = out["keys"].cpu().numpy().view(np.uint64)
-    g = oracle.gfb(sc, _oracle_view(views[0]), "fp32")
+    g = oracle.gfb(sc, oracle.view_from_angles(0.0, 0.0, [0, 0, 0], 1.0, 17, 9), "fp32")
     assert np.array_equal(keys, g.keys())
     assert set(np.unique(g.idx)) <= {-1, 0}
     with pytest.raises(RuntimeError):
@@ -141,13 +144,10 @@ def _geom_case(sc):
     prm = pipe.default_params(sc.pos, gv)
     geom, g = pipe.build_geometry(pos, nrm, rad, gv, prm)
     api.stream_check()
-    ogv = [_oracle_view(v) for v in gv]
-    ogf = [oracle.gfb(sc, v, "fp32") for v in ogv]
-    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
-                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
-    S = oracle.aggregate(ogf, fp, "fp32")
+    S, ogv, ogf, fp = oracle.build_geometry(sc, vd, "fp32")
+    eps = oracle.default_eps(ogv)
     return dict(sc=sc, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, S=S, ogv=ogv,
-                ogf=ogf, fp=fp)
+                ogf=ogf, fp=fp, eps=eps)
 
 
 @pytest.fixture(scope="module")
@@ -162,10 +162,20 @@ def octar_geom():
     return _geom_case(scenes.octar(3000, size=2.0, seed=13))
 
 
+@pytest.fixture(scope="module")
+def composite_geom():
+    # noisy points with PCA normals (trihedral + plate + cylinder): splats
+    # with scattered normals, rays of up to 3 bounces in the trihedral
+    return _geom_case(scenes.composite(6000, seed=9, pca=True))
+
+
 GEOMS = ["small_geom", "octar_geom"]
+TRACE_ANGLES = {"small_geom": ([90.0, 90.0, 75.0], [45.0, 10.0, 58.0]),
+                "octar_geom": ([60.0, 54.7356, 120.0], [45.0, 45.0, 200.0]),
+                "composite_geom": ([54.7356, 60.0, 50.0], [45.0, 30.0, 60.0])}
 
 
-@pytest.mark.parametrize("case", GEOMS)
+@pytest.mark.parametrize("case", GEOMS + ["composite_geom"])
 def test_aggregate_splats_bitexact(case, request):
     small_geom = request.getfixturevalue(case)
     geom, S = small_geom["geom"], small_geom["S"]
@@ -205,16 +215,16 @@ def test_aggregate_canny_edges_bitexact(case, request):
     assert not np.array_equal(S.id, d["S"].id)
 
 
-@pytest.mark.parametrize("case", GEOMS)
+@pytest.mark.parametrize("case", GEOMS + ["composite_geom"])
 @pytest.mark.parametrize("geom_first", [False, True])
 def test_trace_bounces_bitexact(case, geom_first, request):
     api, pipe = _mods()
     d = request.getfixturevalue(case)
     sc = d["sc"]
     c, r = scenes.bounding_sphere(sc.pos)
-    th, ph = ([90.0, 90.0, 75.0], [45.0, 10.0, 58.0]) if case == "small_geom" else \
-        ([60.0, 54.7356, 120.0], [45.0, 45.0, 200.0])
+    th, ph = TRACE_ANGLES[case]
     views = pipe.views_from_angles(th, ph, c, r * 1.02, 40, 40)
+    ovs = _oviews(th, ph, c, r * 1.02, 40, 40)
     prm = pipe.default_params(sc.pos, d["gv"], first_bounce_from_geom=geom_first)
     mb = 3
     keys = None
@@ -224,11 +234,9 @@ def test_trace_bounces_bitexact(case, geom_first, request):
     h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, prm, stats=stats)
     api.stream_check()
     per = 40 * 40
-    for a, v in enumerate(views):
-        ov = _oracle_view(v)
+    for a, ov in enumerate(ovs):
         first = None if geom_first else oracle.gfb(sc, ov, "fp32")
-        tr = oracle.trace(ov, d["S"], mb, float(prm.eps), float(prm.overlap_r), first=first,
-                          mode="fp32")
+        tr = oracle.trace(ov, d["S"], mb, d["eps"], d["eps"], first=first, mode="fp32")
         sl = slice(a * per, (a + 1) * per)
         assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), f"angle {a}"
         ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
@@ -302,16 +310,16 @@ def test_po_field_matches_oracle_on_traced_hits(small_geom):
     c, r = scenes.bounding_sphere(sc.pos)
     th, ph = [90.0, 80.0], [45.0, 20.0]
     views = pipe.views_from_angles(th, ph, c, r * 1.02, 48, 48)
+    ovs = _oviews(th, ph, c, r * 1.02, 48, 48)
     keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
     h = api.trace_bounces(views, keys, d["nrm"], d["geom"], 2, d["prm"])
     freqs = scenes.freq_grid(2.5e9, 3.5e9, 5)
-    ks = np.array([[-x for x in v.d] for v in views], np.float32)
+    ks = np.array([-ov.d for ov in ovs], np.float32)
     E = _cplx(api.po_field(h, 2, 48 * 48, ks, freqs))
     api.stream_check()
-    for a, v in enumerate(views):
-        ov = _oracle_view(v)
-        tr = oracle.trace(ov, d["S"], 2, float(d["prm"].eps), float(d["prm"].overlap_r),
-                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+    for a, ov in enumerate(ovs):
+        tr = oracle.trace(ov, d["S"], 2, d["eps"], d["eps"], first=oracle.gfb(sc, ov, "fp32"),
+                          mode="fp32")
         Eo = oracle.po_field(tr, freqs, ks[a].astype(np.float64))[0]
         assert field_err(E[a], Eo).max() < 1e-3
 
@@ -326,13 +334,14 @@ def test_po_field_bistatic_matches_oracle(case, request):
     c, r = scenes.bounding_sphere(sc.pos)
     th, ph = [90.0, 70.0, 60.0], [45.0, 20.0, 200.0]
     views = pipe.views_from_angles(th, ph, c, r * 1.02, 40, 40)
+    ovs = _oviews(th, ph, c, r * 1.02, 40, 40)
     mb = 2 if case == "small_geom" else 3
     keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
     h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, d["prm"])
     freqs = scenes.freq_grid(2.5e9, 3.5e9, 3)
     obs = []
-    for v in views:
-        w = -np.asarray(v.d[:], np.float64)
+    for ov in ovs:
+        w = -np.asarray(ov.d, np.float64)
         rows = [w]
         for dphi, dth in ((25.0, 0.0), (60.0, 10.0), (140.0, -20.0)):
             t0 = math.acos(np.clip(w[2], -1, 1)) + math.radians(dth)
@@ -340,14 +349,12 @@ def test_po_field_bistatic_matches_oracle(case, request):
             rows.append([math.sin(t0) * math.cos(p0), math.sin(t0) * math.sin(p0), math.cos(t0)])
         obs.append(rows)
     obs = np.asarray(obs, np.float32)
-    eps = float(d["prm"].eps)
-    E = _cplx(api.po_field_bistatic(h, 3, 40 * 40, obs, d["geom"], eps, freqs))
+    E = _cplx(api.po_field_bistatic(h, 3, 40 * 40, obs, d["geom"], float(d["prm"].eps), freqs))
     api.stream_check()
+    eps = d["eps"]
     blocked = 0
-    for a, v in enumerate(views):
-        ov = _oracle_view(v)
-        tr = oracle.trace(ov, d["S"], mb, eps, float(d["prm"].overlap_r),
-                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+    for a, ov in enumerate(ovs):
+        tr = oracle.trace(ov, d["S"], mb, eps, eps, first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
         o64 = obs[a].astype(np.float64)
         Eo = oracle.po_field_bistatic(tr, d["S"], freqs, o64, eps)
         blocked += int((oracle.shadow_dirs(tr, d["S"], o64, eps) == 0)[:, tr.M > 0].sum())
@@ -362,16 +369,16 @@ def test_po_at_every_bounce_matches_oracle(case, request):
     sc = d["sc"]
     c, r = scenes.bounding_sphere(sc.pos)
     views = pipe.views_from_angles([90.0, 60.0], [45.0, 30.0], c, r * 1.02, 40, 40)
+    ovs = _oviews([90.0, 60.0], [45.0, 30.0], c, r * 1.02, 40, 40)
     mb = 2 if case == "small_geom" else 3
     keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
     freqs = scenes.freq_grid(2.5e9, 3.5e9, 3)
     E = _cplx(pipe.field_every_bounce(views, keys, d["nrm"], d["geom"], d["prm"], mb, freqs))
     api.stream_check()
-    eps = float(d["prm"].eps)
-    for a, v in enumerate(views):
-        ov = _oracle_view(v)
-        Eo = oracle.po_field_every_bounce(ov, d["S"], oracle.gfb(sc, ov, "fp32"), mb, eps,
-                                          float(d["prm"].overlap_r), freqs)
+    eps = d["eps"]
+    for a, ov in enumerate(ovs):
+        Eo = oracle.po_field_every_bounce(ov, d["S"], oracle.gfb(sc, ov, "fp32"), mb, eps, eps,
+                                          freqs)
         assert field_err(E[a], Eo).max() < 1e-3, f"angle {a}"
 
 
@@ -396,8 +403,7 @@ def test_rcs_sweep_matches_oracle(case, request):
     args = api.SweepArgs.from_sweep(sw, angle_batch=4)     # two batches, ragged tail
     E, sig = api.rcs_sweep(args, d["pos"], d["nrm"], d["rad"], d["geom"], d["prm"])
     api.stream_check()
-    eps = float(d["prm"].eps)
-    ref = oracle.rcs_sweep(sc, sw, d["S"], eps, eps, mode="fp32")
+    ref = oracle.rcs_sweep(sc, sw, d["S"], d["eps"], d["eps"], mode="fp32")
     Eg = _cplx(E)
     assert field_err(Eg, ref.E).max() < 1e-3
     s = sig.cpu().numpy()
@@ -420,7 +426,7 @@ def test_rcs_sweep_vs_fp64_physics_oracle(small_geom):
                            d["geom"], d["prm"])
     vd = scenes.aggregation_views(sc, 80, 80)
     S64, gv64, _, _ = oracle.build_geometry(sc, vd, "fp64")
-    eps = float(d["prm"].eps)
+    eps = oracle.default_eps(gv64)
     ref = oracle.rcs_sweep(sc, sw, S64, eps, eps, mode="fp64")
     s = sig.cpu().numpy()
     assert _sigma_check(s[..., 0, 0], ref.sigma[..., 0, 0], peak_db=20.0) < 0.1
@@ -449,6 +455,7 @@ def test_trace_ragged_screen_bitexact(small_geom):
     sc = d["sc"]
     c, r = scenes.bounding_sphere(sc.pos)
     views = pipe.views_from_angles([90.0, 80.0], [45.0, 30.0], c, r * 1.02, 37, 23)
+    ovs = _oviews([90.0, 80.0], [45.0, 30.0], c, r * 1.02, 37, 23)
     keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
     stats = torch.zeros(8, dtype=torch.int64, device=DEV)
     h = api.trace_bounces(views, keys, d["nrm"], d["geom"], 3, d["prm"], stats=stats)
@@ -462,10 +469,9 @@ def test_trace_ragged_screen_bitexact(small_geom):
     assert st[0] == 2 * per + int((M >= 1).sum()) + int((M >= 2).sum())
     assert st[1] == int((M >= 2).sum())
     multi = 0
-    for a, v in enumerate(views):
-        ov = _oracle_view(v)
-        tr = oracle.trace(ov, d["S"], 3, float(d["prm"].eps), float(d["prm"].overlap_r),
-                          first=oracle.gfb(sc, ov, "fp32"), mode="fp32")
+    for a, ov in enumerate(ovs):
+        tr = oracle.trace(ov, d["S"], 3, d["eps"], d["eps"], first=oracle.gfb(sc, ov, "fp32"),
+                          mode="fp32")
         sl = slice(a * per, (a + 1) * per)
         assert np.array_equal(h.M[sl].cpu().numpy(), tr.M)
         ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
@@ -486,6 +492,7 @@ def test_empty_geometry_and_missing_screen_give_zero_field():
     c, r = scenes.bounding_sphere(sc.pos)
     far = np.asarray(c) + np.array([10.0, 0.0, 0.0])
     gv = pipe.views_from_angles([60.0, 120.0], [45.0, 135.0], far, r, 32, 32)
+    ogv = _oviews([60.0, 120.0], [45.0, 135.0], far, r, 32, 32)
     prm = pipe.default_params(sc.pos, gv)
     geom, g = pipe.build_geometry(pos, nrm, rad, gv, prm)
     api.stream_check()
@@ -493,12 +500,11 @@ def test_empty_geometry_and_missing_screen_give_zero_field():
     assert int((cr[:, 3] > 0).sum()) == 0
     sw = scenes._sweep_over(sc, [90.0, 70.0], [0.0, 30.0], 24, [3e9, 3.1e9], 3)
     E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), pos, nrm, rad, geom, prm)
-    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
-    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
-                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
-    S = oracle.aggregate(ogf, fp, "fp32")
+    ogf = [oracle.gfb(sc, v, "fp32") for v in ogv]
+    S = oracle.aggregate(ogf, oracle.fuse_params(sc), "fp32")
     assert S.ns == 0
-    ref = oracle.rcs_sweep(sc, sw, S, float(prm.eps), float(prm.overlap_r), mode="fp32")
+    eps = oracle.default_eps(ogv)
+    ref = oracle.rcs_sweep(sc, sw, S, eps, eps, mode="fp32")
     # with no splats only the primary bounce contributes
     assert field_err(_cplx(E), ref.E).max() < 1e-3
     sw2 = scenes.Sweep(theta_deg=np.array([90.0]), phi_deg=np.array([0.0]), W=16, H=16,
@@ -519,13 +525,15 @@ def test_two_point_scene_through_the_path():
                       rad=np.array([0.05, 0.04], np.float32))
     pos, nrm, rad = pipe.scene_to_device(sc, DEV)
     centre = sc.pos.mean(axis=0).astype(np.float64)
-    gv = pipe.views_from_angles([60.0, 60.0, 120.0, 120.0], [45.0, 225.0, 135.0, 315.0],
-                                centre, 0.12, 48, 48)
+    th, ph = [60.0, 60.0, 120.0, 120.0], [45.0, 225.0, 135.0, 315.0]
+    gv = pipe.views_from_angles(th, ph, centre, 0.12, 48, 48)
     prm = pipe.default_params(sc.pos, gv)
     geom, g = pipe.build_geometry(pos, nrm, rad, gv, prm)
     api.stream_check()
-    ogf = [oracle.gfb(sc, _oracle_view(v), "fp32") for v in gv]
-    S = oracle.aggregate(ogf, oracle.fuse_params(sc, prm.fuse_grid, float(prm.edge_tau)), "fp32")
+    ogv = _oviews(th, ph, centre, 0.12, 48, 48)
+    ogf = [oracle.gfb(sc, v, "fp32") for v in ogv]
+    S = oracle.aggregate(ogf, oracle.fuse_params(sc), "fp32")
+    eps = oracle.default_eps(ogv)
     cr, nf = geom.planes()
     cr = cr.cpu().numpy()
     ids = np.flatnonzero(cr[:, 3] > 0)
@@ -535,7 +543,7 @@ def test_two_point_scene_through_the_path():
                       centre=centre, extent=0.12, freqs_hz=np.array([5e9]), max_bounces=3)
     E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), pos, nrm, rad, geom, prm)
     api.stream_check()
-    ref = oracle.rcs_sweep(sc, sw, S, float(prm.eps), float(prm.overlap_r), mode="fp32")
+    ref = oracle.rcs_sweep(sc, sw, S, eps, eps, mode="fp32")
     assert field_err(_cplx(E), ref.E).max() < 1e-3
 
 
