@@ -1,19 +1,28 @@
 """Parity at the workloads' full sizes, in the launch configuration bench.py
 times (the same entry points, angle batches and screens).
 
+The oracle computes every expected value from the seeded inputs alone: its
+own views, fusion grid, epsilon and overlap radius, its own 8 GFBs of the
+whole point set, its own fusion and its own traces of every ray.  At these
+sizes its searches take their candidates from a uniform grid (the same result
+as brute force, bit for bit, pinned on the CPU).
+
 * Dihedral workload (10k points, 8 fused views at 512^2, 91 angles at 128^2,
   3 GHz, 2 bounces): every splat bit-exact; for angles spread over both angle
   batches of the sweep (64 + 27), every ray's hit ids, bounce counts and Psi
   bit-exact, the field within 1e-3 and sigma within 0.1 dB of the oracle.
-* Sphere workload (200k points, 8 fused views at 512^2, 360 angles at 1024^2,
-  64 frequencies 8-12 GHz): sampled pixels of the fused views and of one
-  8-angle batch of ray screens have the oracle's GFB keys bit for bit (the
-  oracle computes them pixel by pixel); the whole 360 x 64 sweep is within
-  0.2 dB of the exact physical-optics backscatter of the sphere (a property
-  that holds at any size; the surfel sampling adds a few hundredths of a dB).
+* Sphere workload, the bench's default (200k points, 8 fused views at 512^2,
+  360 angles at 1024^2, 64 frequencies 8-12 GHz, 2 bounces): every GFB key
+  of the 8 views, every splat, and for 8 angles spread over the sweep every
+  ray's records bit-exact; the field of those angles from the 360-angle sweep
+  (as bench.py runs it) within 1e-3 of the oracle's field over all rays and
+  frequencies, sigma within 0.1 dB, reported per angle; the whole 360 x 64
+  sweep within 0.2 dB of the sphere's exact physical-optics backscatter.
+* Composite workload (1M noisy points with PCA normals, 8 fused views at
+  512^2, 2048^2 rays, 10 GHz, 5 bounces): every splat bit-exact; two angles,
+  every ray's records bit-exact, field and sigma, reported per angle.
 
-The C oracle keeps no state between calls, and ctypes releases the GIL
-during them, so independent views and angles run in a thread pool.
+Run with `-s` to see the per-angle table.
 """
 import math
 from concurrent.futures import ThreadPoolExecutor
@@ -45,12 +54,6 @@ def _mods():
     return api, pipeline
 
 
-def _oracle_view(v):
-    return oracle.View(o=np.array(v.o[:], np.float64), u=np.array(v.u[:], np.float64),
-                       v=np.array(v.v[:], np.float64), d=np.array(v.d[:], np.float64),
-                       pitch=float(v.pitch), W=v.W, H=v.H)
-
-
 def _pool():
     import os
     return ThreadPoolExecutor(max(2, min(16, os.cpu_count() or 2)))
@@ -67,6 +70,17 @@ def _field_err(E, Eref):
     return d / np.maximum(r, 1e-3 * r.max())
 
 
+def _sigma_err_db(sig, ref, peak_db=40.0):
+    """|delta sigma| in dB over the co-polarised samples within peak_db of
+    the reference's peak (c24)."""
+    worst = 0.0
+    for p in (0, 1):
+        sd, so = oracle.db(sig[..., p, p]), oracle.db(ref[..., p, p])
+        keep = so >= so.max() - peak_db
+        worst = max(worst, float(np.abs(sd - so)[keep].max()))
+    return worst
+
+
 def _gpu_geometry(wl):
     api, pipe = _mods()
     sc, vd = wl.scene, wl.views
@@ -76,6 +90,78 @@ def _gpu_geometry(wl):
     geom, _ = pipe.build_geometry(pos, nrm, rad, gv, prm)
     api.stream_check()
     return pos, nrm, rad, gv, prm, geom
+
+
+def _oracle_geometry(wl):
+    """The oracle's fused splats from its own 8 GFBs (every pixel), its own
+    fusion grid, and its epsilon = overlap radius."""
+    S, ogv, ogf, fp = oracle.build_geometry(wl.scene, wl.views, "fp32")
+    return S, ogv, ogf, oracle.default_eps(ogv)
+
+
+def _splats_equal(geom, S):
+    cr, nf = geom.planes()
+    cr = cr.cpu().numpy()
+    nf = nf.cpu().numpy()
+    ids = np.flatnonzero(cr[:, 3] > 0)
+    assert np.array_equal(ids, S.id)
+    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
+    assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
+    assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
+    assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
+
+
+def _records_equal(h, sl, tr, tag):
+    """Every record of one angle's rays bit-exact (path length to 1e-13)."""
+    assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), tag
+    ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
+    ids[ids == 0xFFFFFFFF] = -1
+    assert np.array_equal(ids.T, tr.ids), tag
+    assert np.array_equal(h.psi[sl].cpu().numpy(), tr.psi), tag
+    live = tr.M > 0
+    for name in ("p", "n", "k", "u", "v"):
+        got = getattr(h, name)[sl].cpu().numpy().astype(np.float64)
+        assert np.array_equal(got[live], getattr(tr, name)[live]), f"{tag}: {name}"
+    assert np.allclose(h.path[sl].cpu().numpy()[live], tr.path[live], rtol=1e-13, atol=1e-13), tag
+
+
+def _sweep_parity(wl, d, angles, label):
+    """Trace `angles` of the workload's sweep as one batch through the ABI
+    and compare every ray with the oracle's trace of that angle; compare the
+    sweep's field and sigma at those angles (d["E"], d["sig"]: the whole
+    sweep as bench.py runs it) with the oracle's over every ray.  Prints and
+    returns the per-angle errors."""
+    api, pipe = _mods()
+    sc, sw = wl.scene, wl.sweep
+    views = [api.view_from_angles(sw.theta_deg[a], sw.phi_deg[a], sw.centre, sw.extent,
+                                  sw.W, sw.H) for a in angles]
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], sw.max_bounces, d["prm"])
+    api.stream_check()
+    Eg = _cplx(d["E"])
+    sg = d["sig"].cpu().numpy()
+    per = sw.W * sw.H
+    rows = []
+    for k, a in enumerate(angles):
+        ref = oracle.rcs_sweep(sc, sw, d["S"], d["eps"], d["eps"], mode="fp32", angles=[a])
+        tr = ref.traces[0]
+        _records_equal(h, slice(k * per, (k + 1) * per), tr, f"{label} angle {a}")
+        fe = float(_field_err(Eg[a:a + 1], ref.E).max())
+        de = _sigma_err_db(sg[a:a + 1], ref.sigma)
+        rows.append(dict(angle=a, theta=float(sw.theta_deg[a]), phi=float(sw.phi_deg[a]),
+                         hits=int((tr.M > 0).sum()), multi=int((tr.M >= 2).sum()),
+                         field_err=fe, dsigma_db=de))
+        del ref, tr
+    print(f"\n{label}: per-angle parity against the oracle (every ray, "
+          f"{sw.n_freq} frequencies, 2 polarisations)")
+    print("  angle  theta    phi     hits  M>=2  max field err (c24)  max |d sigma| dB")
+    for r in rows:
+        print(f"  {r['angle']:5d} {r['theta']:6.1f} {r['phi']:6.1f} {r['hits']:8d} {r['multi']:5d}"
+              f"  {r['field_err']:19.3e}  {r['dsigma_db']:16.3e}")
+    for r in rows:
+        assert r["field_err"] < 1e-3, r
+        assert r["dsigma_db"] < 0.1, r
+    return rows
 
 
 # ----------------------------------------------------------------------------
@@ -91,126 +177,68 @@ def dihedral_full():
     args = api.SweepArgs.from_sweep(sw)
     E, sig = api.rcs_sweep(args, pos, nrm, rad, geom, prm)
     api.stream_check()
-    ogv = [_oracle_view(v) for v in gv]
-    with _pool() as ex:
-        ogf = list(ex.map(lambda v: oracle.gfb(sc, v, "fp32"), ogv))
-    fp = oracle.FuseParams(tau=float(prm.edge_tau), bmin=np.array(prm.bbox_min[:], np.float64),
-                           inv_vox=float(prm.inv_voxel), G=prm.fuse_grid)
-    S = oracle.aggregate(ogf, fp, "fp32")
-    return dict(sc=sc, sw=sw, pos=pos, nrm=nrm, rad=rad, prm=prm, geom=geom, E=E, sig=sig, S=S,
-                args=args)
+    S, ogv, ogf, eps = _oracle_geometry(wl)
+    return dict(wl=wl, pos=pos, nrm=nrm, rad=rad, prm=prm, geom=geom, E=E, sig=sig, S=S,
+                eps=eps, args=args)
 
 
 def test_dihedral_full_splats_bitexact(dihedral_full):
-    d = dihedral_full
-    cr, nf = d["geom"].planes()
-    cr = cr.cpu().numpy()
-    nf = nf.cpu().numpy()
-    ids = np.flatnonzero(cr[:, 3] > 0)
-    S = d["S"]
-    assert S.ns > 50_000
-    assert np.array_equal(ids, S.id)
-    assert np.array_equal(cr[ids, :3].astype(np.float64), S.c)
-    assert np.array_equal(cr[ids, 3].astype(np.float64), S.r)
-    assert np.array_equal(nf[ids, :3].astype(np.float64), S.n)
-    assert np.array_equal(nf[ids, 3].astype(np.int64), S.count)
+    assert dihedral_full["S"].ns > 50_000
+    _splats_equal(dihedral_full["geom"], dihedral_full["S"])
 
 
 def test_dihedral_full_sweep_and_traces(dihedral_full):
-    api, pipe = _mods()
     d = dihedral_full
-    sc, sw, prm = d["sc"], d["sw"], d["prm"]
     assert d["args"].c.angle_batch == 0          # the library picks the batch, as in bench.py
     # angles of both angle batches (0..63, 64..90), the batch edges included
-    angles = [0, 1, 22, 45, 63, 64, 65, 90]
-    eps, r_ov = float(prm.eps), float(prm.overlap_r)
-    with _pool() as ex:
-        refs = list(ex.map(lambda a: oracle.rcs_sweep(sc, sw, d["S"], eps, r_ov, mode="fp32",
-                                                      angles=[a]), angles))
-    Eg = _cplx(d["E"])
-    sg = d["sig"].cpu().numpy()
-    for a, ref in zip(angles, refs):
-        assert _field_err(Eg[a:a + 1], ref.E).max() < 1e-3, f"angle {a}"
-        for p in (0, 1):
-            s0, s1 = sg[a, :, p, p], ref.sigma[0, :, p, p]
-            assert np.all(np.abs(oracle.db(s0) - oracle.db(s1)) < 0.1), f"angle {a} pol {p}"
-    # every ray of those angles, traced as one 8-angle batch through the ABI
-    views = [api.view_from_angles(sw.theta_deg[a], sw.phi_deg[a], sw.centre, sw.extent,
-                                  sw.W, sw.H) for a in angles]
-    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
-    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], sw.max_bounces, prm)
-    api.stream_check()
-    per = sw.W * sw.H
-    multi = 0
-    for k, ref in enumerate(refs):
-        tr = ref.traces[0]
-        sl = slice(k * per, (k + 1) * per)
-        assert np.array_equal(h.M[sl].cpu().numpy(), tr.M), f"angle {angles[k]}"
-        ids = h.ids[:, sl].cpu().numpy().view(np.uint32).astype(np.int64)
-        ids[ids == 0xFFFFFFFF] = -1
-        assert np.array_equal(ids.T, tr.ids), f"angle {angles[k]}"
-        assert np.array_equal(h.psi[sl].cpu().numpy(), tr.psi)
-        multi += int((tr.M >= 2).sum())
-    assert multi > 1000        # the dihedral's double bounces are exercised
+    rows = _sweep_parity(d["wl"], d, [0, 1, 22, 45, 63, 64, 65, 90], "dihedral")
+    assert sum(r["multi"] for r in rows) > 1000   # the dihedral's double bounces
 
 
 # ----------------------------------------------------------------------------
-# sphere workload (the default bench workload), sampled + closed form
+# sphere workload (the default bench workload)
 # ----------------------------------------------------------------------------
 
 @pytest.fixture(scope="module")
 def sphere_full():
+    api, pipe = _mods()
     wl = scenes.workload_sphere()
     pos, nrm, rad, gv, prm, geom = _gpu_geometry(wl)
-    return dict(wl=wl, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom)
+    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(wl.sweep), pos, nrm, rad, geom, prm)
+    api.stream_check()
+    S, ogv, ogf, eps = _oracle_geometry(wl)
+    return dict(wl=wl, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, E=E, sig=sig,
+                S=S, ogv=ogv, ogf=ogf, eps=eps)
 
 
-def _sampled_keys_match(sc, views, keys, n_sample, seed):
-    per = views[0].W * views[0].H
-    rng = np.random.default_rng(seed)
-    jobs = []
-    for k, v in enumerate(views):
-        pix = np.sort(rng.choice(per, n_sample, replace=False))
-        jobs.append((k, v, pix))
-    with _pool() as ex:
-        refs = list(ex.map(lambda j: oracle.gfb(sc, _oracle_view(j[1]), "fp32", pix=j[2]).keys(),
-                           jobs))
-    kk = keys.cpu().numpy().view(np.uint64)
-    hits = 0
-    for (k, v, pix), ref in zip(jobs, refs):
-        got = kk[k * per + pix]
-        assert np.array_equal(got, ref), f"view {k}: {np.flatnonzero(got != ref)[:5]}"
-        hits += int((ref != np.uint64(0xFFFFFFFFFFFFFFFF)).sum())
-    return hits
-
-
-def test_sphere_full_gfb_keys_sampled(sphere_full):
+def test_sphere_full_gfb_keys_and_splats_bitexact(sphere_full):
+    # the 8 fused views at 512^2, all in one launch as the bench builds
+    # them: every pixel's key, then every splat of the fusion
     api, pipe = _mods()
     d = sphere_full
-    sc, sw = d["wl"].scene, d["wl"].sweep
-    # the 8 fused views at 512^2 (all in one launch, as the bench builds them)
     kg = api.build_gfb(d["gv"], d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
-    # one 8-angle batch of 1024^2 ray screens (the sweep's batch shape)
-    angles = [0, 45, 90, 135, 180, 225, 270, 359]
-    views = [api.view_from_angles(sw.theta_deg[a], sw.phi_deg[a], sw.centre, sw.extent,
-                                  sw.W, sw.H) for a in angles]
-    ks = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
     api.stream_check()
-    h1 = _sampled_keys_match(sc, d["gv"], kg, 600, 1)
-    h2 = _sampled_keys_match(sc, views, ks, 600, 2)
-    assert h1 > 1000 and h2 > 1000
+    kk = kg.cpu().numpy().view(np.uint64).reshape(len(d["ogf"]), -1)
+    for v, g in enumerate(d["ogf"]):
+        assert np.array_equal(kk[v], g.keys()), f"view {v}"
+    assert d["S"].ns > 200_000
+    _splats_equal(d["geom"], d["S"])
+
+
+def test_sphere_full_sweep_parity_per_angle(sphere_full):
+    # 8 angles spread over the 360-angle sweep (several of the library's
+    # angle batches): every one of the 1024^2 rays per angle, 64 frequencies
+    rows = _sweep_parity(sphere_full["wl"], sphere_full, [0, 7, 45, 90, 133, 180, 271, 359],
+                         "sphere")
+    assert all(r["hits"] > 600_000 for r in rows)
 
 
 def test_sphere_full_sweep_vs_exact_po(sphere_full):
     # exact PO backscatter of a PEC sphere of radius a:
     # sigma = 4 pi k^2 a^4 |e^{jb}/(jb) + (e^{jb} - 1)/b^2|^2, b = 2 k a
-    api, pipe = _mods()
     d = sphere_full
     sw = d["wl"].sweep
-    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(sw), d["pos"], d["nrm"], d["rad"],
-                           d["geom"], d["prm"])
-    api.stream_check()
-    s = sig.cpu().numpy()
+    s = d["sig"].cpu().numpy()
     assert s.shape[:2] == (360, 64)
     a = 1.0
     k = 2 * math.pi * np.asarray(sw.freqs_hz) / C0
@@ -226,23 +254,28 @@ def test_sphere_full_sweep_vs_exact_po(sphere_full):
 
 
 # ----------------------------------------------------------------------------
-# composite workload: sampled GFB keys at full size
+# composite workload: noisy points, PCA normals, 5 bounces
 # ----------------------------------------------------------------------------
 
-def test_composite_full_gfb_keys_sampled():
-    # 1M noisy points with PCA normals; the 8 fused views at 512^2 and one
-    # 8-angle batch of the sweep's 2048^2 ray screens, sampled pixels against
-    # the oracle's per-pixel search over all points
+@pytest.fixture(scope="module")
+def composite_full():
     api, pipe = _mods()
     wl = scenes.workload_composite()
-    sc, sw, vd = wl.scene, wl.sweep, wl.views
-    pos, nrm, rad = pipe.scene_to_device(sc, DEV)
-    gv = pipe.views_from_angles(vd.theta_deg, vd.phi_deg, vd.centre, vd.extent, vd.W, vd.H)
-    kg = api.build_gfb(gv, pos, nrm, rad, 0, outputs=("keys",))["keys"]
-    angles = [0, 9, 18, 27, 36, 45, 54, 71]
-    views = [api.view_from_angles(sw.theta_deg[a], sw.phi_deg[a], sw.centre, sw.extent,
-                                  sw.W, sw.H) for a in angles]
-    ks = api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))["keys"]
+    pos, nrm, rad, gv, prm, geom = _gpu_geometry(wl)
+    E, sig = api.rcs_sweep(api.SweepArgs.from_sweep(wl.sweep), pos, nrm, rad, geom, prm)
     api.stream_check()
-    assert _sampled_keys_match(sc, gv, kg, 200, 3) > 200
-    assert _sampled_keys_match(sc, views, ks, 200, 4) > 100
+    S, ogv, ogf, eps = _oracle_geometry(wl)
+    return dict(wl=wl, pos=pos, nrm=nrm, rad=rad, gv=gv, prm=prm, geom=geom, E=E, sig=sig,
+                S=S, eps=eps)
+
+
+def test_composite_full_splats_bitexact(composite_full):
+    assert composite_full["S"].ns > 40_000
+    _splats_equal(composite_full["geom"], composite_full["S"])
+
+
+def test_composite_full_traces_mb5_per_angle(composite_full):
+    # two angles of the 72-angle sweep, every one of the 2048^2 rays, up to
+    # five bounces through splats fused from PCA normals of noisy points
+    rows = _sweep_parity(composite_full["wl"], composite_full, [0, 9], "composite")
+    assert sum(r["multi"] for r in rows) > 100_000
