@@ -19,7 +19,7 @@ from ._lib import PeGeom, PeHits, PeParams, PeSweep, PeView, check
 
 __all__ = ["view_from_angles", "make_params", "build_gfb", "aggregate_views", "alloc_hits",
            "trace_bounces", "po_field", "rcs_sweep", "stream_check", "Geom", "Hits",
-           "point_attributes", "build_gfb_topk", "po_field_bistatic",
+           "point_attributes", "build_gfb_topk", "po_field_bistatic", "po_field_every_bounce",
            "views_to_array", "workspace"]
 
 
@@ -276,6 +276,28 @@ def po_field(hits: Hits, n_groups: int, rays_per_group: int, ks: np.ndarray,
     check(_lib().pe_po_field(C.byref(hits.c), n_groups, rays_per_group,
                              ks.ctypes.data_as(C.c_void_p), fr.ctypes.data_as(C.c_void_p),
                              fr.shape[0], _p(ws), ws_bytes, _p(E), _s(stream)), "pe_po_field")
+    return E
+
+
+def po_field_every_bounce(views: Sequence[PeView], keys: Optional[torch.Tensor],
+                          nrm: Optional[torch.Tensor], geom: "Geom", params: PeParams,
+                          max_bounces: int, freqs_hz: np.ndarray, stream=None) -> torch.Tensor:
+    """PO at every bounce (``pe_po_field_every_bounce``): float64
+    [n_views, F, 2 pol, 3, re/im]."""
+    n = len(views)
+    arr = views_to_array(views)
+    fr = np.ascontiguousarray(freqs_hz, dtype=np.float64).ravel()
+    dev = geom.blob.device
+    ws_bytes = _lib().pe_po_field_every_bounce_workspace(arr, n, fr.shape[0])
+    if ws_bytes == 0:
+        raise ValueError("pe_po_field_every_bounce: invalid views or frequencies")
+    ws = workspace(ws_bytes, dev)
+    E = torch.empty((n, fr.shape[0], 2, 3, 2), dtype=torch.float64, device=dev)
+    check(_lib().pe_po_field_every_bounce(arr, n, _p(keys), _p(nrm), C.byref(geom.c),
+                                          int(max_bounces), C.byref(params),
+                                          fr.ctypes.data_as(C.c_void_p), fr.shape[0], _p(ws),
+                                          ws_bytes, _p(E), _s(stream)),
+          "pe_po_field_every_bounce")
     return E
 
 

@@ -498,3 +498,113 @@ extern "C" pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups,
   }
   return PE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// PO at every bounce: Eq. 14 applied at each hit of a ray instead of its last
+// one.  For b = 1..max_bounces the rays are traced to b bounces; those whose
+// b-th hit is their last (M == b) contribute Eq. 14 at that hit, with Psi
+// tested toward the monostatic receiver; the b fields are summed in b order.
+// ---------------------------------------------------------------------------
+
+namespace {
+struct every_ws {
+  pe_hits h;
+  uint8_t *psi;
+  double *Eb;
+  char *po;
+  size_t po_bytes;
+};
+
+every_ws carve_every(pe_carve &c, int32_t n_views, int64_t per, int32_t n_freq) {
+  every_ws w;
+  memset(&w, 0, sizeof(w));
+  const int64_t n = per * n_views;
+  w.h.p = c.take<float>((size_t)n * 3);
+  w.h.n = c.take<float>((size_t)n * 3);
+  w.h.k = c.take<float>((size_t)n * 3);
+  w.h.u = c.take<float>((size_t)n * 3);
+  w.h.v = c.take<float>((size_t)n * 3);
+  w.h.path = c.take<double>((size_t)n);
+  w.h.M = c.take<int32_t>((size_t)n);
+  w.h.psi = c.take<uint8_t>((size_t)n);
+  w.h.ids = nullptr;
+  w.h.n_rays = n;
+  w.psi = c.take<uint8_t>((size_t)n);
+  w.Eb = c.take<double>((size_t)n_views * n_freq * 12);
+  w.po_bytes = pe_po_ws_bytes(n_views, per, n_freq);
+  w.po = c.take<char>(w.po_bytes);
+  return w;
+}
+
+// E[i] += Eb[i] (one FP64 addition per element, in bounce order).
+__global__ void field_add_kernel(double *__restrict__ E, const double *__restrict__ Eb, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    E[i] = __dadd_rn(E[i], Eb[i]);
+}
+}  // namespace
+
+extern "C" size_t pe_po_field_every_bounce_workspace(int32_t n_views, const pe_view *views,
+                                                     int32_t n_freq) {
+  if (n_views < 1 || n_views > PE_MAX_BATCH || !views || n_freq < 1) return 0;
+  pe_carve c{nullptr, 0};
+  carve_every(c, n_views, (int64_t)views[0].W * views[0].H, n_freq);
+  return c.bytes() + 256;
+}
+
+extern "C" pe_status pe_po_field_every_bounce(const pe_view *views, int32_t n_views,
+                                              const uint64_t *keys, const float *nrm,
+                                              const pe_geom *geom, int32_t max_bounces,
+                                              const pe_params *prm, const double *freqs,
+                                              int32_t n_freq, void *ws, size_t ws_bytes,
+                                              double *E, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!views || n_views < 1 || n_views > PE_MAX_BATCH || !prm || !geom || !freqs || !E ||
+      n_freq < 1 || max_bounces < 1 || max_bounces > 64 || !(prm->eps >= 0.0f))
+    return pe_fail(PE_EINVAL, "pe_po_field_every_bounce: bad arguments");
+  for (int i = 1; i < n_views; ++i)
+    if (views[i].W != views[0].W || views[i].H != views[0].H)
+      return pe_fail(PE_EINVAL, "pe_po_field_every_bounce: all screens must share W x H");
+  const int64_t per = (int64_t)views[0].W * views[0].H;
+  if (per < 1 || per * n_views >= (int64_t)PE_NONE)
+    return pe_fail(PE_EINVAL, "pe_po_field_every_bounce: screen size");
+  if (!prm->first_bounce_from_geom && (!keys || !nrm))
+    return pe_fail(PE_EINVAL, "pe_po_field_every_bounce: bounce 1 from the GFB needs keys and nrm");
+  for (int f = 0; f < n_freq; ++f)
+    if (!(freqs[f] > 0))
+      return pe_fail(PE_EINVAL, "pe_po_field_every_bounce: frequencies must be > 0");
+  const size_t need = pe_po_field_every_bounce_workspace(n_views, views, n_freq);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_po_field_every_bounce: workspace needs %zu bytes", need);
+  pe_carve c{static_cast<char *>(ws), 0};
+  every_ws w = carve_every(c, n_views, per, n_freq);
+  pe_view_batch vb;
+  memset(&vb, 0, sizeof(vb));
+  vb.n = n_views;
+  vb.W = views[0].W;
+  vb.H = views[0].H;
+  float dirs[PE_MAX_BATCH * 3];
+  for (int i = 0; i < n_views; ++i) {
+    vb.v[i] = views[i];
+    for (int k = 0; k < 3; ++k) dirs[3 * i + k] = -views[i].d[k];
+  }
+  const int64_t nE = (int64_t)n_views * n_freq * 12;
+  for (int b = 1; b <= max_bounces; ++b) {
+    pe_hits h = w.h;
+    h.max_bounces = b;
+    pe_status st = pe_launch_trace(vb, reinterpret_cast<const unsigned long long *>(keys), nrm,
+                                   geom, b, *prm, h, nullptr, s);
+    if (st != PE_OK) return st;
+    st = pe_launch_shadow_dirs(geom, h, n_views, per, dirs, prm->eps, b, w.psi, nullptr, s);
+    if (st != PE_OK) return st;
+    h.psi = w.psi;
+    st = pe_launch_po(h, n_views, per, dirs, freqs, n_freq, w.po, w.po_bytes, b == 1 ? E : w.Eb,
+                      s);
+    if (st != PE_OK) return st;
+    if (b > 1) {
+      field_add_kernel<<<(int)((nE + 255) / 256), 256, 0, s>>>(E, w.Eb, nE);
+      PE_TRY_LAUNCH("field_add_kernel");
+    }
+  }
+  return PE_OK;
+}

@@ -40,17 +40,9 @@ def build_geometry(pos, nrm, rad, gviews: Sequence[PeView], params: PeParams, st
 
 
 def field_every_bounce(views, keys, nrm, geom, prm, mb: int, freqs_hz, stream=None):
-    """PO at every bounce (instead of Eq. 14's last hit): for b = 1..mb the
-    rays traced to b bounces whose b-th hit is their last contribute Eq. 14
-    at that hit, Psi tested toward the monostatic receiver; the b fields are
-    summed.  Returns float64 [n_views, F, 2 pol, 3, re/im]."""
-    n = len(views)
-    per = views[0].W * views[0].H
-    obs = np.array([[[-x for x in v.d]] for v in views], np.float32)
-    E = None
-    for b in range(1, mb + 1):
-        h = api.trace_bounces(views, keys, nrm, geom, b, prm, ids=False, stream=stream)
-        Eb = api.po_field_bistatic(h, n, per, obs, geom, prm.eps, freqs_hz, only_bounce=b,
-                                   stream=stream)[:, 0]
-        E = Eb if E is None else E + Eb
-    return E
+    """PO at every bounce (instead of Eq. 14's last hit), one library call
+    (``pe_po_field_every_bounce``): for b = 1..mb the rays traced to b
+    bounces whose b-th hit is their last contribute Eq. 14 at that hit, Psi
+    tested toward the monostatic receiver; the b fields are summed in the
+    library.  Returns float64 [n_views, F, 2 pol, 3, re/im]."""
+    return api.po_field_every_bounce(views, keys, nrm, geom, prm, mb, freqs_hz, stream=stream)
