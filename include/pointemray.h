@@ -390,6 +390,27 @@ pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups, int64_t ra
                                int32_t n_freq, void *ws, size_t ws_bytes, double *E_dev,
                                void *stream);
 
+/* PO at every bounce (the variant of Eq. 14 that applies it at each hit of a
+ * ray, not only at the last; Sec. II-C, Eq. 14, Alg. 3).  For each b =
+ * 1..max_bounces the n_views monostatic screens are traced to b bounces
+ * (bounce 1 from the GFB keys, or from the geometry when
+ * prm->first_bounce_from_geom), the rays whose b-th hit is their last
+ * (M == b) are shadow-tested toward the screen's own transmitter (-d) from
+ * that hit, and Eq. 14 is summed over them; the b fields are added in
+ * increasing b (one FP64 addition each, so the result is deterministic).
+ * views: host [n_views] screens of one W x H; keys: device uint64
+ * [n_views][H][W] from pe_build_gfb (NULL with first_bounce_from_geom); nrm:
+ * device [N][3]; geom: the aggregated splats (required); freqs_hz: host
+ * [n_freq] > 0.  E_dev: device float64 [n_views][n_freq][2 pol][3][re, im],
+ * overwritten.  ws: device, 256-byte aligned, of
+ * pe_po_field_every_bounce_workspace() bytes (0 = invalid arguments).
+ * Errors: PE_EINVAL (arguments), PE_ENOMEM (workspace), PE_ECUDA. */
+size_t pe_po_field_every_bounce_workspace(int32_t n_views, const pe_view *views, int32_t n_freq);
+pe_status pe_po_field_every_bounce(const pe_view *views, int32_t n_views, const uint64_t *keys,
+                                   const float *nrm, const pe_geom *geom, int32_t max_bounces,
+                                   const pe_params *prm, const double *freqs_hz, int32_t n_freq,
+                                   void *ws, size_t ws_bytes, double *E_dev, void *stream);
+
 /* pe_po_field without a workspace -- for callers that cannot allocate device
  * memory for the library (their memory belongs to a host application's own
  * pool, or allocation is not allowed where they call from).  The paper has no
@@ -400,7 +421,10 @@ pe_status pe_po_field_bistatic(const pe_hits *hits, int32_t n_groups, int64_t ra
  * need more than 16 MiB (pe_po_workspace() - 256 > 16 MiB) return PE_EINVAL
  * with a message.  The first call on each device looks up the array's device
  * address (cudaGetSymbolAddress, once per device, with that device current);
- * make that first call before any stream capture.  All calls share the one
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: after a cudaDeviceReset() on a device, do not call
+ * this entry point on that device again (the kept address belongs to the
+ * destroyed context).  All calls share the one
  * array: calls whose work overlaps on the GPU (different streams, or
  * different host threads on the same device) race and corrupt each other's
  * results; serialise them.  Nothing in the array needs clearing between
@@ -481,6 +505,15 @@ size_t pe_nn_gemm_workspace(int32_t M, int32_t N, int64_t K);
  * needed, else the mma.sync kernel (default); 1 = the mma.sync kernel only.
  * Both give the same result up to FP32 summation order. */
 int32_t pe_nn_gemm_path(int32_t path);
+/* Diagnostics (no counterpart in the paper): the number of polls each
+ * bounded mbarrier wait of the tcgen05 GEMM's main loop and epilogue makes
+ * before it gives up (process-wide; polls < 0 restores the default of 2^22,
+ * 0 makes every such wait give up at once).  A wait that gives up skips the
+ * rest of the tile, waits (with the default limit) for the copies and
+ * products it has issued, frees its tensor memory and sets the status word:
+ * the next pe_stream_check() returns PE_ETIMEOUT and clears it, and later
+ * calls run normally.  For tests of that path; PE_EINVAL above 2^32 - 1. */
+pe_status pe_nn_set_wait_limit(int64_t polls);
 pe_status pe_nn_gemm(int32_t M, int32_t N, int64_t K, const void *A, int64_t sam, int64_t sak,
                      const void *B, int64_t sbk, int64_t sbn, void *C, int64_t ldc,
                      int32_t c_f32, const float *bias, const void *R, int64_t ldr, void *Z,

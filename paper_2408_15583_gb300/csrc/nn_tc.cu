@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "nn_gemm.cuh"
@@ -76,10 +77,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the phase with the given parity to complete: at most
+// `limit` polls (each mbarrier.try_wait may itself suspend the thread for a
+// short, system-dependent time); false if the phase has not completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t limit = kWaitLimit) {
   const uint32_t a = sm_u32(bar);
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -142,7 +146,10 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 3)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const pe_gemm_args g, int stages, unsigned int *err) {
+                   const pe_gemm_args g, int stages, uint32_t wait_limit, unsigned int *err) {
+  // wait_limit bounds the waits of the main loop and of the epilogue; the
+  // clean-up after a failed wait always waits the full kWaitLimit for the
+  // copies and products already issued (they complete in microseconds)
   using cfg = tc_cfg<BN>;
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
@@ -187,7 +194,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % stages;
       const uint32_t ph = (uint32_t)(kb / stages) & 1u;
-      if (!mbar_wait(empty + s, ph ^ 1u)) {
+      if (!mbar_wait(empty + s, ph ^ 1u, wait_limit)) {
         atomicOr(&s_fail, 1);
         break;
       }
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
     for (; kb < nk; ++kb) {
       const int s = kb % stages;
       const uint32_t ph = (uint32_t)(kb / stages) & 1u;
-      if (!mbar_wait(full + s, ph)) {
+      if (!mbar_wait(full + s, ph, wait_limit)) {
         atomicOr(&s_fail, 1);
         break;
       }
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS, 3)
   // is free once every product has completed), then all threads write
   // coalesced rows.  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31
   // (its rows) for half of the columns.
-  const bool ready = mbar_wait(accum, 0u);
+  const bool ready = mbar_wait(accum, 0u, wait_limit);
   if (!ready) atomicOr(&s_fail, 1);
   tc_fence_after();
   __syncwarp();
@@ -314,6 +321,9 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int64_
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Polls of the kernel's main-loop waits (pe_nn_set_wait_limit).
+std::atomic<uint32_t> g_wait_limit{kWaitLimit};
+
 template <int BN>
 pe_status launch_bn(const pe_gemm_args &g, cudaStream_t s) {
   using cfg = tc_cfg<BN>;
@@ -337,7 +347,8 @@ pe_status launch_bn(const pe_gemm_args &g, cudaStream_t s) {
     attr = true;
   }
   dim3 grid((unsigned)((g.M + TC_BM - 1) / TC_BM), (unsigned)((g.N + BN - 1) / BN));
-  gemm_tc_kernel<BN><<<grid, TC_THREADS, smem, s>>>(ma, mb, g, stages, pe_err_word());
+  gemm_tc_kernel<BN><<<grid, TC_THREADS, smem, s>>>(ma, mb, g, stages, g_wait_limit.load(),
+                                                     pe_err_word());
   PE_TRY_LAUNCH("gemm_tc_kernel");
   return PE_OK;
 }
@@ -355,4 +366,10 @@ pe_status pe_gemm_tc(const pe_gemm_args &g, cudaStream_t s) {
   if (g.N <= 64) return launch_bn<64>(g, s);
   if (g.N <= 128) return launch_bn<128>(g, s);
   return launch_bn<256>(g, s);
+}
+
+extern "C" pe_status pe_nn_set_wait_limit(int64_t polls) {
+  if (polls > (int64_t)UINT32_MAX) return pe_fail(PE_EINVAL, "pe_nn_set_wait_limit: at most 2^32 - 1");
+  g_wait_limit.store(polls < 0 ? kWaitLimit : (uint32_t)polls);
+  return PE_OK;
 }

@@ -82,6 +82,43 @@ def test_gemm_layouts(M, N, K, gemm_path):
     assert rel(out2, ref) < 1e-5
 
 
+def test_tcgen05_gemm_waits_give_up_report_a_timeout_and_recover():
+    """The tcgen05 GEMM's bounded mbarrier waits: with a limit of zero polls
+    every main-loop wait gives up at once; the kernel skips its tiles (the
+    output keeps its contents), frees its tensor memory and sets the status
+    word, so pe_stream_check returns PE_ETIMEOUT (and clears it); with the
+    default limit restored the same call computes the product."""
+    from paper_2408_15583_gb300 import _lib
+    lib = _lib.load()
+    o = ops()
+    M, N, K = 256, 64, 128
+    g = torch.Generator().manual_seed(7)
+    A = bf(torch.randn(M, K, generator=g))
+    B = bf(torch.randn(K, N, generator=g))
+    ref = A.double() @ B.double()
+    Ad, Bt = A.to(DEV), B.t().contiguous().to(DEV)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    prev = lib.pe_nn_gemm_path(0)
+    try:
+        assert lib.pe_nn_set_wait_limit(0) == 0
+        out = torch.zeros(M, N, dtype=torch.float32, device=DEV)
+        o.gemm(M, N, K, Ad, K, 1, Bt, 1, K, out, N)
+        assert lib.pe_stream_check(stream) == 4            # PE_ETIMEOUT
+        assert b"bounded device wait" in lib.pe_last_error()
+        assert torch.count_nonzero(out) == 0
+        assert lib.pe_stream_check(stream) == 0            # the status word was cleared
+    finally:
+        lib.pe_nn_set_wait_limit(-1)
+    try:
+        out = torch.zeros(M, N, dtype=torch.float32, device=DEV)
+        o.gemm(M, N, K, Ad, K, 1, Bt, 1, K, out, N)
+        assert lib.pe_stream_check(stream) == 0
+        assert rel(out, ref) < 1e-5
+    finally:
+        lib.pe_nn_gemm_path(prev)
+    assert lib.pe_nn_set_wait_limit(1 << 33) == 1          # PE_EINVAL
+
+
 @pytest.fixture(params=[0, 1], ids=["tcgen05-where-it-applies", "mma.sync-only"])
 def gemm_path(request):
     from paper_2408_15583_gb300 import _lib
