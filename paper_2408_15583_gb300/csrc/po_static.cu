@@ -22,7 +22,9 @@
 static __device__ __align__(256) double g_po_scratch[PE_PO_STATIC_DOUBLES];
 
 // Device address of g_po_scratch for the current device, looked up once per
-// device (the host-side name of the array is not a device address).
+// device (the host-side name of the array is not a device address) and kept
+// for the life of the process; a cudaDeviceReset() destroys the context the
+// address belongs to, so the header rules out calls after a reset.
 static double *po_scratch_address() {
   static std::mutex mu;
   static double *addr[64] = {nullptr};
