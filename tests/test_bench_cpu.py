@@ -30,3 +30,13 @@ def test_alu_peak_from_the_sampled_clock():
     v2, how2 = bench.alu_peak(1455.0)
     assert v2 == pytest.approx(v * 1455.0 / 2070.0)
     assert bench.alu_peak(None)[0] == pytest.approx(v)             # maximum clock when unsampled
+
+
+def test_oracle_query_count_matches_the_device_counters_rule():
+    # 6 screen rays, mb = 3: M = 0 (primary miss), 1 (bounce-2 query misses),
+    # 2 (bounce-3 query misses, shadow ray), 3 (stops at mb, shadow ray)
+    M = [0, 1, 2, 3, 3, 1]
+    # primary 6; bounce 2: rays with M >= 1 (5); bounce 3: rays with M >= 2
+    # (3); shadow rays: M >= 2 (3)
+    assert bench._angle_queries(M, 3, 6) == 6 + 5 + 3 + 3
+    assert bench._angle_queries([1, 0], 1, 2) == 2

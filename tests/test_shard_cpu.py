@@ -71,3 +71,65 @@ def test_one_rank_is_the_plain_sweep():
         shard.rank_angles(sw.theta_deg, sw.phi_deg, 2, 2)
     assert shard.phi_step([45.0]) == 1.0
     assert shard.phi_step(np.arange(0.0, 360.0, 5.0)) == 5.0
+
+
+def _rank_oracle_main(rank, world, port, out_dir):
+    # each rank builds the fused geometry from the same points (the shared
+    # read-only input) and runs the CPU oracle's sweep over its own angles;
+    # the ranks' fields are gathered over gloo
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sc, sw0 = _tiny_sweep()
+        th, ph = shard.rank_angles(sw0.theta_deg, sw0.phi_deg, rank, world)
+        sw = scenes.Sweep(theta_deg=th, phi_deg=ph, W=sw0.W, H=sw0.H, centre=sw0.centre,
+                          extent=sw0.extent, freqs_hz=sw0.freqs_hz, max_bounces=sw0.max_bounces)
+        S, gv, _, _ = oracle.build_geometry(sc, scenes.aggregation_views(sc, 48, 48), "fp32")
+        eps = oracle.default_eps(gv)
+        res = oracle.rcs_sweep(sc, sw, S, eps, eps, mode="fp32")
+        mine = torch.from_numpy(np.stack([res.E.real, res.E.imag], -1).copy())
+        parts = [torch.empty_like(mine) for _ in range(world)]
+        dist.all_gather(parts, mine)
+        angs = torch.from_numpy(np.stack([th, ph], 1).copy())
+        aparts = [torch.empty_like(angs) for _ in range(world)]
+        dist.all_gather(aparts, angs)
+        if rank == 0:
+            np.savez(os.path.join(out_dir, "gathered.npz"),
+                     E=np.concatenate([p.numpy() for p in parts]),
+                     ang=np.concatenate([a.numpy() for a in aparts]))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def _tiny_sweep():
+    sc = scenes.dihedral(1500, seed=19)
+    sw = scenes._sweep_over(sc, [90.0, 90.0, 90.0], [0.0, 30.0, 60.0], 24, [3e9, 3.3e9], 2)
+    return sc, sw
+
+
+def test_two_gloo_ranks_run_the_oracle_on_their_shards():
+    # the union of the ranks' fields, gathered, equals one process's sweep
+    # over the union of their angles, bit for bit (angles are independent
+    # problems over the same fused geometry)
+    import torch.multiprocessing as mp
+    import oracle
+    world = 2
+    with tempfile.TemporaryDirectory() as d:
+        mp.spawn(_rank_oracle_main, args=(world, _free_port(), d), nprocs=world, join=True)
+        g = np.load(os.path.join(d, "gathered.npz"))
+    sc, sw0 = _tiny_sweep()
+    ang = g["ang"]
+    assert len(np.unique(ang[:, 1])) == world * sw0.n_angles
+    sw = scenes.Sweep(theta_deg=ang[:, 0], phi_deg=ang[:, 1], W=sw0.W, H=sw0.H,
+                      centre=sw0.centre, extent=sw0.extent, freqs_hz=sw0.freqs_hz,
+                      max_bounces=sw0.max_bounces)
+    S, gv, _, _ = oracle.build_geometry(sc, scenes.aggregation_views(sc, 48, 48), "fp32")
+    eps = oracle.default_eps(gv)
+    ref = oracle.rcs_sweep(sc, sw, S, eps, eps, mode="fp32")
+    E = g["E"][..., 0] + 1j * g["E"][..., 1]
+    assert np.abs(ref.E).max() > 0
+    assert np.array_equal(E, ref.E)
