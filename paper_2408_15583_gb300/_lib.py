@@ -81,7 +81,7 @@ SIGNATURES = {
     "pe_nn_set_wait_limit": (C.c_int, [C.c_int64]),
     "pe_point_attributes_workspace": (C.c_size_t, [C.c_int64]),
     "pe_po_field_bistatic_workspace": (C.c_size_t, [C.c_int32, C.c_int64, C.c_int32]),
-    "pe_po_field_every_bounce_workspace": (C.c_size_t, [P, C.c_int32, C.c_int32]),
+    "pe_po_field_every_bounce_workspace": (C.c_size_t, [C.c_int32, P, C.c_int32]),
     "pe_po_field_every_bounce": (C.c_int, [P, C.c_int32, P, P, P, C.c_int32, P, P, C.c_int32, P,
                                            C.c_size_t, P, P]),
     "pe_po_field_bistatic": (C.c_int, [P, C.c_int32, C.c_int64, P, C.c_int32, P, C.c_float,

@@ -288,7 +288,7 @@ def po_field_every_bounce(views: Sequence[PeView], keys: Optional[torch.Tensor],
     arr = views_to_array(views)
     fr = np.ascontiguousarray(freqs_hz, dtype=np.float64).ravel()
     dev = geom.blob.device
-    ws_bytes = _lib().pe_po_field_every_bounce_workspace(arr, n, fr.shape[0])
+    ws_bytes = _lib().pe_po_field_every_bounce_workspace(n, arr, fr.shape[0])
     if ws_bytes == 0:
         raise ValueError("pe_po_field_every_bounce: invalid views or frequencies")
     ws = workspace(ws_bytes, dev)

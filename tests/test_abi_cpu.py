@@ -77,6 +77,12 @@ def test_workspace_queries(lib):
     assert sw.workspace_bytes() > 3 * 1024 * 1024 * 80
     bad = api.SweepArgs([90.0], [0.0], 1024, 1024, [0, 0, 0], -1.0, [1e9], 2)
     assert bad.workspace_bytes() == 0
+    # PO at every bounce: hit records of every ray, a second Psi, the
+    # per-bounce field and the PO partial sums
+    eb = lib.pe_po_field_every_bounce_workspace(8, arr, 64)
+    assert eb >= 8 * 512 * 512 * (60 + 8 + 4 + 1 + 1) + 8 * 64 * 12 * 8
+    assert lib.pe_po_field_every_bounce_workspace(0, arr, 64) == 0
+    assert lib.pe_po_field_every_bounce_workspace(8, arr, 0) == 0
 
 
 def test_argument_errors_before_any_device_work(lib):
@@ -108,6 +114,10 @@ def test_argument_errors_before_any_device_work(lib):
     assert b"W x H" in lib.pe_last_error()
     assert lib.pe_trace_bounces(v, 1, None, None, None, 0, None, None, 0, None, None, None) == 1
     assert lib.pe_po_field(None, 1, 1, None, None, 1, None, 0, None, None) == 1
+    fr = (C.c_double * 1)(3e9)
+    assert lib.pe_po_field_every_bounce(mixed, 2, None, None, None, 2, C.byref(prm), fr, 1,
+                                        None, 0, None, None) == 1
+    assert lib.pe_nn_set_wait_limit(1 << 33) == 1
 
 
 def test_probe_arguments_rejected_before_any_device_work(lib):
