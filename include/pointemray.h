@@ -112,7 +112,9 @@ typedef struct {
  * rays only descend the pyramids of views met along their path.
  * Layout is fully determined by the views; use pe_geom_bytes() to size it.
  * vgrid_* are written by pe_aggregate_views (callers leave them zero). */
+#ifndef PE_VGRID
 #define PE_VGRID 32
+#endif
 typedef struct {
   int32_t n_views;
   pe_view views[PE_MAX_VIEWS];

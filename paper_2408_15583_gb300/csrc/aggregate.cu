@@ -520,6 +520,112 @@ __global__ void pyramid_up_kernel(const __grid_constant__ pe_geom_layout L, int 
   }
 }
 
+// Node slabs: for the pyramid nodes of levels 0..kSlabLevels-1 (up to
+// 64 x 64 pixels), an axis n (the normalised sum of the node's splat
+// normals, each turned toward its view) and the interval of heights
+// n . (x - view origin) that the points x of the node's disks take: a disk
+// (c, R, normal m) spans n . (c - o) +- R sqrt(1 - (n . m)^2), padded by
+// 1e-6 under the root (the rounding of m) and by the view's absolute box
+// pad.  Over a smooth patch the slab is far thinner than the node's box, so
+// a ray that leaves the patch is rejected as soon as it is above the slab.
+// One warp per node (all those levels of all views in one launch), sums in
+// a fixed order, so the slabs are the same on every run.  Higher nodes, a
+// node without splats and a node whose normals cancel get no slab (lower
+// bound -inf).
+constexpr int kSlabLevels = 5;
+
+__global__ void __launch_bounds__(128)
+    pyramid_slab_kernel(const __grid_constant__ pe_geom_layout L, int64_t n_slab_nodes,
+                        float4 *__restrict__ slab, float *__restrict__ slab_hi) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n_slab_nodes) return;  // uniform over the warp
+  // warp w -> (view, level, node): views in order, levels 0.. within each
+  int v = 0, l = 0;
+  int64_t k = w;
+  for (v = 0; v < L.nv; ++v) {
+    bool found = false;
+    for (l = 0; l < min(L.nlev[v], kSlabLevels); ++l) {
+      const int64_t cnt = (int64_t)L.tw[v][l] * L.th[v][l];
+      if (k < cnt) {
+        found = true;
+        break;
+      }
+      k -= cnt;
+    }
+    if (found) break;
+  }
+  const int64_t nid = L.node_off[v][l] + k;
+  const pe_view &V = L.view[v];
+  const int tx = (int)(k % L.tw[v][l]), ty = (int)(k / L.tw[v][l]);
+  const int span = PE_LEAF << l;
+  const int i0 = tx * span, j0 = ty * span;
+  const int iw = min(span, V.W - i0), jh = min(span, V.H - j0);
+  const int npx = iw * jh;
+  const float4 *cr = L.cr + L.pix_off[v];
+  const float4 *nf = L.nf + L.pix_off[v];
+  // pass 1: the axis
+  float sx = 0.f, sy = 0.f, sz = 0.f, cnt = 0.f;
+  for (int q = lane; q < npx; q += 32) {
+    const int64_t g = (int64_t)(j0 + q / iw) * V.W + (i0 + q % iw);
+    if (!(cr[g].w > 0.0f)) continue;
+    const float4 m = nf[g];
+    const float sg = (m.x * V.d[0] + m.y * V.d[1] + m.z * V.d[2]) > 0.0f ? -1.0f : 1.0f;
+    sx += sg * m.x;
+    sy += sg * m.y;
+    sz += sg * m.z;
+    cnt += 1.0f;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(FULL, sx, o);
+    sy += __shfl_xor_sync(FULL, sy, o);
+    sz += __shfl_xor_sync(FULL, sz, o);
+    cnt += __shfl_xor_sync(FULL, cnt, o);
+  }
+  const float len = sqrtf(sx * sx + sy * sy + sz * sz);
+  if (!(cnt > 0.0f) || !(len > 1e-3f * cnt)) {
+    if (lane == 0) {
+      slab[nid] = make_float4(0.f, 0.f, 1.f, -INFINITY);
+      slab_hi[nid] = INFINITY;
+    }
+    return;
+  }
+  const float nx = sx / len, ny = sy / len, nz = sz / len;
+  // pass 2: the heights
+  const float pad = L.pad[v];
+  float lo = INFINITY, hi = -INFINITY;
+  for (int q = lane; q < npx; q += 32) {
+    const int64_t g = (int64_t)(j0 + q / iw) * V.W + (i0 + q % iw);
+    const float4 c = cr[g];
+    if (!(c.w > 0.0f)) continue;
+    const float4 m = nf[g];
+    const float h = nx * (c.x - V.o[0]) + ny * (c.y - V.o[1]) + nz * (c.z - V.o[2]);
+    const float nm = nx * m.x + ny * m.y + nz * m.z;
+    const float e = c.w * 1.000001f * sqrtf(fmaxf(1.0f - nm * nm, 0.0f) + 1e-6f) + pad;
+    lo = fminf(lo, h - e);
+    hi = fmaxf(hi, h + e);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
+  }
+  if (lane == 0) {
+    slab[nid] = make_float4(nx, ny, nz, lo - pad);
+    slab_hi[nid] = hi + pad;
+  }
+}
+
+// No slab for the nodes above kSlabLevels.
+__global__ void slab_clear_kernel(float4 *__restrict__ slab, float *__restrict__ slab_hi,
+                                  int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    slab[i] = make_float4(0.f, 0.f, 1.f, -INFINITY);
+    slab_hi[i] = INFINITY;
+  }
+}
+
 // Coarse view-occupancy grid: every splat marks, with its owner view's bit,
 // the cells its disk's bounding box overlaps (per world axis k the disk
 // reaches R sqrt(1 - n_k^2) from its centre), padded by 1 % of a cell and for
@@ -640,8 +746,8 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   for (int v = 0; v < n_views; ++v)
     if (memcmp(&out->views[v], &views[v], sizeof(pe_view)) != 0)
       return pe_fail(PE_EINVAL, "pe_aggregate_views: out->views differ from views");
-  size_t o_cr, o_nf, o_nodes, o_vm, tot;
-  pe_layout_offsets(L, &o_cr, &o_nf, &o_nodes, &o_vm, &tot);
+  size_t o_cr, o_nf, o_nodes, o_vm, o_slab, o_slab_hi, tot;
+  pe_layout_offsets(L, &o_cr, &o_nf, &o_nodes, &o_vm, &o_slab, &o_slab_hi, &tot);
   if (out->blob_bytes < tot || !pe_aligned(out->blob_dev, 256))
     return pe_fail(PE_ENOMEM, "pe_aggregate_views: geometry blob needs %zu bytes", tot);
   size_t need = pe_aggregate_workspace(n_views, views, G);
@@ -653,6 +759,8 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   float4 *nf = reinterpret_cast<float4 *>(blob + o_nf);
   float4 *nodes = reinterpret_cast<float4 *>(blob + o_nodes);
   uint32_t *vmask = reinterpret_cast<uint32_t *>(blob + o_vm);
+  float4 *slab = reinterpret_cast<float4 *>(blob + o_slab);
+  float *slab_hi = reinterpret_cast<float *>(blob + o_slab_hi);
   L.cr = cr;
   L.nf = nf;
   L.nodes = nodes;
@@ -739,5 +847,13 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
       PE_TRY_LAUNCH("pyramid_up_kernel");
     }
   }
+  slab_clear_kernel<<<grid_for(L.n_nodes, 256, cap), 256, 0, s>>>(slab, slab_hi, L.n_nodes);
+  PE_TRY_LAUNCH("slab_clear_kernel");
+  int64_t n_slab = 0;
+  for (int v = 0; v < n_views; ++v)
+    for (int l = 0; l < L.nlev[v] && l < kSlabLevels; ++l) n_slab += (int64_t)L.tw[v][l] * L.th[v][l];
+  pyramid_slab_kernel<<<(unsigned)((n_slab * 32 + 127) / 128), 128, 0, s>>>(L, n_slab, slab,
+                                                                          slab_hi);
+  PE_TRY_LAUNCH("pyramid_slab_kernel");
   return PE_OK;
 }

@@ -87,6 +87,11 @@ struct pe_geom_layout {
   const float4 *cr;         // splat centre, radius
   const float4 *nf;         // splat normal, count
   const float4 *nodes;      // [n_nodes][2] lo, hi in (u, v, d) frame
+  // [n_nodes]: a slab bounding every disk below the node, {axis, lower
+  // bound} with the upper bound in slab_hi; heights n . (x - view origin);
+  // lower bound -inf: no slab for that node
+  const float4 *slab;
+  const float *slab_hi;
   // coarse view-occupancy grid: vmask[(ix*n + iy)*n + iz], vmask[n^3] = views
   // with splats outside the grid; n = 0: no grid (walk every view)
   const uint32_t *vmask;
@@ -104,7 +109,8 @@ pe_status pe_exclusive_scan_u32(const uint32_t *in, int64_t n, uint32_t *tile, u
                                 cudaStream_t s);
 // Blob byte offsets of the arrays for a layout.
 void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
-                       size_t *off_nodes, size_t *off_vmask, size_t *total);
+                       size_t *off_nodes, size_t *off_vmask, size_t *off_slab,
+                       size_t *off_slab_hi, size_t *total);
 
 // ---------------------------------------------------------------------------
 // Launchers shared between entry points

@@ -38,6 +38,9 @@ struct po_consts {
   float e1[kPoGroups][3], e2[kPoGroups][3];  // orthonormal basis across ks
   float k[kPoFreqs];                  // wavenumber (rad/m), for the sinc arguments
   float khi[kPoFreqs], klo[kPoFreqs];  // k / 2 pi = f / c (revolutions/m) as a float pair
+  float k2[kPoFreqs];                  // k^2 (uniform grids: the sinc series variable)
+  float dkhi, dklo;                    // uniform grids: the step of k / 2 pi, a float pair
+  float kmax;                          // the launch's largest k
 };
 
 // sin(x)/x: Taylor series through x^8 for |x| < 0.5 (truncation < 3e-11),
@@ -259,6 +262,258 @@ __global__ void __launch_bounds__(kPoThreads, 4)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Uniform frequency grids (k_f = k_0 + f dk): each thread takes kFt
+// consecutive frequencies of a ray.  The phase factor of its first frequency
+// is computed as above (double-float phase in revolutions, one sincos); the
+// next ones follow by rotation, e^{-j k_{f+1} d} = e^{-j k_f d} e^{-j dk d},
+// with the ray's rotation e^{-j dk d} staged once per ray (re-anchored at
+// every thread's first frequency, so the float32 rotation drifts over at most
+// kFt - 1 steps).  The two sinc factors are one power series in t = k^2:
+// sinc(k a) sinc(k b) = sum_n c_n t^n, whose five coefficients through t^4
+// (x^8 in each factor, truncation below 3e-11 for |k a|, |k b| < 0.5) are
+// staged per ray; a ray with a larger argument anywhere in the launch takes
+// the direct form instead.  Per term: four multiply-adds of the series, four
+// of the rotation, two for the complex amplitude and eight for the sums.
+// ---------------------------------------------------------------------------
+#ifndef PE_PO_FT
+#define PE_PO_FT 2   // frequencies per thread of the rotation kernel
+#endif
+#ifndef PE_PO_SMC
+#define PE_PO_SMC 1  // 1: the compensated sums live in shared memory, not registers
+#endif
+#ifndef PE_PO_MINB
+#define PE_PO_MINB 3  // resident blocks per SM the rotation kernel's registers allow
+#endif
+#ifndef PE_PO_ROT
+#define PE_PO_ROT 1  // 0: every grid takes the direct kernel
+#endif
+#ifndef PE_PO_JU
+#define PE_PO_JU 1   // rays per unrolled step of the series pass
+#endif
+constexpr int kFt = PE_PO_FT;
+constexpr int kJu = PE_PO_JU;
+
+__device__ __forceinline__ void series_coeffs(float au, float av, float c[4]) {
+  // sinc x = 1 - x^2/6 + x^4/120 - x^6/5040 + x^8/362880; with A = au^2,
+  // B = av^2 the product's coefficients of t^1..t^4 (t^0: 1)
+  const float A = au * au, B = av * av;
+  const float A2 = A * A, B2 = B * B, AB = A * B;
+  c[0] = -(A + B) * (1.0f / 6.0f);
+  c[1] = (A2 + B2) * (1.0f / 120.0f) + AB * (1.0f / 36.0f);
+  c[2] = -(A2 * A + B2 * B) * (1.0f / 5040.0f) - AB * (A + B) * (1.0f / 720.0f);
+  c[3] = (A2 * A2 + B2 * B2) * (1.0f / 362880.0f) + AB * (A2 + B2) * (1.0f / 30240.0f) +
+         AB * AB * (1.0f / 14400.0f);
+}
+
+// One term: the complex amplitude sc e^{-j phase} (pr, pi) into the eight
+// sums b (V[i] x re, im), then the phase factor rotated by the ray's step.
+__device__ __forceinline__ void rot_term(float sc, float4 V, float4 r2, float &pr, float &pi,
+                                         float *b) {
+  const float re = sc * pr, im = sc * pi;
+  b[0] = fmaf(V.x, re, b[0]);
+  b[1] = fmaf(V.x, im, b[1]);
+  b[2] = fmaf(V.y, re, b[2]);
+  b[3] = fmaf(V.y, im, b[3]);
+  b[4] = fmaf(V.z, re, b[4]);
+  b[5] = fmaf(V.z, im, b[5]);
+  b[6] = fmaf(V.w, re, b[6]);
+  b[7] = fmaf(V.w, im, b[7]);
+  const float nr = fmaf(pr, r2.z, -pi * r2.w);
+  pi = fmaf(pr, r2.w, pi * r2.z);
+  pr = nr;
+}
+
+// The reduced phase (revolutions in [-1/2, 1/2] plus the carried low part)
+// of the float-pair product (khi + klo)(dhi + dlo), as in add_term.
+__device__ __forceinline__ float rev_phase(float khi, float klo, float dhi, float dlo) {
+  const float ph = khi * dhi;
+  const float er = fmaf(khi, dhi, -ph) + fmaf(khi, dlo, klo * dhi);
+  return (ph - rintf(ph)) + er;
+}
+
+template <int FT, bool SMC>
+__global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
+    po_rot_kernel(const pe_hits h, const __grid_constant__ po_consts C, double *__restrict__ part) {
+  // SMC: the per-thread compensated sums (hi, lo) in dynamic shared memory,
+  // [2][FT * kAcc][kPoThreads] floats, instead of registers
+  extern __shared__ float s_hl[];
+  // per staged ray: the series {c1..c4}, the area-weighted vector factors
+  // {Va.e1, Va.e2, Vc.e1, Vc.e2}, {dh, dl, rotation re, im}, and the sinc
+  // arguments for the direct form (au, av)
+  __shared__ float4 s_ray[3][kPoThreads];
+  __shared__ float2 s_arg[kPoThreads];
+  __shared__ int s_warp[2 * (kPoThreads / 32)];
+  __shared__ double s_red[kPoThreads][kAcc];
+
+  const int g = blockIdx.y;
+  const int chunk = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int FL = C.fl, RL = kPoThreads / FL;  // frequency-chunk lanes, ray lanes
+  const int lane_f = tid % FL, lane_r = tid / FL;
+  const pe_f3 ks = {C.ks[g][0], C.ks[g][1], C.ks[g][2]};
+  const pe_f3 e1 = {C.e1[g][0], C.e1[g][1], C.e1[g][2]};
+  const pe_f3 e2 = {C.e2[g][0], C.e2[g][1], C.e2[g][2]};
+  const int64_t r_begin = (int64_t)chunk * C.chunk;
+  int64_t r_end = r_begin + C.chunk;
+  if (r_end > C.rpg) r_end = C.rpg;
+  const int64_t slot0 = (int64_t)(C.g0 + g) * C.rpg;
+  const int n_fc = (C.nf + FT - 1) / FT;  // frequency chunks of the launch
+
+  for (int c0 = 0; c0 < n_fc; c0 += FL) {
+    const int f1 = (c0 + lane_f) * FT;  // this thread's first frequency
+    const bool f_ok = f1 < C.nf;
+    float t2[FT];
+#pragma unroll
+    for (int q = 0; q < FT; ++q) t2[q] = f1 + q < C.nf ? C.k2[f1 + q] : 0.0f;
+    const float khi = f_ok ? C.khi[f1] : 0.0f, klo = f_ok ? C.klo[f1] : 0.0f;
+    constexpr int NA = FT * kAcc;
+    float hi[SMC ? 1 : NA], lo[SMC ? 1 : NA], b[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) b[i] = 0.0f;
+    if (SMC) {
+#pragma unroll
+      for (int i = 0; i < NA; ++i) s_hl[i * kPoThreads + tid] = s_hl[(NA + i) * kPoThreads + tid] = 0.0f;
+    } else {
+#pragma unroll
+      for (int i = 0; i < NA; ++i) hi[SMC ? 0 : i] = lo[SMC ? 0 : i] = 0.0f;
+    }
+    int pending = 0;
+
+    for (int64_t sb = r_begin; sb < r_end; sb += kPoThreads) {
+      // ---- stage the frequency-independent per-ray factors ----------------
+      const int64_t r = sb + tid;
+      float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
+      const bool valid = r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V);
+      // two stable compactions: rays whose sinc arguments stay in the series'
+      // range for every frequency of the launch first, the others after them
+      const bool ser = valid && fmaxf(fabsf(au), fabsf(av)) * C.kmax < 0.5f;
+      const unsigned ma = __ballot_sync(0xffffffffu, ser);
+      const unsigned mb = __ballot_sync(0xffffffffu, valid && !ser);
+      int wid = tid >> 5, lane = tid & 31;
+      __syncthreads();  // previous sub-batch's readers are done
+      if (lane == 0) {
+        s_warp[wid] = __popc(ma);
+        s_warp[kPoThreads / 32 + wid] = __popc(mb);
+      }
+      __syncthreads();
+      int before_a = 0, n_a = 0, before_b = 0, n_b = 0;
+      for (int w = 0; w < kPoThreads / 32; ++w) {
+        if (w < wid) {
+          before_a += s_warp[w];
+          before_b += s_warp[kPoThreads / 32 + w];
+        }
+        n_a += s_warp[w];
+        n_b += s_warp[kPoThreads / 32 + w];
+      }
+      if (valid) {
+        const unsigned below = (1u << lane) - 1u;
+        const int at = ser ? before_a + __popc(ma & below) : n_a + before_b + __popc(mb & below);
+        float c[4];
+        series_coeffs(au, av, c);
+        float rs, rc;
+        __sincosf(rev_phase(C.dkhi, C.dklo, dh, dl) * kTwoPi, &rs, &rc);
+        s_ray[0][at] = make_float4(c[0], c[1], c[2], c[3]);
+        s_ray[1][at] = make_float4(V[0], V[1], V[2], V[3]);
+        s_ray[2][at] = make_float4(dh, dl, rc, -rs);
+        s_arg[at] = make_float2(au, av);
+      }
+      __syncthreads();
+      // ---- FT frequencies per thread over the staged rays ---------------
+      if (f_ok) {
+        for (int pass = 0; pass < 2; ++pass) {
+          const int jb = pass == 0 ? 0 : n_a, je = pass == 0 ? n_a : n_a + n_b;
+          for (int j0 = jb + lane_r; j0 < je; j0 += kFlush * RL) {
+            const int jn = min(je, j0 + kFlush * RL);
+            if (pass == 0) {
+#pragma unroll kJu
+              for (int j = j0; j < jn; j += RL) {
+                const float4 r0 = s_ray[0][j], r1 = s_ray[1][j], r2 = s_ray[2][j];
+                float sn, cs;
+                __sincosf(rev_phase(khi, klo, r2.x, r2.y) * kTwoPi, &sn, &cs);
+                float pr = cs, pi = -sn;  // e^{-j phase} at frequency f1
+#pragma unroll
+                for (int q = 0; q < FT; ++q) {
+                  const float t = t2[q];
+                  const float sc = fmaf(fmaf(fmaf(fmaf(r0.w, t, r0.z), t, r0.y), t, r0.x), t, 1.0f);
+                  rot_term(sc, r1, r2, pr, pi, b + q * kAcc);
+                }
+              }
+            } else {
+              for (int j = j0; j < jn; j += RL) {
+                const float4 r1 = s_ray[1][j], r2 = s_ray[2][j];
+                const float2 arg = s_arg[j];
+                float sn, cs;
+                __sincosf(rev_phase(khi, klo, r2.x, r2.y) * kTwoPi, &sn, &cs);
+                float pr = cs, pi = -sn;
+#pragma unroll
+                for (int q = 0; q < FT; ++q) {
+                  const float kq = C.k[min(f1 + q, C.nf - 1)];
+                  const float sc = sincf_(kq * arg.x) * sincf_(kq * arg.y);
+                  rot_term(sc, r1, r2, pr, pi, b + q * kAcc);
+                }
+              }
+            }
+            pending += ((jn - j0 - 1) >> C.rl_shift) + 1;
+            if (pending >= kFlush) {
+#pragma unroll
+              for (int i = 0; i < NA; ++i) {
+                if (SMC) {
+                  float x = s_hl[i * kPoThreads + tid], y = s_hl[(NA + i) * kPoThreads + tid];
+                  two_sum_into(x, y, b[i]);
+                  s_hl[i * kPoThreads + tid] = x;
+                  s_hl[(NA + i) * kPoThreads + tid] = y;
+                } else {
+                  two_sum_into(hi[SMC ? 0 : i], lo[SMC ? 0 : i], b[i]);
+                }
+                b[i] = 0.0f;
+              }
+              pending = 0;
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      if (SMC) {
+        float x = s_hl[i * kPoThreads + tid], y = s_hl[(NA + i) * kPoThreads + tid];
+        two_sum_into(x, y, b[i]);
+        s_hl[i * kPoThreads + tid] = x;
+        s_hl[(NA + i) * kPoThreads + tid] = y;
+      } else {
+        two_sum_into(hi[SMC ? 0 : i], lo[SMC ? 0 : i], b[i]);
+      }
+    }
+    // ---- fixed-order FP64 reduction over the ray lanes, per frequency ----
+#pragma unroll
+    for (int q = 0; q < FT; ++q) {
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < kAcc; ++i) {
+        const int a = q * kAcc + i;
+        s_red[tid][i] = SMC ? (double)s_hl[a * kPoThreads + tid] +
+                                  (double)s_hl[(NA + a) * kPoThreads + tid]
+                            : (double)hi[SMC ? 0 : a] + (double)lo[SMC ? 0 : a];
+      }
+      __syncthreads();
+      const int f = (c0 + tid) * FT + q;
+      if (tid < FL && c0 + tid < n_fc && f < C.nf) {
+        double acc[kAcc];
+#pragma unroll
+        for (int i = 0; i < kAcc; ++i) acc[i] = 0.0;
+        for (int rl = 0; rl < RL; ++rl)
+#pragma unroll
+          for (int i = 0; i < kAcc; ++i) acc[i] += s_red[rl * FL + tid][i];
+        int64_t o = (((int64_t)g * C.n_chunks + chunk) * C.nf + f) * kAcc;
+#pragma unroll
+        for (int i = 0; i < kAcc; ++i) part[o + i] = acc[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // E[g0+g][f][12] = the chunks' sums (fixed order) taken back from the basis
 // (e1, e2) across ks to Cartesian components: for polarisation p, component
 // x and re/im r, E = e1[x] S[p][e1][r] + e2[x] S[p][e2][r].
@@ -386,18 +641,50 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
         for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];
         transverse_basis(C.ks[g], C.e1[g], C.e2[g]);
       }
+      double kmax = 0.0;
       for (int f = 0; f < nf; ++f) {
         const double kd = two_pi * freqs[fb + f] / c0;
         const double kr = freqs[fb + f] / c0;  // k / 2 pi
         C.k[f] = (float)kd;
         C.khi[f] = (float)kr;
         C.klo[f] = (float)(kr - (double)C.khi[f]);
+        C.k2[f] = (float)(kd * kd);
+        kmax = fmax(kmax, kd);
       }
+      C.kmax = (float)(kmax * (1.0 + 1e-6));
+      // a uniform grid (every frequency within 1e-9 of its place on the
+      // line through the first and the last) takes the rotation kernel
+      bool uniform = PE_PO_ROT && nf >= kFt;
+      const double df = nf > 1 ? (freqs[fb + nf - 1] - freqs[fb]) / (double)(nf - 1) : 0.0;
+      for (int f = 0; uniform && f < nf; ++f)
+        uniform = fabs(freqs[fb + f] - (freqs[fb] + f * df)) <= 1e-9 * fabs(freqs[fb + f]);
       dim3 grid(C.n_chunks, ng);
-      pe_event_before("po_kernel", s);
-      po_kernel<<<grid, kPoThreads, 0, s>>>(h, C, part);
-      pe_event_after("po_kernel", s);
-      PE_TRY_LAUNCH("po_kernel");
+      if (uniform) {
+        const double dkr = df / c0;
+        C.dkhi = (float)dkr;
+        C.dklo = (float)(dkr - (double)C.dkhi);
+        const int n_fc = (nf + kFt - 1) / kFt;
+        int fl = 1;
+        while (fl < n_fc && fl < 64) fl <<= 1;
+        C.fl = fl;
+        C.rl_shift = __builtin_ctz((unsigned)(kPoThreads / C.fl));
+        const size_t smem = PE_PO_SMC ? sizeof(float) * 2 * kFt * kAcc * kPoThreads : 0;
+        static bool attr = false;
+        if (!attr && smem > 0) {
+          PE_TRY_CUDA(cudaFuncSetAttribute(po_rot_kernel<kFt, PE_PO_SMC != 0>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          attr = true;
+        }
+        pe_event_before("po_kernel", s);
+        po_rot_kernel<kFt, PE_PO_SMC != 0><<<grid, kPoThreads, smem, s>>>(h, C, part);
+        pe_event_after("po_kernel", s);
+        PE_TRY_LAUNCH("po_rot_kernel");
+      } else {
+        pe_event_before("po_kernel", s);
+        po_kernel<<<grid, kPoThreads, 0, s>>>(h, C, part);
+        pe_event_after("po_kernel", s);
+        PE_TRY_LAUNCH("po_kernel");
+      }
       int64_t n = (int64_t)ng * nf;
       int blocks = (int)((n + 127) / 128);
       po_reduce_kernel<<<blocks, 128, 0, s>>>(part, C, n_freq, fb, E);

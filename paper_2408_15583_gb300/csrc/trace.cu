@@ -65,14 +65,51 @@ struct qstate {
   uint32_t cid[PE_MAX_CAND];
 };
 
-__device__ __forceinline__ bool box_hit(float4 lo, float4 hi, const vray &r, float t0, float t1) {
-  if (lo.x > hi.x) return false;
+// The ray's parameters inside a node's box in the view frame, within
+// [t0, t1]: [tn, tf], empty when tn > tf.
+__device__ __forceinline__ void box_range(float4 lo, float4 hi, const vray &r, float t0, float t1,
+                                          float &tn, float &tf) {
   float ax = fmaf(lo.x, r.ix, r.nx), bx = fmaf(hi.x, r.ix, r.nx);
   float ay = fmaf(lo.y, r.iy, r.ny), by = fmaf(hi.y, r.iy, r.ny);
   float az = fmaf(lo.z, r.iz, r.nz), bz = fmaf(hi.z, r.iz, r.nz);
-  float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), t0));
-  float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), t1));
-  return tn <= tf;
+  tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), t0));
+  tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), t1));
+  if (lo.x > hi.x) tn = INFINITY;  // an empty node
+}
+
+// [tn, tf] narrowed to the parameters where the ray lies inside the node's
+// slab (axis sl.xyz, heights [sl.w, shi] above the view origin; q = ray
+// origin - view origin).  The fast reciprocal's relative error (2 ulp)
+// moves the ends by ~1e-7 t, far inside the slab's padding; a direction
+// within 1e-20 of the slab's plane keeps a finite reciprocal (slab_dir), so
+// a ray along the plane is inside for all t or for none.
+__device__ __forceinline__ bool slab_cut(float4 sl, float shi, pe_f3 q, pe_f3 d, float tn,
+                                         float tf) {
+  const float sd = sl.x * d.x + sl.y * d.y + sl.z * d.z;
+  const float s0 = sl.x * q.x + sl.y * q.y + sl.z * q.z;
+  const float rs = __fdividef(1.0f, slab_dir(sd));
+  const float ta = (sl.w - s0) * rs, tb = (shi - s0) * rs;
+  return fmaxf(tn, fminf(ta, tb)) <= fminf(tf, fmaxf(ta, tb));
+}
+
+// Whether any active lane's ray meets node `nid` (box lo/hi): the box test,
+// then, for a box some lane meets, the node's slab (when it has one; the
+// branch is uniform over the warp, whose lanes test the same node).
+__device__ __forceinline__ bool warp_meets(const pe_geom_layout &L, int64_t nid, float4 lo,
+                                           float4 hi, const vray &r, pe_f3 q, pe_f3 d, bool lv,
+                                           float t0, float t1) {
+  const unsigned FULL = 0xffffffffu;
+  float tn, tf;
+  box_range(lo, hi, r, t0, t1, tn, tf);
+  bool h = lv && tn <= tf;
+  if (!__any_sync(FULL, h)) return false;
+  const float4 sl = __ldg(L.slab + nid);
+  if (sl.w > -INFINITY) {
+    const float shi = __ldg(L.slab_hi + nid);
+    h = h && slab_cut(sl, shi, q, d, tn, tf);
+    return __any_sync(FULL, h);
+  }
+  return true;
 }
 
 __device__ __forceinline__ void note_hit(qstate &S, float t, uint32_t id, float r_ov,
@@ -300,7 +337,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       const float4 hi = ls == top ? rhi : __ldg(L.nodes + 2 * nid + 1);
       bool lv = active && !(ANY && hit_any);
       n_node += lv;
-      if (!__any_sync(FULL, lv && box_hit(lo, hi, r, t0, t_far()))) continue;
+      if (!warp_meets(L, nid, lo, hi, r, q, d, lv, t0, t_far())) continue;
       occ4 = __float_as_uint(lo.w) & 0xffffu;  // the start node when it is a leaf
     }
     // Traversal state, all in registers: `expand` asks to expand node
@@ -327,13 +364,14 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
           const int64_t base = L.node_off[v][cl];
           float4 blo[4], bhi[4];
           bool ex[4];
+          int64_t cid[4];
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             int cx = 2 * px + (c & 1), cy = 2 * py + (c >> 1);
             ex[c] = cx < cw && cy < ch;
-            int64_t nid = base + (ex[c] ? (int64_t)cy * cw + cx : 0);
-            blo[c] = __ldg(L.nodes + 2 * nid);
-            bhi[c] = __ldg(L.nodes + 2 * nid + 1);
+            cid[c] = base + (ex[c] ? (int64_t)cy * cw + cx : 0);
+            blo[c] = __ldg(L.nodes + 2 * cid[c]);
+            bhi[c] = __ldg(L.nodes + 2 * cid[c] + 1);
           }
           bool lv = active && !(ANY && hit_any);
           float t1 = t_far();
@@ -341,8 +379,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             n_node += lv && ex[c];
-            bool h = ex[c] && lv && box_hit(blo[c], bhi[c], r, t0, t1);
-            if (__any_sync(FULL, h)) m |= 1u << c;
+            if (ex[c] && warp_meets(L, cid[c], blo[c], bhi[c], r, q, d, lv, t0, t1)) m |= 1u << c;
           }
           if (cl == 0) {
             occ4 = 0;
@@ -795,14 +832,16 @@ int grid_all(int64_t n) {
 bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
   if (!g || !g->blob_dev) return false;
   if (!pe_make_layout(g->n_views, g->views, L)) return false;
-  size_t a, b, c, d, t;
-  pe_layout_offsets(*L, &a, &b, &c, &d, &t);
+  size_t a, b, c, d, e, f, t;
+  pe_layout_offsets(*L, &a, &b, &c, &d, &e, &f, &t);
   if (g->blob_bytes < t) return false;
   char *blob = static_cast<char *>(g->blob_dev);
   L->cr = reinterpret_cast<const float4 *>(blob + a);
   L->nf = reinterpret_cast<const float4 *>(blob + b);
   L->nodes = reinterpret_cast<const float4 *>(blob + c);
   L->vmask = reinterpret_cast<const uint32_t *>(blob + d);
+  L->slab = reinterpret_cast<const float4 *>(blob + e);
+  L->slab_hi = reinterpret_cast<const float *>(blob + f);
   if (g->vgrid_n == PE_VGRID && g->vgrid_cell > 0.0f) {
     L->vg_n = g->vgrid_n;
     L->vg_cell = g->vgrid_cell;

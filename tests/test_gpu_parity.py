@@ -303,6 +303,35 @@ def test_po_field_synthetic_plate_many_freqs():
     assert field_err(E, Eo).max() < 1e-3
 
 
+@pytest.mark.parametrize("grid", ["uniform", "uniform-5", "random", "geometric"])
+def test_po_field_frequency_grids(grid, small_geom):
+    # uniform grids take the rotation kernel (phase by a per-ray rotation
+    # across a thread's frequencies, the sinc product as one series in k^2);
+    # other grids the direct kernel; both within the field bar on traced hits
+    api, pipe = _mods()
+    d = small_geom
+    sc = d["sc"]
+    c, r = scenes.bounding_sphere(sc.pos)
+    th, ph = [90.0, 75.0], [45.0, 20.0]
+    views = pipe.views_from_angles(th, ph, c, r * 1.02, 48, 48)
+    ovs = _oviews(th, ph, c, r * 1.02, 48, 48)
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], 2, d["prm"])
+    rng = np.random.default_rng(8)
+    freqs = {"uniform": scenes.freq_grid(2.5e9, 9.5e9, 67),
+             "uniform-5": scenes.freq_grid(2.9e9, 3.1e9, 5),
+             "random": np.sort(rng.uniform(2.5e9, 9.5e9, 37)),
+             "geometric": np.geomspace(2e9, 12e9, 41)}[grid]
+    ks = np.array([-ov.d for ov in ovs], np.float32)
+    E = _cplx(api.po_field(h, 2, 48 * 48, ks, freqs))
+    api.stream_check()
+    for a, ov in enumerate(ovs):
+        tr = oracle.trace(ov, d["S"], 2, d["eps"], d["eps"], first=oracle.gfb(sc, ov, "fp32"),
+                          mode="fp32")
+        Eo = oracle.po_field(tr, freqs, ks[a].astype(np.float64))[0]
+        assert field_err(E[a], Eo).max() < 1e-3, (grid, a)
+
+
 def test_po_field_matches_oracle_on_traced_hits(small_geom):
     api, pipe = _mods()
     d = small_geom
