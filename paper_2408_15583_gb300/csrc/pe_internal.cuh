@@ -115,8 +115,13 @@ void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
 // ---------------------------------------------------------------------------
 // Launchers shared between entry points
 // ---------------------------------------------------------------------------
+// Splat into keys (set to all ones by the caller).  Surfel mode with hz
+// (pe_splat_tiles(n_views, W, H) floats of scratch) runs the two-pass splat
+// that skips back-facing disks hidden behind the first pass's keys; hz =
+// null: one pass.
+size_t pe_splat_tiles(int32_t n_views, int32_t W, int32_t H);
 pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float *nrm,
-                          const float *rad, int64_t n, int mode, float delta,
+                          const float *rad, int64_t n, int mode, float delta, float *hz,
                           unsigned long long *keys, cudaStream_t s);
 
 pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,

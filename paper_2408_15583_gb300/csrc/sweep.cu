@@ -34,6 +34,7 @@ __global__ void sigma_kernel(const __grid_constant__ pe_view_batch vb, const dou
 
 struct sweep_ws {
   unsigned long long *keys;
+  float *hz;
   pe_hits h;
   double *kw;
   void *po;
@@ -60,6 +61,7 @@ sweep_ws carve_sweep(pe_carve &c, const pe_sweep *sw, int B) {
   memset(&w, 0, sizeof(w));
   int64_t n = (int64_t)sw->W * sw->H * B;
   w.keys = c.take<unsigned long long>((size_t)n);
+  w.hz = c.take<float>(pe_splat_tiles(B, sw->W, sw->H));
   w.h.p = c.take<float>((size_t)n * 3);
   w.h.n = c.take<float>((size_t)n * 3);
   w.h.k = c.take<float>((size_t)n * 3);
@@ -139,7 +141,7 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
     h.n_rays = per * nb;
     if (!prm->first_bounce_from_geom) {
       PE_TRY_CUDA(cudaMemsetAsync(w.keys, 0xff, sizeof(unsigned long long) * per * nb, s));
-      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.keys, s);
+      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.hz, w.keys, s);
       if (st != PE_OK) return st;
     }
     pe_status st = pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, h, stats, s);
