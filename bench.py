@@ -270,6 +270,10 @@ def run_gpu(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (march_kernel, timed in the steps above)
     roof = roofline_march(march_ms, march_queries / march_launches_per_step)
+    # the incidence splats of one sweep: 64-bit key updates per second
+    # against the measured fire-and-forget atomicMin rate of this device
+    roof_splat = roofline_splat(lib, api, sargs, pos, nrm, rad, geom, prm, ws, E, sig, dev,
+                                stream)
     # the PO field kernel, timed alone on the launching stream
     roof_po = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream,
                           clocks.get("sm_mhz") if isinstance(clocks, dict) else None)
@@ -304,6 +308,7 @@ def run_gpu(args, rank, world, local_rank):
         "phases": phases,
         "roofline": roof,
         "roofline_po": roof_po,
+        "roofline_splat": roof_splat,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
@@ -322,14 +327,14 @@ MARCH_BYTES_PER_QUERY = 152
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 472.7 MB
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 441.3 MB
 # over 6,332,964 queries), valid only for the sources it was taken on (their
 # SHA-256 prefixes); scaled to a full launch by the number of queries.
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 74.6,
-                     "sources": {"include/pointemray.h": "1940109feadd0e91",
-                                 "paper_2408_15583_gb300/csrc/trace.cu": "a3504acfc8ded0a6",
-                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "76d8a06e2e9d487f",
-                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "bf62c78936fbcb0f"}}
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 69.7,
+                     "sources": {"include/pointemray.h": "5a1708589ddf1285",
+                                 "paper_2408_15583_gb300/csrc/trace.cu": "14d59099d1d3e9d9",
+                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "0b2baddc9be50ddd",
+                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "fa84708542497d5a"}}
 
 
 def _traffic_valid(rec):
@@ -359,6 +364,38 @@ def roofline_march(ms_list, queries_per_launch):
             "peak_source": src, "bytes_per_query": MARCH_BYTES_PER_QUERY,
             "queries_per_launch": queries_per_launch, "ms_per_launch": ms,
             "launches_timed": len(ms_list)}
+
+
+def roofline_splat(lib, api, sargs, pos, nrm, rad, geom, prm, ws, E, sig, dev, stream):
+    """The sweep's incidence splats (both passes, every angle batch), timed
+    per launch with CUDA events on the launching stream, against the
+    device's measured rate of fire-and-forget 64-bit atomicMin (the
+    splat's key update; pe_probe_units).  Counters: exact per-pixel tests
+    and key updates (pe_rcs_sweep stats words 5 and 6)."""
+    import torch
+    from paper_2408_15583_gb300 import peaks
+    n_ev = 256
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_ev)]
+    for e in ev:
+        e.record(stream)
+    torch.cuda.synchronize()
+    ptrs = (ctypes.c_void_p * len(ev))(*[e.cuda_event for e in ev])
+    st = torch.zeros(8, dtype=torch.int64, device=dev)
+    lib.pe_set_kernel_events(b"splat_kernel", ptrs, n_ev)
+    api.rcs_sweep(sargs, pos, nrm, rad, geom, prm, ws=ws, E=E, sigma=sig, stats=st)
+    n = lib.pe_set_kernel_events(None, None, 0)
+    torch.cuda.synchronize()
+    api.stream_check()
+    ms = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(n))
+    s = st.cpu().numpy()
+    tests, updates = int(s[5]), int(s[6])
+    probe = peaks.measure(str(dev), reps=3, only=("atomic_min_u64",))["atomic_min_u64"]["value"]
+    achieved = updates / (ms / 1e3) / 1e9
+    return {"kernel": "splat_kernel (both passes)", "bound": "l2_atomics", "achieved": achieved,
+            "peak": probe, "unit": "G atomics/s", "frac": achieved / probe, "traffic": None,
+            "peak_source": "pe_probe_units fire-and-forget 64-bit atomicMin, measured in this run",
+            "launches": n, "ms_per_sweep": ms, "key_updates_per_sweep": updates,
+            "exact_tests_per_sweep": tests}
 
 
 def hbm_peak():

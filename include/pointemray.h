@@ -155,7 +155,9 @@ typedef struct {
  * [2] exact ray/splat tests, [3] pyramid node tests, [4] views whose
  * splats lie along the query's ray per the coarse occupancy grid (the
  * pyramids its walk searches, each over the stretch of the ray crossing
- * that view's occupied cells). */
+ * that view's occupied cells); pe_rcs_sweep also counts its incidence
+ * splats: [5] exact per-pixel ray/disk tests, [6] 64-bit key updates
+ * (atomicMin, one per test that hits). */
 #define PE_STATS_WORDS 8
 
 /* Alg. 1 (screen-based PRI, tube mode) with a finite heap of K points per

@@ -103,9 +103,11 @@ __device__ __forceinline__ bool in_pass(const pe_view &V, const footprint &F, in
   return !(tmin > hmax);
 }
 
-// Every pixel of the footprint whose exact test passes lowers its key.
+// Every pixel of the footprint whose exact test passes lowers its key;
+// n_test / n_hit count the exact tests and the key updates.
 __device__ __forceinline__ void splat_point(const pe_view &V, const footprint &F, int64_t p,
-                                            int mode, unsigned long long *__restrict__ kv) {
+                                            int mode, unsigned long long *__restrict__ kv,
+                                            long long &n_test, long long &n_hit) {
   // Per row, the columns whose ray can hit: the screen points (a, b)
   // (metres from c's projection along u, v) hitting the disk satisfy
   //   a^2 nw^2 + (a nu + b nv)^2 + b^2 nw^2 <= R^2 nw^2
@@ -136,9 +138,11 @@ __device__ __forceinline__ void splat_point(const pe_view &V, const footprint &F
       ia = max(ia, (int)floorf(F.ci + alo * inv - 0.05f));
       ib = min(ib, (int)ceilf(F.ci + ahi * inv + 0.05f));
     }
+    n_test += ib - ia + 1 > 0 ? ib - ia + 1 : 0;
     for (int i = ia; i <= ib; ++i) {
       float depth;
       if (!splat_test(V, i, j, F.c, nn, F.R, mode, depth)) continue;
+      ++n_hit;
       unsigned long long key =
           ((unsigned long long)__float_as_uint(depth) << 32) | (unsigned long long)p;
       // the result is unused, so the atomic is a fire-and-forget reduction
@@ -158,8 +162,9 @@ __global__ void __launch_bounds__(kSplatThreads)
     splat_kernel(const __grid_constant__ pe_view_batch vb, const float *__restrict__ pos,
                  const float *__restrict__ nrm, const float *__restrict__ rad, int64_t n,
                  int mode, float delta, int pass, const float *__restrict__ hz,
-                 unsigned long long *__restrict__ keys) {
+                 unsigned long long *__restrict__ keys, long long *__restrict__ stats) {
   __shared__ int64_t queue[kSplatThreads / 32][64];
+  long long n_test = 0, n_hit = 0;
   const int vi = blockIdx.y;
   const pe_view &V = vb.v[vi];
   unsigned long long *kv = keys + (int64_t)vi * V.W * V.H;
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(kSplatThreads)
       const int64_t pp = q[lane];
       footprint G;
       point_footprint(V, pos, nrm, rad, pp, mode, delta, G);
-      splat_point(V, G, pp, mode, kv);
+      splat_point(V, G, pp, mode, kv, n_test, n_hit);
       __syncwarp();
       if (lane < count - 32) q[lane] = q[lane + 32];
       count -= 32;
@@ -193,7 +198,17 @@ __global__ void __launch_bounds__(kSplatThreads)
     const int64_t pp = q[lane];
     footprint G;
     point_footprint(V, pos, nrm, rad, pp, mode, delta, G);
-    splat_point(V, G, pp, mode, kv);
+    splat_point(V, G, pp, mode, kv, n_test, n_hit);
+  }
+  if (stats) {  // one atomic per warp and counter
+    for (int o = 16; o > 0; o >>= 1) {
+      n_test += __shfl_down_sync(0xffffffffu, n_test, o);
+      n_hit += __shfl_down_sync(0xffffffffu, n_hit, o);
+    }
+    if (lane == 0) {
+      if (n_test) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 5), (unsigned long long)n_test);
+      if (n_hit) atomicAdd(reinterpret_cast<unsigned long long *>(stats + 6), (unsigned long long)n_hit);
+    }
   }
 }
 
@@ -279,7 +294,8 @@ size_t pe_splat_tiles(int32_t n_views, int32_t W, int32_t H) {
 
 pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float *nrm,
                           const float *rad, int64_t n, int mode, float delta, float *hz,
-                          unsigned long long *keys, cudaStream_t s) {
+                          unsigned long long *keys, int64_t *stats, cudaStream_t s) {
+  long long *st = reinterpret_cast<long long *>(stats);
   if (n <= 0) return PE_OK;
   int64_t blocks_needed = (n + kSplatThreads - 1) / kSplatThreads;
   // enough blocks to fill the GPU across the batch; points loop grid-stride
@@ -290,7 +306,7 @@ pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float
   const bool two = mode == 0 && hz != nullptr;
   pe_event_before("splat_kernel", s);
   splat_kernel<<<grid, kSplatThreads, 0, s>>>(vb, pos, nrm, rad, n, mode, delta, two ? 1 : 0,
-                                               nullptr, keys);
+                                               nullptr, keys, st);
   pe_event_after("splat_kernel", s);
   PE_TRY_LAUNCH("splat_kernel");
   if (two) {
@@ -301,7 +317,8 @@ pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float
     tile_max_kernel<<<blocks, 256, 0, s>>>(keys, vb.n, vb.W, vb.H, hz);
     PE_TRY_LAUNCH("tile_max_kernel");
     pe_event_before("splat_kernel", s);
-    splat_kernel<<<grid, kSplatThreads, 0, s>>>(vb, pos, nrm, rad, n, mode, delta, 2, hz, keys);
+    splat_kernel<<<grid, kSplatThreads, 0, s>>>(vb, pos, nrm, rad, n, mode, delta, 2, hz, keys,
+                                                 st);
     pe_event_after("splat_kernel", s);
     PE_TRY_LAUNCH("splat_kernel");
   }
@@ -365,7 +382,7 @@ extern "C" pe_status pe_build_gfb(const pe_view *views, int32_t n_views, const f
   float *hz = wc.take<float>(pe_splat_tiles(vb.n, vb.W, vb.H));
   unsigned long long *keys = keys_out ? reinterpret_cast<unsigned long long *>(keys_out) : ws_keys;
   PE_TRY_CUDA(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * per_view * n_views, s));
-  pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, mode, delta, hz, keys, s);
+  pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, mode, delta, hz, keys, nullptr, s);
   if (st != PE_OK) return st;
   if (gfb_nd || gfb_hit || gfb_mask) {
     int64_t total = per_view * n_views;

@@ -120,9 +120,10 @@ void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
 // that skips back-facing disks hidden behind the first pass's keys; hz =
 // null: one pass.
 size_t pe_splat_tiles(int32_t n_views, int32_t W, int32_t H);
+// stats (nullable): [5] += exact pixel tests, [6] += key updates.
 pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float *nrm,
                           const float *rad, int64_t n, int mode, float delta, float *hz,
-                          unsigned long long *keys, cudaStream_t s);
+                          unsigned long long *keys, int64_t *stats, cudaStream_t s);
 
 pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,
                           const float *nrm, const pe_geom *geom, int32_t mb,

@@ -141,7 +141,7 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
     h.n_rays = per * nb;
     if (!prm->first_bounce_from_geom) {
       PE_TRY_CUDA(cudaMemsetAsync(w.keys, 0xff, sizeof(unsigned long long) * per * nb, s));
-      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.hz, w.keys, s);
+      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.hz, w.keys, stats, s);
       if (st != PE_OK) return st;
     }
     pe_status st = pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, h, stats, s);

@@ -64,9 +64,10 @@ def _clock_stop(p) -> Optional[Dict[str, float]]:
     return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "samples": len(sm)}
 
 
-def measure(device: str = "cuda:0", reps: int = 5, scale: float = 1.0) -> dict:
+def measure(device: str = "cuda:0", reps: int = 5, scale: float = 1.0, only=None) -> dict:
     """Best rate over `reps` timed launches of each probe (after one warm-up
-    launch), in the units of PROBES.  `scale` shortens every probe."""
+    launch), in the units of PROBES.  `scale` shortens every probe; `only`
+    names the probes to run (all by default)."""
     lib = _lib.load()
     dev = torch.device(device)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -77,6 +78,8 @@ def measure(device: str = "cuda:0", reps: int = 5, scale: float = 1.0) -> dict:
     out = {"sms": sms, "blocks": blocks, "threads_per_block": 256}
     try:
         for name, (kind, n_iter, div, unit) in PROBES.items():
+            if only is not None and name not in only:
+                continue
             if kind == 3:
                 scratch.zero_()
             elif kind == 4:
@@ -101,7 +104,7 @@ def measure(device: str = "cuda:0", reps: int = 5, scale: float = 1.0) -> dict:
     finally:
         clocks = _clock_stop(sampler)
     out["clocks"] = clocks
-    if clocks:
+    if clocks and "fp32_fma" in out:
         derived = sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12
         out["fp32_fma"]["derived_peak_tflops"] = derived
         out["fp32_fma"]["frac_of_derived"] = out["fp32_fma"]["value"] / derived
