@@ -525,37 +525,55 @@ def oracle_workload(wl, angles, threads=None, E_gpu=None, sig_gpu=None):
 # serving (continuous batching vs one request at a time)
 # ----------------------------------------------------------------------------
 
-def run_serving(n_requests=100, slots=4, budget_gb=150.0, seed=5):
-    """C5-shaped request mix, scaled to a bench-sized window: targets from
-    the dihedral / sphere / trihedral / composite generators (10k-120k
-    points), screens 128^2-512^2, 1-32 angles, 1-16 frequencies, 1-3 bounces,
-    fused geometry from 8 views at 256^2.  Poisson arrivals at 70% of the
-    one-at-a-time service rate measured first on the same requests."""
+def run_serving(n_requests=48, slots=4, budget_gb=150.0, seed=5):
+    """The serving mix (serve.make_c5_requests): Poisson arrivals; per
+    request its own target of 10k-4M points (radii computed on the device),
+    a 128^2-4096^2 screen, 1-720 azimuths, 1-128 frequencies, 1-5 bounces,
+    fused geometry from 8 views at 256^2; HBM budget 150 GB.  The one-at-a-
+    time service rate is measured first on the same requests; arrivals then
+    come at 70 % of it, served one at a time, in plain batches of `slots`
+    (a batch starts when the previous one is done) and continuously (a
+    request starts as soon as a slot and memory are free)."""
     import torch
     from paper_2408_15583_gb300 import serve
-    pool = [("dihedral", scenes.dihedral(10_000, seed=1)),
-            ("sphere", scenes.sphere(120_000)),
-            ("trihedral", scenes.trihedral(30_000, a=0.6)),
-            ("composite", scenes.composite(60_000, seed=7, pca=True))]
     budget = int(budget_gb * (1 << 30))
-    # service rate, one at a time, back to back (also warms the geometry cache)
-    reqs = serve.make_requests(pool, n_requests, rate_hz=1e9, seed=seed, view_W=256)
+    reqs = serve.make_c5_requests(n_requests, rate_hz=1e9, seed=seed)
     cal = serve.Scheduler(serve.GpuExecutor(n_slots=1), budget, n_slots=1)
     t0 = time.perf_counter()
     cal.run(reqs)
     torch.cuda.synchronize()
     busy = time.perf_counter() - t0
     rate = 0.7 * n_requests / busy
-    reqs = serve.make_requests(pool, n_requests, rate_hz=rate, seed=seed, view_W=256)
+    for r in reqs:
+        r.arrival = 0.0
+    import dataclasses
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    t = 0.0
+    timed = []
+    for r in reqs:
+        t += rng.exponential(1.0 / rate)
+        timed.append(dataclasses.replace(r, arrival=t))
+    shapes = {(r.n_points, r.W, len(r.theta_deg), len(r.freqs_hz), r.max_bounces) for r in reqs}
     out = {"requests": n_requests, "rate_hz": rate, "slots": slots, "hbm_budget_gb": budget_gb,
+           "one_at_a_time_service_s": busy,
+           "distinct_shapes": len(shapes),
            "workload": "Poisson arrivals at 70% of the one-at-a-time service rate; per request "
-                       "a target of 10k-120k points, screen 128^2-512^2, 1-32 angles, 1-16 "
-                       "freqs, 1-3 bounces, fused geometry 8 x 256^2 kept resident"}
-    for name, n_slots in (("plain_batched", 1), ("continuous", slots)):
-        sch = serve.Scheduler(serve.GpuExecutor(n_slots=n_slots), budget, n_slots=n_slots)
-        res = sch.run(reqs)
+                       "its own target (dihedral / sphere / trihedral / composite / OctAR shape) "
+                       "of N ~ logU(10k, 4M) points, radii computed on the device, screen "
+                       "128^2-4096^2 (log-uniform powers of two), A ~ logU(1, 720) azimuths, "
+                       "F ~ logU(1, 128) frequencies, mb ~ U{1..5}, fused geometry 8 x 256^2"}
+    for name, n_slots, policy in (("one_at_a_time", 1, "continuous"),
+                                  ("plain_batched", slots, "static"),
+                                  ("continuous", slots, "continuous")):
+        sch = serve.Scheduler(serve.GpuExecutor(n_slots=n_slots), budget, n_slots=n_slots,
+                              policy=policy)
+        res = sch.run(timed)
+        torch.cuda.synchronize()
         st = serve.latency_stats(res)
         st["max_concurrent"] = sch.max_running
+        st["peak_device_gb"] = sch.peak_in_use / (1 << 30)
+        ok = [r for r in res if r.ok]
+        st["host_exceeds_device"] = sum(1 for r in ok if r.host_ms > r.device_ms)
         out[name] = st
     return out
 

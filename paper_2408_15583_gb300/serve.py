@@ -4,10 +4,15 @@ Requests of uneven size (point count, ray screen, angles, frequencies, bounce
 limit) arrive over time.  The scheduler admits them, in arrival order, as soon
 as an execution slot (a CUDA stream) and enough of the HBM budget are free, so
 requests that arrive while others run join the GPU immediately and their
-kernels overlap.  Each admitted request: points to the device, fused splat
-geometry (reused from a resident cache when the same target was seen before),
-the whole sweep, results back to pinned host memory, a completion event.
-Latency = completion - arrival.
+kernels overlap ("continuous").  The "static" policy is plain batching: it
+admits a batch of up to n_slots queued requests only when the previous batch
+has completed.  Each admitted request: points to the device, surfel radii
+computed on the device when the request brings none, fused splat geometry
+(reused from a resident cache when the same target was seen before), the
+whole sweep, results back to pinned host memory, a completion event.
+Latency = completion - arrival.  A request's device memory (the admission
+charge) is the sum of the library's own workspace and buffer queries for its
+sizes.
 
 The scheduler (admission, queue, bookkeeping) is host logic independent of the
 GPU; `GpuExecutor` is the device side, built only from the C-ABI calls.
@@ -30,7 +35,7 @@ class RcsRequest:
     scene_key: str
     pos: np.ndarray          # float32 [N,3]
     nrm: np.ndarray          # float32 [N,3]
-    rad: np.ndarray          # float32 [N]
+    rad: Optional[np.ndarray]  # float32 [N], or None: computed on the device
     theta_deg: np.ndarray
     phi_deg: np.ndarray
     W: int
@@ -55,6 +60,8 @@ class RcsResult:
     admitted: float = 0.0
     finished: float = 0.0
     ray_bounces: int = 0
+    host_ms: float = 0.0      # host time to issue the request's device work
+    device_ms: float = 0.0    # device time from its first to its last operation
 
     @property
     def latency(self) -> float:
@@ -65,10 +72,14 @@ def validate(req: RcsRequest) -> Optional[str]:
     """Reject malformed requests before they reach the device."""
     if req.pos.ndim != 2 or req.pos.shape[1] != 3 or req.pos.shape[0] < 1:
         return "points must be a non-empty [N,3] array"
-    if req.nrm.shape != req.pos.shape or req.rad.shape != (req.pos.shape[0],):
+    if req.nrm.shape != req.pos.shape or (req.rad is not None and
+                                          req.rad.shape != (req.pos.shape[0],)):
         return "normals/radii do not match the points"
-    if not (np.isfinite(req.pos).all() and np.isfinite(req.nrm).all() and np.isfinite(req.rad).all()):
+    if not (np.isfinite(req.pos).all() and np.isfinite(req.nrm).all() and
+            (req.rad is None or np.isfinite(req.rad).all())):
         return "non-finite point data"
+    if req.rad is None and req.pos.shape[0] < 17:
+        return "radii computed on the device need at least 17 points"
     if len(req.theta_deg) < 1 or len(req.theta_deg) != len(req.phi_deg):
         return "angles"
     f = np.asarray(req.freqs_hz)
@@ -79,27 +90,53 @@ def validate(req: RcsRequest) -> Optional[str]:
     return None
 
 
+# The 8 aggregation views (theta 60/120 deg x phi 45/135/225/315 deg).
+AGG_THETA = [60.0] * 4 + [120.0] * 4
+AGG_PHI = [45.0, 135.0, 225.0, 315.0] * 2
+
+
+def _agg_views(view_W: int):
+    from . import api
+    return [api.view_from_angles(t, p, [0.0, 0.0, 0.0], 1.0, view_W, view_W)
+            for t, p in zip(AGG_THETA, AGG_PHI)]
+
+
 def geometry_bytes(view_W: int, n_views: int = 8) -> int:
-    """Resident splat planes + pyramids of the fused geometry."""
-    pix = n_views * view_W * view_W
-    return pix * 32 + pix // 64 * 2 * 32 * 2 + (1 << 20)
+    """Resident fused geometry (splat planes, pyramids, slabs, view grid):
+    the library's pe_geom_bytes for the aggregation views."""
+    from . import _lib, api
+    return int(_lib.load().pe_geom_bytes(n_views, api.views_to_array(_agg_views(view_W)[:n_views])))
 
 
 def estimate(req: RcsRequest, geometry_cached: bool):
     """(transient, new_resident) device bytes of a request: what it holds
-    while it runs, and the fused geometry it leaves resident if not cached."""
+    while it runs, and the fused geometry it leaves resident if not cached.
+    Every term is the library's own query for the request's sizes: the
+    sweep's workspace (pe_rcs_sweep_workspace), the surfel attributes'
+    (pe_point_attributes_workspace), the GFBs' and the fusion's
+    (pe_build_gfb_workspace, pe_aggregate_workspace), the geometry blob
+    (pe_geom_bytes); plus the points, the GFB buffers, the field and sigma,
+    256 bytes of alignment per buffer and 64 KB for the allocator's
+    rounding of a request's ~20 buffers (512-byte blocks)."""
+    from . import _lib, api
+    lib = _lib.load()
     n = req.n_points
-    per_angle = req.W * req.W * (8 + 60 + 8 + 4 + 1 + 8)
-    batch = max(1, min(64, len(req.theta_deg), (16 << 30) // max(per_angle, 1)))  # the library's rule
-    b = 28 * n                                   # points
-    b += batch * per_angle                       # sweep workspace
-    b += len(req.theta_deg) * len(req.freqs_hz) * 12 * 8 * 2   # field + sigma
-    b += 64 << 20                                # PO partials and slack
+    args = api.SweepArgs(req.theta_deg, req.phi_deg, req.W, req.W, [0.0, 0.0, 0.0], 1.0,
+                         req.freqs_hz, req.max_bounces)
+    A, F = len(req.theta_deg), len(req.freqs_hz)
+    b = 28 * n + 3 * 256 + (64 << 10)                     # points, normals, radii; rounding
+    if req.rad is None:
+        b += int(lib.pe_point_attributes_workspace(n)) + 256
+    b += int(args.workspace_bytes()) + 256                # the sweep
+    b += A * F * (12 + 4) * 8 + 8 * 8 + 3 * 256           # field, sigma, counters
     resident = 0
     if not geometry_cached:
+        vs = _agg_views(req.view_W)
+        arr = api.views_to_array(vs)
         pix = 8 * req.view_W * req.view_W
-        b += 256 ** 3 * 8 + pix * (16 + 1 + 12)  # fusion workspace + GFBs
-        resident = geometry_bytes(req.view_W)
+        b += int(lib.pe_build_gfb_workspace(8, arr)) + pix * (16 + 1) + 3 * 256
+        b += int(lib.pe_aggregate_workspace(8, arr, 256)) + 256
+        resident = int(lib.pe_geom_bytes(8, arr)) + 256
     return int(b), int(resident)
 
 
@@ -118,7 +155,10 @@ class Scheduler:
     """
 
     def __init__(self, executor, hbm_budget: int, n_slots: int = 4,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, policy: str = "continuous"):
+        if policy not in ("continuous", "static"):
+            raise ValueError("policy: continuous or static")
+        self.policy = policy
         self.ex = executor
         self.budget = int(hbm_budget)
         self.n_slots = int(n_slots)
@@ -163,6 +203,9 @@ class Scheduler:
         return None
 
     def _admit(self):
+        # plain batching admits a new batch only once the last one is done
+        if self.policy == "static" and self.running:
+            return
         while self.queue:
             slot = self._free_slot()
             if slot is None:
@@ -173,6 +216,9 @@ class Scheduler:
             if self.in_use + resident + charge + new_res > self.budget:
                 need = self.in_use + resident + charge + new_res - self.budget
                 self.ex.evict(need)
+                # the eviction may have taken this request's own (idle)
+                # geometry: charge it again as the executor now holds it
+                charge, new_res = estimate(req, self.ex.geometry_cached(req.scene_key))
                 resident = self.ex.resident_bytes()
                 if self.in_use + resident + charge + new_res > self.budget:
                     return          # wait for running requests to finish (FIFO)
@@ -288,15 +334,22 @@ class GpuExecutor:
         torch, api, pipe = self.torch, self.api, self.pipe
         s = self.streams[slot]
         hp = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-              for a in (req.pos, req.nrm, req.rad)]
+              for a in ((req.pos, req.nrm) if req.rad is None else (req.pos, req.nrm, req.rad))]
+        t_host = time.perf_counter()
+        t0 = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(s):
-            pos, nrm, rad = [t.to(self.dev, non_blocking=True) for t in hp]
+            t0.record(s)
+            pos, nrm = [t.to(self.dev, non_blocking=True) for t in hp[:2]]
+            if req.rad is None:
+                rad, _ = api.point_attributes(pos, 8, 16, None, radius=True, normal=False,
+                                              stream=s)
+            else:
+                rad = hp[2].to(self.dev, non_blocking=True)
             g = self.geo.get(req.scene_key)
             c, r = self._sphere(req)
             if g is None:
-                th = [60.0] * 4 + [120.0] * 4
-                ph = [45.0, 135.0, 225.0, 315.0] * 2
-                gv = pipe.views_from_angles(th, ph, c, r * 1.02, req.view_W, req.view_W)
+                gv = pipe.views_from_angles(AGG_THETA, AGG_PHI, c, r * 1.02, req.view_W,
+                                            req.view_W)
                 prm = pipe.default_params(req.pos, gv)
                 geom, _ = pipe.build_geometry(pos, nrm, rad, gv, prm, stream=s)
                 ready = torch.cuda.Event()
@@ -319,9 +372,10 @@ class GpuExecutor:
             hE.copy_(E, non_blocking=True)
             hS.copy_(sig, non_blocking=True)
             hst.copy_(stats, non_blocking=True)
-            done = torch.cuda.Event()
+            done = torch.cuda.Event(enable_timing=True)
             done.record(s)
-        return {"req": req, "done": done, "keep": (pos, nrm, rad, E, sig, stats, args, hp),
+        return {"req": req, "done": done, "t0": t0, "host_ms": (time.perf_counter() - t_host) * 1e3,
+                "keep": (pos, nrm, rad, E, sig, stats, args, hp),
                 "hE": hE, "hS": hS, "hst": hst, "g": g}
 
     def poll(self, h) -> bool:
@@ -332,7 +386,8 @@ class GpuExecutor:
         E = h["hE"].numpy()
         st = h["hst"].numpy()
         return RcsResult(h["req"].rid, True, E=E[..., 0] + 1j * E[..., 1],
-                         sigma=h["hS"].numpy().copy(), ray_bounces=int(st[0] + st[1]))
+                         sigma=h["hS"].numpy().copy(), ray_bounces=int(st[0] + st[1]),
+                         host_ms=h["host_ms"], device_ms=h["t0"].elapsed_time(h["done"]))
 
 
 def _bounding_sphere(pos: np.ndarray):
@@ -373,6 +428,36 @@ def make_requests(scene_pool: List, n: int, rate_hz: float, seed: int = 5,
     return out
 
 
+def make_c5_requests(n: int, rate_hz: float, seed: int = 5, max_points: int = 4_000_000,
+                     view_W: int = 256) -> List[RcsRequest]:
+    """The serving mix: Poisson arrivals; per request its own target
+    (scenes.c5_target: one of the standard workloads' shapes at a random
+    size) of N ~ logU(10k, max_points) points with exact normals and no
+    radii (the server computes them), a power-of-two screen of 128^2 to
+    4096^2 rays (log-uniform), A ~ logU(1, 720) azimuths at one elevation,
+    F ~ logU(1, 128) frequencies on a uniform grid over 20 % of a band
+    starting at 2-12 GHz, mb ~ U{1..5}."""
+    import scenes
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate_hz)
+        N = int(round(loguniform(rng, 10_000, max_points)))
+        pos, nrm, kind = scenes.c5_target(seed * 100_003 + i, N)
+        W = int(2 ** int(rng.integers(7, 13)))
+        A = max(1, int(round(loguniform(rng, 1, 720))))
+        F = max(1, int(round(loguniform(rng, 1, 128))))
+        mb = int(rng.integers(1, 6))
+        th = np.full(A, float(rng.uniform(30.0, 150.0)))
+        ph = float(rng.uniform(0.0, 360.0)) + np.arange(A) * (360.0 / A)
+        f0 = float(rng.uniform(2e9, 12e9))
+        freqs = f0 * (1.0 + 0.2 * np.arange(F) / max(F - 1, 1))
+        out.append(RcsRequest(i, f"c5-{seed}-{i}-{kind}", pos, nrm, None, th, ph, W, freqs, mb,
+                              view_W=view_W, arrival=t))
+    return out
+
+
 def latency_stats(results: List[RcsResult]) -> dict:
     ok = [r for r in results if r.ok]
     if not ok:
@@ -384,4 +469,6 @@ def latency_stats(results: List[RcsResult]) -> dict:
             "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3),
             "requests_per_s": len(ok) / span if span > 0 else None,
-            "ray_bounces_per_s": sum(r.ray_bounces for r in ok) / span if span > 0 else None}
+            "ray_bounces_per_s": sum(r.ray_bounces for r in ok) / span if span > 0 else None,
+            "host_ms_p50": float(np.percentile([r.host_ms for r in ok], 50)),
+            "device_ms_p50": float(np.percentile([r.device_ms for r in ok], 50))}

@@ -30,7 +30,7 @@ __all__ = [
     "C0", "Scene", "Sweep", "GfbViews", "Workload",
     "knn_radius", "pca_normals", "bounding_sphere",
     "plate", "dihedral", "trihedral", "sphere", "cylinder", "composite", "octar",
-    "random_primitives", "aggregation_views", "freq_grid",
+    "random_primitives", "aggregation_views", "freq_grid", "c5_target",
     "workload_dihedral", "workload_sphere", "workload_composite", "workload_octar",
     "workload_small",
 ]
@@ -394,6 +394,76 @@ def random_primitives(seed: int, lam: float, bbox_lambdas: float = 25.6,
             parts_p.append(ctr + r * v)
             parts_n.append(v)
     return _finish(np.concatenate(parts_p), np.concatenate(parts_n), "primitives", seed)
+
+
+def c5_target(seed: int, n_points: int):
+    """A serving request's target: positions and exact normals (no radii:
+    the server computes them on the device), n_points on one of the shapes
+    of the standard workloads at a random size: a dihedral or trihedral of
+    0.3-1.5 m faces, a sphere of radius 0.3-1.5 m, the composite layout
+    (trihedral, plate, cylinder; position noise 0.6 mm), or the OctAR plates
+    of 2-20 m.  Returns (pos float32 [n,3], nrm float32 [n,3], kind)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    kinds = ("dihedral", "sphere", "trihedral", "composite", "octar")
+    kind = kinds[int(rng.integers(0, len(kinds)))]
+    n = int(n_points)
+
+    def plates(axes, size, offset=0.0, centred=False):
+        per = [n // len(axes)] * len(axes)
+        per[0] += n - sum(per)
+        ps, ns = [], []
+        for ax, m in zip(axes, per):
+            uv = rng.random((m, 2)) * size - (size / 2 if centred else 0.0)
+            p = np.zeros((m, 3))
+            o1, o2 = [i for i in range(3) if i != ax]
+            p[:, o1], p[:, o2] = uv[:, 0], uv[:, 1]
+            q = np.zeros_like(p)
+            q[:, ax] = 1.0
+            ps.append(p)
+            ns.append(q)
+        return np.concatenate(ps), np.concatenate(ns)
+
+    if kind == "dihedral":
+        pos, nrm = plates((1, 0), float(rng.uniform(0.3, 1.5)))
+    elif kind == "trihedral":
+        pos, nrm = plates((0, 1, 2), float(rng.uniform(0.3, 1.5)))
+    elif kind == "octar":
+        pos, nrm = plates((0, 1, 2), float(rng.uniform(2.0, 20.0)), centred=True)
+    elif kind == "sphere":
+        a = float(rng.uniform(0.3, 1.5))
+        i = np.arange(n, dtype=np.float64)
+        z = 1.0 - (2.0 * i + 1.0) / n
+        r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+        t = i * (math.pi * (3.0 - math.sqrt(5.0)))
+        nrm = np.stack([r * np.cos(t), r * np.sin(t), z], axis=1)
+        pos = a * nrm
+    else:
+        a_tri, a_pl, a_cy = 3 * 0.36, 1.0, 2 * math.pi * 0.3 + 2 * math.pi * 0.09
+        tot = a_tri + a_pl + a_cy
+        n_tri, n_pl = int(n * a_tri / tot), int(n * a_pl / tot)
+        n_cy = n - n_tri - n_pl
+        per = [n_tri // 3] * 3
+        per[0] += n_tri - sum(per)
+        ps, ns = [], []
+        for ax, m in zip(range(3), per):
+            uv = rng.random((m, 2)) * 0.6
+            p = np.zeros((m, 3))
+            o1, o2 = [i for i in range(3) if i != ax]
+            p[:, o1], p[:, o2] = uv[:, 0], uv[:, 1]
+            q = np.zeros_like(p)
+            q[:, ax] = 1.0
+            ps.append(p)
+            ns.append(q)
+        uv = rng.random((n_pl, 2)) - 0.5
+        ps.append(np.stack([np.full(n_pl, -1.5), uv[:, 0], uv[:, 1]], axis=1))
+        ns.append(np.tile([1.0, 0.0, 0.0], (n_pl, 1)))
+        pc, nc = _cylinder_samples(rng, n_cy, 0.3, 1.0, (0.0, -1.5, 0.0))
+        ps.append(pc)
+        ns.append(nc)
+        pos = np.concatenate(ps)
+        pos = pos + rng.normal(0.0, 0.6e-3, size=pos.shape)
+        nrm = np.concatenate(ns)
+    return pos.astype(np.float32), nrm.astype(np.float32), kind
 
 
 # ----------------------------------------------------------------------------

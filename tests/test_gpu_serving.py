@@ -55,3 +55,67 @@ def test_budget_respected_with_resident_geometry(pool):
     res = s.run(reqs)
     assert all(r.ok for r in res)
     assert s.peak_in_use <= s.budget
+
+
+def test_c5_requests_device_radii_and_policies():
+    # requests that bring no radii (the server computes them on the device,
+    # pe_point_attributes), served one at a time, in plain batches and
+    # continuously: every policy gives every request the same field, bit for
+    # bit, as the direct library calls on the same inputs
+    from paper_2408_15583_gb300 import api, pipeline, serve
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    reqs = serve.make_c5_requests(6, rate_hz=1e6, seed=7, max_points=60_000, view_W=64)
+    for r in reqs:          # keep the screens and sweeps small
+        r.W = min(r.W, 128)
+        r.theta_deg, r.phi_deg = r.theta_deg[:5], r.phi_deg[:5]
+        r.freqs_hz = r.freqs_hz[:6]
+    runs = {}
+    for name, slots, policy in (("one", 1, "continuous"), ("static", 3, "static"),
+                                ("cont", 3, "continuous")):
+        s = serve.Scheduler(serve.GpuExecutor(n_slots=slots), hbm_budget=40 << 30, n_slots=slots,
+                            policy=policy)
+        res = {r.rid: r for r in s.run(reqs)}
+        assert all(r.ok for r in res.values()), [r.error for r in res.values()]
+        runs[name] = res
+    for rq in reqs:
+        dev = "cuda:0"
+        pos = torch.from_numpy(rq.pos).to(dev)
+        nrm = torch.from_numpy(rq.nrm).to(dev)
+        rad, _ = api.point_attributes(pos, 8, 16, None, radius=True, normal=False)
+        c, r = serve._bounding_sphere(rq.pos)
+        gv = pipeline.views_from_angles(serve.AGG_THETA, serve.AGG_PHI, c, r * 1.02, rq.view_W,
+                                        rq.view_W)
+        prm = pipeline.default_params(rq.pos, gv)
+        geom, _ = pipeline.build_geometry(pos, nrm, rad, gv, prm)
+        args = api.SweepArgs(rq.theta_deg, rq.phi_deg, rq.W, rq.W, c, r * 1.02, rq.freqs_hz,
+                             rq.max_bounces)
+        E, _ = api.rcs_sweep(args, pos, nrm, rad, geom if rq.max_bounces > 1 else None, prm)
+        api.stream_check()
+        Eh = E.cpu().numpy()
+        Eh = Eh[..., 0] + 1j * Eh[..., 1]
+        for name in runs:
+            assert np.array_equal(runs[name][rq.rid].E, Eh), (name, rq.rid)
+
+
+def test_admission_charge_bounds_the_devices_allocations():
+    # the charge the scheduler admits a request with (the library's sizes)
+    # covers what the executor actually allocates for it
+    from paper_2408_15583_gb300 import serve
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    reqs = serve.make_c5_requests(3, rate_hz=1e6, seed=11, max_points=300_000, view_W=128)
+    for rq in reqs:
+        rq.theta_deg, rq.phi_deg = rq.theta_deg[:40], rq.phi_deg[:40]
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        base = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        ex = serve.GpuExecutor(n_slots=1)
+        s = serve.Scheduler(ex, hbm_budget=100 << 30, n_slots=1)
+        res = s.run([rq])
+        assert res[0].ok, res[0].error
+        torch.cuda.synchronize()
+        used = torch.cuda.max_memory_allocated() - base
+        t, r = serve.estimate(rq, False)
+        assert used <= t + r, (rq.rid, used, t + r)

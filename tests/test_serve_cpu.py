@@ -4,6 +4,7 @@ Failures are injected on the host (a start that raises, a poll that raises,
 malformed requests, cancellation); nothing here touches a device.
 """
 import numpy as np
+import pytest
 
 from paper_2408_15583_gb300.serve import (RcsRequest, RcsResult, Scheduler, estimate_bytes,
                                           geometry_bytes, latency_stats, validate)
@@ -158,3 +159,58 @@ def test_latency_stats():
     rs = [RcsResult(i, True, arrival=0.0, finished=0.1 * (i + 1), ray_bounces=10) for i in range(10)]
     st = latency_stats(rs)
     assert abs(st["p50_ms"] - 550.0) < 1e-6 and st["n"] == 10
+
+
+def test_static_batches_wait_for_the_whole_batch():
+    # plain batching: a new batch of up to n_slots requests starts only when
+    # every request of the previous batch has completed
+    clock = FakeClock()
+    ex = FakeExecutor(clock)
+    s = Scheduler(ex, hbm_budget=100 * estimate_bytes(req(0), False), n_slots=3, clock=clock,
+                  policy="static")
+    reqs = [req(i, n=1000 * (1 + i % 4), arrival=0.1 * i, key=f"s{i}") for i in range(9)]
+    assert drive(s, clock, reqs)
+    done = {r.rid: r for r in s.results if r.ok}
+    assert sorted(done) == list(range(9))
+    starts = sorted(t for _, _, t in ex.started)
+    for rid, _, t in ex.started:
+        # every request that started before this one's batch has finished by then
+        earlier = [r for r in done.values() if r.admitted < t]
+        assert all(r.finished <= t + 1e-9 for r in earlier)
+    assert ex.max_concurrent <= 3
+    with pytest.raises(ValueError):
+        Scheduler(ex, 1, policy="greedy")
+
+
+def test_admission_charge_is_the_librarys_own_sizes():
+    # the sweep term of a 4096^2, 720-angle request is the library's
+    # pe_rcs_sweep_workspace; an uncached target adds its fusion workspace and
+    # the resident geometry blob (pe_geom_bytes)
+    from paper_2408_15583_gb300 import _lib, api
+    from paper_2408_15583_gb300 import serve
+    lib = _lib.load()
+    big = req(0, W=4096, A=720, F=128, mb=5)
+    big.rad = None
+    t_c, r_c = serve.estimate(big, True)
+    t_u, r_u = serve.estimate(big, False)
+    args = api.SweepArgs(big.theta_deg, big.phi_deg, 4096, 4096, [0, 0, 0], 1.0, big.freqs_hz, 5)
+    assert t_c >= args.workspace_bytes() and r_c == 0
+    assert t_c >= lib.pe_point_attributes_workspace(big.n_points)
+    arr = api.views_to_array(serve._agg_views(big.view_W))
+    assert r_u == lib.pe_geom_bytes(8, arr) + 256 == geometry_bytes(big.view_W) + 256
+    assert t_u - t_c >= lib.pe_aggregate_workspace(8, arr, 256)
+    assert t_c < 20 << 30          # the sweep's angle batch keeps it near 16 GB
+
+
+def test_c5_request_mix():
+    from paper_2408_15583_gb300.serve import make_c5_requests
+    reqs = make_c5_requests(40, rate_hz=10.0, seed=3, max_points=200_000)
+    assert len({r.scene_key for r in reqs}) == 40          # every request its own target
+    for r in reqs:
+        assert validate(r) is None and r.rad is None
+        assert 9_990 <= r.n_points <= 200_000
+        assert r.W in (128, 256, 512, 1024, 2048, 4096)
+        assert 1 <= len(r.theta_deg) <= 720 and 1 <= len(r.freqs_hz) <= 128
+        assert 1 <= r.max_bounces <= 5
+    arr = [r.arrival for r in reqs]
+    assert arr == sorted(arr) and arr[0] > 0
