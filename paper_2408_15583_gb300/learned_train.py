@@ -17,6 +17,7 @@ views of each target with the floor of c23 (max(sigma_ref) - 60 dB).
 from __future__ import annotations
 
 import ctypes as C
+import json
 import math
 import time
 from dataclasses import dataclass
@@ -65,8 +66,13 @@ def make_pairs(sparse, dense, vs: ViewSet, delta_px: float, device="cuda:0"):
     lib = _lib.load()
     n = len(vs.views)
     P = vs.W * vs.W
-    ps, _, _ = pipeline.scene_to_device(sparse, device)
-    pd, nd_, rd = pipeline.scene_to_device(dense, device)
+    ps = torch.from_numpy(np.ascontiguousarray(sparse.pos, dtype=np.float32)).to(device)
+    pd = torch.from_numpy(np.ascontiguousarray(dense.pos, dtype=np.float32)).to(device)
+    nd_ = torch.from_numpy(np.ascontiguousarray(dense.nrm, dtype=np.float32)).to(device)
+    if dense.rad is None:   # surfel radii on the device (8 nearest, pe_point_attributes)
+        rd, _ = api.point_attributes(pd, 8, 16, None, radius=True, normal=False)
+    else:
+        rd = torch.from_numpy(np.ascontiguousarray(dense.rad, dtype=np.float32)).to(device)
     delta = float(delta_px * vs.views[0].pitch)
     keys = api.build_gfb(vs.views, ps, None, None, 1, delta, outputs=("keys",))["keys"]
     nd = api.build_gfb(vs.views, pd, nd_, rd, 0, outputs=("nd",))["nd"]
@@ -85,13 +91,18 @@ def make_pairs(sparse, dense, vs: ViewSet, delta_px: float, device="cuda:0"):
 
 def dataset(n_scenes: int, views_per_scene: int, W: int, seed: int, device="cuda:0",
             dense_density=200.0, keep_scenes=False):
+    """Pairs of n_scenes random targets x views_per_scene views.  The tube
+    mode needs no radii; the dense cloud's surfel radii are computed on the
+    device unless the scenes are kept (for the paths that splat them
+    again)."""
     import scenes
     out = []
     for k in range(n_scenes):
         sd = seed * 100_003 + k
         rng = np.random.Generator(np.random.PCG64(sd))
-        sparse = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0)
-        dense = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0, density=dense_density)
+        sparse = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0, radius=keep_scenes)
+        dense = scenes.random_primitives(sd, 1.0, bbox_lambdas=W / 10.0, density=dense_density,
+                                         radius=keep_scenes)
         vs = view_set(sparse, views_per_scene, W, sd + 1)
         item = make_pairs(sparse, dense, vs, float(rng.uniform(1.0, 3.0)), device)
         if keep_scenes:
@@ -312,12 +323,12 @@ def study(n_train=160, n_held=16, views_train=16, views_held=12, W=256, steps=(5
         rows.append({"steps": target, "train_s": dt,
                      "rmse_db_learned": float(np.mean([r["learned"] for r in res])),
                      "rmse_db_coarse": float(np.mean([r["coarse"] for r in res]))})
+        print(json.dumps(rows[-1]), flush=True)
     return {"pairs": len(train_set) * views_train, "held_out_views": n_held * views_held,
             "W": W, "batch": batch, "data_s": t_data, "checkpoints": rows}
 
 
 if __name__ == "__main__":
-    import json
     import sys
     if len(sys.argv) > 1 and sys.argv[1] == "study":
         kw = {}

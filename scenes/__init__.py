@@ -161,7 +161,7 @@ def _stratified_rect(rng, n_u, n_v, lu, lv):
     return su, sv
 
 
-def _finish(pos, nrm, name, seed, noise=0.0, rng=None, pca_k=0):
+def _finish(pos, nrm, name, seed, noise=0.0, rng=None, pca_k=0, radius=True):
     pos = np.asarray(pos, dtype=np.float64)
     nrm = np.asarray(nrm, dtype=np.float64)
     nrm = nrm / np.linalg.norm(nrm, axis=1, keepdims=True)
@@ -172,7 +172,7 @@ def _finish(pos, nrm, name, seed, noise=0.0, rng=None, pca_k=0):
         nrm32 = pca_normals(pos32, nrm, k=pca_k)
     else:
         nrm32 = nrm.astype(np.float32)
-    rad = knn_radius(pos32, 8)
+    rad = knn_radius(pos32, 8) if radius else None
     return Scene(pos=pos32, nrm=nrm32, rad=rad, name=name, seed=seed)
 
 
@@ -340,7 +340,7 @@ def composite(n_points: int = 1_000_000, seed: int = 7, freq_hz: float = 10e9,
 
 def random_primitives(seed: int, lam: float, bbox_lambdas: float = 25.6,
                       n_min: int = 3, n_max: int = 12, density: Optional[float] = None,
-                      sample_seed: Optional[int] = None) -> Scene:
+                      sample_seed: Optional[int] = None, radius: bool = True) -> Scene:
     """3-12 random boxes / cylinders / spheres of 0.2-2 m (then rescaled so the
     scene's longest bbox edge is ``bbox_lambdas`` wavelengths), sampled at a
     uniform density of 5-50 points per lambda^2 (or ``density`` points per
@@ -393,7 +393,10 @@ def random_primitives(seed: int, lam: float, bbox_lambdas: float = 25.6,
             v /= np.linalg.norm(v, axis=1, keepdims=True)
             parts_p.append(ctr + r * v)
             parts_n.append(v)
-    return _finish(np.concatenate(parts_p), np.concatenate(parts_n), "primitives", seed)
+    # radius=False: positions and normals only (rad None; a caller with a
+    # GPU computes the radii there)
+    return _finish(np.concatenate(parts_p), np.concatenate(parts_n), "primitives", seed,
+                   radius=radius)
 
 
 def c5_target(seed: int, n_points: int):
