@@ -212,7 +212,9 @@ pe_status pe_point_attributes(const float *pos_dev, int64_t n_points, int32_t k_
  *           the buffer, sizes it below the L2 and runs a warm-up launch);
  *   kind 4  64-bit atomicMin, result unused (the splat's form): n_iter per
  *           thread at hashed addresses of a power-of-two table in scratch
- *           (atomics).
+ *           (atomics);
+ *   kind 5  packed FP32x2 FMA (__ffma2_rn): n_iter x 8 independent chains
+ *           of float pairs per thread (flops, a pair's FMA counted as 4).
  * scratch_dev: device buffer of at least 4096 bytes, 256-byte aligned, that
  * every kind may write; blocks in [1, 2^20]; n_iter in [1, 2^24]. */
 int64_t pe_probe_units(int32_t kind, int32_t blocks, int32_t n_iter, void *scratch_dev,

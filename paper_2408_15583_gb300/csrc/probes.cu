@@ -26,6 +26,24 @@ __global__ void __launch_bounds__(kProbeThreads) probe_fma32(int n_iter, float b
   if (s == -1.0f) sink[0] = s;
 }
 
+// The same chains as probe_fma32, two per packed FP32x2 FMA (__ffma2_rn):
+// the issue rate of the paired form the PO kernel's accumulations use.
+__global__ void __launch_bounds__(kProbeThreads) probe_fma32x2(int n_iter, float b, float c,
+                                                               float *sink) {
+  float2 a[kChains];
+  const float2 bb = make_float2(b, b), cc = make_float2(c, c);
+#pragma unroll
+  for (int k = 0; k < kChains; ++k)
+    a[k] = make_float2((float)(threadIdx.x + k) * 1e-3f, (float)(threadIdx.x + k) * 2e-3f);
+  for (int i = 0; i < n_iter; ++i)
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = __ffma2_rn(a[k], bb, cc);
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += a[k].x + a[k].y;
+  if (s == -1.0f) sink[0] = s;
+}
+
 // x <- sin(x) from x in [1, 1.8): positive, decreasing like sqrt(3 / i),
 // far from the denormal range for any trip count used here.
 __global__ void __launch_bounds__(kProbeThreads) probe_sin(int n_iter, float *sink) {
@@ -100,8 +118,8 @@ __global__ void __launch_bounds__(kProbeThreads) probe_atomic_min64(unsigned lon
 extern "C" int64_t pe_probe_units(int32_t kind, int32_t blocks, int32_t n_iter, void *scratch,
                                   size_t scratch_bytes, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (kind < 0 || kind > 4) {
-    pe_fail(PE_EINVAL, "pe_probe_units: kind in [0, 4]");
+  if (kind < 0 || kind > 5) {
+    pe_fail(PE_EINVAL, "pe_probe_units: kind in [0, 5]");
     return -1;
   }
   if (blocks < 1 || blocks > (1 << 20) || n_iter < 1 || n_iter > (1 << 24)) {
@@ -145,6 +163,11 @@ extern "C" int64_t pe_probe_units(int32_t kind, int32_t blocks, int32_t n_iter, 
       ops = threads * n_iter;  // atomics
       break;
     }
+    case 5:
+      probe_fma32x2<<<blocks, kProbeThreads, 0, s>>>(n_iter, 0.9999f, 1e-4f,
+                                                     static_cast<float *>(scratch));
+      ops = threads * n_iter * kChains * 4;  // flops (two FMAs per instruction)
+      break;
   }
   cudaError_t e = cudaGetLastError();
   pe_count_launch();

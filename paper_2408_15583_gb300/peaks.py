@@ -1,5 +1,6 @@
 """Measured unit rates of the device in use, through ``pe_probe_units``: FP32
-FMA, ``__sinf`` (the PO term's sine path), FP64 FMA, L2-resident reads and
+FMA (scalar and the packed FP32x2 form), ``__sinf`` (the PO term's sine
+path), FP64 FMA, L2-resident reads and
 fire-and-forget 64-bit atomicMin (the splat's update).  They bound the
 ALU- and atomic-bound kernels of the path; the FP32 figure is reported beside
 the peak derived from the unit counts (SMs x 128 FP32 lanes x 2 flops x SM
@@ -26,6 +27,7 @@ PROBES = {
     "fp64_fma": (2, 2_000, 1e12, "TFLOP/s"),
     "l2_read": (3, 4_000, 1e9, "GB/s"),
     "atomic_min_u64": (4, 1_000, 1e9, "G atomics/s"),
+    "fp32x2_fma": (5, 50_000, 1e12, "TFLOP/s"),
 }
 SCRATCH_BYTES = 32 << 20   # well inside the 129 MB L2
 BLOCKS_PER_SM = 8

@@ -121,7 +121,7 @@ def test_argument_errors_before_any_device_work(lib):
 
 
 def test_probe_arguments_rejected_before_any_device_work(lib):
-    assert lib.pe_probe_units(7, 1, 1, None, 0, None) == -1
+    assert lib.pe_probe_units(6, 1, 1, None, 0, None) == -1
     assert b"kind" in lib.pe_last_error()
     assert lib.pe_probe_units(0, 0, 1, None, 0, None) == -1
     assert lib.pe_probe_units(0, 1, 0, None, 0, None) == -1

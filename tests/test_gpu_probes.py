@@ -30,6 +30,7 @@ def test_operation_counts():
     assert lib.pe_probe_units(0, blocks, it, buf.data_ptr(), nbytes, s) == th * it * 8 * 2
     assert lib.pe_probe_units(1, blocks, it, buf.data_ptr(), nbytes, s) == th * it * 8
     assert lib.pe_probe_units(2, blocks, it, buf.data_ptr(), nbytes, s) == th * it * 8 * 2
+    assert lib.pe_probe_units(5, blocks, it, buf.data_ptr(), nbytes, s) == th * it * 8 * 4
     buf.zero_()
     assert lib.pe_probe_units(3, blocks, it, buf.data_ptr(), nbytes, s) == (nbytes - 16) * it
     buf.fill_(255)
