@@ -327,12 +327,12 @@ MARCH_BYTES_PER_QUERY = 152
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 441.3 MB
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 441.7 MB
 # over 6,332,964 queries), valid only for the sources it was taken on (their
 # SHA-256 prefixes); scaled to a full launch by the number of queries.
 MARCH_NCU_TRAFFIC = {"bytes_per_query": 69.7,
-                     "sources": {"include/pointemray.h": "5a1708589ddf1285",
-                                 "paper_2408_15583_gb300/csrc/trace.cu": "14d59099d1d3e9d9",
+                     "sources": {"include/pointemray.h": "ebaf4ce1ba6be3d4",
+                                 "paper_2408_15583_gb300/csrc/trace.cu": "8478cf218437cb2f",
                                  "paper_2408_15583_gb300/csrc/pe_internal.cuh": "0b2baddc9be50ddd",
                                  "paper_2408_15583_gb300/csrc/aggregate.cu": "fa84708542497d5a"}}
 

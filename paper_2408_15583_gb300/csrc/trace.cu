@@ -279,15 +279,19 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       float lim = pe_add(S.tb, r_ov);
       return ANY ? T.y : fminf(fmaf(fabsf(lim), 1e-6f, lim) + pad, T.y);
     };
-    // Start node: the lowest node holding every leaf slot that a lane's
-    // ray can reach in this view.  A ray hitting a splat passes within the
+    // Start set: the nodes (sx + {0, 1}, sy + {0, 1}) of the lowest level ls
+    // at which the leaf slots that a lane's ray can reach in this view span
+    // at most two nodes per axis.  A ray hitting a splat passes within the
     // view's reach (root hi.w, in pixels) of the splat's slot, and the hit
     // lies on the lane's stretch [t0, T.y] of the ray, so the slots lie in
-    // the projection of that stretch widened by the reach.  Lanes whose
-    // stretch is unbounded keep the root.
-    const int64_t rid = L.node_off[v][top];
-    const float4 rlo = __ldg(L.nodes + 2 * rid), rhi = __ldg(L.nodes + 2 * rid + 1);
+    // the projection of that stretch widened by the reach.  The warp's union
+    // of those rectangles, [rx0, rx1] x [ry0, ry1] in leaf tiles, bounds the
+    // start set and filters the children of every node the walk expands (a
+    // node whose tiles miss it holds no splat a lane can hit).  Lanes whose
+    // stretch is unbounded keep the root and the whole screen.
+    const float4 rhi = __ldg(L.nodes + 2 * L.node_off[v][top] + 1);
     int ls = top, sx = 0, sy = 0;
+    int rx0 = 0, ry0 = 0, rx1 = L.tw[v][0] - 1, ry1 = L.th[v][0] - 1;
     {
       const bool lv = active && !(ANY && hit_any) && T.x <= T.y;
       const bool fin = isfinite(t0) && isfinite(T.y);
@@ -320,95 +324,92 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
         lx1 = __reduce_max_sync(FULL, lx1);
         ly1 = __reduce_max_sync(FULL, ly1);
         if (lx1 < 0) continue;  // no lane reaches a slot of this view
+        rx0 = lx0;
+        rx1 = lx1;
+        ry0 = ly0;
+        ry1 = ly1;
         ls = 0;
-        while (ls < top && ((lx0 >> ls) != (lx1 >> ls) || (ly0 >> ls) != (ly1 >> ls))) ++ls;
+        while (ls < top && ((lx1 >> ls) - (lx0 >> ls) > 1 || (ly1 >> ls) - (ly0 >> ls) > 1)) ++ls;
         sx = lx0 >> ls;
         sy = ly0 >> ls;
       }
     }
-    // the start node's box
-    // occ4: the occupancy masks (lo.w, 16 bits each) of the four children
-    // of the last expanded level-1 node, i.e. of the leaves pending at level
-    // 0, so a leaf visit needs no reload of its node
-    uint64_t occ4 = 0;
-    {
-      const int64_t nid = L.node_off[v][ls] + (int64_t)sy * L.tw[v][ls] + sx;
-      const float4 lo = ls == top ? rlo : __ldg(L.nodes + 2 * nid);
-      const float4 hi = ls == top ? rhi : __ldg(L.nodes + 2 * nid + 1);
-      bool lv = active && !(ANY && hit_any);
-      n_node += lv;
-      if (!warp_meets(L, nid, lo, hi, r, q, d, lv, t0, t_far())) continue;
-      occ4 = __float_as_uint(lo.w) & 0xffffu;  // the start node when it is a leaf
-    }
     // Traversal state, all in registers: `expand` asks to expand node
     // (px, py) of level l (its four children at level l-1 are box-tested
     // together; the accepted ones become pending bits [4(l-1), 4(l-1)+4) of
-    // `masks`).  Otherwise the pending bits of level l are children of node
-    // (px, py) at level l+1; going up one level halves (px, py).  The walk
-    // ends when it climbs back to the start level.
-    uint64_t masks = 0;
-    int l = ls, px = sx, py = sy;
-    bool expand = ls > 0;
+    // `masks`).  Otherwise the pending bits of level l < ls are children of
+    // node (px, py) at level l+1, and those of level ls are the start set;
+    // going up one level halves (px, py).  The walk ends when it climbs
+    // above the start level.  occ4: the occupancy masks (lo.w, 16 bits each)
+    // of the four nodes last tested at level 0, i.e. of the pending leaves,
+    // so a leaf visit needs no reload of its node.
+    uint64_t masks = 0, occ4 = 0;
+    int l = ls + 1, px = 0, py = 0;
+    bool expand = true;
     int leaf_x = 0, leaf_y = 0, leaf_c = 0;
-    bool root_leaf = ls == 0;
     for (;;) {
-      if (root_leaf) {
-        root_leaf = false;
-        leaf_x = sx;
-        leaf_y = sy;
-      } else {
-        if (expand) {
-          expand = false;
-          const int cl = l - 1;
-          const int cw = L.tw[v][cl], ch = L.th[v][cl];
-          const int64_t base = L.node_off[v][cl];
-          float4 blo[4], bhi[4];
-          bool ex[4];
-          int64_t cid[4];
+      if (expand) {
+        expand = false;
+        const int cl = l - 1;
+        const int cw = L.tw[v][cl];
+        const int64_t base = L.node_off[v][cl];
+        float4 blo[4], bhi[4];
+        bool ex[4];
+        int64_t cid[4];
+        // the children (bx + {0, 1}, by + {0, 1}) that lie in the warp's
+        // rectangle at this level (which also keeps them on the screen:
+        // rx1 >> cl < tw[cl])
+        const int bx = cl == ls ? sx : 2 * px, by = cl == ls ? sy : 2 * py;
+        const int xhi = rx1 >> cl, yhi = ry1 >> cl, xlo = rx0 >> cl, ylo = ry0 >> cl;
+        const bool in_x0 = bx >= xlo && bx <= xhi, in_x1 = bx + 1 >= xlo && bx + 1 <= xhi;
+        const bool in_y0 = by >= ylo && by <= yhi, in_y1 = by + 1 >= ylo && by + 1 <= yhi;
+        ex[0] = in_x0 && in_y0;
+        ex[1] = in_x1 && in_y0;
+        ex[2] = in_x0 && in_y1;
+        ex[3] = in_x1 && in_y1;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            int cx = 2 * px + (c & 1), cy = 2 * py + (c >> 1);
-            ex[c] = cx < cw && cy < ch;
-            cid[c] = base + (ex[c] ? (int64_t)cy * cw + cx : 0);
-            blo[c] = __ldg(L.nodes + 2 * cid[c]);
-            bhi[c] = __ldg(L.nodes + 2 * cid[c] + 1);
-          }
-          bool lv = active && !(ANY && hit_any);
-          float t1 = t_far();
-          uint32_t m = 0;
+        for (int c = 0; c < 4; ++c) {
+          const int cx = bx + (c & 1), cy = by + (c >> 1);
+          cid[c] = base + (ex[c] ? (int64_t)cy * cw + cx : 0);
+          blo[c] = __ldg(L.nodes + 2 * cid[c]);
+          bhi[c] = __ldg(L.nodes + 2 * cid[c] + 1);
+        }
+        bool lv = active && !(ANY && hit_any);
+        float t1 = t_far();
+        uint32_t m = 0;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            n_node += lv && ex[c];
-            if (ex[c] && warp_meets(L, cid[c], blo[c], bhi[c], r, q, d, lv, t0, t1)) m |= 1u << c;
-          }
-          if (cl == 0) {
-            occ4 = 0;
+        for (int c = 0; c < 4; ++c) {
+          n_node += lv && ex[c];
+          if (ex[c] && warp_meets(L, cid[c], blo[c], bhi[c], r, q, d, lv, t0, t1)) m |= 1u << c;
+        }
+        if (cl == 0) {
+          occ4 = 0;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-              occ4 |= (uint64_t)(__float_as_uint(blo[c].w) & 0xffffu) << (16 * c);
-          }
-          masks |= (uint64_t)m << (4 * cl);
-          l = cl;
+          for (int c = 0; c < 4; ++c)
+            occ4 |= (uint64_t)(__float_as_uint(blo[c].w) & 0xffffu) << (16 * c);
         }
-        while (l < ls && ((masks >> (4 * l)) & 0xfull) == 0) {
-          ++l;
-          px >>= 1;
-          py >>= 1;
-        }
-        if (l >= ls) break;
-        const int c = __ffs((uint32_t)((masks >> (4 * l)) & 0xfull)) - 1;
-        masks &= ~(1ull << (4 * l + c));
-        const int cx = 2 * px + (c & 1), cy = 2 * py + (c >> 1);
-        if (l > 0) {
-          px = cx;
-          py = cy;
-          expand = true;
-          continue;
-        }
-        leaf_x = cx;
-        leaf_y = cy;
-        leaf_c = c;
+        masks |= (uint64_t)m << (4 * cl);
+        l = cl;
       }
+      while (l <= ls && ((masks >> (4 * l)) & 0xfull) == 0) {
+        ++l;
+        px >>= 1;
+        py >>= 1;
+      }
+      if (l > ls) break;
+      const int c = __ffs((uint32_t)((masks >> (4 * l)) & 0xfull)) - 1;
+      masks &= ~(1ull << (4 * l + c));
+      const int cx = l == ls ? sx + (c & 1) : 2 * px + (c & 1);
+      const int cy = l == ls ? sy + (c >> 1) : 2 * py + (c >> 1);
+      if (l > 0) {
+        px = cx;
+        py = cy;
+        expand = true;
+        continue;
+      }
+      leaf_x = cx;
+      leaf_y = cy;
+      leaf_c = c;
       // leaf tile: test its splats (the occupied slots of the leaf's mask).
       // The warp fetches the whole leaf at once: lane b loads slot b's
       // centre/radius and lane 16 + b its normal (one memory round trip per
