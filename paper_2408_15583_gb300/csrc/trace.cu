@@ -176,6 +176,8 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
     t1 = fminf(t1, fmaxf(a, b));
   }
   if (!(t0 <= t1)) return m;
+  // the DDA state per axis in named registers (a runtime axis index into
+  // small arrays would put them in local memory)
   int ix[3], st[3];
   float tmax[3], tdel[3];
   for (int k = 0; k < 3; ++k) {
@@ -196,12 +198,19 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
       tdel[k] = INFINITY;
     }
   }
+  int x0 = ix[0], x1 = ix[1], x2 = ix[2];
+  float m0 = tmax[0], m1 = tmax[1], m2 = tmax[2];
+  const float d0 = tdel[0], d1 = tdel[1], d2 = tdel[2];
+  const int s0 = st[0], s1 = st[1], s2 = st[2];
   float t_in = t0;
   bool ended = false;
   for (int it = 0; it < 3 * n + 3; ++it) {
-    const int k = tmax[0] < tmax[1] ? (tmax[0] < tmax[2] ? 0 : 2) : (tmax[1] < tmax[2] ? 1 : 2);
-    const float t_out = tmax[k];
-    const uint32_t b = __ldg(L.vmask + ((int64_t)ix[0] * n + ix[1]) * n + ix[2]) & ~outside;
+    // the axis whose boundary comes first (ties as x < y < z order of the
+    // comparisons: k = m0 < m1 ? (m0 < m2 ? 0 : 2) : (m1 < m2 ? 1 : 2))
+    const bool k0 = m0 < m1 && m0 < m2;
+    const bool k1 = !(m0 < m1) && m1 < m2;
+    const float t_out = k0 ? m0 : (k1 ? m1 : m2);
+    const uint32_t b = __ldg(L.vmask + ((int64_t)x0 * n + x1) * n + x2) & ~outside;
     for (uint32_t r = b; r; r &= r - 1) {
       const int v = __ffs(r) - 1;
       float2 &T = tv[v * stride];
@@ -213,12 +222,20 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
       ended = true;
       break;
     }
-    ix[k] += st[k];
-    if (ix[k] < 0 || ix[k] >= n) {
+    if (k0) {
+      x0 += s0;
+      m0 = m0 + d0;
+    } else if (k1) {
+      x1 += s1;
+      m1 = m1 + d1;
+    } else {
+      x2 += s2;
+      m2 = m2 + d2;
+    }
+    if ((unsigned)x0 >= (unsigned)n || (unsigned)x1 >= (unsigned)n || (unsigned)x2 >= (unsigned)n) {
       ended = true;
       break;
     }
-    tmax[k] += tdel[k];
     t_in = t_out;
   }
   if (!ended)  // cannot happen for a line through an n^3 grid; stay conservative
@@ -628,11 +645,12 @@ __device__ __forceinline__ bool tile_pixel(const tile_map &m, int W, int H, int6
   return i < W && j < H;
 }
 
-// Bounce 1 from the incidence screen's GFB keys (or, geom_first, by marching
-// the splats from the screen).  Writes every slot's M and Psi, and the rest
-// of the record for the rays that hit.
+// Bounce 1 by marching the splats from the incidence screen (the first
+// bounce taken from the aggregated geometry, in 8x4 tiles for the warp's
+// walk).  Writes every slot's M and Psi, and the rest of the record for the
+// rays that hit.
 __global__ void __launch_bounds__(kTraceThreads)
-    primary_kernel(const __grid_constant__ march_args A, int geom_first) {
+    primary_kernel(const __grid_constant__ march_args A) {
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
   const tile_map tm = make_tile_map(W, H, A.vb.n);
@@ -655,20 +673,7 @@ __global__ void __launch_bounds__(kTraceThreads)
     pe_f3 x = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 0.f};
     uint32_t id = PE_NONE;
     nq += active;
-    if (geom_first) {
-      hit = nearest(A.L, o, d, 0.0f, A.r_ov, active, A.err, x, n, id, ns, nn, nv);
-    } else if (active) {
-      unsigned long long key = A.keys[slot];
-      if (key != ~0ull) {
-        hit = true;
-        float tt = __uint_as_float((uint32_t)(key >> 32));
-        id = (uint32_t)(key & 0xffffffffull);
-        x = pe_ray_at(o, tt, d);
-        n = {__ldg(A.nrm + 3 * (int64_t)id), __ldg(A.nrm + 3 * (int64_t)id + 1),
-             __ldg(A.nrm + 3 * (int64_t)id + 2)};
-        if (pe_dot(n, d) > 0.0f) n = pe_neg3(n);
-      }
-    }
+    hit = nearest(A.L, o, d, 0.0f, A.r_ov, active, A.err, x, n, id, ns, nn, nv);
     if (active) {
       A.h.M[slot] = hit ? 1 : 0;
       A.h.psi[slot] = 1;
@@ -685,6 +690,51 @@ __global__ void __launch_bounds__(kTraceThreads)
     }
   }
   flush_stats(A.stats, sacc, nq, 0, ns, nn, nv);
+}
+
+// Bounce 1 from the incidence screen's GFB keys, one thread per slot in
+// slot order: no walk, so no tiles; a warp reads 32 consecutive keys and
+// writes 32 consecutive records (whole cache lines), and the kernel's few
+// registers keep the SMs full of loads and stores in flight.
+__global__ void __launch_bounds__(kTraceThreads)
+    primary_gfb_kernel(const __grid_constant__ march_args A) {
+  const int W = A.vb.W;
+  const int64_t per_view = (int64_t)W * A.vb.H;
+  const int64_t n = per_view * A.vb.n;
+  __shared__ stats_acc sacc;
+  stats_begin(sacc);
+  long long nq = 0;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < n;
+       slot += (int64_t)gridDim.x * blockDim.x) {
+    const int vi = (int)(slot / per_view);
+    const int64_t r = slot - (int64_t)vi * per_view;
+    const int j = (int)(r / W), i = (int)(r - (int64_t)j * W);
+    const pe_view &V = A.vb.v[vi];
+    ++nq;
+    const unsigned long long key = __ldcs(A.keys + slot);
+    A.h.psi[slot] = 1;
+    if (key == ~0ull) {
+      A.h.M[slot] = 0;
+      if (A.h.ids) A.h.ids[slot] = PE_NONE;
+      continue;
+    }
+    const pe_f3 o = pe_pixel_origin(V, i, j);
+    const pe_f3 d = pe_v3(V.d);
+    const uint32_t id = (uint32_t)(key & 0xffffffffull);
+    const pe_f3 x = pe_ray_at(o, __uint_as_float((uint32_t)(key >> 32)), d);
+    pe_f3 nn = {__ldg(A.nrm + 3 * (int64_t)id), __ldg(A.nrm + 3 * (int64_t)id + 1),
+                __ldg(A.nrm + 3 * (int64_t)id + 2)};
+    if (pe_dot(nn, d) > 0.0f) nn = pe_neg3(nn);
+    A.h.M[slot] = 1;
+    if (A.h.ids) A.h.ids[slot] = id;
+    st3(A.h.p, slot, x);
+    st3(A.h.n, slot, nn);
+    st3(A.h.k, slot, d);
+    st3(A.h.u, slot, {pe_mul(V.pitch, V.u[0]), pe_mul(V.pitch, V.u[1]), pe_mul(V.pitch, V.u[2])});
+    st3(A.h.v, slot, {pe_mul(V.pitch, V.v[0]), pe_mul(V.pitch, V.v[1]), pe_mul(V.pitch, V.v[2])});
+    A.h.path[slot] = path_start(d, x);
+  }
+  flush_stats(A.stats, sacc, nq, 0, 0, 0, 0);
 }
 
 // One bounce (b >= 2).  Threads map to slots by the same 8x4 tiles as bounce
@@ -829,6 +879,21 @@ int grid_all(int64_t n) {
   return (int)(b < 0x7fffffff ? b : 0x7fffffff);
 }
 
+// A streaming pass: enough blocks of kTraceThreads to fill every SM several
+// times over, each looping over the slots with a grid stride.
+int grid_stream(int64_t n) {
+  static int sm = 0;
+  if (!sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev);
+    if (sm <= 0) sm = 1;
+  }
+  const int64_t cap = (int64_t)sm * 16;
+  const int64_t b = (n + kTraceThreads - 1) / kTraceThreads;
+  return (int)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
 
 bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
   if (!g || !g->blob_dev) return false;
@@ -882,9 +947,15 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   // per-lane ray intervals of every view (walk's shared memory)
   const size_t tv_bytes = have_geom ? (size_t)A.L.nv * kTraceThreads * sizeof(float2) : 0;
   pe_event_before("primary_kernel", s);
-  primary_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A, prm.first_bounce_from_geom ? 1 : 0);
-  pe_event_after("primary_kernel", s);
-  PE_TRY_LAUNCH("primary_kernel");
+  if (prm.first_bounce_from_geom) {
+    primary_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A);
+    pe_event_after("primary_kernel", s);
+    PE_TRY_LAUNCH("primary_kernel");
+  } else {
+    primary_gfb_kernel<<<grid_stream(n_rays), kTraceThreads, 0, s>>>(A);
+    pe_event_after("primary_kernel", s);
+    PE_TRY_LAUNCH("primary_gfb_kernel");
+  }
   for (int b = 2; b <= mb; ++b) {
     A.bounce = b;
     pe_event_before("march_kernel", s);
