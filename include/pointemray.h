@@ -108,8 +108,10 @@ typedef struct {
  * A splat's id is its owner pixel's global index off_v + p.
  * The blob also holds a coarse 32^3 grid over the fusion bounding box: per
  * cell, a bit mask of the views that own a splat whose (padded) sphere
- * overlaps the cell, plus one mask of views with splats outside the grid;
- * rays only descend the pyramids of views met along their path.
+ * overlaps the cell, plus one mask of views with splats outside the grid,
+ * and per cell a slab (an axis and an interval of heights along it) bounding
+ * every disk its mask counts; rays only descend the pyramids of views met
+ * along their path, within the stretches of the ray inside those slabs.
  * Layout is fully determined by the views; use pe_geom_bytes() to size it.
  * vgrid_* are written by pe_aggregate_views (callers leave them zero). */
 #ifndef PE_VGRID

@@ -626,13 +626,48 @@ __global__ void slab_clear_kernel(float4 *__restrict__ slab, float *__restrict__
   }
 }
 
-// Coarse view-occupancy grid: every splat marks, with its owner view's bit,
-// the cells its disk's bounding box overlaps (per world axis k the disk
-// reaches R sqrt(1 - n_k^2) from its centre), padded by 1 % of a cell and for
-// rounding; splats reaching outside the grid mark the extra word vmask[n^3].
-__global__ void vgrid_kernel(const __grid_constant__ pe_geom_layout L, uint32_t *__restrict__ vmask) {
+// The cells of the coarse grid that splat g marks: per world axis k the disk
+// reaches R sqrt(1 - n_k^2) from its centre, padded by 1 % of a cell and the
+// view's box pad (for rounding); cells clamped to the grid, `outside` when
+// the padded box leaves it.  The view mask, the cell slabs' axes and their
+// heights all take the same cells.
+struct cell_box {
+  int lo[3], hi[3];
+  bool outside;
+};
+__device__ __forceinline__ cell_box splat_cells(const pe_geom_layout &L, float4 c, float4 nn,
+                                                int v) {
   const int n = L.vg_n;
   const float cell = L.vg_cell;
+  const float cc[3] = {c.x, c.y, c.z}, nk[3] = {nn.x, nn.y, nn.z};
+  cell_box b;
+  b.outside = false;
+  for (int k = 0; k < 3; ++k) {
+    const float pad = c.w * 1.00001f * sqrtf(fmaxf(1.0f - nk[k] * nk[k], 0.0f) + 1e-6f) +
+                      1e-2f * cell + L.pad[v];
+    float a = floorf((cc[k] - pad - L.vg_min[k]) / cell);
+    float e = floorf((cc[k] + pad - L.vg_min[k]) / cell);
+    if (!(a >= 0.0f) || !(e <= (float)(n - 1))) b.outside = true;
+    b.lo[k] = (int)fminf(fmaxf(a, 0.0f), (float)(n - 1));
+    b.hi[k] = (int)fminf(fmaxf(e, 0.0f), (float)(n - 1));
+  }
+  return b;
+}
+
+// Fixed-point scale of the cell axis sums (a normal component times 2^32,
+// summed in 64-bit integers: the sum does not depend on the atomics' order;
+// 2^28 terms at most, far below overflow).
+constexpr float kAxisScale = 4294967296.0f;
+
+// Coarse view-occupancy grid: every splat marks its cells with its owner
+// view's bit (vmask[n^3] for splats reaching outside the grid), adds its
+// normal, turned toward its view, to each cell's axis sum and counts itself
+// there.
+__global__ void vgrid_kernel(const __grid_constant__ pe_geom_layout L, uint32_t *__restrict__ vmask,
+                             unsigned long long *__restrict__ axis_sum,
+                             unsigned int *__restrict__ axis_cnt) {
+  const int n = L.vg_n;
+  const int64_t n3 = (int64_t)n * n * n;
   const int64_t total = L.pix_off[L.nv];
   for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -641,22 +676,108 @@ __global__ void vgrid_kernel(const __grid_constant__ pe_geom_layout L, uint32_t 
     const int v = view_of(L, g);
     const uint32_t bit = 1u << v;
     const float4 nn = L.nf[g];
-    const float cc[3] = {c.x, c.y, c.z}, nk[3] = {nn.x, nn.y, nn.z};
-    int lo[3], hi[3];
-    bool outside = false;
-    for (int k = 0; k < 3; ++k) {
-      const float pad = c.w * 1.00001f * sqrtf(fmaxf(1.0f - nk[k] * nk[k], 0.0f) + 1e-6f) +
-                        1e-2f * cell + L.pad[v];
-      float a = floorf((cc[k] - pad - L.vg_min[k]) / cell);
-      float b = floorf((cc[k] + pad - L.vg_min[k]) / cell);
-      if (!(a >= 0.0f) || !(b <= (float)(n - 1))) outside = true;
-      lo[k] = (int)fminf(fmaxf(a, 0.0f), (float)(n - 1));
-      hi[k] = (int)fminf(fmaxf(b, 0.0f), (float)(n - 1));
+    const pe_view &V = L.view[v];
+    const float sg = (nn.x * V.d[0] + nn.y * V.d[1] + nn.z * V.d[2]) > 0.0f ? -1.0f : 1.0f;
+    const unsigned long long qx = (unsigned long long)__float2ll_rn(sg * nn.x * kAxisScale);
+    const unsigned long long qy = (unsigned long long)__float2ll_rn(sg * nn.y * kAxisScale);
+    const unsigned long long qz = (unsigned long long)__float2ll_rn(sg * nn.z * kAxisScale);
+    const cell_box b = splat_cells(L, c, nn, v);
+    if (b.outside) atomicOr(vmask + n3, bit);
+    for (int x = b.lo[0]; x <= b.hi[0]; ++x)
+      for (int y = b.lo[1]; y <= b.hi[1]; ++y)
+        for (int z = b.lo[2]; z <= b.hi[2]; ++z) {
+          const int64_t cid = ((int64_t)x * n + y) * n + z;
+          atomicOr(vmask + cid, bit);
+          atomicAdd(axis_sum + 3 * cid, qx);
+          atomicAdd(axis_sum + 3 * cid + 1, qy);
+          atomicAdd(axis_sum + 3 * cid + 2, qz);
+          atomicAdd(axis_cnt + cid, 1u);
+        }
+  }
+}
+
+// A float as an unsigned key with the same order (for atomicMin/Max).
+__device__ __forceinline__ unsigned int f_key(float f) {
+  const unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_f(unsigned int k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Per cell: the axis (normalised sum; none for an empty cell or when the
+// normals cancel, as for the node slabs), and the height keys' start values.
+__global__ void cell_axis_kernel(int64_t n3, const unsigned long long *__restrict__ axis_sum,
+                                 const unsigned int *__restrict__ axis_cnt,
+                                 float4 *__restrict__ axis, unsigned int *__restrict__ hkey) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double inv = 1.0 / (double)kAxisScale;
+    const double sx = (double)(long long)axis_sum[3 * i] * inv;
+    const double sy = (double)(long long)axis_sum[3 * i + 1] * inv;
+    const double sz = (double)(long long)axis_sum[3 * i + 2] * inv;
+    const double cnt = (double)axis_cnt[i];
+    const double len = sqrt(sx * sx + sy * sy + sz * sz);
+    if (cnt > 0.0 && len > 1e-3 * cnt)
+      axis[i] = make_float4((float)(sx / len), (float)(sy / len), (float)(sz / len), 1.0f);
+    else
+      axis[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    hkey[2 * i] = 0xffffffffu;  // lowest height: min over keys
+    hkey[2 * i + 1] = 0u;       // highest height: max over keys
+  }
+}
+
+// Heights axis . (x - cell centre) over the disks a cell counts: the centre's
+// height +- R sqrt(1 - (axis . m)^2), padded like the node slabs.
+__global__ void cell_height_kernel(const __grid_constant__ pe_geom_layout L,
+                                   const float4 *__restrict__ axis,
+                                   unsigned int *__restrict__ hkey) {
+  const int n = L.vg_n;
+  const float cell = L.vg_cell;
+  const int64_t total = L.pix_off[L.nv];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    float4 c = L.cr[g];
+    if (!(c.w > 0.0f)) continue;
+    const int v = view_of(L, g);
+    const float4 m = L.nf[g];
+    const cell_box b = splat_cells(L, c, m, v);
+    const float rx = c.x - L.vg_min[0], ry = c.y - L.vg_min[1], rz = c.z - L.vg_min[2];
+    for (int x = b.lo[0]; x <= b.hi[0]; ++x)
+      for (int y = b.lo[1]; y <= b.hi[1]; ++y)
+        for (int z = b.lo[2]; z <= b.hi[2]; ++z) {
+          const int64_t cid = ((int64_t)x * n + y) * n + z;
+          const float4 a = axis[cid];
+          if (a.w == 0.0f) continue;
+          const float h = a.x * (rx - (x + 0.5f) * cell) + a.y * (ry - (y + 0.5f) * cell) +
+                          a.z * (rz - (z + 0.5f) * cell);
+          const float am = a.x * m.x + a.y * m.y + a.z * m.z;
+          const float e = c.w * 1.000001f * sqrtf(fmaxf(1.0f - am * am, 0.0f) + 1e-6f) + L.pad[v];
+          atomicMin(hkey + 2 * cid, f_key(h - e));
+          atomicMax(hkey + 2 * cid + 1, f_key(h + e));
+        }
+  }
+}
+
+// The cell slabs in the form the march tests (see pe_geom_layout::cslab),
+// padded by 1e-3 of a cell and 1e-5 of the grid's coordinate magnitude: far
+// above the rounding of the heights here and of the ray positions in the
+// march, so every point of a counted disk passes.
+__global__ void cell_slab_kernel(int64_t n3, const float4 *__restrict__ axis,
+                                 const unsigned int *__restrict__ hkey, float pad,
+                                 float4 *__restrict__ cslab) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = axis[i];
+    const unsigned int klo = hkey[2 * i], khi = hkey[2 * i + 1];
+    if (a.w == 0.0f || klo == 0xffffffffu) {
+      cslab[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
     }
-    if (outside) atomicOr(vmask + (int64_t)n * n * n, bit);
-    for (int x = lo[0]; x <= hi[0]; ++x)
-      for (int y = lo[1]; y <= hi[1]; ++y)
-        for (int z = lo[2]; z <= hi[2]; ++z) atomicOr(vmask + ((int64_t)x * n + y) * n + z, bit);
+    const float lo = key_f(klo), hi = key_f(khi);
+    const float half = 0.5f * (hi - lo) + pad;
+    const float mid = 0.5f * (hi + lo);
+    cslab[i] = make_float4(a.x / half, a.y / half, a.z / half, mid / half);
   }
 }
 
@@ -682,6 +803,10 @@ struct agg_ws {
   unsigned long long *entries;
   uint8_t *canny_state;     // edge mode 1 (the other Canny buffers alias
   unsigned int *changed;    // entries and vox_of, which the fusion fills later)
+  unsigned long long *axis_sum;  // cell slabs: [n^3][3] fixed-point normal sums
+  unsigned int *axis_cnt;        // [n^3]
+  float4 *axis;                  // [n^3] axis, w = 1 when the cell has one
+  unsigned int *hkey;            // [n^3][2] lowest / highest height keys
 };
 
 agg_ws carve_agg(pe_carve &c, int64_t total_pix, int G) {
@@ -694,6 +819,11 @@ agg_ws carve_agg(pe_carve &c, int64_t total_pix, int G) {
   w.entries = c.take<unsigned long long>((size_t)total_pix);
   w.canny_state = c.take<uint8_t>((size_t)total_pix);
   w.changed = c.take<unsigned int>(1);
+  const int64_t n3 = (int64_t)PE_VGRID * PE_VGRID * PE_VGRID;
+  w.axis_sum = c.take<unsigned long long>((size_t)n3 * 3);
+  w.axis_cnt = c.take<unsigned int>((size_t)n3);
+  w.axis = c.take<float4>((size_t)n3);
+  w.hkey = c.take<unsigned int>((size_t)n3 * 2);
   return w;
 }
 
@@ -746,8 +876,8 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   for (int v = 0; v < n_views; ++v)
     if (memcmp(&out->views[v], &views[v], sizeof(pe_view)) != 0)
       return pe_fail(PE_EINVAL, "pe_aggregate_views: out->views differ from views");
-  size_t o_cr, o_nf, o_nodes, o_vm, o_slab, o_slab_hi, tot;
-  pe_layout_offsets(L, &o_cr, &o_nf, &o_nodes, &o_vm, &o_slab, &o_slab_hi, &tot);
+  size_t o_cr, o_nf, o_nodes, o_vm, o_slab, o_slab_hi, o_cslab, tot;
+  pe_layout_offsets(L, &o_cr, &o_nf, &o_nodes, &o_vm, &o_slab, &o_slab_hi, &o_cslab, &tot);
   if (out->blob_bytes < tot || !pe_aligned(out->blob_dev, 256))
     return pe_fail(PE_ENOMEM, "pe_aggregate_views: geometry blob needs %zu bytes", tot);
   size_t need = pe_aggregate_workspace(n_views, views, G);
@@ -761,6 +891,7 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   uint32_t *vmask = reinterpret_cast<uint32_t *>(blob + o_vm);
   float4 *slab = reinterpret_cast<float4 *>(blob + o_slab);
   float *slab_hi = reinterpret_cast<float *>(blob + o_slab_hi);
+  float4 *cslab = reinterpret_cast<float4 *>(blob + o_cslab);
   L.cr = cr;
   L.nf = nf;
   L.nodes = nodes;
@@ -831,9 +962,25 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   fuse_segment_kernel<<<grid_for(total_pix, 128, cap), 128, 0, s>>>(L, nd, w.entries, w.offs,
                                                                      nvox, cr, nf);
   PE_TRY_LAUNCH("fuse_segment_kernel");
-  PE_TRY_CUDA(cudaMemsetAsync(vmask, 0, sizeof(uint32_t) * ((size_t)PE_VGRID * PE_VGRID * PE_VGRID + 1), s));
-  vgrid_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, vmask);
+  const int64_t n3 = (int64_t)PE_VGRID * PE_VGRID * PE_VGRID;
+  PE_TRY_CUDA(cudaMemsetAsync(vmask, 0, sizeof(uint32_t) * ((size_t)n3 + 1), s));
+  PE_TRY_CUDA(cudaMemsetAsync(w.axis_sum, 0, sizeof(unsigned long long) * 3 * (size_t)n3, s));
+  PE_TRY_CUDA(cudaMemsetAsync(w.axis_cnt, 0, sizeof(unsigned int) * (size_t)n3, s));
+  vgrid_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, vmask, w.axis_sum, w.axis_cnt);
   PE_TRY_LAUNCH("vgrid_kernel");
+  cell_axis_kernel<<<grid_for(n3, 256, cap), 256, 0, s>>>(n3, w.axis_sum, w.axis_cnt, w.axis,
+                                                          w.hkey);
+  PE_TRY_LAUNCH("cell_axis_kernel");
+  cell_height_kernel<<<grid_for(total_pix, 256, cap), 256, 0, s>>>(L, w.axis, w.hkey);
+  PE_TRY_LAUNCH("cell_height_kernel");
+  {
+    float mag = 0.0f;
+    for (int k = 0; k < 3; ++k)
+      mag = fmaxf(mag, fabsf(L.vg_min[k]) + L.vg_cell * (float)L.vg_n);
+    const float pad = 1e-3f * L.vg_cell + 1e-5f * mag;
+    cell_slab_kernel<<<grid_for(n3, 256, cap), 256, 0, s>>>(n3, w.axis, w.hkey, pad, cslab);
+    PE_TRY_LAUNCH("cell_slab_kernel");
+  }
   out->vgrid_n = L.vg_n;
   out->vgrid_cell = L.vg_cell;
   for (int k = 0; k < 3; ++k) out->vgrid_min[k] = L.vg_min[k];

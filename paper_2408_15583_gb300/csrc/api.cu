@@ -159,7 +159,7 @@ bool pe_make_layout(int32_t nv, const pe_view *views, pe_geom_layout *L) {
 
 void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
                        size_t *off_nodes, size_t *off_vmask, size_t *off_slab,
-                       size_t *off_slab_hi, size_t *total) {
+                       size_t *off_slab_hi, size_t *off_cslab, size_t *total) {
   pe_carve c{nullptr, 0};
   int64_t np = L.pix_off[L.nv];
   c.take<float4>((size_t)np);
@@ -179,13 +179,16 @@ void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
   size_t f = c.bytes();
   c.take<float>((size_t)L.n_nodes);
   *off_slab_hi = f;
+  size_t g = c.bytes();
+  c.take<float4>((size_t)PE_VGRID * PE_VGRID * PE_VGRID);
+  *off_cslab = g;
   *total = c.bytes();
 }
 
 extern "C" size_t pe_geom_bytes(int32_t n_views, const pe_view *views) {
   pe_geom_layout L;
   if (!pe_make_layout(n_views, views, &L)) return 0;
-  size_t a, b, c, d, e, f, t;
-  pe_layout_offsets(L, &a, &b, &c, &d, &e, &f, &t);
+  size_t a, b, c, d, e, f, g, t;
+  pe_layout_offsets(L, &a, &b, &c, &d, &e, &f, &g, &t);
   return t;
 }

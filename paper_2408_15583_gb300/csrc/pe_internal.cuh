@@ -95,6 +95,11 @@ struct pe_geom_layout {
   // coarse view-occupancy grid: vmask[(ix*n + iy)*n + iz], vmask[n^3] = views
   // with splats outside the grid; n = 0: no grid (walk every view)
   const uint32_t *vmask;
+  // per cell of that grid, a slab bounding every disk the cell's mask counts:
+  // {axis / h, mid / h} with heights axis . (x - cell centre) within mid +- h
+  // (padded); a point x of those disks has |cslab.xyz . (x - centre) -
+  // cslab.w| <= 1.  All zeros: no slab (every point passes).
+  const float4 *cslab;
   float vg_min[3];
   float vg_cell;
   int32_t vg_n;
@@ -110,7 +115,7 @@ pe_status pe_exclusive_scan_u32(const uint32_t *in, int64_t n, uint32_t *tile, u
 // Blob byte offsets of the arrays for a layout.
 void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
                        size_t *off_nodes, size_t *off_vmask, size_t *off_slab,
-                       size_t *off_slab_hi, size_t *total);
+                       size_t *off_slab_hi, size_t *off_cslab, size_t *total);
 
 // ---------------------------------------------------------------------------
 // Launchers shared between entry points

@@ -210,12 +210,31 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
     const bool k0 = m0 < m1 && m0 < m2;
     const bool k1 = !(m0 < m1) && m1 < m2;
     const float t_out = k0 ? m0 : (k1 ? m1 : m2);
-    const uint32_t b = __ldg(L.vmask + ((int64_t)x0 * n + x1) * n + x2) & ~outside;
+    const int64_t cid = ((int64_t)x0 * n + x1) * n + x2;
+    uint32_t b = __ldg(L.vmask + cid) & ~outside;
+    float s_in = t_in, s_out = t_out;
+    if (b) {
+      // the cell's slab: the ray's stretch through the cell that lies inside
+      // it, [s_in, s_out] (|hs + t hd| <= 1 in the slab's scaled heights);
+      // a stretch outside the slab meets none of the cell's disks, so the
+      // cell adds no view
+      const float4 cs = __ldg(L.cslab + cid);
+      const float qx = fmaf(-((float)x0 + 0.5f), cell, oo[0]);
+      const float qy = fmaf(-((float)x1 + 0.5f), cell, oo[1]);
+      const float qz = fmaf(-((float)x2 + 0.5f), cell, oo[2]);
+      const float hs = fmaf(cs.x, qx, fmaf(cs.y, qy, fmaf(cs.z, qz, -cs.w)));
+      const float hd = fmaf(cs.x, dd[0], fmaf(cs.y, dd[1], cs.z * dd[2]));
+      const float r = __fdividef(1.0f, slab_dir(hd));
+      const float ta = (-1.0f - hs) * r, tb = (1.0f - hs) * r;
+      s_in = fmaxf(s_in, fminf(ta, tb));
+      s_out = fminf(s_out, fmaxf(ta, tb));
+      if (!(s_in <= s_out)) b = 0u;
+    }
     for (uint32_t r = b; r; r &= r - 1) {
       const int v = __ffs(r) - 1;
       float2 &T = tv[v * stride];
-      if (!((m >> v) & 1u)) T.x = t_in;
-      T.y = t_out;
+      if (!((m >> v) & 1u)) T.x = s_in;
+      T.y = s_out;
     }
     m |= b;
     if (t_out > t1) {
@@ -898,8 +917,8 @@ int grid_stream(int64_t n) {
 bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
   if (!g || !g->blob_dev) return false;
   if (!pe_make_layout(g->n_views, g->views, L)) return false;
-  size_t a, b, c, d, e, f, t;
-  pe_layout_offsets(*L, &a, &b, &c, &d, &e, &f, &t);
+  size_t a, b, c, d, e, f, cs, t;
+  pe_layout_offsets(*L, &a, &b, &c, &d, &e, &f, &cs, &t);
   if (g->blob_bytes < t) return false;
   char *blob = static_cast<char *>(g->blob_dev);
   L->cr = reinterpret_cast<const float4 *>(blob + a);
@@ -908,6 +927,7 @@ bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
   L->vmask = reinterpret_cast<const uint32_t *>(blob + d);
   L->slab = reinterpret_cast<const float4 *>(blob + e);
   L->slab_hi = reinterpret_cast<const float *>(blob + f);
+  L->cslab = reinterpret_cast<const float4 *>(blob + cs);
   if (g->vgrid_n == PE_VGRID && g->vgrid_cell > 0.0f) {
     L->vg_n = g->vgrid_n;
     L->vg_cell = g->vgrid_cell;
