@@ -183,8 +183,10 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     # timed region: K steps, L2 flushed between steps (outside the events);
-    # the library also records events around every march_kernel launch on
-    # the launching stream (the dominant kernel) for the roofline.
+    # the library also records events around every PO field launch on the
+    # launching stream (the step's dominant kernel on this workload) for the
+    # roofline; the march kernel's launches are timed the same way in the
+    # end-to-end steps below.
     max_pairs = 512
     mev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * max_pairs)]
     for e in mev:          # torch creates the CUDA event on its first record
@@ -195,7 +197,7 @@ def run_gpu(args, rank, world, local_rank):
     clk.start()
     l0 = lib.pe_kernel_launches()
     barrier()
-    lib.pe_set_kernel_events(b"march_kernel", mev_ptrs, max_pairs)
+    lib.pe_set_kernel_events(b"po_kernel", mev_ptrs, max_pairs)
     total_ms = 0.0
     for _ in range(args.steps):
         flush.zero_()
@@ -209,13 +211,14 @@ def run_gpu(args, rank, world, local_rank):
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
     barrier()
-    n_march = lib.pe_set_kernel_events(None, None, 0)
+    n_po = lib.pe_set_kernel_events(None, None, 0)
     launches = lib.pe_kernel_launches() - l0
     clocks = clk.stop()
     api.stream_check()
-    march_ms = [mev[2 * k].elapsed_time(mev[2 * k + 1]) for k in range(n_march)]
+    po_ms = [mev[2 * k].elapsed_time(mev[2 * k + 1]) for k in range(n_po)]
+    po_terms = int(st[7])                                 # Eq. 14 terms per step
+    po_launches_per_step = max(1, n_po // args.steps)
     march_queries = int(st[0]) - A * sw.W * sw.H          # bounce >= 2 queries per step
-    march_launches_per_step = max(1, n_march // args.steps)
 
     # end to end through the C ABI with host buffers: pinned H2D of the
     # points each step, D2H of the field and sigma
@@ -226,6 +229,7 @@ def run_gpu(args, rank, world, local_rank):
     hS = torch.empty(sig.shape, dtype=sig.dtype).pin_memory()
     dp, dn, dr = torch.empty_like(pos), torch.empty_like(nrm), torch.empty_like(rad)
     barrier()
+    lib.pe_set_kernel_events(b"march_kernel", mev_ptrs, max_pairs)
     e2e_ms = 0.0
     for _ in range(args.steps):
         flush.zero_()
@@ -242,6 +246,9 @@ def run_gpu(args, rank, world, local_rank):
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     barrier()
+    n_march = lib.pe_set_kernel_events(None, None, 0)
+    march_ms = [mev[2 * k].elapsed_time(mev[2 * k + 1]) for k in range(n_march)]
+    march_launches_per_step = max(1, n_march // args.steps)
     h2d = int(hp.numel() * 4 + hn.numel() * 4 + hr.numel() * 4)
     d2h = int(hE.numel() * 8 + hS.numel() * 8)
 
@@ -268,15 +275,25 @@ def run_gpu(args, rank, world, local_rank):
     phases = {"point_attributes_ms": pattr_ms, "gfb_views_and_fusion_ms": geom_ms,
               "sweep_ms": sweep_ms, "sweep_ms_per_angle": sweep_ms / A}
 
-    # roofline of the dominant kernel (march_kernel, timed in the steps above)
-    roof = roofline_march(march_ms, march_queries / march_launches_per_step)
+    # rooflines of the two largest kernels, each timed per launch with CUDA
+    # events on the launching stream inside timed steps; `roofline` is the
+    # one with more device time per step
+    roof_po = roofline_po(po_ms, po_terms / po_launches_per_step,
+                          "po_rot_kernel" if F >= 2 else "po_kernel",
+                          clocks.get("sm_mhz") if isinstance(clocks, dict) else None,
+                          A * sw.W * sw.H / po_launches_per_step)
+    roof_march = roofline_march(march_ms, march_queries / march_launches_per_step)
+    for r, n in ((roof_po, n_po), (roof_march, n_march)):
+        if r:
+            r["ms_per_step"] = r["ms_per_launch"] * n / args.steps
+    cands = [r for r in (roof_po, roof_march) if r]
+    roof = max(cands, key=lambda r: r["ms_per_step"]) if cands else None
+    others = {("roofline_march" if r is roof_march else "roofline_po"): r
+              for r in cands if r is not roof}
     # the incidence splats of one sweep: 64-bit key updates per second
     # against the measured fire-and-forget atomicMin rate of this device
     roof_splat = roofline_splat(lib, api, sargs, pos, nrm, rad, geom, prm, ws, E, sig, dev,
                                 stream)
-    # the PO field kernel, timed alone on the launching stream
-    roof_po = roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream,
-                          clocks.get("sm_mhz") if isinstance(clocks, dict) else None)
 
     # the job: units of all ranks over the slowest rank's time
     job_units, t_ms, value = shard.job_throughput(bounces_per_step * args.steps, total_ms, dev)
@@ -307,7 +324,7 @@ def run_gpu(args, rank, world, local_rank):
                 "rcs_samples_per_s": samples / (e2e_ms / 1e3)},
         "phases": phases,
         "roofline": roof,
-        "roofline_po": roof_po,
+        **others,
         "roofline_splat": roof_splat,
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -327,14 +344,23 @@ MARCH_BYTES_PER_QUERY = 152
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 441.7 MB
+# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 440.7 MB
 # over 6,332,964 queries), valid only for the sources it was taken on (their
 # SHA-256 prefixes); scaled to a full launch by the number of queries.
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 69.7,
-                     "sources": {"include/pointemray.h": "ebaf4ce1ba6be3d4",
-                                 "paper_2408_15583_gb300/csrc/trace.cu": "8478cf218437cb2f",
-                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "0b2baddc9be50ddd",
-                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "fa84708542497d5a"}}
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 69.58,
+                     "sources": {"include/pointemray.h": "409aa4b309cdd7f0",
+                                 "paper_2408_15583_gb300/csrc/trace.cu": "db061c3dfe644367",
+                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "a14be3f8629c9849",
+                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "f70f79715eb43faf"}}
+
+# DRAM bytes (read + write) per ray slot of po_rot_kernel from one ncu capture
+# of one 8-angle sphere batch (profiles/po_kernel_sphere_batch.md: 483.6 MB
+# over 8 x 1024^2 slots), valid for the sources it was taken on; scaled to a
+# full launch by its slots (angles x W x H).
+PO_NCU_TRAFFIC = {"bytes_per_slot": 57.65,
+                  "sources": {"include/pointemray.h": "409aa4b309cdd7f0",
+                              "paper_2408_15583_gb300/csrc/po.cu": "9a53dc870eaf92b2",
+                              "paper_2408_15583_gb300/csrc/pe_internal.cuh": "a14be3f8629c9849"}}
 
 
 def _traffic_valid(rec):
@@ -406,45 +432,28 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def roofline_po(api, pipeline, sc, sw, pos, nrm, rad, geom, prm, dev, stream, sm_mhz=None):
-    """Time pe_po_field alone (same kernel and launch shape as inside the
-    sweep) on one batch of traced angles; ALU roofline."""
-    import torch
-    nb = min(sw.n_angles, 16)
-    views = [api.view_from_angles(sw.theta_deg[a], sw.phi_deg[a], sw.centre, sw.extent, sw.W, sw.H)
-             for a in range(nb)]
-    keys = api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))["keys"]
-    h = api.trace_bounces(views, keys, nrm, geom, sw.max_bounces, prm, ids=False)
-    ks = np.array([[-x for x in v.d] for v in views], np.float32)
-    valid = int(((h.M >= 1) & (h.psi > 0)).sum())
-    terms = valid * sw.n_freq
-    E = api.po_field(h, nb, sw.W * sw.H, ks, sw.freqs_hz)
-    torch.cuda.synchronize()
-    reps = 5
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        api.po_field(h, nb, sw.W * sw.H, ks, sw.freqs_hz, out=E)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    flops_per_term = PO_FLOPS_PER_TERM
-    achieved = terms * flops_per_term / (ms / 1e3) / 1e12
+def roofline_po(ms_list, terms_per_launch, name="po_rot_kernel", sm_mhz=None,
+                slots_per_launch=None):
+    """The PO field kernel of the sweep (po_rot_kernel on uniform frequency
+    grids, po_kernel otherwise), timed per launch inside the timed steps;
+    terms = the Eq. 14 terms of a step (device counter, stats word 7) over
+    its PO launches.  ALU roofline at PO_FLOPS_PER_TERM flops per term."""
+    if not ms_list or terms_per_launch <= 0:
+        return None
+    ms = float(np.mean(ms_list))
+    achieved = terms_per_launch * PO_FLOPS_PER_TERM / (ms / 1e3) / 1e12
     peak, src = alu_peak(sm_mhz)
-    return {"kernel": "po_kernel (+po_reduce_kernel)", "bound": "alu", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": src, "flops_per_term": flops_per_term, "terms_per_launch": terms,
-            "ms_per_launch": ms}
+    traffic = None
+    if slots_per_launch and name == "po_rot_kernel" and _traffic_valid(PO_NCU_TRAFFIC):
+        traffic = PO_NCU_TRAFFIC["bytes_per_slot"] * slots_per_launch
+    return {"kernel": name, "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": "bytes per launch, scaled by ray slots from a smaller ncu capture",
+            "peak_source": src, "flops_per_term": PO_FLOPS_PER_TERM,
+            "terms_per_launch": terms_per_launch, "ms_per_launch": ms,
+            "launches_timed": len(ms_list)}
 
 
-# Algorithmic FP32 work of one (ray, frequency) term of Eq. 14 (FMA = 2): two
-# sinc arguments (2), two sinc evaluations (Taylor, 5 FMA each: 20), their
-# product and the amplitude split (3), double-float phase k*delta and its
-# reduction mod 2 pi (2 mul + 5 FMA + 1 add: 13), e^{-j phi} (2
-# special-function ops, counted 1 each: 2), and the field's 3 Cartesian
-# components x 2 polarisations, complex: 12 multiply-adds (24).  (The kernel
-# needs 8 of those 12, in a basis across ks.)
 PO_FLOPS_PER_TERM = 64
 
 

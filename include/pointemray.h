@@ -159,7 +159,8 @@ typedef struct {
  * pyramids its walk searches, each over the stretch of the ray crossing
  * that view's occupied cells); pe_rcs_sweep also counts its incidence
  * splats: [5] exact per-pixel ray/disk tests, [6] 64-bit key updates
- * (atomicMin, one per test that hits). */
+ * (atomicMin, one per test that hits), and its field sums: [7] Eq. 14
+ * terms (rays with a contribution x frequencies). */
 #define PE_STATS_WORDS 8
 
 /* Alg. 1 (screen-based PRI, tube mode) with a finite heap of K points per

@@ -144,9 +144,10 @@ pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n
                                 int32_t only_bounce, uint8_t *psi, int64_t *stats,
                                 cudaStream_t s);
 size_t pe_po_ws_bytes(int32_t n_groups, int64_t rays_per_group, int32_t n_freq);
+// stats (nullable): [7] += contributing rays x frequencies (the Eq. 14 terms).
 pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rays_per_group,
                        const float *ks, const double *freqs, int32_t n_freq, void *ws,
-                       size_t ws_bytes, double *E, cudaStream_t s);
+                       size_t ws_bytes, double *E, cudaStream_t s, int64_t *stats = nullptr);
 
 // ---------------------------------------------------------------------------
 // Device helpers: IEEE binary32 without contraction, left to right.

@@ -41,7 +41,20 @@ struct po_consts {
   float k2[kPoFreqs];                  // k^2 (uniform grids: the sinc series variable)
   float dkhi, dklo;                    // uniform grids: the step of k / 2 pi, a float pair
   float kmax;                          // the launch's largest k
+  long long *stats;                    // nullable: [7] += contributing rays x nf
 };
+
+// Adds this thread's count of contributing rays, times the launch's
+// frequencies, to stats[7] (one atomic per warp).  Every thread of the block
+// calls it at the end of the kernel.
+__device__ __forceinline__ void count_terms(const po_consts &C, long long rays) {
+  if (!C.stats) return;  // a kernel argument: uniform over the block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) rays += __shfl_down_sync(0xffffffffu, rays, o);
+  if ((threadIdx.x & 31) == 0 && rays)
+    atomicAdd(reinterpret_cast<unsigned long long *>(C.stats + 7),
+              (unsigned long long)(rays * C.nf));
+}
 
 // sin(x)/x: Taylor series through x^8 for |x| < 0.5 (truncation < 3e-11),
 // otherwise the hardware sine divided by x.
@@ -165,6 +178,7 @@ __global__ void __launch_bounds__(kPoThreads, 4)
   int64_t r_end = r_begin + C.chunk;
   if (r_end > C.rpg) r_end = C.rpg;
   const int64_t slot0 = (int64_t)(C.g0 + g) * C.rpg;
+  long long n_rays = 0;  // contributing rays (counted in the first frequency chunk)
 
   for (int f0 = 0; f0 < C.nf; f0 += FL) {
     const int f = f0 + lane_f;
@@ -181,6 +195,7 @@ __global__ void __launch_bounds__(kPoThreads, 4)
       for (int64_t r = r_begin + tid; r < r_end; r += kPoThreads) {
         float au, av, dh, dl, V[4];
         if (!ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V)) continue;
+        n_rays += f0 == 0;
         add_term(kf, khi, klo, au, av, dh, dl, V, b);
         if (++pending == kFlush) {
 #pragma unroll
@@ -208,6 +223,7 @@ __global__ void __launch_bounds__(kPoThreads, 4)
           if (w < wid) before += s_warp[w];
           total += s_warp[w];
         }
+        if (tid == 0 && f0 == 0) n_rays += total;
         if (valid) {
           int at = before + __popc(m & ((1u << lane) - 1u));
           s_ray[0][at] = make_float4(au, av, dh, dl);
@@ -260,6 +276,7 @@ __global__ void __launch_bounds__(kPoThreads, 4)
     }
     __syncthreads();
   }
+  count_terms(C, n_rays);
 }
 
 // ---------------------------------------------------------------------------
@@ -359,6 +376,7 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
   if (r_end > C.rpg) r_end = C.rpg;
   const int64_t slot0 = (int64_t)(C.g0 + g) * C.rpg;
   const int n_fc = (C.nf + FT - 1) / FT;  // frequency chunks of the launch
+  long long n_rays = 0;  // contributing rays (counted in the first frequency chunk)
 
   for (int c0 = 0; c0 < n_fc; c0 += FL) {
     const int f1 = (c0 + lane_f) * FT;  // this thread's first frequency
@@ -406,6 +424,7 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
         n_a += s_warp[w];
         n_b += s_warp[kPoThreads / 32 + w];
       }
+      if (tid == 0 && c0 == 0) n_rays += n_a + n_b;
       if (valid) {
         const unsigned below = (1u << lane) - 1u;
         const int at = ser ? before_a + __popc(ma & below) : n_a + before_b + __popc(mb & below);
@@ -512,6 +531,7 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
     }
     __syncthreads();
   }
+  count_terms(C, n_rays);
 }
 
 // E[g0+g][f][12] = the chunks' sums (fixed order) taken back from the basis
@@ -618,7 +638,7 @@ size_t pe_po_ws_bytes(int32_t n_groups, int64_t rpg, int32_t n_freq) {
 
 pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const float *ks,
                        const double *freqs, int32_t n_freq, void *ws, size_t ws_bytes,
-                       double *E, cudaStream_t s) {
+                       double *E, cudaStream_t s, int64_t *stats) {
   if (n_groups < 1 || rpg < 1 || n_freq < 1) return PE_OK;
   if (ws_bytes < pe_po_ws_bytes(n_groups, rpg, n_freq))
     return pe_fail(PE_ENOMEM, "po: workspace too small");
@@ -636,6 +656,7 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
       po_shape(ng, rpg, nf, &C.fl, &C.n_chunks, &C.chunk);
       C.rpg = rpg;
       C.g0 = g0;
+      C.stats = reinterpret_cast<long long *>(stats);
       C.rl_shift = __builtin_ctz((unsigned)(kPoThreads / C.fl));
       for (int g = 0; g < ng; ++g) {
         for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];

@@ -148,7 +148,7 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
     if (st != PE_OK) return st;
     // PO: E rows [a0, a0 + nb)
     st = pe_launch_po(h, nb, per, ks, sw->freqs_hz, sw->n_freq, w.po, w.po_bytes,
-                      E + (int64_t)a0 * sw->n_freq * 12, s);
+                      E + (int64_t)a0 * sw->n_freq * 12, s, stats);
     if (st != PE_OK) return st;
     if (sigma) {
       int n = nb * sw->n_freq;

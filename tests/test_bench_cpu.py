@@ -23,6 +23,20 @@ def test_march_roofline_arithmetic(monkeypatch):
     assert bench.roofline_march([], 10) is None
 
 
+def test_po_roofline_arithmetic():
+    # 1e9 terms of 64 flops per launch in 2 ms: 32 TFLOP/s; against the FP32
+    # peak at 2070 MHz (80.55 TFLOP/s), 0.397
+    r = bench.roofline_po([1.0, 3.0], 1e9, "po_rot_kernel", 2070.0)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["kernel"] == "po_rot_kernel"
+    assert r["ms_per_launch"] == pytest.approx(2.0)
+    assert r["achieved"] == pytest.approx(1e9 * bench.PO_FLOPS_PER_TERM / 2e-3 / 1e12)
+    assert r["achieved"] == pytest.approx(32.0)
+    assert r["frac"] == pytest.approx(32.0 / (152 * 128 * 2 * 2.07e9 / 1e12))
+    assert r["launches_timed"] == 2
+    assert bench.roofline_po([], 1e9) is None
+    assert bench.roofline_po([1.0], 0) is None
+
+
 def test_alu_peak_from_the_sampled_clock():
     v, how = bench.alu_peak(2070.0)
     assert v == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)       # 80.55 TFLOP/s
