@@ -130,10 +130,13 @@ pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float
                           const float *rad, int64_t n, int mode, float delta, float *hz,
                           unsigned long long *keys, int64_t *stats, cudaStream_t s);
 
+// implicit1 (bounce 1 from the GFB keys, mb >= 2): no bounce-1 records are
+// written; the bounce-2 pass takes each ray's bounce-1 record from its key
+// and writes M and Psi of every slot (the records of later hits as usual).
 pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,
                           const float *nrm, const pe_geom *geom, int32_t mb,
                           const pe_params &prm, const pe_hits &h,
-                          int64_t *stats, cudaStream_t s);
+                          int64_t *stats, cudaStream_t s, bool implicit1 = false);
 
 // Psi toward receiver direction dirs[g] (host [n_groups][3]) for every slot
 // of group g (rays_per_group consecutive slots): 1 unless a splat is hit from
@@ -144,10 +147,22 @@ pe_status pe_launch_shadow_dirs(const pe_geom *geom, const pe_hits &h, int32_t n
                                 int32_t only_bounce, uint8_t *psi, int64_t *stats,
                                 cudaStream_t s);
 size_t pe_po_ws_bytes(int32_t n_groups, int64_t rays_per_group, int32_t n_freq);
+// Bounce-1 records held implicitly by the incidence GFB (pe_rcs_sweep): a
+// slot whose last hit is bounce 1 (M == 1) takes its record from its key
+// (pe_primary_record) instead of the record arrays, which then hold only the
+// records of later bounces.  views: host, one per group of the launch, each
+// group's slots in raster order (rays_per_group = W * H).
+struct pe_gfb_src {
+  const unsigned long long *keys;  // device [n_groups][W * H]
+  const float *nrm;                // device point normals [n][3]
+  const pe_view *views;            // host [n_groups]
+};
+
 // stats (nullable): [7] += contributing rays x frequencies (the Eq. 14 terms).
 pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rays_per_group,
                        const float *ks, const double *freqs, int32_t n_freq, void *ws,
-                       size_t ws_bytes, double *E, cudaStream_t s, int64_t *stats = nullptr);
+                       size_t ws_bytes, double *E, cudaStream_t s, int64_t *stats = nullptr,
+                       const pe_gfb_src *gfb1 = nullptr);
 
 // ---------------------------------------------------------------------------
 // Device helpers: IEEE binary32 without contraction, left to right.
@@ -198,6 +213,35 @@ __device__ __forceinline__ bool pe_hit_disk(pe_f3 o, pe_f3 d, pe_f3 c, pe_f3 n, 
   if (!(pe_dot(e, e) <= pe_mul(R, R))) return false;
   if (!(t > tmin)) return false;
   return true;
+}
+
+// Image-method path length at the first hit, k . p in FP64.
+__device__ __forceinline__ double pe_path_start(pe_f3 d, pe_f3 p) {
+  return __dadd_rn(__dadd_rn(__dmul_rn((double)d.x, (double)p.x), __dmul_rn((double)d.y, (double)p.y)),
+                   __dmul_rn((double)d.z, (double)p.z));
+}
+
+// The bounce-1 record of pixel (i, j) of view V from its GFB key (a hit:
+// key != ~0): hit point at the key's depth along the pixel's ray, the key
+// point's normal turned against the ray, incoming direction d, tube vectors
+// pitch u and pitch v, path d . p.  The one definition of those values:
+// written by the primary pass, or recomputed from the key where the records
+// are implicit, bit for bit the same.
+__device__ __forceinline__ void pe_primary_record(const pe_view &V, int i, int j,
+                                                  unsigned long long key,
+                                                  const float *__restrict__ nrm, pe_f3 &p,
+                                                  pe_f3 &n, pe_f3 &k, pe_f3 &u, pe_f3 &v,
+                                                  double &path) {
+  const pe_f3 o = pe_pixel_origin(V, i, j);
+  k = pe_v3(V.d);
+  const uint32_t id = (uint32_t)(key & 0xffffffffull);
+  p = pe_ray_at(o, __uint_as_float((uint32_t)(key >> 32)), k);
+  n = {__ldg(nrm + 3 * (int64_t)id), __ldg(nrm + 3 * (int64_t)id + 1),
+       __ldg(nrm + 3 * (int64_t)id + 2)};
+  if (pe_dot(n, k) > 0.0f) n = pe_neg3(n);
+  u = {pe_mul(V.pitch, V.u[0]), pe_mul(V.pitch, V.u[1]), pe_mul(V.pitch, V.u[2])};
+  v = {pe_mul(V.pitch, V.v[0]), pe_mul(V.pitch, V.v[1]), pe_mul(V.pitch, V.v[2])};
+  path = pe_path_start(k, p);
 }
 
 // Reflection a - (2 (a . n)) n (Eq. 4; also H and the tube vectors).

@@ -42,6 +42,12 @@ struct po_consts {
   float dkhi, dklo;                    // uniform grids: the step of k / 2 pi, a float pair
   float kmax;                          // the launch's largest k
   long long *stats;                    // nullable: [7] += contributing rays x nf
+  // implicit bounce-1 records (pe_gfb_src): null keys1 = every record is
+  // in the arrays; else a slot with M == 1 takes its record from its key
+  const unsigned long long *keys1;
+  const float *nrm1;
+  pe_view view1[kPoGroups];            // the launch's groups' views
+  int32_t mono1[kPoGroups];            // ks == -d of that view, bit for bit
 };
 
 // Adds this thread's count of contributing rays, times the launch's
@@ -86,15 +92,29 @@ __device__ __forceinline__ float dotf(pe_f3 a, pe_f3 b) { return a.x * b.x + a.y
 // pair (dh, dl) and the area-weighted vector factors of both polarisations in
 // the basis (e1, e2).  False for a ray without a contribution (a miss,
 // Psi = 0, or a tube edge-on to the surface).
+// (r: the slot's index within its group g of the launch.)
 __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f3 ks, pe_f3 e1,
                                             pe_f3 e2, float &au, float &av, float &dh,
-                                            float &dl, float V[4]) {
-  if (!(h.M[slot] >= 1 && h.psi[slot] != 0)) return false;
-  pe_f3 kk = {h.k[3 * slot], h.k[3 * slot + 1], h.k[3 * slot + 2]};
-  pe_f3 n = {h.n[3 * slot], h.n[3 * slot + 1], h.n[3 * slot + 2]};
-  pe_f3 u = {h.u[3 * slot], h.u[3 * slot + 1], h.u[3 * slot + 2]};
-  pe_f3 v = {h.v[3 * slot], h.v[3 * slot + 1], h.v[3 * slot + 2]};
-  pe_f3 p = {h.p[3 * slot], h.p[3 * slot + 1], h.p[3 * slot + 2]};
+                                            float &dl, float V[4], const po_consts &C, int g,
+                                            int64_t r) {
+  const int32_t M = h.M[slot];
+  if (!(M >= 1 && h.psi[slot] != 0)) return false;
+  pe_f3 kk, n, u, v, p;
+  double path;
+  bool twice = false;  // d - ks . p = 2 path (below)
+  if (M == 1 && C.keys1) {
+    const pe_view &W = C.view1[g];
+    const int j = (int)(r / W.W), i = (int)(r - (int64_t)j * W.W);
+    pe_primary_record(W, i, j, C.keys1[slot], C.nrm1, p, n, kk, u, v, path);
+    twice = C.mono1[g] != 0;
+  } else {
+    kk = {h.k[3 * slot], h.k[3 * slot + 1], h.k[3 * slot + 2]};
+    n = {h.n[3 * slot], h.n[3 * slot + 1], h.n[3 * slot + 2]};
+    u = {h.u[3 * slot], h.u[3 * slot + 1], h.u[3 * slot + 2]};
+    v = {h.v[3 * slot], h.v[3 * slot + 1], h.v[3 * slot + 2]};
+    p = {h.p[3 * slot], h.p[3 * slot + 1], h.p[3 * slot + 2]};
+    path = h.path[slot];
+  }
   float nk = dotf(n, kk);
   if (nk == 0.0f) return false;
   float su = dotf(n, u) / nk, sv = dotf(n, v) / nk;
@@ -114,8 +134,17 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f
   V[1] = area * dotf(a, e2);
   V[2] = area * dotf(c, e1);
   V[3] = area * dotf(c, e2);
-  double ksp = (double)ks.x * (double)p.x + (double)ks.y * (double)p.y + (double)ks.z * (double)p.z;
-  double delta = h.path[slot] - ksp;
+  // Backscatter from a bounce-1 record (ks = -d exactly): every product of
+  // two floats is exact in FP64 and rounding to nearest is odd-symmetric, so
+  // ks . p = -path bit for bit and the difference is exactly 2 path.
+  double delta;
+  if (twice) {
+    delta = 2.0 * path;
+  } else {
+    const double ksp =
+        (double)ks.x * (double)p.x + (double)ks.y * (double)p.y + (double)ks.z * (double)p.z;
+    delta = path - ksp;
+  }
   dh = (float)delta;
   dl = (float)(delta - (double)dh);
   return true;
@@ -194,7 +223,7 @@ __global__ void __launch_bounds__(kPoThreads, 4)
       // one frequency: each thread takes its own rays, nothing to share
       for (int64_t r = r_begin + tid; r < r_end; r += kPoThreads) {
         float au, av, dh, dl, V[4];
-        if (!ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V)) continue;
+        if (!ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V, C, g, r)) continue;
         n_rays += f0 == 0;
         add_term(kf, khi, klo, au, av, dh, dl, V, b);
         if (++pending == kFlush) {
@@ -211,7 +240,8 @@ __global__ void __launch_bounds__(kPoThreads, 4)
         // ---- stage the frequency-independent per-ray factors --------------
         const int64_t r = sb + tid;
         float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
-        const bool valid = r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V);
+        const bool valid =
+            r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V, C, g, r);
         // stable compaction of the valid rays (order = slot order)
         unsigned m = __ballot_sync(0xffffffffu, valid);
         int wid = tid >> 5, lane = tid & 31;
@@ -402,7 +432,8 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
       // ---- stage the frequency-independent per-ray factors ----------------
       const int64_t r = sb + tid;
       float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
-      const bool valid = r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V);
+      const bool valid =
+          r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V, C, g, r);
       // two stable compactions: rays whose sinc arguments stay in the series'
       // range for every frequency of the launch first, the others after them
       const bool ser = valid && fmaxf(fabsf(au), fabsf(av)) * C.kmax < 0.5f;
@@ -638,10 +669,17 @@ size_t pe_po_ws_bytes(int32_t n_groups, int64_t rpg, int32_t n_freq) {
 
 pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const float *ks,
                        const double *freqs, int32_t n_freq, void *ws, size_t ws_bytes,
-                       double *E, cudaStream_t s, int64_t *stats) {
+                       double *E, cudaStream_t s, int64_t *stats, const pe_gfb_src *gfb1) {
   if (n_groups < 1 || rpg < 1 || n_freq < 1) return PE_OK;
   if (ws_bytes < pe_po_ws_bytes(n_groups, rpg, n_freq))
     return pe_fail(PE_ENOMEM, "po: workspace too small");
+  if (gfb1) {
+    if (!gfb1->keys || !gfb1->nrm || !gfb1->views)
+      return pe_fail(PE_EINVAL, "po: implicit bounce-1 records need keys, normals and views");
+    for (int g = 0; g < n_groups; ++g)
+      if ((int64_t)gfb1->views[g].W * gfb1->views[g].H != rpg)
+        return pe_fail(PE_EINVAL, "po: implicit bounce-1 records need W * H rays per group");
+  }
   double *part = static_cast<double *>(ws);
   const double two_pi = 2.0 * M_PI;
   const double c0 = 299792458.0;
@@ -657,6 +695,16 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
       C.rpg = rpg;
       C.g0 = g0;
       C.stats = reinterpret_cast<long long *>(stats);
+      if (gfb1) {
+        C.keys1 = gfb1->keys;
+        C.nrm1 = gfb1->nrm;
+        for (int g = 0; g < ng; ++g) {
+          C.view1[g] = gfb1->views[g0 + g];
+          C.mono1[g] = 1;
+          for (int k = 0; k < 3; ++k)
+            if (!(C.ks[g][k] == -C.view1[g].d[k])) C.mono1[g] = 0;
+        }
+      }
       C.rl_shift = __builtin_ctz((unsigned)(kPoThreads / C.fl));
       for (int g = 0; g < ng; ++g) {
         for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];

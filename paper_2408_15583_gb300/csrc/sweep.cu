@@ -144,11 +144,17 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
       pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.hz, w.keys, stats, s);
       if (st != PE_OK) return st;
     }
-    pe_status st = pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, h, stats, s);
+    // bounce-1 records stay implicit in the incidence GFB (bounce 1 from the
+    // keys and a march to follow): the bounce-2 pass and the PO sum take them
+    // from the keys, and only later hits are written as records
+    const bool implicit1 = !prm->first_bounce_from_geom && sw->max_bounces >= 2;
+    pe_status st =
+        pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, h, stats, s, implicit1);
     if (st != PE_OK) return st;
     // PO: E rows [a0, a0 + nb)
+    const pe_gfb_src src{w.keys, nrm, vb.v};
     st = pe_launch_po(h, nb, per, ks, sw->freqs_hz, sw->n_freq, w.po, w.po_bytes,
-                      E + (int64_t)a0 * sw->n_freq * 12, s, stats);
+                      E + (int64_t)a0 * sw->n_freq * 12, s, stats, implicit1 ? &src : nullptr);
     if (st != PE_OK) return st;
     if (sigma) {
       int n = nb * sw->n_freq;

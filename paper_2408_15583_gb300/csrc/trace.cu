@@ -32,6 +32,7 @@ struct march_args {
   const float *nrm;
   int32_t bounce;
   int32_t mb;
+  int32_t implicit1;  // bounce 2 takes the bounce-1 records from the keys
   float eps;
   float r_ov;
   unsigned int *err;
@@ -577,11 +578,6 @@ __device__ bool nearest(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, f
   return true;
 }
 
-__device__ __forceinline__ double path_start(pe_f3 d, pe_f3 p) {
-  return __dadd_rn(__dadd_rn(__dmul_rn((double)d.x, (double)p.x), __dmul_rn((double)d.y, (double)p.y)),
-                   __dmul_rn((double)d.z, (double)p.z));
-}
-
 __device__ __forceinline__ double seg_len(pe_f3 a, pe_f3 b) {
   double dx = __dsub_rn((double)b.x, (double)a.x);
   double dy = __dsub_rn((double)b.y, (double)a.y);
@@ -704,7 +700,7 @@ __global__ void __launch_bounds__(kTraceThreads)
         st3(A.h.k, slot, d);
         st3(A.h.u, slot, u);
         st3(A.h.v, slot, v);
-        A.h.path[slot] = path_start(d, x);
+        A.h.path[slot] = pe_path_start(d, x);
       }
     }
   }
@@ -737,21 +733,17 @@ __global__ void __launch_bounds__(kTraceThreads)
       if (A.h.ids) A.h.ids[slot] = PE_NONE;
       continue;
     }
-    const pe_f3 o = pe_pixel_origin(V, i, j);
-    const pe_f3 d = pe_v3(V.d);
-    const uint32_t id = (uint32_t)(key & 0xffffffffull);
-    const pe_f3 x = pe_ray_at(o, __uint_as_float((uint32_t)(key >> 32)), d);
-    pe_f3 nn = {__ldg(A.nrm + 3 * (int64_t)id), __ldg(A.nrm + 3 * (int64_t)id + 1),
-                __ldg(A.nrm + 3 * (int64_t)id + 2)};
-    if (pe_dot(nn, d) > 0.0f) nn = pe_neg3(nn);
+    pe_f3 x, nn, d, u, v;
+    double path;
+    pe_primary_record(V, i, j, key, A.nrm, x, nn, d, u, v, path);
     A.h.M[slot] = 1;
-    if (A.h.ids) A.h.ids[slot] = id;
+    if (A.h.ids) A.h.ids[slot] = (uint32_t)(key & 0xffffffffull);
     st3(A.h.p, slot, x);
     st3(A.h.n, slot, nn);
     st3(A.h.k, slot, d);
-    st3(A.h.u, slot, {pe_mul(V.pitch, V.u[0]), pe_mul(V.pitch, V.u[1]), pe_mul(V.pitch, V.u[2])});
-    st3(A.h.v, slot, {pe_mul(V.pitch, V.v[0]), pe_mul(V.pitch, V.v[1]), pe_mul(V.pitch, V.v[2])});
-    A.h.path[slot] = path_start(d, x);
+    st3(A.h.u, slot, u);
+    st3(A.h.v, slot, v);
+    A.h.path[slot] = path;
   }
   flush_stats(A.stats, sacc, nq, 0, 0, 0, 0);
 }
@@ -777,16 +769,38 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
     int vi = 0, i = 0, j = 0;
     bool active = t < tm.n_threads && tile_pixel(tm, W, H, t, vi, i, j);
     const uint32_t slot = active ? (uint32_t)((int64_t)vi * per_view + (int64_t)j * W + i) : 0u;
-    active = active && A.h.M[slot] == A.bounce - 1;
+    // implicit bounce-1 records: the ray is live when its pixel's key holds
+    // a hit, and this pass writes M and Psi of every pixel (the primary pass
+    // does not run)
+    const bool pix = active;
+    unsigned long long key = ~0ull;
+    if (A.implicit1) {
+      if (pix) {
+        key = __ldcs(A.keys + slot);
+        const bool h1 = key != ~0ull;
+        A.h.M[slot] = h1 ? 1 : 0;  // raised to 2 below on a hit
+        A.h.psi[slot] = 1;
+        if (A.h.ids) A.h.ids[slot] = h1 ? (uint32_t)(key & 0xffffffffull) : PE_NONE;
+      }
+      active = pix && key != ~0ull;
+      nq += pix;  // the pixel's bounce-1 lookup
+    } else {
+      active = active && A.h.M[slot] == A.bounce - 1;
+    }
     if (!__any_sync(0xffffffffu, active)) continue;
     pe_f3 p = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 1.f}, d = {0.f, 0.f, 1.f};
     pe_f3 u = {0.f, 0.f, 0.f}, v = {0.f, 0.f, 0.f};
     if (active) {
-      p = ld3(A.h.p, slot);
-      n = ld3(A.h.n, slot);
-      d = ld3(A.h.k, slot);
-      u = ld3(A.h.u, slot);
-      v = ld3(A.h.v, slot);
+      if (A.implicit1) {
+        double path0;  // recomputed below for a hit (fewer registers live across the walk)
+        pe_primary_record(A.vb.v[vi], i, j, key, A.nrm, p, n, d, u, v, path0);
+      } else {
+        p = ld3(A.h.p, slot);
+        n = ld3(A.h.n, slot);
+        d = ld3(A.h.k, slot);
+        u = ld3(A.h.u, slot);
+        v = ld3(A.h.v, slot);
+      }
       pe_f3 rd = pe_reflect(d, n);
       float len = pe_sqrt(pe_dot(rd, rd));
       d = {pe_div(rd.x, len), pe_div(rd.y, len), pe_div(rd.z, len)};
@@ -798,7 +812,10 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
     nq += active;
     bool hit = nearest(A.L, p, d, A.eps, A.r_ov, active, A.err, x, n2, id, ns, nn, nv);
     if (hit) {
-      A.h.path[slot] = __dadd_rn(A.h.path[slot], seg_len(p, x));
+      // the bounce-1 path d . p (the primary record's, bit for bit)
+      const double path0 =
+          A.implicit1 ? pe_path_start(pe_v3(A.vb.v[slot / per_view].d), p) : A.h.path[slot];
+      A.h.path[slot] = __dadd_rn(path0, seg_len(p, x));
       st3(A.h.p, slot, x);
       st3(A.h.n, slot, n2);
       st3(A.h.k, slot, d);
@@ -943,7 +960,7 @@ bool geom_layout(const pe_geom *g, pe_geom_layout *L) {
 pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *keys,
                           const float *nrm, const pe_geom *geom, int32_t mb,
                           const pe_params &prm, const pe_hits &h, int64_t *stats,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool implicit1) {
   march_args A;
   memset(&A, 0, sizeof(A));
   bool have_geom = geom != nullptr;
@@ -963,21 +980,26 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
   const int64_t n_rays = (int64_t)vb.W * vb.H * vb.n;
   if (h.ids) PE_TRY_CUDA(cudaMemsetAsync(h.ids, 0xff, sizeof(uint32_t) * n_rays * mb, s));
   A.bounce = 1;
+  implicit1 = implicit1 && mb >= 2 && !prm.first_bounce_from_geom && have_geom;
   const int64_t n_thr = make_tile_map(vb.W, vb.H, vb.n).n_threads;
   // per-lane ray intervals of every view (walk's shared memory)
   const size_t tv_bytes = have_geom ? (size_t)A.L.nv * kTraceThreads * sizeof(float2) : 0;
-  pe_event_before("primary_kernel", s);
-  if (prm.first_bounce_from_geom) {
+  if (implicit1) {
+    // no bounce-1 records: the bounce-2 pass takes them from the keys
+  } else if (prm.first_bounce_from_geom) {
+    pe_event_before("primary_kernel", s);
     primary_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("primary_kernel", s);
     PE_TRY_LAUNCH("primary_kernel");
   } else {
+    pe_event_before("primary_kernel", s);
     primary_gfb_kernel<<<grid_stream(n_rays), kTraceThreads, 0, s>>>(A);
     pe_event_after("primary_kernel", s);
     PE_TRY_LAUNCH("primary_gfb_kernel");
   }
   for (int b = 2; b <= mb; ++b) {
     A.bounce = b;
+    A.implicit1 = implicit1 && b == 2;
     pe_event_before("march_kernel", s);
     march_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("march_kernel", s);

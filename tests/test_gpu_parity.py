@@ -443,6 +443,33 @@ def test_rcs_sweep_matches_oracle(case, request):
     assert torch.equal(E, E2)
 
 
+@pytest.mark.parametrize("case", GEOMS)
+def test_rcs_sweep_equals_trace_and_field(case, request):
+    # The sweep keeps every ray's bounce-1 record implicit in its incidence
+    # GFB keys (the bounce-2 march and the PO sum recompute it from the key);
+    # the public trace writes it out.  The same rays through both paths (one
+    # batch of angles, so the PO launch shape is the same) give the same
+    # field bit for bit, for rays ending at bounce 1 and at later bounces.
+    api, pipe = _mods()
+    d = request.getfixturevalue(case)
+    sc = d["sc"]
+    th = [90.0] * 5 + [70.0] if case == "small_geom" else [60.0] * 5 + [54.7356]
+    ph = [0.0, 13.0, 45.0, 62.0, 90.0, 30.0]
+    mb = 2 if case == "small_geom" else 3
+    sw = scenes._sweep_over(sc, th, ph, 48, [2.9e9, 3.0e9, 3.3e9], mb)
+    args = api.SweepArgs.from_sweep(sw, angle_batch=len(th))
+    E, _ = api.rcs_sweep(args, d["pos"], d["nrm"], d["rad"], d["geom"], d["prm"])
+    views = [api.view_from_angles(t, p, sw.centre, sw.extent, sw.W, sw.H) for t, p in zip(th, ph)]
+    keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+    h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, d["prm"], ids=False)
+    ks = np.array([[-x for x in v.d] for v in views], np.float32)
+    E2 = api.po_field(h, len(views), sw.W * sw.H, ks, sw.freqs_hz)
+    api.stream_check()
+    M = h.M.cpu().numpy()
+    assert (M == 1).any() and (M >= 2).any()      # both kinds of last hit occur
+    assert torch.equal(E, E2)
+
+
 def test_rcs_sweep_vs_fp64_physics_oracle(small_geom):
     # The FP64 oracle traces in double precision: a handful of grazing rays
     # can fall on the other side of a disk edge, so the bar is sigma within
