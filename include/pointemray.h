@@ -233,8 +233,10 @@ int64_t pe_kernel_launches(void);
 
 /* Diagnostics (no counterpart in the paper): make the library record CUDA
  * events around the next launches of one of its kernels on the calling host
- * thread.  `kernel` names it ("march_kernel", "po_kernel", "splat_kernel",
- * "primary_kernel", "shadow_kernel"); events[2k] / events[2k+1] (created by the
+ * thread.  `kernel` names it ("march_kernel" (the bounces after the first;
+ * with max_bounces = 2 also the shadow rays), "po_kernel", "splat_kernel",
+ * "primary_kernel", "shadow_kernel");
+ * events[2k] / events[2k+1] (created by the
  * caller, cudaEvent_t passed as void*) are recorded on the launching stream
  * immediately before / after the k-th such launch, for k < n_pairs.  Pass
  * n_pairs = 0 to stop.  Returns the pairs recorded since the last call. */

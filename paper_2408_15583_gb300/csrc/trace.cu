@@ -12,10 +12,11 @@
 // the candidate set and its selection do not depend on visiting order, the
 // hit ids equal those of a brute-force search over all splats.
 //
-// Every pass (bounce 1, each later bounce, the shadow rays) runs one warp
-// per 8x4 tile of the incidence screen, one block per 128 rays; a lane is
-// live when its ray's bounce count M says so.  Per-ray state lives in the
-// last-hit records, so a ray that misses simply keeps its previous record.
+// Every pass (bounce 1 from the geometry, each later bounce, the shadow rays:
+// with mb = 2 inside the bounce-2 pass) runs one warp per 8x4 tile of the
+// incidence screen, one block per 128 rays; a lane is live when its ray's
+// bounce count M says so.  Per-ray state lives in the last-hit records, so a ray that
+// misses simply keeps its previous record.
 #include <cstring>
 
 #include "pe_internal.cuh"
@@ -754,7 +755,10 @@ __global__ void __launch_bounds__(kTraceThreads)
 // reflections stay close, so the warp's union walk is nearly each lane's own.
 // (A compacted queue of live rays would mix tiles from anywhere on the
 // screen into one warp; the per-lane results are the same either way.)
-// Warps with no live lane only read M.
+// Warps with no live lane only read M.  With mb = 2 this pass also runs the
+// shadow rays of Psi (Eq. 14): the rays with two hits are its own hits, and
+// their lanes walk from the new hit toward the receiver with an any-hit walk
+// (saving a pass over every tile when few rays hit twice).
 __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_constant__ march_args A) {
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
@@ -762,7 +766,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
   const int64_t n_rays = A.h.n_rays;
   __shared__ stats_acc sacc;
   stats_begin(sacc);
-  long long nq = 0, ns = 0, nn = 0, nv = 0;
+  long long nq = 0, nsh = 0, ns = 0, nn = 0, nv = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < tm.n_threads;
        base += (int64_t)gridDim.x * blockDim.x) {
     int64_t t = base + threadIdx.x;
@@ -773,7 +777,13 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
     // a hit, and this pass writes M and Psi of every pixel (the primary pass
     // does not run)
     const bool pix = active;
+    // with mb = 2 this pass also runs the shadow rays (the rays with two
+    // hits are exactly its hits); with more bounces a pass of their own
+    // does (rays settle at different bounces, and one walk per warp over
+    // all of them, from their stored records, measured faster)
+    const bool last = A.bounce == A.mb && A.mb == 2;
     unsigned long long key = ~0ull;
+    int m0 = 0;  // the ray's bounce count before this pass
     if (A.implicit1) {
       if (pix) {
         key = __ldcs(A.keys + slot);
@@ -783,11 +793,13 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
         if (A.h.ids) A.h.ids[slot] = h1 ? (uint32_t)(key & 0xffffffffull) : PE_NONE;
       }
       active = pix && key != ~0ull;
+      m0 = active ? 1 : 0;
       nq += pix;  // the pixel's bounce-1 lookup
     } else {
-      active = active && A.h.M[slot] == A.bounce - 1;
+      m0 = pix ? A.h.M[slot] : 0;
+      active = pix && m0 == A.bounce - 1;
     }
-    if (!__any_sync(0xffffffffu, active)) continue;
+    if (!__any_sync(0xffffffffu, active || (last && m0 >= 2))) continue;
     pe_f3 p = {0.f, 0.f, 0.f}, n = {0.f, 0.f, 1.f}, d = {0.f, 0.f, 1.f};
     pe_f3 u = {0.f, 0.f, 0.f}, v = {0.f, 0.f, 0.f};
     if (active) {
@@ -824,11 +836,31 @@ __global__ void __launch_bounds__(kTraceThreads, 8) march_kernel(const __grid_co
       A.h.M[slot] = A.bounce;
       if (A.h.ids) A.h.ids[(int64_t)(A.bounce - 1) * n_rays + slot] = id;
     }
+    // Psi (mb = 2) of every ray with two hits: a shadow ray from its last hit
+    // toward the receiver (w, the reverse of the view's direction); rays with
+    // one hit keep Psi = 1.  (The general form: this pass's hit x, the origin
+    // p of a ray that missed here, or the stored record of a ray settled
+    // earlier.)
+    const bool need = last && (hit || m0 >= 2);
+    if (__any_sync(0xffffffffu, need)) {
+      const pe_view &V = A.vb.v[need ? slot / per_view : 0];
+      const pe_f3 w = {-V.d[0], -V.d[1], -V.d[2]};
+      const pe_f3 o = hit ? x : (active ? p : (need ? ld3(A.h.p, slot) : p));
+      qstate S;
+      S.tb = INFINITY;
+      S.ib = PE_NONE;
+      S.nc = 0;
+      nsh += need;
+      bool blocked = false;
+      walk<true>(A.L, o, w, A.eps, A.r_ov, need, S, blocked, A.err, ns, nn, nv);
+      if (need) A.h.psi[slot] = blocked ? 0 : 1;
+    }
   }
-  flush_stats(A.stats, sacc, nq, 0, ns, nn, nv);
+  flush_stats(A.stats, sacc, nq, nsh, ns, nn, nv);
 }
 
-// Psi: shadow ray from the last hit toward the receiver (monostatic: w).
+// Psi: shadow ray from the last hit toward the receiver (monostatic: w),
+// a pass of its own when mb >= 3 (with mb = 2 the march runs it).
 __global__ void __launch_bounds__(kTraceThreads, 8) shadow_kernel(const __grid_constant__ march_args A) {
   const int W = A.vb.W, H = A.vb.H;
   const int64_t per_view = (int64_t)W * H;
@@ -1005,7 +1037,7 @@ pe_status pe_launch_trace(const pe_view_batch &vb, const unsigned long long *key
     pe_event_after("march_kernel", s);
     PE_TRY_LAUNCH("march_kernel");
   }
-  if (mb >= 2) {
+  if (mb >= 3) {  // (with mb = 2 the march ran the shadow rays)
     pe_event_before("shadow_kernel", s);
     shadow_kernel<<<grid_all(n_thr), kTraceThreads, tv_bytes, s>>>(A);
     pe_event_after("shadow_kernel", s);
