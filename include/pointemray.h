@@ -462,7 +462,9 @@ typedef struct {
   const double *freqs_hz;    /* host [n_freq] */
   int32_t max_bounces;
   int32_t angle_batch;       /* angles per batch (1..PE_MAX_BATCH), 0 = auto
-                                (as many as fit ~16 GB of ray records) */
+                                (as many as fit ~16 GB of ray records, or
+                                ~8 GB per set of batch buffers when there
+                                are two: see pe_rcs_sweep) */
 } pe_sweep;
 
 /* The view of a monostatic incidence (a1): w = (sin t cos p, sin t sin p,
@@ -480,7 +482,12 @@ size_t pe_rcs_sweep_workspace(const pe_sweep *sweep);
  * (bounce 1), trace bounces 2..mb, test Psi, and sum the PO field.
  * E_dev: float64 [n_angles][n_freq][2][3][2] (device, required);
  * sigma_dev: float64 [n_angles][n_freq][2 tx][2 rx] m^2 (device, nullable),
- * tx/rx in (V, H); stats_dev as in pe_trace_bounces (nullable). */
+ * tx/rx in (V, H); stats_dev as in pe_trace_bounces (nullable).
+ * With more than one batch and n_freq >= 8 the workspace holds two sets of
+ * batch buffers and the library sums one batch's field on a second CUDA
+ * stream of its own (created and released within the call) while the next
+ * batch traces on `stream`; `stream` waits for that work before the call's
+ * later operations, so the results are ordered on `stream` as usual. */
 pe_status pe_rcs_sweep(const pe_sweep *sweep, const float *pos_dev,
                        const float *nrm_dev, const float *rad_dev, int64_t n_points,
                        const pe_geom *geom, const pe_params *params, void *ws,

@@ -32,52 +32,97 @@ __global__ void sigma_kernel(const __grid_constant__ pe_view_batch vb, const dou
   }
 }
 
-struct sweep_ws {
+// The buffers of one batch of angles: incidence keys and tile depths, ray
+// records, PO partial sums.
+struct batch_ws {
   unsigned long long *keys;
   float *hz;
   pe_hits h;
-  double *kw;
   void *po;
   size_t po_bytes;
 };
 
+// With more than one batch and a field sum of some size (at least
+// kLaneFreqs frequencies) the sweep keeps two sets of batch buffers
+// ("lanes"): the PO sum of one batch runs on a second stream while the next
+// batch splats and traces on the caller's, so the ALU-bound field sum and the
+// latency-bound march share the SMs (sphere workload, 64 frequencies: 80.0
+// -> 74.9 ms per step).  With few frequencies the sum is short and the
+// smaller batches of two lanes cost more than the overlap gains.
+constexpr int kLaneFreqs = 8;
+struct sweep_ws {
+  batch_ws lane[2];
+  int n_lanes;
+  double *kw;
+};
+
+// Ray-record bytes per angle of a batch.
+int64_t record_bytes(const pe_sweep *sw) {
+  return (int64_t)sw->W * sw->H * (8 + 60 + 8 + 4 + 1 + 8) + 4096;
+}
+
 // Angles per batch: the caller's, else as many as fit ray records of about
 // 16 GB (a few percent of the device's memory; more angles per launch
 // amortise each pass's tail: the composite sweep at 2048^2 rays runs 168 ms
-// with 5 angles per batch, 144 ms with 39).
+// with 5 angles per batch, 144 ms with 39), split over two lanes when the
+// sweep takes more than one batch and its field sum is of some size.
 int batch_of(const pe_sweep *sw) {
   if (sw->angle_batch > 0) return sw->angle_batch < PE_MAX_BATCH ? sw->angle_batch : PE_MAX_BATCH;
-  int64_t per = (int64_t)sw->W * sw->H;
-  int64_t bytes = per * (8 + 60 + 8 + 4 + 1 + 8) + 4096;
+  const int64_t bytes = record_bytes(sw);
   int64_t b = ((int64_t)16 << 30) / bytes;
   if (b < 1) b = 1;
   if (b > PE_MAX_BATCH) b = PE_MAX_BATCH;
-  if (b > sw->n_angles) b = sw->n_angles;
+  if (b >= sw->n_angles) return sw->n_angles;
+  if (sw->n_freq < kLaneFreqs) return (int)b;
+  b = ((int64_t)8 << 30) / bytes;  // two lanes
+  if (b < 1) b = 1;
+  if (b > PE_MAX_BATCH) b = PE_MAX_BATCH;
   return (int)b;
+}
+
+int lanes_of(const pe_sweep *sw, int B) {
+  return sw->n_angles > B && sw->n_freq >= kLaneFreqs ? 2 : 1;
 }
 
 sweep_ws carve_sweep(pe_carve &c, const pe_sweep *sw, int B) {
   sweep_ws w;
   memset(&w, 0, sizeof(w));
+  w.n_lanes = lanes_of(sw, B);
   int64_t n = (int64_t)sw->W * sw->H * B;
-  w.keys = c.take<unsigned long long>((size_t)n);
-  w.hz = c.take<float>(pe_splat_tiles(B, sw->W, sw->H));
-  w.h.p = c.take<float>((size_t)n * 3);
-  w.h.n = c.take<float>((size_t)n * 3);
-  w.h.k = c.take<float>((size_t)n * 3);
-  w.h.u = c.take<float>((size_t)n * 3);
-  w.h.v = c.take<float>((size_t)n * 3);
-  w.h.path = c.take<double>((size_t)n);
-  w.h.M = c.take<int32_t>((size_t)n);
-  w.h.psi = c.take<uint8_t>((size_t)n);
-  w.h.ids = nullptr;
-  w.h.n_rays = n;
-  w.h.max_bounces = sw->max_bounces;
+  for (int l = 0; l < w.n_lanes; ++l) {
+    batch_ws &b = w.lane[l];
+    b.keys = c.take<unsigned long long>((size_t)n);
+    b.hz = c.take<float>(pe_splat_tiles(B, sw->W, sw->H));
+    b.h.p = c.take<float>((size_t)n * 3);
+    b.h.n = c.take<float>((size_t)n * 3);
+    b.h.k = c.take<float>((size_t)n * 3);
+    b.h.u = c.take<float>((size_t)n * 3);
+    b.h.v = c.take<float>((size_t)n * 3);
+    b.h.path = c.take<double>((size_t)n);
+    b.h.M = c.take<int32_t>((size_t)n);
+    b.h.psi = c.take<uint8_t>((size_t)n);
+    b.h.ids = nullptr;
+    b.h.n_rays = n;
+    b.h.max_bounces = sw->max_bounces;
+    b.po_bytes = pe_po_ws_bytes(B, (int64_t)sw->W * sw->H, sw->n_freq);
+    b.po = c.take<char>(b.po_bytes);
+  }
   w.kw = c.take<double>((size_t)sw->n_freq);
-  w.po_bytes = pe_po_ws_bytes(B, (int64_t)sw->W * sw->H, sw->n_freq);
-  w.po = c.take<char>(w.po_bytes);
   return w;
 }
+
+// The second stream and its events, released when the call returns (the
+// runtime frees them once the work queued on them has completed).
+struct lane_sync {
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t traced = nullptr, done[2] = {nullptr, nullptr};
+  ~lane_sync() {
+    if (traced) cudaEventDestroy(traced);
+    for (int l = 0; l < 2; ++l)
+      if (done[l]) cudaEventDestroy(done[l]);
+    if (s2) cudaStreamDestroy(s2);
+  }
+};
 
 bool sweep_ok(const pe_sweep *sw) {
   return sw && sw->n_angles >= 1 && sw->theta_deg && sw->phi_deg && sw->W > 0 && sw->H > 0 &&
@@ -123,8 +168,18 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
     PE_TRY_CUDA(cudaMemcpyAsync(w.kw + f0, kw_h, sizeof(double) * nf, cudaMemcpyHostToDevice, s));
   }
 
-  for (int a0 = 0; a0 < sw->n_angles; a0 += B) {
+  lane_sync ls;
+  if (w.n_lanes == 2) {
+    PE_TRY_CUDA(cudaStreamCreateWithFlags(&ls.s2, cudaStreamNonBlocking));
+    PE_TRY_CUDA(cudaEventCreateWithFlags(&ls.traced, cudaEventDisableTiming));
+    for (int l = 0; l < 2; ++l)
+      PE_TRY_CUDA(cudaEventCreateWithFlags(&ls.done[l], cudaEventDisableTiming));
+  }
+  bool used[2] = {false, false};
+  for (int a0 = 0, bi = 0; a0 < sw->n_angles; a0 += B, ++bi) {
     int nb = sw->n_angles - a0 < B ? sw->n_angles - a0 : B;
+    const int L = bi % w.n_lanes;
+    batch_ws &W = w.lane[L];
     pe_view_batch vb;
     memset(&vb, 0, sizeof(vb));
     vb.n = nb;
@@ -137,11 +192,13 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
       if (st != PE_OK) return st;
       for (int k = 0; k < 3; ++k) ks[3 * a + k] = -vb.v[a].d[k];
     }
-    pe_hits h = w.h;
+    // the lane's buffers are free once its previous batch's field is summed
+    if (used[L]) PE_TRY_CUDA(cudaStreamWaitEvent(s, ls.done[L], 0));
+    pe_hits h = W.h;
     h.n_rays = per * nb;
     if (!prm->first_bounce_from_geom) {
-      PE_TRY_CUDA(cudaMemsetAsync(w.keys, 0xff, sizeof(unsigned long long) * per * nb, s));
-      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, w.hz, w.keys, stats, s);
+      PE_TRY_CUDA(cudaMemsetAsync(W.keys, 0xff, sizeof(unsigned long long) * per * nb, s));
+      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, W.hz, W.keys, stats, s);
       if (st != PE_OK) return st;
     }
     // bounce-1 records stay implicit in the incidence GFB (bounce 1 from the
@@ -149,18 +206,31 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
     // from the keys, and only later hits are written as records
     const bool implicit1 = !prm->first_bounce_from_geom && sw->max_bounces >= 2;
     pe_status st =
-        pe_launch_trace(vb, w.keys, nrm, geom, sw->max_bounces, *prm, h, stats, s, implicit1);
+        pe_launch_trace(vb, W.keys, nrm, geom, sw->max_bounces, *prm, h, stats, s, implicit1);
     if (st != PE_OK) return st;
-    // PO: E rows [a0, a0 + nb)
-    const pe_gfb_src src{w.keys, nrm, vb.v};
-    st = pe_launch_po(h, nb, per, ks, sw->freqs_hz, sw->n_freq, w.po, w.po_bytes,
-                      E + (int64_t)a0 * sw->n_freq * 12, s, stats, implicit1 ? &src : nullptr);
+    // PO: E rows [a0, a0 + nb), on the second stream when there is one
+    cudaStream_t sp = s;
+    if (w.n_lanes == 2) {
+      PE_TRY_CUDA(cudaEventRecord(ls.traced, s));
+      PE_TRY_CUDA(cudaStreamWaitEvent(ls.s2, ls.traced, 0));
+      sp = ls.s2;
+    }
+    const pe_gfb_src src{W.keys, nrm, vb.v};
+    st = pe_launch_po(h, nb, per, ks, sw->freqs_hz, sw->n_freq, W.po, W.po_bytes,
+                      E + (int64_t)a0 * sw->n_freq * 12, sp, stats, implicit1 ? &src : nullptr);
     if (st != PE_OK) return st;
     if (sigma) {
       int n = nb * sw->n_freq;
-      sigma_kernel<<<(n + 127) / 128, 128, 0, s>>>(vb, E, w.kw, sw->n_freq, a0, sigma);
+      sigma_kernel<<<(n + 127) / 128, 128, 0, sp>>>(vb, E, w.kw, sw->n_freq, a0, sigma);
       PE_TRY_LAUNCH("sigma_kernel");
     }
+    if (w.n_lanes == 2) {
+      PE_TRY_CUDA(cudaEventRecord(ls.done[L], ls.s2));
+      used[L] = true;
+    }
   }
+  // the caller's stream continues once every field sum has finished
+  for (int l = 0; l < 2; ++l)
+    if (used[l]) PE_TRY_CUDA(cudaStreamWaitEvent(s, ls.done[l], 0));
   return PE_OK;
 }

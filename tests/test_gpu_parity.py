@@ -470,6 +470,33 @@ def test_rcs_sweep_equals_trace_and_field(case, request):
     assert torch.equal(E, E2)
 
 
+@pytest.mark.parametrize("case", GEOMS)
+def test_rcs_sweep_two_lanes_equal_trace_and_field_per_batch(case, request):
+    # With several batches and at least 8 frequencies the sweep sums one
+    # batch's field on a second stream while the next batch traces, in two
+    # sets of batch buffers.  Each batch's field must equal, bit for bit, the
+    # public trace + field of that batch alone (same launch shape).
+    api, pipe = _mods()
+    d = request.getfixturevalue(case)
+    sc = d["sc"]
+    th = [90.0] * 5 + [70.0] if case == "small_geom" else [60.0] * 5 + [54.7356]
+    ph = [0.0, 13.0, 45.0, 62.0, 90.0, 30.0]
+    mb = 2 if case == "small_geom" else 3
+    freqs = scenes.freq_grid(2.6e9, 3.4e9, 9)
+    sw = scenes._sweep_over(sc, th, ph, 48, freqs, mb)
+    args = api.SweepArgs.from_sweep(sw, angle_batch=2)      # three batches, two lanes
+    E, _ = api.rcs_sweep(args, d["pos"], d["nrm"], d["rad"], d["geom"], d["prm"])
+    for a0 in range(0, len(th), 2):
+        views = [api.view_from_angles(t, p, sw.centre, sw.extent, sw.W, sw.H)
+                 for t, p in zip(th[a0:a0 + 2], ph[a0:a0 + 2])]
+        keys = api.build_gfb(views, d["pos"], d["nrm"], d["rad"], 0, outputs=("keys",))["keys"]
+        h = api.trace_bounces(views, keys, d["nrm"], d["geom"], mb, d["prm"], ids=False)
+        ks = np.array([[-x for x in v.d] for v in views], np.float32)
+        E2 = api.po_field(h, len(views), sw.W * sw.H, ks, sw.freqs_hz)
+        assert torch.equal(E[a0:a0 + 2], E2), f"batch at angle {a0}"
+    api.stream_check()
+
+
 def test_rcs_sweep_vs_fp64_physics_oracle(small_geom):
     # The FP64 oracle traces in double precision: a handful of grazing rays
     # can fall on the other side of a disk edge, so the bar is sigma within
