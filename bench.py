@@ -282,7 +282,8 @@ def run_gpu(args, rank, world, local_rank):
                           "po_rot_kernel" if F >= 2 else "po_kernel",
                           clocks.get("sm_mhz") if isinstance(clocks, dict) else None,
                           A * sw.W * sw.H / po_launches_per_step)
-    roof_march = roofline_march(march_ms, march_queries / march_launches_per_step)
+    roof_march = roofline_march(march_ms, march_queries / march_launches_per_step,
+                                int(st[1]) / march_launches_per_step)
     for r, n in ((roof_po, n_po), (roof_march, n_march)):
         if r:
             r["ms_per_step"] = r["ms_per_launch"] * n / args.steps
@@ -336,31 +337,39 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-# Algorithmic bytes of one bounce query of the march: the ray's state is
-# read (hit point, normal, direction, tube vectors: 15 floats; path length:
-# 8 bytes; bounce count: 4 bytes; hit splat id: 4 bytes; 76 bytes) and, on a
-# hit, rewritten (76 bytes).
-MARCH_BYTES_PER_QUERY = 152
+# Algorithmic bytes of the sweep's march: a bounce-2 query reads its pixel's
+# GFB key (8 bytes) and the key point's normal (12 bytes; its bounce-1 record
+# is implicit in them) and writes the pixel's bounce count and Psi (5 bytes);
+# a hit writes a record (hit point, normal, direction, tube vectors: 15
+# floats; path length: 8 bytes; 76 bytes with the count and the id).  Hits at
+# bounces >= 2 per step = the shadow queries (each ray with two or more hits
+# takes one).  With more than two bounces the later queries also read a
+# stored record (76 bytes), which this count leaves out: a lower bound there.
+MARCH_BYTES_PER_QUERY = 25
+MARCH_BYTES_PER_HIT = 76
 
 
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
-# capture of a smaller case (profiles/march_kernel_sphere_batch.md: 440.7 MB
-# over 6,332,964 queries), valid only for the sources it was taken on (their
-# SHA-256 prefixes); scaled to a full launch by the number of queries.
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 69.58,
-                     "sources": {"include/pointemray.h": "409aa4b309cdd7f0",
-                                 "paper_2408_15583_gb300/csrc/trace.cu": "db061c3dfe644367",
-                                 "paper_2408_15583_gb300/csrc/pe_internal.cuh": "a14be3f8629c9849",
-                                 "paper_2408_15583_gb300/csrc/aggregate.cu": "f70f79715eb43faf"}}
+# capture of the sweep's march on a smaller case (one 8-angle batch of the
+# sphere workload through pe_rcs_sweep; profiles/march_kernel_sphere_batch.md:
+# 91.1 MB over 6,332,964 queries), valid only for the sources it was taken on
+# (their SHA-256 prefixes); scaled to a full launch by the number of queries.
+_SWEEP_SOURCES = {"include/pointemray.h": "6d692fe01ba1e08a",
+                  "paper_2408_15583_gb300/csrc/pe_internal.cuh": "845aae3e105fbb3d",
+                  "paper_2408_15583_gb300/csrc/sweep.cu": "7e9b009c70868a41"}
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 14.39,
+                     "sources": dict(_SWEEP_SOURCES, **{
+                         "paper_2408_15583_gb300/csrc/trace.cu": "54b6a350204c8464",
+                         "paper_2408_15583_gb300/csrc/aggregate.cu": "f70f79715eb43faf"})}
 
 # DRAM bytes (read + write) per ray slot of po_rot_kernel from one ncu capture
-# of one 8-angle sphere batch (profiles/po_kernel_sphere_batch.md: 483.6 MB
-# over 8 x 1024^2 slots), valid for the sources it was taken on; scaled to a
-# full launch by its slots (angles x W x H).
-PO_NCU_TRAFFIC = {"bytes_per_slot": 57.65,
-                  "sources": {"include/pointemray.h": "409aa4b309cdd7f0",
-                              "paper_2408_15583_gb300/csrc/po.cu": "9a53dc870eaf92b2",
-                              "paper_2408_15583_gb300/csrc/pe_internal.cuh": "a14be3f8629c9849"}}
+# of the sweep's field sum on one 8-angle sphere batch
+# (profiles/po_kernel_sphere_batch.md: 98.6 MB over 8 x 1024^2 slots), valid
+# for the sources it was taken on; scaled to a full launch by its slots
+# (angles x W x H).
+PO_NCU_TRAFFIC = {"bytes_per_slot": 11.76,
+                  "sources": dict(_SWEEP_SOURCES, **{
+                      "paper_2408_15583_gb300/csrc/po.cu": "b4f92c9cc28dd824"})}
 
 
 def _traffic_valid(rec):
@@ -375,11 +384,12 @@ def _traffic_valid(rec):
     return True
 
 
-def roofline_march(ms_list, queries_per_launch):
+def roofline_march(ms_list, queries_per_launch, hits_per_launch=0.0):
     if not ms_list:
         return None
     ms = float(np.mean(ms_list))
-    achieved = queries_per_launch * MARCH_BYTES_PER_QUERY / (ms / 1e3) / 1e9
+    nbytes = queries_per_launch * MARCH_BYTES_PER_QUERY + hits_per_launch * MARCH_BYTES_PER_HIT
+    achieved = nbytes / (ms / 1e3) / 1e9
     peak, src = hbm_peak()
     traffic = None
     if _traffic_valid(MARCH_NCU_TRAFFIC):
@@ -388,7 +398,8 @@ def roofline_march(ms_list, queries_per_launch):
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "traffic_note": "bytes per launch, scaled by queries from a smaller ncu capture",
             "peak_source": src, "bytes_per_query": MARCH_BYTES_PER_QUERY,
-            "queries_per_launch": queries_per_launch, "ms_per_launch": ms,
+            "bytes_per_hit": MARCH_BYTES_PER_HIT, "queries_per_launch": queries_per_launch,
+            "hits_per_launch": hits_per_launch, "ms_per_launch": ms,
             "launches_timed": len(ms_list)}
 
 
@@ -397,7 +408,10 @@ def roofline_splat(lib, api, sargs, pos, nrm, rad, geom, prm, ws, E, sig, dev, s
     per launch with CUDA events on the launching stream, against the
     device's measured rate of fire-and-forget 64-bit atomicMin (the
     splat's key update; pe_probe_units).  Counters: exact per-pixel tests
-    and key updates (pe_rcs_sweep stats words 5 and 6)."""
+    and key updates (pe_rcs_sweep stats words 5 and 6).  The sweep runs
+    here with one frequency: the same angles, screens and batches, so the
+    same splat launches, but one set of batch buffers, so no field sum of a
+    previous batch shares the SMs with a splat launch being timed."""
     import torch
     from paper_2408_15583_gb300 import peaks
     n_ev = 256
@@ -407,8 +421,14 @@ def roofline_splat(lib, api, sargs, pos, nrm, rad, geom, prm, ws, E, sig, dev, s
     torch.cuda.synchronize()
     ptrs = (ctypes.c_void_p * len(ev))(*[e.cuda_event for e in ev])
     st = torch.zeros(8, dtype=torch.int64, device=dev)
+    c = sargs.c
+    one = api.SweepArgs(sargs.theta, sargs.phi, c.W, c.H, list(c.centre), c.extent,
+                        sargs.freqs[:1], c.max_bounces, c.angle_batch)
+    ws1 = api.workspace(one.workspace_bytes(), dev)
+    E1 = torch.empty((E.shape[0], 1) + tuple(E.shape[2:]), dtype=E.dtype, device=dev)
+    api.rcs_sweep(one, pos, nrm, rad, geom, prm, ws=ws1, E=E1)      # warm
     lib.pe_set_kernel_events(b"splat_kernel", ptrs, n_ev)
-    api.rcs_sweep(sargs, pos, nrm, rad, geom, prm, ws=ws, E=E, sigma=sig, stats=st)
+    api.rcs_sweep(one, pos, nrm, rad, geom, prm, ws=ws1, E=E1, stats=st)
     n = lib.pe_set_kernel_events(None, None, 0)
     torch.cuda.synchronize()
     api.stream_check()

@@ -3,6 +3,7 @@
     python -m paper_2408_15583_gb300.profile_case march [reps] [workload]  # one traced batch
     python -m paper_2408_15583_gb300.profile_case po [reps] [workload]     # PO over that batch
     python -m paper_2408_15583_gb300.profile_case splat [reps] [workload]  # incidence splats
+    python -m paper_2408_15583_gb300.profile_case sweep [reps] [workload]  # pe_rcs_sweep of the batch
     python -m paper_2408_15583_gb300.profile_case unet [reps] [batch] [mma]  # U-Net training steps
 
 By default each case is the sphere workload's geometry (200k points, 8 fused
@@ -56,6 +57,18 @@ def main(argv):
     stats = torch.zeros(8, dtype=torch.int64, device=dev)
     h = api.trace_bounces(views, keys, nrm, geom, mb, prm, ids=False, stats=stats)
     ks = [[-x for x in v.d] for v in views]
+    if case == "sweep":
+        import numpy as np
+        sub = [a * na // nb for a in range(nb)]
+        sargs = api.SweepArgs(theta_deg=np.asarray(sw.theta_deg, np.float64)[sub],
+                              phi_deg=np.asarray(sw.phi_deg, np.float64)[sub], W=sw.W, H=sw.H,
+                              centre=sw.centre, extent=sw.extent,
+                              freqs_hz=np.asarray(sw.freqs_hz, np.float64), max_bounces=mb,
+                              angle_batch=nb)
+        sws = api.workspace(sargs.workspace_bytes(), dev)
+        sE = torch.empty((nb, len(sw.freqs_hz), 2, 3, 2), dtype=torch.float64, device=dev)
+        sS = torch.empty((nb, len(sw.freqs_hz), 2, 2), dtype=torch.float64, device=dev)
+        api.rcs_sweep(sargs, pos, nrm, rad, geom, prm, ws=sws, E=sE, sigma=sS)
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(reps):
@@ -65,6 +78,10 @@ def main(argv):
             api.po_field(h, nb, sw.W * sw.H, ks, sw.freqs_hz)
         elif case == "splat":
             api.build_gfb(views, pos, nrm, rad, 0, outputs=("keys",))
+        elif case == "sweep":
+            # the same 8 angles through the whole sweep (one batch: its march
+            # and field sum keep the bounce-1 records implicit in the keys)
+            api.rcs_sweep(sargs, pos, nrm, rad, geom, prm, ws=sws, E=sE, sigma=sS)
         else:
             raise SystemExit(f"unknown case {case}")
     torch.cuda.synchronize()

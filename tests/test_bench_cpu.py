@@ -8,15 +8,16 @@ import bench  # noqa: E402
 
 
 def test_march_roofline_arithmetic(monkeypatch):
-    # 1e6 queries of 152 algorithmic bytes in 2 ms: 76 GB/s; against a
-    # 7600 GB/s peak, 0.01
+    # 1e6 queries of 25 algorithmic bytes and 1e5 hits of 76 in 2 ms:
+    # 32.6e6 B / 2e-3 s = 16.3 GB/s; against a 7600 GB/s peak, 0.00214
     monkeypatch.setattr(bench, "hbm_peak", lambda: (7600.0, "test"))
-    r = bench.roofline_march([1.5, 2.5], 1_000_000)
+    r = bench.roofline_march([1.5, 2.5], 1_000_000, 100_000)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["ms_per_launch"] == pytest.approx(2.0)
-    assert r["achieved"] == pytest.approx(1e6 * bench.MARCH_BYTES_PER_QUERY / 2e-3 / 1e9)
-    assert r["achieved"] == pytest.approx(76.0)
-    assert r["frac"] == pytest.approx(0.01)
+    assert r["achieved"] == pytest.approx(
+        (1e6 * bench.MARCH_BYTES_PER_QUERY + 1e5 * bench.MARCH_BYTES_PER_HIT) / 2e-3 / 1e9)
+    assert r["achieved"] == pytest.approx(16.3)
+    assert r["frac"] == pytest.approx(16.3 / 7600.0)
     assert r["launches_timed"] == 2
     if r["traffic"] is not None:
         assert r["traffic"] == pytest.approx(bench.MARCH_NCU_TRAFFIC["bytes_per_query"] * 1e6)
