@@ -349,85 +349,117 @@ __device__ __forceinline__ void seg_add(seg_acc &a, const pe_geom_layout &L,
 
 // One thread per voxel segment: order the keys, FP64 sums in that order,
 // Eq. 22 maximum, write the splat at the owner pixel.
-__global__ void fuse_segment_kernel(const __grid_constant__ pe_geom_layout L,
-                                    const float4 *__restrict__ nd,
-                                    const unsigned long long *__restrict__ entries,
-                                    const uint32_t *__restrict__ offs, int64_t nvox,
-                                    float4 *__restrict__ cr, float4 *__restrict__ nf) {
-  const int64_t n_entries = offs[nvox];  // kept pixels, written by scan_apply
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_entries;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long k0 = entries[s];
-    uint32_t vox = (uint32_t)(k0 >> 40);
-    if (offs[vox] != (uint32_t)s) continue;
-    int64_t len = (int64_t)offs[vox + 1] - s;
-    seg_acc a;
-    a.sp[0] = a.sp[1] = a.sp[2] = a.sn[0] = a.sn[1] = a.sn[2] = 0.0;
-    a.rmax = 0.0;
-    a.first = true;
-    unsigned long long owner;
-    if (len <= kSegLocal) {
-      unsigned long long buf[kSegLocal];
-      for (int64_t e = 0; e < len; ++e) {
-        unsigned long long k = entries[s + e];
-        int64_t m = e;
-        while (m > 0 && buf[m - 1] > k) {
-          buf[m] = buf[m - 1];
-          --m;
-        }
-        buf[m] = k;
+// One voxel segment (entries [s, offs[vox + 1]) of voxel vox, s = offs[vox]):
+// the fused splat at its owner pixel.
+__device__ __forceinline__ void fuse_one_segment(const pe_geom_layout &L,
+                                                 const float4 *__restrict__ nd,
+                                                 const unsigned long long *__restrict__ entries,
+                                                 const uint32_t *__restrict__ offs, int64_t s,
+                                                 float4 *__restrict__ cr, float4 *__restrict__ nf) {
+  const uint32_t vox = (uint32_t)(entries[s] >> 40);
+  int64_t len = (int64_t)offs[vox + 1] - s;
+  seg_acc a;
+  a.sp[0] = a.sp[1] = a.sp[2] = a.sn[0] = a.sn[1] = a.sn[2] = 0.0;
+  a.rmax = 0.0;
+  a.first = true;
+  unsigned long long owner;
+  if (len <= kSegLocal) {
+    unsigned long long buf[kSegLocal];
+    for (int64_t e = 0; e < len; ++e) {
+      unsigned long long k = entries[s + e];
+      int64_t m = e;
+      while (m > 0 && buf[m - 1] > k) {
+        buf[m] = buf[m - 1];
+        --m;
       }
-      owner = buf[0];
-      for (int64_t e = 0; e < len; ++e) seg_add(a, L, nd, buf[e]);
-    } else {
-      // long segment: visit keys in increasing order by repeated minimum
-      unsigned long long last = 0;
-      bool have = false;
-      owner = ~0ull;
-      for (int64_t e = 0; e < len; ++e) {
-        unsigned long long best = ~0ull;
-        for (int64_t f = 0; f < len; ++f) {
-          unsigned long long k = entries[s + f];
-          if ((!have || k > last) && k < best) best = k;
-        }
-        if (!have) owner = best;
-        seg_add(a, L, nd, best);
-        last = best;
-        have = true;
+      buf[m] = k;
+    }
+    owner = buf[0];
+    for (int64_t e = 0; e < len; ++e) seg_add(a, L, nd, buf[e]);
+  } else {
+    // long segment: visit keys in increasing order by repeated minimum
+    unsigned long long last = 0;
+    bool have = false;
+    owner = ~0ull;
+    for (int64_t e = 0; e < len; ++e) {
+      unsigned long long best = ~0ull;
+      for (int64_t f = 0; f < len; ++f) {
+        unsigned long long k = entries[s + f];
+        if ((!have || k > last) && k < best) best = k;
       }
+      if (!have) owner = best;
+      seg_add(a, L, nd, best);
+      last = best;
+      have = true;
     }
-    double cnt = (double)len;
-    double m = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a.sn[0], a.sn[0]), __dmul_rn(a.sn[1], a.sn[1])),
-                                    __dmul_rn(a.sn[2], a.sn[2])));
-    const pe_f3 nrm = {__double2float_rn(__ddiv_rn(a.sn[0], m)),
-                       __double2float_rn(__ddiv_rn(a.sn[1], m)),
-                       __double2float_rn(__ddiv_rn(a.sn[2], m))};
-    // Owner: the contributing view facing the fused normal most directly, by
-    // |n . d_v| in quarters (floor(4 |n . d_v|), so near-equal views tie),
-    // the smaller (view, pixel) key on a tie; the first entry if the normal
-    // vanishes.  Owners of neighbouring voxels then mostly come from the same
-    // view, which keeps each stretch of surface in few pyramids.
-    if (m > 0.0) {
-      float bs = -1.0f;
-      unsigned long long bk = owner;
-      auto consider = [&](unsigned long long k) {
-        const pe_view &V = L.view[(int)((k >> 32) & 0xff)];
-        const float sc = floorf(__fmul_rn(fabsf(pe_dot(nrm, pe_f3{V.d[0], V.d[1], V.d[2]})), 4.0f));
-        if (sc > bs || (sc == bs && k < bk)) {
-          bs = sc;
-          bk = k;
-        }
-      };
-      for (int64_t e = 0; e < len; ++e) consider(entries[s + e]);
-      owner = bk;
-    }
-    int v0 = (int)((owner >> 32) & 0xff);
-    int64_t id = L.pix_off[v0] + (int64_t)(owner & 0xffffffffull);
-    cr[id] = make_float4(__double2float_rn(__ddiv_rn(a.sp[0], cnt)),
-                         __double2float_rn(__ddiv_rn(a.sp[1], cnt)),
-                         __double2float_rn(__ddiv_rn(a.sp[2], cnt)), __double2float_rn(a.rmax));
-    nf[id] = make_float4(nrm.x, nrm.y, nrm.z, (float)len);
   }
+  double cnt = (double)len;
+  double m = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a.sn[0], a.sn[0]), __dmul_rn(a.sn[1], a.sn[1])),
+                                  __dmul_rn(a.sn[2], a.sn[2])));
+  const pe_f3 nrm = {__double2float_rn(__ddiv_rn(a.sn[0], m)),
+                     __double2float_rn(__ddiv_rn(a.sn[1], m)),
+                     __double2float_rn(__ddiv_rn(a.sn[2], m))};
+  // Owner: the contributing view facing the fused normal most directly, by
+  // |n . d_v| in quarters (floor(4 |n . d_v|), so near-equal views tie),
+  // the smaller (view, pixel) key on a tie; the first entry if the normal
+  // vanishes.  Owners of neighbouring voxels then mostly come from the same
+  // view, which keeps each stretch of surface in few pyramids.
+  if (m > 0.0) {
+    float bs = -1.0f;
+    unsigned long long bk = owner;
+    auto consider = [&](unsigned long long k) {
+      const pe_view &V = L.view[(int)((k >> 32) & 0xff)];
+      const float sc = floorf(__fmul_rn(fabsf(pe_dot(nrm, pe_f3{V.d[0], V.d[1], V.d[2]})), 4.0f));
+      if (sc > bs || (sc == bs && k < bk)) {
+        bs = sc;
+        bk = k;
+      }
+    };
+    for (int64_t e = 0; e < len; ++e) consider(entries[s + e]);
+    owner = bk;
+  }
+  int v0 = (int)((owner >> 32) & 0xff);
+  int64_t id = L.pix_off[v0] + (int64_t)(owner & 0xffffffffull);
+  cr[id] = make_float4(__double2float_rn(__ddiv_rn(a.sp[0], cnt)),
+                       __double2float_rn(__ddiv_rn(a.sp[1], cnt)),
+                       __double2float_rn(__ddiv_rn(a.sp[2], cnt)), __double2float_rn(a.rmax));
+  nf[id] = make_float4(nrm.x, nrm.y, nrm.z, (float)len);
+}
+
+// One segment per lane: each warp examines 32 entries at a time and queues,
+// in shared memory, the ones that start a voxel's segment; whenever 32 are
+// queued its lanes take one each (a segment's work is a serial chain of FP64
+// sums, so a lane per segment, not per entry, keeps the warp full).
+constexpr int kFuseThreads = 128;
+
+__global__ void __launch_bounds__(kFuseThreads)
+    fuse_segment_kernel(const __grid_constant__ pe_geom_layout L, const float4 *__restrict__ nd,
+                        const unsigned long long *__restrict__ entries,
+                        const uint32_t *__restrict__ offs, int64_t nvox,
+                        float4 *__restrict__ cr, float4 *__restrict__ nf) {
+  __shared__ uint32_t queue[kFuseThreads / 32][64];
+  const int64_t n_entries = offs[nvox];  // kept pixels, written by scan_apply
+  const int lane = threadIdx.x & 31;
+  uint32_t *q = queue[threadIdx.x >> 5];
+  int count = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_entries;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = base + lane;
+    bool head = false;
+    if (s < n_entries) head = offs[(uint32_t)(entries[s] >> 40)] == (uint32_t)s;
+    const unsigned m = __ballot_sync(0xffffffffu, head);
+    if (head) q[count + __popc(m & ((1u << lane) - 1u))] = (uint32_t)s;
+    count += __popc(m);
+    __syncwarp();
+    if (count >= 32) {
+      fuse_one_segment(L, nd, entries, offs, q[lane], cr, nf);
+      __syncwarp();
+      if (lane < count - 32) q[lane] = q[lane + 32];
+      count -= 32;
+      __syncwarp();
+    }
+  }
+  if (lane < count) fuse_one_segment(L, nd, entries, offs, q[lane], cr, nf);
 }
 
 // Leaf boxes: bounds of the owned splats' spheres in the view's (u, v, d)
@@ -959,8 +991,8 @@ extern "C" pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
   PE_TRY_LAUNCH("fuse_scatter_kernel");
   // segment heads are found by slot; the kernel reads the entry count
   // offs[nvox] on the device (at most total_pix)
-  fuse_segment_kernel<<<grid_for(total_pix, 128, cap), 128, 0, s>>>(L, nd, w.entries, w.offs,
-                                                                     nvox, cr, nf);
+  fuse_segment_kernel<<<grid_for(total_pix, kFuseThreads, cap), kFuseThreads, 0, s>>>(
+      L, nd, w.entries, w.offs, nvox, cr, nf);
   PE_TRY_LAUNCH("fuse_segment_kernel");
   const int64_t n3 = (int64_t)PE_VGRID * PE_VGRID * PE_VGRID;
   PE_TRY_CUDA(cudaMemsetAsync(vmask, 0, sizeof(uint32_t) * ((size_t)n3 + 1), s));
