@@ -59,6 +59,27 @@ def test_view_setup_matches_oracle_bitwise(lib):
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
+def test_sweep_workspace_two_lanes(lib):
+    # A sweep of several batches with at least 8 frequencies holds two sets
+    # of batch buffers (its field sums run beside the next batch's trace);
+    # one frequency, or a single batch, holds one.
+    from paper_2408_15583_gb300 import api
+    import numpy as np
+
+    def ws(n_angles, n_freq):
+        args = api.SweepArgs(np.full(n_angles, 90.0), np.linspace(0, 359, n_angles), 1024, 1024,
+                             [0.0, 0.0, 0.0], 1.0, np.linspace(8e9, 12e9, n_freq), 2)
+        return args.workspace_bytes()
+
+    per_angle = 1024 * 1024 * (8 + 60 + 8 + 4 + 1)      # keys and ray records
+    one = ws(360, 1)
+    two = ws(360, 64)
+    assert 64 * per_angle <= one < 2 * 64 * per_angle
+    assert two >= 2 * 64 * per_angle                     # two sets of 64-angle batches
+    assert ws(10, 64) < 11 * per_angle + (1 << 30)       # one batch of 10 angles, one set
+    assert ws(0, 64) == 0
+
+
 def test_workspace_queries(lib):
     from paper_2408_15583_gb300 import api
     vs = [api.view_from_angles(60, 45 + 90 * i, [0, 0, 0], 1.0, 512, 512) for i in range(8)]
