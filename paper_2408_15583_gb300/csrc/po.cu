@@ -115,19 +115,23 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f
     p = {h.p[3 * slot], h.p[3 * slot + 1], h.p[3 * slot + 2]};
     path = h.path[slot];
   }
+  // (the field is summed to a relative tolerance, so the per-ray factors use
+  // the fast reciprocal and reciprocal square root: a few ulp each)
   float nk = dotf(n, kk);
   if (nk == 0.0f) return false;
-  float su = dotf(n, u) / nk, sv = dotf(n, v) / nk;
+  const float ink = __fdividef(1.0f, nk);
+  float su = dotf(n, u) * ink, sv = dotf(n, v) * ink;
   pe_f3 up = {u.x - kk.x * su, u.y - kk.y * su, u.z - kk.z * su};
   pe_f3 vp = {v.x - kk.x * sv, v.y - kk.y * sv, v.z - kk.z * sv};
   pe_f3 cr = cross(up, vp);
-  float area = sqrtf(dotf(cr, cr));
+  const float c2 = dotf(cr, cr);
+  float area = c2 > 0.0f ? c2 * rsqrtf(c2) : 0.0f;
   pe_f3 q = {kk.x - ks.x, kk.y - ks.y, kk.z - ks.z};
   au = 0.5f * dotf(q, up);
   av = 0.5f * dotf(q, vp);
-  float lu = sqrtf(dotf(u, u)), lv = sqrtf(dotf(v, v));
-  pe_f3 hv = {-v.x / lv, -v.y / lv, -v.z / lv};
-  pe_f3 hh = {u.x / lu, u.y / lu, u.z / lu};
+  const float ilu = rsqrtf(dotf(u, u)), ilv = rsqrtf(dotf(v, v));
+  pe_f3 hv = {-v.x * ilv, -v.y * ilv, -v.z * ilv};
+  pe_f3 hh = {u.x * ilu, u.y * ilu, u.z * ilu};
   pe_f3 a = cross(cross(cross(n, hv), ks), ks);
   pe_f3 c = cross(cross(cross(n, hh), ks), ks);
   V[0] = area * dotf(a, e1);
