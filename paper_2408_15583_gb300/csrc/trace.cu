@@ -168,7 +168,9 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
   float t0 = tmin - 1e-3f * cell, t1 = INFINITY;
   float inv[3];
   for (int k = 0; k < 3; ++k) {
-    inv[k] = 1.0f / slab_dir(dd[k]);  // finite; exact zeros take the branch below
+    // fast reciprocal: the cell boundaries it places move by ~1e-7 of t,
+    // far inside the marking pad and the walk's slack
+    inv[k] = __fdividef(1.0f, slab_dir(dd[k]));  // finite; exact zeros take the branch below
     float a = (0.0f - oo[k]) * inv[k], b = (size - oo[k]) * inv[k];
     if (dd[k] == 0.0f) {
       if (oo[k] < 0.0f || oo[k] > size) return m;
@@ -182,9 +184,10 @@ __device__ uint32_t view_mask(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float t
   // small arrays would put them in local memory)
   int ix[3], st[3];
   float tmax[3], tdel[3];
+  const float icell = __fdividef(1.0f, cell);
   for (int k = 0; k < 3; ++k) {
     float p = oo[k] + t0 * dd[k];
-    int c = (int)floorf(p / cell);
+    int c = (int)floorf(p * icell);
     ix[k] = c < 0 ? 0 : (c > n - 1 ? n - 1 : c);
     if (dd[k] > 0.0f) {
       st[k] = 1;
@@ -304,9 +307,10 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
     // (the FMA slab form moves a face by ~1e-7 |origin|, far inside the
     // boxes' padding of 1e-5 of the view's span)
     vray r;
-    r.ix = 1.0f / slab_dir(d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2]);
-    r.iy = 1.0f / slab_dir(d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2]);
-    r.iz = 1.0f / slab_dir(d.x * V.d[0] + d.y * V.d[1] + d.z * V.d[2]);
+    // (fast reciprocals: 2 ulp, far inside the boxes' padding)
+    r.ix = __fdividef(1.0f, slab_dir(d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2]));
+    r.iy = __fdividef(1.0f, slab_dir(d.x * V.v[0] + d.y * V.v[1] + d.z * V.v[2]));
+    r.iz = __fdividef(1.0f, slab_dir(d.x * V.d[0] + d.y * V.d[1] + d.z * V.d[2]));
     r.nx = -(q.x * V.u[0] + q.y * V.u[1] + q.z * V.u[2]) * r.ix;
     r.ny = -(q.x * V.v[0] + q.y * V.v[1] + q.z * V.v[2]) * r.iy;
     r.nz = -(q.x * V.d[0] + q.y * V.d[1] + q.z * V.d[2]) * r.iz;
@@ -336,7 +340,7 @@ __device__ void walk(const pe_geom_layout &L, pe_f3 o, pe_f3 d, float tmin, floa
       if (top > 0 && __all_sync(FULL, !lv || fin)) {
         int lx0 = 0x7fffffff, ly0 = 0x7fffffff, lx1 = -1, ly1 = -1;
         if (lv) {
-          const float il = 1.0f / V.pitch, reach = rhi.w + 2.0f;
+          const float il = __fdividef(1.0f, V.pitch), reach = rhi.w + 2.0f;
           const float au = q.x * V.u[0] + q.y * V.u[1] + q.z * V.u[2];
           const float av = q.x * V.v[0] + q.y * V.v[1] + q.z * V.v[2];
           const float du = d.x * V.u[0] + d.y * V.u[1] + d.z * V.u[2];
