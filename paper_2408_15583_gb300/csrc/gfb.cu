@@ -68,7 +68,7 @@ __device__ __forceinline__ bool point_footprint(const pe_view &V, const float *_
   }
   if (!(F.R >= 0.0f)) return false;
   const float qx = F.c.x - V.o[0], qy = F.c.y - V.o[1], qz = F.c.z - V.o[2];
-  const float inv = 1.0f / V.pitch;
+  const float inv = __fdividef(1.0f, V.pitch);  // (bounds only: 2 ulp is far below their margin)
   F.ci = (qx * V.u[0] + qy * V.u[1] + qz * V.u[2]) * inv + 0.5f * V.W - 0.5f;
   F.cj = (qx * V.v[0] + qy * V.v[1] + qz * V.v[2]) * inv + 0.5f * V.H - 0.5f;
   F.dc = qx * V.d[0] + qy * V.d[1] + qz * V.d[2];
@@ -121,7 +121,7 @@ __device__ __forceinline__ void splat_point(const pe_view &V, const footprint &F
     nv = nn.x * V.v[0] + nn.y * V.v[1] + nn.z * V.v[2];
     nw = -(nn.x * V.d[0] + nn.y * V.d[1] + nn.z * V.d[2]);
   }
-  const float inv = 1.0f / V.pitch;
+  const float inv = __fdividef(1.0f, V.pitch);
   const float Rw = F.R * 1.0001f + 0.02f * V.pitch;
   const float qa = nw * nw + nu * nu;
   const bool rows = qa > 1e-3f;
@@ -133,7 +133,8 @@ __device__ __forceinline__ void splat_point(const pe_view &V, const footprint &F
       const float qc = b * b * (nw * nw + nv * nv) - Rw * Rw * nw * nw;
       const float disc = qb * qb - 4.0f * qa * qc;
       if (disc < 0.0f) continue;
-      const float sq = sqrtf(disc), inv2a = 0.5f / qa;
+      // (fast square root and reciprocal: the bounds keep 0.05 px of slack)
+      const float sq = disc > 0.0f ? disc * rsqrtf(disc) : 0.0f, inv2a = __fdividef(0.5f, qa);
       const float alo = (-qb - sq) * inv2a, ahi = (-qb + sq) * inv2a;
       ia = max(ia, (int)floorf(F.ci + alo * inv - 0.05f));
       ib = min(ib, (int)ceilf(F.ci + ahi * inv + 0.05f));
