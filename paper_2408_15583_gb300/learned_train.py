@@ -28,7 +28,7 @@ import torch
 
 from . import _lib, api, pipeline
 from ._lib import check
-from .learned import UNet, lr_schedule
+from .learned import GraphedUNet, UNet, lr_schedule
 
 C0 = 299_792_458.0
 
@@ -239,7 +239,8 @@ def evaluate(model: UNet, data: List[dict]):
 
 def time_paths(model: UNet, sparse, dense, vs: ViewSet, reps=5):
     """Per-view time of the learned path (tube splat of the sparse cloud +
-    network inference) and of plain surfel splatting of the dense cloud."""
+    network inference; the network eager, and replayed as a captured CUDA
+    graph) and of plain surfel splatting of the dense cloud."""
     dev = model.dev
     ps, _, _ = pipeline.scene_to_device(sparse, dev)
     pd, nd_, rd = pipeline.scene_to_device(dense, dev)
@@ -249,20 +250,30 @@ def time_paths(model: UNet, sparse, dense, vs: ViewSet, reps=5):
     x = torch.empty(n * vs.W * vs.W, dtype=torch.bfloat16, device=dev)
     arr = api.views_to_array(vs.views)
 
-    def learned():
+    graphed = GraphedUNet(model, n, vs.W, vs.W)
+
+    def coarse():
         keys = api.build_gfb(vs.views, ps, None, None, 1, delta, outputs=("keys",))["keys"]
         check(lib.pe_learned_pairs(arr, n, vs.t_near.ctypes.data_as(C.c_void_p),
                                    vs.t_scale.ctypes.data_as(C.c_void_p), _p(keys), None, _p(x),
                                    None, None, None,
                                    C.c_void_p(torch.cuda.current_stream().cuda_stream)),
               "pe_learned_pairs")
+
+    def learned():
+        coarse()
         model.forward(x, n, vs.W, vs.W)
+
+    def learned_graphed():
+        coarse()
+        graphed.forward(x)
 
     def plain():
         api.build_gfb(vs.views, pd, nd_, rd, 0, outputs=("nd", "mask"))
 
     out = {}
-    for name, fn in (("learned", learned), ("plain_splatting", plain)):
+    for name, fn in (("learned", learned), ("learned_graphed", learned_graphed),
+                     ("plain_splatting", plain)):
         fn()
         torch.cuda.synchronize()
         t = time.perf_counter()

@@ -352,6 +352,33 @@ def test_training_reduces_the_loss():
     assert last < 0.8 * first, hist
 
 
+def test_graphed_steps_equal_the_eager_steps():
+    # The U-Net's training step (forward, losses, backward) and its forward
+    # pass replayed as captured CUDA graphs give the eager calls' results bit
+    # for bit: losses, every parameter after two AdamW updates, and the
+    # inference outputs.
+    from paper_2408_15583_gb300.learned import GraphedUNet
+    Bn, H, W = 2, 64, 64
+    _, net_a = _net(WID, BLK, 11)
+    _, net_b = _net(WID, BLK, 11)
+    g = torch.Generator().manual_seed(5)
+    x = torch.rand(Bn * H * W, generator=g).to(DEV, torch.bfloat16)
+    d, n, m = _rand_targets(Bn, H, W, 12)
+    dg = torch.tensor(d, dtype=torch.float32, device=DEV).reshape(-1)
+    ng = torch.tensor(n, dtype=torch.float32, device=DEV).reshape(-1, 3)
+    mg = torch.tensor(m, dtype=torch.float32, device=DEV).reshape(-1)
+    gb = GraphedUNet(net_b, Bn, H, W)
+    for step in range(2):
+        la = net_a.train_step(x, dg, ng, mg, Bn, H, W, 1e-3)
+        lb = gb.train_step(x, dg, ng, mg, 1e-3)
+        assert torch.equal(la, lb), f"step {step}"
+    assert torch.equal(net_a.master, net_b.master)
+    oa, _ = net_a.forward(x, Bn, H, W)
+    ob = gb.forward(x)
+    for k in oa:
+        assert torch.equal(oa[k], ob[k]), k
+
+
 def test_learned_gfb_beats_the_coarse_gfb_on_held_out_targets():
     """What the trained network gains over the method without it: the
     coarse tube-tracing GFB with Eq. 16 normals vs the network's GFB, both
