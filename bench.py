@@ -157,9 +157,15 @@ def run_gpu(args, rank, world, local_rank):
     stats = torch.zeros(8, dtype=torch.int64, device=dev)
     gfb_ws = None
 
+    # the incidence splat takes the points in a spatially coherent order,
+    # computed from the step's points inside the step
+    order = torch.empty(sc.n, dtype=torch.int32, device=dev)
+    sargs.set_point_order(order)
+
     def step(p, n, r, st=None):
         g = api.build_gfb(gv, p, n, r, 0, 0.0, outputs=("nd", "mask"))
         api.aggregate_views(gv, g["nd"], g["mask"], prm, geom=geom)
+        api.order_points(p, out=order)
         api.rcs_sweep(sargs, p, n, r, geom, prm, ws=ws, E=E, sigma=sig, stats=st)
 
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -424,6 +430,7 @@ def roofline_splat(lib, api, sargs, pos, nrm, rad, geom, prm, ws, E, sig, dev, s
     c = sargs.c
     one = api.SweepArgs(sargs.theta, sargs.phi, c.W, c.H, list(c.centre), c.extent,
                         sargs.freqs[:1], c.max_bounces, c.angle_batch)
+    one.set_point_order(sargs.order)
     ws1 = api.workspace(one.workspace_bytes(), dev)
     E1 = torch.empty((E.shape[0], 1) + tuple(E.shape[2:]), dtype=E.dtype, device=dev)
     api.rcs_sweep(one, pos, nrm, rad, geom, prm, ws=ws1, E=E1)      # warm

@@ -197,6 +197,18 @@ pe_status pe_build_gfb_topk(const pe_view *views, int32_t n_views, const float *
  * 32, n >= max(k_r + 1, k_n), n < 2^32; ws of
  * pe_point_attributes_workspace(n) bytes (256-byte aligned). */
 size_t pe_point_attributes_workspace(int64_t n_points);
+
+/* A spatially coherent processing order of the points (no counterpart in the
+ * paper): order_dev[0..n) = a permutation of 0..n-1 grouping the points by
+ * the Morton cell of a 32^3 grid over their bounding box (cells in Morton
+ * order; the order within a cell is unspecified).  Neighbouring points then
+ * project to footprints of similar size, so the lanes of a splat warp stay
+ * busy together (pe_sweep.point_order).  ws of pe_order_points_workspace(n)
+ * bytes (256-byte aligned); 1 <= n < 2^32; positions are clamped into the
+ * grid (a non-finite one lands in an edge cell). */
+size_t pe_order_points_workspace(int64_t n_points);
+pe_status pe_order_points(const float *pos_dev, int64_t n_points, void *ws, size_t ws_bytes,
+                          uint32_t *order_dev, void *stream);
 pe_status pe_point_attributes(const float *pos_dev, int64_t n_points, int32_t k_r, int32_t k_n,
                               const float *ref_nrm_dev, void *ws, size_t ws_bytes,
                               float *radius_dev, float *normal_dev, void *stream);
@@ -465,6 +477,11 @@ typedef struct {
                                 (as many as fit ~16 GB of ray records, or
                                 ~8 GB per set of batch buffers when there
                                 are two: see pe_rcs_sweep) */
+  const uint32_t *point_order; /* device [n_points] or NULL: the order in which
+                                the incidence splat takes the points (a
+                                permutation, e.g. from pe_order_points); the
+                                keys, which hold the points' own indices, do
+                                not depend on it */
 } pe_sweep;
 
 /* The view of a monostatic incidence (a1): w = (sin t cos p, sin t sin p,

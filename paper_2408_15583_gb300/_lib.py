@@ -47,7 +47,8 @@ class PeSweep(C.Structure):
     _fields_ = [("n_angles", C.c_int32), ("theta_deg", C.c_void_p), ("phi_deg", C.c_void_p),
                 ("W", C.c_int32), ("H", C.c_int32), ("centre", C.c_double * 3),
                 ("extent", C.c_double), ("n_freq", C.c_int32), ("freqs_hz", C.c_void_p),
-                ("max_bounces", C.c_int32), ("angle_batch", C.c_int32)]
+                ("max_bounces", C.c_int32), ("angle_batch", C.c_int32),
+                ("point_order", C.c_void_p)]
 
 
 # name -> (restype, argtypes)
@@ -80,6 +81,8 @@ SIGNATURES = {
     "pe_nn_gemm_path": (C.c_int32, [C.c_int32]),
     "pe_nn_set_wait_limit": (C.c_int, [C.c_int64]),
     "pe_point_attributes_workspace": (C.c_size_t, [C.c_int64]),
+    "pe_order_points_workspace": (C.c_size_t, [C.c_int64]),
+    "pe_order_points": (C.c_int, [P, C.c_int64, P, C.c_size_t, P, P]),
     "pe_po_field_bistatic_workspace": (C.c_size_t, [C.c_int32, C.c_int64, C.c_int32]),
     "pe_po_field_every_bounce_workspace": (C.c_size_t, [C.c_int32, P, C.c_int32]),
     "pe_po_field_every_bounce": (C.c_int, [P, C.c_int32, P, P, P, C.c_int32, P, P, C.c_int32, P,

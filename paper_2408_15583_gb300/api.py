@@ -180,6 +180,19 @@ def point_attributes(pos: torch.Tensor, k_r: int = 8, k_n: int = 16,
     return r, nr
 
 
+def order_points(pos: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """A spatially coherent processing order of the points
+    (``pe_order_points``): int32 [n] permutation grouping them by cell of a
+    32^3 grid, for SweepArgs.set_point_order."""
+    lib = _lib()
+    n = int(pos.shape[0])
+    ws = workspace(lib.pe_order_points_workspace(n), pos.device)
+    order = out if out is not None else torch.empty(n, dtype=torch.int32, device=pos.device)
+    check(lib.pe_order_points(_p(pos), n, _p(ws), ws.numel(), _p(order), _s(stream)),
+          "pe_order_points")
+    return order
+
+
 def alloc_geom(views: Sequence[PeView], device) -> Geom:
     n = len(views)
     arr = views_to_array(views)
@@ -346,7 +359,16 @@ class SweepArgs:
         s.freqs_hz = self.freqs.ctypes.data
         s.max_bounces = int(max_bounces)
         s.angle_batch = int(angle_batch)
+        s.point_order = None
+        self.order = None
         self.c = s
+
+    def set_point_order(self, order: Optional[torch.Tensor]):
+        """The incidence splat's processing order of the points (device
+        int32 permutation from order_points, or None); it does not change
+        the results.  The tensor must stay alive while the sweep runs."""
+        self.order = order
+        self.c.point_order = None if order is None else order.data_ptr()
 
     @classmethod
     def from_sweep(cls, sw, angle_batch=0):

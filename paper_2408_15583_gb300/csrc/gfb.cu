@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(kSplatThreads)
     splat_kernel(const __grid_constant__ pe_view_batch vb, const float *__restrict__ pos,
                  const float *__restrict__ nrm, const float *__restrict__ rad, int64_t n,
                  int mode, float delta, int pass, const float *__restrict__ hz,
-                 unsigned long long *__restrict__ keys, long long *__restrict__ stats) {
+                 unsigned long long *__restrict__ keys, long long *__restrict__ stats,
+                 const uint32_t *__restrict__ order) {
   __shared__ int64_t queue[kSplatThreads / 32][64];
   long long n_test = 0, n_hit = 0;
   const int vi = blockIdx.y;
@@ -176,9 +177,12 @@ __global__ void __launch_bounds__(kSplatThreads)
   int count = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
        base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = base + lane;
+    // the point this lane examines: the i-th of the processing order (a
+    // permutation, or the identity); its key holds its own index either way
+    const int64_t i = base + lane;
+    const int64_t p = i < n ? (order ? (int64_t)__ldg(order + i) : i) : n;
     footprint F;
-    const bool keep = p < n && point_footprint(V, pos, nrm, rad, p, mode, delta, F) &&
+    const bool keep = i < n && p < n && point_footprint(V, pos, nrm, rad, p, mode, delta, F) &&
                       in_pass(V, F, pass, hv, tw);
     const unsigned m = __ballot_sync(0xffffffffu, keep);
     if (keep) q[count + __popc(m & ((1u << lane) - 1u))] = p;
@@ -295,7 +299,8 @@ size_t pe_splat_tiles(int32_t n_views, int32_t W, int32_t H) {
 
 pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float *nrm,
                           const float *rad, int64_t n, int mode, float delta, float *hz,
-                          unsigned long long *keys, int64_t *stats, cudaStream_t s) {
+                          unsigned long long *keys, int64_t *stats, cudaStream_t s,
+                          const uint32_t *order) {
   long long *st = reinterpret_cast<long long *>(stats);
   if (n <= 0) return PE_OK;
   int64_t blocks_needed = (n + kSplatThreads - 1) / kSplatThreads;
@@ -307,7 +312,7 @@ pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float
   const bool two = mode == 0 && hz != nullptr;
   pe_event_before("splat_kernel", s);
   splat_kernel<<<grid, kSplatThreads, 0, s>>>(vb, pos, nrm, rad, n, mode, delta, two ? 1 : 0,
-                                               nullptr, keys, st);
+                                               nullptr, keys, st, order);
   pe_event_after("splat_kernel", s);
   PE_TRY_LAUNCH("splat_kernel");
   if (two) {
@@ -319,7 +324,7 @@ pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float
     PE_TRY_LAUNCH("tile_max_kernel");
     pe_event_before("splat_kernel", s);
     splat_kernel<<<grid, kSplatThreads, 0, s>>>(vb, pos, nrm, rad, n, mode, delta, 2, hz, keys,
-                                                 st);
+                                                 st, order);
     pe_event_after("splat_kernel", s);
     PE_TRY_LAUNCH("splat_kernel");
   }

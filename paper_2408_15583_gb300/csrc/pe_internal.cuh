@@ -125,10 +125,13 @@ void pe_layout_offsets(const pe_geom_layout &L, size_t *off_cr, size_t *off_nf,
 // that skips back-facing disks hidden behind the first pass's keys; hz =
 // null: one pass.
 size_t pe_splat_tiles(int32_t n_views, int32_t W, int32_t H);
-// stats (nullable): [5] += exact pixel tests, [6] += key updates.
+// stats (nullable): [5] += exact pixel tests, [6] += key updates.  order
+// (nullable): the processing order of the points (a permutation of 0..n-1);
+// the keys do not depend on it.
 pe_status pe_launch_splat(const pe_view_batch &vb, const float *pos, const float *nrm,
                           const float *rad, int64_t n, int mode, float delta, float *hz,
-                          unsigned long long *keys, int64_t *stats, cudaStream_t s);
+                          unsigned long long *keys, int64_t *stats, cudaStream_t s,
+                          const uint32_t *order = nullptr);
 
 // implicit1 (bounce 1 from the GFB keys, mb >= 2): no bounce-1 records are
 // written; the bounce-2 pass takes each ray's bounce-1 record from its key

@@ -300,6 +300,64 @@ pt_ws carve(pe_carve &c, int64_t n) {
 
 }  // namespace
 
+namespace {
+
+// The processing order of pe_order_points: the same counting sort into a
+// 32^3 grid over the bounding box, cells in raster order (a warp's 32 points
+// then mostly share a cell of about 1/32 of the target's extent).
+constexpr int kOrderGrid = 32;
+
+pt_ws carve_order(pe_carve &c, int64_t n) {
+  const int64_t cells = (int64_t)kOrderGrid * kOrderGrid * kOrderGrid;
+  pt_ws w;
+  w.part = c.take<float>(kBoxBlocks * 6);
+  w.gi = c.take<grid_info>(1);
+  w.count = c.take<uint32_t>((size_t)cells);
+  w.offs = c.take<uint32_t>((size_t)cells + 1);
+  w.cursor = c.take<uint32_t>((size_t)cells);
+  w.tile = c.take<uint32_t>((size_t)((cells + 4095) / 4096 + 1));
+  w.cell_of = c.take<uint32_t>((size_t)n);
+  w.sorted = nullptr;  // the caller's order buffer
+  return w;
+}
+
+}  // namespace
+
+extern "C" size_t pe_order_points_workspace(int64_t n_points) {
+  if (n_points < 1 || n_points >= (int64_t)UINT32_MAX) return 0;
+  pe_carve c{nullptr, 0};
+  carve_order(c, n_points);
+  return c.bytes() + 256;
+}
+
+extern "C" pe_status pe_order_points(const float *pos, int64_t n_points, void *ws, size_t ws_bytes,
+                                     uint32_t *order, void *stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!pos || !order || n_points < 1 || n_points >= (int64_t)UINT32_MAX)
+    return pe_fail(PE_EINVAL, "pe_order_points: bad arguments");
+  const size_t need = pe_order_points_workspace(n_points);
+  if (!ws || ws_bytes < need || !pe_aligned(ws, 256))
+    return pe_fail(PE_ENOMEM, "pe_order_points: workspace needs %zu bytes", need);
+  pe_carve c{static_cast<char *>(ws), 0};
+  pt_ws w = carve_order(c, n_points);
+  const int64_t cells = (int64_t)kOrderGrid * kOrderGrid * kOrderGrid;
+  bbox_partial<<<kBoxBlocks, kPtThreads, 0, s>>>(pos, n_points, w.part);
+  PE_TRY_LAUNCH("bbox_partial");
+  bbox_final<<<1, 32, 0, s>>>(w.part, kBoxBlocks, kOrderGrid, w.gi);
+  PE_TRY_LAUNCH("bbox_final");
+  PE_TRY_CUDA(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * cells, s));
+  PE_TRY_CUDA(cudaMemsetAsync(w.cursor, 0, sizeof(uint32_t) * cells, s));
+  int64_t b = (n_points + 255) / 256;
+  const int blocks = (int)(b < 4096 ? b : 4096);
+  count_cells<<<blocks, 256, 0, s>>>(pos, n_points, w.gi, w.count, w.cell_of);
+  PE_TRY_LAUNCH("count_cells");
+  pe_status st = pe_exclusive_scan_u32(w.count, cells, w.tile, w.offs, s);
+  if (st != PE_OK) return st;
+  scatter_cells<<<blocks, 256, 0, s>>>(n_points, w.cell_of, w.offs, w.cursor, order);
+  PE_TRY_LAUNCH("scatter_cells");
+  return PE_OK;
+}
+
 extern "C" size_t pe_point_attributes_workspace(int64_t n_points) {
   if (n_points < 1) return 0;
   pe_carve c{nullptr, 0};

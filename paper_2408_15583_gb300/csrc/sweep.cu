@@ -198,7 +198,8 @@ extern "C" pe_status pe_rcs_sweep(const pe_sweep *sw, const float *pos, const fl
     h.n_rays = per * nb;
     if (!prm->first_bounce_from_geom) {
       PE_TRY_CUDA(cudaMemsetAsync(W.keys, 0xff, sizeof(unsigned long long) * per * nb, s));
-      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, W.hz, W.keys, stats, s);
+      pe_status st = pe_launch_splat(vb, pos, nrm, rad, n_points, 0, 0.0f, W.hz, W.keys, stats, s,
+                                     sw->point_order);
       if (st != PE_OK) return st;
     }
     // bounce-1 records stay implicit in the incidence GFB (bounce 1 from the

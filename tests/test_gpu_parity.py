@@ -497,6 +497,32 @@ def test_rcs_sweep_two_lanes_equal_trace_and_field_per_batch(case, request):
     api.stream_check()
 
 
+@pytest.mark.parametrize("case", GEOMS)
+def test_rcs_sweep_point_order_changes_nothing(case, request):
+    # pe_order_points gives a permutation; the incidence splat taking the
+    # points in that order gives the same field and the same splat counters
+    api, pipe = _mods()
+    d = request.getfixturevalue(case)
+    sc = d["sc"]
+    th = [90.0] * 5 + [70.0] if case == "small_geom" else [60.0] * 5 + [54.7356]
+    sw = scenes._sweep_over(sc, th, [0.0, 13.0, 45.0, 62.0, 90.0, 30.0], 48,
+                            scenes.freq_grid(2.6e9, 3.4e9, 9), 2 if case == "small_geom" else 3)
+    order = api.order_points(d["pos"])
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(sc.n))
+    runs = []
+    for with_order in (False, True):
+        args = api.SweepArgs.from_sweep(sw, angle_batch=2)
+        if with_order:
+            args.set_point_order(order)
+        st = torch.zeros(8, dtype=torch.int64, device=DEV)
+        E, sig = api.rcs_sweep(args, d["pos"], d["nrm"], d["rad"], d["geom"], d["prm"], stats=st)
+        api.stream_check()
+        runs.append((E, sig, st.cpu().numpy()))
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+    assert np.array_equal(runs[0][2], runs[1][2])
+
+
 def test_rcs_sweep_vs_fp64_physics_oracle(small_geom):
     # The FP64 oracle traces in double precision: a handful of grazing rays
     # can fall on the other side of a disk edge, so the bar is sigma within
