@@ -65,6 +65,7 @@ def main(argv):
                               centre=sw.centre, extent=sw.extent,
                               freqs_hz=np.asarray(sw.freqs_hz, np.float64), max_bounces=mb,
                               angle_batch=nb)
+        sargs.set_point_order(api.order_points(pos))   # as the bench's step does
         sws = api.workspace(sargs.workspace_bytes(), dev)
         sE = torch.empty((nb, len(sw.freqs_hz), 2, 3, 2), dtype=torch.float64, device=dev)
         sS = torch.empty((nb, len(sw.freqs_hz), 2, 2), dtype=torch.float64, device=dev)
