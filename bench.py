@@ -358,24 +358,24 @@ MARCH_BYTES_PER_HIT = 76
 # DRAM bytes (read + write) per bounce query of march_kernel from one ncu
 # capture of the sweep's march on a smaller case (one 8-angle batch of the
 # sphere workload through pe_rcs_sweep; profiles/march_kernel_sphere_batch.md:
-# 90.6 MB over 6,332,964 queries), valid only for the sources it was taken on
+# 91.1 MB over 6,332,964 queries), valid only for the sources it was taken on
 # (their SHA-256 prefixes); scaled to a full launch by the number of queries.
-_SWEEP_SOURCES = {"include/pointemray.h": "6d692fe01ba1e08a",
-                  "paper_2408_15583_gb300/csrc/pe_internal.cuh": "845aae3e105fbb3d",
-                  "paper_2408_15583_gb300/csrc/sweep.cu": "7e9b009c70868a41"}
-MARCH_NCU_TRAFFIC = {"bytes_per_query": 14.30,
+_SWEEP_SOURCES = {"include/pointemray.h": "f6d55b40007929cd",
+                  "paper_2408_15583_gb300/csrc/pe_internal.cuh": "2dc3ec4e588ae1ce",
+                  "paper_2408_15583_gb300/csrc/sweep.cu": "9f2bcf7b228eaa30"}
+MARCH_NCU_TRAFFIC = {"bytes_per_query": 14.39,
                      "sources": dict(_SWEEP_SOURCES, **{
                          "paper_2408_15583_gb300/csrc/trace.cu": "9a00f34e95823c9b",
                          "paper_2408_15583_gb300/csrc/aggregate.cu": "55364132016cd83f"})}
 
 # DRAM bytes (read + write) per ray slot of po_rot_kernel from one ncu capture
 # of the sweep's field sum on one 8-angle sphere batch
-# (profiles/po_kernel_sphere_batch.md: 98.5 MB over 8 x 1024^2 slots), valid
+# (profiles/po_kernel_sphere_batch.md: 98.2 MB over 8 x 1024^2 slots), valid
 # for the sources it was taken on; scaled to a full launch by its slots
 # (angles x W x H).
-PO_NCU_TRAFFIC = {"bytes_per_slot": 11.74,
+PO_NCU_TRAFFIC = {"bytes_per_slot": 11.71,
                   "sources": dict(_SWEEP_SOURCES, **{
-                      "paper_2408_15583_gb300/csrc/po.cu": "7d73a192beef1136"})}
+                      "paper_2408_15583_gb300/csrc/po.cu": "bf0ccca2dfa5ef5a"})}
 
 
 def _traffic_valid(rec):

@@ -200,8 +200,8 @@ size_t pe_point_attributes_workspace(int64_t n_points);
 
 /* A spatially coherent processing order of the points (no counterpart in the
  * paper): order_dev[0..n) = a permutation of 0..n-1 grouping the points by
- * the Morton cell of a 32^3 grid over their bounding box (cells in Morton
- * order; the order within a cell is unspecified).  Neighbouring points then
+ * their cell of a 32^3 grid over their bounding box (cells in raster order,
+ * x slowest and z fastest; the order within a cell is unspecified).  Neighbouring points then
  * project to footprints of similar size, so the lanes of a splat warp stay
  * busy together (pe_sweep.point_order).  ws of pe_order_points_workspace(n)
  * bytes (256-byte aligned); 1 <= n < 2^32; positions are clamped into the
@@ -387,6 +387,9 @@ size_t pe_po_workspace(int32_t n_groups, int64_t rays_per_group, int32_t n_freq)
  * (pol, xyz, re/im), device.  Per-term arithmetic is float32 with the phase
  * argument in double-float and reduced modulo 2 pi; sums are compensated in
  * float32 per thread and reduced in float64 in a fixed order (deterministic).
+ * A bounce-1 record (M = 1) seen in backscatter (ks = -k exactly) has
+ * d - ks . p = 2 k . p; that is formed from its k and p as a float pair, and
+ * its path field is not read.
  * RCS: sigma = k^2/pi |e_rx . Sigma|^2. */
 pe_status pe_po_field(const pe_hits *hits, int32_t n_groups, int64_t rays_per_group,
                       const float *ks, const double *freqs_hz, int32_t n_freq,

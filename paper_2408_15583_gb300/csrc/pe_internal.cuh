@@ -229,12 +229,12 @@ __device__ __forceinline__ double pe_path_start(pe_f3 d, pe_f3 p) {
 // point's normal turned against the ray, incoming direction d, tube vectors
 // pitch u and pitch v, path d . p.  The one definition of those values:
 // written by the primary pass, or recomputed from the key where the records
-// are implicit, bit for bit the same.
-__device__ __forceinline__ void pe_primary_record(const pe_view &V, int i, int j,
-                                                  unsigned long long key,
-                                                  const float *__restrict__ nrm, pe_f3 &p,
-                                                  pe_f3 &n, pe_f3 &k, pe_f3 &u, pe_f3 &v,
-                                                  double &path) {
+// are implicit, bit for bit the same.  pe_primary_geom: the record without
+// its path.
+__device__ __forceinline__ void pe_primary_geom(const pe_view &V, int i, int j,
+                                                unsigned long long key,
+                                                const float *__restrict__ nrm, pe_f3 &p,
+                                                pe_f3 &n, pe_f3 &k, pe_f3 &u, pe_f3 &v) {
   const pe_f3 o = pe_pixel_origin(V, i, j);
   k = pe_v3(V.d);
   const uint32_t id = (uint32_t)(key & 0xffffffffull);
@@ -244,6 +244,13 @@ __device__ __forceinline__ void pe_primary_record(const pe_view &V, int i, int j
   if (pe_dot(n, k) > 0.0f) n = pe_neg3(n);
   u = {pe_mul(V.pitch, V.u[0]), pe_mul(V.pitch, V.u[1]), pe_mul(V.pitch, V.u[2])};
   v = {pe_mul(V.pitch, V.v[0]), pe_mul(V.pitch, V.v[1]), pe_mul(V.pitch, V.v[2])};
+}
+__device__ __forceinline__ void pe_primary_record(const pe_view &V, int i, int j,
+                                                  unsigned long long key,
+                                                  const float *__restrict__ nrm, pe_f3 &p,
+                                                  pe_f3 &n, pe_f3 &k, pe_f3 &u, pe_f3 &v,
+                                                  double &path) {
+  pe_primary_geom(V, i, j, key, nrm, p, n, k, u, v);
   path = pe_path_start(k, p);
 }
 

@@ -87,6 +87,31 @@ __device__ __forceinline__ pe_f3 cross(pe_f3 a, pe_f3 b) {
 }
 __device__ __forceinline__ float dotf(pe_f3 a, pe_f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// 2 (a . b) as an unevaluated float pair hi + lo (|lo| <= ulp(hi) / 2) in
+// FP32 operations alone: each product split exactly by an FMA (TwoProduct),
+// the three products added by Knuth's TwoSum with their low parts gathered;
+// the error stays below 2^-44 of the largest product (a phase error below
+// 1e-10 revolutions at 18 GHz 30 m from the origin).  (FP64 issues at 1/64 of
+// the FP32 rate on sm_103a, and the FP64 form of this dot product, with its
+// conversions, cost the field sum as much as a third of its time.)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+__device__ __forceinline__ void twice_dot_pair(pe_f3 a, pe_f3 b, float &hi, float &lo) {
+  const float p0 = __fmul_rn(a.x, b.x), p1 = __fmul_rn(a.y, b.y), p2 = __fmul_rn(a.z, b.z);
+  const float e0 = __fmaf_rn(a.x, b.x, -p0), e1 = __fmaf_rn(a.y, b.y, -p1),
+              e2 = __fmaf_rn(a.z, b.z, -p2);
+  float s, t0, t1;
+  two_sum(p0, p1, s, t0);
+  two_sum(s, p2, s, t1);
+  const float l = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), e2), __fadd_rn(t0, t1));
+  two_sum(s, l, hi, lo);
+  hi = __fmul_rn(2.0f, hi);
+  lo = __fmul_rn(2.0f, lo);
+}
+
 // The frequency-independent factors of ray `slot` (Eq. 12-14): the sinc
 // arguments per unit wavenumber (au, av), the phase path d - ks.p as a float
 // pair (dh, dl) and the area-weighted vector factors of both polarisations in
@@ -100,12 +125,12 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f
   const int32_t M = h.M[slot];
   if (!(M >= 1 && h.psi[slot] != 0)) return false;
   pe_f3 kk, n, u, v, p;
-  double path;
-  bool twice = false;  // d - ks . p = 2 path (below)
-  if (M == 1 && C.keys1) {
+  const bool implicit = M == 1 && C.keys1;
+  bool twice;  // backscatter from a bounce-1 record (below)
+  if (implicit) {
     const pe_view &W = C.view1[g];
     const int j = (int)(r / W.W), i = (int)(r - (int64_t)j * W.W);
-    pe_primary_record(W, i, j, C.keys1[slot], C.nrm1, p, n, kk, u, v, path);
+    pe_primary_geom(W, i, j, C.keys1[slot], C.nrm1, p, n, kk, u, v);
     twice = C.mono1[g] != 0;
   } else {
     kk = {h.k[3 * slot], h.k[3 * slot + 1], h.k[3 * slot + 2]};
@@ -113,7 +138,7 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f
     u = {h.u[3 * slot], h.u[3 * slot + 1], h.u[3 * slot + 2]};
     v = {h.v[3 * slot], h.v[3 * slot + 1], h.v[3 * slot + 2]};
     p = {h.p[3 * slot], h.p[3 * slot + 1], h.p[3 * slot + 2]};
-    path = h.path[slot];
+    twice = M == 1 && ks.x == -kk.x && ks.y == -kk.y && ks.z == -kk.z;
   }
   // (the field is summed to a relative tolerance, so the per-ray factors use
   // the fast reciprocal and reciprocal square root: a few ulp each)
@@ -138,19 +163,20 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f
   V[1] = area * dotf(a, e2);
   V[2] = area * dotf(c, e1);
   V[3] = area * dotf(c, e2);
-  // Backscatter from a bounce-1 record (ks = -d exactly): every product of
-  // two floats is exact in FP64 and rounding to nearest is odd-symmetric, so
-  // ks . p = -path bit for bit and the difference is exactly 2 path.
-  double delta;
+  // Backscatter from a bounce-1 record (ks = -k exactly): the path of such a
+  // record is k . p by its definition, so d - ks . p = 2 k . p, taken from
+  // the record's k and p as a float pair whether the record is implicit or
+  // written (the two give the same bits).  Every other record: its FP64 path.
   if (twice) {
-    delta = 2.0 * path;
+    twice_dot_pair(kk, p, dh, dl);
   } else {
+    const double path = implicit ? pe_path_start(kk, p) : h.path[slot];
     const double ksp =
         (double)ks.x * (double)p.x + (double)ks.y * (double)p.y + (double)ks.z * (double)p.z;
-    delta = path - ksp;
+    const double delta = path - ksp;
+    dh = (float)delta;
+    dl = (float)(delta - (double)dh);
   }
-  dh = (float)delta;
-  dl = (float)(delta - (double)dh);
   return true;
 }
 
@@ -699,6 +725,10 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
       C.rpg = rpg;
       C.g0 = g0;
       C.stats = reinterpret_cast<long long *>(stats);
+      for (int g = 0; g < ng; ++g) {
+        for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];
+        transverse_basis(C.ks[g], C.e1[g], C.e2[g]);
+      }
       if (gfb1) {
         C.keys1 = gfb1->keys;
         C.nrm1 = gfb1->nrm;
@@ -710,10 +740,6 @@ pe_status pe_launch_po(const pe_hits &h, int32_t n_groups, int64_t rpg, const fl
         }
       }
       C.rl_shift = __builtin_ctz((unsigned)(kPoThreads / C.fl));
-      for (int g = 0; g < ng; ++g) {
-        for (int k = 0; k < 3; ++k) C.ks[g][k] = ks[3 * (g0 + g) + k];
-        transverse_basis(C.ks[g], C.e1[g], C.e2[g]);
-      }
       double kmax = 0.0;
       for (int f = 0; f < nf; ++f) {
         const double kd = two_pi * freqs[fb + f] / c0;
