@@ -375,7 +375,7 @@ MARCH_NCU_TRAFFIC = {"bytes_per_query": 14.39,
 # (angles x W x H).
 PO_NCU_TRAFFIC = {"bytes_per_slot": 11.71,
                   "sources": dict(_SWEEP_SOURCES, **{
-                      "paper_2408_15583_gb300/csrc/po.cu": "bf0ccca2dfa5ef5a"})}
+                      "paper_2408_15583_gb300/csrc/po.cu": "74b9c0ab14b42f12"})}
 
 
 def _traffic_valid(rec):

@@ -347,11 +347,15 @@ __global__ void __launch_bounds__(kPoThreads, 4)
 // with the ray's rotation e^{-j dk d} staged once per ray (re-anchored at
 // every thread's first frequency, so the float32 rotation drifts over at most
 // kFt - 1 steps).  The two sinc factors are one power series in t = k^2:
-// sinc(k a) sinc(k b) = sum_n c_n t^n, whose five coefficients through t^4
-// (x^8 in each factor, truncation below 3e-11 for |k a|, |k b| < 0.5) are
-// staged per ray; a ray with a larger argument anywhere in the launch takes
-// the direct form instead.  Per term: four multiply-adds of the series, four
-// of the rotation, two for the complex amplitude and eight for the sums.
+// sinc(k a) sinc(k b) = sum_n c_n t^n, whose coefficients through t^6 are
+// staged per ray.  With |k a|, |k b| <= 1 the tail n >= 7 stays below
+// sum_{n>=7} 2^(2n+1) / (2n+2)! < 1.6e-9 (the sum over i + j = n of
+// 1 / ((2i+1)! (2j+1)!) is 2^(2n+1) / (2n+2)!); a ray with a larger argument
+// anywhere in the launch takes the direct form instead.  (Through t^4 the
+// range would be |k a|, |k b| < 0.5, which leaves about half of a sphere's
+// rays, those beyond 45 degrees incidence, to the direct form at a 2 mm
+// pitch and 12 GHz.)  Per term: six multiply-adds of the series, four of the
+// rotation, two for the complex amplitude and eight for the sums.
 // ---------------------------------------------------------------------------
 #ifndef PE_PO_FT
 #define PE_PO_FT 2   // frequencies per thread of the rotation kernel
@@ -371,16 +375,29 @@ __global__ void __launch_bounds__(kPoThreads, 4)
 constexpr int kFt = PE_PO_FT;
 constexpr int kJu = PE_PO_JU;
 
-__device__ __forceinline__ void series_coeffs(float au, float av, float c[4]) {
-  // sinc x = 1 - x^2/6 + x^4/120 - x^6/5040 + x^8/362880; with A = au^2,
-  // B = av^2 the product's coefficients of t^1..t^4 (t^0: 1)
+constexpr int kSer = 6;        // series coefficients beyond the constant 1
+constexpr float kSerRange = 1.0f;  // largest |k a|, |k b| of a series ray
+
+__device__ __forceinline__ void series_coeffs(float au, float av, float c[kSer]) {
+  // sinc x = sum_i (-1)^i x^(2i) / (2i+1)!.  With a_i = A^i / (2i+1)!,
+  // b_j = B^j / (2j+1)! (A = au^2, B = av^2; a_i = a_(i-1) A / (2i (2i+1)))
+  // the product's coefficient of t^n is (-1)^n sum_{i+j=n} a_i b_j.
   const float A = au * au, B = av * av;
-  const float A2 = A * A, B2 = B * B, AB = A * B;
-  c[0] = -(A + B) * (1.0f / 6.0f);
-  c[1] = (A2 + B2) * (1.0f / 120.0f) + AB * (1.0f / 36.0f);
-  c[2] = -(A2 * A + B2 * B) * (1.0f / 5040.0f) - AB * (A + B) * (1.0f / 720.0f);
-  c[3] = (A2 * A2 + B2 * B2) * (1.0f / 362880.0f) + AB * (A2 + B2) * (1.0f / 30240.0f) +
-         AB * AB * (1.0f / 14400.0f);
+  float a[kSer + 1], b[kSer + 1];
+  a[0] = b[0] = 1.0f;
+#pragma unroll
+  for (int i = 1; i <= kSer; ++i) {
+    const float r = 1.0f / (float)((2 * i) * (2 * i + 1));
+    a[i] = a[i - 1] * A * r;
+    b[i] = b[i - 1] * B * r;
+  }
+#pragma unroll
+  for (int n = 1; n <= kSer; ++n) {
+    float x = 0.0f;
+#pragma unroll
+    for (int i = 0; i <= n; ++i) x = fmaf(a[i], b[n - i], x);
+    c[n - 1] = (n & 1) ? -x : x;
+  }
 }
 
 // One term: the complex amplitude sc e^{-j phase} (pr, pi) into the eight
@@ -416,8 +433,8 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
   // [2][FT * kAcc][kPoThreads] floats, instead of registers
   extern __shared__ float s_hl[];
   // per staged ray: the series {c1..c4}, the area-weighted vector factors
-  // {Va.e1, Va.e2, Vc.e1, Vc.e2}, {dh, dl, rotation re, im}, and the sinc
-  // arguments for the direct form (au, av)
+  // {Va.e1, Va.e2, Vc.e1, Vc.e2}, {dh, dl, rotation re, im}, and {c5, c6}
+  // for a series ray or the sinc arguments (au, av) for the direct form
   __shared__ float4 s_ray[3][kPoThreads];
   __shared__ float2 s_arg[kPoThreads];
   __shared__ int s_warp[2 * (kPoThreads / 32)];
@@ -441,9 +458,12 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
   for (int c0 = 0; c0 < n_fc; c0 += FL) {
     const int f1 = (c0 + lane_f) * FT;  // this thread's first frequency
     const bool f_ok = f1 < C.nf;
-    float t2[FT];
+    float t2[FT], kq[FT];
 #pragma unroll
-    for (int q = 0; q < FT; ++q) t2[q] = f1 + q < C.nf ? C.k2[f1 + q] : 0.0f;
+    for (int q = 0; q < FT; ++q) {
+      t2[q] = f1 + q < C.nf ? C.k2[f1 + q] : 0.0f;
+      kq[q] = C.k[min(f1 + q, C.nf - 1)];
+    }
     const float khi = f_ok ? C.khi[f1] : 0.0f, klo = f_ok ? C.klo[f1] : 0.0f;
     constexpr int NA = FT * kAcc;
     float hi[SMC ? 1 : NA], lo[SMC ? 1 : NA], b[NA];
@@ -466,7 +486,7 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
           r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V, C, g, r);
       // two stable compactions: rays whose sinc arguments stay in the series'
       // range for every frequency of the launch first, the others after them
-      const bool ser = valid && fmaxf(fabsf(au), fabsf(av)) * C.kmax < 0.5f;
+      const bool ser = valid && fmaxf(fabsf(au), fabsf(av)) * C.kmax <= kSerRange;
       const unsigned ma = __ballot_sync(0xffffffffu, ser);
       const unsigned mb = __ballot_sync(0xffffffffu, valid && !ser);
       int wid = tid >> 5, lane = tid & 31;
@@ -489,14 +509,14 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
       if (valid) {
         const unsigned below = (1u << lane) - 1u;
         const int at = ser ? before_a + __popc(ma & below) : n_a + before_b + __popc(mb & below);
-        float c[4];
+        float c[kSer];
         series_coeffs(au, av, c);
         float rs, rc;
         __sincosf(rev_phase(C.dkhi, C.dklo, dh, dl) * kTwoPi, &rs, &rc);
         s_ray[0][at] = make_float4(c[0], c[1], c[2], c[3]);
         s_ray[1][at] = make_float4(V[0], V[1], V[2], V[3]);
         s_ray[2][at] = make_float4(dh, dl, rc, -rs);
-        s_arg[at] = make_float2(au, av);
+        s_arg[at] = ser ? make_float2(c[4], c[5]) : make_float2(au, av);
       }
       __syncthreads();
       // ---- FT frequencies per thread over the staged rays ---------------
@@ -509,13 +529,17 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
 #pragma unroll kJu
               for (int j = j0; j < jn; j += RL) {
                 const float4 r0 = s_ray[0][j], r1 = s_ray[1][j], r2 = s_ray[2][j];
+                const float2 c56 = s_arg[j];
                 float sn, cs;
                 __sincosf(rev_phase(khi, klo, r2.x, r2.y) * kTwoPi, &sn, &cs);
                 float pr = cs, pi = -sn;  // e^{-j phase} at frequency f1
 #pragma unroll
                 for (int q = 0; q < FT; ++q) {
                   const float t = t2[q];
-                  const float sc = fmaf(fmaf(fmaf(fmaf(r0.w, t, r0.z), t, r0.y), t, r0.x), t, 1.0f);
+                  const float sc = fmaf(
+                      fmaf(fmaf(fmaf(fmaf(fmaf(c56.y, t, c56.x), t, r0.w), t, r0.z), t, r0.y), t,
+                           r0.x),
+                      t, 1.0f);
                   rot_term(sc, r1, r2, pr, pi, b + q * kAcc);
                 }
               }
@@ -528,8 +552,7 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
                 float pr = cs, pi = -sn;
 #pragma unroll
                 for (int q = 0; q < FT; ++q) {
-                  const float kq = C.k[min(f1 + q, C.nf - 1)];
-                  const float sc = sincf_(kq * arg.x) * sincf_(kq * arg.y);
+                  const float sc = sincf_(kq[q] * arg.x) * sincf_(kq[q] * arg.y);
                   rot_term(sc, r1, r2, pr, pi, b + q * kAcc);
                 }
               }

@@ -270,16 +270,26 @@ def _hits_from_trace(api, tr):
     return h
 
 
-def test_po_field_synthetic_plate_many_freqs():
+@pytest.mark.parametrize("th_deg,nu,ka_range", [
+    (25.0, 60, (0.35, 0.55)),    # the sinc series, below the former 0.5 bound
+    (50.0, 60, (0.6, 1.0)),      # the series up to its |k a| <= 1 bound
+    (60.0, 30, (1.4, 2.3)),      # the direct form
+])
+def test_po_field_synthetic_plate_many_freqs(th_deg, nu, ka_range):
     # synthetic (oracle-free) inputs: a plate tiled by projected screen cells
-    # at oblique incidence; 64 frequencies 8-12 GHz.
+    # at oblique incidence; 64 frequencies 8-12 GHz.  In backscatter a cell's
+    # sinc argument is k (a / nu) sin(theta) along u and 0 along v; the cases
+    # put the band's arguments in the two classes of the rotation kernel.
     api, _ = _mods()
-    th = math.radians(25.0)
+    th = math.radians(th_deg)
     w = np.array([math.sin(th), 0, math.cos(th)])
     u = np.array([math.cos(th), 0, -math.sin(th)])
     v = np.array([0, 1.0, 0])
     d = -w
-    a, b, nu, nv = 0.3, 0.2, 60, 40
+    a, b, nv = 0.3, 0.2, 40
+    k_lo, k_hi = 2 * math.pi * 8e9 / 299792458.0, 2 * math.pi * 12e9 / 299792458.0
+    ka = a / nu * math.sin(th)
+    assert ka_range[0] <= k_lo * ka and k_hi * ka <= ka_range[1]
     us = (a / nu * math.cos(th)) * u
     vs = (b / nv) * v
     up = us - d * (us[2] / d[2])
