@@ -23,7 +23,10 @@ namespace {
 constexpr int kPoThreads = 256;
 constexpr int kPoGroups = 64;    // groups (angles) per launch
 constexpr int kPoFreqs = 256;    // frequencies per launch
-constexpr int kFlush = 32;       // terms between TwoSum flushes
+#ifndef PE_PO_FLUSH
+#define PE_PO_FLUSH 64
+#endif
+constexpr int kFlush = PE_PO_FLUSH;  // terms between TwoSum flushes
 constexpr int kAcc = 8;          // sums per (ray, frequency): 2 pol x (e1, e2) x (re, im)
 constexpr float kTwoPi = 6.28318530717958647692f;
 
@@ -112,25 +115,42 @@ __device__ __forceinline__ void twice_dot_pair(pe_f3 a, pe_f3 b, float &hi, floa
   lo = __fmul_rn(2.0f, lo);
 }
 
+// The words of slot `slot` that decide its record: bounce count, Psi and,
+// where bounce-1 records are implicit, its GFB key (loaded whatever M is, so
+// the three loads are independent).
+struct ray_words {
+  int32_t M;
+  uint32_t psi;
+  unsigned long long key;
+};
+__device__ __forceinline__ ray_words load_words(const pe_hits &h, const po_consts &C,
+                                                int64_t slot) {
+  ray_words w;
+  w.M = h.M[slot];
+  w.psi = h.psi[slot];
+  w.key = C.keys1 ? __ldg(C.keys1 + slot) : 0ull;
+  return w;
+}
+
 // The frequency-independent factors of ray `slot` (Eq. 12-14): the sinc
 // arguments per unit wavenumber (au, av), the phase path d - ks.p as a float
 // pair (dh, dl) and the area-weighted vector factors of both polarisations in
 // the basis (e1, e2).  False for a ray without a contribution (a miss,
 // Psi = 0, or a tube edge-on to the surface).
 // (r: the slot's index within its group g of the launch.)
-__device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f3 ks, pe_f3 e1,
-                                            pe_f3 e2, float &au, float &av, float &dh,
-                                            float &dl, float V[4], const po_consts &C, int g,
-                                            int64_t r) {
-  const int32_t M = h.M[slot];
-  if (!(M >= 1 && h.psi[slot] != 0)) return false;
+__device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, const ray_words &w,
+                                            pe_f3 ks, pe_f3 e1, pe_f3 e2, float &au, float &av,
+                                            float &dh, float &dl, float V[4], const po_consts &C,
+                                            int g, int64_t r) {
+  const int32_t M = w.M;
+  if (!(M >= 1 && w.psi != 0)) return false;
   pe_f3 kk, n, u, v, p;
   const bool implicit = M == 1 && C.keys1;
   bool twice;  // backscatter from a bounce-1 record (below)
   if (implicit) {
     const pe_view &W = C.view1[g];
     const int j = (int)(r / W.W), i = (int)(r - (int64_t)j * W.W);
-    pe_primary_geom(W, i, j, C.keys1[slot], C.nrm1, p, n, kk, u, v);
+    pe_primary_geom(W, i, j, w.key, C.nrm1, p, n, kk, u, v);
     twice = C.mono1[g] != 0;
   } else {
     kk = {h.k[3 * slot], h.k[3 * slot + 1], h.k[3 * slot + 2]};
@@ -155,14 +175,16 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, pe_f
   au = 0.5f * dotf(q, up);
   av = 0.5f * dotf(q, vp);
   const float ilu = rsqrtf(dotf(u, u)), ilv = rsqrtf(dotf(v, v));
-  pe_f3 hv = {-v.x * ilv, -v.y * ilv, -v.z * ilv};
-  pe_f3 hh = {u.x * ilu, u.y * ilu, u.z * ilu};
-  pe_f3 a = cross(cross(cross(n, hv), ks), ks);
-  pe_f3 c = cross(cross(cross(n, hh), ks), ks);
-  V[0] = area * dotf(a, e1);
-  V[1] = area * dotf(a, e2);
-  V[2] = area * dotf(c, e1);
-  V[3] = area * dotf(c, e2);
+  // [(n x h) x ks] x ks in the basis (e1, e2): for unit ks,
+  // (m x ks) x ks = ks (m . ks) - m, and e1, e2 lie across ks, so its
+  // coordinates are -m . e = -h . (e x n) with m = n x h (h = -v/|v| for V,
+  // u/|u| for H): two cross products per ray instead of six.
+  const pe_f3 g1 = cross(e1, n), g2 = cross(e2, n);
+  const float sv_ = area * ilv, su_ = -area * ilu;
+  V[0] = sv_ * dotf(v, g1);
+  V[1] = sv_ * dotf(v, g2);
+  V[2] = su_ * dotf(u, g1);
+  V[3] = su_ * dotf(u, g2);
   // Backscatter from a bounce-1 record (ks = -k exactly): the path of such a
   // record is k . p by its definition, so d - ks . p = 2 k . p, taken from
   // the record's k and p as a float pair whether the record is implicit or
@@ -253,7 +275,9 @@ __global__ void __launch_bounds__(kPoThreads, 4)
       // one frequency: each thread takes its own rays, nothing to share
       for (int64_t r = r_begin + tid; r < r_end; r += kPoThreads) {
         float au, av, dh, dl, V[4];
-        if (!ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V, C, g, r)) continue;
+        if (!ray_factors(h, slot0 + r, load_words(h, C, slot0 + r), ks, e1, e2, au, av, dh, dl, V,
+                         C, g, r))
+          continue;
         n_rays += f0 == 0;
         add_term(kf, khi, klo, au, av, dh, dl, V, b);
         if (++pending == kFlush) {
@@ -270,8 +294,8 @@ __global__ void __launch_bounds__(kPoThreads, 4)
         // ---- stage the frequency-independent per-ray factors --------------
         const int64_t r = sb + tid;
         float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
-        const bool valid =
-            r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V, C, g, r);
+        const bool valid = r < r_end && ray_factors(h, slot0 + r, load_words(h, C, slot0 + r), ks,
+                                                    e1, e2, au, av, dh, dl, V, C, g, r);
         // stable compaction of the valid rays (order = slot order)
         unsigned m = __ballot_sync(0xffffffffu, valid);
         int wid = tid >> 5, lane = tid & 31;
@@ -482,8 +506,8 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
       // ---- stage the frequency-independent per-ray factors ----------------
       const int64_t r = sb + tid;
       float au = 0, av = 0, dh = 0, dl = 0, V[4] = {0, 0, 0, 0};
-      const bool valid =
-          r < r_end && ray_factors(h, slot0 + r, ks, e1, e2, au, av, dh, dl, V, C, g, r);
+      const bool valid = r < r_end && ray_factors(h, slot0 + r, load_words(h, C, slot0 + r), ks,
+                                                  e1, e2, au, av, dh, dl, V, C, g, r);
       // two stable compactions: rays whose sinc arguments stay in the series'
       // range for every frequency of the launch first, the others after them
       const bool ser = valid && fmaxf(fabsf(au), fabsf(av)) * C.kmax <= kSerRange;
