@@ -370,12 +370,12 @@ MARCH_NCU_TRAFFIC = {"bytes_per_query": 14.39,
 
 # DRAM bytes (read + write) per ray slot of po_rot_kernel from one ncu capture
 # of the sweep's field sum on one 8-angle sphere batch
-# (profiles/po_kernel_sphere_batch.md: 116.1 MB over 8 x 1024^2 slots), valid
+# (profiles/po_kernel_sphere_batch.md: 115.9 MB over 8 x 1024^2 slots), valid
 # for the sources it was taken on; scaled to a full launch by its slots
 # (angles x W x H).
-PO_NCU_TRAFFIC = {"bytes_per_slot": 13.84,
+PO_NCU_TRAFFIC = {"bytes_per_slot": 13.81,
                   "sources": dict(_SWEEP_SOURCES, **{
-                      "paper_2408_15583_gb300/csrc/po.cu": "8aa638a2f0c8fafb"})}
+                      "paper_2408_15583_gb300/csrc/po.cu": "f9b1d7b1945d56c4"})}
 
 
 def _traffic_valid(rec):

@@ -482,11 +482,12 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
   for (int c0 = 0; c0 < n_fc; c0 += FL) {
     const int f1 = (c0 + lane_f) * FT;  // this thread's first frequency
     const bool f_ok = f1 < C.nf;
-    float t2[FT], kq[FT];
+    float t2[FT], kq[FT], ik[FT];
 #pragma unroll
     for (int q = 0; q < FT; ++q) {
       t2[q] = f1 + q < C.nf ? C.k2[f1 + q] : 0.0f;
       kq[q] = C.k[min(f1 + q, C.nf - 1)];
+      ik[q] = __frcp_rn(kq[q]);  // (frequencies are > 0)
     }
     const float khi = f_ok ? C.khi[f1] : 0.0f, klo = f_ok ? C.klo[f1] : 0.0f;
     constexpr int NA = FT * kAcc;
@@ -533,14 +534,41 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
       if (valid) {
         const unsigned below = (1u << lane) - 1u;
         const int at = ser ? before_a + __popc(ma & below) : n_a + before_b + __popc(mb & below);
-        float c[kSer];
-        series_coeffs(au, av, c);
+        float4 r0;
+        float2 r3;
+        if (ser) {
+          float c[kSer];
+          series_coeffs(au, av, c);
+          r0 = make_float4(c[0], c[1], c[2], c[3]);
+          r3 = make_float2(c[4], c[5]);
+        } else {
+          // the direct form as sin(k A) sin(k B) / (k^2 A B) with A >= B the
+          // two arguments' sizes (sinc is even) and the reciprocals staged,
+          // so that a term takes no division; a B whose factor stays in the
+          // one-factor series' range (|k B| < 0.5) takes that series in t
+          // (through x^8, tail below 3e-11) and flags the ray by A > 0
+          float A = fabsf(au), B = fabsf(av);
+          if (B > A) {
+            const float x = A;
+            A = B;
+            B = x;
+          }
+          if (B * C.kmax < 0.5f) {
+            const float B2 = B * B, B4 = B2 * B2;
+            r0 = make_float4(-B2 * (1.0f / 6.0f), B4 * (1.0f / 120.0f), -B4 * B2 * (1.0f / 5040.0f),
+                             B4 * B4 * (1.0f / 362880.0f));
+            r3 = make_float2(A, __frcp_rn(A));
+          } else {
+            r0 = make_float4(__frcp_rn(A * B), 0.0f, 0.0f, 0.0f);
+            r3 = make_float2(-A, B);
+          }
+        }
         float rs, rc;
         __sincosf(rev_phase(C.dkhi, C.dklo, dh, dl) * kTwoPi, &rs, &rc);
-        s_ray[0][at] = make_float4(c[0], c[1], c[2], c[3]);
+        s_ray[0][at] = r0;
         s_ray[1][at] = make_float4(V[0], V[1], V[2], V[3]);
         s_ray[2][at] = make_float4(dh, dl, rc, -rs);
-        s_arg[at] = ser ? make_float2(c[4], c[5]) : make_float2(au, av);
+        s_arg[at] = r3;
       }
       __syncthreads();
       // ---- FT frequencies per thread over the staged rays ---------------
@@ -569,15 +597,26 @@ __global__ void __launch_bounds__(kPoThreads, PE_PO_MINB)
               }
             } else {
               for (int j = j0; j < jn; j += RL) {
-                const float4 r1 = s_ray[1][j], r2 = s_ray[2][j];
+                const float4 r0 = s_ray[0][j], r1 = s_ray[1][j], r2 = s_ray[2][j];
                 const float2 arg = s_arg[j];
                 float sn, cs;
                 __sincosf(rev_phase(khi, klo, r2.x, r2.y) * kTwoPi, &sn, &cs);
                 float pr = cs, pi = -sn;
+                if (arg.x > 0.0f) {  // sinc(k B) by its series (a warp shares the ray when FL = 32)
 #pragma unroll
-                for (int q = 0; q < FT; ++q) {
-                  const float sc = sincf_(kq[q] * arg.x) * sincf_(kq[q] * arg.y);
-                  rot_term(sc, r1, r2, pr, pi, b + q * kAcc);
+                  for (int q = 0; q < FT; ++q) {
+                    const float t = t2[q];
+                    const float sb = fmaf(fmaf(fmaf(fmaf(r0.w, t, r0.z), t, r0.y), t, r0.x), t, 1.0f);
+                    const float sc = sb * __sinf(kq[q] * arg.x) * (arg.y * ik[q]);
+                    rot_term(sc, r1, r2, pr, pi, b + q * kAcc);
+                  }
+                } else {
+#pragma unroll
+                  for (int q = 0; q < FT; ++q) {
+                    const float sc =
+                        __sinf(kq[q] * -arg.x) * __sinf(kq[q] * arg.y) * (r0.x * ik[q] * ik[q]);
+                    rot_term(sc, r1, r2, pr, pi, b + q * kAcc);
+                  }
                 }
               }
             }

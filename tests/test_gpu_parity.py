@@ -311,6 +311,14 @@ def test_po_field_synthetic_plate_many_freqs(th_deg, nu, ka_range):
     # the hardware sincos adds up to 2^-21.4; near a pattern null that shows as
     # a few 1e-4 of the 1e-3 floor.
     assert field_err(E, Eo).max() < 1e-3
+    # In backscatter (ks = -k) a bounce-1 record's phase path is 2 k . p,
+    # formed from k and p: its path word is not read, so the same field
+    # comes back with every path set to NaN.
+    assert np.array_equal(f32(w), -f32(d))
+    h.path.fill_(float("nan"))
+    E2 = _cplx(api.po_field(h, 1, n, f32(w)[None], freqs))[0]
+    api.stream_check()
+    assert np.array_equal(E2, E)
 
 
 @pytest.mark.parametrize("grid", ["uniform", "uniform-5", "random", "geometric"])
