@@ -360,13 +360,13 @@ MARCH_BYTES_PER_HIT = 76
 # sphere workload through pe_rcs_sweep; profiles/march_kernel_sphere_batch.md:
 # 91.1 MB over 6,332,964 queries), valid only for the sources it was taken on
 # (their SHA-256 prefixes); scaled to a full launch by the number of queries.
-_SWEEP_SOURCES = {"include/pointemray.h": "f6d55b40007929cd",
+_SWEEP_SOURCES = {"include/pointemray.h": "867cc444e32855cc",
                   "paper_2408_15583_gb300/csrc/pe_internal.cuh": "2dc3ec4e588ae1ce",
                   "paper_2408_15583_gb300/csrc/sweep.cu": "9f2bcf7b228eaa30"}
 MARCH_NCU_TRAFFIC = {"bytes_per_query": 14.39,
                      "sources": dict(_SWEEP_SOURCES, **{
-                         "paper_2408_15583_gb300/csrc/trace.cu": "9a00f34e95823c9b",
-                         "paper_2408_15583_gb300/csrc/aggregate.cu": "55364132016cd83f"})}
+                         "paper_2408_15583_gb300/csrc/trace.cu": "04fbdf628ec696d9",
+                         "paper_2408_15583_gb300/csrc/aggregate.cu": "a2f21815ee049028"})}
 
 # DRAM bytes (read + write) per ray slot of po_rot_kernel from one ncu capture
 # of the sweep's field sum on one 8-angle sphere batch

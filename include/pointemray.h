@@ -98,7 +98,7 @@ typedef struct {
   int32_t edge_mode;
 } pe_params;
 
-/* Aggregated splat geometry (Alg. 3 lines 1-3).  One caller-allocated device
+/* Aggregated splat geometry (Alg. 3, aggregation steps).  One caller-allocated device
  * blob holds, for each view v (pixel offset off_v = sum of earlier W*H):
  *   splat_cr[off_v + p] = {cx, cy, cz, R}   (R = 0: no splat owned here)
  *   splat_nf[off_v + p] = {nx, ny, nz, count}
@@ -297,7 +297,7 @@ pe_status pe_build_gfb(const pe_view *views, int32_t n_views,
                        uint8_t *gfb_mask_dev, uint64_t *keys_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
- * a4  GFB aggregation: edge filter, voxel fusion, splats (Alg. 3 lines 1-3,
+ * a4  GFB aggregation: edge filter, voxel fusion, splats (Alg. 3, aggregation steps,
  *     Eq. 22).
  * ------------------------------------------------------------------------- */
 
@@ -333,7 +333,7 @@ pe_status pe_aggregate_views(const pe_view *views, int32_t n_views,
                              pe_geom *out, void *stream);
 
 /* ---------------------------------------------------------------------------
- * a5  GFB-assisted multiple-bounce computation (Alg. 3 lines 4-9, Eq. 2-4,
+ * a5  GFB-assisted multiple-bounce computation (Alg. 3, bounce loop, Eq. 2-4,
  *     Eq. 23) and the visibility test Psi (Eq. 14).
  * ------------------------------------------------------------------------- */
 

@@ -10,8 +10,8 @@ the same result bit for bit: ``oracle_grid.h``):
   a1  view / ray screen from (theta, phi)          Sec. III-A (uvwo frame)
   a2  PRI: nearest point per pixel ray (GFB)        Alg. 1, surfel or tube
   a3  GFB resolve (depth, oriented normal, mask)    Alg. 1 output, Eq. 16 frame
-  a4  edge filter + 256^3 voxel fusion + Eq. 22     Alg. 3 lines 1-2
-  a5  bounce tracing with Eq. 23 overlap + epsilon  Alg. 3 lines 4-9, Eq. 2-4
+  a4  edge filter + 256^3 voxel fusion + Eq. 22     Alg. 3, aggregation steps
+  a5  bounce tracing with Eq. 23 overlap + epsilon  Alg. 3, bounce loop, Eq. 2-4
   a6  PO field sum (FP64, Neumaier)                 Eq. 5-14
   a7  monostatic RCS sigma = k^2/pi |e . Sigma|^2   Eq. 14 + far field
 Two arithmetic modes: ``fp32`` (geometry in FP32 with a fixed op order: the
@@ -239,7 +239,7 @@ def gfb_topk(pos: np.ndarray, view: View, delta: float, K: int, mode: str = "fp3
 
 
 # ----------------------------------------------------------------------------
-# a4: aggregation (Alg. 3 lines 1-2, Eq. 22)
+# a4: aggregation (Alg. 3, aggregation steps, Eq. 22)
 # ----------------------------------------------------------------------------
 
 @dataclass

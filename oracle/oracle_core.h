@@ -13,7 +13,7 @@
  *   - screen / uvwo frame: Sec. III-A, around Eq. 15-16;
  *   - point-ray intersection (GFB): Alg. 1 (screen-based PRI), surfel reading
  *     of "assigning finite surface areas to points" (Sec. III-A intro);
- *   - edge filter, voxel fusion, splat radius: Alg. 3 lines 1-2, Eq. 22;
+ *   - edge filter, voxel fusion, splat radius: Alg. 3, aggregation steps, Eq. 22;
  *   - ray-splat intersection with overlap sphere and normal blend: Eq. 23,
  *     Fig. 4; minimum travel distance epsilon: Sec. III-B;
  *   - reflection: Eq. 2-4;  visibility Psi: Sec. II-C, Eq. 14.
@@ -232,7 +232,7 @@ static void SFX(gfb_topk)(const or_view *vin, const float *pos, int64_t n, doubl
 }
 
 /* ---------------------------------------------------------------------------
- * Alg. 3 lines 1-2: edge filtering, voxel fusion, conversion to splats.
+ * Alg. 3, aggregation steps: edge filtering, voxel fusion, conversion to splats.
  * ------------------------------------------------------------------------- */
 
 /* Edge rule (the paper names a Canny operator without thresholds): a hit
@@ -521,7 +521,7 @@ static int64_t SFX(aggregate)(int nv, const or_view *views, const double *depth_
 }
 
 /* ---------------------------------------------------------------------------
- * Alg. 3 lines 4-9: bounce tracing against splats, Eq. 23 overlap selection.
+ * Alg. 3, bounce loop: bounce tracing against splats, Eq. 23 overlap selection.
  * ------------------------------------------------------------------------- */
 
 typedef struct {

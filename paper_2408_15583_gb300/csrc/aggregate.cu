@@ -1,4 +1,4 @@
-// a4: GFB aggregation (Alg. 3 lines 1-3): edge filter, voxel fusion, Eq. 22
+// a4: GFB aggregation (Alg. 3, aggregation steps): edge filter, voxel fusion, Eq. 22
 // splat radius, owner-pixel placement, and the bounding pyramids the march
 // uses in place of the paper's splat acceleration structure.
 //

@@ -1,4 +1,4 @@
-// a5: GFB-assisted multiple-bounce computation (Alg. 3 lines 4-9).
+// a5: GFB-assisted multiple-bounce computation (Alg. 3, bounce loop).
 //
 // Rays march through the aggregated splats of every view.  Each splat lives
 // at its owner pixel of one view, and every view keeps a pyramid of

@@ -80,7 +80,7 @@ C_MUTANTS = [
      "while (at > 0 && ka[at - 1] > a) {",
      "while (at > 0 && ka[at - 1] < a) {",
      [lambda g: P.test_alg1_finite_k_hand_case("fp32")]),
-    # Alg. 3 lines 1-2: edge rule, Canny, fusion, Eq. 22
+    # Alg. 3, aggregation steps: edge rule, Canny, fusion, Eq. 22
     ("edge rule dropped", "oracle_core.h",
      "if (dt > tauL) return 1;",
      "if (dt > tauL && 0) return 1;",
@@ -114,7 +114,7 @@ C_MUTANTS = [
      "if (s < 2.5) return (1.4142135623730951 * L) * s;",
      "if (s < 2.5) return (1.5 * L) * s;",
      [lambda g: P.test_eq22_radius_values("fp64")]),
-    # Alg. 3 lines 4-9: bounces, Eq. 23, epsilon, Psi
+    # Alg. 3, bounce loop: bounces, Eq. 23, epsilon, Psi
     ("Eq. 4: reflection sign", "oracle_core.h",
      "for (int k = 0; k < 3; ++k) out[k] = a[k] - s * n[k];",
      "for (int k = 0; k < 3; ++k) out[k] = a[k] + s * n[k];",
