@@ -375,7 +375,7 @@ MARCH_NCU_TRAFFIC = {"bytes_per_query": 14.39,
 # (angles x W x H).
 PO_NCU_TRAFFIC = {"bytes_per_slot": 13.81,
                   "sources": dict(_SWEEP_SOURCES, **{
-                      "paper_2408_15583_gb300/csrc/po.cu": "f9b1d7b1945d56c4"})}
+                      "paper_2408_15583_gb300/csrc/po.cu": "4eb889207db41b89"})}
 
 
 def _traffic_valid(rec):

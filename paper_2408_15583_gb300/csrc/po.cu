@@ -209,7 +209,8 @@ __device__ __forceinline__ bool ray_factors(const pe_hits &h, int64_t slot, cons
 __device__ __forceinline__ void add_term(float kf, float khi, float klo, float au, float av,
                                          float dhi, float dlo, const float V[4], float b[kAcc]) {
   // the common case, both arguments small, as one branch: the product of the
-  // two Taylor series of sin(x)/x in x^2 (through x^8, truncation < 3e-11)
+  // two Taylor series of sin(x)/x in x^2 (each through x^8, truncation
+  // < 2.5e-11 per factor, < 5e-11 for the product)
   const float xa = kf * au, xb = kf * av;
   float s;
   if (fmaxf(fabsf(xa), fabsf(xb)) < 0.5f) {
