@@ -386,6 +386,12 @@ def rcs_sweep(args: SweepArgs, pos: torch.Tensor, nrm: torch.Tensor, rad: torch.
     """Returns (E [A][F][2][3][2] f64, sigma [A][F][2][2] f64) on the device."""
     s = args.c
     dev = pos.device
+    o = getattr(args, "order", None)
+    if o is not None and not (o.dtype == torch.int32 and o.dim() == 1 and o.is_contiguous()
+                              and o.numel() == pos.shape[0] and o.device == dev):
+        # the library reads n_points entries through the raw pointer
+        raise ValueError("point order: a contiguous int32 tensor with one entry per point, "
+                         "on the points' device")
     nbytes = args.workspace_bytes()
     if nbytes == 0:
         raise ValueError("invalid sweep")

@@ -80,6 +80,25 @@ def test_sweep_workspace_two_lanes(lib):
     assert ws(0, 64) == 0
 
 
+def test_sweep_point_order_checked_before_the_call(lib):
+    # The library reads one order entry per point through a raw pointer, so
+    # the binding refuses an order of the wrong type, size or layout before
+    # it calls anything.
+    from paper_2408_15583_gb300 import api
+    import numpy as np
+    import torch
+
+    args = api.SweepArgs(np.full(4, 90.0), np.linspace(0, 90, 4), 64, 64, [0.0, 0.0, 0.0], 1.0,
+                         np.linspace(8e9, 12e9, 8), 2)
+    pos = torch.zeros(10, 3)
+    for bad in (torch.arange(9, dtype=torch.int32),              # too short
+                torch.arange(10, dtype=torch.int64),             # wrong type
+                torch.arange(20, dtype=torch.int32)[::2]):       # not contiguous
+        args.set_point_order(bad)
+        with pytest.raises(ValueError, match="point order"):
+            api.rcs_sweep(args, pos, pos, pos[:, 0], None, api.PeParams())
+
+
 def test_workspace_queries(lib):
     from paper_2408_15583_gb300 import api
     vs = [api.view_from_angles(60, 45 + 90 * i, [0, 0, 0], 1.0, 512, 512) for i in range(8)]
