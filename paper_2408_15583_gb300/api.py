@@ -186,6 +186,10 @@ def order_points(pos: torch.Tensor, out: Optional[torch.Tensor] = None, stream=N
     32^3 grid, for SweepArgs.set_point_order."""
     lib = _lib()
     n = int(pos.shape[0])
+    if out is not None and not (out.dtype == torch.int32 and out.dim() == 1 and out.is_contiguous()
+                                and out.numel() == n and out.device == pos.device):
+        raise ValueError("order_points: out must be a contiguous int32 tensor with one entry "
+                         "per point, on the points' device")
     ws = workspace(lib.pe_order_points_workspace(n), pos.device)
     order = out if out is not None else torch.empty(n, dtype=torch.int32, device=pos.device)
     check(lib.pe_order_points(_p(pos), n, _p(ws), ws.numel(), _p(order), _s(stream)),

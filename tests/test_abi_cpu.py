@@ -97,6 +97,8 @@ def test_sweep_point_order_checked_before_the_call(lib):
         args.set_point_order(bad)
         with pytest.raises(ValueError, match="point order"):
             api.rcs_sweep(args, pos, pos, pos[:, 0], None, api.PeParams())
+        with pytest.raises(ValueError, match="order_points"):
+            api.order_points(pos, out=bad)
 
 
 def test_workspace_queries(lib):
