@@ -36,6 +36,14 @@ def _s(stream):
     return C.c_void_p(st.cuda_stream)
 
 
+def _check_out(t: Optional[torch.Tensor], dtype, numel: int, device, what: str):
+    """An output the library writes through a raw pointer: refused unless it
+    is a contiguous tensor of the right type, size and device."""
+    if t is not None and not (t.dtype == dtype and t.is_contiguous() and t.numel() == numel
+                              and t.device == torch.device(device)):
+        raise ValueError(f"{what}: a contiguous {dtype} tensor of {numel} elements on {device}")
+
+
 def workspace(nbytes: int, device) -> torch.Tensor:
     """A caller-owned scratch buffer, 256-byte aligned."""
     t = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
@@ -286,6 +294,7 @@ def po_field(hits: Hits, n_groups: int, rays_per_group: int, ks: np.ndarray,
     ks = np.ascontiguousarray(ks, dtype=np.float32).reshape(n_groups, 3)
     fr = np.ascontiguousarray(freqs_hz, dtype=np.float64).ravel()
     dev = hits.M.device
+    _check_out(out, torch.float64, n_groups * fr.shape[0] * 12, dev, "po_field: out")
     E = out if out is not None else torch.empty((n_groups, fr.shape[0], 2, 3, 2),
                                                 dtype=torch.float64, device=dev)
     ws_bytes = _lib().pe_po_workspace(n_groups, rays_per_group, fr.shape[0])
@@ -396,6 +405,8 @@ def rcs_sweep(args: SweepArgs, pos: torch.Tensor, nrm: torch.Tensor, rad: torch.
         # the library reads n_points entries through the raw pointer
         raise ValueError("point order: a contiguous int32 tensor with one entry per point, "
                          "on the points' device")
+    _check_out(E, torch.float64, s.n_angles * s.n_freq * 12, dev, "rcs_sweep: E")
+    _check_out(sigma, torch.float64, s.n_angles * s.n_freq * 4, dev, "rcs_sweep: sigma")
     nbytes = args.workspace_bytes()
     if nbytes == 0:
         raise ValueError("invalid sweep")

@@ -101,6 +101,31 @@ def test_sweep_point_order_checked_before_the_call(lib):
             api.order_points(pos, out=bad)
 
 
+def test_outputs_checked_before_the_call(lib):
+    # Outputs the library writes through raw pointers: the binding refuses a
+    # wrong type, size or layout before any call.
+    from paper_2408_15583_gb300 import api
+    import numpy as np
+    import torch
+
+    h = api.alloc_hits(16, 1, "cpu", ids=False)
+    ks = np.array([[0.0, 0.0, 1.0]], np.float32)
+    fr = np.array([8e9, 9e9])
+    for bad in (torch.empty(1, 2, 2, 3, 2, dtype=torch.float32),      # wrong type
+                torch.empty(1, 3, 2, 3, 2, dtype=torch.float64)):     # wrong size
+        with pytest.raises(ValueError, match="po_field: out"):
+            api.po_field(h, 1, 16, ks, fr, out=bad)
+    args = api.SweepArgs(np.full(4, 90.0), np.linspace(0, 90, 4), 64, 64, [0.0, 0.0, 0.0], 1.0,
+                         fr, 2)
+    pos = torch.zeros(10, 3)
+    with pytest.raises(ValueError, match="rcs_sweep: E"):
+        api.rcs_sweep(args, pos, pos, pos[:, 0], None, api.PeParams(),
+                      E=torch.empty(4, 2, 2, 3, 2, dtype=torch.float64)[:, ::2])
+    with pytest.raises(ValueError, match="rcs_sweep: sigma"):
+        api.rcs_sweep(args, pos, pos, pos[:, 0], None, api.PeParams(),
+                      sigma=torch.empty(4, 2, 2, dtype=torch.float64))
+
+
 def test_workspace_queries(lib):
     from paper_2408_15583_gb300 import api
     vs = [api.view_from_angles(60, 45 + 90 * i, [0, 0, 0], 1.0, 512, 512) for i in range(8)]
